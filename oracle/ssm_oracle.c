@@ -1,0 +1,355 @@
+/*
+ * ssm_oracle.c -- plain, slow FP64 CPU oracle for the simplified string method of
+ * Heistracher et al., "GPU-accelerated atomistic energy barrier calculations of skyrmion
+ * annihilations" (arXiv:1804.07135).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the benchmark's CPU-baseline leg
+ * may load this library.  It shares no code, header or table with the CUDA path; the two meet only
+ * through the seeded inputs that the tests hand to both.
+ *
+ * Reduced units (stated once, used everywhere below):
+ *   - energies are in units of the exchange constant J's unit; lengths in lattice constants a;
+ *   - spins are the unit vectors s_i (the paper's \hat s_i);
+ *   - the field is h_i = -dE/ds_i, i.e. mu0 |S| H_eff of Eq. 2 with mu0|S| absorbed;
+ *   - the dipole strength is w = mu0 |S|^2 / (4 pi a^3), so the last term of Eq. 1 reads
+ *     -w sum_{i<j} [3 (s_i.r)(s_j.r) - s_i.s_j] / r^3 with r in lattice units.
+ * Lattice: simple cubic, nx*ny*nz sites, open (free) boundaries (Sec. II).  Site index
+ * i = (z*ny + y)*nx + x; spin arrays are [site][3] (x,y,z components); a string is [image][site][3].
+ *
+ * Parity status: every function here is pinned by a CPU test against closed forms, finite
+ * differences or geometry, except or_string_run's barrier value, whose only check beyond the pinned
+ * parts it is composed of is sanity (barrier >= 0): "parity unpinned" for the barrier number itself.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct {
+    int nx, ny, nz;
+    double J, D, K, w;
+} or_model;
+
+static int site(const or_model* m, int x, int y, int z) { return (z * m->ny + y) * m->nx + x; }
+
+/* Eq. 7: dipole-dipole tensor D(r) = (1/4pi) (3 r r^T / r^5 - I / r^3) for r != 0, returned as its
+ * six unique entries (xx, yy, zz, xy, xz, yz). */
+void or_dipole_tensor(double rx, double ry, double rz, double out[6]) {
+    const double r2 = rx * rx + ry * ry + rz * rz;
+    const double r = sqrt(r2);
+    const double r3 = r2 * r, r5 = r3 * r2;
+    const double c = 1.0 / (4.0 * M_PI);
+    out[0] = c * (3.0 * rx * rx / r5 - 1.0 / r3);
+    out[1] = c * (3.0 * ry * ry / r5 - 1.0 / r3);
+    out[2] = c * (3.0 * rz * rz / r5 - 1.0 / r3);
+    out[3] = c * (3.0 * rx * ry / r5);
+    out[4] = c * (3.0 * rx * rz / r5);
+    out[5] = c * (3.0 * ry * rz / r5);
+}
+
+/* Eq. 1, term by term, straight from the Hamiltonian (not from the field).
+ * <i,j> runs over nearest-neighbour bonds, each unordered bond once; r_ij points from i to j.
+ *   exchange:  -J s_i.s_j
+ *   DMI:        D (r_ij x z).(s_i x s_j)
+ *   anisotropy: -K (s_i.z)^2
+ *   dipole:     -w [3 (s_i.r)(s_j.r) - s_i.s_j] / r^3 over unordered pairs i<j (the paper's
+ *               1/(8pi) over ordered pairs i != j is 1/(4pi) over unordered ones).
+ * out = {E_exchange, E_dmi, E_anisotropy, E_dipole, E_total}. */
+void or_energy_terms(const or_model* m, const double* s, double out[5]) {
+    const int N = m->nx * m->ny * m->nz;
+    double e_exc = 0, e_dmi = 0, e_ani = 0, e_dip = 0;
+    static const int dirs[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    for (int z = 0; z < m->nz; ++z)
+        for (int y = 0; y < m->ny; ++y)
+            for (int x = 0; x < m->nx; ++x) {
+                const int i = site(m, x, y, z);
+                const double* si = s + 3 * i;
+                for (int d = 0; d < 3; ++d) {
+                    const int xj = x + dirs[d][0], yj = y + dirs[d][1], zj = z + dirs[d][2];
+                    if (xj >= m->nx || yj >= m->ny || zj >= m->nz) continue; /* open boundary */
+                    const double* sj = s + 3 * site(m, xj, yj, zj);
+                    e_exc += -m->J * (si[0] * sj[0] + si[1] * sj[1] + si[2] * sj[2]);
+                    /* r_ij x z for r_ij = (rx, ry, rz): (ry, -rx, 0) */
+                    const double a0 = (double)dirs[d][1], a1 = -(double)dirs[d][0], a2 = 0.0;
+                    const double c0 = si[1] * sj[2] - si[2] * sj[1];
+                    const double c1 = si[2] * sj[0] - si[0] * sj[2];
+                    const double c2 = si[0] * sj[1] - si[1] * sj[0];
+                    e_dmi += m->D * (a0 * c0 + a1 * c1 + a2 * c2);
+                }
+                e_ani += -m->K * si[2] * si[2];
+            }
+    if (m->w != 0.0) {
+        for (int i = 0; i < N; ++i) {
+            const int xi = i % m->nx, yi = (i / m->nx) % m->ny, zi = i / (m->nx * m->ny);
+            const double* si = s + 3 * i;
+            for (int j = i + 1; j < N; ++j) {
+                const int xj = j % m->nx, yj = (j / m->nx) % m->ny, zj = j / (m->nx * m->ny);
+                const double rx = xj - xi, ry = yj - yi, rz = zj - zi;
+                const double r = sqrt(rx * rx + ry * ry + rz * rz);
+                const double ux = rx / r, uy = ry / r, uz = rz / r;
+                const double* sj = s + 3 * j;
+                const double sir = si[0] * ux + si[1] * uy + si[2] * uz;
+                const double sjr = sj[0] * ux + sj[1] * uy + sj[2] * uz;
+                const double sij = si[0] * sj[0] + si[1] * sj[1] + si[2] * sj[2];
+                e_dip += -m->w * (3.0 * sir * sjr - sij) / (r * r * r);
+            }
+        }
+    }
+    out[0] = e_exc;
+    out[1] = e_dmi;
+    out[2] = e_ani;
+    out[3] = e_dip;
+    out[4] = e_exc + e_dmi + e_ani + e_dip;
+}
+
+/* Table of Eq. 7 at every lattice offset (dx, dy, dz), |dx|<nx, |dy|<ny, |dz|<nz; entry 0 at the
+ * origin (no self term).  Layout [dz+nz-1][dy+ny-1][dx+nx-1][6].  Caller frees. */
+static double* dipole_table(const or_model* m) {
+    const int Lx = 2 * m->nx - 1, Ly = 2 * m->ny - 1, Lz = 2 * m->nz - 1;
+    double* t = (double*)calloc((size_t)Lx * Ly * Lz * 6, sizeof(double));
+    if (!t) return NULL;
+    for (int dz = -(m->nz - 1); dz <= m->nz - 1; ++dz)
+        for (int dy = -(m->ny - 1); dy <= m->ny - 1; ++dy)
+            for (int dx = -(m->nx - 1); dx <= m->nx - 1; ++dx) {
+                if (dx == 0 && dy == 0 && dz == 0) continue;
+                double* e = t + 6 * (((size_t)(dz + m->nz - 1) * Ly + (dy + m->ny - 1)) * Lx + (dx + m->nx - 1));
+                or_dipole_tensor(dx, dy, dz, e);
+            }
+    return t;
+}
+
+/* Eqs. 2-6: the effective field h_i = -dE/ds_i of one image.
+ *   exchange   (Eq. 3): J sum over the (up to 6) nearest neighbours of s_j
+ *   DMI        (Eq. 4): -D ( s_z^{i+x} - s_z^{i-x},  s_z^{i+y} - s_z^{i-y},
+ *                            -s_x^{i+x} + s_x^{i-x} - s_y^{i+y} + s_y^{i-y} ), missing neighbours 0
+ *   anisotropy (Eq. 5): 2 K (s_i.z) z
+ *   dipole     (Eq. 6): 4 pi w sum_{j != i} D(r_ij) s_j with D of Eq. 7, summed directly (O(N^2)).
+ * `table` is the Eq. 7 table of dipole_table() (may be NULL when w == 0). */
+static void field_one(const or_model* m, const double* table, const double* s, double* h) {
+    const int nx = m->nx, ny = m->ny, nz = m->nz, N = nx * ny * nz;
+#define S(xx, yy, zz, c) \
+    (((xx) < 0 || (xx) >= nx || (yy) < 0 || (yy) >= ny || (zz) < 0 || (zz) >= nz) ? 0.0 : s[3 * site(m, xx, yy, zz) + (c)])
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                const int i = site(m, x, y, z);
+                double hx = 0, hy = 0, hz = 0;
+                /* Eq. 3 */
+                for (int c = 0; c < 3; ++c) {
+                    const double sum = S(x + 1, y, z, c) + S(x - 1, y, z, c) + S(x, y + 1, z, c) + S(x, y - 1, z, c) +
+                                       S(x, y, z + 1, c) + S(x, y, z - 1, c);
+                    if (c == 0) hx += m->J * sum;
+                    if (c == 1) hy += m->J * sum;
+                    if (c == 2) hz += m->J * sum;
+                }
+                /* Eq. 4 */
+                hx += -m->D * (S(x + 1, y, z, 2) - S(x - 1, y, z, 2));
+                hy += -m->D * (S(x, y + 1, z, 2) - S(x, y - 1, z, 2));
+                hz += -m->D * (-S(x + 1, y, z, 0) + S(x - 1, y, z, 0) - S(x, y + 1, z, 1) + S(x, y - 1, z, 1));
+                /* Eq. 5 */
+                hz += 2.0 * m->K * s[3 * i + 2];
+                h[3 * i + 0] = hx;
+                h[3 * i + 1] = hy;
+                h[3 * i + 2] = hz;
+            }
+#undef S
+    if (m->w != 0.0 && table) {
+        /* Eq. 6 */
+        const int Lx = 2 * nx - 1, Ly = 2 * ny - 1;
+        const double pref = 4.0 * M_PI * m->w;
+        for (int i = 0; i < N; ++i) {
+            const int xi = i % nx, yi = (i / nx) % ny, zi = i / (nx * ny);
+            double ax = 0, ay = 0, az = 0;
+            for (int j = 0; j < N; ++j) {
+                if (j == i) continue;
+                const int xj = j % nx, yj = (j / nx) % ny, zj = j / (nx * ny);
+                const double* d = table + 6 * (((size_t)(zj - zi + nz - 1) * Ly + (yj - yi + ny - 1)) * Lx + (xj - xi + nx - 1));
+                const double* sj = s + 3 * j;
+                ax += d[0] * sj[0] + d[3] * sj[1] + d[4] * sj[2];
+                ay += d[3] * sj[0] + d[1] * sj[1] + d[5] * sj[2];
+                az += d[4] * sj[0] + d[5] * sj[1] + d[2] * sj[2];
+            }
+            h[3 * i + 0] += pref * ax;
+            h[3 * i + 1] += pref * ay;
+            h[3 * i + 2] += pref * az;
+        }
+    }
+}
+
+/* Eqs. 2-6 for `n_images` images stored back to back ([image][site][3]). Returns 0, or -1 when out of memory. */
+int or_field(const or_model* m, int n_images, const double* s, double* h) {
+    const int N = m->nx * m->ny * m->nz;
+    double* table = NULL;
+    if (m->w != 0.0) {
+        table = dipole_table(m);
+        if (!table) return -1;
+    }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int k = 0; k < n_images; ++k) field_one(m, table, s + (size_t)3 * N * k, h + (size_t)3 * N * k);
+    free(table);
+    return 0;
+}
+
+/* Only the dipole part of Eq. 6 (exchange, DMI and anisotropy left out), for one image. */
+int or_dipole_field(const or_model* m, const double* s, double* h) {
+    or_model d = *m;
+    d.J = 0.0;
+    d.D = 0.0;
+    d.K = 0.0;
+    return or_field(&d, 1, s, h);
+}
+
+/* Eq. 8: E = -(1/2) sum_i h_i . s_i (exact for Eq. 1, which is a homogeneous quadratic in the spins). */
+double or_energy_from_field(int n_sites, const double* s, const double* h) {
+    double e = 0.0;
+    for (int i = 0; i < 3 * n_sites; ++i) e += h[i] * s[i];
+    return -0.5 * e;
+}
+
+/* Eq. 10 with the potential force of Eq. 13 (Appendix A): one explicit step of length dt along
+ * F = h - (s.h) s (the component of h perpendicular to s; the LLG prefactors are absorbed into dt),
+ * followed by renormalisation to unit length, at every site. */
+void or_step(int n_sites, double dt, const double* h, double* s) {
+    for (int i = 0; i < n_sites; ++i) {
+        double* si = s + 3 * i;
+        const double* hi = h + 3 * i;
+        const double sh = si[0] * hi[0] + si[1] * hi[1] + si[2] * hi[2];
+        double u[3];
+        for (int c = 0; c < 3; ++c) u[c] = si[c] + dt * (hi[c] - sh * si[c]);
+        const double n = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        for (int c = 0; c < 3; ++c) si[c] = u[c] / n;
+    }
+}
+
+/* Eqs. 11-12 and the interpolation onto the uniform grid (Sec. III).
+ *   s_0 = 0, s_k = s_{k-1} + ||phi*_k - phi*_{k-1}|| (Euclidean over all 3N components),
+ *   alpha*_k = s_k / s_{K-1}, targets alpha_k = k/(K-1);
+ *   for 0 < k < K-1: j = largest index with alpha*_j <= alpha_k, t = (alpha_k - alpha*_j) /
+ *   (alpha*_{j+1} - alpha*_j), phi_k = per-site normalise((1-t) phi*_j + t phi*_{j+1});
+ *   phi_0 and phi_{K-1} are kept; if s_{K-1} == 0 the path is returned unchanged.
+ * phi_star and phi are [K][N][3] and must not overlap.  alpha_out (K entries, may be NULL)
+ * receives alpha*. */
+void or_reparam(int K, int n_sites, const double* phi_star, double* phi, double* alpha_out) {
+    const size_t M = (size_t)3 * n_sites;
+    double* sk = (double*)malloc(sizeof(double) * K);
+    sk[0] = 0.0;
+    for (int k = 1; k < K; ++k) {
+        double d2 = 0.0;
+        for (size_t c = 0; c < M; ++c) {
+            const double d = phi_star[k * M + c] - phi_star[(k - 1) * M + c];
+            d2 += d * d;
+        }
+        sk[k] = sk[k - 1] + sqrt(d2);
+    }
+    memcpy(phi, phi_star, sizeof(double) * M * K);
+    if (sk[K - 1] == 0.0) {
+        if (alpha_out)
+            for (int k = 0; k < K; ++k) alpha_out[k] = 0.0;
+        free(sk);
+        return;
+    }
+    for (int k = 0; k < K; ++k) sk[k] = sk[k] / sk[K - 1];
+    if (alpha_out) memcpy(alpha_out, sk, sizeof(double) * K);
+    for (int k = 1; k < K - 1; ++k) {
+        const double ak = (double)k / (double)(K - 1);
+        int j = 0;
+        for (int i = 0; i <= K - 2; ++i)
+            if (sk[i] <= ak) j = i;
+        const double t = (ak - sk[j]) / (sk[j + 1] - sk[j]);
+        for (int i = 0; i < n_sites; ++i) {
+            double u[3];
+            for (int c = 0; c < 3; ++c) u[c] = (1.0 - t) * phi_star[j * M + 3 * i + c] + t * phi_star[(j + 1) * M + 3 * i + c];
+            const double n = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+            for (int c = 0; c < 3; ++c) phi[k * M + 3 * i + c] = u[c] / n;
+        }
+    }
+    free(sk);
+}
+
+/* The string iteration of Sec. III: n_iter times { every image takes one step (Eq. 10/13) on its
+ * own field (Eqs. 2-7); then the images are reparametrised to equal arc length (Eqs. 11-12) }.
+ * `phi` ([K][N][3]) is updated in place.  When `energies` is not NULL it receives the energy
+ * (Eq. 8) of every image of the final string, from a fresh field evaluation.
+ * Returns 0, or -1 when out of memory. */
+int or_string_run(const or_model* m, int K, int n_iter, double dt, double* phi, double* energies) {
+    const int N = m->nx * m->ny * m->nz;
+    const size_t M = (size_t)3 * N;
+    double* table = NULL;
+    if (m->w != 0.0) {
+        table = dipole_table(m);
+        if (!table) return -1;
+    }
+    double* h = (double*)malloc(sizeof(double) * M * K);
+    double* star = (double*)malloc(sizeof(double) * M * K);
+    if (!h || !star) {
+        free(table);
+        free(h);
+        free(star);
+        return -1;
+    }
+    for (int it = 0; it < n_iter; ++it) {
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int k = 0; k < K; ++k) {
+            field_one(m, table, phi + k * M, h + k * M);
+            or_step(N, dt, h + k * M, phi + k * M);
+        }
+        memcpy(star, phi, sizeof(double) * M * K);
+        or_reparam(K, N, star, phi, NULL);
+    }
+    if (energies) {
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int k = 0; k < K; ++k) {
+            field_one(m, table, phi + k * M, h + k * M);
+            energies[k] = or_energy_from_field(N, phi + k * M, h + k * M);
+        }
+    }
+    free(table);
+    free(h);
+    free(star);
+    return 0;
+}
+
+/* Sec. III: the barrier is the energy of the highest image relative to the first image.  Ties go
+ * to the lowest index. */
+double or_barrier(int K, const double* energies, int* k_max) {
+    int kb = 0;
+    for (int k = 1; k < K; ++k)
+        if (energies[k] > energies[kb]) kb = k;
+    if (k_max) *k_max = kb;
+    return energies[kb] - energies[0];
+}
+
+/* Eq. 1 is linear in (J, D, K, w): out = (dE/dJ, dE/dD, dE/dK, dE/dw) of one image, each the
+ * corresponding term of or_energy_terms evaluated with that constant set to 1. */
+void or_energy_param_grad(const or_model* m, const double* s, double out[4]) {
+    or_model u = *m;
+    u.J = 1.0;
+    u.D = 1.0;
+    u.K = 1.0;
+    u.w = 1.0;
+    double t[5];
+    or_energy_terms(&u, s, t);
+    out[0] = t[0];
+    out[1] = t[1];
+    out[2] = t[2];
+    out[3] = t[3];
+}
+
+/* Threads the OpenMP loops above may use (1 when built without OpenMP). */
+int or_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void or_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
