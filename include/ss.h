@@ -1,0 +1,144 @@
+/*
+ * ss.h -- C ABI of libss: the simplified string method of Heistracher et al. (arXiv:1804.07135)
+ * for atomistic skyrmion annihilation barriers, on one NVIDIA GB300 (sm_103a).
+ *
+ * Model (Sec. II, Eq. 1): classical unit spins s_i on an nx*ny*nz simple cubic lattice with free
+ * (open) boundaries; Hamiltonian = exchange J over nearest-neighbour bonds + interfacial DMI D with
+ * the (r_ij x z).(s_i x s_j) form + uniaxial anisotropy K along z + dipole-dipole coupling.
+ * Reduced units throughout: energies in the unit of J, lengths in lattice constants, the field is
+ * h_i = -dE/ds_i (Eq. 2 with mu0|S| absorbed) and the dipole strength is w = mu0|S|^2/(4 pi a^3).
+ *
+ * One iteration of the string (Sec. III) = for every image: effective field (Eqs. 2-7, the dipole
+ * part as a zero-padded FFT convolution with the tensor of Eq. 7), per-image FP64 energy (Eq. 8),
+ * one explicit projected-descent step s <- normalise(s + dt (h - (s.h) s)) (Eq. 10 with the force of
+ * Eq. 13); then equal-arc-length reparametrisation of the images (Eqs. 11-12, piecewise-linear
+ * interpolation followed by per-site renormalisation; the two end images are kept).
+ *
+ * Conventions shared by every entry point:
+ *   - Return codes only; nothing is thrown across the ABI.  On failure ss_last_error() describes it.
+ *   - Spin/field arrays crossing the ABI are [image][site][3] (x, y, z components), site index
+ *     (z*ny + y)*nx + x, dtype SS_DTYPE_F32 or SS_DTYPE_F64, on the host (on_device = 0) or on the
+ *     context's device (on_device = 1).  They are caller-owned and never retained.
+ *   - All device memory is owned by the context (allocated in ss_create*, freed in ss_destroy).
+ *   - Work is issued on an internal stream that is ordered after, and before, opts.stream (or the
+ *     legacy default stream when opts.stream is NULL).  ss_step is asynchronous; every other call
+ *     that returns data synchronises.  A sticky device error word (non-finite values) is read at
+ *     every synchronising call and reported as SS_ERR_NONFINITE.
+ *   - A context is not thread-safe: calls on one context must not overlap.
+ */
+#ifndef SS_H
+#define SS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ss_ctx ss_ctx; /* opaque; owned by the library */
+
+typedef enum {
+    SS_OK = 0,
+    SS_ERR_INVALID_ARG = 1, /* bad dims, parameters, indices, dtype, or a zero-norm/non-finite spin */
+    SS_ERR_CUDA = 2,        /* a CUDA runtime call failed (message in ss_last_error) */
+    SS_ERR_OOM = 3,         /* device or host allocation failed */
+    SS_ERR_NONFINITE = 4,   /* a NaN/Inf appeared in an energy or arc length on the device */
+    SS_ERR_TIMEOUT = 5,     /* reserved for bounded device waits */
+    SS_ERR_STATE = 6        /* call out of order (e.g. ss_step before any ss_set_path) */
+} ss_status;
+
+enum { SS_DTYPE_F32 = 0, SS_DTYPE_F64 = 1 };
+enum { SS_PREC_FP32 = 0, /* FP32 spins, fields and FFTs; FP64 energies and arc lengths */
+       SS_PREC_FP64 = 1  /* the plain FP64 GPU method: FP64 everywhere */ };
+enum { SS_DIPOLE_OFF = 0, SS_DIPOLE_FFT = 2 };
+
+typedef struct {
+    double dt;          /* step length of the projected-descent step (> 0); prefactors of Eq. 9 absorbed */
+    int precision;      /* SS_PREC_FP32 or SS_PREC_FP64 */
+    int dipole;         /* SS_DIPOLE_FFT (default) or SS_DIPOLE_OFF (dipole term dropped whatever w) */
+    int reparam_every;  /* 1 = reparametrise after every step (Sec. III); 0 = never (plain relaxation) */
+    void* stream;       /* cudaStream_t to order against, e.g. torch.cuda.current_stream(); NULL = legacy */
+} ss_opts;
+
+typedef struct {
+    int nx, ny, nz;        /* lattice dimensions, each >= 1 */
+    double J, D, K, w;     /* exchange, DMI, anisotropy, dipole strength (finite) */
+    int n_images;          /* images of this string, >= 2 */
+} ss_string_desc;
+
+/* Fills *opts with dt = 0.1, SS_PREC_FP32, SS_DIPOLE_FFT, reparam_every = 1, stream = NULL. */
+void ss_default_opts(ss_opts* opts);
+
+/* Creates a context holding one string of n_images images on an nx*ny*nz lattice (Sec. II, III).
+ * opts may be NULL (defaults).  Errors: SS_ERR_INVALID_ARG, SS_ERR_OOM, SS_ERR_CUDA; *out is NULL
+ * on failure. */
+ss_status ss_create(int nx, int ny, int nz, double J, double D, double K, double w_dip, int n_images,
+                    const ss_opts* opts, ss_ctx** out);
+
+/* Creates a context holding n_strings independent strings (a parameter study, Sec. IV), each with its
+ * own lattice, constants and image count; strings of equal lattice size share one batched launch per
+ * kernel and one dipole spectrum. */
+ss_status ss_create_batch(int n_strings, const ss_string_desc* descs, const ss_opts* opts, ss_ctx** out);
+
+/* Sets the path of string `string` from `spins` ([n_images][N][3], dtype, host or device).  Each spin
+ * is normalised on copy.  Errors: SS_ERR_INVALID_ARG for a bad index/dtype or any zero-norm or
+ * non-finite input spin (the stored path is then unspecified until the next successful call).
+ * Synchronises. */
+ss_status ss_set_path(ss_ctx* ctx, int string, const void* spins, int dtype, int on_device);
+
+/* Copies the current (reparametrised) path of `string` into `out` ([n_images][N][3]).  Synchronises.
+ * ss_get_path followed by ss_set_path resumes bit-exactly (checkpoint/resume). */
+ss_status ss_get_path(ss_ctx* ctx, int string, void* out, int dtype, int on_device);
+
+/* Runs n_iter >= 0 iterations of the string method (Sec. III) on every string of the context.
+ * Asynchronous on the context's stream (replayed from a captured CUDA graph).  Errors raised on the
+ * device are reported by the next synchronising call.  SS_ERR_STATE if some string has no path. */
+ss_status ss_step(ss_ctx* ctx, int n_iter);
+
+/* Energy (Eq. 1 / Eq. 8) of every image of the current path of `string`, into host out[n_images], in
+ * FP64: a fresh field evaluation of the current path; the local terms are summed in FP64 from the
+ * stored spins renormalised in FP64.  Synchronises. */
+ss_status ss_energies(ss_ctx* ctx, int string, double* out);
+
+/* Per-image energies from the last ss_step iteration (the state before that iteration's step),
+ * reduced in FP64 from per-site FP32 terms (FP64 terms on the FP64 path): the energy curve of each
+ * iteration (Sec. III).  Host out[n_images].  Synchronises. */
+ss_status ss_step_energies(ss_ctx* ctx, int string, double* out);
+
+/* Barrier of `string` (Sec. III): *dE = max_k E_k - E_0 over ss_energies, *k_max = the maximising
+ * image (lowest index on ties).  Either pointer may be NULL.  Synchronises. */
+ss_status ss_barrier(ss_ctx* ctx, int string, double* dE, int* k_max);
+
+/* Effective field h = -dE/ds (Eqs. 2-7) of every image of the current path of `string` into `out`
+ * ([n_images][N][3], dtype, host or device).  Synchronises. */
+ss_status ss_field(ss_ctx* ctx, int string, void* out, int dtype, int on_device);
+
+/* Derivatives of the energy of image `image` of `string` (Eq. 2 and the linearity of Eq. 1 in its
+ * constants): dE_ds ([N][3], dtype, host or device; may be NULL) receives dE/ds = -h, and
+ * dE_dJDKw (host, 4 doubles; may be NULL) receives (dE/dJ, dE/dD, dE/dK, dE/dw), each the energy
+ * term with its constant set to 1, in FP64.  Synchronises. */
+ss_status ss_grad(ss_ctx* ctx, int string, int image, void* dE_ds, int dtype, int on_device, double* dE_dJDKw);
+
+/* Measures the kernels of one iteration: each kernel is launched on its own (not from the graph) on
+ * the context's stream, bracketed by CUDA events, for `reps` >= 1 timed iterations after one untimed
+ * iteration.  ms_out[i] (host, up to max_out entries) receives the mean duration in milliseconds of
+ * kernel i, in launch order: for each size group xfwd, yz (when the group has a dipole term), xinv,
+ * arc.  *n_out receives the number of kernels.  The strings advance by reps + 1 iterations.
+ * Synchronises. */
+ss_status ss_time_kernels(ss_ctx* ctx, int reps, double* ms_out, int max_out, int* n_out);
+
+/* Shape queries. */
+int ss_num_strings(const ss_ctx* ctx);
+ss_status ss_string_info(const ss_ctx* ctx, int string, ss_string_desc* out);
+
+/* Number of kernels ss_step launches per iteration (all strings), for launch accounting. */
+int ss_kernels_per_iteration(const ss_ctx* ctx);
+
+/* Last error message of this context (or of the last failed ss_create* when ctx is NULL). */
+const char* ss_last_error(const ss_ctx* ctx);
+
+/* Frees every resource of the context; NULL is allowed. */
+void ss_destroy(ss_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SS_H */

@@ -61,6 +61,7 @@ def _load():
             "or_energy_terms": (None, [mp, dp, dp]),
             "or_field": (i, [mp, i, dp, dp]),
             "or_dipole_field": (i, [mp, dp, dp]),
+            "or_field_at": (i, [mp, dp, i, P(i), dp]),
             "or_energy_from_field": (d, [i, dp, dp]),
             "or_step": (None, [i, d, dp, dp]),
             "or_reparam": (None, [i, i, dp, dp, dp]),
@@ -123,6 +124,18 @@ def field(m: OracleModel, s) -> np.ndarray:
     return h
 
 
+def field_at(m: OracleModel, s, sites) -> np.ndarray:
+    """Eqs. 2-7 of one image [N,3] at the given site indices -> [len(sites), 3]."""
+    s = _f64(s)
+    sites = np.ascontiguousarray(np.asarray(sites, dtype=np.int32))
+    out = np.zeros((sites.size, 3))
+    st = _load().or_field_at(ctypes.byref(m), _ptr(s), int(sites.size),
+                             sites.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _ptr(out))
+    if st != 0:
+        raise ValueError("oracle field_at: out of memory or site index out of range")
+    return out
+
+
 def dipole_field(m: OracleModel, s) -> np.ndarray:
     """Eq. 6 alone (direct O(N^2) sum) for one image."""
     s = _f64(s)
@@ -163,12 +176,13 @@ def reparam(path, return_alpha: bool = False):
     return (out, alpha) if return_alpha else out
 
 
-def string_run(m: OracleModel, path, n_iter: int, dt: float):
-    """Sec. III loop: n_iter x (step all images, reparametrise).  Returns (final path, energies)."""
+def string_run(m: OracleModel, path, n_iter: int, dt: float, with_energies: bool = True):
+    """Sec. III loop: n_iter x (step all images, reparametrise).  Returns (final path, energies or None)."""
     phi = _f64(path).copy()
     K = phi.shape[0]
-    e = np.zeros(K)
-    if _load().or_string_run(ctypes.byref(m), K, int(n_iter), float(dt), _ptr(phi), _ptr(e)) != 0:
+    e = np.zeros(K) if with_energies else None
+    if _load().or_string_run(ctypes.byref(m), K, int(n_iter), float(dt), _ptr(phi),
+                             _ptr(e) if with_energies else None) != 0:
         raise MemoryError("oracle string run: out of memory")
     return phi, e
 

@@ -120,62 +120,81 @@ static double* dipole_table(const or_model* m) {
     return t;
 }
 
-/* Eqs. 2-6: the effective field h_i = -dE/ds_i of one image.
+/* Eqs. 2-6: the effective field h_i = -dE/ds_i at site (x, y, z) of one image.
  *   exchange   (Eq. 3): J sum over the (up to 6) nearest neighbours of s_j
  *   DMI        (Eq. 4): -D ( s_z^{i+x} - s_z^{i-x},  s_z^{i+y} - s_z^{i-y},
  *                            -s_x^{i+x} + s_x^{i-x} - s_y^{i+y} + s_y^{i-y} ), missing neighbours 0
  *   anisotropy (Eq. 5): 2 K (s_i.z) z
- *   dipole     (Eq. 6): 4 pi w sum_{j != i} D(r_ij) s_j with D of Eq. 7, summed directly (O(N^2)).
+ *   dipole     (Eq. 6): 4 pi w sum_{j != i} D(r_ij) s_j with D of Eq. 7, summed directly (O(N)).
  * `table` is the Eq. 7 table of dipole_table() (may be NULL when w == 0). */
-static void field_one(const or_model* m, const double* table, const double* s, double* h) {
+static void field_site(const or_model* m, const double* table, const double* s, int x, int y, int z, double* hout) {
     const int nx = m->nx, ny = m->ny, nz = m->nz, N = nx * ny * nz;
 #define S(xx, yy, zz, c) \
     (((xx) < 0 || (xx) >= nx || (yy) < 0 || (yy) >= ny || (zz) < 0 || (zz) >= nz) ? 0.0 : s[3 * site(m, xx, yy, zz) + (c)])
-    for (int z = 0; z < nz; ++z)
-        for (int y = 0; y < ny; ++y)
-            for (int x = 0; x < nx; ++x) {
-                const int i = site(m, x, y, z);
-                double hx = 0, hy = 0, hz = 0;
-                /* Eq. 3 */
-                for (int c = 0; c < 3; ++c) {
-                    const double sum = S(x + 1, y, z, c) + S(x - 1, y, z, c) + S(x, y + 1, z, c) + S(x, y - 1, z, c) +
-                                       S(x, y, z + 1, c) + S(x, y, z - 1, c);
-                    if (c == 0) hx += m->J * sum;
-                    if (c == 1) hy += m->J * sum;
-                    if (c == 2) hz += m->J * sum;
-                }
-                /* Eq. 4 */
-                hx += -m->D * (S(x + 1, y, z, 2) - S(x - 1, y, z, 2));
-                hy += -m->D * (S(x, y + 1, z, 2) - S(x, y - 1, z, 2));
-                hz += -m->D * (-S(x + 1, y, z, 0) + S(x - 1, y, z, 0) - S(x, y + 1, z, 1) + S(x, y - 1, z, 1));
-                /* Eq. 5 */
-                hz += 2.0 * m->K * s[3 * i + 2];
-                h[3 * i + 0] = hx;
-                h[3 * i + 1] = hy;
-                h[3 * i + 2] = hz;
-            }
+    const int i = site(m, x, y, z);
+    double hx = 0, hy = 0, hz = 0;
+    /* Eq. 3 */
+    for (int c = 0; c < 3; ++c) {
+        const double sum = S(x + 1, y, z, c) + S(x - 1, y, z, c) + S(x, y + 1, z, c) + S(x, y - 1, z, c) +
+                           S(x, y, z + 1, c) + S(x, y, z - 1, c);
+        if (c == 0) hx += m->J * sum;
+        if (c == 1) hy += m->J * sum;
+        if (c == 2) hz += m->J * sum;
+    }
+    /* Eq. 4 */
+    hx += -m->D * (S(x + 1, y, z, 2) - S(x - 1, y, z, 2));
+    hy += -m->D * (S(x, y + 1, z, 2) - S(x, y - 1, z, 2));
+    hz += -m->D * (-S(x + 1, y, z, 0) + S(x - 1, y, z, 0) - S(x, y + 1, z, 1) + S(x, y - 1, z, 1));
+    /* Eq. 5 */
+    hz += 2.0 * m->K * s[3 * i + 2];
 #undef S
     if (m->w != 0.0 && table) {
         /* Eq. 6 */
         const int Lx = 2 * nx - 1, Ly = 2 * ny - 1;
         const double pref = 4.0 * M_PI * m->w;
-        for (int i = 0; i < N; ++i) {
-            const int xi = i % nx, yi = (i / nx) % ny, zi = i / (nx * ny);
-            double ax = 0, ay = 0, az = 0;
-            for (int j = 0; j < N; ++j) {
-                if (j == i) continue;
-                const int xj = j % nx, yj = (j / nx) % ny, zj = j / (nx * ny);
-                const double* d = table + 6 * (((size_t)(zj - zi + nz - 1) * Ly + (yj - yi + ny - 1)) * Lx + (xj - xi + nx - 1));
-                const double* sj = s + 3 * j;
-                ax += d[0] * sj[0] + d[3] * sj[1] + d[4] * sj[2];
-                ay += d[3] * sj[0] + d[1] * sj[1] + d[5] * sj[2];
-                az += d[4] * sj[0] + d[5] * sj[1] + d[2] * sj[2];
-            }
-            h[3 * i + 0] += pref * ax;
-            h[3 * i + 1] += pref * ay;
-            h[3 * i + 2] += pref * az;
+        double ax = 0, ay = 0, az = 0;
+        for (int j = 0; j < N; ++j) {
+            if (j == i) continue;
+            const int xj = j % nx, yj = (j / nx) % ny, zj = j / (nx * ny);
+            const double* d = table + 6 * (((size_t)(zj - z + nz - 1) * Ly + (yj - y + ny - 1)) * Lx + (xj - x + nx - 1));
+            const double* sj = s + 3 * j;
+            ax += d[0] * sj[0] + d[3] * sj[1] + d[4] * sj[2];
+            ay += d[3] * sj[0] + d[1] * sj[1] + d[5] * sj[2];
+            az += d[4] * sj[0] + d[5] * sj[1] + d[2] * sj[2];
         }
+        hx += pref * ax;
+        hy += pref * ay;
+        hz += pref * az;
     }
+    hout[0] = hx;
+    hout[1] = hy;
+    hout[2] = hz;
+}
+
+static void field_one(const or_model* m, const double* table, const double* s, double* h) {
+    for (int z = 0; z < m->nz; ++z)
+        for (int y = 0; y < m->ny; ++y)
+            for (int x = 0; x < m->nx; ++x) field_site(m, table, s, x, y, z, h + 3 * site(m, x, y, z));
+}
+
+/* Eqs. 2-7 at selected sites of one image: h_out[3*q..] = h at site index sites[q]. Returns 0, or -1
+ * when out of memory or a site index is out of range. */
+int or_field_at(const or_model* m, const double* s, int n_sel, const int* sites, double* h_out) {
+    const int N = m->nx * m->ny * m->nz;
+    for (int q = 0; q < n_sel; ++q)
+        if (sites[q] < 0 || sites[q] >= N) return -1;
+    double* table = NULL;
+    if (m->w != 0.0) {
+        table = dipole_table(m);
+        if (!table) return -1;
+    }
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int q = 0; q < n_sel; ++q) {
+        const int i = sites[q];
+        field_site(m, table, s, i % m->nx, (i / m->nx) % m->ny, i / (m->nx * m->ny), h_out + 3 * q);
+    }
+    free(table);
+    return 0;
 }
 
 /* Eqs. 2-6 for `n_images` images stored back to back ([image][site][3]). Returns 0, or -1 when out of memory. */

@@ -1,0 +1,850 @@
+// ss_api.cu -- host runtime of libss: contexts, size groups, device buffers, the dipole-tensor
+// spectrum, launch configuration, CUDA-graph replay of the iteration, and the C ABI of ss.h.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ss.h"
+#include "ss_fft.cuh"
+#include "ss_internal.h"
+
+using namespace ss;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+// ---- small helpers --------------------------------------------------------------------------------
+bool is_smooth23(int m) {
+    while (m % 2 == 0) m /= 2;
+    while (m % 3 == 0) m /= 3;
+    return m == 1;
+}
+
+// Padded transform length: the smallest 2^a 3^b >= 2n - 1, enough for the linear (non-circular)
+// convolution of n sites with offsets -(n-1)..(n-1) (Sec. II-A, the zero-padded kernel).
+int padded_len(int n) {
+    int m = std::max(1, 2 * n - 1);
+    while (!is_smooth23(m)) ++m;
+    return m;
+}
+
+FftPlan make_plan(int P) {
+    FftPlan p{};
+    p.P = P;
+    int a = 0, b = 0, q = P;
+    while (q % 2 == 0) q /= 2, ++a;
+    while (q % 3 == 0) q /= 3, ++b;
+    std::vector<int> r;
+    const int n8 = a / 3, rem = a % 3;
+    if (rem == 0) {
+        r.assign(n8, 8);
+    } else if (rem == 1) {
+        if (n8 >= 1) {
+            r.assign(n8 - 1, 8);
+            r.push_back(4);
+            r.push_back(4);
+        } else {
+            r.push_back(2);
+        }
+    } else {
+        r.assign(n8, 8);
+        r.push_back(4);
+    }
+    for (int i = 0; i < b; ++i) r.push_back(3);
+    p.nstages = (int)r.size();
+    for (int i = 0; i < p.nstages; ++i) p.radix[i] = r[i];
+    return p;
+}
+
+// Eq. 7 at an integer lattice offset (entries xx, yy, zz, xy, xz, yz), with its 1/(4 pi).
+void dipole_tensor_at(int dx, int dy, int dz, double out[6]) {
+    const double x = dx, y = dy, z = dz;
+    const double r2 = x * x + y * y + z * z;
+    const double r = sqrt(r2);
+    const double inv3 = 1.0 / (r2 * r), inv5 = inv3 / r2;
+    const double c = 0.25 / M_PI;
+    out[0] = c * (3.0 * x * x * inv5 - inv3);
+    out[1] = c * (3.0 * y * y * inv5 - inv3);
+    out[2] = c * (3.0 * z * z * inv5 - inv3);
+    out[3] = c * 3.0 * x * y * inv5;
+    out[4] = c * 3.0 * x * z * inv5;
+    out[5] = c * 3.0 * y * z * inv5;
+}
+
+// exp(-2 pi i k / P), k = 0..P-1, in FP64.
+std::vector<double2> twiddles(int P) {
+    std::vector<double2> w(P);
+    for (int k = 0; k < P; ++k) {
+        const double a = 2.0 * M_PI * (double)k / (double)P;
+        w[k] = make_double2(cos(a), -sin(a));
+    }
+    return w;
+}
+
+int round_up(int v, int m) { return ((v + m - 1) / m) * m; }
+
+}  // namespace
+
+// ---- context --------------------------------------------------------------------------------------
+struct Group {
+    int nx = 0, ny = 0, nz = 0, N = 0, Px = 1, Py = 1;
+    int n_img = 0, n_pairs = 0;
+    std::vector<int> strs;  // context string ids, in group order
+    std::vector<int> str_img0, str_K;
+    bool dipole = false;
+    FftPlan planx{}, plany{};
+    int lsx = 1, lsy = 1;
+    int ty_a = 1, ty_c = 1, thr_a = 128, thr_b = 128, thr_c = 128, thr_arc = 256;
+    size_t smem_a = 0, smem_b = 0, smem_c = 0, smem_c_eval = 0;
+    int n_eblk = 0;
+    // device
+    void *s = nullptr, *sp = nullptr, *spec = nullptr, *dhat = nullptr, *twx = nullptr, *twy = nullptr;
+    void *prm = nullptr, *hout = nullptr;
+    InterpEntry* interp = nullptr;
+    double* epart = nullptr;
+    int *d_str_img0 = nullptr, *d_str_K = nullptr;
+    double *dpart = nullptr, *e_last = nullptr, *eval_terms = nullptr, *eval_E = nullptr;
+    unsigned* counters = nullptr;
+    ArcArgs arc{};
+};
+
+struct StringRec {
+    ss_string_desc d;
+    int group;
+    int local;  // index within its group
+    int img0;   // first group-local image
+    bool has_path;
+};
+
+struct ss_ctx {
+    ss_opts opts{};
+    int device = 0;
+    std::vector<StringRec> strs;
+    std::vector<Group> groups;
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    int* d_err = nullptr;
+    void* stage = nullptr;  // device staging buffer for host copies
+    size_t stage_bytes = 0;
+    std::vector<void*> allocs;
+    cudaGraphExec_t graph1 = nullptr, graphN = nullptr;
+    int graphN_iters = 16;
+    std::string err;
+};
+
+namespace {
+
+ss_status fail(ss_ctx* c, ss_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c)
+        c->err = buf;
+    else
+        g_create_error = buf;
+    return st;
+}
+
+#define CUDA_TRY(ctx, call)                                                                      \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess)                                                                   \
+            return fail((ctx), e_ == cudaErrorMemoryAllocation ? SS_ERR_OOM : SS_ERR_CUDA,       \
+                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+ss_status dalloc(ss_ctx* c, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(c, SS_ERR_OOM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    c->allocs.push_back(*p);
+    return SS_OK;
+}
+
+#define TRY(x)                        \
+    do {                              \
+        ss_status s_ = (x);           \
+        if (s_ != SS_OK) return s_;   \
+    } while (0)
+
+bool use_fp64(const ss_ctx* c) { return c->opts.precision == SS_PREC_FP64; }
+size_t real_size(const ss_ctx* c) { return use_fp64(c) ? sizeof(double) : sizeof(float); }
+
+template <typename T> GroupArgs<T> group_args(const ss_ctx* c, const Group& g) {
+    GroupArgs<T> a{};
+    a.nx = g.nx;
+    a.ny = g.ny;
+    a.nz = g.nz;
+    a.N = g.N;
+    a.Px = g.Px;
+    a.Py = g.Py;
+    a.n_img = g.n_img;
+    a.n_pairs = g.n_pairs;
+    a.lsx = g.lsx;
+    a.lsy = g.lsy;
+    a.s = (T*)g.s;
+    a.sp = (T*)g.sp;
+    a.spec = (cplx<T>*)g.spec;
+    a.dhat = (const T*)g.dhat;
+    a.twx = (const cplx<T>*)g.twx;
+    a.twy = (const cplx<T>*)g.twy;
+    a.planx = g.planx;
+    a.plany = g.plany;
+    a.prm = (const ImgParam<T>*)g.prm;
+    a.interp = g.interp;
+    a.epart = g.epart;
+    a.n_eblk = g.n_eblk;
+    a.ty_a = g.ty_a;
+    a.ty_c = g.ty_c;
+    a.err = c->d_err;
+    return a;
+}
+
+// Launch shapes of one size group (shared memory, rows per CTA, block sizes).
+void configure_group(const ss_ctx* c, Group& g) {
+    const size_t cs = 2 * real_size(c);  // complex element
+    g.lsx = g.Px | 1;
+    g.lsy = g.Py | 1;
+    const size_t budget = use_fp64(c) ? 96 * 1024 : 64 * 1024;
+    // x kernels: rows per CTA such that 3*rows lines fit the budget
+    int ty = std::min(g.ny, use_fp64(c) ? 4 : 8);
+    while (ty > 1 && (size_t)(g.Px + 3 * ty * g.lsx) * cs > budget) --ty;
+    g.ty_a = g.ty_c = ty;
+    auto x_threads = [&](int rows) {
+        int need = std::max(fft_min_threads(g.Px), 1);
+        int t = std::max(128, std::min(kMaxThreadsX, round_up(rows * g.nx, 32)));
+        t = std::max(t, round_up(need, 32));
+        // enough threads for all lines in one pass when that is within the ceiling
+        while (t < kMaxThreadsX && fft_lines_per_pass(t, g.Px) < 3 * rows) t += 32;
+        return std::min(t, kMaxThreadsX);
+    };
+    g.thr_a = x_threads(g.ty_a);
+    g.thr_c = x_threads(g.ty_c);
+    g.smem_a = (size_t)(g.Px + 3 * g.ty_a * g.lsx) * cs;
+    g.smem_c = (size_t)(g.Px + 3 * g.ty_c * g.lsx) * cs + 32 * 8 * sizeof(double);
+    g.smem_c_eval = g.smem_c;
+    // y/z kernel: all 3*nz lines of one (pair, kx) in shared memory
+    int tb = std::max(128, round_up(fft_min_threads(g.Py), 32));
+    while (tb < kMaxThreadsYz && fft_lines_per_pass(tb, g.Py) < 3 * g.nz) tb += 32;
+    g.thr_b = std::min(tb, kMaxThreadsYz);
+    g.smem_b = (size_t)(g.Py + 3 * g.nz * g.lsy) * cs;
+    g.n_eblk = g.nz * ((g.ny + g.ty_c - 1) / g.ty_c);
+}
+
+template <typename T> ss_status build_tensor_spectrum(ss_ctx* c, Group& g) {
+    const int Px = g.Px, Py = g.Py, nz = g.nz;
+    const size_t plane = (size_t)Px * Py;
+    const size_t n = (size_t)6 * nz * plane;
+    std::vector<double2> host(n, make_double2(0.0, 0.0));
+    for (int dz = 0; dz < nz; ++dz)
+        for (int dy = -(g.ny - 1); dy <= g.ny - 1; ++dy)
+            for (int dx = -(g.nx - 1); dx <= g.nx - 1; ++dx) {
+                if (dx == 0 && dy == 0 && dz == 0) continue;
+                double d[6];
+                dipole_tensor_at(dx, dy, dz, d);
+                const int ix = ((dx % Px) + Px) % Px, iy = ((dy % Py) + Py) % Py;
+                for (int k = 0; k < 6; ++k) host[((size_t)k * nz + dz) * plane + (size_t)iy * Px + ix].x = d[k];
+            }
+    double2 *d_data = nullptr, *d_twx = nullptr, *d_twy = nullptr;
+    CUDA_TRY(c, cudaMalloc(&d_data, n * sizeof(double2)));
+    auto twx = twiddles(Px), twy = twiddles(Py);
+    cudaError_t e = cudaMalloc(&d_twx, Px * sizeof(double2));
+    if (e == cudaSuccess) e = cudaMalloc(&d_twy, Py * sizeof(double2));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_data, host.data(), n * sizeof(double2), cudaMemcpyHostToDevice, c->cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_twx, twx.data(), Px * sizeof(double2), cudaMemcpyHostToDevice, c->cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_twy, twy.data(), Py * sizeof(double2), cudaMemcpyHostToDevice, c->cs);
+    if (e == cudaSuccess) {
+        const FftPlan px = make_plan(Px), py = make_plan(Py);
+        // x: rows of length Px, contiguous
+        launch_fft_strided_f64(d_data, d_twx, px, 6 * nz * Py, 1, 1, 0, Px, c->cs);
+        // y: columns of length Py, stride Px
+        launch_fft_strided_f64(d_data, d_twy, py, 6 * nz * Px, Px, Px, 1, (long)plane, c->cs);
+        launch_extract_octant<T>(d_data, (T*)g.dhat, Px, Py, nz, 4.0 * M_PI / ((double)Px * Py), c->cs);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->cs);
+    cudaFree(d_data);
+    cudaFree(d_twx);
+    cudaFree(d_twy);
+    if (e != cudaSuccess) return fail(c, SS_ERR_CUDA, "dipole tensor spectrum: %s", cudaGetErrorString(e));
+    return SS_OK;
+}
+
+template <typename T> ss_status setup_group(ss_ctx* c, Group& g) {
+    using C = cplx<T>;
+    const size_t M = (size_t)3 * g.N;
+    TRY(dalloc(c, &g.s, g.n_img * M * sizeof(T)));
+    TRY(dalloc(c, &g.sp, g.n_img * M * sizeof(T)));
+    TRY(dalloc(c, (void**)&g.interp, g.n_img * sizeof(InterpEntry)));
+    TRY(dalloc(c, &g.prm, g.n_img * sizeof(ImgParam<T>)));
+    TRY(dalloc(c, (void**)&g.epart, (size_t)g.n_img * 4 * g.n_eblk * sizeof(double)));
+    TRY(dalloc(c, &g.twx, g.Px * sizeof(C)));
+    TRY(dalloc(c, &g.twy, g.Py * sizeof(C)));
+    if (g.dipole) {
+        TRY(dalloc(c, &g.spec, (size_t)g.n_pairs * g.Px * 3 * g.nz * g.ny * sizeof(C)));
+        TRY(dalloc(c, &g.dhat, (size_t)(g.Px / 2 + 1) * (g.Py / 2 + 1) * g.nz * 6 * sizeof(T)));
+    }
+    // per-image constants
+    std::vector<ImgParam<T>> prm(g.n_img);
+    const int nstr = (int)g.strs.size();
+    int maxK = 0;
+    for (int i = 0; i < nstr; ++i) {
+        const ss_string_desc& d = c->strs[g.strs[i]].d;
+        for (int k = 0; k < d.n_images; ++k) {
+            ImgParam<T>& p = prm[g.str_img0[i] + k];
+            p.J = T(d.J);
+            p.D = T(d.D);
+            p.K = T(d.K);
+            p.w = (c->opts.dipole == SS_DIPOLE_OFF) ? T(0) : T(d.w);
+        }
+        maxK = std::max(maxK, d.n_images);
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(g.prm, prm.data(), prm.size() * sizeof(ImgParam<T>), cudaMemcpyHostToDevice, c->cs));
+    auto twx = twiddles(g.Px), twy = twiddles(g.Py);
+    std::vector<C> tx(g.Px), ty(g.Py);
+    for (int i = 0; i < g.Px; ++i) tx[i] = C{T(twx[i].x), T(twx[i].y)};
+    for (int i = 0; i < g.Py; ++i) ty[i] = C{T(twy[i].x), T(twy[i].y)};
+    CUDA_TRY(c, cudaMemcpyAsync(g.twx, tx.data(), g.Px * sizeof(C), cudaMemcpyHostToDevice, c->cs));
+    CUDA_TRY(c, cudaMemcpyAsync(g.twy, ty.data(), g.Py * sizeof(C), cudaMemcpyHostToDevice, c->cs));
+    // arc-length bookkeeping
+    ArcArgs& a = g.arc;
+    a.n_str = nstr;
+    a.maxK = maxK;
+    a.tile_elems = 2048;
+    a.n_tiles = (int)((M + a.tile_elems - 1) / a.tile_elems);
+    a.kchunk = std::max(1, std::min(8, maxK - 1));
+    a.n_kchunks = std::max(1, (maxK - 1 + a.kchunk - 1) / a.kchunk);
+    a.reparam = c->opts.reparam_every != 0;
+    TRY(dalloc(c, (void**)&g.d_str_img0, nstr * sizeof(int)));
+    TRY(dalloc(c, (void**)&g.d_str_K, nstr * sizeof(int)));
+    TRY(dalloc(c, (void**)&g.dpart, (size_t)nstr * maxK * a.n_tiles * sizeof(double)));
+    TRY(dalloc(c, (void**)&g.counters, nstr * sizeof(unsigned)));
+    TRY(dalloc(c, (void**)&g.e_last, (size_t)nstr * maxK * sizeof(double)));
+    TRY(dalloc(c, (void**)&g.eval_terms, (size_t)nstr * maxK * 4 * sizeof(double)));
+    TRY(dalloc(c, (void**)&g.eval_E, (size_t)nstr * maxK * sizeof(double)));
+    CUDA_TRY(c, cudaMemcpyAsync(g.d_str_img0, g.str_img0.data(), nstr * sizeof(int), cudaMemcpyHostToDevice, c->cs));
+    CUDA_TRY(c, cudaMemcpyAsync(g.d_str_K, g.str_K.data(), nstr * sizeof(int), cudaMemcpyHostToDevice, c->cs));
+    CUDA_TRY(c, cudaMemsetAsync(g.counters, 0, nstr * sizeof(unsigned), c->cs));
+    CUDA_TRY(c, cudaMemsetAsync(g.dpart, 0, (size_t)nstr * maxK * a.n_tiles * sizeof(double), c->cs));
+    CUDA_TRY(c, cudaMemsetAsync(g.e_last, 0, (size_t)nstr * maxK * sizeof(double), c->cs));
+    CUDA_TRY(c, cudaMemsetAsync(g.s, 0, g.n_img * M * sizeof(T), c->cs));
+    CUDA_TRY(c, cudaMemsetAsync(g.sp, 0, g.n_img * M * sizeof(T), c->cs));
+    a.str_img0 = g.d_str_img0;
+    a.str_K = g.d_str_K;
+    a.dpart = g.dpart;
+    a.counters = g.counters;
+    a.e_last = g.e_last;
+    launch_interp_identity(g.interp, 0, g.n_img, c->cs);
+    CUDA_TRY(c, cudaGetLastError());
+    if (g.dipole) TRY(build_tensor_spectrum<T>(c, g));
+    return SS_OK;
+}
+
+// Issue one iteration (Sec. III) of every size group on stream st.
+template <typename T> void issue_iteration(ss_ctx* c, cudaStream_t st) {
+    const T dt = T(c->opts.dt);
+    for (Group& g : c->groups) {
+        GroupArgs<T> a = group_args<T>(c, g);
+        launch_xfwd<T>(a, g.dipole, g.thr_a, g.smem_a, st);
+        if (g.dipole) launch_yz<T>(a, g.thr_b, g.smem_b, st);
+        launch_xinv_step<T>(a, g.dipole, dt, g.thr_c, g.smem_c, st);
+        launch_arc<T>(a, g.arc, g.thr_arc, st);
+    }
+}
+
+template <typename T> void issue_eval(ss_ctx* c, Group& g, T* hout, cudaStream_t st) {
+    GroupArgs<T> a = group_args<T>(c, g);
+    launch_xfwd<T>(a, g.dipole, g.thr_a, g.smem_a, st);
+    if (g.dipole) launch_yz<T>(a, g.thr_b, g.smem_b, st);
+    launch_xinv_eval<T>(a, g.dipole, hout, g.thr_c, g.smem_c_eval, st);
+    launch_eval_reduce<T>(a, g.arc, g.eval_terms, g.eval_E, st);
+}
+
+template <typename T> void issue_materialise(ss_ctx* c, Group& g, cudaStream_t st) {
+    GroupArgs<T> a = group_args<T>(c, g);
+    launch_xfwd<T>(a, false, g.thr_a, 0, st);
+}
+
+cudaStream_t user_stream(const ss_ctx* c) { return (cudaStream_t)c->opts.stream; }
+
+ss_status enter(ss_ctx* c) {
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    CUDA_TRY(c, cudaEventRecord(c->ev_in, user_stream(c)));
+    CUDA_TRY(c, cudaStreamWaitEvent(c->cs, c->ev_in, 0));
+    return SS_OK;
+}
+
+ss_status leave(ss_ctx* c) {
+    CUDA_TRY(c, cudaGetLastError());
+    CUDA_TRY(c, cudaEventRecord(c->ev_out, c->cs));
+    CUDA_TRY(c, cudaStreamWaitEvent(user_stream(c), c->ev_out, 0));
+    return SS_OK;
+}
+
+// Synchronise the internal stream and consume the sticky error word.
+ss_status sync_check(ss_ctx* c) {
+    CUDA_TRY(c, cudaStreamSynchronize(c->cs));
+    int h = 0;
+    CUDA_TRY(c, cudaMemcpy(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) {
+        CUDA_TRY(c, cudaMemset(c->d_err, 0, sizeof(int)));
+        if (h & kErrInvalidSpin) return fail(c, SS_ERR_INVALID_ARG, "input spin with zero norm or non-finite component");
+        return fail(c, SS_ERR_NONFINITE, "non-finite energy or arc length on the device");
+    }
+    return SS_OK;
+}
+
+ss_status check_string(ss_ctx* c, int string) {
+    if (!c) return SS_ERR_INVALID_ARG;
+    if (string < 0 || string >= (int)c->strs.size()) return fail(c, SS_ERR_INVALID_ARG, "string index %d out of range", string);
+    return SS_OK;
+}
+
+ss_status check_dtype(ss_ctx* c, int dtype) {
+    if (dtype != SS_DTYPE_F32 && dtype != SS_DTYPE_F64) return fail(c, SS_ERR_INVALID_ARG, "dtype %d", dtype);
+    return SS_OK;
+}
+
+size_t dtype_size(int dtype) { return dtype == SS_DTYPE_F64 ? 8 : 4; }
+
+// Copy K images of [K][3][N] SoA data (scaled) into a caller buffer ([K][N][3], dtype, host/device).
+ss_status export_soa(ss_ctx* c, const void* src, int K, int N, void* out, int dtype, int on_device, double scale) {
+    const size_t bytes = (size_t)K * N * 3 * dtype_size(dtype);
+    void* dst = on_device ? out : c->stage;
+    if (!on_device && bytes > c->stage_bytes) return fail(c, SS_ERR_INVALID_ARG, "staging buffer too small");
+    if (use_fp64(c)) {
+        if (dtype == SS_DTYPE_F64)
+            launch_soa_to_aos<double, double>((const double*)src, (double*)dst, K, N, scale, c->cs);
+        else
+            launch_soa_to_aos<double, float>((const double*)src, (float*)dst, K, N, (float)scale, c->cs);
+    } else {
+        if (dtype == SS_DTYPE_F64)
+            launch_soa_to_aos<float, double>((const float*)src, (double*)dst, K, N, scale, c->cs);
+        else
+            launch_soa_to_aos<float, float>((const float*)src, (float*)dst, K, N, (float)scale, c->cs);
+    }
+    CUDA_TRY(c, cudaGetLastError());
+    if (!on_device) CUDA_TRY(c, cudaMemcpyAsync(out, c->stage, bytes, cudaMemcpyDeviceToHost, c->cs));
+    return SS_OK;
+}
+
+ss_status ensure_hout(ss_ctx* c, Group& g) {
+    if (!g.hout) TRY(dalloc(c, &g.hout, (size_t)g.n_img * 3 * g.N * real_size(c)));
+    return SS_OK;
+}
+
+ss_status evaluate_group(ss_ctx* c, Group& g, bool want_field) {
+    if (want_field) TRY(ensure_hout(c, g));
+    if (use_fp64(c))
+        issue_eval<double>(c, g, want_field ? (double*)g.hout : nullptr, c->cs);
+    else
+        issue_eval<float>(c, g, want_field ? (float*)g.hout : nullptr, c->cs);
+    CUDA_TRY(c, cudaGetLastError());
+    return SS_OK;
+}
+
+ss_status check_paths(ss_ctx* c, const Group& g) {
+    for (int id : g.strs)
+        if (!c->strs[id].has_path) return fail(c, SS_ERR_STATE, "string %d has no path (call ss_set_path first)", id);
+    return SS_OK;
+}
+
+ss_status capture_graph(ss_ctx* c, int iters, cudaGraphExec_t* out) {
+    cudaGraph_t graph = nullptr;
+    CUDA_TRY(c, cudaStreamBeginCapture(c->cs, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < iters; ++i) {
+        if (use_fp64(c))
+            issue_iteration<double>(c, c->cs);
+        else
+            issue_iteration<float>(c, c->cs);
+    }
+    cudaError_t e = cudaStreamEndCapture(c->cs, &graph);
+    if (e != cudaSuccess) return fail(c, SS_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(c, SS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    return SS_OK;
+}
+
+ss_status validate_desc(const ss_string_desc& d) {
+    if (d.nx < 1 || d.ny < 1 || d.nz < 1)
+        return fail(nullptr, SS_ERR_INVALID_ARG, "lattice dims must be >= 1 (got %d x %d x %d)", d.nx, d.ny, d.nz);
+    if ((long long)d.nx * d.ny * d.nz > (1LL << 26))
+        return fail(nullptr, SS_ERR_INVALID_ARG, "lattice of %lld sites is too large", (long long)d.nx * d.ny * d.nz);
+    if (d.n_images < 2 || d.n_images > kArcMaxK)
+        return fail(nullptr, SS_ERR_INVALID_ARG, "n_images must be in [2, %d] (got %d)", kArcMaxK, d.n_images);
+    if (!isfinite(d.J) || !isfinite(d.D) || !isfinite(d.K) || !isfinite(d.w))
+        return fail(nullptr, SS_ERR_INVALID_ARG, "constants must be finite");
+    if (d.nx > 1024 || d.ny > 1024 || d.nz > 64)
+        return fail(nullptr, SS_ERR_INVALID_ARG, "nx, ny must be <= 1024 and nz <= 64");
+    return SS_OK;
+}
+
+}  // namespace
+
+// ===================================================================================================
+// C ABI
+extern "C" {
+
+void ss_default_opts(ss_opts* o) {
+    if (!o) return;
+    o->dt = 0.1;
+    o->precision = SS_PREC_FP32;
+    o->dipole = SS_DIPOLE_FFT;
+    o->reparam_every = 1;
+    o->stream = nullptr;
+}
+
+ss_status ss_create(int nx, int ny, int nz, double J, double D, double K, double w_dip, int n_images,
+                    const ss_opts* opts, ss_ctx** out) {
+    ss_string_desc d;
+    d.nx = nx;
+    d.ny = ny;
+    d.nz = nz;
+    d.J = J;
+    d.D = D;
+    d.K = K;
+    d.w = w_dip;
+    d.n_images = n_images;
+    return ss_create_batch(1, &d, opts, out);
+}
+
+ss_status ss_create_batch(int n_strings, const ss_string_desc* descs, const ss_opts* opts, ss_ctx** out) {
+    if (!out) return fail(nullptr, SS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_strings < 1 || !descs) return fail(nullptr, SS_ERR_INVALID_ARG, "need at least one string");
+    ss_opts o;
+    ss_default_opts(&o);
+    if (opts) o = *opts;
+    if (!(o.dt > 0.0) || !isfinite(o.dt)) return fail(nullptr, SS_ERR_INVALID_ARG, "dt must be finite and > 0");
+    if (o.precision != SS_PREC_FP32 && o.precision != SS_PREC_FP64)
+        return fail(nullptr, SS_ERR_INVALID_ARG, "precision %d", o.precision);
+    if (o.dipole != SS_DIPOLE_OFF && o.dipole != SS_DIPOLE_FFT) return fail(nullptr, SS_ERR_INVALID_ARG, "dipole mode %d", o.dipole);
+    for (int i = 0; i < n_strings; ++i) TRY(validate_desc(descs[i]));
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return fail(nullptr, SS_ERR_CUDA, "no CUDA device");
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return fail(nullptr, SS_ERR_CUDA, "cudaGetDeviceProperties failed");
+    if (prop.major != 10 || prop.minor != 3)
+        return fail(nullptr, SS_ERR_CUDA, "libss is built for sm_103a; device %d is sm_%d%d", dev, prop.major, prop.minor);
+
+    ss_ctx* c = new (std::nothrow) ss_ctx();
+    if (!c) return fail(nullptr, SS_ERR_OOM, "host allocation failed");
+    c->opts = o;
+    c->device = dev;
+    auto bail = [&](ss_status st) {
+        g_create_error = c->err;
+        ss_destroy(c);
+        return st;
+    };
+    if (cudaStreamCreateWithFlags(&c->cs, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess)
+        return bail(fail(c, SS_ERR_CUDA, "stream/event creation failed"));
+    // group strings by lattice size, in order of first appearance
+    for (int i = 0; i < n_strings; ++i) {
+        const ss_string_desc& d = descs[i];
+        int gi = -1;
+        for (int k = 0; k < (int)c->groups.size(); ++k)
+            if (c->groups[k].nx == d.nx && c->groups[k].ny == d.ny && c->groups[k].nz == d.nz) gi = k;
+        if (gi < 0) {
+            Group g;
+            g.nx = d.nx;
+            g.ny = d.ny;
+            g.nz = d.nz;
+            g.N = d.nx * d.ny * d.nz;
+            c->groups.push_back(g);
+            gi = (int)c->groups.size() - 1;
+        }
+        Group& g = c->groups[gi];
+        StringRec r{d, gi, (int)g.strs.size(), g.n_img, false};
+        g.strs.push_back(i);
+        g.str_img0.push_back(g.n_img);
+        g.str_K.push_back(d.n_images);
+        g.n_img += d.n_images;
+        if (o.dipole != SS_DIPOLE_OFF && d.w != 0.0) g.dipole = true;
+        c->strs.push_back(r);
+    }
+    size_t stage = 0;
+    for (Group& g : c->groups) {
+        g.n_pairs = (g.n_img + 1) / 2;
+        g.Px = g.dipole ? padded_len(g.nx) : 1;
+        g.Py = g.dipole ? padded_len(g.ny) : 1;
+        g.planx = make_plan(g.Px);
+        g.plany = make_plan(g.Py);
+        configure_group(c, g);
+        const size_t smem_max = 227 * 1024;
+        if (g.smem_a > smem_max || g.smem_b > smem_max || g.smem_c > smem_max)
+            return bail(fail(c, SS_ERR_INVALID_ARG, "lattice %d x %d x %d needs more shared memory than a CTA has",
+                             g.nx, g.ny, g.nz));
+        for (int id : g.strs) stage = std::max(stage, (size_t)c->strs[id].d.n_images * g.N * 3 * sizeof(double));
+    }
+    if (use_fp64(c))
+        set_smem_limits<double>(227 * 1024);
+    else
+        set_smem_limits<float>(227 * 1024);
+    {
+        ss_status st = dalloc(c, (void**)&c->d_err, sizeof(int));
+        if (st != SS_OK) return bail(st);
+        st = dalloc(c, &c->stage, stage);
+        if (st != SS_OK) return bail(st);
+        c->stage_bytes = stage;
+        if (cudaMemsetAsync(c->d_err, 0, sizeof(int), c->cs) != cudaSuccess) return bail(fail(c, SS_ERR_CUDA, "memset"));
+    }
+    for (Group& g : c->groups) {
+        ss_status st = use_fp64(c) ? setup_group<double>(c, g) : setup_group<float>(c, g);
+        if (st != SS_OK) return bail(st);
+    }
+    if (cudaStreamSynchronize(c->cs) != cudaSuccess) return bail(fail(c, SS_ERR_CUDA, "setup failed"));
+    *out = c;
+    return SS_OK;
+}
+
+ss_status ss_set_path(ss_ctx* c, int string, const void* spins, int dtype, int on_device) {
+    TRY(check_string(c, string));
+    TRY(check_dtype(c, dtype));
+    if (!spins) return fail(c, SS_ERR_INVALID_ARG, "spins is NULL");
+    StringRec& r = c->strs[string];
+    Group& g = c->groups[r.group];
+    const int K = r.d.n_images;
+    const size_t bytes = (size_t)K * g.N * 3 * dtype_size(dtype);
+    TRY(enter(c));
+    const void* src = spins;
+    if (!on_device) {
+        CUDA_TRY(c, cudaMemcpyAsync(c->stage, spins, bytes, cudaMemcpyHostToDevice, c->cs));
+        src = c->stage;
+    }
+    const size_t off = (size_t)r.img0 * 3 * g.N;
+    if (use_fp64(c)) {
+        double* dst = (double*)g.sp + off;
+        if (dtype == SS_DTYPE_F64)
+            launch_aos_to_soa<double, double>((const double*)src, dst, K, g.N, c->d_err, c->cs);
+        else
+            launch_aos_to_soa<double, float>((const float*)src, dst, K, g.N, c->d_err, c->cs);
+    } else {
+        float* dst = (float*)g.sp + off;
+        if (dtype == SS_DTYPE_F64)
+            launch_aos_to_soa<float, double>((const double*)src, dst, K, g.N, c->d_err, c->cs);
+        else
+            launch_aos_to_soa<float, float>((const float*)src, dst, K, g.N, c->d_err, c->cs);
+    }
+    launch_interp_identity(g.interp, r.img0, K, c->cs);
+    CUDA_TRY(c, cudaGetLastError());
+    ss_status st = sync_check(c);
+    TRY(leave(c));
+    if (st != SS_OK) return st;
+    r.has_path = true;
+    return SS_OK;
+}
+
+ss_status ss_get_path(ss_ctx* c, int string, void* out, int dtype, int on_device) {
+    TRY(check_string(c, string));
+    TRY(check_dtype(c, dtype));
+    if (!out) return fail(c, SS_ERR_INVALID_ARG, "out is NULL");
+    StringRec& r = c->strs[string];
+    Group& g = c->groups[r.group];
+    TRY(check_paths(c, g));
+    TRY(enter(c));
+    if (use_fp64(c))
+        issue_materialise<double>(c, g, c->cs);
+    else
+        issue_materialise<float>(c, g, c->cs);
+    const char* base = (const char*)g.s + (size_t)r.img0 * 3 * g.N * real_size(c);
+    TRY(export_soa(c, base, r.d.n_images, g.N, out, dtype, on_device, 1.0));
+    ss_status st = sync_check(c);
+    TRY(leave(c));
+    return st;
+}
+
+ss_status ss_step(ss_ctx* c, int n_iter) {
+    if (!c) return SS_ERR_INVALID_ARG;
+    if (n_iter < 0) return fail(c, SS_ERR_INVALID_ARG, "n_iter < 0");
+    for (const Group& g : c->groups) TRY(check_paths(c, g));
+    if (n_iter == 0) return SS_OK;
+    TRY(enter(c));
+    const int G = c->graphN_iters;
+    if (n_iter >= G && !c->graphN) TRY(capture_graph(c, G, &c->graphN));
+    if (n_iter % G && !c->graph1) TRY(capture_graph(c, 1, &c->graph1));
+    for (int i = 0; i < n_iter / G; ++i) CUDA_TRY(c, cudaGraphLaunch(c->graphN, c->cs));
+    for (int i = 0; i < n_iter % G; ++i) CUDA_TRY(c, cudaGraphLaunch(c->graph1, c->cs));
+    return leave(c);
+}
+
+ss_status ss_energies(ss_ctx* c, int string, double* out) {
+    TRY(check_string(c, string));
+    if (!out) return fail(c, SS_ERR_INVALID_ARG, "out is NULL");
+    StringRec& r = c->strs[string];
+    Group& g = c->groups[r.group];
+    TRY(check_paths(c, g));
+    TRY(enter(c));
+    TRY(evaluate_group(c, g, false));
+    CUDA_TRY(c, cudaMemcpyAsync(out, g.eval_E + (size_t)r.local * g.arc.maxK, r.d.n_images * sizeof(double),
+                                cudaMemcpyDeviceToHost, c->cs));
+    ss_status st = sync_check(c);
+    TRY(leave(c));
+    return st;
+}
+
+ss_status ss_step_energies(ss_ctx* c, int string, double* out) {
+    TRY(check_string(c, string));
+    if (!out) return fail(c, SS_ERR_INVALID_ARG, "out is NULL");
+    StringRec& r = c->strs[string];
+    Group& g = c->groups[r.group];
+    TRY(enter(c));
+    CUDA_TRY(c, cudaMemcpyAsync(out, g.e_last + (size_t)r.local * g.arc.maxK, r.d.n_images * sizeof(double),
+                                cudaMemcpyDeviceToHost, c->cs));
+    ss_status st = sync_check(c);
+    TRY(leave(c));
+    return st;
+}
+
+ss_status ss_barrier(ss_ctx* c, int string, double* dE, int* k_max) {
+    TRY(check_string(c, string));
+    const int K = c->strs[string].d.n_images;
+    std::vector<double> e(K);
+    TRY(ss_energies(c, string, e.data()));
+    int kb = 0;
+    for (int k = 1; k < K; ++k)
+        if (e[k] > e[kb]) kb = k;
+    if (dE) *dE = e[kb] - e[0];
+    if (k_max) *k_max = kb;
+    return SS_OK;
+}
+
+ss_status ss_field(ss_ctx* c, int string, void* out, int dtype, int on_device) {
+    TRY(check_string(c, string));
+    TRY(check_dtype(c, dtype));
+    if (!out) return fail(c, SS_ERR_INVALID_ARG, "out is NULL");
+    StringRec& r = c->strs[string];
+    Group& g = c->groups[r.group];
+    TRY(check_paths(c, g));
+    TRY(enter(c));
+    TRY(evaluate_group(c, g, true));
+    const char* base = (const char*)g.hout + (size_t)r.img0 * 3 * g.N * real_size(c);
+    TRY(export_soa(c, base, r.d.n_images, g.N, out, dtype, on_device, 1.0));
+    ss_status st = sync_check(c);
+    TRY(leave(c));
+    return st;
+}
+
+ss_status ss_grad(ss_ctx* c, int string, int image, void* dE_ds, int dtype, int on_device, double* dE_dJDKw) {
+    TRY(check_string(c, string));
+    StringRec& r = c->strs[string];
+    if (image < 0 || image >= r.d.n_images) return fail(c, SS_ERR_INVALID_ARG, "image %d out of range", image);
+    if (dE_ds) TRY(check_dtype(c, dtype));
+    Group& g = c->groups[r.group];
+    TRY(check_paths(c, g));
+    TRY(enter(c));
+    TRY(evaluate_group(c, g, dE_ds != nullptr));
+    if (dE_ds) {
+        const char* base = (const char*)g.hout + (size_t)(r.img0 + image) * 3 * g.N * real_size(c);
+        TRY(export_soa(c, base, 1, g.N, dE_ds, dtype, on_device, -1.0));
+    }
+    if (dE_dJDKw)
+        CUDA_TRY(c, cudaMemcpyAsync(dE_dJDKw, g.eval_terms + ((size_t)r.local * g.arc.maxK + image) * 4,
+                                    4 * sizeof(double), cudaMemcpyDeviceToHost, c->cs));
+    ss_status st = sync_check(c);
+    TRY(leave(c));
+    return st;
+}
+
+ss_status ss_time_kernels(ss_ctx* c, int reps, double* ms_out, int max_out, int* n_out) {
+    if (!c || reps < 1 || !n_out) return c ? fail(c, SS_ERR_INVALID_ARG, "reps >= 1 and n_out required") : SS_ERR_INVALID_ARG;
+    for (const Group& g : c->groups) TRY(check_paths(c, g));
+    const int nk = ss_kernels_per_iteration(c);
+    *n_out = nk;
+    std::vector<cudaEvent_t> ev(2 * nk, nullptr);
+    for (auto& e : ev) CUDA_TRY(c, cudaEventCreate(&e));
+    std::vector<double> acc(nk, 0.0);
+    TRY(enter(c));
+    ss_status st = SS_OK;
+    for (int r = 0; r <= reps && st == SS_OK; ++r) {
+        int k = 0;
+        for (Group& g : c->groups) {
+            auto run = [&](int which) {
+                if (use_fp64(c)) {
+                    GroupArgs<double> a = group_args<double>(c, g);
+                    if (which == 0) launch_xfwd<double>(a, g.dipole, g.thr_a, g.smem_a, c->cs);
+                    if (which == 1) launch_yz<double>(a, g.thr_b, g.smem_b, c->cs);
+                    if (which == 2) launch_xinv_step<double>(a, g.dipole, c->opts.dt, g.thr_c, g.smem_c, c->cs);
+                    if (which == 3) launch_arc<double>(a, g.arc, g.thr_arc, c->cs);
+                } else {
+                    GroupArgs<float> a = group_args<float>(c, g);
+                    if (which == 0) launch_xfwd<float>(a, g.dipole, g.thr_a, g.smem_a, c->cs);
+                    if (which == 1) launch_yz<float>(a, g.thr_b, g.smem_b, c->cs);
+                    if (which == 2) launch_xinv_step<float>(a, g.dipole, (float)c->opts.dt, g.thr_c, g.smem_c, c->cs);
+                    if (which == 3) launch_arc<float>(a, g.arc, g.thr_arc, c->cs);
+                }
+            };
+            for (int which = 0; which < 4; ++which) {
+                if (which == 1 && !g.dipole) continue;
+                cudaEventRecord(ev[2 * k], c->cs);
+                run(which);
+                cudaEventRecord(ev[2 * k + 1], c->cs);
+                ++k;
+            }
+        }
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(c->cs) != cudaSuccess) {
+            st = fail(c, SS_ERR_CUDA, "kernel timing launch failed");
+            break;
+        }
+        if (r == 0) continue;  // untimed iteration
+        for (int i = 0; i < nk; ++i) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]);
+            acc[i] += ms;
+        }
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    if (st != SS_OK) return st;
+    for (int i = 0; i < nk && i < max_out; ++i) ms_out[i] = acc[i] / reps;
+    st = sync_check(c);
+    TRY(leave(c));
+    return st;
+}
+
+int ss_num_strings(const ss_ctx* c) { return c ? (int)c->strs.size() : 0; }
+
+ss_status ss_string_info(const ss_ctx* c, int string, ss_string_desc* out) {
+    if (!c || !out || string < 0 || string >= (int)c->strs.size()) return SS_ERR_INVALID_ARG;
+    *out = c->strs[string].d;
+    return SS_OK;
+}
+
+int ss_kernels_per_iteration(const ss_ctx* c) {
+    if (!c) return 0;
+    int n = 0;
+    for (const Group& g : c->groups) n += g.dipole ? 4 : 3;
+    return n;
+}
+
+const char* ss_last_error(const ss_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+void ss_destroy(ss_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->cs) cudaStreamSynchronize(c->cs);
+    if (c->graph1) cudaGraphExecDestroy(c->graph1);
+    if (c->graphN) cudaGraphExecDestroy(c->graphN);
+    for (void* p : c->allocs) cudaFree(p);
+    if (c->ev_in) cudaEventDestroy(c->ev_in);
+    if (c->ev_out) cudaEventDestroy(c->ev_out);
+    if (c->cs) cudaStreamDestroy(c->cs);
+    delete c;
+}
+
+}  // extern "C"

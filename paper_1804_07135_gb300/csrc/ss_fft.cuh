@@ -1,0 +1,152 @@
+// ss_fft.cuh -- batched complex FFTs of lines held in shared memory (Sec. II-A: the dipole field as a
+// zero-padded convolution evaluated with FFTs).
+//
+// Lines of length P (P = 2^a 3^b) sit in shared memory with stride LS >= P complex elements.  The
+// transform is a mixed-radix Stockham autosort FFT (radices 8, 4, 3, 2) done in place: in each stage
+// every thread reads its butterflies' inputs into registers, the block synchronises, and the outputs
+// are written to their autosorted positions.  Twiddles W_P^k = exp(-2 pi i k / P) come from a table in
+// shared memory that the host computed in FP64.  Forward transforms only; an inverse is obtained by
+// conjugating on load and on store.
+#pragma once
+#include "ss_internal.h"
+
+namespace ss {
+
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return C{a.x + b.x, a.y + b.y}; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return C{a.x - b.x, a.y - b.y}; }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+    return C{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename C> __device__ __forceinline__ C cconj(C a) { return C{a.x, -a.y}; }
+// multiply by -i
+template <typename C> __device__ __forceinline__ C cmi(C a) { return C{a.y, -a.x}; }
+
+// Size-R forward DFTs in registers.
+template <int R, typename C> struct Dft;
+
+template <typename C> struct Dft<2, C> {
+    static __device__ __forceinline__ void run(C* v) {
+        C a = v[0];
+        v[0] = cadd(a, v[1]);
+        v[1] = csub(a, v[1]);
+    }
+};
+
+template <typename C> struct Dft<3, C> {
+    static __device__ __forceinline__ void run(C* v) {
+        using R = decltype(v[0].x);
+        const R h = R(0.8660254037844386467637231707529362);  // sqrt(3)/2
+        C s = cadd(v[1], v[2]);
+        C d = csub(v[1], v[2]);
+        C m = C{v[0].x - R(0.5) * s.x, v[0].y - R(0.5) * s.y};
+        C r = cmi(d);  // -i d
+        v[0] = cadd(v[0], s);
+        v[1] = C{m.x + h * r.x, m.y + h * r.y};
+        v[2] = C{m.x - h * r.x, m.y - h * r.y};
+    }
+};
+
+template <typename C> struct Dft<4, C> {
+    static __device__ __forceinline__ void run(C* v) {
+        C a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
+        C c = cadd(v[1], v[3]), d = cmi(csub(v[1], v[3]));
+        v[0] = cadd(a, c);
+        v[2] = csub(a, c);
+        v[1] = cadd(b, d);
+        v[3] = csub(b, d);
+    }
+};
+
+template <typename C> struct Dft<8, C> {
+    static __device__ __forceinline__ void run(C* v) {
+        using R = decltype(v[0].x);
+        const R q = R(0.7071067811865475244008443621048490);  // sqrt(2)/2
+        C e[4] = {v[0], v[2], v[4], v[6]};
+        C o[4] = {v[1], v[3], v[5], v[7]};
+        Dft<4, C>::run(e);
+        Dft<4, C>::run(o);
+        // twiddles W8^k, k = 0..3: 1, (q,-q), -i, (-q,-q)
+        C t1 = C{q * (o[1].x + o[1].y), q * (o[1].y - o[1].x)};
+        C t2 = cmi(o[2]);
+        C t3 = C{q * (o[3].y - o[3].x), -q * (o[3].x + o[3].y)};
+        v[0] = cadd(e[0], o[0]);
+        v[4] = csub(e[0], o[0]);
+        v[1] = cadd(e[1], t1);
+        v[5] = csub(e[1], t1);
+        v[2] = cadd(e[2], t2);
+        v[6] = csub(e[2], t2);
+        v[3] = cadd(e[3], t3);
+        v[7] = csub(e[3], t3);
+    }
+};
+
+// Elements each thread holds in registers per stage: 8 (9 for radix 3).  Lines are transformed in
+// passes of fft_lines_per_pass() lines, so any block of at least P/8 threads can transform any number
+// of lines.
+template <int R> struct StageCap { static constexpr int B = R == 2 ? 4 : R == 3 ? 3 : R == 4 ? 2 : 1; };
+constexpr int kFftElemsPerThread = 8;
+
+__host__ __device__ inline int fft_lines_per_pass(int nthr, int P) { return (nthr * kFftElemsPerThread) / P; }
+// Smallest block that can transform lines of length P.
+__host__ __device__ inline int fft_min_threads(int P) { return (P + kFftElemsPerThread - 1) / kFftElemsPerThread; }
+
+template <int R, typename C>
+__device__ __forceinline__ void fft_stage(C* buf, const C* tw, int P, int LS, int L, int Ns, int tid, int nthr) {
+    constexpr int B = StageCap<R>::B;
+    const int Q = P / R;
+    const int total = L * Q;
+    const int twstep = P / (Ns * R);
+    C v[B][R];
+    int dst[B];
+#pragma unroll
+    for (int i = 0; i < B; ++i) {
+        const int b = tid + i * nthr;
+        dst[i] = -1;
+        if (b < total) {
+            const int line = b / Q, j = b - line * Q;
+            const int jm = j % Ns;
+            const C* src = buf + line * LS + j;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                C x = src[r * Q];
+                if (r > 0) x = cmul(x, tw[jm * r * twstep]);
+                v[i][r] = x;
+            }
+            Dft<R, C>::run(v[i]);
+            dst[i] = line * LS + (j - jm) * R + jm;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < B; ++i) {
+        if (dst[i] >= 0) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) buf[dst[i] + r * Ns] = v[i][r];
+        }
+    }
+    __syncthreads();
+}
+
+// Forward FFT of L lines (stride LS) in shared memory.  Must be called by every thread of the block,
+// with blockDim.x >= fft_min_threads(P).  Ends synchronised.
+template <typename C>
+__device__ __forceinline__ void fft_lines(C* buf, const C* tw, const FftPlan& plan, int LS, int L, int tid, int nthr) {
+    const int lpp = max(1, fft_lines_per_pass(nthr, plan.P));  // the host guarantees >= 1; never loop forever
+    for (int l0 = 0; l0 < L; l0 += lpp) {
+        const int nl = min(lpp, L - l0);
+        C* b = buf + l0 * LS;
+        int Ns = 1;
+        for (int st = 0; st < plan.nstages; ++st) {
+            const int R = plan.radix[st];
+            switch (R) {
+                case 8: fft_stage<8>(b, tw, plan.P, LS, nl, Ns, tid, nthr); break;
+                case 4: fft_stage<4>(b, tw, plan.P, LS, nl, Ns, tid, nthr); break;
+                case 3: fft_stage<3>(b, tw, plan.P, LS, nl, Ns, tid, nthr); break;
+                default: fft_stage<2>(b, tw, plan.P, LS, nl, Ns, tid, nthr); break;
+            }
+            Ns *= R;
+        }
+    }
+}
+
+}  // namespace ss

@@ -1,0 +1,109 @@
+// ss_internal.h -- types shared by the host runtime (ss_api.cu) and the kernels (ss_kernels.cuh).
+//
+// Data layout in device memory, per size group (strings whose lattices have the same dimensions):
+//   s, sp   [image][3][N]            spins before / after the step (SoA planes, x fastest), N = nx*ny*nz
+//   spec    [pair][Px][3][nz][ny]    complex spectra of image pairs after the x transform (y fastest);
+//                                    the y/z kernel overwrites them in place with the field spectra
+//   dhat    [Px/2+1][Py/2+1][nz][6]  one octant of the dipole-tensor spectrum (real coefficients)
+// Two images (2p, 2p+1) share one complex field (real part = image 2p, imaginary part = image 2p+1):
+// the dipole kernel is real in real space, so one complex convolution serves both images.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ss {
+
+template <typename T> struct cplx_of;
+template <> struct cplx_of<float> { using type = float2; };
+template <> struct cplx_of<double> { using type = double2; };
+template <typename T> using cplx = typename cplx_of<T>::type;
+
+constexpr int kMaxStages = 16;
+constexpr int kMaxThreadsX = 512;   // block-size ceiling of the x-transform kernels
+constexpr int kMaxThreadsYz = 768;  // block-size ceiling of the y/z kernel
+constexpr int kArcMaxChunk = 8;     // image differences one arc CTA accumulates
+constexpr int kArcMaxK = 1024;      // images per string
+
+// Mixed-radix (2, 3, 4, 8) plan of a length-P complex FFT, stages in Stockham order.
+struct FftPlan {
+    int P;
+    int nstages;
+    int radix[kMaxStages];
+};
+
+// Reparametrisation source of one image: normalise((1 - t) sp[src0] + t sp[src1]), or an exact copy
+// of sp[src0] when copy != 0.  Image indices are local to the size group.
+struct InterpEntry {
+    int src0, src1;
+    double t;
+    int copy;
+    int pad;
+};
+
+// Constants of the string an image belongs to.
+template <typename T> struct ImgParam {
+    T J, D, K, w;
+};
+
+template <typename T> struct GroupArgs {
+    int nx, ny, nz, N;
+    int Px, Py;
+    int n_img, n_pairs;
+    int lsx, lsy;  // shared-memory line strides (complex elements) of the x and y transforms
+    T* s;
+    T* sp;
+    cplx<T>* spec;
+    const T* dhat;
+    const cplx<T>* twx;
+    const cplx<T>* twy;
+    FftPlan planx, plany;
+    const ImgParam<T>* prm;
+    const InterpEntry* interp;
+    double* epart;  // per-image energy partials, [image][n_eblk] (step) or [image][4][n_eblk] (eval)
+    int n_eblk;     // = nz * ceil(ny / ty_c)
+    int ty_a, ty_c; // y rows per CTA in the x-forward and x-inverse kernels
+    int* err;       // sticky error word (bit 1: invalid input spin, bit 2: non-finite value)
+};
+
+// Arc-length / reparametrisation bookkeeping of one size group.
+struct ArcArgs {
+    int n_str;             // strings in the group
+    const int* str_img0;   // [n_str] first group-local image of each string
+    const int* str_K;      // [n_str] images per string
+    int maxK;
+    int n_tiles;           // spatial tiles of the 3N component vector
+    int tile_elems;        // components per tile
+    int kchunk;            // image differences per CTA along the string
+    int n_kchunks;
+    double* dpart;         // [n_str][maxK][n_tiles] squared-distance partials
+    unsigned* counters;    // [n_str] arrival tickets of the last-CTA finalisation
+    double* e_last;        // [n_str][maxK] energies of the state before the step
+    int reparam;           // 0: keep images where they are
+};
+
+enum { kErrInvalidSpin = 1, kErrNonFinite = 2 };
+
+// ---- launchers (defined in ss_kernels.cuh, instantiated for float and double) ----
+template <typename T> void launch_xfwd(const GroupArgs<T>& g, bool do_fft, int nthr, size_t smem, cudaStream_t st);
+template <typename T> void launch_yz(const GroupArgs<T>& g, int nthr, size_t smem, cudaStream_t st);
+template <typename T>
+void launch_xinv_step(const GroupArgs<T>& g, bool do_fft, T dt, int nthr, size_t smem, cudaStream_t st);
+template <typename T>
+void launch_xinv_eval(const GroupArgs<T>& g, bool do_fft, T* hout, int nthr, size_t smem, cudaStream_t st);
+template <typename T> void launch_arc(const GroupArgs<T>& g, const ArcArgs& a, int nthr, cudaStream_t st);
+template <typename T>
+void launch_eval_reduce(const GroupArgs<T>& g, const ArcArgs& a, double* terms, double* energies, cudaStream_t st);
+template <typename T, typename Tin>
+void launch_aos_to_soa(const Tin* src, T* dst, int K, int N, int* err, cudaStream_t st);
+template <typename T, typename Tout>
+void launch_soa_to_aos(const T* src, Tout* dst, int K, int N, Tout scale, cudaStream_t st);
+void launch_interp_identity(InterpEntry* tab, int img0, int K, cudaStream_t st);
+// FP64 setup of the dipole-tensor spectrum: x then y transforms of the padded real-space tensor
+// (data [6*nz][Py][Px] complex, in place), then the octant extraction into dhat.
+void launch_fft_strided_f64(double2* data, const double2* tw, const FftPlan& plan, int n_lines, long elem_stride,
+                            int inner_count, long inner_stride, long outer_stride, cudaStream_t st);
+template <typename T> void set_smem_limits(int bytes);
+template <typename T>
+void launch_extract_octant(const double2* spec, T* dhat, int Px, int Py, int nz, double scale, cudaStream_t st);
+
+}  // namespace ss

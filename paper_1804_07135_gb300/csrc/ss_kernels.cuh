@@ -1,0 +1,677 @@
+// ss_kernels.cuh -- the per-iteration kernels of the string method, templated on the real type
+// (float: FP32 spins/fields/FFTs with FP64 reductions; double: the plain FP64 method).
+//
+// One iteration over a size group is four launches:
+//   xfwd   (Sec. III interpolation + Sec. II-A)  materialise s = reparam(sp), x-transform of image pairs
+//   yz     (Sec. II-A, Eqs. 6-7)                 y-transform, z-convolution with the tensor spectrum,
+//                                                inverse y-transform (in place on the spectra)
+//   xinv   (Eqs. 3-5, 8, 10, 13)                 inverse x-transform -> dipole field, local field,
+//                                                per-image energy partials, projected step -> sp
+//   arc    (Eqs. 11-12)                          squared image distances; the last CTA of each string
+//                                                sums energies and distances in a fixed order, scans the
+//                                                arc length and writes the interpolation table
+#pragma once
+#include <math.h>
+
+#include <algorithm>
+
+#include "ss_fft.cuh"
+
+namespace ss {
+
+// ------------------------------------------------------------------------------------------------
+// small helpers
+template <typename T> __device__ __forceinline__ T rsqrt_t(T x);
+template <> __device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return 1.0 / sqrt(x); }
+
+// Fixed-order block reduction of NV doubles per thread; result valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_reduce_d(double (&v)[NV], double* scratch /* [32*NV] */) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) scratch[warp * NV + k] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double a = 0.0;
+            for (int w = 0; w < nwarp; ++w) a += scratch[w * NV + k];
+            v[k] = a;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// xfwd: grid (ceil(ny/ty_a), nz, n_pairs).  Each CTA takes rows [y0, y0+rows) of layer z for the two
+// images of pair p: s[img] = normalise((1-t) sp[src0] + t sp[src1]) (or a copy), written back to s,
+// packed as re/im of 3*rows complex lines, zero-padded to Px and transformed along x.
+// Output spec[p][kx][c][z][y].
+template <typename T, bool DO_FFT>
+__global__ void __launch_bounds__(kMaxThreadsX) xfwd_kernel(GroupArgs<T> g) {
+    using C = cplx<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* buf = tw + g.Px;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int p = blockIdx.z, z = blockIdx.y, y0 = blockIdx.x * g.ty_a;
+    const int rows = min(g.ty_a, g.ny - y0);
+    const int nx = g.nx, N = g.N;
+    const int ia = 2 * p;
+    if (DO_FFT)
+        for (int i = tid; i < g.Px; i += nthr) tw[i] = g.twx[i];
+    for (int it = tid; it < rows * nx; it += nthr) {
+        const int yy = it / nx, x = it - yy * nx;
+        const int site = (z * g.ny + y0 + yy) * nx + x;
+        T out[2][3];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int im = ia + h;
+            out[h][0] = out[h][1] = out[h][2] = T(0);
+            if (im < g.n_img) {
+                const InterpEntry e = g.interp[im];
+                const T* a = g.sp + (size_t)e.src0 * 3 * N + site;
+                T u0 = a[0], u1 = a[N], u2 = a[2 * N];
+                if (!e.copy) {
+                    const T t = T(e.t), omt = T(1.0 - e.t);
+                    const T* b = g.sp + (size_t)e.src1 * 3 * N + site;
+                    u0 = omt * u0 + t * b[0];
+                    u1 = omt * u1 + t * b[N];
+                    u2 = omt * u2 + t * b[2 * N];
+                    const T r = rsqrt_t<T>(u0 * u0 + u1 * u1 + u2 * u2);
+                    u0 *= r;
+                    u1 *= r;
+                    u2 *= r;
+                }
+                T* d = g.s + (size_t)im * 3 * N + site;
+                d[0] = u0;
+                d[N] = u1;
+                d[2 * N] = u2;
+                out[h][0] = u0;
+                out[h][1] = u1;
+                out[h][2] = u2;
+            }
+        }
+        if (DO_FFT) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) buf[(c * rows + yy) * g.lsx + x] = C{out[0][c], out[1][c]};
+        }
+    }
+    if (!DO_FFT) return;
+    const int padw = g.Px - nx;
+    for (int it = tid; it < 3 * rows * padw; it += nthr) {
+        const int line = it / padw, x = nx + (it - line * padw);
+        buf[line * g.lsx + x] = C{T(0), T(0)};
+    }
+    __syncthreads();
+    fft_lines(buf, tw, g.planx, g.lsx, 3 * rows, tid, nthr);
+    // transpose out: consecutive threads take consecutive y of one (kx, c)
+    C* outp = g.spec + (size_t)p * g.Px * 3 * g.nz * g.ny;
+    for (int it = tid; it < g.Px * 3 * rows; it += nthr) {
+        const int yy = it % rows, rest = it / rows;
+        const int c = rest % 3, kx = rest / 3;
+        outp[((size_t)(kx * 3 + c) * g.nz + z) * g.ny + y0 + yy] = buf[(c * rows + yy) * g.lsx + kx];
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Dipole-tensor spectrum lookup: stored octant value with the per-axis parity signs of Eq. 7's
+// components (xx, yy, zz, xy: real; xz, yz: imaginary, returned as the coefficient of i).
+// Parities (x, y, z): xx/yy/zz even-even-even, xy odd-odd-even, xz odd-even-odd, yz even-odd-odd.
+
+// yz: grid (Px, n_pairs).  Lines (c, z) of length Py: y-transform (rows y >= ny are zero), then for
+// each (ky, z) the field spectrum H_a(z) = sum_{z', b} Dhat_ab(kx, ky, z - z') S_b(z'), then the
+// inverse y-transform; rows y < ny are written back in place.  The z-convolution stages up to
+// kYzItems (ky, z) results per thread in registers, so one shared buffer serves both transforms.
+constexpr int kYzItems = 4;
+
+template <typename T>
+__global__ void __launch_bounds__(kMaxThreadsYz) yz_kernel(GroupArgs<T> g) {
+    using C = cplx<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* A = tw + g.Py;  // 3*nz lines of stride lsy
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int kx = blockIdx.x, p = blockIdx.y;
+    const int ny = g.ny, nz = g.nz, Py = g.Py, L = 3 * nz;
+    C* blk = g.spec + ((size_t)p * g.Px + kx) * 3 * nz * ny;
+    for (int i = tid; i < Py; i += nthr) tw[i] = g.twy[i];
+    for (int it = tid; it < L * Py; it += nthr) {
+        const int line = it / Py, y = it - line * Py;
+        A[line * g.lsy + y] = (y < ny) ? blk[line * ny + y] : C{T(0), T(0)};
+    }
+    __syncthreads();
+    fft_lines(A, tw, g.plany, g.lsy, L, tid, nthr);
+    // z-convolution with the tensor spectrum, in passes of whole ky columns (item = ky * nz + z)
+    const int hx = g.Px / 2, hy = Py / 2;
+    const int kxo = min(kx, g.Px - kx);
+    const T sxg = kx > hx ? T(-1) : T(1);
+    const int n_items = Py * nz;
+    const int per_pass = max(nz, ((nthr * kYzItems) / nz) * nz);
+    for (int base = 0; base < n_items; base += per_pass) {
+        const int end = min(n_items, base + per_pass);
+        C res[kYzItems][3];
+#pragma unroll
+        for (int q = 0; q < kYzItems; ++q) {
+            const int it = base + tid + q * nthr;
+            if (it < end) {
+                const int ky = it / nz, z = it - ky * nz;
+                const int kyo = min(ky, Py - ky);
+                const T syg = ky > hy ? T(-1) : T(1);
+                const T* dcol = g.dhat + ((size_t)kxo * (hy + 1) + kyo) * nz * 6;
+                C hx_ = {T(0), T(0)}, hy_ = {T(0), T(0)}, hz_ = {T(0), T(0)};
+#pragma unroll 1
+                for (int zp = 0; zp < nz; ++zp) {
+                    const int dz = z - zp;
+                    const T szg = dz < 0 ? T(-1) : T(1);
+                    const T* d = dcol + (dz < 0 ? -dz : dz) * 6;
+                    const T dxx = d[0], dyy = d[1], dzz = d[2];
+                    const T dxy = d[3] * sxg * syg;
+                    const T dxz = d[4] * sxg * szg;  // coefficient of i
+                    const T dyz = d[5] * syg * szg;  // coefficient of i
+                    const C sx = A[(0 * nz + zp) * g.lsy + ky];
+                    const C sy = A[(1 * nz + zp) * g.lsy + ky];
+                    const C sz = A[(2 * nz + zp) * g.lsy + ky];
+                    // i*c*S = (-c S.y, c S.x)
+                    hx_.x += dxx * sx.x + dxy * sy.x - dxz * sz.y;
+                    hx_.y += dxx * sx.y + dxy * sy.y + dxz * sz.x;
+                    hy_.x += dxy * sx.x + dyy * sy.x - dyz * sz.y;
+                    hy_.y += dxy * sx.y + dyy * sy.y + dyz * sz.x;
+                    hz_.x += -dxz * sx.y - dyz * sy.y + dzz * sz.x;
+                    hz_.y += dxz * sx.x + dyz * sy.x + dzz * sz.y;
+                }
+                res[q][0] = hx_;
+                res[q][1] = hy_;
+                res[q][2] = hz_;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kYzItems; ++q) {
+            const int it = base + tid + q * nthr;
+            if (it < end) {
+                const int ky = it / nz, z = it - ky * nz;
+                // conjugated: the inverse transform is the conjugate of the forward transform of the conjugate
+#pragma unroll
+                for (int c = 0; c < 3; ++c) A[(c * nz + z) * g.lsy + ky] = cconj(res[q][c]);
+            }
+        }
+        __syncthreads();
+    }
+    fft_lines(A, tw, g.plany, g.lsy, L, tid, nthr);
+    for (int it = tid; it < L * ny; it += nthr) {
+        const int line = it / ny, y = it - line * ny;
+        blk[line * ny + y] = cconj(A[line * g.lsy + y]);
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// xinv: grid (ceil(ny/ty_c), nz, n_pairs).  Inverse x-transform of the pair's field spectra (the
+// tensor spectrum already carries 4 pi / (Px Py)), then per site of both images:
+//   h = J sum_nn s_j                                                     (Eq. 3)
+//     - D (s_z^{+x} - s_z^{-x}, s_z^{+y} - s_z^{-y}, -s_x^{+x} + s_x^{-x} - s_y^{+y} + s_y^{-y})  (Eq. 4)
+//     + 2 K s_z z                                                        (Eq. 5)
+//     + w * dipole convolution                                           (Eq. 6)
+// MODE 0 (step): e += -(1/2) h.s (Eq. 8), s' = normalise(s + dt (h - (s.h) s)) (Eqs. 10, 13).
+// MODE 1 (eval): FP64 energy terms of the FP64-renormalised spins, bonds to +x, +y, +z counted once
+//                (Eq. 1): tJ = -sum s_i.s_j, tD = sum (r_ij x z).(s_i x s_j), tK = -sum s_z^2,
+//                tw = -(1/2) sum conv.s; optionally the field h.
+template <typename T, bool DO_FFT, int MODE>
+__global__ void __launch_bounds__(kMaxThreadsX) xinv_kernel(GroupArgs<T> g, T dt, T* hout) {
+    using C = cplx<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* buf = tw + g.Px;
+    double* red = reinterpret_cast<double*>(buf + (DO_FFT ? 3 * g.ty_c * g.lsx : 0));
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int p = blockIdx.z, z = blockIdx.y, y0 = blockIdx.x * g.ty_c;
+    const int rows = min(g.ty_c, g.ny - y0);
+    const int nx = g.nx, ny = g.ny, nz = g.nz, N = g.N;
+    const int ia = 2 * p;
+    if (DO_FFT) {
+        for (int i = tid; i < g.Px; i += nthr) tw[i] = g.twx[i];
+        const C* inp = g.spec + (size_t)p * g.Px * 3 * nz * ny;
+        for (int it = tid; it < g.Px * 3 * rows; it += nthr) {
+            const int yy = it % rows, rest = it / rows;
+            const int c = rest % 3, kx = rest / 3;
+            buf[(c * rows + yy) * g.lsx + kx] = cconj(inp[((size_t)(kx * 3 + c) * nz + z) * ny + y0 + yy]);
+        }
+        __syncthreads();
+        fft_lines(buf, tw, g.planx, g.lsx, 3 * rows, tid, nthr);
+    }
+    constexpr int NV = MODE == 0 ? 2 : 8;
+    double acc[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+    for (int it = tid; it < 2 * rows * nx; it += nthr) {
+        const int h = it / (rows * nx);
+        const int rem = it - h * rows * nx;
+        const int yy = rem / nx, x = rem - yy * nx;
+        const int im = ia + h;
+        if (im >= g.n_img) continue;
+        const int y = y0 + yy;
+        const int site = (z * ny + y) * nx + x;
+        const ImgParam<T> pr = g.prm[im];
+        const T* sb = g.s + (size_t)im * 3 * N;
+        T s0[3], xp[3], xm[3], yp[3], ym[3], zp[3], zm[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const T* q = sb + (size_t)c * N + site;
+            s0[c] = q[0];
+            xp[c] = x + 1 < nx ? q[1] : T(0);
+            xm[c] = x > 0 ? q[-1] : T(0);
+            yp[c] = y + 1 < ny ? q[nx] : T(0);
+            ym[c] = y > 0 ? q[-nx] : T(0);
+            zp[c] = z + 1 < nz ? q[nx * ny] : T(0);
+            zm[c] = z > 0 ? q[-nx * ny] : T(0);
+        }
+        T conv[3] = {T(0), T(0), T(0)};
+        if (DO_FFT) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const C v = buf[(c * rows + yy) * g.lsx + x];
+                conv[c] = h == 0 ? v.x : -v.y;  // conjugate of the forward transform of the conjugate
+            }
+        }
+        T hf[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) hf[c] = pr.J * (xp[c] + xm[c] + yp[c] + ym[c] + zp[c] + zm[c]) + pr.w * conv[c];
+        hf[0] += -pr.D * (xp[2] - xm[2]);
+        hf[1] += -pr.D * (yp[2] - ym[2]);
+        hf[2] += -pr.D * (-xp[0] + xm[0] - yp[1] + ym[1]) + T(2) * pr.K * s0[2];
+        if (MODE == 0) {
+            const T sh = s0[0] * hf[0] + s0[1] * hf[1] + s0[2] * hf[2];
+            acc[h] += double(T(-0.5) * sh);
+            T u[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) u[c] = s0[c] + dt * (hf[c] - sh * s0[c]);
+            const T r = rsqrt_t<T>(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+            T* o = g.sp + (size_t)im * 3 * N + site;
+            o[0] = u[0] * r;
+            o[N] = u[1] * r;
+            o[2 * N] = u[2] * r;
+        } else {
+            auto nrm = [](const T* v, double* o) {
+                const double a = v[0], b = v[1], c = v[2];
+                const double n2 = a * a + b * b + c * c;
+                const double r = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
+                o[0] = a * r;
+                o[1] = b * r;
+                o[2] = c * r;
+            };
+            double si[3], sx[3], sy[3], sz[3];
+            nrm(s0, si);
+            double tJ = 0.0, tD = 0.0;
+            if (x + 1 < nx) {
+                nrm(xp, sx);
+                tJ -= si[0] * sx[0] + si[1] * sx[1] + si[2] * sx[2];
+                tD -= si[2] * sx[0] - si[0] * sx[2];  // (x x z) = -y: -(s_i x s_j)_y
+            }
+            if (y + 1 < ny) {
+                nrm(yp, sy);
+                tJ -= si[0] * sy[0] + si[1] * sy[1] + si[2] * sy[2];
+                tD += si[1] * sy[2] - si[2] * sy[1];  // (y x z) = +x: (s_i x s_j)_x
+            }
+            if (z + 1 < nz) {
+                nrm(zp, sz);
+                tJ -= si[0] * sz[0] + si[1] * sz[1] + si[2] * sz[2];
+            }
+            const double tK = -si[2] * si[2];
+            const double tw_ = -0.5 * ((double)conv[0] * si[0] + (double)conv[1] * si[1] + (double)conv[2] * si[2]);
+            acc[4 * h + 0] += tJ;
+            acc[4 * h + 1] += tD;
+            acc[4 * h + 2] += tK;
+            acc[4 * h + 3] += tw_;
+            if (hout) {
+                T* o = hout + (size_t)im * 3 * N + site;
+                o[0] = hf[0];
+                o[N] = hf[1];
+                o[2 * N] = hf[2];
+            }
+        }
+    }
+    block_reduce_d<NV>(acc, red);
+    if (tid == 0) {
+        const int blk = blockIdx.y * gridDim.x + blockIdx.x;
+        for (int h = 0; h < 2; ++h) {
+            const int im = ia + h;
+            if (im >= g.n_img) continue;
+            if (MODE == 0) {
+                g.epart[(size_t)im * g.n_eblk + blk] = acc[h];
+            } else {
+                for (int k = 0; k < 4; ++k) g.epart[((size_t)im * 4 + k) * g.n_eblk + blk] = acc[4 * h + k];
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// arc: grid (n_tiles, n_kchunks, n_str).  Squared distances |sp_k - sp_{k-1}|^2 over all 3N
+// components (Eq. 11), partial per tile.  The last CTA of a string (arrival ticket) sums the
+// partials in tile order, sums the energy partials in block order, scans the arc length, and for
+// every interior image k finds the largest j with alpha*_j <= k/(K-1) and t (Eq. 12).
+
+template <typename T>
+__global__ void __launch_bounds__(256) arc_kernel(GroupArgs<T> g, ArcArgs a) {
+    __shared__ double red[32 * kArcMaxChunk];
+    __shared__ double alpha[kArcMaxK];
+    __shared__ int is_last;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int str = blockIdx.z;
+    const int K = a.str_K[str], img0 = a.str_img0[str];
+    const int k_lo = blockIdx.y * a.kchunk;
+    const int nd = max(0, min(a.kchunk, K - 1 - k_lo));  // differences (k_lo+i, k_lo+i+1), i < nd
+    const size_t M = (size_t)3 * g.N;
+    const size_t e0 = (size_t)blockIdx.x * a.tile_elems;
+    const size_t e1 = min(M, e0 + a.tile_elems);
+    double acc[kArcMaxChunk];
+#pragma unroll
+    for (int i = 0; i < kArcMaxChunk; ++i) acc[i] = 0.0;
+    if (nd > 0) {
+        for (size_t e = e0 + tid; e < e1; e += nthr) {
+            const T* col = g.sp + (size_t)(img0 + k_lo) * M + e;
+            T prev = col[0];
+#pragma unroll
+            for (int i = 0; i < kArcMaxChunk; ++i) {
+                if (i < nd) {
+                    const T cur = col[(size_t)(i + 1) * M];
+                    const T d = cur - prev;
+                    acc[i] += double(d * d);
+                    prev = cur;
+                }
+            }
+        }
+    }
+    block_reduce_d<kArcMaxChunk>(acc, red);
+    if (tid == 0) {
+        for (int i = 0; i < nd; ++i) a.dpart[((size_t)str * a.maxK + k_lo + i + 1) * a.n_tiles + blockIdx.x] = acc[i];
+        __threadfence();
+        const unsigned total = gridDim.x * gridDim.y;
+        const unsigned ticket = atomicAdd(a.counters + str, 1u);
+        is_last = (ticket == total - 1);
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    // ---- finalisation by the last CTA of this string ----
+    for (int k = tid; k < K; k += nthr) {
+        double e = 0.0;
+        const double* ep = g.epart + (size_t)(img0 + k) * g.n_eblk;
+        for (int b = 0; b < g.n_eblk; ++b) e += ep[b];
+        a.e_last[(size_t)str * a.maxK + k] = e;
+        double d2 = 0.0;
+        if (k > 0) {
+            const double* dp = a.dpart + ((size_t)str * a.maxK + k) * a.n_tiles;
+            for (int t = 0; t < a.n_tiles; ++t) d2 += __ldcg(dp + t);  // written by other CTAs
+        }
+        alpha[k] = sqrt(d2);
+        if (!isfinite(e) || !isfinite(d2)) atomicOr(g.err, kErrNonFinite);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double s = 0.0;
+        for (int k = 0; k < K; ++k) {
+            s += alpha[k];
+            alpha[k] = s;  // s_k, with s_0 = 0
+        }
+        a.counters[str] = 0u;
+    }
+    __syncthreads();
+    const double sK = alpha[K - 1];
+    const bool move = a.reparam && sK > 0.0 && isfinite(sK);
+    for (int k = tid; k < K; k += nthr) {
+        InterpEntry e;
+        e.src0 = img0 + k;
+        e.src1 = img0 + k;
+        e.t = 0.0;
+        e.copy = 1;
+        e.pad = 0;
+        if (move && k > 0 && k < K - 1) {
+            const double ak = (double)k / (double)(K - 1);
+            int j = 0;
+            for (int i = 0; i <= K - 2; ++i)
+                if (alpha[i] / sK <= ak) j = i;
+            const double aj = alpha[j] / sK, aj1 = alpha[j + 1] / sK;
+            e.src0 = img0 + j;
+            e.src1 = img0 + j + 1;
+            e.t = (ak - aj) / (aj1 - aj);
+            e.copy = 0;
+        }
+        const_cast<InterpEntry*>(g.interp)[img0 + k] = e;
+    }
+}
+
+// eval reduce: grid (n_str), thread per image: terms[str][k][4] and energies[str][k] in FP64.
+template <typename T>
+__global__ void eval_reduce_kernel(GroupArgs<T> g, ArcArgs a, double* terms, double* energies) {
+    const int str = blockIdx.x;
+    const int K = a.str_K[str], img0 = a.str_img0[str];
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        const int im = img0 + k;
+        double t[4];
+        for (int q = 0; q < 4; ++q) {
+            double v = 0.0;
+            const double* ep = g.epart + ((size_t)im * 4 + q) * g.n_eblk;
+            for (int b = 0; b < g.n_eblk; ++b) v += ep[b];
+            t[q] = v;
+            terms[((size_t)str * a.maxK + k) * 4 + q] = v;
+        }
+        const ImgParam<T> pr = g.prm[im];
+        const double e = (double)pr.J * t[0] + (double)pr.D * t[1] + (double)pr.K * t[2] + (double)pr.w * t[3];
+        energies[(size_t)str * a.maxK + k] = e;
+        if (!isfinite(e)) atomicOr(g.err, kErrNonFinite);
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// layout conversion: caller [K][N][3] <-> internal [K][3][N]; input spins normalised in FP64.
+template <typename T, typename Tin>
+__global__ void aos_to_soa_kernel(const Tin* src, T* dst, int K, int N, int* err) {
+    const size_t total = (size_t)K * N;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t k = i / N, n = i - k * N;
+        const double a = src[3 * i], b = src[3 * i + 1], c = src[3 * i + 2];
+        const double n2 = a * a + b * b + c * c;
+        double r = 0.0;
+        if (!(n2 > 0.0) || !isfinite(n2)) {
+            atomicOr(err, kErrInvalidSpin);
+        } else {
+            r = 1.0 / sqrt(n2);
+        }
+        T* d = dst + k * 3 * N + n;
+        d[0] = T(a * r);
+        d[N] = T(b * r);
+        d[2 * N] = T(c * r);
+    }
+}
+
+template <typename T, typename Tout>
+__global__ void soa_to_aos_kernel(const T* src, Tout* dst, int K, int N, Tout scale) {
+    const size_t total = (size_t)K * N;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t k = i / N, n = i - k * N;
+        const T* s = src + k * 3 * N + n;
+        dst[3 * i] = scale * Tout(s[0]);
+        dst[3 * i + 1] = scale * Tout(s[N]);
+        dst[3 * i + 2] = scale * Tout(s[2 * N]);
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+#ifdef SS_COMMON_LAUNCHERS
+// setup: strided FP64 line FFTs (one line per 1..n lines per CTA) and the octant extraction.
+__global__ void __launch_bounds__(256) fft_strided_f64_kernel(double2* data, const double2* twg, FftPlan plan, int n_lines, int lines_per_cta,
+                                       long elem_stride, int inner_count, long inner_stride, long outer_stride) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double2* tw = reinterpret_cast<double2*>(smem_raw);
+    double2* buf = tw + plan.P;
+    const int P = plan.P, tid = threadIdx.x, nthr = blockDim.x;
+    const int l0 = blockIdx.x * lines_per_cta;
+    const int L = min(lines_per_cta, n_lines - l0);
+    for (int i = tid; i < P; i += nthr) tw[i] = twg[i];
+    for (int it = tid; it < L * P; it += nthr) {
+        const int i = it / P, e = it - i * P;
+        const int l = l0 + i;
+        const long base = (long)(l % inner_count) * inner_stride + (long)(l / inner_count) * outer_stride;
+        buf[i * P + e] = data[base + e * elem_stride];
+    }
+    __syncthreads();
+    fft_lines(buf, tw, plan, P, L, tid, nthr);
+    for (int it = tid; it < L * P; it += nthr) {
+        const int i = it / P, e = it - i * P;
+        const int l = l0 + i;
+        const long base = (long)(l % inner_count) * inner_stride + (long)(l / inner_count) * outer_stride;
+        data[base + e * elem_stride] = buf[i * P + e];
+    }
+}
+
+#endif
+
+// spec [6][nz][Py][Px] complex (component-major) -> dhat [Px/2+1][Py/2+1][nz][6], scaled.
+template <typename T>
+__global__ void extract_octant_kernel(const double2* spec, T* dhat, int Px, int Py, int nz, double scale) {
+    const int hx = Px / 2 + 1, hy = Py / 2 + 1;
+    const size_t total = (size_t)hx * hy * nz * 6;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int c = i % 6;
+        size_t r = i / 6;
+        const int dz = r % nz;
+        r /= nz;
+        const int ky = r % hy;
+        const int kx = r / hy;
+        const double2 v = spec[(((size_t)c * nz + dz) * Py + ky) * Px + kx];
+        dhat[i] = T(scale * (c >= 4 ? v.y : v.x));
+    }
+}
+
+#ifdef SS_COMMON_LAUNCHERS
+__global__ void interp_identity_kernel(InterpEntry* tab, int img0, int K) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
+        InterpEntry e;
+        e.src0 = e.src1 = img0 + k;
+        e.t = 0.0;
+        e.copy = 1;
+        e.pad = 0;
+        tab[img0 + k] = e;
+    }
+}
+#endif
+
+// ------------------------------------------------------------------------------------------------
+// launchers
+static inline int grid1d(size_t n, int thr) {
+    size_t b = (n + thr - 1) / thr;
+    if (b > 152 * 16) b = 152 * 16;
+    return (int)(b ? b : 1);
+}
+
+template <typename T> void launch_xfwd(const GroupArgs<T>& g, bool do_fft, int nthr, size_t smem, cudaStream_t st) {
+    dim3 grid((g.ny + g.ty_a - 1) / g.ty_a, g.nz, g.n_pairs);
+    if (do_fft) {
+        xfwd_kernel<T, true><<<grid, nthr, smem, st>>>(g);
+    } else {
+        xfwd_kernel<T, false><<<grid, nthr, 0, st>>>(g);
+    }
+}
+
+template <typename T> void launch_yz(const GroupArgs<T>& g, int nthr, size_t smem, cudaStream_t st) {
+    dim3 grid(g.Px, g.n_pairs);
+    yz_kernel<T><<<grid, nthr, smem, st>>>(g);
+}
+
+template <typename T>
+void launch_xinv_step(const GroupArgs<T>& g, bool do_fft, T dt, int nthr, size_t smem, cudaStream_t st) {
+    dim3 grid((g.ny + g.ty_c - 1) / g.ty_c, g.nz, g.n_pairs);
+    if (do_fft) {
+        xinv_kernel<T, true, 0><<<grid, nthr, smem, st>>>(g, dt, nullptr);
+    } else {
+        xinv_kernel<T, false, 0><<<grid, nthr, smem, st>>>(g, dt, nullptr);
+    }
+}
+
+template <typename T>
+void launch_xinv_eval(const GroupArgs<T>& g, bool do_fft, T* hout, int nthr, size_t smem, cudaStream_t st) {
+    dim3 grid((g.ny + g.ty_c - 1) / g.ty_c, g.nz, g.n_pairs);
+    if (do_fft) {
+        xinv_kernel<T, true, 1><<<grid, nthr, smem, st>>>(g, T(0), hout);
+    } else {
+        xinv_kernel<T, false, 1><<<grid, nthr, smem, st>>>(g, T(0), hout);
+    }
+}
+
+template <typename T> void launch_arc(const GroupArgs<T>& g, const ArcArgs& a, int nthr, cudaStream_t st) {
+    dim3 grid(a.n_tiles, a.n_kchunks, a.n_str);
+    arc_kernel<T><<<grid, nthr, 0, st>>>(g, a);
+}
+
+template <typename T>
+void launch_eval_reduce(const GroupArgs<T>& g, const ArcArgs& a, double* terms, double* energies, cudaStream_t st) {
+    eval_reduce_kernel<T><<<a.n_str, 128, 0, st>>>(g, a, terms, energies);
+}
+
+template <typename T, typename Tin>
+void launch_aos_to_soa(const Tin* src, T* dst, int K, int N, int* err, cudaStream_t st) {
+    aos_to_soa_kernel<T, Tin><<<grid1d((size_t)K * N, 256), 256, 0, st>>>(src, dst, K, N, err);
+}
+
+template <typename T, typename Tout>
+void launch_soa_to_aos(const T* src, Tout* dst, int K, int N, Tout scale, cudaStream_t st) {
+    soa_to_aos_kernel<T, Tout><<<grid1d((size_t)K * N, 256), 256, 0, st>>>(src, dst, K, N, scale);
+}
+
+template <typename T>
+void launch_extract_octant(const double2* spec, T* dhat, int Px, int Py, int nz, double scale, cudaStream_t st) {
+    const size_t total = (size_t)(Px / 2 + 1) * (Py / 2 + 1) * nz * 6;
+    extract_octant_kernel<T><<<grid1d(total, 256), 256, 0, st>>>(spec, dhat, Px, Py, nz, scale);
+}
+
+// Raises the dynamic shared-memory limit of every kernel that stages lines in shared memory.
+template <typename T> void set_smem_limits(int bytes) {
+    cudaFuncSetAttribute(xfwd_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(yz_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(xinv_kernel<T, true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(xinv_kernel<T, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(xinv_kernel<T, false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(xinv_kernel<T, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+#ifdef SS_COMMON_LAUNCHERS
+void launch_fft_strided_f64(double2* data, const double2* tw, const FftPlan& plan, int n_lines, long elem_stride,
+                            int inner_count, long inner_stride, long outer_stride, cudaStream_t st) {
+    const int P = plan.P;  // <= 2048 (validated by the host)
+    int nthr = 128;
+    while (nthr < 256 && fft_lines_per_pass(nthr, P) < 1) nthr *= 2;
+    int lpc = std::max(1, std::min(n_lines, fft_lines_per_pass(nthr, P)));
+    const size_t smem = (size_t)(P + lpc * P) * sizeof(double2);
+    cudaFuncSetAttribute(fft_strided_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int grid = (n_lines + lpc - 1) / lpc;
+    fft_strided_f64_kernel<<<grid, nthr, smem, st>>>(data, tw, plan, n_lines, lpc, elem_stride, inner_count,
+                                                      inner_stride, outer_stride);
+}
+
+void launch_interp_identity(InterpEntry* tab, int img0, int K, cudaStream_t st) {
+    interp_identity_kernel<<<(K + 127) / 128, 128, 0, st>>>(tab, img0, K);
+}
+#endif
+
+#define SS_INSTANTIATE(T)                                                                                      \
+    template void set_smem_limits<T>(int);                                                                     \
+    template void launch_xfwd<T>(const GroupArgs<T>&, bool, int, size_t, cudaStream_t);                        \
+    template void launch_yz<T>(const GroupArgs<T>&, int, size_t, cudaStream_t);                                \
+    template void launch_xinv_step<T>(const GroupArgs<T>&, bool, T, int, size_t, cudaStream_t);                \
+    template void launch_xinv_eval<T>(const GroupArgs<T>&, bool, T*, int, size_t, cudaStream_t);               \
+    template void launch_arc<T>(const GroupArgs<T>&, const ArcArgs&, int, cudaStream_t);                       \
+    template void launch_eval_reduce<T>(const GroupArgs<T>&, const ArcArgs&, double*, double*, cudaStream_t);  \
+    template void launch_aos_to_soa<T, float>(const float*, T*, int, int, int*, cudaStream_t);                 \
+    template void launch_aos_to_soa<T, double>(const double*, T*, int, int, int*, cudaStream_t);               \
+    template void launch_soa_to_aos<T, float>(const T*, float*, int, int, float, cudaStream_t);                \
+    template void launch_soa_to_aos<T, double>(const T*, double*, int, int, double, cudaStream_t);             \
+    template void launch_extract_octant<T>(const double2*, T*, int, int, int, double, cudaStream_t);
+
+}  // namespace ss

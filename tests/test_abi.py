@@ -1,0 +1,62 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point include/ss.h declares.
+
+No compute calls: these run without a GPU.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1804_07135_gb300 import binding, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "ss.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ss_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("ss_create", "ss_create_batch", "ss_set_path", "ss_get_path", "ss_step", "ss_energies",
+                     "ss_barrier", "ss_field", "ss_grad", "ss_destroy", "ss_last_error"):
+        assert required in names
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_every_declared_symbol():
+    assert set(declared_functions()) <= set(binding._SIGNATURES)
+    binding.load()
+
+
+def test_create_without_gpu_reports_cuda_error():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(binding.SsError) as e:
+        binding.ss_create(8, 8, 1, 1.0, 0.3, 0.05, 0.01, 4)
+    assert e.value.status == binding.SS_ERR_CUDA
+
+
+def test_argument_validation_on_host():
+    with pytest.raises(binding.SsError) as e:
+        binding.ss_create(0, 8, 1, 1.0, 0.3, 0.05, 0.01, 4)
+    assert e.value.status == binding.SS_ERR_INVALID_ARG
+    with pytest.raises(binding.SsError) as e:
+        binding.ss_create(8, 8, 1, 1.0, 0.3, 0.05, 0.01, 1)
+    assert e.value.status == binding.SS_ERR_INVALID_ARG
+    with pytest.raises(binding.SsError) as e:
+        binding.ss_create(8, 8, 1, float("nan"), 0.3, 0.05, 0.01, 4)
+    assert e.value.status == binding.SS_ERR_INVALID_ARG
+    with pytest.raises(binding.SsError) as e:
+        binding.ss_create(8, 8, 1, 1.0, 0.3, 0.05, 0.01, 4, binding.make_opts(dt=-1.0))
+    assert e.value.status == binding.SS_ERR_INVALID_ARG

@@ -1,0 +1,245 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle, on seeded inputs.
+
+Tolerances:
+  * field (Eqs. 2-7): max |h_gpu - h_oracle| <= 1e-5 * max |h_oracle| on the FP32 path, 1e-12 on FP64;
+  * energies (Eq. 8) evaluated on the same stored state: |dE| <= 1e-6 (units of J) on FP32, 1e-9 on FP64;
+  * trajectories (Sec. III loop): final path and barrier against the oracle run from the GPU's own
+    starting state, with bounds stated in each test.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1804_07135_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FP32, FP64 = 0, 1
+
+
+def _sm(ss, strings, **kw):
+    return ss.StringMethod(strings, **kw)
+
+
+def _unit(a):
+    return a / np.linalg.norm(a, axis=-1, keepdims=True)
+
+
+def _model(t):
+    nx, ny, nz, J, D, K, w, _ = t
+    return oracle.model(nx, ny, nz, J, D, K, w)
+
+
+FIELD_CASES = [
+    (16, 16, 1, 1.0, 0.3, 0.05, 0.01, 3),   # odd image count: one pair has an empty partner
+    (5, 3, 2, 1.0, 0.3, 0.05, 0.02, 2),     # padded lengths 9 and 6 (radix 3)
+    (12, 7, 3, 0.8, -0.25, 0.1, 0.05, 4),   # negative D, ragged rows
+    (1, 6, 2, 1.0, 0.3, 0.05, 0.02, 2),     # nx = 1
+    (33, 10, 1, 1.0, 0.3, 0.05, 0.02, 2),   # padded length 72 = 8*9
+    (20, 21, 5, 1.0, 0.25, 0.1, 0.02, 3),   # rows not a multiple of the CTA row count
+    (9, 9, 4, 1.0, 0.0, 0.0, 0.5, 2),       # dipole only, strong
+]
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+@pytest.mark.parametrize("case", FIELD_CASES)
+def test_field_parity(ss, case, prec):
+    nx, ny, nz, J, D, K, w, n = case
+    path = W.random_spins((n, nx * ny * nz, 3), seed=nx * 100 + ny)
+    with _sm(ss, [case], precision=prec) as sm:
+        sm.set_path(0, path)
+        state = sm.get_path(0)
+        h = sm.field(0)
+    ref = oracle.field(_model(case), _unit(state))
+    tol = (1e-5 if prec == FP32 else 1e-12) * np.abs(ref).max()
+    assert np.abs(h - ref).max() <= tol
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_energy_and_terms_parity(ss, prec):
+    case = (12, 10, 3, 1.0, 0.3, 0.05, 0.02, 4)
+    m = _model(case)
+    path = W.random_spins((4, 360, 3), seed=3)
+    with _sm(ss, [case], precision=prec) as sm:
+        sm.set_path(0, path)
+        state = _unit(sm.get_path(0))
+        e = sm.energies(0)
+        grads = [sm.grad(0, k) for k in range(4)]
+    tol = 1e-6 if prec == FP32 else 1e-9
+    e_ref = oracle.energies(m, state)
+    np.testing.assert_allclose(e, e_ref, rtol=0, atol=tol)
+    h_ref = oracle.field(m, state)
+    for k, (ds, terms) in enumerate(grads):
+        np.testing.assert_allclose(terms, oracle.energy_param_grad(m, state[k]), rtol=0, atol=tol)
+        assert np.abs(ds + h_ref[k]).max() <= (1e-5 if prec == FP32 else 1e-12) * np.abs(h_ref[k]).max()
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_single_step_without_reparam(ss, prec):
+    spec = W.tiny_bloch().strings[0]
+    case = (spec.nx, spec.ny, spec.nz, spec.J, spec.D, spec.K, spec.w, spec.n_images)
+    with _sm(ss, [case], precision=prec, reparam_every=0) as sm:
+        sm.set_path(0, spec.initial_path())
+        start = sm.get_path(0)
+        sm.step(1)
+        got = sm.get_path(0)
+        e_pre = sm.step_energies(0)
+    m = _model(case)
+    h = oracle.field(m, start)
+    ref = np.stack([oracle.step(start[k], h[k], 0.1) for k in range(spec.n_images)])
+    assert np.abs(got - ref).max() <= (2e-6 if prec == FP32 else 1e-13)
+    e_ref = np.array([oracle.energy_from_field(start[k], h[k]) for k in range(spec.n_images)])
+    np.testing.assert_allclose(e_pre, e_ref, rtol=0, atol=1e-4 if prec == FP32 else 1e-10)
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_one_iteration_with_reparam(ss, prec):
+    spec = W.tiny_bloch().strings[0]
+    case = (spec.nx, spec.ny, spec.nz, spec.J, spec.D, spec.K, spec.w, spec.n_images)
+    with _sm(ss, [case], precision=prec) as sm:
+        sm.set_path(0, spec.initial_path())
+        start = sm.get_path(0)
+        sm.step(1)
+        got = sm.get_path(0)
+    ref, _ = oracle.string_run(_model(case), start, 1, 0.1)
+    assert np.abs(got - ref).max() <= (5e-6 if prec == FP32 else 1e-12)
+
+
+def _run_both(ss, case, path, n_iter, prec):
+    with _sm(ss, [case], precision=prec) as sm:
+        sm.set_path(0, path)
+        start = sm.get_path(0)
+        sm.step(n_iter)
+        got = sm.get_path(0)
+        e = sm.energies(0)
+        b = sm.barrier(0)
+    ref, e_ref = oracle.string_run(_model(case), _unit(start), n_iter, 0.1)
+    return got, e, b, ref, e_ref, oracle.barrier(e_ref)
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_trajectory_tiny_bloch_200_iterations(ss, prec):
+    wl = W.tiny_bloch()
+    spec = wl.strings[0]
+    case = (spec.nx, spec.ny, spec.nz, spec.J, spec.D, spec.K, spec.w, spec.n_images)
+    got, e, (dE, k), ref, e_ref, (dE_ref, k_ref) = _run_both(ss, case, spec.initial_path(), wl.n_iter, prec)
+    if prec == FP64:
+        assert np.abs(got - ref).max() < 1e-10
+        assert abs(dE - dE_ref) < 1e-10 and k == k_ref
+    else:
+        assert np.abs(got - ref).max() < 1e-4
+        np.testing.assert_allclose(e, e_ref, rtol=0, atol=1e-5)
+        assert abs(dE - dE_ref) < 1e-5 and k == k_ref
+
+
+def test_trajectory_bloch_collapse_crop(ss):
+    full = W.bloch_collapse().strings[0]
+    crop = W.bloch_collapse_crop_path(full.initial_path())
+    case = (16, 16, 4, full.J, full.D, full.K, full.w, full.n_images)
+    got, e, (dE, k), ref, e_ref, (dE_ref, k_ref) = _run_both(ss, case, crop, 60, FP32)
+    assert np.abs(got - ref).max() < 1e-4
+    np.testing.assert_allclose(e, e_ref, rtol=0, atol=1e-4)
+    assert abs(dE - dE_ref) < 2e-5 and k == k_ref
+
+
+def test_batched_strings_of_uneven_size(ss):
+    cases = [(16, 16, 1, 1.0, 0.3, 0.05, 0.01, 5), (12, 10, 2, 1.0, 0.2, 0.1, 0.02, 4),
+             (16, 16, 1, 1.0, 0.35, 0.0, 0.02, 3), (7, 9, 3, 1.0, 0.25, 0.15, 0.0, 4)]
+    paths = [W.bloch_point_path(c[0], c[1], c[2], c[7], R=3.0, D=c[4]) for c in cases]
+    n_iter = 15
+    with _sm(ss, cases) as sm:
+        for i, p in enumerate(paths):
+            sm.set_path(i, p)
+        starts = [sm.get_path(i) for i in range(len(cases))]
+        sm.step(n_iter)
+        got = [sm.get_path(i) for i in range(len(cases))]
+        es = [sm.energies(i) for i in range(len(cases))]
+    for c, s0, g, e in zip(cases, starts, got, es):
+        ref, e_ref = oracle.string_run(_model(c), _unit(s0), n_iter, 0.1)
+        assert np.abs(g - ref).max() < 1e-5
+        np.testing.assert_allclose(e, e_ref, rtol=0, atol=1e-5)
+
+
+@pytest.mark.parametrize("dims", [(64, 64, 8), (192, 192, 8)])
+def test_full_size_field_on_sampled_sites(ss, dims):
+    nx, ny, nz = dims
+    case = (nx, ny, nz, 1.0, 0.25, 0.1, 0.02, 2)
+    N = nx * ny * nz
+    path = np.stack([W.skyrmion(nx, ny, nz, R=nx / 8, D=0.25), W.random_spins((N, 3), seed=21)])
+    with _sm(ss, [case]) as sm:
+        sm.set_path(0, path.astype(np.float32))
+        state = sm.get_path(0)
+        h = sm.field(0)
+    rng = np.random.default_rng(5)
+    sites = np.concatenate([[0, N - 1, nx - 1, nx * ny - 1], rng.integers(0, N, size=28)])
+    m = _model(case)
+    for k in range(2):
+        ref = oracle.field_at(m, _unit(state[k]), sites)
+        scale = np.abs(ref).max()
+        assert np.abs(h[k][sites] - ref).max() <= 1e-5 * scale
+
+
+def test_deterministic_and_resumable(ss):
+    spec = W.tiny_bloch().strings[0]
+    case = (spec.nx, spec.ny, spec.nz, spec.J, spec.D, spec.K, spec.w, spec.n_images)
+    outs = []
+    for split in (False, True):
+        with _sm(ss, [case]) as sm:
+            sm.set_path(0, spec.initial_path())
+            if split:
+                sm.step(17)
+                sm.step(23)
+            else:
+                sm.step(40)
+            outs.append((sm.get_path(0, np.float32), sm.energies(0), sm.step_energies(0)))
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])
+    np.testing.assert_array_equal(outs[0][2], outs[1][2])
+
+
+def test_device_and_host_buffers_agree(ss):
+    spec = W.tiny_bloch().strings[0]
+    case = (spec.nx, spec.ny, spec.nz, spec.J, spec.D, spec.K, spec.w, spec.n_images)
+    path = spec.initial_path()
+    with _sm(ss, [case]) as sm:
+        sm.set_path(0, torch.from_numpy(path.astype(np.float32)).cuda())
+        sm.step(5)
+        dev = torch.zeros(path.shape, dtype=torch.float32, device="cuda")
+        ss.ss_get_path(sm.ctx, 0, dev)
+        host = sm.get_path(0, np.float32)
+        np.testing.assert_array_equal(dev.cpu().numpy(), host)
+
+
+def test_invalid_inputs_and_state(ss):
+    case = (8, 8, 1, 1.0, 0.3, 0.05, 0.01, 3)
+    with _sm(ss, [case]) as sm:
+        with pytest.raises(ss.SsError) as e:
+            sm.step(1)
+        assert e.value.status == ss.SS_ERR_STATE
+        bad = W.random_spins((3, 64, 3), seed=1)
+        bad[1, 7] = 0.0
+        with pytest.raises(ss.SsError) as e:
+            sm.set_path(0, bad)
+        assert e.value.status == ss.SS_ERR_INVALID_ARG
+        bad[1, 7] = [np.nan, 0, 1]
+        with pytest.raises(ss.SsError) as e:
+            sm.set_path(0, bad)
+        assert e.value.status == ss.SS_ERR_INVALID_ARG
+        with pytest.raises(ss.SsError) as e:
+            ss.ss_energies(sm.ctx, 3)
+        assert e.value.status == ss.SS_ERR_INVALID_ARG
+        sm.set_path(0, W.random_spins((3, 64, 3), seed=2))  # recovers
+        sm.step(2)
+        assert np.isfinite(sm.energies(0)).all()
+
+
+def test_overflow_is_reported_as_nonfinite(ss):
+    # a finite but huge exchange constant overflows the FP32 field: the energy reduction sees inf
+    case = (8, 8, 1, 1e38, 0.0, 0.0, 0.0, 3)
+    with _sm(ss, [case]) as sm:
+        sm.set_path(0, W.random_spins((3, 64, 3), seed=4))
+        sm.step(1)
+        with pytest.raises(ss.SsError) as e:
+            sm.step_energies(0)
+        assert e.value.status == ss.SS_ERR_NONFINITE

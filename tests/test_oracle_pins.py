@@ -333,3 +333,10 @@ def test_barrier_definition():
     # Sec. III: energy of the highest image relative to the first; ties go to the lowest index
     assert oracle.barrier([1.0, 3.0, 2.5, 3.0, 0.0]) == (2.0, 1)
     assert oracle.barrier([5.0, 1.0, 2.0]) == (0.0, 0)
+
+
+def test_field_at_sites_equals_full_field():
+    m = oracle.model(7, 5, 3, 1.0, 0.3, 0.05, 0.02)
+    s = W.random_spins((105, 3), seed=12)
+    sites = [0, 6, 17, 52, 104, 33]
+    np.testing.assert_array_equal(oracle.field_at(m, s, sites), oracle.field(m, s)[sites])
