@@ -125,6 +125,30 @@ ss_status ss_grad(ss_ctx* ctx, int string, int image, void* dE_ds, int dtype, in
  * Synchronises. */
 ss_status ss_time_kernels(ss_ctx* ctx, int reps, double* ms_out, int max_out, int* n_out);
 
+/* Effective field of a batch of images, for callers that cannot allocate device memory.  The paper
+ * has no counterpart: this exists for code that must not call cudaMalloc -- an application that owns
+ * all device memory through its own pool, a plugin whose host forbids allocation, or code running
+ * while an allocation would disturb the caller's memory accounting.  It computes the same field as
+ * ss_field (Eqs. 2-7, FP32 path, dipole by the zero-padded FFT convolution) without a context and
+ * without allocating: every intermediate lives in one device array built into libss, of 32 MiB,
+ * which each GPU that loads the library keeps reserved until the process exits.
+ *   spins  device, [n_images][N][3] float32 (normalised on the fly; need not be unit length)
+ *   field  device, [n_images][N][3] float32, written
+ *   stream cudaStream_t (NULL = legacy default stream); the call synchronises it before returning
+ * Limits: dims in [1,1024] x [1,1024] x [1,64], n_images in [1,1024], and the scratch the call needs
+ * must fit the 32 MiB array -- roughly 96*nz*Px*Py bytes while the dipole spectrum is built (Px, Py
+ * the padded lengths, about 2*nx and 2*ny) and 24*n_images*N + 48*ceil(n_images/2)*nz*ny*Px bytes
+ * for the images; larger requests return SS_ERR_INVALID_ARG without touching the GPU.
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress, with that
+ * device current) and raises kernel shared-memory limits: make that first call before any stream
+ * capture.  All calls share the one array and it keeps the last call's contents (each call rewrites
+ * what it reads and clears its error word), so calls whose GPU work overlaps -- on two streams, or
+ * from two threads -- race and must be serialised by the caller.
+ * Errors: SS_ERR_INVALID_ARG (bad dims/constants/pointers, too large, or a zero-norm/non-finite input
+ * spin), SS_ERR_CUDA (no sm_103 device or a CUDA failure).  ss_last_error does not cover this call. */
+ss_status ss_field_noalloc(int nx, int ny, int nz, double J, double D, double K, double w_dip, int n_images,
+                           const float* spins, float* field, void* stream);
+
 /* Shape queries. */
 int ss_num_strings(const ss_ctx* ctx);
 ss_status ss_string_info(const ss_ctx* ctx, int string, ss_string_desc* out);

@@ -64,6 +64,9 @@ _SIGNATURES = {
                                ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "ss_time_kernels": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_int)]),
+    "ss_field_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p]),
     "ss_num_strings": (ctypes.c_int, [ctypes.c_void_p]),
     "ss_string_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ss_string_desc)]),
     "ss_kernels_per_iteration": (ctypes.c_int, [ctypes.c_void_p]),
@@ -276,6 +279,23 @@ def ss_time_kernels(ctx, reps: int = 10) -> np.ndarray:
     _check(_lib.ss_time_kernels(ctx, int(reps), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 64,
                                 ctypes.byref(n)), ctx)
     return out[: n.value].copy()
+
+
+def ss_field_noalloc(nx, ny, nz, J, D, K, w_dip, n_images, spins, field, stream=None) -> None:
+    """Effective field without any device allocation (see include/ss.h): spins and field are CUDA
+    float32 tensors of n_images * nx * ny * nz * 3 values.  Raises SsError on a non-zero status."""
+    load()
+    n = int(n_images) * int(nx) * int(ny) * int(nz) * 3
+    for name, x in (("spins", spins), ("field", field)):
+        if not _is_torch(x) or not x.is_cuda or _dtype_code(x) != SS_DTYPE_F32 or not x.is_contiguous():
+            raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+        if _numel(x) != n:
+            raise ValueError(f"{name} must hold {n} values")
+    st = _lib.ss_field_noalloc(int(nx), int(ny), int(nz), float(J), float(D), float(K), float(w_dip), int(n_images),
+                               ctypes.c_void_p(spins.data_ptr()), ctypes.c_void_p(field.data_ptr()),
+                               ctypes.c_void_p(stream) if stream else None)
+    if st != SS_OK:
+        raise SsError(st, "ss_field_noalloc failed")
 
 
 # ---- a small owning wrapper ---------------------------------------------------------------------------

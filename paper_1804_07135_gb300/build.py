@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libss.so")
-SOURCES = ("ss_kernels_f32.cu", "ss_kernels_f64.cu", "ss_api.cu")
+SOURCES = ("ss_kernels_f32.cu", "ss_kernels_f64.cu", "ss_api.cu", "ss_noalloc.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,0 +1,263 @@
+// ss_noalloc.cu -- ss_field_noalloc: the effective field of a batch of images without allocating
+// device memory.
+//
+// Who needs it: callers that must not call cudaMalloc -- code running inside an application that
+// owns all device memory through its own pool, plugins whose host forbids allocation, or code that
+// runs while a device-wide allocation would break an ongoing stream capture.  Everything the field
+// evaluation needs beyond the caller's input and output (the pair spectra, the dipole-tensor
+// spectrum and its FP64 build area, twiddles, the SoA copies of spins and field, bookkeeping) lives in
+// one file-scope device array, g_scratch, of kNoAllocScratchBytes.  Every GPU that loads libss
+// reserves that array until the process exits.
+//
+// Host code must not use g_scratch's name as a device address (in host code it names a host-side
+// stand-in); the device address comes from cudaGetSymbolAddress, taken once per device with that
+// device current, on the first call.
+#include <limits.h>
+#include <math.h>
+
+#include <mutex>
+
+#include "ss.h"
+#include "ss_fft.cuh"
+#include "ss_internal.h"
+
+using namespace ss;
+
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;  // 32 MiB
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_scratch[kNoAllocScratchBytes];
+
+struct ScratchSlot {
+    unsigned char* ptr;
+    bool ready;
+};
+std::mutex g_mu;
+ScratchSlot g_slots[kMaxDevices];
+
+// Device address of g_scratch on the current device, looked up once per device.
+ss_status scratch_of_current_device(unsigned char** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SS_ERR_CUDA;
+    if (dev < 0 || dev >= kMaxDevices) return SS_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_slots[dev].ready) {
+        cudaDeviceProp prop;
+        if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return SS_ERR_CUDA;
+        if (prop.major != 10 || prop.minor != 3) return SS_ERR_CUDA;
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+        if (e != cudaSuccess || !p) return SS_ERR_CUDA;
+        set_smem_limits<float>(227 * 1024);
+        g_slots[dev].ptr = static_cast<unsigned char*>(p);
+        g_slots[dev].ready = true;
+    }
+    *out = g_slots[dev].ptr;
+    return SS_OK;
+}
+
+// ---- sizes and launch shapes (same rules as the context path, restated without containers) ----
+bool smooth23(int m) {
+    while (m % 2 == 0) m /= 2;
+    while (m % 3 == 0) m /= 3;
+    return m == 1;
+}
+int pad_len(int n) {
+    int m = n > 1 ? 2 * n - 1 : 1;
+    while (!smooth23(m)) ++m;
+    return m;
+}
+FftPlan plan_of(int P) {
+    FftPlan p{};
+    p.P = P;
+    int a = 0, b = 0, q = P;
+    while (q % 2 == 0) q /= 2, ++a;
+    while (q % 3 == 0) q /= 3, ++b;
+    int n = 0;
+    const int n8 = a / 3, rem = a % 3;
+    if (rem == 1 && n8 == 0) {
+        p.radix[n++] = 2;
+    } else {
+        const int eights = rem == 1 ? n8 - 1 : n8;
+        for (int i = 0; i < eights; ++i) p.radix[n++] = 8;
+        if (rem == 1) {
+            p.radix[n++] = 4;
+            p.radix[n++] = 4;
+        }
+        if (rem == 2) p.radix[n++] = 4;
+    }
+    for (int i = 0; i < b; ++i) p.radix[n++] = 3;
+    p.nstages = n;
+    return p;
+}
+int up32(int v) { return ((v + 31) / 32) * 32; }
+size_t up256(size_t v) { return (v + 255) & ~size_t(255); }
+
+__global__ void na_twiddles(double2* tw64, float2* tw32, int P) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < P; k += gridDim.x * blockDim.x) {
+        double s, c;
+        sincospi(2.0 * (double)k / (double)P, &s, &c);
+        tw64[k] = make_double2(c, -s);
+        tw32[k] = make_float2((float)c, (float)-s);
+    }
+}
+
+// Eq. 7 at every lattice offset (dx, dy, dz >= 0) of the zero-padded, circularly ordered grid:
+// data [6][nz][Py][Px] complex, imaginary parts zero, origin zero.
+__global__ void na_tensor_fill(double2* data, int nx, int ny, int nz, int Px, int Py) {
+    const size_t plane = (size_t)Px * Py, total = plane * nz;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(i % Px), iy = (int)((i / Px) % Py), dz = (int)(i / plane);
+        const int dx = ix <= nx - 1 ? ix : (ix >= Px - (nx - 1) ? ix - Px : INT_MAX);
+        const int dy = iy <= ny - 1 ? iy : (iy >= Py - (ny - 1) ? iy - Py : INT_MAX);
+        double d[6] = {0, 0, 0, 0, 0, 0};
+        if (dx != INT_MAX && dy != INT_MAX && (dx | dy | dz) != 0) {
+            const double x = dx, y = dy, z = dz;
+            const double r2 = x * x + y * y + z * z;
+            const double r = sqrt(r2);
+            const double inv3 = 1.0 / (r2 * r), inv5 = inv3 / r2;
+            const double c = 0.25 / M_PI;
+            d[0] = c * (3.0 * x * x * inv5 - inv3);
+            d[1] = c * (3.0 * y * y * inv5 - inv3);
+            d[2] = c * (3.0 * z * z * inv5 - inv3);
+            d[3] = c * 3.0 * x * y * inv5;
+            d[4] = c * 3.0 * x * z * inv5;
+            d[5] = c * 3.0 * y * z * inv5;
+        }
+        for (int k = 0; k < 6; ++k) data[(size_t)k * total + i] = make_double2(d[k], 0.0);
+    }
+}
+
+__global__ void na_params(ImgParam<float>* prm, int n, float J, float D, float K, float w) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        ImgParam<float> p;
+        p.J = J;
+        p.D = D;
+        p.K = K;
+        p.w = w;
+        prm[k] = p;
+    }
+}
+
+}  // namespace
+
+extern "C" ss_status ss_field_noalloc(int nx, int ny, int nz, double J, double D, double K, double w, int n_images,
+                                      const float* spins, float* field, void* stream) {
+    if (nx < 1 || ny < 1 || nz < 1 || nx > 1024 || ny > 1024 || nz > 64 || n_images < 1 || n_images > kArcMaxK)
+        return SS_ERR_INVALID_ARG;
+    if (!isfinite(J) || !isfinite(D) || !isfinite(K) || !isfinite(w)) return SS_ERR_INVALID_ARG;
+    if (!spins || !field) return SS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool dip = w != 0.0;
+    const int N = nx * ny * nz;
+    const int Px = dip ? pad_len(nx) : 1, Py = dip ? pad_len(ny) : 1;
+    const int lsx = Px | 1, lsy = Py | 1, pairs = (n_images + 1) / 2;
+    // launch shapes, as for a context of FP32 precision
+    int ty = ny < 8 ? ny : 8;
+    while (ty > 1 && (size_t)(Px + 3 * ty * lsx) * sizeof(float2) > 64 * 1024) --ty;
+    int thr = up32(ty * nx);
+    thr = thr < 128 ? 128 : (thr > kMaxThreadsX ? kMaxThreadsX : thr);
+    if (thr < up32(fft_min_threads(Px))) thr = up32(fft_min_threads(Px));
+    while (thr < kMaxThreadsX && fft_lines_per_pass(thr, Px) < 3 * ty) thr += 32;
+    int thr_b = up32(fft_min_threads(Py));
+    if (thr_b < 128) thr_b = 128;
+    while (thr_b < kMaxThreadsYz && fft_lines_per_pass(thr_b, Py) < 3 * nz) thr_b += 32;
+    const size_t smem_a = (size_t)(Px + 3 * ty * lsx) * sizeof(float2);
+    const size_t smem_c = smem_a + 32 * 8 * sizeof(double);
+    const size_t smem_b = (size_t)(Py + 3 * nz * lsy) * sizeof(float2);
+    if (smem_c > 227 * 1024 || smem_b > 227 * 1024) return SS_ERR_INVALID_ARG;
+    const int n_eblk = nz * ((ny + ty - 1) / ty);
+    // scratch layout
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += up256(bytes);
+        return o;
+    };
+    const size_t o_err = take(sizeof(int));
+    const size_t o_tw64x = take(Px * sizeof(double2)), o_tw64y = take(Py * sizeof(double2));
+    const size_t o_twx = take(Px * sizeof(float2)), o_twy = take(Py * sizeof(float2));
+    const size_t o_dhat = take(dip ? (size_t)(Px / 2 + 1) * (Py / 2 + 1) * nz * 6 * sizeof(float) : 0);
+    const size_t o_prm = take(n_images * sizeof(ImgParam<float>));
+    const size_t o_interp = take(n_images * sizeof(InterpEntry));
+    const size_t o_epart = take((size_t)n_images * 4 * n_eblk * sizeof(double));
+    const size_t o_work = off;
+    const size_t tensor_bytes = dip ? (size_t)6 * nz * Px * Py * sizeof(double2) : 0;
+    const size_t o_s = o_work;
+    const size_t o_h = o_s + up256((size_t)n_images * 3 * N * sizeof(float));
+    const size_t o_spec = o_h + up256((size_t)n_images * 3 * N * sizeof(float));
+    const size_t spec_end = o_spec + (dip ? up256((size_t)pairs * Px * 3 * nz * ny * sizeof(float2)) : 0);
+    const size_t need = spec_end > o_work + tensor_bytes ? spec_end : o_work + tensor_bytes;
+    if (need > kNoAllocScratchBytes) return SS_ERR_INVALID_ARG;  // beyond the built-in scratch
+    unsigned char* base = nullptr;
+    {
+        const ss_status s = scratch_of_current_device(&base);
+        if (s != SS_OK) return s;
+    }
+    int* err = reinterpret_cast<int*>(base + o_err);
+    if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return SS_ERR_CUDA;
+    double2* tw64x = reinterpret_cast<double2*>(base + o_tw64x);
+    double2* tw64y = reinterpret_cast<double2*>(base + o_tw64y);
+    float2* twx = reinterpret_cast<float2*>(base + o_twx);
+    float2* twy = reinterpret_cast<float2*>(base + o_twy);
+    na_twiddles<<<(Px + 127) / 128, 128, 0, st>>>(tw64x, twx, Px);
+    na_twiddles<<<(Py + 127) / 128, 128, 0, st>>>(tw64y, twy, Py);
+    float* dhat = reinterpret_cast<float*>(base + o_dhat);
+    const FftPlan px = plan_of(Px), py = plan_of(Py);
+    if (dip) {
+        // the tensor spectrum is rebuilt on every call: the build area is shared with the spins below
+        double2* tens = reinterpret_cast<double2*>(base + o_work);
+        const size_t cells = (size_t)nz * Px * Py;
+        na_tensor_fill<<<(int)((cells + 255) / 256 < 4096 ? (cells + 255) / 256 : 4096), 256, 0, st>>>(tens, nx, ny, nz, Px, Py);
+        launch_fft_strided_f64(tens, tw64x, px, 6 * nz * Py, 1, 1, 0, Px, st);
+        launch_fft_strided_f64(tens, tw64y, py, 6 * nz * Px, Px, Px, 1, (long)Px * Py, st);
+        launch_extract_octant<float>(tens, dhat, Px, Py, nz, 4.0 * M_PI / ((double)Px * Py), st);
+    }
+    ImgParam<float>* prm = reinterpret_cast<ImgParam<float>*>(base + o_prm);
+    InterpEntry* interp = reinterpret_cast<InterpEntry*>(base + o_interp);
+    na_params<<<(n_images + 127) / 128, 128, 0, st>>>(prm, n_images, (float)J, (float)D, (float)K, (float)w);
+    launch_interp_identity(interp, 0, n_images, st);
+    float* s = reinterpret_cast<float*>(base + o_s);
+    float* h = reinterpret_cast<float*>(base + o_h);
+    launch_aos_to_soa<float, float>(spins, s, n_images, N, err, st);
+    GroupArgs<float> g{};
+    g.nx = nx;
+    g.ny = ny;
+    g.nz = nz;
+    g.N = N;
+    g.Px = Px;
+    g.Py = Py;
+    g.n_img = n_images;
+    g.n_pairs = pairs;
+    g.lsx = lsx;
+    g.lsy = lsy;
+    g.s = s;
+    g.sp = s;  // identity reparametrisation: every image copies itself in place
+    g.spec = dip ? reinterpret_cast<float2*>(base + o_spec) : nullptr;
+    g.dhat = dhat;
+    g.twx = twx;
+    g.twy = twy;
+    g.planx = px;
+    g.plany = py;
+    g.prm = prm;
+    g.interp = interp;
+    g.epart = reinterpret_cast<double*>(base + o_epart);
+    g.n_eblk = n_eblk;
+    g.ty_a = ty;
+    g.ty_c = ty;
+    g.err = err;
+    launch_xfwd<float>(g, dip, thr, smem_a, st);
+    if (dip) launch_yz<float>(g, thr_b, smem_b, st);
+    launch_xinv_eval<float>(g, dip, h, thr, smem_c, st);
+    launch_soa_to_aos<float, float>(h, field, n_images, N, 1.0f, st);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return SS_ERR_CUDA;
+    int herr = 0;
+    if (cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return SS_ERR_CUDA;
+    if (herr & kErrInvalidSpin) return SS_ERR_INVALID_ARG;
+    return SS_OK;
+}
