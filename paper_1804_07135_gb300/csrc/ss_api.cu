@@ -35,33 +35,7 @@ int padded_len(int n) {
     return m;
 }
 
-FftPlan make_plan(int P) {
-    FftPlan p{};
-    p.P = P;
-    int a = 0, b = 0, q = P;
-    while (q % 2 == 0) q /= 2, ++a;
-    while (q % 3 == 0) q /= 3, ++b;
-    std::vector<int> r;
-    const int n8 = a / 3, rem = a % 3;
-    if (rem == 0) {
-        r.assign(n8, 8);
-    } else if (rem == 1) {
-        if (n8 >= 1) {
-            r.assign(n8 - 1, 8);
-            r.push_back(4);
-            r.push_back(4);
-        } else {
-            r.push_back(2);
-        }
-    } else {
-        r.assign(n8, 8);
-        r.push_back(4);
-    }
-    for (int i = 0; i < b; ++i) r.push_back(3);
-    p.nstages = (int)r.size();
-    for (int i = 0; i < p.nstages; ++i) p.radix[i] = r[i];
-    return p;
-}
+FftPlan make_plan(int P) { return fft_make_plan(P); }
 
 // Eq. 7 at an integer lattice offset (entries xx, yy, zz, xy, xz, yz), with its 1/(4 pi).
 void dipole_tensor_at(int dx, int dy, int dz, double out[6]) {
@@ -88,7 +62,6 @@ std::vector<double2> twiddles(int P) {
     return w;
 }
 
-int round_up(int v, int m) { return ((v + m - 1) / m) * m; }
 
 }  // namespace
 
@@ -216,31 +189,29 @@ template <typename T> GroupArgs<T> group_args(const ss_ctx* c, const Group& g) {
 // Launch shapes of one size group (shared memory, rows per CTA, block sizes).
 void configure_group(const ss_ctx* c, Group& g) {
     const size_t cs = 2 * real_size(c);  // complex element
-    g.lsx = g.Px | 1;
-    g.lsy = g.Py | 1;
-    const size_t budget = use_fp64(c) ? 96 * 1024 : 64 * 1024;
-    // x kernels: rows per CTA such that 3*rows lines fit the budget
-    int ty = std::min(g.ny, use_fp64(c) ? 4 : 8);
-    while (ty > 1 && (size_t)(g.Px + 3 * ty * g.lsx) * cs > budget) --ty;
+    g.lsx = fft_line_stride(g.Px);
+    g.lsy = fft_line_stride(g.Py);
+    // x kernels: 256 threads; rows per CTA such that the 3*rows lines take one FFT pass and the
+    // shared memory allows several resident CTAs
+    g.thr_a = g.thr_c = kMaxThreadsX;
+    int ty = 1;
+    for (int cand : {8, 4, 2}) {
+        if (cand <= g.ny && 3 * cand <= fft_lines_per_pass(kMaxThreadsX, g.Px) &&
+            (size_t)(g.Px + 3 * cand * g.lsx) * cs <= 48 * 1024) {
+            ty = cand;
+            break;
+        }
+    }
     g.ty_a = g.ty_c = ty;
-    auto x_threads = [&](int rows) {
-        int need = std::max(fft_min_threads(g.Px), 1);
-        int t = std::max(128, std::min(kMaxThreadsX, round_up(rows * g.nx, 32)));
-        t = std::max(t, round_up(need, 32));
-        // enough threads for all lines in one pass when that is within the ceiling
-        while (t < kMaxThreadsX && fft_lines_per_pass(t, g.Px) < 3 * rows) t += 32;
-        return std::min(t, kMaxThreadsX);
-    };
-    g.thr_a = x_threads(g.ty_a);
-    g.thr_c = x_threads(g.ty_c);
     g.smem_a = (size_t)(g.Px + 3 * g.ty_a * g.lsx) * cs;
     g.smem_c = (size_t)(g.Px + 3 * g.ty_c * g.lsx) * cs + 32 * 8 * sizeof(double);
     g.smem_c_eval = g.smem_c;
-    // y/z kernel: all 3*nz lines of one (pair, kx) in shared memory
-    int tb = std::max(128, round_up(fft_min_threads(g.Py), 32));
-    while (tb < kMaxThreadsYz && fft_lines_per_pass(tb, g.Py) < 3 * g.nz) tb += 32;
-    g.thr_b = std::min(tb, kMaxThreadsYz);
+    // y/z kernel: all 3*nz lines of one (pair, kx) in shared memory, plus the kx slab of the tensor
+    // spectrum when it is small enough to stage
+    g.thr_b = kMaxThreadsYz;
     g.smem_b = (size_t)(g.Py + 3 * g.nz * g.lsy) * cs;
+    const size_t slab = (size_t)(g.Py / 2 + 1) * g.nz * 6 * real_size(c);
+    if (slab <= 24 * 1024) g.smem_b += slab;
     g.n_eblk = g.nz * ((g.ny + g.ty_c - 1) / g.ty_c);
 }
 
@@ -323,7 +294,7 @@ template <typename T> ss_status setup_group(ss_ctx* c, Group& g) {
     ArcArgs& a = g.arc;
     a.n_str = nstr;
     a.maxK = maxK;
-    a.tile_elems = 2048;
+    a.tile_elems = 1024;
     a.n_tiles = (int)((M + a.tile_elems - 1) / a.tile_elems);
     a.kchunk = std::max(1, std::min(8, maxK - 1));
     a.n_kchunks = std::max(1, (maxK - 1 + a.kchunk - 1) / a.kchunk);

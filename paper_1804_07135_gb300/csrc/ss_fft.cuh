@@ -1,7 +1,8 @@
 // ss_fft.cuh -- batched complex FFTs of lines held in shared memory (Sec. II-A: the dipole field as a
 // zero-padded convolution evaluated with FFTs).
 //
-// Lines of length P (P = 2^a 3^b) sit in shared memory with stride LS >= P complex elements.  The
+// Lines of length P (P = 2^a 3^b) sit in shared memory with stride LS = fft_line_stride(P); element i
+// of a line is stored at fft_pad(i) (one padding slot per 16 elements against bank conflicts).  The
 // transform is a mixed-radix Stockham autosort FFT (radices 8, 4, 3, 2) done in place: in each stage
 // every thread reads its butterflies' inputs into registers, the block synchronises, and the outputs
 // are written to their autosorted positions.  Twiddles W_P^k = exp(-2 pi i k / P) come from a table in
@@ -80,6 +81,40 @@ template <typename C> struct Dft<8, C> {
     }
 };
 
+// Host-side plan: radices 8, 4, 2 first (largest first), then 3s.
+inline FftPlan fft_make_plan(int P) {
+    FftPlan p{};
+    p.P = P;
+    int a = 0, b = 0, q = P;
+    while (q % 2 == 0) q /= 2, ++a;
+    while (q % 3 == 0) q /= 3, ++b;
+    int n = 0;
+    const int n8 = a / 3, rem = a % 3;
+    if (rem == 1 && n8 == 0) {
+        p.radix[n++] = 2;
+    } else {
+        const int eights = rem == 1 ? n8 - 1 : n8;
+        for (int i = 0; i < eights; ++i) p.radix[n++] = 8;
+        if (rem == 1) {
+            p.radix[n++] = 4;
+            p.radix[n++] = 4;
+        }
+        if (rem == 2) p.radix[n++] = 4;
+    }
+    for (int i = 0; i < b; ++i) p.radix[n++] = 3;
+    p.nstages = n;
+    int ns = 1;
+    for (int s = 0; s < n; ++s) {
+        const int R = p.radix[s];
+        p.q[s] = P / R;
+        p.ns[s] = ns;
+        p.tw[s] = P / (ns * R);
+        p.ns_mask[s] = (ns & (ns - 1)) == 0 ? ns - 1 : -1;
+        ns *= R;
+    }
+    return p;
+}
+
 // Elements each thread holds in registers per stage: 8 (9 for radix 3).  Lines are transformed in
 // passes of fft_lines_per_pass() lines, so any block of at least P/8 threads can transform any number
 // of lines.
@@ -91,60 +126,66 @@ __host__ __device__ inline int fft_lines_per_pass(int nthr, int P) { return (nth
 __host__ __device__ inline int fft_min_threads(int P) { return (P + kFftElemsPerThread - 1) / kFftElemsPerThread; }
 
 template <int R, typename C>
-__device__ __forceinline__ void fft_stage(C* buf, const C* tw, int P, int LS, int L, int Ns, int tid, int nthr) {
+__device__ __forceinline__ void fft_stage(C* buf, const C* tw, int LS, int L, int Q, int Ns, int twstep, int ns_mask,
+                                          int tid, int nthr) {
     constexpr int B = StageCap<R>::B;
-    const int Q = P / R;
-    const int total = L * Q;
-    const int twstep = P / (Ns * R);
+    // butterfly b = tid + i*nthr of the pass: line = b / Q, j = b % Q, advanced without divisions
+    int line = tid / Q;
+    int j = tid - line * Q;
+    const int dl = nthr / Q, dj = nthr - dl * Q;
     C v[B][R];
-    int dst[B];
+    int dline[B], de[B];
 #pragma unroll
     for (int i = 0; i < B; ++i) {
-        const int b = tid + i * nthr;
-        dst[i] = -1;
-        if (b < total) {
-            const int line = b / Q, j = b - line * Q;
-            const int jm = j % Ns;
-            const C* src = buf + line * LS + j;
+        dline[i] = -1;
+        de[i] = 0;
+        if (line < L) {
+            const int jm = ns_mask >= 0 ? (j & ns_mask) : (j % Ns);
+            const C* src = buf + line * LS;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                C x = src[r * Q];
+                C x = src[fft_pad(j + r * Q)];
                 if (r > 0) x = cmul(x, tw[jm * r * twstep]);
                 v[i][r] = x;
             }
             Dft<R, C>::run(v[i]);
-            dst[i] = line * LS + (j - jm) * R + jm;
+            dline[i] = line * LS;
+            de[i] = (j - jm) * R + jm;
+        }
+        j += dj;
+        line += dl;
+        if (j >= Q) {
+            j -= Q;
+            ++line;
         }
     }
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < B; ++i) {
-        if (dst[i] >= 0) {
+        if (dline[i] >= 0) {
 #pragma unroll
-            for (int r = 0; r < R; ++r) buf[dst[i] + r * Ns] = v[i][r];
+            for (int r = 0; r < R; ++r) buf[dline[i] + fft_pad(de[i] + r * Ns)] = v[i][r];
         }
     }
     __syncthreads();
 }
 
-// Forward FFT of L lines (stride LS) in shared memory.  Must be called by every thread of the block,
-// with blockDim.x >= fft_min_threads(P).  Ends synchronised.
+// Forward FFT of L lines (stride LS, elements at fft_pad positions) in shared memory.  Must be called
+// by every thread of the block, with blockDim.x >= fft_min_threads(P).  Ends synchronised.
 template <typename C>
 __device__ __forceinline__ void fft_lines(C* buf, const C* tw, const FftPlan& plan, int LS, int L, int tid, int nthr) {
     const int lpp = max(1, fft_lines_per_pass(nthr, plan.P));  // the host guarantees >= 1; never loop forever
     for (int l0 = 0; l0 < L; l0 += lpp) {
         const int nl = min(lpp, L - l0);
         C* b = buf + l0 * LS;
-        int Ns = 1;
         for (int st = 0; st < plan.nstages; ++st) {
-            const int R = plan.radix[st];
-            switch (R) {
-                case 8: fft_stage<8>(b, tw, plan.P, LS, nl, Ns, tid, nthr); break;
-                case 4: fft_stage<4>(b, tw, plan.P, LS, nl, Ns, tid, nthr); break;
-                case 3: fft_stage<3>(b, tw, plan.P, LS, nl, Ns, tid, nthr); break;
-                default: fft_stage<2>(b, tw, plan.P, LS, nl, Ns, tid, nthr); break;
+            const int Q = plan.q[st], Ns = plan.ns[st], tws = plan.tw[st], msk = plan.ns_mask[st];
+            switch (plan.radix[st]) {
+                case 8: fft_stage<8>(b, tw, LS, nl, Q, Ns, tws, msk, tid, nthr); break;
+                case 4: fft_stage<4>(b, tw, LS, nl, Q, Ns, tws, msk, tid, nthr); break;
+                case 3: fft_stage<3>(b, tw, LS, nl, Q, Ns, tws, msk, tid, nthr); break;
+                default: fft_stage<2>(b, tw, LS, nl, Q, Ns, tws, msk, tid, nthr); break;
             }
-            Ns *= R;
         }
     }
 }

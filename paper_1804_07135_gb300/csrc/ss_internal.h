@@ -19,17 +19,33 @@ template <> struct cplx_of<double> { using type = double2; };
 template <typename T> using cplx = typename cplx_of<T>::type;
 
 constexpr int kMaxStages = 16;
-constexpr int kMaxThreadsX = 512;   // block-size ceiling of the x-transform kernels
-constexpr int kMaxThreadsYz = 768;  // block-size ceiling of the y/z kernel
+constexpr int kMaxThreadsX = 256;   // block size of the x-transform kernels
+constexpr int kMinBlocksX = 4;      // resident blocks per SM they are compiled for (64 registers)
+constexpr int kMaxThreadsYz = 256;  // block size of the y/z kernel
+constexpr int kMinBlocksYz = 4;
 constexpr int kArcMaxChunk = 8;     // image differences one arc CTA accumulates
 constexpr int kArcMaxK = 1024;      // images per string
 
-// Mixed-radix (2, 3, 4, 8) plan of a length-P complex FFT, stages in Stockham order.
+// Mixed-radix (2, 3, 4, 8) plan of a length-P complex FFT, stages in Stockham order (powers of two
+// first, so the stride Ns of every power-of-two stage and of the first radix-3 stage is a power of two).
+// Per stage: q = P/R butterflies per line, ns = product of the earlier radices, tw = P/(ns*R) (twiddle
+// index step); ns_mask = ns - 1 when ns is a power of two, else -1.
 struct FftPlan {
     int P;
     int nstages;
     int radix[kMaxStages];
+    int q[kMaxStages];
+    int ns[kMaxStages];
+    int tw[kMaxStages];
+    int ns_mask[kMaxStages];
 };
+
+// Shared-memory position of element i of a line: one padding slot per 16 elements, which spreads the
+// strided stores of the early FFT stages over all banks.
+__host__ __device__ inline int fft_pad(int i) { return i + (i >> 4); }
+// Line stride (in elements) for lines of length P: padded length, made odd so that a column read
+// across consecutive lines touches distinct banks.
+__host__ __device__ inline int fft_line_stride(int P) { return (P + (P >> 4) + 1) | 1; }
 
 // Reparametrisation source of one image: normalise((1 - t) sp[src0] + t sp[src1]), or an exact copy
 // of sp[src0] when copy != 0.  Image indices are local to the size group.

@@ -54,7 +54,7 @@ __device__ __forceinline__ void block_reduce_d(double (&v)[NV], double* scratch 
 // packed as re/im of 3*rows complex lines, zero-padded to Px and transformed along x.
 // Output spec[p][kx][c][z][y].
 template <typename T, bool DO_FFT>
-__global__ void __launch_bounds__(kMaxThreadsX) xfwd_kernel(GroupArgs<T> g) {
+__global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xfwd_kernel(GroupArgs<T> g) {
     using C = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tw = reinterpret_cast<C*>(smem_raw);
@@ -100,14 +100,14 @@ __global__ void __launch_bounds__(kMaxThreadsX) xfwd_kernel(GroupArgs<T> g) {
         }
         if (DO_FFT) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) buf[(c * rows + yy) * g.lsx + x] = C{out[0][c], out[1][c]};
+            for (int c = 0; c < 3; ++c) buf[(c * rows + yy) * g.lsx + fft_pad(x)] = C{out[0][c], out[1][c]};
         }
     }
     if (!DO_FFT) return;
     const int padw = g.Px - nx;
     for (int it = tid; it < 3 * rows * padw; it += nthr) {
         const int line = it / padw, x = nx + (it - line * padw);
-        buf[line * g.lsx + x] = C{T(0), T(0)};
+        buf[line * g.lsx + fft_pad(x)] = C{T(0), T(0)};
     }
     __syncthreads();
     fft_lines(buf, tw, g.planx, g.lsx, 3 * rows, tid, nthr);
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(kMaxThreadsX) xfwd_kernel(GroupArgs<T> g) {
     for (int it = tid; it < g.Px * 3 * rows; it += nthr) {
         const int yy = it % rows, rest = it / rows;
         const int c = rest % 3, kx = rest / 3;
-        outp[((size_t)(kx * 3 + c) * g.nz + z) * g.ny + y0 + yy] = buf[(c * rows + yy) * g.lsx + kx];
+        outp[((size_t)(kx * 3 + c) * g.nz + z) * g.ny + y0 + yy] = buf[(c * rows + yy) * g.lsx + fft_pad(kx)];
     }
 }
 
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(kMaxThreadsX) xfwd_kernel(GroupArgs<T> g) {
 constexpr int kYzItems = 4;
 
 template <typename T>
-__global__ void __launch_bounds__(kMaxThreadsYz) yz_kernel(GroupArgs<T> g) {
+__global__ void __launch_bounds__(kMaxThreadsYz, kMinBlocksYz) yz_kernel(GroupArgs<T> g, int stage_dhat) {
     using C = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tw = reinterpret_cast<C*>(smem_raw);
@@ -140,17 +140,24 @@ __global__ void __launch_bounds__(kMaxThreadsYz) yz_kernel(GroupArgs<T> g) {
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int kx = blockIdx.x, p = blockIdx.y;
     const int ny = g.ny, nz = g.nz, Py = g.Py, L = 3 * nz;
+    const int hx = g.Px / 2, hy = Py / 2;
+    const int kxo = min(kx, g.Px - kx);
     C* blk = g.spec + ((size_t)p * g.Px + kx) * 3 * nz * ny;
+    // this kx's slab of the tensor-spectrum octant: [kyo][|dz|][6], staged when it fits
+    const T* dslab = g.dhat + (size_t)kxo * (hy + 1) * nz * 6;
+    T* dsm = reinterpret_cast<T*>(A + L * g.lsy);
+    if (stage_dhat) {
+        for (int i = tid; i < (hy + 1) * nz * 6; i += nthr) dsm[i] = dslab[i];
+        dslab = dsm;
+    }
     for (int i = tid; i < Py; i += nthr) tw[i] = g.twy[i];
     for (int it = tid; it < L * Py; it += nthr) {
         const int line = it / Py, y = it - line * Py;
-        A[line * g.lsy + y] = (y < ny) ? blk[line * ny + y] : C{T(0), T(0)};
+        A[line * g.lsy + fft_pad(y)] = (y < ny) ? blk[line * ny + y] : C{T(0), T(0)};
     }
     __syncthreads();
     fft_lines(A, tw, g.plany, g.lsy, L, tid, nthr);
     // z-convolution with the tensor spectrum, in passes of whole ky columns (item = ky * nz + z)
-    const int hx = g.Px / 2, hy = Py / 2;
-    const int kxo = min(kx, g.Px - kx);
     const T sxg = kx > hx ? T(-1) : T(1);
     const int n_items = Py * nz;
     const int per_pass = max(nz, ((nthr * kYzItems) / nz) * nz);
@@ -164,20 +171,22 @@ __global__ void __launch_bounds__(kMaxThreadsYz) yz_kernel(GroupArgs<T> g) {
                 const int ky = it / nz, z = it - ky * nz;
                 const int kyo = min(ky, Py - ky);
                 const T syg = ky > hy ? T(-1) : T(1);
-                const T* dcol = g.dhat + ((size_t)kxo * (hy + 1) + kyo) * nz * 6;
+                const T sxy = sxg * syg;
+                const T* dcol = dslab + (size_t)kyo * nz * 6;
+                const int pky = fft_pad(ky);
                 C hx_ = {T(0), T(0)}, hy_ = {T(0), T(0)}, hz_ = {T(0), T(0)};
-#pragma unroll 1
+#pragma unroll 2
                 for (int zp = 0; zp < nz; ++zp) {
                     const int dz = z - zp;
                     const T szg = dz < 0 ? T(-1) : T(1);
                     const T* d = dcol + (dz < 0 ? -dz : dz) * 6;
                     const T dxx = d[0], dyy = d[1], dzz = d[2];
-                    const T dxy = d[3] * sxg * syg;
-                    const T dxz = d[4] * sxg * szg;  // coefficient of i
-                    const T dyz = d[5] * syg * szg;  // coefficient of i
-                    const C sx = A[(0 * nz + zp) * g.lsy + ky];
-                    const C sy = A[(1 * nz + zp) * g.lsy + ky];
-                    const C sz = A[(2 * nz + zp) * g.lsy + ky];
+                    const T dxy = d[3] * sxy;
+                    const T dxz = d[4] * (sxg * szg);  // coefficient of i
+                    const T dyz = d[5] * (syg * szg);  // coefficient of i
+                    const C sx = A[(0 * nz + zp) * g.lsy + pky];
+                    const C sy = A[(1 * nz + zp) * g.lsy + pky];
+                    const C sz = A[(2 * nz + zp) * g.lsy + pky];
                     // i*c*S = (-c S.y, c S.x)
                     hx_.x += dxx * sx.x + dxy * sy.x - dxz * sz.y;
                     hx_.y += dxx * sx.y + dxy * sy.y + dxz * sz.x;
@@ -197,9 +206,10 @@ __global__ void __launch_bounds__(kMaxThreadsYz) yz_kernel(GroupArgs<T> g) {
             const int it = base + tid + q * nthr;
             if (it < end) {
                 const int ky = it / nz, z = it - ky * nz;
+                const int pky = fft_pad(ky);
                 // conjugated: the inverse transform is the conjugate of the forward transform of the conjugate
 #pragma unroll
-                for (int c = 0; c < 3; ++c) A[(c * nz + z) * g.lsy + ky] = cconj(res[q][c]);
+                for (int c = 0; c < 3; ++c) A[(c * nz + z) * g.lsy + pky] = cconj(res[q][c]);
             }
         }
         __syncthreads();
@@ -207,7 +217,7 @@ __global__ void __launch_bounds__(kMaxThreadsYz) yz_kernel(GroupArgs<T> g) {
     fft_lines(A, tw, g.plany, g.lsy, L, tid, nthr);
     for (int it = tid; it < L * ny; it += nthr) {
         const int line = it / ny, y = it - line * ny;
-        blk[line * ny + y] = cconj(A[line * g.lsy + y]);
+        blk[line * ny + y] = cconj(A[line * g.lsy + fft_pad(y)]);
     }
 }
 
@@ -223,7 +233,7 @@ __global__ void __launch_bounds__(kMaxThreadsYz) yz_kernel(GroupArgs<T> g) {
 //                (Eq. 1): tJ = -sum s_i.s_j, tD = sum (r_ij x z).(s_i x s_j), tK = -sum s_z^2,
 //                tw = -(1/2) sum conv.s; optionally the field h.
 template <typename T, bool DO_FFT, int MODE>
-__global__ void __launch_bounds__(kMaxThreadsX) xinv_kernel(GroupArgs<T> g, T dt, T* hout) {
+__global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xinv_kernel(GroupArgs<T> g, T dt, T* hout) {
     using C = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tw = reinterpret_cast<C*>(smem_raw);
@@ -240,7 +250,7 @@ __global__ void __launch_bounds__(kMaxThreadsX) xinv_kernel(GroupArgs<T> g, T dt
         for (int it = tid; it < g.Px * 3 * rows; it += nthr) {
             const int yy = it % rows, rest = it / rows;
             const int c = rest % 3, kx = rest / 3;
-            buf[(c * rows + yy) * g.lsx + kx] = cconj(inp[((size_t)(kx * 3 + c) * nz + z) * ny + y0 + yy]);
+            buf[(c * rows + yy) * g.lsx + fft_pad(kx)] = cconj(inp[((size_t)(kx * 3 + c) * nz + z) * ny + y0 + yy]);
         }
         __syncthreads();
         fft_lines(buf, tw, g.planx, g.lsx, 3 * rows, tid, nthr);
@@ -249,6 +259,7 @@ __global__ void __launch_bounds__(kMaxThreadsX) xinv_kernel(GroupArgs<T> g, T dt
     double acc[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+    T eacc[2] = {T(0), T(0)};  // step mode: the thread's few per-site terms, summed in T before FP64
     for (int it = tid; it < 2 * rows * nx; it += nthr) {
         const int h = it / (rows * nx);
         const int rem = it - h * rows * nx;
@@ -275,7 +286,7 @@ __global__ void __launch_bounds__(kMaxThreadsX) xinv_kernel(GroupArgs<T> g, T dt
         if (DO_FFT) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const C v = buf[(c * rows + yy) * g.lsx + x];
+                const C v = buf[(c * rows + yy) * g.lsx + fft_pad(x)];
                 conv[c] = h == 0 ? v.x : -v.y;  // conjugate of the forward transform of the conjugate
             }
         }
@@ -287,7 +298,7 @@ __global__ void __launch_bounds__(kMaxThreadsX) xinv_kernel(GroupArgs<T> g, T dt
         hf[2] += -pr.D * (-xp[0] + xm[0] - yp[1] + ym[1]) + T(2) * pr.K * s0[2];
         if (MODE == 0) {
             const T sh = s0[0] * hf[0] + s0[1] * hf[1] + s0[2] * hf[2];
-            acc[h] += double(T(-0.5) * sh);
+            eacc[h] += T(-0.5) * sh;
             T u[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) u[c] = s0[c] + dt * (hf[c] - sh * s0[c]);
@@ -336,6 +347,10 @@ __global__ void __launch_bounds__(kMaxThreadsX) xinv_kernel(GroupArgs<T> g, T dt
             }
         }
     }
+    if (MODE == 0) {
+        acc[0] = double(eacc[0]);
+        acc[1] = double(eacc[1]);
+    }
     block_reduce_d<NV>(acc, red);
     if (tid == 0) {
         const int blk = blockIdx.y * gridDim.x + blockIdx.x;
@@ -371,8 +386,9 @@ __global__ void __launch_bounds__(256) arc_kernel(GroupArgs<T> g, ArcArgs a) {
     const size_t e0 = (size_t)blockIdx.x * a.tile_elems;
     const size_t e1 = min(M, e0 + a.tile_elems);
     double acc[kArcMaxChunk];
+    T part[kArcMaxChunk];  // the thread's few squared differences per image pair, summed in T first
 #pragma unroll
-    for (int i = 0; i < kArcMaxChunk; ++i) acc[i] = 0.0;
+    for (int i = 0; i < kArcMaxChunk; ++i) part[i] = T(0);
     if (nd > 0) {
         for (size_t e = e0 + tid; e < e1; e += nthr) {
             const T* col = g.sp + (size_t)(img0 + k_lo) * M + e;
@@ -382,12 +398,14 @@ __global__ void __launch_bounds__(256) arc_kernel(GroupArgs<T> g, ArcArgs a) {
                 if (i < nd) {
                     const T cur = col[(size_t)(i + 1) * M];
                     const T d = cur - prev;
-                    acc[i] += double(d * d);
+                    part[i] += d * d;
                     prev = cur;
                 }
             }
         }
     }
+#pragma unroll
+    for (int i = 0; i < kArcMaxChunk; ++i) acc[i] = double(part[i]);
     block_reduce_d<kArcMaxChunk>(acc, red);
     if (tid == 0) {
         for (int i = 0; i < nd; ++i) a.dpart[((size_t)str * a.maxK + k_lo + i + 1) * a.n_tiles + blockIdx.x] = acc[i];
@@ -400,31 +418,43 @@ __global__ void __launch_bounds__(256) arc_kernel(GroupArgs<T> g, ArcArgs a) {
     if (!is_last) return;
     __threadfence();
     // ---- finalisation by the last CTA of this string ----
-    for (int k = tid; k < K; k += nthr) {
-        double e = 0.0;
+    // one warp per image: lanes stride over the partials, then a fixed shuffle tree (deterministic)
+    const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
+    for (int k = warp; k < K; k += nwarp) {
+        double e = 0.0, d2 = 0.0;
         const double* ep = g.epart + (size_t)(img0 + k) * g.n_eblk;
-        for (int b = 0; b < g.n_eblk; ++b) e += ep[b];
-        a.e_last[(size_t)str * a.maxK + k] = e;
-        double d2 = 0.0;
+        for (int b = lane; b < g.n_eblk; b += 32) e += ep[b];
         if (k > 0) {
             const double* dp = a.dpart + ((size_t)str * a.maxK + k) * a.n_tiles;
-            for (int t = 0; t < a.n_tiles; ++t) d2 += __ldcg(dp + t);  // written by other CTAs
+            for (int t = lane; t < a.n_tiles; t += 32) d2 += __ldcg(dp + t);  // written by other CTAs
         }
-        alpha[k] = sqrt(d2);
-        if (!isfinite(e) || !isfinite(d2)) atomicOr(g.err, kErrNonFinite);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            e += __shfl_down_sync(0xffffffffu, e, o);
+            d2 += __shfl_down_sync(0xffffffffu, d2, o);
+        }
+        if (lane == 0) {
+            a.e_last[(size_t)str * a.maxK + k] = e;
+            alpha[k] = sqrt(d2);
+            if (!isfinite(e) || !isfinite(d2)) atomicOr(g.err, kErrNonFinite);
+        }
     }
     __syncthreads();
     if (tid == 0) {
         double s = 0.0;
         for (int k = 0; k < K; ++k) {
             s += alpha[k];
-            alpha[k] = s;  // s_k, with s_0 = 0
+            alpha[k] = s;  // s_k, with s_0 = 0 (Eq. 11)
         }
         a.counters[str] = 0u;
     }
     __syncthreads();
     const double sK = alpha[K - 1];
     const bool move = a.reparam && sK > 0.0 && isfinite(sK);
+    __syncthreads();
+    if (move)
+        for (int k = tid; k < K; k += nthr) alpha[k] = alpha[k] / sK;  // alpha*_k (Eq. 12)
+    __syncthreads();
     for (int k = tid; k < K; k += nthr) {
         InterpEntry e;
         e.src0 = img0 + k;
@@ -434,13 +464,19 @@ __global__ void __launch_bounds__(256) arc_kernel(GroupArgs<T> g, ArcArgs a) {
         e.pad = 0;
         if (move && k > 0 && k < K - 1) {
             const double ak = (double)k / (double)(K - 1);
-            int j = 0;
-            for (int i = 0; i <= K - 2; ++i)
-                if (alpha[i] / sK <= ak) j = i;
-            const double aj = alpha[j] / sK, aj1 = alpha[j + 1] / sK;
+            // largest j in [0, K-2] with alpha*_j <= ak (alpha* is non-decreasing; alpha*_0 = 0 <= ak)
+            int lo = 0, hi = K - 2;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (alpha[mid] <= ak)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+            const int j = lo;
             e.src0 = img0 + j;
             e.src1 = img0 + j + 1;
-            e.t = (ak - aj) / (aj1 - aj);
+            e.t = (ak - alpha[j]) / (alpha[j + 1] - alpha[j]);
             e.copy = 0;
         }
         const_cast<InterpEntry*>(g.interp)[img0 + k] = e;
@@ -515,19 +551,20 @@ __global__ void __launch_bounds__(256) fft_strided_f64_kernel(double2* data, con
     const int l0 = blockIdx.x * lines_per_cta;
     const int L = min(lines_per_cta, n_lines - l0);
     for (int i = tid; i < P; i += nthr) tw[i] = twg[i];
+    const int LS = fft_line_stride(P);
     for (int it = tid; it < L * P; it += nthr) {
         const int i = it / P, e = it - i * P;
         const int l = l0 + i;
         const long base = (long)(l % inner_count) * inner_stride + (long)(l / inner_count) * outer_stride;
-        buf[i * P + e] = data[base + e * elem_stride];
+        buf[i * LS + fft_pad(e)] = data[base + e * elem_stride];
     }
     __syncthreads();
-    fft_lines(buf, tw, plan, P, L, tid, nthr);
+    fft_lines(buf, tw, plan, LS, L, tid, nthr);
     for (int it = tid; it < L * P; it += nthr) {
         const int i = it / P, e = it - i * P;
         const int l = l0 + i;
         const long base = (long)(l % inner_count) * inner_stride + (long)(l / inner_count) * outer_stride;
-        data[base + e * elem_stride] = buf[i * P + e];
+        data[base + e * elem_stride] = buf[i * LS + fft_pad(e)];
     }
 }
 
@@ -582,7 +619,9 @@ template <typename T> void launch_xfwd(const GroupArgs<T>& g, bool do_fft, int n
 
 template <typename T> void launch_yz(const GroupArgs<T>& g, int nthr, size_t smem, cudaStream_t st) {
     dim3 grid(g.Px, g.n_pairs);
-    yz_kernel<T><<<grid, nthr, smem, st>>>(g);
+    const size_t base = (size_t)(g.Py + 3 * g.nz * g.lsy) * sizeof(cplx<T>);
+    const int stage = smem >= base + (size_t)(g.Py / 2 + 1) * g.nz * 6 * sizeof(T);
+    yz_kernel<T><<<grid, nthr, smem, st>>>(g, stage);
 }
 
 template <typename T>
@@ -648,7 +687,7 @@ void launch_fft_strided_f64(double2* data, const double2* tw, const FftPlan& pla
     int nthr = 128;
     while (nthr < 256 && fft_lines_per_pass(nthr, P) < 1) nthr *= 2;
     int lpc = std::max(1, std::min(n_lines, fft_lines_per_pass(nthr, P)));
-    const size_t smem = (size_t)(P + lpc * P) * sizeof(double2);
+    const size_t smem = (size_t)(P + lpc * fft_line_stride(P)) * sizeof(double2);
     cudaFuncSetAttribute(fft_strided_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int grid = (n_lines + lpc - 1) / lpc;
     fft_strided_f64_kernel<<<grid, nthr, smem, st>>>(data, tw, plan, n_lines, lpc, elem_stride, inner_count,

@@ -69,29 +69,7 @@ int pad_len(int n) {
     while (!smooth23(m)) ++m;
     return m;
 }
-FftPlan plan_of(int P) {
-    FftPlan p{};
-    p.P = P;
-    int a = 0, b = 0, q = P;
-    while (q % 2 == 0) q /= 2, ++a;
-    while (q % 3 == 0) q /= 3, ++b;
-    int n = 0;
-    const int n8 = a / 3, rem = a % 3;
-    if (rem == 1 && n8 == 0) {
-        p.radix[n++] = 2;
-    } else {
-        const int eights = rem == 1 ? n8 - 1 : n8;
-        for (int i = 0; i < eights; ++i) p.radix[n++] = 8;
-        if (rem == 1) {
-            p.radix[n++] = 4;
-            p.radix[n++] = 4;
-        }
-        if (rem == 2) p.radix[n++] = 4;
-    }
-    for (int i = 0; i < b; ++i) p.radix[n++] = 3;
-    p.nstages = n;
-    return p;
-}
+FftPlan plan_of(int P) { return fft_make_plan(P); }
 int up32(int v) { return ((v + 31) / 32) * 32; }
 size_t up256(size_t v) { return (v + 255) & ~size_t(255); }
 
@@ -153,20 +131,21 @@ extern "C" ss_status ss_field_noalloc(int nx, int ny, int nz, double J, double D
     const bool dip = w != 0.0;
     const int N = nx * ny * nz;
     const int Px = dip ? pad_len(nx) : 1, Py = dip ? pad_len(ny) : 1;
-    const int lsx = Px | 1, lsy = Py | 1, pairs = (n_images + 1) / 2;
+    const int lsx = fft_line_stride(Px), lsy = fft_line_stride(Py), pairs = (n_images + 1) / 2;
     // launch shapes, as for a context of FP32 precision
-    int ty = ny < 8 ? ny : 8;
-    while (ty > 1 && (size_t)(Px + 3 * ty * lsx) * sizeof(float2) > 64 * 1024) --ty;
-    int thr = up32(ty * nx);
-    thr = thr < 128 ? 128 : (thr > kMaxThreadsX ? kMaxThreadsX : thr);
-    if (thr < up32(fft_min_threads(Px))) thr = up32(fft_min_threads(Px));
-    while (thr < kMaxThreadsX && fft_lines_per_pass(thr, Px) < 3 * ty) thr += 32;
-    int thr_b = up32(fft_min_threads(Py));
-    if (thr_b < 128) thr_b = 128;
-    while (thr_b < kMaxThreadsYz && fft_lines_per_pass(thr_b, Py) < 3 * nz) thr_b += 32;
+    const int thr = kMaxThreadsX, thr_b = kMaxThreadsYz;
+    int ty = 1;
+    for (int cand = 8; cand >= 2; cand /= 2) {
+        if (cand <= ny && 3 * cand <= fft_lines_per_pass(thr, Px) && (size_t)(Px + 3 * cand * lsx) * sizeof(float2) <= 48 * 1024) {
+            ty = cand;
+            break;
+        }
+    }
     const size_t smem_a = (size_t)(Px + 3 * ty * lsx) * sizeof(float2);
     const size_t smem_c = smem_a + 32 * 8 * sizeof(double);
-    const size_t smem_b = (size_t)(Py + 3 * nz * lsy) * sizeof(float2);
+    size_t smem_b = (size_t)(Py + 3 * nz * lsy) * sizeof(float2);
+    const size_t slab = (size_t)(Py / 2 + 1) * nz * 6 * sizeof(float);
+    if (slab <= 24 * 1024) smem_b += slab;
     if (smem_c > 227 * 1024 || smem_b > 227 * 1024) return SS_ERR_INVALID_ARG;
     const int n_eblk = nz * ((ny + ty - 1) / ty);
     // scratch layout
