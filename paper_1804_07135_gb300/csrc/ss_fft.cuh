@@ -190,4 +190,88 @@ __device__ __forceinline__ void fft_lines(C* buf, const C* tw, const FftPlan& pl
     }
 }
 
+// ---- compile-time plans for the padded lengths the workloads use --------------------------------
+// Same radix order and stage constants as fft_make_plan, but known to the compiler, so every index
+// of a butterfly is a shift, mask or constant multiply.
+__host__ __device__ constexpr int cx_pow(int P, int f) { return P % f == 0 ? 1 + cx_pow(P / f, f) : 0; }
+__host__ __device__ constexpr int cx_nstages(int P) {
+    return (cx_pow(P, 2) % 3 == 1 && cx_pow(P, 2) / 3 == 0 ? 1
+            : cx_pow(P, 2) % 3 == 1                        ? cx_pow(P, 2) / 3 + 1
+            : cx_pow(P, 2) % 3 == 2                        ? cx_pow(P, 2) / 3 + 1
+                                                           : cx_pow(P, 2) / 3) +
+           cx_pow(P, 3);
+}
+// radix of stage s
+__host__ __device__ constexpr int cx_radix(int P, int s) {
+    return (cx_pow(P, 2) % 3 == 1 && cx_pow(P, 2) / 3 == 0)
+               ? (s == 0 ? 2 : 3)
+               : (cx_pow(P, 2) % 3 == 1
+                      ? (s < cx_pow(P, 2) / 3 - 1 ? 8 : s < cx_pow(P, 2) / 3 + 1 ? 4 : 3)
+                      : (cx_pow(P, 2) % 3 == 2 ? (s < cx_pow(P, 2) / 3 ? 8 : s == cx_pow(P, 2) / 3 ? 4 : 3)
+                                               : (s < cx_pow(P, 2) / 3 ? 8 : 3)));
+}
+__host__ __device__ constexpr int cx_ns(int P, int s) { return s == 0 ? 1 : cx_ns(P, s - 1) * cx_radix(P, s - 1); }
+
+template <int P, int S, int R = cx_radix(P, S), int NS = cx_ns(P, S), typename C>
+__device__ __forceinline__ void fft_stage_c(C* buf, const C* tw, int LS, int L, int tid, int nthr) {
+    constexpr int B = StageCap<R>::B;
+    constexpr int Q = P / R;
+    constexpr int TWS = P / (NS * R);
+    C v[B][R];
+    int dline[B], de[B];
+#pragma unroll
+    for (int i = 0; i < B; ++i) {
+        const int b = tid + i * nthr;
+        const int line = b / Q, j = b % Q;
+        dline[i] = -1;
+        de[i] = 0;
+        if (line < L) {
+            const int jm = j % NS;
+            const C* src = buf + line * LS;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                C x = src[fft_pad(j + r * Q)];
+                if (r > 0) x = cmul(x, tw[jm * r * TWS]);
+                v[i][r] = x;
+            }
+            Dft<R, C>::run(v[i]);
+            dline[i] = line * LS;
+            de[i] = (j - jm) * R + jm;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < B; ++i) {
+        if (dline[i] >= 0) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) buf[dline[i] + fft_pad(de[i] + r * NS)] = v[i][r];
+        }
+    }
+    __syncthreads();
+}
+
+template <int P, int S, typename C>
+__device__ __forceinline__ void fft_stages_c(C* buf, const C* tw, int LS, int L, int tid, int nthr) {
+    if constexpr (S < cx_nstages(P)) {
+        fft_stage_c<P, S>(buf, tw, LS, L, tid, nthr);
+        fft_stages_c<P, S + 1>(buf, tw, LS, L, tid, nthr);
+    }
+}
+
+// Forward FFT of L lines of compile-time length P; same contract as fft_lines.
+template <int P, typename C>
+__device__ __forceinline__ void fft_lines_c(C* buf, const C* tw, int LS, int L, int tid, int nthr) {
+    const int lpp = max(1, fft_lines_per_pass(nthr, P));
+    for (int l0 = 0; l0 < L; l0 += lpp) fft_stages_c<P, 0>(buf + l0 * LS, tw, LS, min(lpp, L - l0), tid, nthr);
+}
+
+// Dispatch: compile-time plan when PC > 0, the runtime plan otherwise.
+template <int PC, typename C>
+__device__ __forceinline__ void fft_lines_any(C* buf, const C* tw, const FftPlan& plan, int LS, int L, int tid, int nthr) {
+    if constexpr (PC > 0)
+        fft_lines_c<PC>(buf, tw, LS, L, tid, nthr);
+    else
+        fft_lines(buf, tw, plan, LS, L, tid, nthr);
+}
+
 }  // namespace ss

@@ -21,8 +21,8 @@ template <typename T> using cplx = typename cplx_of<T>::type;
 constexpr int kMaxStages = 16;
 constexpr int kMaxThreadsX = 256;   // block size of the x-transform kernels
 constexpr int kMinBlocksX = 4;      // resident blocks per SM they are compiled for (64 registers)
-constexpr int kMaxThreadsYz = 256;  // block size of the y/z kernel
-constexpr int kMinBlocksYz = 4;
+constexpr int kMaxThreadsYz = 384;  // block size of the y/z kernel (3 x 128: one z-convolution row per warp)
+constexpr int kMinBlocksYz = 2;
 constexpr int kArcMaxChunk = 8;     // image differences one arc CTA accumulates
 constexpr int kArcMaxK = 1024;      // images per string
 

@@ -14,6 +14,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "ss_fft.cuh"
 
@@ -48,12 +49,36 @@ __device__ __forceinline__ void block_reduce_d(double (&v)[NV], double* scratch 
     }
 }
 
+// Block reduction of NV values per thread: summed in T within each warp (fixed shuffle tree), then
+// in FP64 across warps by thread 0 (fixed order).  out valid in thread 0.
+template <int NV, typename T>
+__device__ __forceinline__ void block_reduce_t2d(T (&v)[NV], double (&out)[NV], double* scratch /* [32*NV] */) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) scratch[warp * NV + k] = double(v[k]);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double a = 0.0;
+            for (int w = 0; w < nwarp; ++w) a += scratch[w * NV + k];
+            out[k] = a;
+        }
+    }
+}
+
 // ------------------------------------------------------------------------------------------------
 // xfwd: grid (ceil(ny/ty_a), nz, n_pairs).  Each CTA takes rows [y0, y0+rows) of layer z for the two
 // images of pair p: s[img] = normalise((1-t) sp[src0] + t sp[src1]) (or a copy), written back to s,
 // packed as re/im of 3*rows complex lines, zero-padded to Px and transformed along x.
 // Output spec[p][kx][c][z][y].
-template <typename T, bool DO_FFT>
+template <typename T, bool DO_FFT, int PX>
 __global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xfwd_kernel(GroupArgs<T> g) {
     using C = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -110,13 +135,15 @@ __global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xfwd_kernel(GroupAr
         buf[line * g.lsx + fft_pad(x)] = C{T(0), T(0)};
     }
     __syncthreads();
-    fft_lines(buf, tw, g.planx, g.lsx, 3 * rows, tid, nthr);
-    // transpose out: consecutive threads take consecutive y of one (kx, c)
-    C* outp = g.spec + (size_t)p * g.Px * 3 * g.nz * g.ny;
-    for (int it = tid; it < g.Px * 3 * rows; it += nthr) {
-        const int yy = it % rows, rest = it / rows;
-        const int c = rest % 3, kx = rest / 3;
-        outp[((size_t)(kx * 3 + c) * g.nz + z) * g.ny + y0 + yy] = buf[(c * rows + yy) * g.lsx + fft_pad(kx)];
+    fft_lines_any<PX>(buf, tw, g.planx, g.lsx, 3 * rows, tid, nthr);
+    // transpose out: each thread writes the rows of one (kx, c), contiguous in y
+    const int Px = PX > 0 ? PX : g.Px;
+    C* outp = g.spec + (size_t)p * Px * 3 * g.nz * g.ny;
+    for (int kc = tid; kc < Px * 3; kc += nthr) {
+        const int kx = kc / 3, c = kc - 3 * kx;
+        C* o = outp + ((size_t)kc * g.nz + z) * g.ny + y0;
+        const C* b = buf + c * rows * g.lsx + fft_pad(kx);
+        for (int yy = 0; yy < rows; ++yy) o[yy] = b[yy * g.lsx];
     }
 }
 
@@ -131,33 +158,86 @@ __global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xfwd_kernel(GroupAr
 // kYzItems (ky, z) results per thread in registers, so one shared buffer serves both transforms.
 constexpr int kYzItems = 4;
 
-template <typename T>
-__global__ void __launch_bounds__(kMaxThreadsYz, kMinBlocksYz) yz_kernel(GroupArgs<T> g, int stage_dhat) {
-    using C = cplx<T>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* tw = reinterpret_cast<C*>(smem_raw);
-    C* A = tw + g.Py;  // 3*nz lines of stride lsy
-    const int tid = threadIdx.x, nthr = blockDim.x;
-    const int kx = blockIdx.x, p = blockIdx.y;
-    const int ny = g.ny, nz = g.nz, Py = g.Py, L = 3 * nz;
-    const int hx = g.Px / 2, hy = Py / 2;
-    const int kxo = min(kx, g.Px - kx);
-    C* blk = g.spec + ((size_t)p * g.Px + kx) * 3 * nz * ny;
-    // this kx's slab of the tensor-spectrum octant: [kyo][|dz|][6], staged when it fits
-    const T* dslab = g.dhat + (size_t)kxo * (hy + 1) * nz * 6;
-    T* dsm = reinterpret_cast<T*>(A + L * g.lsy);
-    if (stage_dhat) {
-        for (int i = tid; i < (hy + 1) * nz * 6; i += nthr) dsm[i] = dslab[i];
-        dslab = dsm;
+// z-convolution for a compile-time layer count NZ: one thread per (output component a, ky), a uniform
+// across a warp (nthr/3 a multiple of 32), both z loops unrolled so |z - z'| and the z-parity sign are
+// constants.  Row a of the tensor: a = x: (xx, xy, i xz); a = y: (xy, yy, i yz); a = z: (i xz, i yz, zz).
+template <int NZ, typename T, typename C>
+__device__ __forceinline__ void zconv_c(C* A, int lsy, int Py, int kx, int Px, const T* dslab, int tid, int nthr) {
+    const int hx = Px / 2, hy = Py / 2;
+    const T sxg = kx > hx ? T(-1) : T(1);
+    const int nk = nthr / 3;
+    for (int k0 = 0; k0 < Py; k0 += nk) {
+        const int a = tid / nk;
+        const int ky = k0 + (tid - a * nk);
+        const bool act = a < 3 && ky < Py;
+        C out[NZ];
+        int pky = 0;
+        if (act) {
+            const int kyo = min(ky, Py - ky);
+            const T syg = ky > hy ? T(-1) : T(1);
+            const T* d = dslab + (size_t)kyo * NZ * 6;
+            pky = fft_pad(ky);
+            // coefficient slots (xx 0, yy 1, zz 2, xy 3, xz 4, yz 5) and x/y parity signs of row a
+            const int i0 = a == 0 ? 0 : (a == 1 ? 3 : 4);
+            const int i1 = a == 0 ? 3 : (a == 1 ? 1 : 5);
+            const int i2 = a == 0 ? 4 : (a == 1 ? 5 : 2);
+            const T f0 = a == 0 ? T(1) : (a == 1 ? sxg * syg : sxg);
+            const T f1 = a == 0 ? sxg * syg : (a == 1 ? T(1) : syg);
+            const T f2 = a == 0 ? sxg : (a == 1 ? syg : T(1));
+            T e0[NZ], e1[NZ], e2[NZ];
+#pragma unroll
+            for (int q = 0; q < NZ; ++q) {
+                e0[q] = d[q * 6 + i0] * f0;
+                e1[q] = d[q * 6 + i1] * f1;
+                e2[q] = d[q * 6 + i2] * f2;
+            }
+#pragma unroll
+            for (int z = 0; z < NZ; ++z) out[z] = C{T(0), T(0)};
+            if (a < 2) {
+#pragma unroll
+                for (int zp = 0; zp < NZ; ++zp) {
+                    const C sx = A[(0 * NZ + zp) * lsy + pky];
+                    const C sy = A[(1 * NZ + zp) * lsy + pky];
+                    const C sz = A[(2 * NZ + zp) * lsy + pky];
+#pragma unroll
+                    for (int z = 0; z < NZ; ++z) {
+                        const int q = z >= zp ? z - zp : zp - z;
+                        const T g2 = z >= zp ? e2[q] : -e2[q];  // odd in z
+                        out[z].x += e0[q] * sx.x + e1[q] * sy.x - g2 * sz.y;
+                        out[z].y += e0[q] * sx.y + e1[q] * sy.y + g2 * sz.x;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int zp = 0; zp < NZ; ++zp) {
+                    const C sx = A[(0 * NZ + zp) * lsy + pky];
+                    const C sy = A[(1 * NZ + zp) * lsy + pky];
+                    const C sz = A[(2 * NZ + zp) * lsy + pky];
+#pragma unroll
+                    for (int z = 0; z < NZ; ++z) {
+                        const int q = z >= zp ? z - zp : zp - z;
+                        const T g0 = z >= zp ? e0[q] : -e0[q];  // odd in z
+                        const T g1 = z >= zp ? e1[q] : -e1[q];  // odd in z
+                        out[z].x += -g0 * sx.y - g1 * sy.y + e2[q] * sz.x;
+                        out[z].y += g0 * sx.x + g1 * sy.x + e2[q] * sz.y;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (act) {
+            // conjugated: the inverse transform is the conjugate of the forward transform of the conjugate
+#pragma unroll
+            for (int z = 0; z < NZ; ++z) A[(a * NZ + z) * lsy + pky] = cconj(out[z]);
+        }
+        __syncthreads();
     }
-    for (int i = tid; i < Py; i += nthr) tw[i] = g.twy[i];
-    for (int it = tid; it < L * Py; it += nthr) {
-        const int line = it / Py, y = it - line * Py;
-        A[line * g.lsy + fft_pad(y)] = (y < ny) ? blk[line * ny + y] : C{T(0), T(0)};
-    }
-    __syncthreads();
-    fft_lines(A, tw, g.plany, g.lsy, L, tid, nthr);
-    // z-convolution with the tensor spectrum, in passes of whole ky columns (item = ky * nz + z)
+}
+
+// z-convolution for any layer count, in passes of whole ky columns (item = ky * nz + z).
+template <typename T, typename C>
+__device__ __forceinline__ void zconv_any(C* A, int lsy, int Py, int nz, int kx, int Px, const T* dslab, int tid, int nthr) {
+    const int hx = Px / 2, hy = Py / 2;
     const T sxg = kx > hx ? T(-1) : T(1);
     const int n_items = Py * nz;
     const int per_pass = max(nz, ((nthr * kYzItems) / nz) * nz);
@@ -184,9 +264,9 @@ __global__ void __launch_bounds__(kMaxThreadsYz, kMinBlocksYz) yz_kernel(GroupAr
                     const T dxy = d[3] * sxy;
                     const T dxz = d[4] * (sxg * szg);  // coefficient of i
                     const T dyz = d[5] * (syg * szg);  // coefficient of i
-                    const C sx = A[(0 * nz + zp) * g.lsy + pky];
-                    const C sy = A[(1 * nz + zp) * g.lsy + pky];
-                    const C sz = A[(2 * nz + zp) * g.lsy + pky];
+                    const C sx = A[(0 * nz + zp) * lsy + pky];
+                    const C sy = A[(1 * nz + zp) * lsy + pky];
+                    const C sz = A[(2 * nz + zp) * lsy + pky];
                     // i*c*S = (-c S.y, c S.x)
                     hx_.x += dxx * sx.x + dxy * sy.x - dxz * sz.y;
                     hx_.y += dxx * sx.y + dxy * sy.y + dxz * sz.x;
@@ -207,14 +287,47 @@ __global__ void __launch_bounds__(kMaxThreadsYz, kMinBlocksYz) yz_kernel(GroupAr
             if (it < end) {
                 const int ky = it / nz, z = it - ky * nz;
                 const int pky = fft_pad(ky);
-                // conjugated: the inverse transform is the conjugate of the forward transform of the conjugate
 #pragma unroll
-                for (int c = 0; c < 3; ++c) A[(c * nz + z) * g.lsy + pky] = cconj(res[q][c]);
+                for (int c = 0; c < 3; ++c) A[(c * nz + z) * lsy + pky] = cconj(res[q][c]);
             }
         }
         __syncthreads();
     }
-    fft_lines(A, tw, g.plany, g.lsy, L, tid, nthr);
+}
+
+template <typename T, int PY, int NZ>
+__global__ void __launch_bounds__(kMaxThreadsYz, kMinBlocksYz) yz_kernel(GroupArgs<T> g, int stage_dhat) {
+    using C = cplx<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* A = tw + g.Py;  // 3*nz lines of stride lsy
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int kx = blockIdx.x, p = blockIdx.y;
+    const int Py = PY > 0 ? PY : g.Py;
+    const int nz = NZ > 0 ? NZ : g.nz;
+    const int ny = g.ny, L = 3 * nz;
+    const int hy = Py / 2;
+    const int kxo = min(kx, g.Px - kx);
+    C* blk = g.spec + ((size_t)p * g.Px + kx) * 3 * nz * ny;
+    // this kx's slab of the tensor-spectrum octant: [kyo][|dz|][6], staged when it fits
+    const T* dslab = g.dhat + (size_t)kxo * (hy + 1) * nz * 6;
+    T* dsm = reinterpret_cast<T*>(A + L * g.lsy);
+    if (stage_dhat) {
+        for (int i = tid; i < (hy + 1) * nz * 6; i += nthr) dsm[i] = dslab[i];
+        dslab = dsm;
+    }
+    for (int i = tid; i < Py; i += nthr) tw[i] = g.twy[i];
+    for (int it = tid; it < L * Py; it += nthr) {
+        const int line = it / Py, y = it - line * Py;  // Py is a constant in the specialised variants
+        A[line * g.lsy + fft_pad(y)] = (y < ny) ? blk[line * ny + y] : C{T(0), T(0)};
+    }
+    __syncthreads();
+    fft_lines_any<PY>(A, tw, g.plany, g.lsy, L, tid, nthr);
+    if constexpr (NZ > 0)
+        zconv_c<NZ>(A, g.lsy, Py, kx, g.Px, dslab, tid, nthr);
+    else
+        zconv_any(A, g.lsy, Py, nz, kx, g.Px, dslab, tid, nthr);
+    fft_lines_any<PY>(A, tw, g.plany, g.lsy, L, tid, nthr);
     for (int it = tid; it < L * ny; it += nthr) {
         const int line = it / ny, y = it - line * ny;
         blk[line * ny + y] = cconj(A[line * g.lsy + fft_pad(y)]);
@@ -232,7 +345,7 @@ __global__ void __launch_bounds__(kMaxThreadsYz, kMinBlocksYz) yz_kernel(GroupAr
 // MODE 1 (eval): FP64 energy terms of the FP64-renormalised spins, bonds to +x, +y, +z counted once
 //                (Eq. 1): tJ = -sum s_i.s_j, tD = sum (r_ij x z).(s_i x s_j), tK = -sum s_z^2,
 //                tw = -(1/2) sum conv.s; optionally the field h.
-template <typename T, bool DO_FFT, int MODE>
+template <typename T, bool DO_FFT, int MODE, int PX>
 __global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xinv_kernel(GroupArgs<T> g, T dt, T* hout) {
     using C = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -246,14 +359,16 @@ __global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xinv_kernel(GroupAr
     const int ia = 2 * p;
     if (DO_FFT) {
         for (int i = tid; i < g.Px; i += nthr) tw[i] = g.twx[i];
-        const C* inp = g.spec + (size_t)p * g.Px * 3 * nz * ny;
-        for (int it = tid; it < g.Px * 3 * rows; it += nthr) {
-            const int yy = it % rows, rest = it / rows;
-            const int c = rest % 3, kx = rest / 3;
-            buf[(c * rows + yy) * g.lsx + fft_pad(kx)] = cconj(inp[((size_t)(kx * 3 + c) * nz + z) * ny + y0 + yy]);
+        const int Px = PX > 0 ? PX : g.Px;
+        const C* inp = g.spec + (size_t)p * Px * 3 * nz * ny;
+        for (int kc = tid; kc < Px * 3; kc += nthr) {
+            const int kx = kc / 3, c = kc - 3 * kx;
+            const C* s = inp + ((size_t)kc * nz + z) * ny + y0;
+            C* b = buf + c * rows * g.lsx + fft_pad(kx);
+            for (int yy = 0; yy < rows; ++yy) b[yy * g.lsx] = cconj(s[yy]);
         }
         __syncthreads();
-        fft_lines(buf, tw, g.planx, g.lsx, 3 * rows, tid, nthr);
+        fft_lines_any<PX>(buf, tw, g.planx, g.lsx, 3 * rows, tid, nthr);
     }
     constexpr int NV = MODE == 0 ? 2 : 8;
     double acc[NV];
@@ -347,11 +462,10 @@ __global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xinv_kernel(GroupAr
             }
         }
     }
-    if (MODE == 0) {
-        acc[0] = double(eacc[0]);
-        acc[1] = double(eacc[1]);
-    }
-    block_reduce_d<NV>(acc, red);
+    if constexpr (MODE == 0)
+        block_reduce_t2d<2>(eacc, acc, red);
+    else
+        block_reduce_d<NV>(acc, red);
     if (tid == 0) {
         const int blk = blockIdx.y * gridDim.x + blockIdx.x;
         for (int h = 0; h < 2; ++h) {
@@ -404,9 +518,7 @@ __global__ void __launch_bounds__(256) arc_kernel(GroupArgs<T> g, ArcArgs a) {
             }
         }
     }
-#pragma unroll
-    for (int i = 0; i < kArcMaxChunk; ++i) acc[i] = double(part[i]);
-    block_reduce_d<kArcMaxChunk>(acc, red);
+    block_reduce_t2d<kArcMaxChunk>(part, acc, red);
     if (tid == 0) {
         for (int i = 0; i < nd; ++i) a.dpart[((size_t)str * a.maxK + k_lo + i + 1) * a.n_tiles + blockIdx.x] = acc[i];
         __threadfence();
@@ -608,39 +720,83 @@ static inline int grid1d(size_t n, int thr) {
     return (int)(b ? b : 1);
 }
 
+// Compile-time padded lengths and (Py, nz) pairs of the workloads (FP32 only; the FP64 path and any
+// other size use the runtime plans).
+#define SS_FOR_PX(X) X(32) X(128) X(192) X(256) X(384)
+#define SS_FOR_PYNZ(X) X(32, 1) X(128, 4) X(128, 8) X(192, 4) X(256, 4) X(256, 8) X(384, 8)
+#define SS_FOR_NZ(X) X(1) X(4) X(8)
+
 template <typename T> void launch_xfwd(const GroupArgs<T>& g, bool do_fft, int nthr, size_t smem, cudaStream_t st) {
     dim3 grid((g.ny + g.ty_a - 1) / g.ty_a, g.nz, g.n_pairs);
-    if (do_fft) {
-        xfwd_kernel<T, true><<<grid, nthr, smem, st>>>(g);
-    } else {
-        xfwd_kernel<T, false><<<grid, nthr, 0, st>>>(g);
+    if (!do_fft) {
+        xfwd_kernel<T, false, 0><<<grid, nthr, 0, st>>>(g);
+        return;
     }
+    if constexpr (std::is_same<T, float>::value) {
+        switch (g.Px) {
+#define SS_CASE(P)                                                \
+    case P:                                                       \
+        xfwd_kernel<T, true, P><<<grid, nthr, smem, st>>>(g);     \
+        return;
+            SS_FOR_PX(SS_CASE)
+#undef SS_CASE
+            default: break;
+        }
+    }
+    xfwd_kernel<T, true, 0><<<grid, nthr, smem, st>>>(g);
 }
 
 template <typename T> void launch_yz(const GroupArgs<T>& g, int nthr, size_t smem, cudaStream_t st) {
     dim3 grid(g.Px, g.n_pairs);
     const size_t base = (size_t)(g.Py + 3 * g.nz * g.lsy) * sizeof(cplx<T>);
     const int stage = smem >= base + (size_t)(g.Py / 2 + 1) * g.nz * 6 * sizeof(T);
-    yz_kernel<T><<<grid, nthr, smem, st>>>(g, stage);
+    if constexpr (std::is_same<T, float>::value) {
+#define SS_CASE(P, Z)                                                   \
+    if (g.Py == P && g.nz == Z) {                                       \
+        yz_kernel<T, P, Z><<<grid, nthr, smem, st>>>(g, stage);         \
+        return;                                                         \
+    }
+        SS_FOR_PYNZ(SS_CASE)
+#undef SS_CASE
+#define SS_CASE(Z)                                                      \
+    if (g.nz == Z) {                                                    \
+        yz_kernel<T, 0, Z><<<grid, nthr, smem, st>>>(g, stage);         \
+        return;                                                         \
+    }
+        SS_FOR_NZ(SS_CASE)
+#undef SS_CASE
+    }
+    yz_kernel<T, 0, 0><<<grid, nthr, smem, st>>>(g, stage);
 }
 
 template <typename T>
 void launch_xinv_step(const GroupArgs<T>& g, bool do_fft, T dt, int nthr, size_t smem, cudaStream_t st) {
     dim3 grid((g.ny + g.ty_c - 1) / g.ty_c, g.nz, g.n_pairs);
-    if (do_fft) {
-        xinv_kernel<T, true, 0><<<grid, nthr, smem, st>>>(g, dt, nullptr);
-    } else {
-        xinv_kernel<T, false, 0><<<grid, nthr, smem, st>>>(g, dt, nullptr);
+    if (!do_fft) {
+        xinv_kernel<T, false, 0, 0><<<grid, nthr, smem, st>>>(g, dt, nullptr);
+        return;
     }
+    if constexpr (std::is_same<T, float>::value) {
+        switch (g.Px) {
+#define SS_CASE(P)                                                            \
+    case P:                                                                   \
+        xinv_kernel<T, true, 0, P><<<grid, nthr, smem, st>>>(g, dt, nullptr); \
+        return;
+            SS_FOR_PX(SS_CASE)
+#undef SS_CASE
+            default: break;
+        }
+    }
+    xinv_kernel<T, true, 0, 0><<<grid, nthr, smem, st>>>(g, dt, nullptr);
 }
 
 template <typename T>
 void launch_xinv_eval(const GroupArgs<T>& g, bool do_fft, T* hout, int nthr, size_t smem, cudaStream_t st) {
     dim3 grid((g.ny + g.ty_c - 1) / g.ty_c, g.nz, g.n_pairs);
     if (do_fft) {
-        xinv_kernel<T, true, 1><<<grid, nthr, smem, st>>>(g, T(0), hout);
+        xinv_kernel<T, true, 1, 0><<<grid, nthr, smem, st>>>(g, T(0), hout);
     } else {
-        xinv_kernel<T, false, 1><<<grid, nthr, smem, st>>>(g, T(0), hout);
+        xinv_kernel<T, false, 1, 0><<<grid, nthr, smem, st>>>(g, T(0), hout);
     }
 }
 
@@ -672,12 +828,26 @@ void launch_extract_octant(const double2* spec, T* dhat, int Px, int Py, int nz,
 
 // Raises the dynamic shared-memory limit of every kernel that stages lines in shared memory.
 template <typename T> void set_smem_limits(int bytes) {
-    cudaFuncSetAttribute(xfwd_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaFuncSetAttribute(yz_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaFuncSetAttribute(xinv_kernel<T, true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaFuncSetAttribute(xinv_kernel<T, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaFuncSetAttribute(xinv_kernel<T, false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaFuncSetAttribute(xinv_kernel<T, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaFuncSetAttribute(xfwd_kernel<T, true, 0>, attr, bytes);
+    cudaFuncSetAttribute(yz_kernel<T, 0, 0>, attr, bytes);
+    cudaFuncSetAttribute(xinv_kernel<T, true, 0, 0>, attr, bytes);
+    cudaFuncSetAttribute(xinv_kernel<T, true, 1, 0>, attr, bytes);
+    cudaFuncSetAttribute(xinv_kernel<T, false, 0, 0>, attr, bytes);
+    cudaFuncSetAttribute(xinv_kernel<T, false, 1, 0>, attr, bytes);
+    if constexpr (std::is_same<T, float>::value) {
+#define SS_CASE(P)                                                       \
+    cudaFuncSetAttribute(xfwd_kernel<T, true, P>, attr, bytes);          \
+    cudaFuncSetAttribute(xinv_kernel<T, true, 0, P>, attr, bytes);
+        SS_FOR_PX(SS_CASE)
+#undef SS_CASE
+#define SS_CASE(P, Z) cudaFuncSetAttribute(yz_kernel<T, P, Z>, attr, bytes);
+        SS_FOR_PYNZ(SS_CASE)
+#undef SS_CASE
+#define SS_CASE(Z) cudaFuncSetAttribute(yz_kernel<T, 0, Z>, attr, bytes);
+        SS_FOR_NZ(SS_CASE)
+#undef SS_CASE
+    }
 }
 
 #ifdef SS_COMMON_LAUNCHERS
