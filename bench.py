@@ -40,8 +40,9 @@ L2_FLUSH_BYTES = 256 << 20
 #   yz:   read + write the pair spectrum 24 + 24 (plus the tensor octant once per launch)
 #   xinv: read the spectrum 24, read s 12, write sp 12
 #   arc:  read sp 12
-KERNEL_NAMES = ("xfwd", "yz", "xinv", "arc")
-BYTES_PER_SITE_IMAGE = {"xfwd": 48, "yz": 48, "xinv": 48, "arc": 12}
+#   reparam: per-image partial sums only (no per-site traffic)
+KERNEL_NAMES = ("xfwd", "yz", "xinv", "arc", "reparam")
+BYTES_PER_SITE_IMAGE = {"xfwd": 48, "yz": 48, "xinv": 48, "arc": 12, "reparam": 0}
 REF_IMAGES = 8
 
 
@@ -267,7 +268,7 @@ def main():
     # per-kernel roofline (kernels launched one by one on the library stream, CUDA-event timed)
     sm.set_path(0, path_dev)
     ms = sm.time_kernels(reps=20)
-    names = [n for n in KERNEL_NAMES if n != "yz" or len(ms) == 4]
+    names = [n for n in KERNEL_NAMES if n != "yz" or len(ms) == len(KERNEL_NAMES)]
     share = ms / ms.sum()
     dom = int(np.argmax(ms))
     dname = names[dom]

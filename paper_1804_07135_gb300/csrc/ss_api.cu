@@ -74,7 +74,7 @@ struct Group {
     bool dipole = false;
     FftPlan planx{}, plany{};
     int lsx = 1, lsy = 1;
-    int ty_a = 1, ty_c = 1, thr_a = 128, thr_b = 128, thr_c = 128, thr_arc = 256;
+    int ty_a = 1, ty_c = 1, thr_a = 128, thr_b = 128, thr_c = 128, thr_arc = 1024;
     size_t smem_a = 0, smem_b = 0, smem_c = 0, smem_c_eval = 0;
     int n_eblk = 0;
     // device
@@ -84,7 +84,6 @@ struct Group {
     double* epart = nullptr;
     int *d_str_img0 = nullptr, *d_str_K = nullptr;
     double *dpart = nullptr, *e_last = nullptr, *eval_terms = nullptr, *eval_E = nullptr;
-    unsigned* counters = nullptr;
     ArcArgs arc{};
 };
 
@@ -294,7 +293,7 @@ template <typename T> ss_status setup_group(ss_ctx* c, Group& g) {
     ArcArgs& a = g.arc;
     a.n_str = nstr;
     a.maxK = maxK;
-    a.tile_elems = 1024;
+    a.tile_elems = 4096;  // 4 components per thread of a 1024-thread CTA
     a.n_tiles = (int)((M + a.tile_elems - 1) / a.tile_elems);
     a.kchunk = std::max(1, std::min(8, maxK - 1));
     a.n_kchunks = std::max(1, (maxK - 1 + a.kchunk - 1) / a.kchunk);
@@ -302,13 +301,11 @@ template <typename T> ss_status setup_group(ss_ctx* c, Group& g) {
     TRY(dalloc(c, (void**)&g.d_str_img0, nstr * sizeof(int)));
     TRY(dalloc(c, (void**)&g.d_str_K, nstr * sizeof(int)));
     TRY(dalloc(c, (void**)&g.dpart, (size_t)nstr * maxK * a.n_tiles * sizeof(double)));
-    TRY(dalloc(c, (void**)&g.counters, nstr * sizeof(unsigned)));
     TRY(dalloc(c, (void**)&g.e_last, (size_t)nstr * maxK * sizeof(double)));
     TRY(dalloc(c, (void**)&g.eval_terms, (size_t)nstr * maxK * 4 * sizeof(double)));
     TRY(dalloc(c, (void**)&g.eval_E, (size_t)nstr * maxK * sizeof(double)));
     CUDA_TRY(c, cudaMemcpyAsync(g.d_str_img0, g.str_img0.data(), nstr * sizeof(int), cudaMemcpyHostToDevice, c->cs));
     CUDA_TRY(c, cudaMemcpyAsync(g.d_str_K, g.str_K.data(), nstr * sizeof(int), cudaMemcpyHostToDevice, c->cs));
-    CUDA_TRY(c, cudaMemsetAsync(g.counters, 0, nstr * sizeof(unsigned), c->cs));
     CUDA_TRY(c, cudaMemsetAsync(g.dpart, 0, (size_t)nstr * maxK * a.n_tiles * sizeof(double), c->cs));
     CUDA_TRY(c, cudaMemsetAsync(g.e_last, 0, (size_t)nstr * maxK * sizeof(double), c->cs));
     CUDA_TRY(c, cudaMemsetAsync(g.s, 0, g.n_img * M * sizeof(T), c->cs));
@@ -316,7 +313,6 @@ template <typename T> ss_status setup_group(ss_ctx* c, Group& g) {
     a.str_img0 = g.d_str_img0;
     a.str_K = g.d_str_K;
     a.dpart = g.dpart;
-    a.counters = g.counters;
     a.e_last = g.e_last;
     launch_interp_identity(g.interp, 0, g.n_img, c->cs);
     CUDA_TRY(c, cudaGetLastError());
@@ -333,6 +329,7 @@ template <typename T> void issue_iteration(ss_ctx* c, cudaStream_t st) {
         if (g.dipole) launch_yz<T>(a, g.thr_b, g.smem_b, st);
         launch_xinv_step<T>(a, g.dipole, dt, g.thr_c, g.smem_c, st);
         launch_arc<T>(a, g.arc, g.thr_arc, st);
+        launch_reparam<T>(a, g.arc, st);
     }
 }
 
@@ -753,15 +750,17 @@ ss_status ss_time_kernels(ss_ctx* c, int reps, double* ms_out, int max_out, int*
                     if (which == 1) launch_yz<double>(a, g.thr_b, g.smem_b, c->cs);
                     if (which == 2) launch_xinv_step<double>(a, g.dipole, c->opts.dt, g.thr_c, g.smem_c, c->cs);
                     if (which == 3) launch_arc<double>(a, g.arc, g.thr_arc, c->cs);
+                    if (which == 4) launch_reparam<double>(a, g.arc, c->cs);
                 } else {
                     GroupArgs<float> a = group_args<float>(c, g);
                     if (which == 0) launch_xfwd<float>(a, g.dipole, g.thr_a, g.smem_a, c->cs);
                     if (which == 1) launch_yz<float>(a, g.thr_b, g.smem_b, c->cs);
                     if (which == 2) launch_xinv_step<float>(a, g.dipole, (float)c->opts.dt, g.thr_c, g.smem_c, c->cs);
                     if (which == 3) launch_arc<float>(a, g.arc, g.thr_arc, c->cs);
+                    if (which == 4) launch_reparam<float>(a, g.arc, c->cs);
                 }
             };
-            for (int which = 0; which < 4; ++which) {
+            for (int which = 0; which < 5; ++which) {
                 if (which == 1 && !g.dipole) continue;
                 cudaEventRecord(ev[2 * k], c->cs);
                 run(which);
@@ -799,7 +798,7 @@ ss_status ss_string_info(const ss_ctx* c, int string, ss_string_desc* out) {
 int ss_kernels_per_iteration(const ss_ctx* c) {
     if (!c) return 0;
     int n = 0;
-    for (const Group& g : c->groups) n += g.dipole ? 4 : 3;
+    for (const Group& g : c->groups) n += g.dipole ? 5 : 4;
     return n;
 }
 

@@ -51,7 +51,8 @@ __host__ __device__ inline int fft_line_stride(int P) { return (P + (P >> 4) + 1
 // of sp[src0] when copy != 0.  Image indices are local to the size group.
 struct InterpEntry {
     int src0, src1;
-    double t;
+    double t;          // FP64 weight (Eq. 12)
+    float tf, omtf;    // t and 1 - t rounded once, for the FP32 blend
     int copy;
     int pad;
 };
@@ -92,7 +93,6 @@ struct ArcArgs {
     int kchunk;            // image differences per CTA along the string
     int n_kchunks;
     double* dpart;         // [n_str][maxK][n_tiles] squared-distance partials
-    unsigned* counters;    // [n_str] arrival tickets of the last-CTA finalisation
     double* e_last;        // [n_str][maxK] energies of the state before the step
     int reparam;           // 0: keep images where they are
 };
@@ -107,6 +107,7 @@ void launch_xinv_step(const GroupArgs<T>& g, bool do_fft, T dt, int nthr, size_t
 template <typename T>
 void launch_xinv_eval(const GroupArgs<T>& g, bool do_fft, T* hout, int nthr, size_t smem, cudaStream_t st);
 template <typename T> void launch_arc(const GroupArgs<T>& g, const ArcArgs& a, int nthr, cudaStream_t st);
+template <typename T> void launch_reparam(const GroupArgs<T>& g, const ArcArgs& a, cudaStream_t st);
 template <typename T>
 void launch_eval_reduce(const GroupArgs<T>& g, const ArcArgs& a, double* terms, double* energies, cudaStream_t st);
 template <typename T, typename Tin>

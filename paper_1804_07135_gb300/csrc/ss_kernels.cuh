@@ -104,7 +104,8 @@ __global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xfwd_kernel(GroupAr
                 const T* a = g.sp + (size_t)e.src0 * 3 * N + site;
                 T u0 = a[0], u1 = a[N], u2 = a[2 * N];
                 if (!e.copy) {
-                    const T t = T(e.t), omt = T(1.0 - e.t);
+                    const T t = sizeof(T) == 4 ? T(e.tf) : T(e.t);
+                    const T omt = sizeof(T) == 4 ? T(e.omtf) : T(1.0 - e.t);
                     const T* b = g.sp + (size_t)e.src1 * 3 * N + site;
                     u0 = omt * u0 + t * b[0];
                     u1 = omt * u1 + t * b[N];
@@ -161,8 +162,10 @@ constexpr int kYzItems = 4;
 // z-convolution for a compile-time layer count NZ: one thread per (output component a, ky), a uniform
 // across a warp (nthr/3 a multiple of 32), both z loops unrolled so |z - z'| and the z-parity sign are
 // constants.  Row a of the tensor: a = x: (xx, xy, i xz); a = y: (xy, yy, i yz); a = z: (i xz, i yz, zz).
+// dslab holds the coefficient (kyo, |dz|, comp) at dslab[kyo*dk + (|dz|*6 + comp)*dq].
 template <int NZ, typename T, typename C>
-__device__ __forceinline__ void zconv_c(C* A, int lsy, int Py, int kx, int Px, const T* dslab, int tid, int nthr) {
+__device__ __forceinline__ void zconv_c(C* A, int lsy, int Py, int kx, int Px, const T* dslab, int dk, int dq, int tid,
+                                        int nthr) {
     const int hx = Px / 2, hy = Py / 2;
     const T sxg = kx > hx ? T(-1) : T(1);
     const int nk = nthr / 3;
@@ -175,7 +178,7 @@ __device__ __forceinline__ void zconv_c(C* A, int lsy, int Py, int kx, int Px, c
         if (act) {
             const int kyo = min(ky, Py - ky);
             const T syg = ky > hy ? T(-1) : T(1);
-            const T* d = dslab + (size_t)kyo * NZ * 6;
+            const T* d = dslab + (size_t)kyo * dk;
             pky = fft_pad(ky);
             // coefficient slots (xx 0, yy 1, zz 2, xy 3, xz 4, yz 5) and x/y parity signs of row a
             const int i0 = a == 0 ? 0 : (a == 1 ? 3 : 4);
@@ -187,9 +190,9 @@ __device__ __forceinline__ void zconv_c(C* A, int lsy, int Py, int kx, int Px, c
             T e0[NZ], e1[NZ], e2[NZ];
 #pragma unroll
             for (int q = 0; q < NZ; ++q) {
-                e0[q] = d[q * 6 + i0] * f0;
-                e1[q] = d[q * 6 + i1] * f1;
-                e2[q] = d[q * 6 + i2] * f2;
+                e0[q] = d[(q * 6 + i0) * dq] * f0;
+                e1[q] = d[(q * 6 + i1) * dq] * f1;
+                e2[q] = d[(q * 6 + i2) * dq] * f2;
             }
 #pragma unroll
             for (int z = 0; z < NZ; ++z) out[z] = C{T(0), T(0)};
@@ -236,7 +239,8 @@ __device__ __forceinline__ void zconv_c(C* A, int lsy, int Py, int kx, int Px, c
 
 // z-convolution for any layer count, in passes of whole ky columns (item = ky * nz + z).
 template <typename T, typename C>
-__device__ __forceinline__ void zconv_any(C* A, int lsy, int Py, int nz, int kx, int Px, const T* dslab, int tid, int nthr) {
+__device__ __forceinline__ void zconv_any(C* A, int lsy, int Py, int nz, int kx, int Px, const T* dslab, int dk, int dq,
+                                          int tid, int nthr) {
     const int hx = Px / 2, hy = Py / 2;
     const T sxg = kx > hx ? T(-1) : T(1);
     const int n_items = Py * nz;
@@ -252,18 +256,18 @@ __device__ __forceinline__ void zconv_any(C* A, int lsy, int Py, int nz, int kx,
                 const int kyo = min(ky, Py - ky);
                 const T syg = ky > hy ? T(-1) : T(1);
                 const T sxy = sxg * syg;
-                const T* dcol = dslab + (size_t)kyo * nz * 6;
+                const T* dcol = dslab + (size_t)kyo * dk;
                 const int pky = fft_pad(ky);
                 C hx_ = {T(0), T(0)}, hy_ = {T(0), T(0)}, hz_ = {T(0), T(0)};
 #pragma unroll 2
                 for (int zp = 0; zp < nz; ++zp) {
                     const int dz = z - zp;
                     const T szg = dz < 0 ? T(-1) : T(1);
-                    const T* d = dcol + (dz < 0 ? -dz : dz) * 6;
-                    const T dxx = d[0], dyy = d[1], dzz = d[2];
-                    const T dxy = d[3] * sxy;
-                    const T dxz = d[4] * (sxg * szg);  // coefficient of i
-                    const T dyz = d[5] * (syg * szg);  // coefficient of i
+                    const T* d = dcol + (dz < 0 ? -dz : dz) * 6 * dq;
+                    const T dxx = d[0], dyy = d[dq], dzz = d[2 * dq];
+                    const T dxy = d[3 * dq] * sxy;
+                    const T dxz = d[4 * dq] * (sxg * szg);  // coefficient of i
+                    const T dyz = d[5 * dq] * (syg * szg);  // coefficient of i
                     const C sx = A[(0 * nz + zp) * lsy + pky];
                     const C sy = A[(1 * nz + zp) * lsy + pky];
                     const C sz = A[(2 * nz + zp) * lsy + pky];
@@ -309,12 +313,20 @@ __global__ void __launch_bounds__(kMaxThreadsYz, kMinBlocksYz) yz_kernel(GroupAr
     const int hy = Py / 2;
     const int kxo = min(kx, g.Px - kx);
     C* blk = g.spec + ((size_t)p * g.Px + kx) * 3 * nz * ny;
-    // this kx's slab of the tensor-spectrum octant: [kyo][|dz|][6], staged when it fits
+    // this kx's slab of the tensor-spectrum octant, global layout [kyo][|dz|][6]; staged in shared
+    // memory transposed to [|dz|*6 + comp][kyo] so that a warp (consecutive ky) reads consecutive words
     const T* dslab = g.dhat + (size_t)kxo * (hy + 1) * nz * 6;
+    int dk = nz * 6, dq = 1;  // strides of kyo and of (|dz|*6 + comp)
     T* dsm = reinterpret_cast<T*>(A + L * g.lsy);
     if (stage_dhat) {
-        for (int i = tid; i < (hy + 1) * nz * 6; i += nthr) dsm[i] = dslab[i];
+        const int n6 = nz * 6;
+        for (int i = tid; i < (hy + 1) * n6; i += nthr) {
+            const int kyo = i / n6, r = i - kyo * n6;
+            dsm[r * (hy + 1) + kyo] = dslab[i];
+        }
         dslab = dsm;
+        dk = 1;
+        dq = hy + 1;
     }
     for (int i = tid; i < Py; i += nthr) tw[i] = g.twy[i];
     for (int it = tid; it < L * Py; it += nthr) {
@@ -324,9 +336,9 @@ __global__ void __launch_bounds__(kMaxThreadsYz, kMinBlocksYz) yz_kernel(GroupAr
     __syncthreads();
     fft_lines_any<PY>(A, tw, g.plany, g.lsy, L, tid, nthr);
     if constexpr (NZ > 0)
-        zconv_c<NZ>(A, g.lsy, Py, kx, g.Px, dslab, tid, nthr);
+        zconv_c<NZ>(A, g.lsy, Py, kx, g.Px, dslab, dk, dq, tid, nthr);
     else
-        zconv_any(A, g.lsy, Py, nz, kx, g.Px, dslab, tid, nthr);
+        zconv_any(A, g.lsy, Py, nz, kx, g.Px, dslab, dk, dq, tid, nthr);
     fft_lines_any<PY>(A, tw, g.plany, g.lsy, L, tid, nthr);
     for (int it = tid; it < L * ny; it += nthr) {
         const int line = it / ny, y = it - line * ny;
@@ -482,20 +494,17 @@ __global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xinv_kernel(GroupAr
 
 // ------------------------------------------------------------------------------------------------
 // arc: grid (n_tiles, n_kchunks, n_str).  Squared distances |sp_k - sp_{k-1}|^2 over all 3N
-// components (Eq. 11), partial per tile.  The last CTA of a string (arrival ticket) sums the
-// partials in tile order, sums the energy partials in block order, scans the arc length, and for
-// every interior image k finds the largest j with alpha*_j <= k/(K-1) and t (Eq. 12).
-
+// components (Eq. 11), one partial per (string, k, tile), summed in T per thread and warp, in FP64
+// across warps.
 template <typename T>
-__global__ void __launch_bounds__(256) arc_kernel(GroupArgs<T> g, ArcArgs a) {
+__global__ void __launch_bounds__(1024) arc_kernel(GroupArgs<T> g, ArcArgs a) {
     __shared__ double red[32 * kArcMaxChunk];
-    __shared__ double alpha[kArcMaxK];
-    __shared__ int is_last;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int str = blockIdx.z;
     const int K = a.str_K[str], img0 = a.str_img0[str];
     const int k_lo = blockIdx.y * a.kchunk;
     const int nd = max(0, min(a.kchunk, K - 1 - k_lo));  // differences (k_lo+i, k_lo+i+1), i < nd
+    if (nd == 0) return;  // uniform over the block
     const size_t M = (size_t)3 * g.N;
     const size_t e0 = (size_t)blockIdx.x * a.tile_elems;
     const size_t e1 = min(M, e0 + a.tile_elems);
@@ -503,34 +512,34 @@ __global__ void __launch_bounds__(256) arc_kernel(GroupArgs<T> g, ArcArgs a) {
     T part[kArcMaxChunk];  // the thread's few squared differences per image pair, summed in T first
 #pragma unroll
     for (int i = 0; i < kArcMaxChunk; ++i) part[i] = T(0);
-    if (nd > 0) {
-        for (size_t e = e0 + tid; e < e1; e += nthr) {
-            const T* col = g.sp + (size_t)(img0 + k_lo) * M + e;
-            T prev = col[0];
+    for (size_t e = e0 + tid; e < e1; e += nthr) {
+        const T* col = g.sp + (size_t)(img0 + k_lo) * M + e;
+        T prev = col[0];
 #pragma unroll
-            for (int i = 0; i < kArcMaxChunk; ++i) {
-                if (i < nd) {
-                    const T cur = col[(size_t)(i + 1) * M];
-                    const T d = cur - prev;
-                    part[i] += d * d;
-                    prev = cur;
-                }
+        for (int i = 0; i < kArcMaxChunk; ++i) {
+            if (i < nd) {
+                const T cur = col[(size_t)(i + 1) * M];
+                const T d = cur - prev;
+                part[i] += d * d;
+                prev = cur;
             }
         }
     }
     block_reduce_t2d<kArcMaxChunk>(part, acc, red);
-    if (tid == 0) {
+    if (tid == 0)
         for (int i = 0; i < nd; ++i) a.dpart[((size_t)str * a.maxK + k_lo + i + 1) * a.n_tiles + blockIdx.x] = acc[i];
-        __threadfence();
-        const unsigned total = gridDim.x * gridDim.y;
-        const unsigned ticket = atomicAdd(a.counters + str, 1u);
-        is_last = (ticket == total - 1);
-    }
-    __syncthreads();
-    if (!is_last) return;
-    __threadfence();
-    // ---- finalisation by the last CTA of this string ----
-    // one warp per image: lanes stride over the partials, then a fixed shuffle tree (deterministic)
+}
+
+// reparam: grid (n_str), 1024 threads.  Sums the energy partials (block order) and the distance
+// partials (tile order) of every image in FP64, one warp per image; scans the arc length s_k
+// (Eq. 11); forms alpha*_k = s_k / s_{K-1} (Eq. 12) and, for every interior image k, the largest j
+// with alpha*_j <= k/(K-1) and t; writes the interpolation table the next xfwd applies.
+template <typename T>
+__global__ void __launch_bounds__(1024) reparam_kernel(GroupArgs<T> g, ArcArgs a) {
+    __shared__ double alpha[kArcMaxK];
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int str = blockIdx.x;
+    const int K = a.str_K[str], img0 = a.str_img0[str];
     const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
     for (int k = warp; k < K; k += nwarp) {
         double e = 0.0, d2 = 0.0;
@@ -538,7 +547,7 @@ __global__ void __launch_bounds__(256) arc_kernel(GroupArgs<T> g, ArcArgs a) {
         for (int b = lane; b < g.n_eblk; b += 32) e += ep[b];
         if (k > 0) {
             const double* dp = a.dpart + ((size_t)str * a.maxK + k) * a.n_tiles;
-            for (int t = lane; t < a.n_tiles; t += 32) d2 += __ldcg(dp + t);  // written by other CTAs
+            for (int t = lane; t < a.n_tiles; t += 32) d2 += dp[t];
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -558,7 +567,6 @@ __global__ void __launch_bounds__(256) arc_kernel(GroupArgs<T> g, ArcArgs a) {
             s += alpha[k];
             alpha[k] = s;  // s_k, with s_0 = 0 (Eq. 11)
         }
-        a.counters[str] = 0u;
     }
     __syncthreads();
     const double sK = alpha[K - 1];
@@ -572,6 +580,8 @@ __global__ void __launch_bounds__(256) arc_kernel(GroupArgs<T> g, ArcArgs a) {
         e.src0 = img0 + k;
         e.src1 = img0 + k;
         e.t = 0.0;
+        e.tf = 0.f;
+        e.omtf = 1.f;
         e.copy = 1;
         e.pad = 0;
         if (move && k > 0 && k < K - 1) {
@@ -589,6 +599,8 @@ __global__ void __launch_bounds__(256) arc_kernel(GroupArgs<T> g, ArcArgs a) {
             e.src0 = img0 + j;
             e.src1 = img0 + j + 1;
             e.t = (ak - alpha[j]) / (alpha[j + 1] - alpha[j]);
+            e.tf = (float)e.t;
+            e.omtf = (float)(1.0 - e.t);
             e.copy = 0;
         }
         const_cast<InterpEntry*>(g.interp)[img0 + k] = e;
@@ -705,8 +717,9 @@ __global__ void interp_identity_kernel(InterpEntry* tab, int img0, int K) {
         InterpEntry e;
         e.src0 = e.src1 = img0 + k;
         e.t = 0.0;
+        e.tf = 0.f;
+        e.omtf = 1.f;
         e.copy = 1;
-        e.pad = 0;
         tab[img0 + k] = e;
     }
 }
@@ -805,6 +818,10 @@ template <typename T> void launch_arc(const GroupArgs<T>& g, const ArcArgs& a, i
     arc_kernel<T><<<grid, nthr, 0, st>>>(g, a);
 }
 
+template <typename T> void launch_reparam(const GroupArgs<T>& g, const ArcArgs& a, cudaStream_t st) {
+    reparam_kernel<T><<<a.n_str, 1024, 0, st>>>(g, a);
+}
+
 template <typename T>
 void launch_eval_reduce(const GroupArgs<T>& g, const ArcArgs& a, double* terms, double* energies, cudaStream_t st) {
     eval_reduce_kernel<T><<<a.n_str, 128, 0, st>>>(g, a, terms, energies);
@@ -876,6 +893,7 @@ void launch_interp_identity(InterpEntry* tab, int img0, int K, cudaStream_t st) 
     template void launch_xinv_step<T>(const GroupArgs<T>&, bool, T, int, size_t, cudaStream_t);                \
     template void launch_xinv_eval<T>(const GroupArgs<T>&, bool, T*, int, size_t, cudaStream_t);               \
     template void launch_arc<T>(const GroupArgs<T>&, const ArcArgs&, int, cudaStream_t);                       \
+    template void launch_reparam<T>(const GroupArgs<T>&, const ArcArgs&, cudaStream_t);                        \
     template void launch_eval_reduce<T>(const GroupArgs<T>&, const ArcArgs&, double*, double*, cudaStream_t);  \
     template void launch_aos_to_soa<T, float>(const float*, T*, int, int, int*, cudaStream_t);                 \
     template void launch_aos_to_soa<T, double>(const double*, T*, int, int, int*, cudaStream_t);               \
