@@ -55,6 +55,7 @@ def parse():
     p.add_argument("--iters", type=int, default=None, help="iterations per step (default: the workload's)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-accuracy", action="store_true", help="skip the FP64-GPU barrier comparison")
+    p.add_argument("--no-other-workloads", action="store_true", help="skip the short runs of the batch workloads")
     return p.parse_args()
 
 
@@ -319,6 +320,9 @@ def main():
                             "iterations_timed": iters64, "barrier_dE": dE64, "k_max": k64}
         line["speedup_vs_fp64_gpu"] = value / line["fp64_gpu"]["value"]
         line["barrier_abs_err_vs_fp64_gpu"] = abs(dE - dE64)
+    if not args.no_other_workloads:
+        line["other_workloads"] = {w.name: other_workload(binding, w, stream) for w in
+                                   (workloads.boundary_sweep(), workloads.uneven_study())}
     if not args.no_cpu_baseline and world == 1:
         v, cores, t = cpu_oracle_sample(spec, wl.dt)
         line["cpu_baseline"] = {"value": v, "unit": "spin-updates/s", "cores": cores, "kind": "oracle",
@@ -328,6 +332,28 @@ def main():
     print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
+
+
+def other_workload(binding, wl, stream, iters=20, warm=3):
+    """Device-timed spin-updates/s of a short run of another workload (a batch of strings in one
+    context): `iters` graph-replayed iterations after `warm`, inputs resident."""
+    import torch
+    descs = [(s.nx, s.ny, s.nz, s.J, s.D, s.K, s.w, s.n_images) for s in wl.strings]
+    with binding.StringMethod(descs, dt=wl.dt, stream=stream.cuda_stream) as sm:
+        for i, s in enumerate(wl.strings):
+            sm.set_path(i, torch.from_numpy(s.initial_path().astype(np.float32)).cuda())
+        sm.step(warm)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        sm.step(iters)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        ms = sm.time_kernels(reps=3)
+    return {"value": wl.spin_updates_per_iter * iters / t, "unit": "spin-updates/s", "iterations_timed": iters,
+            "strings": len(wl.strings), "spin_updates_per_iter": wl.spin_updates_per_iter,
+            "ms_per_iter": 1e3 * t / iters, "kernel_ms_total": float(ms.sum())}
 
 
 def padded(n):

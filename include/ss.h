@@ -117,6 +117,11 @@ ss_status ss_field(ss_ctx* ctx, int string, void* out, int dtype, int on_device)
  * term with its constant set to 1, in FP64.  Synchronises. */
 ss_status ss_grad(ss_ctx* ctx, int string, int image, void* dE_ds, int dtype, int on_device, double* dE_dJDKw);
 
+/* The four energy terms of every image of the current path of `string`, from one evaluation: host
+ * out[n_images][4] = (dE/dJ, dE/dD, dE/dK, dE/dw) per image (Eq. 1 is linear in each constant, so each
+ * entry is that term with its constant set to 1), in FP64.  Synchronises. */
+ss_status ss_energy_terms(ss_ctx* ctx, int string, double* out);
+
 /* Measures the kernels of one iteration: each kernel is launched on its own (not from the graph) on
  * the context's stream, bracketed by CUDA events, for `reps` >= 1 timed iterations after one untimed
  * iteration.  ms_out[i] (host, up to max_out entries) receives the mean duration in milliseconds of

@@ -62,6 +62,7 @@ _SIGNATURES = {
     "ss_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "ss_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
                                ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "ss_energy_terms": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "ss_time_kernels": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_int)]),
     "ss_field_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
@@ -272,6 +273,14 @@ def ss_grad(ctx, string: int, image: int, dE_ds=None) -> np.ndarray:
     return terms
 
 
+def ss_energy_terms(ctx, string: int) -> np.ndarray:
+    """[n_images][4] = (dE/dJ, dE/dD, dE/dK, dE/dw) of every image, from one evaluation."""
+    d = ss_string_info(ctx, string)
+    out = np.zeros((d.n_images, 4))
+    _check(_lib.ss_energy_terms(ctx, int(string), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), ctx)
+    return out
+
+
 def ss_time_kernels(ctx, reps: int = 10) -> np.ndarray:
     """Mean milliseconds per kernel of one iteration (xfwd, yz, xinv, arc per size group)."""
     out = np.zeros(64)
@@ -362,6 +371,9 @@ class StringMethod:
         out = np.zeros(self.shape(string), dtype=dtype)
         ss_field(self.ctx, string, out)
         return out
+
+    def energy_terms(self, string=0):
+        return ss_energy_terms(self.ctx, string)
 
     def grad(self, string, image, want_ds=True, dtype=np.float64):
         ds = np.zeros(self.shape(string)[1:], dtype=dtype) if want_ds else None

@@ -730,6 +730,21 @@ ss_status ss_grad(ss_ctx* c, int string, int image, void* dE_ds, int dtype, int 
     return st;
 }
 
+ss_status ss_energy_terms(ss_ctx* c, int string, double* out) {
+    TRY(check_string(c, string));
+    if (!out) return fail(c, SS_ERR_INVALID_ARG, "out is NULL");
+    StringRec& r = c->strs[string];
+    Group& g = c->groups[r.group];
+    TRY(check_paths(c, g));
+    TRY(enter(c));
+    TRY(evaluate_group(c, g, false));
+    CUDA_TRY(c, cudaMemcpyAsync(out, g.eval_terms + (size_t)r.local * g.arc.maxK * 4, (size_t)r.d.n_images * 4 * sizeof(double),
+                                cudaMemcpyDeviceToHost, c->cs));
+    ss_status st = sync_check(c);
+    TRY(leave(c));
+    return st;
+}
+
 ss_status ss_time_kernels(ss_ctx* c, int reps, double* ms_out, int max_out, int* n_out) {
     if (!c || reps < 1 || !n_out) return c ? fail(c, SS_ERR_INVALID_ARG, "reps >= 1 and n_out required") : SS_ERR_INVALID_ARG;
     for (const Group& g : c->groups) TRY(check_paths(c, g));

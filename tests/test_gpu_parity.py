@@ -246,3 +246,30 @@ def test_overflow_is_reported_as_nonfinite(ss):
         with pytest.raises(ss.SsError) as e:
             sm.step_energies(0)
         assert e.value.status == ss.SS_ERR_NONFINITE
+
+
+def test_uneven_parameter_study_batch(ss):
+    # the 20-string, four-size parameter study in one context (one launch per kernel and size)
+    wl = W.uneven_study()
+    cases = [(s.nx, s.ny, s.nz, s.J, s.D, s.K, s.w, s.n_images) for s in wl.strings]
+    with _sm(ss, cases) as sm:
+        for i, s in enumerate(wl.strings):
+            sm.set_path(i, s.initial_path().astype(np.float32))
+        sm.step(3)
+        assert sm.kernels_per_iteration() == 5 * len({(c[0], c[1], c[2]) for c in cases})
+        rng = np.random.default_rng(3)
+        checked = set()
+        for i, s in enumerate(wl.strings):
+            e = sm.energies(i)
+            assert np.isfinite(e).all()
+            if (s.nx, s.nz) in checked:
+                continue
+            checked.add((s.nx, s.nz))
+            state = sm.get_path(i)
+            h = sm.field(i)
+            m = _model(cases[i])
+            sites = rng.integers(0, s.n_sites, size=12)
+            for k in (0, s.n_images // 2):
+                ref = oracle.field_at(m, _unit(state[k]), sites)
+                assert np.abs(h[k][sites] - ref).max() <= 1e-5 * np.abs(ref).max()
+    assert len(checked) == 4
