@@ -39,6 +39,7 @@ class StringEnergy(torch.autograd.Function):
         binding.ss_field(sm.ctx, string, field)
         ctx.save_for_backward(field, torch.from_numpy(terms))
         ctx.spin_dtype = spins.dtype
+        ctx.params_device, ctx.params_dtype = params.device, params.dtype
         return torch.from_numpy(energies).to(spins.device)
 
     @staticmethod
@@ -47,7 +48,7 @@ class StringEnergy(torch.autograd.Function):
         g = grad_e.detach().to(torch.float64)
         grad_spins = -(g.to(field.device)[:, None, None] * field.to(torch.float64)).to(ctx.spin_dtype)
         grad_params = (g.cpu()[:, None] * terms).sum(0)
-        return grad_spins, grad_params.to(grad_e.device), None, None
+        return grad_spins, grad_params.to(ctx.params_device, ctx.params_dtype), None, None
 
 
 def string_energies(sm, string, spins, params):
