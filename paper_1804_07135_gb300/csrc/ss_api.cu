@@ -79,6 +79,7 @@ struct Group {
     int n_eblk = 0;
     // device
     void *s = nullptr, *sp = nullptr, *spec = nullptr, *dhat = nullptr, *twx = nullptr, *twy = nullptr;
+    void *twxs = nullptr, *twys = nullptr;
     void *prm = nullptr, *hout = nullptr;
     InterpEntry* interp = nullptr;
     double* epart = nullptr;
@@ -173,6 +174,8 @@ template <typename T> GroupArgs<T> group_args(const ss_ctx* c, const Group& g) {
     a.dhat = (const T*)g.dhat;
     a.twx = (const cplx<T>*)g.twx;
     a.twy = (const cplx<T>*)g.twy;
+    a.twxs = (const cplx<T>*)g.twxs;
+    a.twys = (const cplx<T>*)g.twys;
     a.planx = g.planx;
     a.plany = g.plany;
     a.prm = (const ImgParam<T>*)g.prm;
@@ -263,6 +266,8 @@ template <typename T> ss_status setup_group(ss_ctx* c, Group& g) {
     TRY(dalloc(c, (void**)&g.epart, (size_t)g.n_img * 4 * g.n_eblk * sizeof(double)));
     TRY(dalloc(c, &g.twx, g.Px * sizeof(C)));
     TRY(dalloc(c, &g.twy, g.Py * sizeof(C)));
+    TRY(dalloc(c, &g.twxs, g.Px * sizeof(C)));
+    TRY(dalloc(c, &g.twys, g.Py * sizeof(C)));
     if (g.dipole) {
         TRY(dalloc(c, &g.spec, (size_t)g.n_pairs * g.Px * 3 * g.nz * g.ny * sizeof(C)));
         TRY(dalloc(c, &g.dhat, (size_t)(g.Px / 2 + 1) * (g.Py / 2 + 1) * g.nz * 6 * sizeof(T)));
@@ -289,6 +294,11 @@ template <typename T> ss_status setup_group(ss_ctx* c, Group& g) {
     for (int i = 0; i < g.Py; ++i) ty[i] = C{T(twy[i].x), T(twy[i].y)};
     CUDA_TRY(c, cudaMemcpyAsync(g.twx, tx.data(), g.Px * sizeof(C), cudaMemcpyHostToDevice, c->cs));
     CUDA_TRY(c, cudaMemcpyAsync(g.twy, ty.data(), g.Py * sizeof(C), cudaMemcpyHostToDevice, c->cs));
+    std::vector<C> sx(g.Px, C{T(0), T(0)}), sy(g.Py, C{T(0), T(0)});
+    fft_stage_twiddles(g.planx, twx.data(), sx.data());
+    fft_stage_twiddles(g.plany, twy.data(), sy.data());
+    CUDA_TRY(c, cudaMemcpyAsync(g.twxs, sx.data(), g.Px * sizeof(C), cudaMemcpyHostToDevice, c->cs));
+    CUDA_TRY(c, cudaMemcpyAsync(g.twys, sy.data(), g.Py * sizeof(C), cudaMemcpyHostToDevice, c->cs));
     // arc-length bookkeeping
     ArcArgs& a = g.arc;
     a.n_str = nstr;

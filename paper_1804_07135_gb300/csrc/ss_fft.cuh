@@ -212,11 +212,36 @@ __host__ __device__ constexpr int cx_radix(int P, int s) {
 }
 __host__ __device__ constexpr int cx_ns(int P, int s) { return s == 0 ? 1 : cx_ns(P, s - 1) * cx_radix(P, s - 1); }
 
+// Offset of stage s's twiddles in the per-stage table: stage s (with ns > 1) holds W_P^{jm*r*tw} at
+// [jm][r-1], jm < ns, 1 <= r < R, so a butterfly reads its R-1 twiddles at base + constants.  The
+// table has P - radix(0) entries in all (fewer than P).
+__host__ __device__ constexpr int cx_tw_off(int P, int s) {
+    return s == 0 ? 0 : cx_tw_off(P, s - 1) + (cx_ns(P, s - 1) > 1 ? cx_ns(P, s - 1) * (cx_radix(P, s - 1) - 1) : 0);
+}
+// True when fft_pad(j + r*Q) - fft_pad(j) does not depend on j (loads at base + constants).
+__host__ __device__ constexpr bool cx_load_linear(int Q, int R) {
+    for (int j = 0; j < Q; ++j)
+        for (int r = 0; r < R; ++r)
+            if (fft_pad(j + r * Q) - fft_pad(j) != fft_pad(r * Q)) return false;
+    return true;
+}
+// True when fft_pad(e0 + r*NS) - fft_pad(e0) does not depend on the butterfly (stores at base + constants).
+__host__ __device__ constexpr bool cx_store_linear(int P, int R, int NS) {
+    for (int j = 0; j < P / R; ++j) {
+        const int jm = j % NS, e0 = (j - jm) * R + jm;
+        for (int r = 0; r < R; ++r)
+            if (fft_pad(e0 + r * NS) - fft_pad(e0) != fft_pad(r * NS)) return false;
+    }
+    return true;
+}
+
 template <int P, int S, int R = cx_radix(P, S), int NS = cx_ns(P, S), typename C>
-__device__ __forceinline__ void fft_stage_c(C* buf, const C* tw, int LS, int L, int tid, int nthr) {
+__device__ __forceinline__ void fft_stage_c(C* buf, const C* tws, int LS, int L, int tid, int nthr) {
     constexpr int B = StageCap<R>::B;
     constexpr int Q = P / R;
-    constexpr int TWS = P / (NS * R);
+    constexpr bool LIN_LD = cx_load_linear(Q, R);
+    constexpr bool LIN_ST = cx_store_linear(P, R, NS);
+    constexpr int TWO = cx_tw_off(P, S);
     C v[B][R];
     int dline[B], de[B];
 #pragma unroll
@@ -228,10 +253,12 @@ __device__ __forceinline__ void fft_stage_c(C* buf, const C* tw, int LS, int L, 
         if (line < L) {
             const int jm = j % NS;
             const C* src = buf + line * LS;
+            const C* s0 = src + fft_pad(j);
+            const C* w = tws + TWO + jm * (R - 1);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                C x = src[fft_pad(j + r * Q)];
-                if (r > 0) x = cmul(x, tw[jm * r * TWS]);
+                C x = LIN_LD ? s0[fft_pad(r * Q)] : src[fft_pad(j + r * Q)];
+                if (NS > 1 && r > 0) x = cmul(x, w[r - 1]);
                 v[i][r] = x;
             }
             Dft<R, C>::run(v[i]);
@@ -243,29 +270,50 @@ __device__ __forceinline__ void fft_stage_c(C* buf, const C* tw, int LS, int L, 
 #pragma unroll
     for (int i = 0; i < B; ++i) {
         if (dline[i] >= 0) {
+            C* d0 = buf + dline[i] + fft_pad(de[i]);
 #pragma unroll
-            for (int r = 0; r < R; ++r) buf[dline[i] + fft_pad(de[i] + r * NS)] = v[i][r];
+            for (int r = 0; r < R; ++r) {
+                if (LIN_ST)
+                    d0[fft_pad(r * NS)] = v[i][r];
+                else
+                    buf[dline[i] + fft_pad(de[i] + r * NS)] = v[i][r];
+            }
         }
     }
     __syncthreads();
 }
 
 template <int P, int S, typename C>
-__device__ __forceinline__ void fft_stages_c(C* buf, const C* tw, int LS, int L, int tid, int nthr) {
+__device__ __forceinline__ void fft_stages_c(C* buf, const C* tws, int LS, int L, int tid, int nthr) {
     if constexpr (S < cx_nstages(P)) {
-        fft_stage_c<P, S>(buf, tw, LS, L, tid, nthr);
-        fft_stages_c<P, S + 1>(buf, tw, LS, L, tid, nthr);
+        fft_stage_c<P, S>(buf, tws, LS, L, tid, nthr);
+        fft_stages_c<P, S + 1>(buf, tws, LS, L, tid, nthr);
     }
 }
 
-// Forward FFT of L lines of compile-time length P; same contract as fft_lines.
+// Forward FFT of L lines of compile-time length P; tws is the per-stage twiddle table.
 template <int P, typename C>
-__device__ __forceinline__ void fft_lines_c(C* buf, const C* tw, int LS, int L, int tid, int nthr) {
+__device__ __forceinline__ void fft_lines_c(C* buf, const C* tws, int LS, int L, int tid, int nthr) {
     const int lpp = max(1, fft_lines_per_pass(nthr, P));
-    for (int l0 = 0; l0 < L; l0 += lpp) fft_stages_c<P, 0>(buf + l0 * LS, tw, LS, min(lpp, L - l0), tid, nthr);
+    for (int l0 = 0; l0 < L; l0 += lpp) fft_stages_c<P, 0>(buf + l0 * LS, tws, LS, min(lpp, L - l0), tid, nthr);
 }
 
-// Dispatch: compile-time plan when PC > 0, the runtime plan otherwise.
+// Host: per-stage twiddle table (see cx_tw_off) of a plan from its flat table w[k] = W_P^k.
+template <typename C, typename W> inline void fft_stage_twiddles(const FftPlan& p, const W* w, C* out) {
+    int o = 0;
+    for (int s = 0; s < p.nstages; ++s) {
+        const int R = p.radix[s], Ns = p.ns[s];
+        if (Ns == 1) continue;
+        for (int jm = 0; jm < Ns; ++jm)
+            for (int r = 1; r < R; ++r) {
+                const W x = w[(jm * r * p.tw[s]) % p.P];
+                out[o++] = C{decltype(C{}.x)(x.x), decltype(C{}.x)(x.y)};
+            }
+    }
+}
+
+// Dispatch: compile-time plan when PC > 0 (tw = per-stage table), the runtime plan otherwise (tw =
+// flat table).
 template <int PC, typename C>
 __device__ __forceinline__ void fft_lines_any(C* buf, const C* tw, const FftPlan& plan, int LS, int L, int tid, int nthr) {
     if constexpr (PC > 0)

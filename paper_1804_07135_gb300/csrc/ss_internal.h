@@ -42,10 +42,10 @@ struct FftPlan {
 
 // Shared-memory position of element i of a line: one padding slot per 16 elements, which spreads the
 // strided stores of the early FFT stages over all banks.
-__host__ __device__ inline int fft_pad(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int fft_pad(int i) { return i + (i >> 4); }
 // Line stride (in elements) for lines of length P: padded length, made odd so that a column read
 // across consecutive lines touches distinct banks.
-__host__ __device__ inline int fft_line_stride(int P) { return (P + (P >> 4) + 1) | 1; }
+__host__ __device__ constexpr int fft_line_stride(int P) { return (P + (P >> 4) + 1) | 1; }
 
 // Reparametrisation source of one image: normalise((1 - t) sp[src0] + t sp[src1]), or an exact copy
 // of sp[src0] when copy != 0.  Image indices are local to the size group.
@@ -71,8 +71,10 @@ template <typename T> struct GroupArgs {
     T* sp;
     cplx<T>* spec;
     const T* dhat;
-    const cplx<T>* twx;
+    const cplx<T>* twx;   // flat twiddle tables W_P^k (runtime plans)
     const cplx<T>* twy;
+    const cplx<T>* twxs;  // per-stage twiddle tables (compile-time plans), P entries each
+    const cplx<T>* twys;
     FftPlan planx, plany;
     const ImgParam<T>* prm;
     const InterpEntry* interp;

@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xfwd_kernel(GroupAr
     const int nx = g.nx, N = g.N;
     const int ia = 2 * p;
     if (DO_FFT)
-        for (int i = tid; i < g.Px; i += nthr) tw[i] = g.twx[i];
+        for (int i = tid; i < g.Px; i += nthr) tw[i] = PX > 0 ? g.twxs[i] : g.twx[i];
     for (int it = tid; it < rows * nx; it += nthr) {
         const int yy = it / nx, x = it - yy * nx;
         const int site = (z * g.ny + y0 + yy) * nx + x;
@@ -328,7 +328,7 @@ __global__ void __launch_bounds__(kMaxThreadsYz, kMinBlocksYz) yz_kernel(GroupAr
         dk = 1;
         dq = hy + 1;
     }
-    for (int i = tid; i < Py; i += nthr) tw[i] = g.twy[i];
+    for (int i = tid; i < Py; i += nthr) tw[i] = PY > 0 ? g.twys[i] : g.twy[i];
     for (int it = tid; it < L * Py; it += nthr) {
         const int line = it / Py, y = it - line * Py;  // Py is a constant in the specialised variants
         A[line * g.lsy + fft_pad(y)] = (y < ny) ? blk[line * ny + y] : C{T(0), T(0)};
@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xinv_kernel(GroupAr
     const int nx = g.nx, ny = g.ny, nz = g.nz, N = g.N;
     const int ia = 2 * p;
     if (DO_FFT) {
-        for (int i = tid; i < g.Px; i += nthr) tw[i] = g.twx[i];
+        for (int i = tid; i < g.Px; i += nthr) tw[i] = PX > 0 ? g.twxs[i] : g.twx[i];
         const int Px = PX > 0 ? PX : g.Px;
         const C* inp = g.spec + (size_t)p * Px * 3 * nz * ny;
         for (int kc = tid; kc < Px * 3; kc += nthr) {

@@ -108,6 +108,21 @@ __global__ void na_tensor_fill(double2* data, int nx, int ny, int nz, int Px, in
     }
 }
 
+// Per-stage twiddle table of a plan from the flat FP64 table (layout of fft_stage_twiddles).
+__global__ void na_stage_twiddles(FftPlan p, const double2* tw64, float2* out) {
+    int o = 0;
+    for (int s = 0; s < p.nstages; ++s) {
+        const int R = p.radix[s], Ns = p.ns[s];
+        if (Ns == 1) continue;
+        for (int e = threadIdx.x; e < Ns * (R - 1); e += blockDim.x) {
+            const int jm = e / (R - 1), r = 1 + e % (R - 1);
+            const double2 x = tw64[(jm * r * p.tw[s]) % p.P];
+            out[o + e] = make_float2((float)x.x, (float)x.y);
+        }
+        o += Ns * (R - 1);
+    }
+}
+
 __global__ void na_params(ImgParam<float>* prm, int n, float J, float D, float K, float w) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         ImgParam<float> p;
@@ -158,6 +173,7 @@ extern "C" ss_status ss_field_noalloc(int nx, int ny, int nz, double J, double D
     const size_t o_err = take(sizeof(int));
     const size_t o_tw64x = take(Px * sizeof(double2)), o_tw64y = take(Py * sizeof(double2));
     const size_t o_twx = take(Px * sizeof(float2)), o_twy = take(Py * sizeof(float2));
+    const size_t o_twxs = take(Px * sizeof(float2)), o_twys = take(Py * sizeof(float2));
     const size_t o_dhat = take(dip ? (size_t)(Px / 2 + 1) * (Py / 2 + 1) * nz * 6 * sizeof(float) : 0);
     const size_t o_prm = take(n_images * sizeof(ImgParam<float>));
     const size_t o_interp = take(n_images * sizeof(InterpEntry));
@@ -185,6 +201,10 @@ extern "C" ss_status ss_field_noalloc(int nx, int ny, int nz, double J, double D
     na_twiddles<<<(Py + 127) / 128, 128, 0, st>>>(tw64y, twy, Py);
     float* dhat = reinterpret_cast<float*>(base + o_dhat);
     const FftPlan px = plan_of(Px), py = plan_of(Py);
+    float2* twxs = reinterpret_cast<float2*>(base + o_twxs);
+    float2* twys = reinterpret_cast<float2*>(base + o_twys);
+    na_stage_twiddles<<<1, 256, 0, st>>>(px, tw64x, twxs);
+    na_stage_twiddles<<<1, 256, 0, st>>>(py, tw64y, twys);
     if (dip) {
         // the tensor spectrum is rebuilt on every call: the build area is shared with the spins below
         double2* tens = reinterpret_cast<double2*>(base + o_work);
@@ -218,6 +238,8 @@ extern "C" ss_status ss_field_noalloc(int nx, int ny, int nz, double J, double D
     g.dhat = dhat;
     g.twx = twx;
     g.twy = twy;
+    g.twxs = twxs;
+    g.twys = twys;
     g.planx = px;
     g.plany = py;
     g.prm = prm;
