@@ -81,6 +81,43 @@ template <typename C> struct Dft<8, C> {
     }
 };
 
+// Size-R DFTs whose inputs R/2..R-1 are zero (the zero-padded half of a forward transform).
+template <int R, typename C> struct DftHalfIn;
+template <typename C> struct DftHalfIn<2, C> {
+    static __device__ __forceinline__ void run(C* v) { v[1] = v[0]; }
+};
+template <typename C> struct DftHalfIn<4, C> {
+    static __device__ __forceinline__ void run(C* v) {
+        const C a = v[0], b = v[1], mb = cmi(v[1]);
+        v[0] = cadd(a, b);
+        v[1] = cadd(a, mb);
+        v[2] = csub(a, b);
+        v[3] = csub(a, mb);
+    }
+};
+template <typename C> struct DftHalfIn<8, C> {
+    static __device__ __forceinline__ void run(C* v) {
+        using R = decltype(v[0].x);
+        const R q = R(0.7071067811865475244008443621048490);
+        // even part DFT4(x0, x2, 0, 0), odd part DFT4(x1, x3, 0, 0)
+        const C x0 = v[0], x1 = v[1], x2 = v[2], x3 = v[3];
+        const C m2 = cmi(x2), m3 = cmi(x3);
+        const C e0 = cadd(x0, x2), e1 = cadd(x0, m2), e2 = csub(x0, x2), e3 = csub(x0, m2);
+        const C o0 = cadd(x1, x3), o1 = cadd(x1, m3), o2 = csub(x1, x3), o3 = csub(x1, m3);
+        const C t1 = C{q * (o1.x + o1.y), q * (o1.y - o1.x)};
+        const C t2 = cmi(o2);
+        const C t3 = C{q * (o3.y - o3.x), -q * (o3.x + o3.y)};
+        v[0] = cadd(e0, o0);
+        v[4] = csub(e0, o0);
+        v[1] = cadd(e1, t1);
+        v[5] = csub(e1, t1);
+        v[2] = cadd(e2, t2);
+        v[6] = csub(e2, t2);
+        v[3] = cadd(e3, t3);
+        v[7] = csub(e3, t3);
+    }
+};
+
 // Host-side plan: radices 8, 4, 2 first (largest first), then 3s.
 inline FftPlan fft_make_plan(int P) {
     FftPlan p{};
@@ -235,9 +272,13 @@ __host__ __device__ constexpr bool cx_store_linear(int P, int R, int NS) {
     return true;
 }
 
-template <int P, int S, int R = cx_radix(P, S), int NS = cx_ns(P, S), typename C>
+// PIN: inputs r >= R/2 of this stage are zero (first stage of a zero-padded forward transform).
+// POUT: only outputs r < R/2 are stored (last stage of a transform read below P/2).
+template <int P, int S, bool PIN, bool POUT, int R = cx_radix(P, S), int NS = cx_ns(P, S), typename C>
 __device__ __forceinline__ void fft_stage_c(C* buf, const C* tws, int LS, int L, int tid, int nthr) {
     constexpr int B = StageCap<R>::B;
+    constexpr int RIN = PIN ? R / 2 : R;    // inputs read
+    constexpr int ROUT = POUT ? R / 2 : R;  // outputs stored
     constexpr int Q = P / R;
     constexpr bool LIN_LD = cx_load_linear(Q, R);
     constexpr bool LIN_ST = cx_store_linear(P, R, NS);
@@ -256,12 +297,15 @@ __device__ __forceinline__ void fft_stage_c(C* buf, const C* tws, int LS, int L,
             const C* s0 = src + fft_pad(j);
             const C* w = tws + TWO + jm * (R - 1);
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
+            for (int r = 0; r < RIN; ++r) {
                 C x = LIN_LD ? s0[fft_pad(r * Q)] : src[fft_pad(j + r * Q)];
                 if (NS > 1 && r > 0) x = cmul(x, w[r - 1]);
                 v[i][r] = x;
             }
-            Dft<R, C>::run(v[i]);
+            if constexpr (PIN)
+                DftHalfIn<R, C>::run(v[i]);
+            else
+                Dft<R, C>::run(v[i]);
             dline[i] = line * LS;
             de[i] = (j - jm) * R + jm;
         }
@@ -272,7 +316,7 @@ __device__ __forceinline__ void fft_stage_c(C* buf, const C* tws, int LS, int L,
         if (dline[i] >= 0) {
             C* d0 = buf + dline[i] + fft_pad(de[i]);
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
+            for (int r = 0; r < ROUT; ++r) {
                 if (LIN_ST)
                     d0[fft_pad(r * NS)] = v[i][r];
                 else
@@ -283,19 +327,25 @@ __device__ __forceinline__ void fft_stage_c(C* buf, const C* tws, int LS, int L,
     __syncthreads();
 }
 
-template <int P, int S, typename C>
+template <int P, int S, bool ZERO_HI_IN, bool HI_OUT_UNUSED, typename C>
 __device__ __forceinline__ void fft_stages_c(C* buf, const C* tws, int LS, int L, int tid, int nthr) {
     if constexpr (S < cx_nstages(P)) {
-        fft_stage_c<P, S>(buf, tws, LS, L, tid, nthr);
-        fft_stages_c<P, S + 1>(buf, tws, LS, L, tid, nthr);
+        constexpr int R = cx_radix(P, S);
+        constexpr bool pin = ZERO_HI_IN && S == 0 && R != 3;
+        constexpr bool pout = HI_OUT_UNUSED && S == cx_nstages(P) - 1 && R != 3;
+        fft_stage_c<P, S, pin, pout>(buf, tws, LS, L, tid, nthr);
+        fft_stages_c<P, S + 1, ZERO_HI_IN, HI_OUT_UNUSED>(buf, tws, LS, L, tid, nthr);
     }
 }
 
 // Forward FFT of L lines of compile-time length P; tws is the per-stage twiddle table.
-template <int P, typename C>
+// ZERO_HI_IN: elements P/2..P-1 of every line are zero on entry (their loads are skipped).
+// HI_OUT_UNUSED: only elements 0..P/2-1 of the result are read afterwards (the rest is left stale).
+template <int P, bool ZERO_HI_IN = false, bool HI_OUT_UNUSED = false, typename C>
 __device__ __forceinline__ void fft_lines_c(C* buf, const C* tws, int LS, int L, int tid, int nthr) {
     const int lpp = max(1, fft_lines_per_pass(nthr, P));
-    for (int l0 = 0; l0 < L; l0 += lpp) fft_stages_c<P, 0>(buf + l0 * LS, tws, LS, min(lpp, L - l0), tid, nthr);
+    for (int l0 = 0; l0 < L; l0 += lpp)
+        fft_stages_c<P, 0, ZERO_HI_IN, HI_OUT_UNUSED>(buf + l0 * LS, tws, LS, min(lpp, L - l0), tid, nthr);
 }
 
 // Host: per-stage twiddle table (see cx_tw_off) of a plan from its flat table w[k] = W_P^k.
@@ -314,10 +364,12 @@ template <typename C, typename W> inline void fft_stage_twiddles(const FftPlan& 
 
 // Dispatch: compile-time plan when PC > 0 (tw = per-stage table), the runtime plan otherwise (tw =
 // flat table).
-template <int PC, typename C>
+// The pruning flags apply to the compile-time path only; they require the zero padding / the unread
+// outputs to cover at least the upper half of the line (true for padded length 2n when n <= P/2).
+template <int PC, bool ZERO_HI_IN = false, bool HI_OUT_UNUSED = false, typename C>
 __device__ __forceinline__ void fft_lines_any(C* buf, const C* tw, const FftPlan& plan, int LS, int L, int tid, int nthr) {
     if constexpr (PC > 0)
-        fft_lines_c<PC>(buf, tw, LS, L, tid, nthr);
+        fft_lines_c<PC, ZERO_HI_IN, HI_OUT_UNUSED>(buf, tw, LS, L, tid, nthr);
     else
         fft_lines(buf, tw, plan, LS, L, tid, nthr);
 }

@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xfwd_kernel(GroupAr
         buf[line * g.lsx + fft_pad(x)] = C{T(0), T(0)};
     }
     __syncthreads();
-    fft_lines_any<PX>(buf, tw, g.planx, g.lsx, 3 * rows, tid, nthr);
+    fft_lines_any<PX, true, false>(buf, tw, g.planx, g.lsx, 3 * rows, tid, nthr);
     // transpose out: each thread writes the rows of one (kx, c), contiguous in y
     const int Px = PX > 0 ? PX : g.Px;
     C* outp = g.spec + (size_t)p * Px * 3 * g.nz * g.ny;
@@ -334,12 +334,12 @@ __global__ void __launch_bounds__(kMaxThreadsYz, kMinBlocksYz) yz_kernel(GroupAr
         A[line * g.lsy + fft_pad(y)] = (y < ny) ? blk[line * ny + y] : C{T(0), T(0)};
     }
     __syncthreads();
-    fft_lines_any<PY>(A, tw, g.plany, g.lsy, L, tid, nthr);
+    fft_lines_any<PY, true, false>(A, tw, g.plany, g.lsy, L, tid, nthr);
     if constexpr (NZ > 0)
         zconv_c<NZ>(A, g.lsy, Py, kx, g.Px, dslab, dk, dq, tid, nthr);
     else
         zconv_any(A, g.lsy, Py, nz, kx, g.Px, dslab, dk, dq, tid, nthr);
-    fft_lines_any<PY>(A, tw, g.plany, g.lsy, L, tid, nthr);
+    fft_lines_any<PY, false, true>(A, tw, g.plany, g.lsy, L, tid, nthr);
     for (int it = tid; it < L * ny; it += nthr) {
         const int line = it / ny, y = it - line * ny;
         blk[line * ny + y] = cconj(A[line * g.lsy + fft_pad(y)]);
@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xinv_kernel(GroupAr
             for (int yy = 0; yy < rows; ++yy) b[yy * g.lsx] = cconj(s[yy]);
         }
         __syncthreads();
-        fft_lines_any<PX>(buf, tw, g.planx, g.lsx, 3 * rows, tid, nthr);
+        fft_lines_any<PX, false, true>(buf, tw, g.planx, g.lsx, 3 * rows, tid, nthr);
     }
     constexpr int NV = MODE == 0 ? 2 : 8;
     double acc[NV];
