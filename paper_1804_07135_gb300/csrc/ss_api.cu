@@ -74,7 +74,7 @@ struct Group {
     bool dipole = false;
     FftPlan planx{}, plany{};
     int lsx = 1, lsy = 1;
-    int ty_a = 1, ty_c = 1, thr_a = 128, thr_b = 128, thr_c = 128, thr_arc = 1024;
+    int ty_a = 1, ty_c = 1, thr_a = 128, thr_b = 128, thr_c = 128, thr_arc = 256;
     size_t smem_a = 0, smem_b = 0, smem_c = 0, smem_c_eval = 0;
     int n_eblk = 0;
     // device
@@ -303,7 +303,7 @@ template <typename T> ss_status setup_group(ss_ctx* c, Group& g) {
     ArcArgs& a = g.arc;
     a.n_str = nstr;
     a.maxK = maxK;
-    a.tile_elems = 4096;  // 4 components per thread of a 1024-thread CTA
+    a.tile_elems = 1024;  // 4 components per thread of a 256-thread CTA
     a.n_tiles = (int)((M + a.tile_elems - 1) / a.tile_elems);
     a.kchunk = std::max(1, std::min(8, maxK - 1));
     a.n_kchunks = std::max(1, (maxK - 1 + a.kchunk - 1) / a.kchunk);

@@ -497,7 +497,7 @@ __global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xinv_kernel(GroupAr
 // components (Eq. 11), one partial per (string, k, tile), summed in T per thread and warp, in FP64
 // across warps.
 template <typename T>
-__global__ void __launch_bounds__(1024) arc_kernel(GroupArgs<T> g, ArcArgs a) {
+__global__ void __launch_bounds__(256) arc_kernel(GroupArgs<T> g, ArcArgs a) {
     __shared__ double red[32 * kArcMaxChunk];
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int str = blockIdx.z;
@@ -512,70 +512,115 @@ __global__ void __launch_bounds__(1024) arc_kernel(GroupArgs<T> g, ArcArgs a) {
     T part[kArcMaxChunk];  // the thread's few squared differences per image pair, summed in T first
 #pragma unroll
     for (int i = 0; i < kArcMaxChunk; ++i) part[i] = T(0);
-    for (size_t e = e0 + tid; e < e1; e += nthr) {
-        const T* col = g.sp + (size_t)(img0 + k_lo) * M + e;
-        T prev = col[0];
+    if (sizeof(T) == 4 && (M & 3) == 0 && (e0 & 3) == 0) {
+        // four components per thread and load: 16-byte loads of every image of the chunk up front
+        const float4* base = reinterpret_cast<const float4*>(g.sp + (size_t)(img0 + k_lo) * M);
+        const size_t M4 = M >> 2;
+        for (size_t e4 = (e0 >> 2) + tid; e4 < (e1 + 3) >> 2; e4 += nthr) {
+            float4 v[kArcMaxChunk + 1];
 #pragma unroll
-        for (int i = 0; i < kArcMaxChunk; ++i) {
-            if (i < nd) {
-                const T cur = col[(size_t)(i + 1) * M];
-                const T d = cur - prev;
-                part[i] += d * d;
-                prev = cur;
+            for (int i = 0; i <= kArcMaxChunk; ++i)
+                if (i <= nd) v[i] = base[e4 + (size_t)i * M4];
+#pragma unroll
+            for (int i = 0; i < kArcMaxChunk; ++i) {
+                if (i < nd) {
+                    const float dx = v[i + 1].x - v[i].x, dy = v[i + 1].y - v[i].y;
+                    const float dz = v[i + 1].z - v[i].z, dw = v[i + 1].w - v[i].w;
+                    part[i] += T(dx * dx + dy * dy + dz * dz + dw * dw);
+                }
+            }
+        }
+    } else {
+        for (size_t e = e0 + tid; e < e1; e += nthr) {
+            const T* col = g.sp + (size_t)(img0 + k_lo) * M + e;
+            T prev = col[0];
+#pragma unroll
+            for (int i = 0; i < kArcMaxChunk; ++i) {
+                if (i < nd) {
+                    const T cur = col[(size_t)(i + 1) * M];
+                    const T d = cur - prev;
+                    part[i] += d * d;
+                    prev = cur;
+                }
             }
         }
     }
     block_reduce_t2d<kArcMaxChunk>(part, acc, red);
     if (tid == 0)
         for (int i = 0; i < nd; ++i) a.dpart[((size_t)str * a.maxK + k_lo + i + 1) * a.n_tiles + blockIdx.x] = acc[i];
+    // the energies E_k of the state before the step (Eq. 8), summed over the step kernel's blocks in
+    // FP64 and in block order: images k_lo..k_lo+nd (plus image 0 in chunk 0), one warp per image, by
+    // the CTAs of tile 0 (spread over the chunks, so over several SMs)
+    if (blockIdx.x == 0) {
+        const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
+        const int k_first = k_lo == 0 ? 0 : k_lo + 1, k_last = k_lo + nd;
+        for (int k = k_first + warp; k <= k_last; k += nwarp) {
+            const double* ep = g.epart + (size_t)(img0 + k) * g.n_eblk;
+            double e = 0.0;
+            for (int b = lane; b < g.n_eblk; b += 32) e += ep[b];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
+            if (lane == 0) a.e_last[(size_t)str * a.maxK + k] = e;
+        }
+    }
 }
 
-// reparam: grid (n_str), 1024 threads.  Sums the energy partials (block order) and the distance
-// partials (tile order) of every image in FP64, one warp per image; scans the arc length s_k
-// (Eq. 11); forms alpha*_k = s_k / s_{K-1} (Eq. 12) and, for every interior image k, the largest j
-// with alpha*_j <= k/(K-1) and t; writes the interpolation table the next xfwd applies.
+// reparam: grid (n_str), 1024 threads, one image per thread.  d_k = sqrt(sum over tiles of the
+// squared-distance partials) in FP64 and tile order; s_k by an inclusive block scan (Eq. 11);
+// alpha*_k = s_k / s_{K-1} (Eq. 12); for every interior image k the largest j with
+// alpha*_j <= k/(K-1) and t; writes the interpolation table the next xfwd applies.  GB300 issues
+// FP64 at a low rate, so each FP64 instruction here serves 32 images at once.
 template <typename T>
 __global__ void __launch_bounds__(1024) reparam_kernel(GroupArgs<T> g, ArcArgs a) {
     __shared__ double alpha[kArcMaxK];
+    __shared__ double wsum[32];
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int str = blockIdx.x;
     const int K = a.str_K[str], img0 = a.str_img0[str];
-    const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
-    for (int k = warp; k < K; k += nwarp) {
-        double e = 0.0, d2 = 0.0;
-        const double* ep = g.epart + (size_t)(img0 + k) * g.n_eblk;
-        for (int b = lane; b < g.n_eblk; b += 32) e += ep[b];
-        if (k > 0) {
-            const double* dp = a.dpart + ((size_t)str * a.maxK + k) * a.n_tiles;
-            for (int t = lane; t < a.n_tiles; t += 32) d2 += dp[t];
+    const int lane = tid & 31, warp = tid >> 5, nwarp = (K + 31) >> 5;
+    if (warp >= nwarp) return;  // whole warps beyond the images; no barrier below counts them
+    double d = 0.0;
+    if (tid < K) {
+        double d2 = 0.0;
+        if (tid > 0) {
+            const double* dp = a.dpart + ((size_t)str * a.maxK + tid) * a.n_tiles;
+            for (int t = 0; t < a.n_tiles; ++t) d2 += dp[t];
         }
+        const double e = a.e_last[(size_t)str * a.maxK + tid];
+        if (!isfinite(e) || !isfinite(d2)) atomicOr(g.err, kErrNonFinite);
+        d = sqrt(d2);
+    }
+    // s_k = d_1 + ... + d_k, s_0 = 0 (Eq. 11): inclusive scan, warp shuffles then warp totals
+    double v = d;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            e += __shfl_down_sync(0xffffffffu, e, o);
-            d2 += __shfl_down_sync(0xffffffffu, d2, o);
-        }
-        if (lane == 0) {
-            a.e_last[(size_t)str * a.maxK + k] = e;
-            alpha[k] = sqrt(d2);
-            if (!isfinite(e) || !isfinite(d2)) atomicOr(g.err, kErrNonFinite);
-        }
+    for (int o = 1; o < 32; o <<= 1) {
+        const double u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
     }
-    __syncthreads();
-    if (tid == 0) {
-        double s = 0.0;
-        for (int k = 0; k < K; ++k) {
-            s += alpha[k];
-            alpha[k] = s;  // s_k, with s_0 = 0 (Eq. 11)
+    if (nwarp > 1) {
+        if (lane == 31) wsum[warp] = v;
+        asm volatile("bar.sync 1, %0;" ::"r"(nwarp * 32));
+        if (warp == 0) {
+            double w = lane < nwarp ? wsum[lane] : 0.0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const double u = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += u;
+            }
+            wsum[lane] = w;
         }
+        asm volatile("bar.sync 1, %0;" ::"r"(nwarp * 32));
+        if (warp > 0) v += wsum[warp - 1];
     }
-    __syncthreads();
+    if (tid < K) alpha[tid] = v;
+    asm volatile("bar.sync 1, %0;" ::"r"(nwarp * 32));
     const double sK = alpha[K - 1];
     const bool move = a.reparam && sK > 0.0 && isfinite(sK);
-    __syncthreads();
-    if (move)
-        for (int k = tid; k < K; k += nthr) alpha[k] = alpha[k] / sK;  // alpha*_k (Eq. 12)
-    __syncthreads();
-    for (int k = tid; k < K; k += nthr) {
+    if (move && tid < K) alpha[tid] = v / sK;  // alpha*_k (Eq. 12)
+    asm volatile("bar.sync 1, %0;" ::"r"(nwarp * 32));
+    (void)nthr;
+    if (tid < K) {
+        const int k = tid;
         InterpEntry e;
         e.src0 = img0 + k;
         e.src1 = img0 + k;
