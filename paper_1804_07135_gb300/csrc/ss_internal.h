@@ -4,7 +4,8 @@
 //   s, sp   [image][3][N]            spins before / after the step (SoA planes, x fastest), N = nx*ny*nz
 //   spec    [pair][Px][3][nz][ny]    complex spectra of image pairs after the x transform (y fastest);
 //                                    the y/z kernel overwrites them in place with the field spectra
-//   dhat    [Px/2+1][Py/2+1][nz][6]  one octant of the dipole-tensor spectrum (real coefficients)
+//   dhat    [Px/2+1][nz*6][Py/2+1]   one octant of the dipole-tensor spectrum (real coefficients),
+//                                    [kxo][|dz|*6 + comp][kyo]
 // Two images (2p, 2p+1) share one complex field (real part = image 2p, imaginary part = image 2p+1):
 // the dipole kernel is real in real space, so one complex convolution serves both images.
 #pragma once

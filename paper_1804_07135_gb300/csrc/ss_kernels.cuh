@@ -313,20 +313,14 @@ __global__ void __launch_bounds__(kMaxThreadsYz, kMinBlocksYz) yz_kernel(GroupAr
     const int hy = Py / 2;
     const int kxo = min(kx, g.Px - kx);
     C* blk = g.spec + ((size_t)p * g.Px + kx) * 3 * nz * ny;
-    // this kx's slab of the tensor-spectrum octant, global layout [kyo][|dz|][6]; staged in shared
-    // memory transposed to [|dz|*6 + comp][kyo] so that a warp (consecutive ky) reads consecutive words
+    // this kx's slab of the tensor-spectrum octant, layout [|dz|*6 + comp][kyo] (a warp over
+    // consecutive ky reads consecutive words), staged in shared memory when it fits
     const T* dslab = g.dhat + (size_t)kxo * (hy + 1) * nz * 6;
-    int dk = nz * 6, dq = 1;  // strides of kyo and of (|dz|*6 + comp)
+    const int dk = 1, dq = hy + 1;  // strides of kyo and of (|dz|*6 + comp)
     T* dsm = reinterpret_cast<T*>(A + L * g.lsy);
     if (stage_dhat) {
-        const int n6 = nz * 6;
-        for (int i = tid; i < (hy + 1) * n6; i += nthr) {
-            const int kyo = i / n6, r = i - kyo * n6;
-            dsm[r * (hy + 1) + kyo] = dslab[i];
-        }
+        for (int i = tid; i < (hy + 1) * nz * 6; i += nthr) dsm[i] = dslab[i];
         dslab = dsm;
-        dk = 1;
-        dq = hy + 1;
     }
     for (int i = tid; i < Py; i += nthr) tw[i] = PY > 0 ? g.twys[i] : g.twy[i];
     for (int it = tid; it < L * Py; it += nthr) {
@@ -739,18 +733,18 @@ __global__ void __launch_bounds__(256) fft_strided_f64_kernel(double2* data, con
 
 #endif
 
-// spec [6][nz][Py][Px] complex (component-major) -> dhat [Px/2+1][Py/2+1][nz][6], scaled.
+// spec [6][nz][Py][Px] complex (component-major) -> dhat [Px/2+1][|dz|*6 + comp][Py/2+1], scaled:
+// for one kx the slab is contiguous and a warp over consecutive ky reads consecutive words.
 template <typename T>
 __global__ void extract_octant_kernel(const double2* spec, T* dhat, int Px, int Py, int nz, double scale) {
     const int hx = Px / 2 + 1, hy = Py / 2 + 1;
     const size_t total = (size_t)hx * hy * nz * 6;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const int c = i % 6;
-        size_t r = i / 6;
-        const int dz = r % nz;
-        r /= nz;
-        const int ky = r % hy;
-        const int kx = r / hy;
+        const int ky = i % hy;
+        size_t r = i / hy;
+        const int q = r % (nz * 6);
+        const int kx = r / (nz * 6);
+        const int dz = q / 6, c = q % 6;
         const double2 v = spec[(((size_t)c * nz + dz) * Py + ky) * Px + kx];
         dhat[i] = T(scale * (c >= 4 ? v.y : v.x));
     }
