@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -188,6 +189,17 @@ template <typename T> GroupArgs<T> group_args(const ss_ctx* c, const Group& g) {
     return a;
 }
 
+// Rows per CTA of the x-forward (ty_a) and x-inverse (ty_c) kernels and the shared memory they need.
+void set_rows(const ss_ctx* c, Group& g, int ty_a, int ty_c) {
+    const size_t cs = 2 * real_size(c);
+    g.ty_a = ty_a;
+    g.ty_c = ty_c;
+    g.smem_a = (size_t)(g.Px + 3 * g.ty_a * g.lsx) * cs;
+    g.smem_c = (size_t)(g.Px + 3 * g.ty_c * g.lsx) * cs + 32 * 8 * sizeof(double);
+    g.smem_c_eval = g.smem_c;
+    g.n_eblk = g.nz * ((g.ny + g.ty_c - 1) / g.ty_c);
+}
+
 // Launch shapes of one size group (shared memory, rows per CTA, block sizes).
 void configure_group(const ss_ctx* c, Group& g) {
     const size_t cs = 2 * real_size(c);  // complex element
@@ -204,17 +216,13 @@ void configure_group(const ss_ctx* c, Group& g) {
             break;
         }
     }
-    g.ty_a = g.ty_c = ty;
-    g.smem_a = (size_t)(g.Px + 3 * g.ty_a * g.lsx) * cs;
-    g.smem_c = (size_t)(g.Px + 3 * g.ty_c * g.lsx) * cs + 32 * 8 * sizeof(double);
-    g.smem_c_eval = g.smem_c;
+    set_rows(c, g, ty, ty);
     // y/z kernel: all 3*nz lines of one (pair, kx) in shared memory, plus the kx slab of the tensor
     // spectrum when it is small enough to stage
     g.thr_b = kMaxThreadsYz;
     g.smem_b = (size_t)(g.Py + 3 * g.nz * g.lsy) * cs;
     const size_t slab = (size_t)(g.Py / 2 + 1) * g.nz * 6 * real_size(c);
     if (slab <= 24 * 1024) g.smem_b += slab;
-    g.n_eblk = g.nz * ((g.ny + g.ty_c - 1) / g.ty_c);
 }
 
 template <typename T> ss_status build_tensor_spectrum(ss_ctx* c, Group& g) {
@@ -263,7 +271,7 @@ template <typename T> ss_status setup_group(ss_ctx* c, Group& g) {
     TRY(dalloc(c, &g.sp, g.n_img * M * sizeof(T)));
     TRY(dalloc(c, (void**)&g.interp, g.n_img * sizeof(InterpEntry)));
     TRY(dalloc(c, &g.prm, g.n_img * sizeof(ImgParam<T>)));
-    TRY(dalloc(c, (void**)&g.epart, (size_t)g.n_img * 4 * g.n_eblk * sizeof(double)));
+    TRY(dalloc(c, (void**)&g.epart, (size_t)g.n_img * 4 * g.nz * g.ny * sizeof(double)));  // any rows per CTA
     TRY(dalloc(c, &g.twx, g.Px * sizeof(C)));
     TRY(dalloc(c, &g.twy, g.Py * sizeof(C)));
     TRY(dalloc(c, &g.twxs, g.Px * sizeof(C)));
@@ -327,6 +335,74 @@ template <typename T> ss_status setup_group(ss_ctx* c, Group& g) {
     launch_interp_identity(g.interp, 0, g.n_img, c->cs);
     CUDA_TRY(c, cudaGetLastError());
     if (g.dipole) TRY(build_tensor_spectrum<T>(c, g));
+    return SS_OK;
+}
+
+// Autotuner: rows per CTA of the x kernels, timed with CUDA events on the context's stream (the
+// kernels are data-independent; the buffers hold zeros and are cleared again afterwards).  Choices
+// are cached per (lattice, precision, device) for the life of the process.
+struct TuneKey {
+    int nx, ny, nz, prec, dev, dipole;
+    bool operator==(const TuneKey& o) const {
+        return nx == o.nx && ny == o.ny && nz == o.nz && prec == o.prec && dev == o.dev && dipole == o.dipole;
+    }
+};
+std::vector<std::pair<TuneKey, std::pair<int, int>>> g_tuned;
+std::mutex g_tune_mu;
+
+template <typename T> ss_status tune_group(ss_ctx* c, Group& g) {
+    const TuneKey key{g.nx, g.ny, g.nz, c->opts.precision, c->device, g.dipole ? 1 : 0};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        for (auto& e : g_tuned)
+            if (e.first == key) {
+                set_rows(c, g, e.second.first, e.second.second);
+                return SS_OK;
+            }
+    }
+    const size_t cs = 2 * real_size(c);
+    std::vector<int> cands;
+    for (int ty : {1, 2, 4, 8})
+        if (ty <= g.ny && (size_t)(g.Px + 3 * ty * g.lsx) * cs + 4096 <= 96 * 1024) cands.push_back(ty);
+    if (cands.size() <= 1) return SS_OK;
+    cudaEvent_t e0, e1;
+    CUDA_TRY(c, cudaEventCreate(&e0));
+    CUDA_TRY(c, cudaEventCreate(&e1));
+    const int reps = 5;
+    float best_a = 1e30f, best_c = 1e30f;
+    int ty_a = g.ty_a, ty_c = g.ty_c;
+    const T dt = T(c->opts.dt);
+    for (int ty : cands) {
+        set_rows(c, g, ty, ty);
+        GroupArgs<T> a = group_args<T>(c, g);
+        for (int which = 0; which < 2; ++which) {
+            auto run = [&]() {
+                if (which == 0)
+                    launch_xfwd<T>(a, g.dipole, g.thr_a, g.smem_a, c->cs);
+                else
+                    launch_xinv_step<T>(a, g.dipole, dt, g.thr_c, g.smem_c, c->cs);
+            };
+            run();
+            CUDA_TRY(c, cudaEventRecord(e0, c->cs));
+            for (int r = 0; r < reps; ++r) run();
+            CUDA_TRY(c, cudaEventRecord(e1, c->cs));
+            CUDA_TRY(c, cudaEventSynchronize(e1));
+            CUDA_TRY(c, cudaGetLastError());
+            float ms = 0.f;
+            CUDA_TRY(c, cudaEventElapsedTime(&ms, e0, e1));
+            if (which == 0 && ms < best_a) best_a = ms, ty_a = ty;
+            if (which == 1 && ms < best_c) best_c = ms, ty_c = ty;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    set_rows(c, g, ty_a, ty_c);
+    const size_t M = (size_t)3 * g.N * g.n_img * real_size(c);
+    CUDA_TRY(c, cudaMemsetAsync(g.s, 0, M, c->cs));
+    CUDA_TRY(c, cudaMemsetAsync(g.sp, 0, M, c->cs));
+    CUDA_TRY(c, cudaStreamSynchronize(c->cs));
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tuned.push_back({key, {ty_a, ty_c}});
     return SS_OK;
 }
 
@@ -585,6 +661,8 @@ ss_status ss_create_batch(int n_strings, const ss_string_desc* descs, const ss_o
     }
     for (Group& g : c->groups) {
         ss_status st = use_fp64(c) ? setup_group<double>(c, g) : setup_group<float>(c, g);
+        if (st != SS_OK) return bail(st);
+        st = use_fp64(c) ? tune_group<double>(c, g) : tune_group<float>(c, g);
         if (st != SS_OK) return bail(st);
     }
     if (cudaStreamSynchronize(c->cs) != cudaSuccess) return bail(fail(c, SS_ERR_CUDA, "setup failed"));

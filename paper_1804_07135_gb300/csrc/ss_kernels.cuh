@@ -381,6 +381,9 @@ __global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xinv_kernel(GroupAr
 #pragma unroll
     for (int k = 0; k < NV; ++k) acc[k] = 0.0;
     T eacc[2] = {T(0), T(0)};  // step mode: the thread's few per-site terms, summed in T before FP64
+    // two sites per thread per pass; restrict-qualified spin planes let the loads of both be issued
+    // before either is stored
+#pragma unroll 2
     for (int it = tid; it < 2 * rows * nx; it += nthr) {
         const int h = it / (rows * nx);
         const int rem = it - h * rows * nx;
@@ -390,7 +393,7 @@ __global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xinv_kernel(GroupAr
         const int y = y0 + yy;
         const int site = (z * ny + y) * nx + x;
         const ImgParam<T> pr = g.prm[im];
-        const T* sb = g.s + (size_t)im * 3 * N;
+        const T* __restrict__ sb = g.s + (size_t)im * 3 * N;
         T s0[3], xp[3], xm[3], yp[3], ym[3], zp[3], zm[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -424,7 +427,7 @@ __global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xinv_kernel(GroupAr
 #pragma unroll
             for (int c = 0; c < 3; ++c) u[c] = s0[c] + dt * (hf[c] - sh * s0[c]);
             const T r = rsqrt_t<T>(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-            T* o = g.sp + (size_t)im * 3 * N + site;
+            T* __restrict__ o = g.sp + (size_t)im * 3 * N + site;
             o[0] = u[0] * r;
             o[N] = u[1] * r;
             o[2 * N] = u[2] * r;
