@@ -15,6 +15,7 @@
 
 #include <algorithm>
 #include <type_traits>
+#include <utility>
 
 #include "ss_fft.cuh"
 
@@ -73,6 +74,13 @@ __device__ __forceinline__ void block_reduce_t2d(T (&v)[NV], double (&out)[NV], 
     }
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream serialisation may start
+// while its predecessor finishes; griddep_wait() blocks until the predecessor grid has completed and
+// its writes are visible (a no-op when launched normally).  Nothing before the wait may read the
+// predecessor's output or write global memory.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
 // ------------------------------------------------------------------------------------------------
 // xfwd: grid (ceil(ny/ty_a), nz, n_pairs).  Each CTA takes rows [y0, y0+rows) of layer z for the two
 // images of pair p: s[img] = normalise((1-t) sp[src0] + t sp[src1]) (or a copy), written back to s,
@@ -91,6 +99,8 @@ __global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xfwd_kernel(GroupAr
     const int ia = 2 * p;
     if (DO_FFT)
         for (int i = tid; i < g.Px; i += nthr) tw[i] = PX > 0 ? g.twxs[i] : g.twx[i];
+    griddep_wait();
+    griddep_launch_dependents();
     for (int it = tid; it < rows * nx; it += nthr) {
         const int yy = it / nx, x = it - yy * nx;
         const int site = (z * g.ny + y0 + yy) * nx + x;
@@ -323,6 +333,8 @@ __global__ void __launch_bounds__(kMaxThreadsYz, kMinBlocksYz) yz_kernel(GroupAr
         dslab = dsm;
     }
     for (int i = tid; i < Py; i += nthr) tw[i] = PY > 0 ? g.twys[i] : g.twy[i];
+    griddep_wait();
+    griddep_launch_dependents();
     for (int it = tid; it < L * Py; it += nthr) {
         const int line = it / Py, y = it - line * Py;  // Py is a constant in the specialised variants
         A[line * g.lsy + fft_pad(y)] = (y < ny) ? blk[line * ny + y] : C{T(0), T(0)};
@@ -363,8 +375,11 @@ __global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xinv_kernel(GroupAr
     const int rows = min(g.ty_c, g.ny - y0);
     const int nx = g.nx, ny = g.ny, nz = g.nz, N = g.N;
     const int ia = 2 * p;
-    if (DO_FFT) {
+    if (DO_FFT)
         for (int i = tid; i < g.Px; i += nthr) tw[i] = PX > 0 ? g.twxs[i] : g.twx[i];
+    griddep_wait();
+    griddep_launch_dependents();
+    if (DO_FFT) {
         const int Px = PX > 0 ? PX : g.Px;
         const C* inp = g.spec + (size_t)p * Px * 3 * nz * ny;
         for (int kc = tid; kc < Px * 3; kc += nthr) {
@@ -501,6 +516,8 @@ __global__ void __launch_bounds__(256) arc_kernel(GroupArgs<T> g, ArcArgs a) {
     const int K = a.str_K[str], img0 = a.str_img0[str];
     const int k_lo = blockIdx.y * a.kchunk;
     const int nd = max(0, min(a.kchunk, K - 1 - k_lo));  // differences (k_lo+i, k_lo+i+1), i < nd
+    griddep_wait();
+    griddep_launch_dependents();
     if (nd == 0) return;  // uniform over the block
     const size_t M = (size_t)3 * g.N;
     const size_t e0 = (size_t)blockIdx.x * a.tile_elems;
@@ -545,21 +562,6 @@ __global__ void __launch_bounds__(256) arc_kernel(GroupArgs<T> g, ArcArgs a) {
     block_reduce_t2d<kArcMaxChunk>(part, acc, red);
     if (tid == 0)
         for (int i = 0; i < nd; ++i) a.dpart[((size_t)str * a.maxK + k_lo + i + 1) * a.n_tiles + blockIdx.x] = acc[i];
-    // the energies E_k of the state before the step (Eq. 8), summed over the step kernel's blocks in
-    // FP64 and in block order: images k_lo..k_lo+nd (plus image 0 in chunk 0), one warp per image, by
-    // the CTAs of tile 0 (spread over the chunks, so over several SMs)
-    if (blockIdx.x == 0) {
-        const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
-        const int k_first = k_lo == 0 ? 0 : k_lo + 1, k_last = k_lo + nd;
-        for (int k = k_first + warp; k <= k_last; k += nwarp) {
-            const double* ep = g.epart + (size_t)(img0 + k) * g.n_eblk;
-            double e = 0.0;
-            for (int b = lane; b < g.n_eblk; b += 32) e += ep[b];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
-            if (lane == 0) a.e_last[(size_t)str * a.maxK + k] = e;
-        }
-    }
 }
 
 // reparam: grid (n_str), 1024 threads, one image per thread.  d_k = sqrt(sum over tiles of the
@@ -575,18 +577,40 @@ __global__ void __launch_bounds__(1024) reparam_kernel(GroupArgs<T> g, ArcArgs a
     const int str = blockIdx.x;
     const int K = a.str_K[str], img0 = a.str_img0[str];
     const int lane = tid & 31, warp = tid >> 5, nwarp = (K + 31) >> 5;
-    if (warp >= nwarp) return;  // whole warps beyond the images; no barrier below counts them
+    // partial sums: warp w takes tiles (and step-kernel blocks) w, w+32, ... for 32 images at a time
+    // (lane = image), so the loads of all warps are in flight together; warp partials are then
+    // combined in warp order.  Fixed order throughout (deterministic).
+    __shared__ double pd[32][33], pe[32][33];
     double d = 0.0;
-    if (tid < K) {
-        double d2 = 0.0;
-        if (tid > 0) {
-            const double* dp = a.dpart + ((size_t)str * a.maxK + tid) * a.n_tiles;
-            for (int t = 0; t < a.n_tiles; ++t) d2 += dp[t];
+    griddep_wait();
+    griddep_launch_dependents();
+    for (int k0 = 0; k0 < K; k0 += 32) {
+        const int k = k0 + lane;
+        double d2 = 0.0, e = 0.0;
+        if (k < K) {
+            if (k > 0) {
+                const double* dp = a.dpart + ((size_t)str * a.maxK + k) * a.n_tiles;
+                for (int t = warp; t < a.n_tiles; t += 32) d2 += dp[t];
+            }
+            const double* ep = g.epart + (size_t)(img0 + k) * g.n_eblk;
+            for (int b = warp; b < g.n_eblk; b += 32) e += ep[b];
         }
-        const double e = a.e_last[(size_t)str * a.maxK + tid];
-        if (!isfinite(e) || !isfinite(d2)) atomicOr(g.err, kErrNonFinite);
-        d = sqrt(d2);
+        pd[warp][lane] = d2;
+        pe[warp][lane] = e;
+        __syncthreads();
+        if (warp == (k0 >> 5) && k < K) {
+            double sd = 0.0, se = 0.0;
+            for (int w = 0; w < 32; ++w) {
+                sd += pd[w][lane];
+                se += pe[w][lane];
+            }
+            a.e_last[(size_t)str * a.maxK + k] = se;
+            if (!isfinite(se) || !isfinite(sd)) atomicOr(g.err, kErrNonFinite);
+            d = sqrt(sd);  // d_k of this thread's image k = tid
+        }
+        __syncthreads();
     }
+    if (warp >= nwarp) return;  // whole warps beyond the images; no barrier below counts them
     // s_k = d_1 + ... + d_k, s_0 = 0 (Eq. 11): inclusive scan, warp shuffles then warp totals
     double v = d;
 #pragma unroll
@@ -769,6 +793,24 @@ __global__ void interp_identity_kernel(InterpEntry* tab, int img0, int K) {
 
 // ------------------------------------------------------------------------------------------------
 // launchers
+// Launch with programmatic stream serialisation (see griddep_wait); errors surface through
+// cudaGetLastError like a <<<>>> launch.
+template <typename... KArgs, typename... Args>
+static inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 static inline int grid1d(size_t n, int thr) {
     size_t b = (n + thr - 1) / thr;
     if (b > 152 * 16) b = 152 * 16;
@@ -784,21 +826,21 @@ static inline int grid1d(size_t n, int thr) {
 template <typename T> void launch_xfwd(const GroupArgs<T>& g, bool do_fft, int nthr, size_t smem, cudaStream_t st) {
     dim3 grid((g.ny + g.ty_a - 1) / g.ty_a, g.nz, g.n_pairs);
     if (!do_fft) {
-        xfwd_kernel<T, false, 0><<<grid, nthr, 0, st>>>(g);
+        launch_pdl(xfwd_kernel<T, false, 0>, grid, dim3(nthr), 0, st, g);
         return;
     }
     if constexpr (std::is_same<T, float>::value) {
         switch (g.Px) {
 #define SS_CASE(P)                                                \
     case P:                                                       \
-        xfwd_kernel<T, true, P><<<grid, nthr, smem, st>>>(g);     \
+        launch_pdl(xfwd_kernel<T, true, P>, grid, dim3(nthr), smem, st, g); \
         return;
             SS_FOR_PX(SS_CASE)
 #undef SS_CASE
             default: break;
         }
     }
-    xfwd_kernel<T, true, 0><<<grid, nthr, smem, st>>>(g);
+    launch_pdl(xfwd_kernel<T, true, 0>, grid, dim3(nthr), smem, st, g);
 }
 
 template <typename T> void launch_yz(const GroupArgs<T>& g, int nthr, size_t smem, cudaStream_t st) {
@@ -808,41 +850,41 @@ template <typename T> void launch_yz(const GroupArgs<T>& g, int nthr, size_t sme
     if constexpr (std::is_same<T, float>::value) {
 #define SS_CASE(P, Z)                                                   \
     if (g.Py == P && g.nz == Z) {                                       \
-        yz_kernel<T, P, Z><<<grid, nthr, smem, st>>>(g, stage);         \
+        launch_pdl(yz_kernel<T, P, Z>, grid, dim3(nthr), smem, st, g, stage); \
         return;                                                         \
     }
         SS_FOR_PYNZ(SS_CASE)
 #undef SS_CASE
 #define SS_CASE(Z)                                                      \
     if (g.nz == Z) {                                                    \
-        yz_kernel<T, 0, Z><<<grid, nthr, smem, st>>>(g, stage);         \
+        launch_pdl(yz_kernel<T, 0, Z>, grid, dim3(nthr), smem, st, g, stage); \
         return;                                                         \
     }
         SS_FOR_NZ(SS_CASE)
 #undef SS_CASE
     }
-    yz_kernel<T, 0, 0><<<grid, nthr, smem, st>>>(g, stage);
+    launch_pdl(yz_kernel<T, 0, 0>, grid, dim3(nthr), smem, st, g, stage);
 }
 
 template <typename T>
 void launch_xinv_step(const GroupArgs<T>& g, bool do_fft, T dt, int nthr, size_t smem, cudaStream_t st) {
     dim3 grid((g.ny + g.ty_c - 1) / g.ty_c, g.nz, g.n_pairs);
     if (!do_fft) {
-        xinv_kernel<T, false, 0, 0><<<grid, nthr, smem, st>>>(g, dt, nullptr);
+        launch_pdl(xinv_kernel<T, false, 0, 0>, grid, dim3(nthr), smem, st, g, dt, (T*)nullptr);
         return;
     }
     if constexpr (std::is_same<T, float>::value) {
         switch (g.Px) {
 #define SS_CASE(P)                                                            \
     case P:                                                                   \
-        xinv_kernel<T, true, 0, P><<<grid, nthr, smem, st>>>(g, dt, nullptr); \
+        launch_pdl(xinv_kernel<T, true, 0, P>, grid, dim3(nthr), smem, st, g, dt, (T*)nullptr); \
         return;
             SS_FOR_PX(SS_CASE)
 #undef SS_CASE
             default: break;
         }
     }
-    xinv_kernel<T, true, 0, 0><<<grid, nthr, smem, st>>>(g, dt, nullptr);
+    launch_pdl(xinv_kernel<T, true, 0, 0>, grid, dim3(nthr), smem, st, g, dt, (T*)nullptr);
 }
 
 template <typename T>
@@ -857,11 +899,11 @@ void launch_xinv_eval(const GroupArgs<T>& g, bool do_fft, T* hout, int nthr, siz
 
 template <typename T> void launch_arc(const GroupArgs<T>& g, const ArcArgs& a, int nthr, cudaStream_t st) {
     dim3 grid(a.n_tiles, a.n_kchunks, a.n_str);
-    arc_kernel<T><<<grid, nthr, 0, st>>>(g, a);
+    launch_pdl(arc_kernel<T>, grid, dim3(nthr), 0, st, g, a);
 }
 
 template <typename T> void launch_reparam(const GroupArgs<T>& g, const ArcArgs& a, cudaStream_t st) {
-    reparam_kernel<T><<<a.n_str, 1024, 0, st>>>(g, a);
+    launch_pdl(reparam_kernel<T>, dim3(a.n_str), dim3(1024), 0, st, g, a);
 }
 
 template <typename T>
