@@ -68,6 +68,7 @@ _SIGNATURES = {
     "ss_field_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                         ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p]),
+    "ss_launch_config": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "ss_num_strings": (ctypes.c_int, [ctypes.c_void_p]),
     "ss_string_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ss_string_desc)]),
     "ss_kernels_per_iteration": (ctypes.c_int, [ctypes.c_void_p]),
@@ -193,6 +194,13 @@ def ss_string_info(ctx, string: int) -> ss_string_desc:
     d = ss_string_desc()
     _check(_lib.ss_string_info(ctx, int(string), ctypes.byref(d)), ctx)
     return d
+
+
+def ss_launch_config(ctx, string: int = 0) -> dict:
+    out = (ctypes.c_int * 8)()
+    _check(_lib.ss_launch_config(ctx, int(string), out), ctx)
+    keys = ("Px", "Py", "rows_xfwd", "rows_xinv", "threads_xfwd", "threads_yz", "threads_xinv", "energy_partials")
+    return dict(zip(keys, list(out)))
 
 
 def ss_num_strings(ctx) -> int:
@@ -382,6 +390,9 @@ class StringMethod:
 
     def kernels_per_iteration(self):
         return ss_kernels_per_iteration(self.ctx)
+
+    def launch_config(self, string=0):
+        return ss_launch_config(self.ctx, string)
 
     def time_kernels(self, reps=10):
         return ss_time_kernels(self.ctx, reps)

@@ -890,6 +890,14 @@ ss_status ss_time_kernels(ss_ctx* c, int reps, double* ms_out, int max_out, int*
     return st;
 }
 
+ss_status ss_launch_config(const ss_ctx* c, int string, int out[8]) {
+    if (!c || !out || string < 0 || string >= (int)c->strs.size()) return SS_ERR_INVALID_ARG;
+    const Group& g = c->groups[c->strs[string].group];
+    const int v[8] = {g.Px, g.Py, g.ty_a, g.ty_c, g.thr_a, g.thr_b, g.thr_c, g.n_eblk};
+    for (int i = 0; i < 8; ++i) out[i] = v[i];
+    return SS_OK;
+}
+
 int ss_num_strings(const ss_ctx* c) { return c ? (int)c->strs.size() : 0; }
 
 ss_status ss_string_info(const ss_ctx* c, int string, ss_string_desc* out) {

@@ -79,7 +79,7 @@ template <typename T> struct GroupArgs {
     FftPlan planx, plany;
     const ImgParam<T>* prm;
     const InterpEntry* interp;
-    double* epart;  // per-image energy partials, [image][n_eblk] (step) or [image][4][n_eblk] (eval)
+    double* epart;  // energy partials, [n_eblk][image] (step) or [n_eblk][image][4] (eval)
     int n_eblk;     // = nz * ceil(ny / ty_c)
     int ty_a, ty_c; // y rows per CTA in the x-forward and x-inverse kernels
     int* err;       // sticky error word (bit 1: invalid input spin, bit 2: non-finite value)
@@ -95,7 +95,7 @@ struct ArcArgs {
     int tile_elems;        // components per tile
     int kchunk;            // image differences per CTA along the string
     int n_kchunks;
-    double* dpart;         // [n_str][maxK][n_tiles] squared-distance partials
+    double* dpart;         // [n_str][n_tiles][maxK] squared-distance partials
     double* e_last;        // [n_str][maxK] energies of the state before the step
     int reparam;           // 0: keep images where they are
 };

@@ -27,6 +27,23 @@ template <typename T> __device__ __forceinline__ T rsqrt_t(T x);
 template <> __device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
 template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return 1.0 / sqrt(x); }
 
+// FP64 square root and reciprocal from FP32 seeds refined by Newton steps of FP64 multiply-adds only
+// (GB300's FP64 division and square root are long instruction sequences); within a few ulp of the
+// correctly rounded results for positive finite arguments in FP32 range.
+__device__ __forceinline__ double sqrt_nr(double x) {
+    if (!(x > 0.0)) return x == 0.0 ? 0.0 : sqrt(x);
+    const double y = (double)rsqrtf((float)x);  // ~1e-7 relative
+    const double s = x * y;
+    const double r = fma(-s, s, x);                // residual x - s^2
+    return fma(0.5 * y, r, s);                     // one Newton step: ~1e-14 relative
+}
+__device__ __forceinline__ double rcp_nr(double x) {
+    double r = (double)(1.0f / (float)x);
+    r = fma(r, fma(-x, r, 1.0), r);
+    r = fma(r, fma(-x, r, 1.0), r);
+    return r;
+}
+
 // Fixed-order block reduction of NV doubles per thread; result valid in thread 0.
 template <int NV>
 __device__ __forceinline__ void block_reduce_d(double (&v)[NV], double* scratch /* [32*NV] */) {
@@ -64,11 +81,14 @@ __device__ __forceinline__ void block_reduce_t2d(T (&v)[NV], double (&out)[NV], 
 #pragma unroll
         for (int k = 0; k < NV; ++k) scratch[warp * NV + k] = double(v[k]);
     __syncthreads();
-    if (threadIdx.x == 0) {
+    // warp totals combined in FP64 by a fixed shuffle tree in warp 0 (dependent FP64 operations are
+    // slow on GB300, so a log-depth tree instead of a sequential loop)
+    if (warp == 0) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-            double a = 0.0;
-            for (int w = 0; w < nwarp; ++w) a += scratch[w * NV + k];
+            double a = lane < nwarp ? scratch[lane * NV + k] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
             out[k] = a;
         }
     }
@@ -496,9 +516,9 @@ __global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xinv_kernel(GroupAr
             const int im = ia + h;
             if (im >= g.n_img) continue;
             if (MODE == 0) {
-                g.epart[(size_t)im * g.n_eblk + blk] = acc[h];
+                g.epart[(size_t)blk * g.n_img + im] = acc[h];  // [block][image]
             } else {
-                for (int k = 0; k < 4; ++k) g.epart[((size_t)im * 4 + k) * g.n_eblk + blk] = acc[4 * h + k];
+                for (int k = 0; k < 4; ++k) g.epart[((size_t)blk * g.n_img + im) * 4 + k] = acc[4 * h + k];
             }
         }
     }
@@ -561,7 +581,7 @@ __global__ void __launch_bounds__(256) arc_kernel(GroupArgs<T> g, ArcArgs a) {
     }
     block_reduce_t2d<kArcMaxChunk>(part, acc, red);
     if (tid == 0)
-        for (int i = 0; i < nd; ++i) a.dpart[((size_t)str * a.maxK + k_lo + i + 1) * a.n_tiles + blockIdx.x] = acc[i];
+        for (int i = 0; i < nd; ++i) a.dpart[((size_t)str * a.n_tiles + blockIdx.x) * a.maxK + k_lo + i + 1] = acc[i];
 }
 
 // reparam: grid (n_str), 1024 threads, one image per thread.  d_k = sqrt(sum over tiles of the
@@ -578,39 +598,44 @@ __global__ void __launch_bounds__(1024) reparam_kernel(GroupArgs<T> g, ArcArgs a
     const int K = a.str_K[str], img0 = a.str_img0[str];
     const int lane = tid & 31, warp = tid >> 5, nwarp = (K + 31) >> 5;
     // partial sums: warp w takes tiles (and step-kernel blocks) w, w+32, ... for 32 images at a time
-    // (lane = image), so the loads of all warps are in flight together; warp partials are then
-    // combined in warp order.  Fixed order throughout (deterministic).
-    __shared__ double pd[32][33], pe[32][33];
-    double d = 0.0;
+    // (lane = image), so the loads of all warps are in flight together; then warp k combines the 32
+    // warp partials of image k0+k by a fixed shuffle tree.  Fixed order throughout (deterministic).
+    __shared__ double pd[32][33], pe[32][33], dd[kArcMaxK];
     griddep_wait();
     griddep_launch_dependents();
     for (int k0 = 0; k0 < K; k0 += 32) {
         const int k = k0 + lane;
         double d2 = 0.0, e = 0.0;
         if (k < K) {
+            // [tile][image] and [block][image] layouts: a warp reads 32 consecutive images
             if (k > 0) {
-                const double* dp = a.dpart + ((size_t)str * a.maxK + k) * a.n_tiles;
-                for (int t = warp; t < a.n_tiles; t += 32) d2 += dp[t];
+                const double* dp = a.dpart + (size_t)str * a.n_tiles * a.maxK + k;
+                for (int t = warp; t < a.n_tiles; t += 32) d2 += dp[(size_t)t * a.maxK];
             }
-            const double* ep = g.epart + (size_t)(img0 + k) * g.n_eblk;
-            for (int b = warp; b < g.n_eblk; b += 32) e += ep[b];
+            const double* ep = g.epart + img0 + k;
+            for (int b = warp; b < g.n_eblk; b += 32) e += ep[(size_t)b * g.n_img];
         }
         pd[warp][lane] = d2;
         pe[warp][lane] = e;
         __syncthreads();
-        if (warp == (k0 >> 5) && k < K) {
-            double sd = 0.0, se = 0.0;
-            for (int w = 0; w < 32; ++w) {
-                sd += pd[w][lane];
-                se += pe[w][lane];
+        const int kk = k0 + warp;  // image combined by this warp
+        if (kk < K) {
+            double sd = pd[lane][warp], se = pe[lane][warp];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                sd += __shfl_down_sync(0xffffffffu, sd, o);
+                se += __shfl_down_sync(0xffffffffu, se, o);
             }
-            a.e_last[(size_t)str * a.maxK + k] = se;
-            if (!isfinite(se) || !isfinite(sd)) atomicOr(g.err, kErrNonFinite);
-            d = sqrt(sd);  // d_k of this thread's image k = tid
+            if (lane == 0) {
+                a.e_last[(size_t)str * a.maxK + kk] = se;
+                if (!isfinite(se) || !isfinite(sd)) atomicOr(g.err, kErrNonFinite);
+                dd[kk] = sqrt_nr(sd);  // d_k (Eq. 11)
+            }
         }
         __syncthreads();
     }
     if (warp >= nwarp) return;  // whole warps beyond the images; no barrier below counts them
+    const double d = tid < K ? dd[tid] : 0.0;
     // s_k = d_1 + ... + d_k, s_0 = 0 (Eq. 11): inclusive scan, warp shuffles then warp totals
     double v = d;
 #pragma unroll
@@ -637,7 +662,7 @@ __global__ void __launch_bounds__(1024) reparam_kernel(GroupArgs<T> g, ArcArgs a
     asm volatile("bar.sync 1, %0;" ::"r"(nwarp * 32));
     const double sK = alpha[K - 1];
     const bool move = a.reparam && sK > 0.0 && isfinite(sK);
-    if (move && tid < K) alpha[tid] = v / sK;  // alpha*_k (Eq. 12)
+    if (move && tid < K) alpha[tid] = v * rcp_nr(sK);  // alpha*_k = s_k / s_{K-1} (Eq. 12)
     asm volatile("bar.sync 1, %0;" ::"r"(nwarp * 32));
     (void)nthr;
     if (tid < K) {
@@ -664,7 +689,7 @@ __global__ void __launch_bounds__(1024) reparam_kernel(GroupArgs<T> g, ArcArgs a
             const int j = lo;
             e.src0 = img0 + j;
             e.src1 = img0 + j + 1;
-            e.t = (ak - alpha[j]) / (alpha[j + 1] - alpha[j]);
+            e.t = (ak - alpha[j]) * rcp_nr(alpha[j + 1] - alpha[j]);
             e.tf = (float)e.t;
             e.omtf = (float)(1.0 - e.t);
             e.copy = 0;
@@ -683,8 +708,8 @@ __global__ void eval_reduce_kernel(GroupArgs<T> g, ArcArgs a, double* terms, dou
         double t[4];
         for (int q = 0; q < 4; ++q) {
             double v = 0.0;
-            const double* ep = g.epart + ((size_t)im * 4 + q) * g.n_eblk;
-            for (int b = 0; b < g.n_eblk; ++b) v += ep[b];
+            const double* ep = g.epart + (size_t)im * 4 + q;
+            for (int b = 0; b < g.n_eblk; ++b) v += ep[(size_t)b * g.n_img * 4];
             t[q] = v;
             terms[((size_t)str * a.maxK + k) * 4 + q] = v;
         }
