@@ -284,6 +284,8 @@ def main():
                 "traffic": ncu_traffic(dname, launch_units),
                 "kernel_ms": {n: float(v) for n, v in zip(names, ms)},
                 "kernel_share": {n: float(v) for n, v in zip(names, share)},
+                "launch_config": sm.launch_config(0),
+                "x_config_env": "SS_X_CONFIG={threads_xfwd}:{rows_xfwd}:{threads_xinv}:{rows_xinv}".format(**sm.launch_config(0)),
                 "alg_bytes_per_launch": alg_bytes}
 
     line = {

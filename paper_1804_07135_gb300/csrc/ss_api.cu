@@ -6,6 +6,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
+#include <cstdlib>
 #include <mutex>
 #include <new>
 #include <string>
@@ -189,11 +191,14 @@ template <typename T> GroupArgs<T> group_args(const ss_ctx* c, const Group& g) {
     return a;
 }
 
-// Rows per CTA of the x-forward (ty_a) and x-inverse (ty_c) kernels and the shared memory they need.
-void set_rows(const ss_ctx* c, Group& g, int ty_a, int ty_c) {
+// Rows per CTA and block sizes of the x-forward (a) and x-inverse (c) kernels and the shared memory
+// they need.
+void set_rows(const ss_ctx* c, Group& g, int ty_a, int ty_c, int thr_a = 256, int thr_c = 256) {
     const size_t cs = 2 * real_size(c);
     g.ty_a = ty_a;
     g.ty_c = ty_c;
+    g.thr_a = thr_a;
+    g.thr_c = thr_c;
     g.smem_a = (size_t)(g.Px + 3 * g.ty_a * g.lsx) * cs;
     g.smem_c = (size_t)(g.Px + 3 * g.ty_c * g.lsx) * cs + 32 * 8 * sizeof(double);
     g.smem_c_eval = g.smem_c;
@@ -207,16 +212,16 @@ void configure_group(const ss_ctx* c, Group& g) {
     g.lsy = fft_line_stride(g.Py);
     // x kernels: 256 threads; rows per CTA such that the 3*rows lines take one FFT pass and the
     // shared memory allows several resident CTAs
-    g.thr_a = g.thr_c = kMaxThreadsX;
+    // default: the largest row count whose 3*rows lines take one FFT pass of a 512-thread block
     int ty = 1;
-    for (int cand : {8, 4, 2}) {
-        if (cand <= g.ny && 3 * cand <= fft_lines_per_pass(kMaxThreadsX, g.Px) &&
-            (size_t)(g.Px + 3 * cand * g.lsx) * cs <= 48 * 1024) {
+    for (int cand : {16, 8, 5, 4, 2}) {
+        if (cand <= g.ny && 3 * cand <= fft_lines_per_pass(512, g.Px) &&
+            (size_t)(g.Px + 3 * cand * g.lsx) * cs <= 96 * 1024) {
             ty = cand;
             break;
         }
     }
-    set_rows(c, g, ty, ty);
+    set_rows(c, g, ty, ty, 512, 512);
     // y/z kernel: all 3*nz lines of one (pair, kx) in shared memory, plus the kx slab of the tensor
     // spectrum when it is small enough to stage
     g.thr_b = kMaxThreadsYz;
@@ -347,33 +352,46 @@ struct TuneKey {
         return nx == o.nx && ny == o.ny && nz == o.nz && prec == o.prec && dev == o.dev && dipole == o.dipole;
     }
 };
-std::vector<std::pair<TuneKey, std::pair<int, int>>> g_tuned;
+std::vector<std::pair<TuneKey, std::array<int, 4>>> g_tuned;  // (thr_a, ty_a, thr_c, ty_c)
 std::mutex g_tune_mu;
 
 template <typename T> ss_status tune_group(ss_ctx* c, Group& g) {
+    // SS_X_CONFIG="thr_a:ty_a:thr_c:ty_c" pins the x-kernel shapes (e.g. to profile the tuned ones)
+    if (const char* env = getenv("SS_X_CONFIG")) {
+        int ta = 0, ya = 0, tc = 0, yc = 0;
+        if (sscanf(env, "%d:%d:%d:%d", &ta, &ya, &tc, &yc) == 4 && (ta == 256 || ta == 512) && (tc == 256 || tc == 512) &&
+            ya >= 1 && yc >= 1 && ya <= g.ny && yc <= g.ny) {
+            set_rows(c, g, ya, yc, ta, tc);
+            return SS_OK;
+        }
+    }
     const TuneKey key{g.nx, g.ny, g.nz, c->opts.precision, c->device, g.dipole ? 1 : 0};
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         for (auto& e : g_tuned)
             if (e.first == key) {
-                set_rows(c, g, e.second.first, e.second.second);
+                const int* v = e.second.data();
+                set_rows(c, g, v[1], v[3], v[0], v[2]);
                 return SS_OK;
             }
     }
     const size_t cs = 2 * real_size(c);
-    std::vector<int> cands;
-    for (int ty : {1, 2, 4, 8})
-        if (ty <= g.ny && (size_t)(g.Px + 3 * ty * g.lsx) * cs + 4096 <= 96 * 1024) cands.push_back(ty);
+    std::vector<std::pair<int, int>> cands;  // (threads, rows)
+    for (int thr : {256, 512})
+        for (int ty : {1, 2, 4, 5, 8, 10, 16})
+            if (ty <= g.ny && (size_t)(g.Px + 3 * ty * g.lsx) * cs + 4096 <= 96 * 1024 &&
+                fft_lines_per_pass(thr, g.Px) >= 1 && 3 * ty <= 2 * fft_lines_per_pass(thr, g.Px))
+                cands.push_back({thr, ty});
     if (cands.size() <= 1) return SS_OK;
     cudaEvent_t e0, e1;
     CUDA_TRY(c, cudaEventCreate(&e0));
     CUDA_TRY(c, cudaEventCreate(&e1));
-    const int reps = 5;
-    float best_a = 1e30f, best_c = 1e30f;
-    int ty_a = g.ty_a, ty_c = g.ty_c;
+    const int reps = 6, trials = 3;
+    float best[2] = {1e30f, 1e30f};
+    std::pair<int, int> pick[2] = {{g.thr_a, g.ty_a}, {g.thr_c, g.ty_c}};
     const T dt = T(c->opts.dt);
-    for (int ty : cands) {
-        set_rows(c, g, ty, ty);
+    for (auto [thr, ty] : cands) {
+        set_rows(c, g, ty, ty, thr, thr);
         GroupArgs<T> a = group_args<T>(c, g);
         for (int which = 0; which < 2; ++which) {
             auto run = [&]() {
@@ -383,26 +401,32 @@ template <typename T> ss_status tune_group(ss_ctx* c, Group& g) {
                     launch_xinv_step<T>(a, g.dipole, dt, g.thr_c, g.smem_c, c->cs);
             };
             run();
-            CUDA_TRY(c, cudaEventRecord(e0, c->cs));
-            for (int r = 0; r < reps; ++r) run();
-            CUDA_TRY(c, cudaEventRecord(e1, c->cs));
-            CUDA_TRY(c, cudaEventSynchronize(e1));
-            CUDA_TRY(c, cudaGetLastError());
-            float ms = 0.f;
-            CUDA_TRY(c, cudaEventElapsedTime(&ms, e0, e1));
-            if (which == 0 && ms < best_a) best_a = ms, ty_a = ty;
-            if (which == 1 && ms < best_c) best_c = ms, ty_c = ty;
+            float ms_best = 1e30f;
+            for (int tr = 0; tr < trials; ++tr) {
+                CUDA_TRY(c, cudaEventRecord(e0, c->cs));
+                for (int r = 0; r < reps; ++r) run();
+                CUDA_TRY(c, cudaEventRecord(e1, c->cs));
+                CUDA_TRY(c, cudaEventSynchronize(e1));
+                CUDA_TRY(c, cudaGetLastError());
+                float ms = 0.f;
+                CUDA_TRY(c, cudaEventElapsedTime(&ms, e0, e1));
+                ms_best = std::min(ms_best, ms);
+            }
+            if (ms_best < best[which]) {
+                best[which] = ms_best;
+                pick[which] = {thr, ty};
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    set_rows(c, g, ty_a, ty_c);
+    set_rows(c, g, pick[0].second, pick[1].second, pick[0].first, pick[1].first);
     const size_t M = (size_t)3 * g.N * g.n_img * real_size(c);
     CUDA_TRY(c, cudaMemsetAsync(g.s, 0, M, c->cs));
     CUDA_TRY(c, cudaMemsetAsync(g.sp, 0, M, c->cs));
     CUDA_TRY(c, cudaStreamSynchronize(c->cs));
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tuned.push_back({key, {ty_a, ty_c}});
+    g_tuned.push_back({key, {pick[0].first, pick[0].second, pick[1].first, pick[1].second}});
     return SS_OK;
 }
 

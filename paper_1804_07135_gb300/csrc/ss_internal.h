@@ -20,8 +20,8 @@ template <> struct cplx_of<double> { using type = double2; };
 template <typename T> using cplx = typename cplx_of<T>::type;
 
 constexpr int kMaxStages = 16;
-constexpr int kMaxThreadsX = 256;   // block size of the x-transform kernels
-constexpr int kMinBlocksX = 4;      // resident blocks per SM they are compiled for (64 registers)
+constexpr int kMaxThreadsX = 512;   // largest block of the x-transform kernels (256 or 512, autotuned)
+constexpr int kMinBlocksX = 2;      // resident 512-thread blocks per SM they are compiled for (64 registers)
 constexpr int kMaxThreadsYz = 384;  // block size of the y/z kernel (3 x 128: one z-convolution row per warp)
 constexpr int kMinBlocksYz = 2;
 constexpr int kArcMaxChunk = 8;     // image differences one arc CTA accumulates

@@ -150,7 +150,7 @@ extern "C" ss_status ss_field_noalloc(int nx, int ny, int nz, double J, double D
     // launch shapes, as for a context of FP32 precision
     const int thr = kMaxThreadsX, thr_b = kMaxThreadsYz;
     int ty = 1;
-    for (int cand = 8; cand >= 2; cand /= 2) {
+    for (int cand = 16; cand >= 2; cand /= 2) {
         if (cand <= ny && 3 * cand <= fft_lines_per_pass(thr, Px) && (size_t)(Px + 3 * cand * lsx) * sizeof(float2) <= 48 * 1024) {
             ty = cand;
             break;
