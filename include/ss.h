@@ -154,6 +154,12 @@ ss_status ss_time_kernels(ss_ctx* ctx, int reps, double* ms_out, int max_out, in
 ss_status ss_field_noalloc(int nx, int ny, int nz, double J, double D, double K, double w_dip, int n_images,
                            const float* spins, float* field, void* stream);
 
+/* Launch configuration chosen for the size group of `string` (diagnostics): out[0..7] = padded
+ * lengths Px, Py, rows per CTA of the x-forward and x-inverse kernels (autotuned at creation),
+ * block sizes of the x-forward, y/z and x-inverse kernels, and the number of energy partials per
+ * image. */
+ss_status ss_launch_config(const ss_ctx* ctx, int string, int out[8]);
+
 /* Shape queries. */
 int ss_num_strings(const ss_ctx* ctx);
 ss_status ss_string_info(const ss_ctx* ctx, int string, ss_string_desc* out);
