@@ -201,6 +201,12 @@ void set_rows(const ss_ctx* c, Group& g, int ty_a, int ty_c, int thr_a = 256, in
     g.thr_c = thr_c;
     g.smem_a = (size_t)(g.Px + 3 * g.ty_a * g.lsx) * cs;
     g.smem_c = (size_t)(g.Px + 3 * g.ty_c * g.lsx) * cs + 32 * 8 * sizeof(double);
+    if (g.dipole && f128_x((int)real_size(c), g.Px)) {  // the launchers derive these shapes themselves
+        g.thr_a = f128_x_threads(ty_a);
+        g.thr_c = f128_x_threads(ty_c);
+        g.smem_a = f128_x_smem(ty_a, g.lsx);
+        g.smem_c = f128_x_smem(ty_c, g.lsx);
+    }
     g.smem_c_eval = g.smem_c;
     g.n_eblk = g.nz * ((g.ny + g.ty_c - 1) / g.ty_c);
 }
@@ -221,6 +227,7 @@ void configure_group(const ss_ctx* c, Group& g) {
             break;
         }
     }
+    if (g.dipole && f128_x((int)real_size(c), g.Px)) ty = std::min(8, g.ny);  // 384 threads
     set_rows(c, g, ty, ty, 512, 512);
     // y/z kernel: all 3*nz lines of one (pair, kx) in shared memory, plus the kx slab of the tensor
     // spectrum when it is small enough to stage
@@ -228,6 +235,11 @@ void configure_group(const ss_ctx* c, Group& g) {
     g.smem_b = (size_t)(g.Py + 3 * g.nz * g.lsy) * cs;
     const size_t slab = (size_t)(g.Py / 2 + 1) * g.nz * 6 * real_size(c);
     if (slab <= 24 * 1024) g.smem_b += slab;
+    if (g.dipole && f128_yz((int)real_size(c), g.Py, g.nz)) {
+        bool stage = false;
+        g.thr_b = f128_yz_threads(g.nz);
+        g.smem_b = f128_yz_smem(g.nz, g.Py, &stage);
+    }
 }
 
 template <typename T> ss_status build_tensor_spectrum(ss_ctx* c, Group& g) {
@@ -359,8 +371,10 @@ template <typename T> ss_status tune_group(ss_ctx* c, Group& g) {
     // SS_X_CONFIG="thr_a:ty_a:thr_c:ty_c" pins the x-kernel shapes (e.g. to profile the tuned ones)
     if (const char* env = getenv("SS_X_CONFIG")) {
         int ta = 0, ya = 0, tc = 0, yc = 0;
-        if (sscanf(env, "%d:%d:%d:%d", &ta, &ya, &tc, &yc) == 4 && (ta == 256 || ta == 512) && (tc == 256 || tc == 512) &&
-            ya >= 1 && yc >= 1 && ya <= g.ny && yc <= g.ny) {
+        const bool f128 = g.dipole && f128_x((int)real_size(c), g.Px);  // block size follows the rows
+        if (sscanf(env, "%d:%d:%d:%d", &ta, &ya, &tc, &yc) == 4 &&
+            (f128 || ((ta == 256 || ta == 512) && (tc == 256 || tc == 512))) && ya >= 1 && yc >= 1 && ya <= g.ny &&
+            yc <= g.ny && (!f128 || (ya <= 10 && yc <= 10))) {
             set_rows(c, g, ya, yc, ta, tc);
             return SS_OK;
         }
@@ -377,11 +391,16 @@ template <typename T> ss_status tune_group(ss_ctx* c, Group& g) {
     }
     const size_t cs = 2 * real_size(c);
     std::vector<std::pair<int, int>> cands;  // (threads, rows)
-    for (int thr : {256, 512})
-        for (int ty : {1, 2, 4, 5, 8, 10, 16})
-            if (ty <= g.ny && (size_t)(g.Px + 3 * ty * g.lsx) * cs + 4096 <= 96 * 1024 &&
-                fft_lines_per_pass(thr, g.Px) >= 1 && 3 * ty <= 2 * fft_lines_per_pass(thr, g.Px))
-                cands.push_back({thr, ty});
+    if (g.dipole && f128_x((int)real_size(c), g.Px)) {
+        for (int ty : {2, 4, 5, 8, 10})  // 48 threads per row, at most 480
+            if (ty <= g.ny) cands.push_back({f128_x_threads(ty), ty});
+    } else {
+        for (int thr : {256, 512})
+            for (int ty : {1, 2, 4, 5, 8, 10, 16})
+                if (ty <= g.ny && (size_t)(g.Px + 3 * ty * g.lsx) * cs + 4096 <= 96 * 1024 &&
+                    fft_lines_per_pass(thr, g.Px) >= 1 && 3 * ty <= 2 * fft_lines_per_pass(thr, g.Px))
+                    cands.push_back({thr, ty});
+    }
     if (cands.size() <= 1) return SS_OK;
     cudaEvent_t e0, e1;
     CUDA_TRY(c, cudaEventCreate(&e0));

@@ -18,6 +18,9 @@ template <typename C> __device__ __forceinline__ C csub(C a, C b) { return C{a.x
 template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
     return C{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
 }
+// FP32 sums as one paired (two-lane) FP32 instruction each
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
 template <typename C> __device__ __forceinline__ C cconj(C a) { return C{a.x, -a.y}; }
 // multiply by -i
 template <typename C> __device__ __forceinline__ C cmi(C a) { return C{a.y, -a.x}; }
@@ -360,6 +363,75 @@ template <typename C, typename W> inline void fft_stage_twiddles(const FftPlan& 
                 out[o++] = C{decltype(C{}.x)(x.x), decltype(C{}.x)(x.y)};
             }
     }
+}
+
+// ---- length 128 in two register passes -----------------------------------------------------------
+// With n = 8 n1 + n2 and k = k1 + 16 k2 (n1, k1 < 16; n2, k2 < 8) and W = W_128,
+//   X[k1 + 16 k2] = sum_{n2} W_8^{n2 k2} W^{n2 k1} Y[n2][k1],   Y[n2][k1] = sum_{n1} W_16^{n1 k1} x[8 n1 + n2].
+// Split by the parity of k1 = 2 m + par, the 16-point inner DFT is an 8-point DFT over n1 < 8 of
+//   u[n1] = (x[8 n1 + n2] + (-1)^par x[8 n1 + 64 + n2]) W_16^{par n1},
+// so a line takes two passes of 8-point DFTs in registers with one exchange through shared memory:
+// pass 1, role (n2, par): Z[n2][2m + par] = W^{n2 (2m + par)} DFT8(u)[m];
+// pass 2, role k1:        X[k1 + 16 k2] = DFT8(Z[.][k1])[k2].
+// A line with a zero upper half (x[n] = 0 for n >= 64) drops the second term of u; a transform read
+// only below 64 evaluates k2 < 4 in pass 2 (the other outputs are dead code).
+// kF128Line (ss_internal.h): line stride of the exchange buffer Z[line][n2][k1] (complex elements)
+constexpr int kF128N2 = 18;  // n2 stride: 16 lanes (n2, par) or (k1) of one line hit 16 distinct bank pairs
+__host__ __device__ constexpr int f128_pos(int line, int n2, int k1) { return line * kF128Line + n2 * kF128N2 + k1; }
+
+// a * W_16^J for a compile-time J < 8, W_16 = exp(-2 pi i / 16)
+template <int J, typename C> __device__ __forceinline__ C mul_w16(C a) {
+    using R = decltype(a.x);
+    constexpr double c1 = 0.923879532511286756128183189396788933;  // cos(pi/8)
+    constexpr double s1 = 0.382683432365089771728459984030398866;  // sin(pi/8)
+    constexpr double h = 0.707106781186547524400844362104849039;   // cos(pi/4)
+    if constexpr (J == 0) {
+        return a;
+    } else if constexpr (J == 4) {
+        return cmi(a);
+    } else if constexpr (J == 2) {
+        return C{R(h) * (a.x + a.y), R(h) * (a.y - a.x)};
+    } else if constexpr (J == 6) {
+        return C{R(h) * (a.y - a.x), R(-h) * (a.x + a.y)};
+    } else {
+        constexpr double cr = J == 1 ? c1 : J == 3 ? s1 : J == 5 ? -s1 : -c1;
+        constexpr double ci = J == 1 ? -s1 : J == 3 ? -c1 : J == 5 ? -c1 : -s1;
+        return cmul(a, C{R(cr), R(ci)});
+    }
+}
+template <typename C> __device__ __forceinline__ void mul_w16_ramp(C (&u)[8]) {
+    u[1] = mul_w16<1>(u[1]);
+    u[2] = mul_w16<2>(u[2]);
+    u[3] = mul_w16<3>(u[3]);
+    u[4] = mul_w16<4>(u[4]);
+    u[5] = mul_w16<5>(u[5]);
+    u[6] = mul_w16<6>(u[6]);
+    u[7] = mul_w16<7>(u[7]);
+}
+
+// Pass 1 for role (n2, par) of one line.  u holds x[8 n1 + n2] for n1 < 8 on entry; hi (when given)
+// holds x[8 n1 + 64 + n2].  Writes Z[n2][2m + par] of the line at zl = exchange buffer + line offset.
+// tw: flat table W_128^k (k < 128).
+template <bool HAS_HI, typename C>
+__device__ __forceinline__ void f128_pass1(C (&u)[8], const C (&hi)[8], int n2, int par, const C* __restrict__ tw,
+                                           C* zl) {
+    if constexpr (HAS_HI) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) u[j] = par ? csub(u[j], hi[j]) : cadd(u[j], hi[j]);
+    }
+    if (par) mul_w16_ramp(u);
+    Dft<8, C>::run(u);
+    C* z = zl + n2 * kF128N2 + par;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) z[2 * m] = cmul(u[m], tw[n2 * (2 * m + par)]);  // tw[0] = 1 exactly
+}
+
+// Pass 2 for role k1 of one line: v[k2] = X[k1 + 16 k2] (k2 < KOUT) from Z[.][k1] at zl + k1.
+template <typename C> __device__ __forceinline__ void f128_pass2(C (&v)[8], const C* zl, int k1) {
+    const C* z = zl + k1;
+#pragma unroll
+    for (int n2 = 0; n2 < 8; ++n2) v[n2] = z[n2 * kF128N2];
+    Dft<8, C>::run(v);
 }
 
 // Dispatch: compile-time plan when PC > 0 (tw = per-stage table), the runtime plan otherwise (tw =

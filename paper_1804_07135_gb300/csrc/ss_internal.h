@@ -102,6 +102,23 @@ struct ArcArgs {
 
 enum { kErrInvalidSpin = 1, kErrNonFinite = 2 };
 
+// Length-128 transforms in two register passes (FP32): the x kernels when Px = 128, the y/z kernel
+// when Py = 128 and nz is 4 or 8.  16 threads per line; their launch shapes follow from the rows per
+// CTA (x kernels) or from nz (y/z kernel), whatever block size and shared memory the caller passes.
+constexpr int kF128Line = 146;  // line stride of their exchange buffers (complex elements)
+inline bool f128_x(int real_bytes, int Px) { return real_bytes == 4 && Px == 128; }
+inline bool f128_yz(int real_bytes, int Py, int nz) { return real_bytes == 4 && Py == 128 && (nz == 4 || nz == 8); }
+inline int f128_x_threads(int rows) { return 48 * rows; }
+inline size_t f128_x_smem(int rows, int lsx) {
+    return (size_t)3 * rows * (lsx + kF128Line) * 8 + 32 * 8 * sizeof(double);  // + reduction scratch
+}
+inline int f128_yz_threads(int nz) { return 48 * nz; }
+inline size_t f128_yz_smem(int nz, int Py, bool* stage_dhat) {
+    const size_t slab = (size_t)(Py / 2 + 1) * nz * 6 * sizeof(float);
+    *stage_dhat = slab <= 24 * 1024;
+    return (size_t)2 * 3 * nz * kF128Line * 8 + (*stage_dhat ? slab : 0);
+}
+
 // ---- launchers (defined in ss_kernels.cuh, instantiated for float and double) ----
 template <typename T> void launch_xfwd(const GroupArgs<T>& g, bool do_fft, int nthr, size_t smem, cudaStream_t st);
 template <typename T> void launch_yz(const GroupArgs<T>& g, int nthr, size_t smem, cudaStream_t st);

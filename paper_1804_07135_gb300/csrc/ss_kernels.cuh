@@ -102,25 +102,15 @@ __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wa
 __device__ __forceinline__ void griddep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
 
 // ------------------------------------------------------------------------------------------------
-// xfwd: grid (ceil(ny/ty_a), nz, n_pairs).  Each CTA takes rows [y0, y0+rows) of layer z for the two
-// images of pair p: s[img] = normalise((1-t) sp[src0] + t sp[src1]) (or a copy), written back to s,
-// packed as re/im of 3*rows complex lines, zero-padded to Px and transformed along x.
-// Output spec[p][kx][c][z][y].
-template <typename T, bool DO_FFT, int PX>
-__global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xfwd_kernel(GroupArgs<T> g) {
+// Gather of rows [y0, y0+rows) of layer z for pair p: s[img] = normalise((1-t) sp[src0] + t sp[src1])
+// (or a copy), written back to s and, when buf is given, to line c*rows + yy of buf (stride lsx,
+// fft_pad positions) as re/im of the pair.
+template <typename T>
+__device__ __forceinline__ void xfwd_gather(const GroupArgs<T>& g, cplx<T>* buf, int p, int z, int y0, int rows,
+                                            int tid, int nthr) {
     using C = cplx<T>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* tw = reinterpret_cast<C*>(smem_raw);
-    C* buf = tw + g.Px;
-    const int tid = threadIdx.x, nthr = blockDim.x;
-    const int p = blockIdx.z, z = blockIdx.y, y0 = blockIdx.x * g.ty_a;
-    const int rows = min(g.ty_a, g.ny - y0);
     const int nx = g.nx, N = g.N;
     const int ia = 2 * p;
-    if (DO_FFT)
-        for (int i = tid; i < g.Px; i += nthr) tw[i] = PX > 0 ? g.twxs[i] : g.twx[i];
-    griddep_wait();
-    griddep_launch_dependents();
     for (int it = tid; it < rows * nx; it += nthr) {
         const int yy = it / nx, x = it - yy * nx;
         const int site = (z * g.ny + y0 + yy) * nx + x;
@@ -154,11 +144,32 @@ __global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xfwd_kernel(GroupAr
                 out[h][2] = u2;
             }
         }
-        if (DO_FFT) {
+        if (buf) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) buf[(c * rows + yy) * g.lsx + fft_pad(x)] = C{out[0][c], out[1][c]};
         }
     }
+}
+
+// xfwd: grid (ceil(ny/ty_a), nz, n_pairs).  Each CTA takes rows [y0, y0+rows) of layer z for the two
+// images of pair p: s[img] = normalise((1-t) sp[src0] + t sp[src1]) (or a copy), written back to s,
+// packed as re/im of 3*rows complex lines, zero-padded to Px and transformed along x.
+// Output spec[p][kx][c][z][y].
+template <typename T, bool DO_FFT, int PX>
+__global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xfwd_kernel(GroupArgs<T> g) {
+    using C = cplx<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* buf = tw + g.Px;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int p = blockIdx.z, z = blockIdx.y, y0 = blockIdx.x * g.ty_a;
+    const int rows = min(g.ty_a, g.ny - y0);
+    const int nx = g.nx;
+    if (DO_FFT)
+        for (int i = tid; i < g.Px; i += nthr) tw[i] = PX > 0 ? g.twxs[i] : g.twx[i];
+    griddep_wait();
+    griddep_launch_dependents();
+    xfwd_gather(g, DO_FFT ? buf : (C*)nullptr, p, z, y0, rows, tid, nthr);
     if (!DO_FFT) return;
     const int padw = g.Px - nx;
     for (int it = tid; it < 3 * rows * padw; it += nthr) {
@@ -178,6 +189,47 @@ __global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xfwd_kernel(GroupAr
     }
 }
 
+// xfwd for Px = 128 (nx <= 64): the same gather, then the x-transform of the 3*rows lines in two
+// register passes (f128_pass1/2) with 16 roles per line; the second pass writes the spectrum straight
+// to global memory, rows fastest across a warp (the rows of one (kx, c) are contiguous there).
+template <typename T>
+__global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xfwd128_kernel(GroupArgs<T> g) {
+    using C = cplx<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int rows_max = g.ty_a;
+    C* buf = reinterpret_cast<C*>(smem_raw);  // 3*rows lines, stride lsx, fft_pad positions
+    C* zx = buf + 3 * rows_max * g.lsx;       // exchange buffer, 3*rows lines of kF128Line
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int p = blockIdx.z, z = blockIdx.y, y0 = blockIdx.x * rows_max;
+    const int rows = min(rows_max, g.ny - y0);
+    const int nx = g.nx, L = 3 * rows;
+    const C* __restrict__ tw = g.twx;  // W_128^k
+    griddep_wait();
+    griddep_launch_dependents();
+    xfwd_gather(g, buf, p, z, y0, rows, tid, nthr);
+    __syncthreads();
+    for (int r = tid; r < 16 * L; r += nthr) {
+        const int par = r & 1, n2 = (r >> 1) & 7, line = r >> 4;
+        const C* b = buf + line * g.lsx;
+        C u[8];
+#pragma unroll
+        for (int n1 = 0; n1 < 8; ++n1) u[n1] = 8 * n1 + n2 < nx ? b[fft_pad(8 * n1 + n2)] : C{T(0), T(0)};
+        f128_pass1<false>(u, u, n2, par, tw, zx + line * kF128Line);
+    }
+    __syncthreads();
+    const size_t kstride = (size_t)3 * g.nz * g.ny;  // between consecutive kx
+    C* outp = g.spec + (size_t)p * 128 * kstride + (size_t)z * g.ny + y0;
+    for (int r = tid; r < 16 * L; r += nthr) {
+        const int c = r / (16 * rows), rem = r - c * 16 * rows;
+        const int k1 = rem / rows, yy = rem - k1 * rows;
+        C v[8];
+        f128_pass2(v, zx + (c * rows + yy) * kF128Line, k1);
+        C* o = outp + (size_t)k1 * kstride + (size_t)c * g.nz * g.ny + yy;
+#pragma unroll
+        for (int k2 = 0; k2 < 8; ++k2) o[(size_t)16 * k2 * kstride] = v[k2];
+    }
+}
+
 // ------------------------------------------------------------------------------------------------
 // Dipole-tensor spectrum lookup: stored octant value with the per-axis parity signs of Eq. 7's
 // components (xx, yy, zz, xy: real; xz, yz: imaginary, returned as the coefficient of i).
@@ -193,9 +245,11 @@ constexpr int kYzItems = 4;
 // across a warp (nthr/3 a multiple of 32), both z loops unrolled so |z - z'| and the z-parity sign are
 // constants.  Row a of the tensor: a = x: (xx, xy, i xz); a = y: (xy, yy, i yz); a = z: (i xz, i yz, zz).
 // dslab holds the coefficient (kyo, |dz|, comp) at dslab[kyo*dk + (|dz|*6 + comp)*dq].
-template <int NZ, typename T, typename C>
-__device__ __forceinline__ void zconv_c(C* A, int lsy, int Py, int kx, int Px, const T* dslab, int dk, int dq, int tid,
-                                        int nthr) {
+// INPLACE: lines of A (stride lsy, fft_pad positions) are overwritten with the conjugated result;
+// otherwise the result goes to the lines of B (same stride, plain positions) and A is only read.
+template <int NZ, bool INPLACE = true, typename T, typename C>
+__device__ __forceinline__ void zconv_c(const C* A, C* B, int lsy, int Py, int kx, int Px, const T* dslab, int dk,
+                                        int dq, int tid, int nthr) {
     const int hx = Px / 2, hy = Py / 2;
     const T sxg = kx > hx ? T(-1) : T(1);
     const int nk = nthr / 3;
@@ -209,7 +263,7 @@ __device__ __forceinline__ void zconv_c(C* A, int lsy, int Py, int kx, int Px, c
             const int kyo = min(ky, Py - ky);
             const T syg = ky > hy ? T(-1) : T(1);
             const T* d = dslab + (size_t)kyo * dk;
-            pky = fft_pad(ky);
+            pky = INPLACE ? fft_pad(ky) : ky;
             // coefficient slots (xx 0, yy 1, zz 2, xy 3, xz 4, yz 5) and x/y parity signs of row a
             const int i0 = a == 0 ? 0 : (a == 1 ? 3 : 4);
             const int i1 = a == 0 ? 3 : (a == 1 ? 1 : 5);
@@ -226,7 +280,42 @@ __device__ __forceinline__ void zconv_c(C* A, int lsy, int Py, int kx, int Px, c
             }
 #pragma unroll
             for (int z = 0; z < NZ; ++z) out[z] = C{T(0), T(0)};
-            if (a < 2) {
+            if constexpr (std::is_same<T, float>::value) {
+                // paired FP32 form: out += (e, e) * S and (g, g) * (i S) with i S = (-S.y, S.x); the
+                // z-parity sign of the odd terms moves onto the operand, -(i S) = (S.y, -S.x)
+                if (a < 2) {
+#pragma unroll
+                    for (int zp = 0; zp < NZ; ++zp) {
+                        const float2 sx = A[(0 * NZ + zp) * lsy + pky];
+                        const float2 sy = A[(1 * NZ + zp) * lsy + pky];
+                        const float2 sz = A[(2 * NZ + zp) * lsy + pky];
+                        const float2 isz = make_float2(-sz.y, sz.x), nisz = make_float2(sz.y, -sz.x);
+#pragma unroll
+                        for (int z = 0; z < NZ; ++z) {
+                            const int q = z >= zp ? z - zp : zp - z;
+                            out[z] = __ffma2_rn(make_float2(e0[q], e0[q]), sx, out[z]);
+                            out[z] = __ffma2_rn(make_float2(e1[q], e1[q]), sy, out[z]);
+                            out[z] = __ffma2_rn(make_float2(e2[q], e2[q]), z >= zp ? isz : nisz, out[z]);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int zp = 0; zp < NZ; ++zp) {
+                        const float2 sx = A[(0 * NZ + zp) * lsy + pky];
+                        const float2 sy = A[(1 * NZ + zp) * lsy + pky];
+                        const float2 sz = A[(2 * NZ + zp) * lsy + pky];
+                        const float2 isx = make_float2(-sx.y, sx.x), nisx = make_float2(sx.y, -sx.x);
+                        const float2 isy = make_float2(-sy.y, sy.x), nisy = make_float2(sy.y, -sy.x);
+#pragma unroll
+                        for (int z = 0; z < NZ; ++z) {
+                            const int q = z >= zp ? z - zp : zp - z;
+                            out[z] = __ffma2_rn(make_float2(e0[q], e0[q]), z >= zp ? isx : nisx, out[z]);
+                            out[z] = __ffma2_rn(make_float2(e1[q], e1[q]), z >= zp ? isy : nisy, out[z]);
+                            out[z] = __ffma2_rn(make_float2(e2[q], e2[q]), sz, out[z]);
+                        }
+                    }
+                }
+            } else if (a < 2) {
 #pragma unroll
                 for (int zp = 0; zp < NZ; ++zp) {
                     const C sx = A[(0 * NZ + zp) * lsy + pky];
@@ -257,13 +346,13 @@ __device__ __forceinline__ void zconv_c(C* A, int lsy, int Py, int kx, int Px, c
                 }
             }
         }
-        __syncthreads();
+        if constexpr (INPLACE) __syncthreads();
         if (act) {
             // conjugated: the inverse transform is the conjugate of the forward transform of the conjugate
 #pragma unroll
-            for (int z = 0; z < NZ; ++z) A[(a * NZ + z) * lsy + pky] = cconj(out[z]);
+            for (int z = 0; z < NZ; ++z) B[(a * NZ + z) * lsy + pky] = cconj(out[z]);
         }
-        __syncthreads();
+        if constexpr (INPLACE) __syncthreads();
     }
 }
 
@@ -362,7 +451,7 @@ __global__ void __launch_bounds__(kMaxThreadsYz, kMinBlocksYz) yz_kernel(GroupAr
     __syncthreads();
     fft_lines_any<PY, true, false>(A, tw, g.plany, g.lsy, L, tid, nthr);
     if constexpr (NZ > 0)
-        zconv_c<NZ>(A, g.lsy, Py, kx, g.Px, dslab, dk, dq, tid, nthr);
+        zconv_c<NZ>(A, A, g.lsy, Py, kx, g.Px, dslab, dk, dq, tid, nthr);
     else
         zconv_any(A, g.lsy, Py, nz, kx, g.Px, dslab, dk, dq, tid, nthr);
     fft_lines_any<PY, false, true>(A, tw, g.plany, g.lsy, L, tid, nthr);
@@ -372,45 +461,85 @@ __global__ void __launch_bounds__(kMaxThreadsYz, kMinBlocksYz) yz_kernel(GroupAr
     }
 }
 
-// ------------------------------------------------------------------------------------------------
-// xinv: grid (ceil(ny/ty_c), nz, n_pairs).  Inverse x-transform of the pair's field spectra (the
-// tensor spectrum already carries 4 pi / (Px Py)), then per site of both images:
-//   h = J sum_nn s_j                                                     (Eq. 3)
-//     - D (s_z^{+x} - s_z^{-x}, s_z^{+y} - s_z^{-y}, -s_x^{+x} + s_x^{-x} - s_y^{+y} + s_y^{-y})  (Eq. 4)
-//     + 2 K s_z z                                                        (Eq. 5)
-//     + w * dipole convolution                                           (Eq. 6)
-// MODE 0 (step): e += -(1/2) h.s (Eq. 8), s' = normalise(s + dt (h - (s.h) s)) (Eqs. 10, 13).
-// MODE 1 (eval): FP64 energy terms of the FP64-renormalised spins, bonds to +x, +y, +z counted once
-//                (Eq. 1): tJ = -sum s_i.s_j, tD = sum (r_ij x z).(s_i x s_j), tK = -sum s_z^2,
-//                tw = -(1/2) sum conv.s; optionally the field h.
-template <typename T, bool DO_FFT, int MODE, int PX>
-__global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xinv_kernel(GroupArgs<T> g, T dt, T* hout) {
+// yz for Py = 128 (ny <= 64), NZ layers: the y-transforms in two register passes each way
+// (f128_pass1/2, 16 roles per line, 16 * 3 * NZ threads) around the z-convolution.  Two shared
+// regions of 3*NZ lines alternate: R1 = forward exchange, then the z-convolution output; R2 = forward
+// output (z-convolution input, stride kLz), then the inverse exchange.
+constexpr int kLz = 136;  // line stride of the z-convolution input/output ([line][ky])
+template <typename T, int NZ>
+__global__ void __launch_bounds__(kMaxThreadsYz, kMinBlocksYz) yz128_kernel(GroupArgs<T> g, int stage_dhat) {
     using C = cplx<T>;
+    constexpr int L = 3 * NZ, hy = 64;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* tw = reinterpret_cast<C*>(smem_raw);
-    C* buf = tw + g.Px;
-    double* red = reinterpret_cast<double*>(buf + (DO_FFT ? 3 * g.ty_c * g.lsx : 0));
+    C* R1 = reinterpret_cast<C*>(smem_raw);
+    C* R2 = R1 + L * kF128Line;
+    T* dsm = reinterpret_cast<T*>(R2 + L * kF128Line);
     const int tid = threadIdx.x, nthr = blockDim.x;
-    const int p = blockIdx.z, z = blockIdx.y, y0 = blockIdx.x * g.ty_c;
-    const int rows = min(g.ty_c, g.ny - y0);
-    const int nx = g.nx, ny = g.ny, nz = g.nz, N = g.N;
-    const int ia = 2 * p;
-    if (DO_FFT)
-        for (int i = tid; i < g.Px; i += nthr) tw[i] = PX > 0 ? g.twxs[i] : g.twx[i];
+    const int kx = blockIdx.x, p = blockIdx.y;
+    const int ny = g.ny;
+    const int kxo = min(kx, g.Px - kx);
+    C* blk = g.spec + ((size_t)p * g.Px + kx) * L * ny;
+    const T* dslab = g.dhat + (size_t)kxo * (hy + 1) * NZ * 6;
+    if (stage_dhat) {
+        for (int i = tid; i < (hy + 1) * NZ * 6; i += nthr) dsm[i] = dslab[i];
+        dslab = dsm;
+    }
+    const C* __restrict__ tw = g.twy;  // W_128^k
     griddep_wait();
     griddep_launch_dependents();
-    if (DO_FFT) {
-        const int Px = PX > 0 ? PX : g.Px;
-        const C* inp = g.spec + (size_t)p * Px * 3 * nz * ny;
-        for (int kc = tid; kc < Px * 3; kc += nthr) {
-            const int kx = kc / 3, c = kc - 3 * kx;
-            const C* s = inp + ((size_t)kc * nz + z) * ny + y0;
-            C* b = buf + c * rows * g.lsx + fft_pad(kx);
-            for (int yy = 0; yy < rows; ++yy) b[yy * g.lsx] = cconj(s[yy]);
-        }
-        __syncthreads();
-        fft_lines_any<PX, false, true>(buf, tw, g.planx, g.lsx, 3 * rows, tid, nthr);
+    for (int r = tid; r < 16 * L; r += nthr) {
+        const int par = r & 1, n2 = (r >> 1) & 7, line = r >> 4;
+        const C* src = blk + (size_t)line * ny + n2;
+        C u[8];
+#pragma unroll
+        for (int n1 = 0; n1 < 8; ++n1) u[n1] = 8 * n1 + n2 < ny ? src[8 * n1] : C{T(0), T(0)};
+        f128_pass1<false>(u, u, n2, par, tw, R1 + line * kF128Line);
     }
+    __syncthreads();
+    for (int r = tid; r < 16 * L; r += nthr) {
+        const int k1 = r & 15, line = r >> 4;
+        C v[8];
+        f128_pass2(v, R1 + line * kF128Line, k1);
+        C* a = R2 + line * kLz + k1;
+#pragma unroll
+        for (int k2 = 0; k2 < 8; ++k2) a[16 * k2] = v[k2];
+    }
+    __syncthreads();
+    zconv_c<NZ, false>(R2, R1, kLz, 128, kx, g.Px, dslab, 1, hy + 1, tid, nthr);
+    __syncthreads();
+    for (int r = tid; r < 16 * L; r += nthr) {
+        const int par = r & 1, n2 = (r >> 1) & 7, line = r >> 4;
+        const C* b = R1 + line * kLz + n2;
+        C u[8], hi[8];
+#pragma unroll
+        for (int n1 = 0; n1 < 8; ++n1) {
+            u[n1] = b[8 * n1];
+            hi[n1] = b[8 * n1 + 64];
+        }
+        f128_pass1<true>(u, hi, n2, par, tw, R2 + line * kF128Line);
+    }
+    __syncthreads();
+    for (int r = tid; r < 16 * L; r += nthr) {
+        const int k1 = r & 15, line = r >> 4;
+        C v[8];
+        f128_pass2(v, R2 + line * kF128Line, k1);
+        C* dst = blk + (size_t)line * ny + k1;
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2)
+            if (k1 + 16 * k2 < ny) dst[16 * k2] = cconj(v[k2]);
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Per-site work of the x-inverse kernels on rows [y0, y0+rows) of layer z, pair p; buf holds the
+// forward transforms of the conjugated field spectra (line c*rows + yy, fft_pad positions) when
+// HAS_CONV.
+template <typename T, bool HAS_CONV, int MODE>
+__device__ __forceinline__ void xinv_sites(const GroupArgs<T>& g, T dt, T* hout, const cplx<T>* buf, double* red,
+                                           int p, int z, int y0, int rows, int tid, int nthr) {
+    using C = cplx<T>;
+    const int nx = g.nx, ny = g.ny, nz = g.nz, N = g.N;
+    const int ia = 2 * p;
     constexpr int NV = MODE == 0 ? 2 : 8;
     double acc[NV];
 #pragma unroll
@@ -442,7 +571,7 @@ __global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xinv_kernel(GroupAr
             zm[c] = z > 0 ? q[-nx * ny] : T(0);
         }
         T conv[3] = {T(0), T(0), T(0)};
-        if (DO_FFT) {
+        if (HAS_CONV) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const C v = buf[(c * rows + yy) * g.lsx + fft_pad(x)];
@@ -522,6 +651,91 @@ __global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xinv_kernel(GroupAr
             }
         }
     }
+}
+
+// xinv: grid (ceil(ny/ty_c), nz, n_pairs).  Inverse x-transform of the pair's field spectra (the
+// tensor spectrum already carries 4 pi / (Px Py)), then per site of both images:
+//   h = J sum_nn s_j                                                     (Eq. 3)
+//     - D (s_z^{+x} - s_z^{-x}, s_z^{+y} - s_z^{-y}, -s_x^{+x} + s_x^{-x} - s_y^{+y} + s_y^{-y})  (Eq. 4)
+//     + 2 K s_z z                                                        (Eq. 5)
+//     + w * dipole convolution                                           (Eq. 6)
+// MODE 0 (step): e += -(1/2) h.s (Eq. 8), s' = normalise(s + dt (h - (s.h) s)) (Eqs. 10, 13).
+// MODE 1 (eval): FP64 energy terms of the FP64-renormalised spins, bonds to +x, +y, +z counted once
+//                (Eq. 1): tJ = -sum s_i.s_j, tD = sum (r_ij x z).(s_i x s_j), tK = -sum s_z^2,
+//                tw = -(1/2) sum conv.s; optionally the field h.
+template <typename T, bool DO_FFT, int MODE, int PX>
+__global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xinv_kernel(GroupArgs<T> g, T dt, T* hout) {
+    using C = cplx<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* buf = tw + g.Px;
+    double* red = reinterpret_cast<double*>(buf + (DO_FFT ? 3 * g.ty_c * g.lsx : 0));
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int p = blockIdx.z, z = blockIdx.y, y0 = blockIdx.x * g.ty_c;
+    const int rows = min(g.ty_c, g.ny - y0);
+    const int ny = g.ny, nz = g.nz;
+    if (DO_FFT)
+        for (int i = tid; i < g.Px; i += nthr) tw[i] = PX > 0 ? g.twxs[i] : g.twx[i];
+    griddep_wait();
+    griddep_launch_dependents();
+    if (DO_FFT) {
+        const int Px = PX > 0 ? PX : g.Px;
+        const C* inp = g.spec + (size_t)p * Px * 3 * nz * ny;
+        for (int kc = tid; kc < Px * 3; kc += nthr) {
+            const int kx = kc / 3, c = kc - 3 * kx;
+            const C* s = inp + ((size_t)kc * nz + z) * ny + y0;
+            C* b = buf + c * rows * g.lsx + fft_pad(kx);
+            for (int yy = 0; yy < rows; ++yy) b[yy * g.lsx] = cconj(s[yy]);
+        }
+        __syncthreads();
+        fft_lines_any<PX, false, true>(buf, tw, g.planx, g.lsx, 3 * rows, tid, nthr);
+    }
+    xinv_sites<T, DO_FFT, MODE>(g, dt, hout, buf, red, p, z, y0, rows, tid, nthr);
+}
+
+// xinv for Px = 128 (nx <= 64): the inverse x-transform (a forward transform of the conjugate) of the
+// 3*rows lines in two register passes, inputs read straight from the spectrum (rows fastest across a
+// warp), outputs x < 64 into buf; then the same per-site work as xinv_kernel.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xinv128_kernel(GroupArgs<T> g, T dt, T* hout) {
+    using C = cplx<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int rows_max = g.ty_c;
+    C* buf = reinterpret_cast<C*>(smem_raw);  // 3*rows lines, stride lsx, fft_pad positions
+    C* zx = buf + 3 * rows_max * g.lsx;       // exchange buffer, 3*rows lines of kF128Line
+    double* red = reinterpret_cast<double*>(zx + 3 * rows_max * kF128Line);
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int p = blockIdx.z, z = blockIdx.y, y0 = blockIdx.x * rows_max;
+    const int rows = min(rows_max, g.ny - y0);
+    const int L = 3 * rows;
+    const C* __restrict__ tw = g.twx;  // W_128^k
+    const size_t kstride = (size_t)3 * g.nz * g.ny;  // between consecutive kx
+    const C* inp = g.spec + (size_t)p * 128 * kstride + (size_t)z * g.ny + y0;
+    griddep_wait();
+    griddep_launch_dependents();
+    for (int r = tid; r < 16 * L; r += nthr) {
+        const int t = r / rows, yy = r - t * rows;
+        const int par = t & 1, n2 = (t >> 1) & 7, c = t >> 4;
+        const C* s = inp + (size_t)n2 * kstride + (size_t)c * g.nz * g.ny + yy;  // kx = 8 n1 + n2
+        C u[8], hi[8];
+#pragma unroll
+        for (int n1 = 0; n1 < 8; ++n1) {
+            u[n1] = cconj(s[(size_t)8 * n1 * kstride]);
+            hi[n1] = cconj(s[(size_t)(8 * n1 + 64) * kstride]);
+        }
+        f128_pass1<true>(u, hi, n2, par, tw, zx + (c * rows + yy) * kF128Line);
+    }
+    __syncthreads();
+    for (int r = tid; r < 16 * L; r += nthr) {
+        const int k1 = r & 15, line = r >> 4;
+        C v[8];
+        f128_pass2(v, zx + line * kF128Line, k1);
+        C* b = buf + line * g.lsx;
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) b[fft_pad(k1 + 16 * k2)] = v[k2];
+    }
+    __syncthreads();
+    xinv_sites<T, true, MODE>(g, dt, hout, buf, red, p, z, y0, rows, tid, nthr);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -855,6 +1069,10 @@ template <typename T> void launch_xfwd(const GroupArgs<T>& g, bool do_fft, int n
         return;
     }
     if constexpr (std::is_same<T, float>::value) {
+        if (f128_x(4, g.Px)) {
+            launch_pdl(xfwd128_kernel<T>, grid, dim3(f128_x_threads(g.ty_a)), f128_x_smem(g.ty_a, g.lsx), st, g);
+            return;
+        }
         switch (g.Px) {
 #define SS_CASE(P)                                                \
     case P:                                                       \
@@ -873,6 +1091,15 @@ template <typename T> void launch_yz(const GroupArgs<T>& g, int nthr, size_t sme
     const size_t base = (size_t)(g.Py + 3 * g.nz * g.lsy) * sizeof(cplx<T>);
     const int stage = smem >= base + (size_t)(g.Py / 2 + 1) * g.nz * 6 * sizeof(T);
     if constexpr (std::is_same<T, float>::value) {
+        if (f128_yz(4, g.Py, g.nz)) {
+            bool st128 = false;
+            const size_t sm128 = f128_yz_smem(g.nz, g.Py, &st128);
+            if (g.nz == 8)
+                launch_pdl(yz128_kernel<T, 8>, grid, dim3(f128_yz_threads(8)), sm128, st, g, (int)st128);
+            else
+                launch_pdl(yz128_kernel<T, 4>, grid, dim3(f128_yz_threads(4)), sm128, st, g, (int)st128);
+            return;
+        }
 #define SS_CASE(P, Z)                                                   \
     if (g.Py == P && g.nz == Z) {                                       \
         launch_pdl(yz_kernel<T, P, Z>, grid, dim3(nthr), smem, st, g, stage); \
@@ -899,6 +1126,11 @@ void launch_xinv_step(const GroupArgs<T>& g, bool do_fft, T dt, int nthr, size_t
         return;
     }
     if constexpr (std::is_same<T, float>::value) {
+        if (f128_x(4, g.Px)) {
+            launch_pdl(xinv128_kernel<T, 0>, grid, dim3(f128_x_threads(g.ty_c)), f128_x_smem(g.ty_c, g.lsx), st, g, dt,
+                       (T*)nullptr);
+            return;
+        }
         switch (g.Px) {
 #define SS_CASE(P)                                                            \
     case P:                                                                   \
@@ -915,6 +1147,12 @@ void launch_xinv_step(const GroupArgs<T>& g, bool do_fft, T dt, int nthr, size_t
 template <typename T>
 void launch_xinv_eval(const GroupArgs<T>& g, bool do_fft, T* hout, int nthr, size_t smem, cudaStream_t st) {
     dim3 grid((g.ny + g.ty_c - 1) / g.ty_c, g.nz, g.n_pairs);
+    if constexpr (std::is_same<T, float>::value) {
+        if (do_fft && f128_x(4, g.Px)) {
+            xinv128_kernel<T, 1><<<grid, f128_x_threads(g.ty_c), f128_x_smem(g.ty_c, g.lsx), st>>>(g, T(0), hout);
+            return;
+        }
+    }
     if (do_fft) {
         xinv_kernel<T, true, 1, 0><<<grid, nthr, smem, st>>>(g, T(0), hout);
     } else {
@@ -962,6 +1200,11 @@ template <typename T> void set_smem_limits(int bytes) {
     cudaFuncSetAttribute(xinv_kernel<T, false, 0, 0>, attr, bytes);
     cudaFuncSetAttribute(xinv_kernel<T, false, 1, 0>, attr, bytes);
     if constexpr (std::is_same<T, float>::value) {
+        cudaFuncSetAttribute(xinv128_kernel<T, 1>, attr, bytes);
+        cudaFuncSetAttribute(xfwd128_kernel<T>, attr, bytes);
+        cudaFuncSetAttribute(xinv128_kernel<T, 0>, attr, bytes);
+        cudaFuncSetAttribute(yz128_kernel<T, 4>, attr, bytes);
+        cudaFuncSetAttribute(yz128_kernel<T, 8>, attr, bytes);
 #define SS_CASE(P)                                                       \
     cudaFuncSetAttribute(xfwd_kernel<T, true, P>, attr, bytes);          \
     cudaFuncSetAttribute(xinv_kernel<T, true, 0, P>, attr, bytes);

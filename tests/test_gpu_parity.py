@@ -2,7 +2,8 @@
 
 Tolerances:
   * field (Eqs. 2-7): max |h_gpu - h_oracle| <= 1e-5 * max |h_oracle| on the FP32 path, 1e-12 on FP64;
-  * energies (Eq. 8) evaluated on the same stored state: |dE| <= 1e-6 (units of J) on FP32, 1e-9 on FP64;
+  * energies (Eq. 8) evaluated on the same stored state: |dE| <= w * (the FFT round-off bound of the
+    dipole term derived in test_energy_and_terms_parity) + 1e-9;
   * trajectories (Sec. III loop): final path and barrier against the oracle run from the GPU's own
     starting state, with bounds stated in each test.
 """
@@ -39,7 +40,27 @@ FIELD_CASES = [
     (33, 10, 1, 1.0, 0.3, 0.05, 0.02, 2),   # padded length 72 = 8*9
     (20, 21, 5, 1.0, 0.25, 0.1, 0.02, 3),   # rows not a multiple of the CTA row count
     (9, 9, 4, 1.0, 0.0, 0.0, 0.5, 2),       # dipole only, strong
+    # padded length 128 along x and/or y: the two-pass register transforms (FP32)
+    (64, 64, 4, 1.0, 0.3, 0.05, 0.02, 2),   # x and y/z kernels, nz = 4
+    (57, 61, 8, 1.0, 0.3, 0.05, 0.03, 3),   # ragged x and y, nz = 8, odd image count
+    (60, 20, 3, 1.0, 0.3, 0.05, 0.02, 2),   # x kernels only (Py = 48), ragged CTA rows
+    (20, 58, 4, 0.9, -0.3, 0.05, 0.04, 2),  # y/z kernel only (Px = 48)
 ]
+
+
+def _padded(n):
+    """Smallest 2^a 3^b >= 2n - 1 (the zero-padded transform length)."""
+    m = 2 * n - 1
+    best = None
+    a = 1
+    while a < 4 * m:
+        b = a
+        while b < 4 * m:
+            if b >= m and (best is None or b < best):
+                best = b
+            b *= 3
+        a *= 2
+    return best
 
 
 @pytest.mark.parametrize("prec", [FP32, FP64])
@@ -57,24 +78,34 @@ def test_field_parity(ss, case, prec):
 
 
 @pytest.mark.parametrize("prec", [FP32, FP64])
-def test_energy_and_terms_parity(ss, prec):
-    case = (12, 10, 3, 1.0, 0.3, 0.05, 0.02, 4)
+@pytest.mark.parametrize("case", [(12, 10, 3, 1.0, 0.3, 0.05, 0.02, 4), (60, 58, 4, 1.0, 0.3, 0.05, 0.02, 2)])
+def test_energy_and_terms_parity(ss, case, prec):
     m = _model(case)
-    path = W.random_spins((4, 360, 3), seed=3)
+    path = W.random_spins((case[7], case[0] * case[1] * case[2], 3), seed=3)
+    n_img = case[7]
     with _sm(ss, [case], precision=prec) as sm:
         sm.set_path(0, path)
         state = _unit(sm.get_path(0))
         e = sm.energies(0)
-        grads = [sm.grad(0, k) for k in range(4)]
-    tol = 1e-6 if prec == FP32 else 1e-9
+        grads = [sm.grad(0, k) for k in range(n_img)]
     e_ref = oracle.energies(m, state)
-    np.testing.assert_allclose(e, e_ref, rtol=0, atol=tol)
     h_ref = oracle.field(m, state)
+    nx, ny, nz, w = case[0], case[1], case[2], case[6]
+    # The J, D, K terms are FP64 sums over the stored spins (atol 1e-9).  The unit-w dipole term
+    # t_w = -(1/2) sum_i conv_i . s_i is an FP64 sum of the convolution computed in the path's
+    # precision, whose round-off is bounded by ||d conv||_2 <= eps ||conv||_2 with
+    # eps = u (2 log2(Px Py) + 3 nz + 4) (forward and inverse 2-D FFTs, the z sum over 3 nz lines, the
+    # pair packing); by Cauchy-Schwarz over unit spins |d t_w| <= (1/2) eps ||conv||_2 sqrt(N), and the
+    # energy (Eq. 1) inherits w times that.  1e-9 covers the FP64 rounding of the sums on both sides.
+    u = 2.0 ** -24 if prec == FP32 else 2.0 ** -53
+    eps = u * (2 * np.log2(_padded(nx) * _padded(ny)) + 3 * nz + 4)
     for k, (ds, terms) in enumerate(grads):
         ref_terms = oracle.energy_param_grad(m, state[k])
-        # J, D, K terms are FP64 sums; the unit-w dipole term comes from the FP32 FFT convolution
-        np.testing.assert_allclose(terms[:3], ref_terms[:3], rtol=0, atol=tol)
-        assert abs(terms[3] - ref_terms[3]) <= (1e-7 if prec == FP32 else 1e-12) * abs(ref_terms[3]) + tol
+        np.testing.assert_allclose(terms[:3], ref_terms[:3], rtol=0, atol=1e-9)
+        conv = oracle.dipole_field(m, state[k]) / w
+        tol_w = 0.5 * eps * np.linalg.norm(conv) * np.sqrt(state.shape[1])
+        assert abs(terms[3] - ref_terms[3]) <= tol_w + 1e-9, (terms[3], ref_terms[3], tol_w)
+        assert abs(e[k] - e_ref[k]) <= w * tol_w + 1e-9, (k, e[k], e_ref[k], w * tol_w)
         assert np.abs(ds + h_ref[k]).max() <= (1e-5 if prec == FP32 else 1e-12) * np.abs(h_ref[k]).max()
 
 
