@@ -39,10 +39,9 @@ L2_FLUSH_BYTES = 256 << 20
 #   xfwd: read sp 12, write s 12, write the pair spectrum 3 * 8 * (Px/nx) / 2 per image = 24
 #   yz:   read + write the pair spectrum 24 + 24 (plus the tensor octant once per launch)
 #   xinv: read the spectrum 24, read s 12, write sp 12
-#   arc:  read sp 12
-#   reparam: per-image partial sums only (no per-site traffic)
-KERNEL_NAMES = ("xfwd", "yz", "xinv", "arc", "reparam")
-BYTES_PER_SITE_IMAGE = {"xfwd": 48, "yz": 48, "xinv": 48, "arc": 12, "reparam": 0}
+#   arc:  read sp 12 (its last CTAs then reduce per-image partials and write the interpolation table)
+KERNEL_NAMES = ("xfwd", "yz", "xinv", "arc")
+BYTES_PER_SITE_IMAGE = {"xfwd": 48, "yz": 48, "xinv": 48, "arc": 12}
 REF_IMAGES = 8
 
 

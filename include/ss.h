@@ -126,7 +126,7 @@ ss_status ss_energy_terms(ss_ctx* ctx, int string, double* out);
  * the context's stream, bracketed by CUDA events, for `reps` >= 1 timed iterations after one untimed
  * iteration.  ms_out[i] (host, up to max_out entries) receives the mean duration in milliseconds of
  * kernel i, in launch order: for each size group xfwd, yz (when the group has a dipole term), xinv,
- * arc, reparam.  *n_out receives the number of kernels.  The strings advance by reps + 1 iterations.
+ * arc (which also reparametrises).  *n_out receives the number of kernels.  The strings advance by reps + 1 iterations.
  * Synchronises. */
 ss_status ss_time_kernels(ss_ctx* ctx, int reps, double* ms_out, int max_out, int* n_out);
 

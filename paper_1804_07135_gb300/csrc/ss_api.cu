@@ -87,7 +87,8 @@ struct Group {
     InterpEntry* interp = nullptr;
     double* epart = nullptr;
     int *d_str_img0 = nullptr, *d_str_K = nullptr;
-    double *dpart = nullptr, *e_last = nullptr, *eval_terms = nullptr, *eval_E = nullptr;
+    double *dpart = nullptr, *dk = nullptr, *e_last = nullptr, *eval_terms = nullptr, *eval_E = nullptr;
+    unsigned* arc_cnt = nullptr;
     ArcArgs arc{};
 };
 
@@ -195,6 +196,10 @@ template <typename T> GroupArgs<T> group_args(const ss_ctx* c, const Group& g) {
 // they need.
 void set_rows(const ss_ctx* c, Group& g, int ty_a, int ty_c, int thr_a = 256, int thr_c = 256) {
     const size_t cs = 2 * real_size(c);
+    if (g.dipole && f128_x((int)real_size(c), g.Px)) {
+        ty_a = f128_x_rows(ty_a);
+        ty_c = f128_x_rows(ty_c);
+    }
     g.ty_a = ty_a;
     g.ty_c = ty_c;
     g.thr_a = thr_a;
@@ -204,8 +209,8 @@ void set_rows(const ss_ctx* c, Group& g, int ty_a, int ty_c, int thr_a = 256, in
     if (g.dipole && f128_x((int)real_size(c), g.Px)) {  // the launchers derive these shapes themselves
         g.thr_a = f128_x_threads(ty_a);
         g.thr_c = f128_x_threads(ty_c);
-        g.smem_a = f128_x_smem(ty_a, g.lsx);
-        g.smem_c = f128_x_smem(ty_c, g.lsx);
+        g.smem_a = f128_x_smem(ty_a);
+        g.smem_c = f128_x_smem(ty_c);
     }
     g.smem_c_eval = g.smem_c;
     g.n_eblk = g.nz * ((g.ny + g.ty_c - 1) / g.ty_c);
@@ -227,7 +232,7 @@ void configure_group(const ss_ctx* c, Group& g) {
             break;
         }
     }
-    if (g.dipole && f128_x((int)real_size(c), g.Px)) ty = std::min(8, g.ny);  // 384 threads
+    if (g.dipole && f128_x((int)real_size(c), g.Px)) ty = 8;  // 384 threads
     set_rows(c, g, ty, ty, 512, 512);
     // y/z kernel: all 3*nz lines of one (pair, kx) in shared memory, plus the kx slab of the tensor
     // spectrum when it is small enough to stage
@@ -337,6 +342,11 @@ template <typename T> ss_status setup_group(ss_ctx* c, Group& g) {
     TRY(dalloc(c, (void**)&g.d_str_K, nstr * sizeof(int)));
     TRY(dalloc(c, (void**)&g.dpart, (size_t)nstr * maxK * a.n_tiles * sizeof(double)));
     TRY(dalloc(c, (void**)&g.e_last, (size_t)nstr * maxK * sizeof(double)));
+    TRY(dalloc(c, (void**)&g.dk, (size_t)nstr * maxK * sizeof(double)));
+    const size_t n_cnt = (size_t)nstr * (a.n_kchunks + 1);
+    TRY(dalloc(c, (void**)&g.arc_cnt, n_cnt * sizeof(unsigned)));
+    CUDA_TRY(c, cudaMemsetAsync(g.arc_cnt, 0, n_cnt * sizeof(unsigned), c->cs));
+    CUDA_TRY(c, cudaMemsetAsync(g.dk, 0, (size_t)nstr * maxK * sizeof(double), c->cs));
     TRY(dalloc(c, (void**)&g.eval_terms, (size_t)nstr * maxK * 4 * sizeof(double)));
     TRY(dalloc(c, (void**)&g.eval_E, (size_t)nstr * maxK * sizeof(double)));
     CUDA_TRY(c, cudaMemcpyAsync(g.d_str_img0, g.str_img0.data(), nstr * sizeof(int), cudaMemcpyHostToDevice, c->cs));
@@ -348,7 +358,9 @@ template <typename T> ss_status setup_group(ss_ctx* c, Group& g) {
     a.str_img0 = g.d_str_img0;
     a.str_K = g.d_str_K;
     a.dpart = g.dpart;
+    a.dk = g.dk;
     a.e_last = g.e_last;
+    a.cnt = g.arc_cnt;
     launch_interp_identity(g.interp, 0, g.n_img, c->cs);
     CUDA_TRY(c, cudaGetLastError());
     if (g.dipole) TRY(build_tensor_spectrum<T>(c, g));
@@ -374,7 +386,7 @@ template <typename T> ss_status tune_group(ss_ctx* c, Group& g) {
         const bool f128 = g.dipole && f128_x((int)real_size(c), g.Px);  // block size follows the rows
         if (sscanf(env, "%d:%d:%d:%d", &ta, &ya, &tc, &yc) == 4 &&
             (f128 || ((ta == 256 || ta == 512) && (tc == 256 || tc == 512))) && ya >= 1 && yc >= 1 && ya <= g.ny &&
-            yc <= g.ny && (!f128 || (ya <= 10 && yc <= 10))) {
+            yc <= g.ny) {  // the x kernels for Px = 128 take 2, 4 or 8 rows (others become 8)
             set_rows(c, g, ya, yc, ta, tc);
             return SS_OK;
         }
@@ -392,8 +404,8 @@ template <typename T> ss_status tune_group(ss_ctx* c, Group& g) {
     const size_t cs = 2 * real_size(c);
     std::vector<std::pair<int, int>> cands;  // (threads, rows)
     if (g.dipole && f128_x((int)real_size(c), g.Px)) {
-        for (int ty : {2, 4, 5, 8, 10})  // 48 threads per row, at most 480
-            if (ty <= g.ny) cands.push_back({f128_x_threads(ty), ty});
+        for (int ty : {2, 4, 8})  // 48 threads per row; row counts that divide 16 keep the passes conflict-free
+            cands.push_back({f128_x_threads(ty), ty});
     } else {
         for (int thr : {256, 512})
             for (int ty : {1, 2, 4, 5, 8, 10, 16})
@@ -458,7 +470,6 @@ template <typename T> void issue_iteration(ss_ctx* c, cudaStream_t st) {
         if (g.dipole) launch_yz<T>(a, g.thr_b, g.smem_b, st);
         launch_xinv_step<T>(a, g.dipole, dt, g.thr_c, g.smem_c, st);
         launch_arc<T>(a, g.arc, g.thr_arc, st);
-        launch_reparam<T>(a, g.arc, st);
     }
 }
 
@@ -896,17 +907,15 @@ ss_status ss_time_kernels(ss_ctx* c, int reps, double* ms_out, int max_out, int*
                     if (which == 1) launch_yz<double>(a, g.thr_b, g.smem_b, c->cs);
                     if (which == 2) launch_xinv_step<double>(a, g.dipole, c->opts.dt, g.thr_c, g.smem_c, c->cs);
                     if (which == 3) launch_arc<double>(a, g.arc, g.thr_arc, c->cs);
-                    if (which == 4) launch_reparam<double>(a, g.arc, c->cs);
                 } else {
                     GroupArgs<float> a = group_args<float>(c, g);
                     if (which == 0) launch_xfwd<float>(a, g.dipole, g.thr_a, g.smem_a, c->cs);
                     if (which == 1) launch_yz<float>(a, g.thr_b, g.smem_b, c->cs);
                     if (which == 2) launch_xinv_step<float>(a, g.dipole, (float)c->opts.dt, g.thr_c, g.smem_c, c->cs);
                     if (which == 3) launch_arc<float>(a, g.arc, g.thr_arc, c->cs);
-                    if (which == 4) launch_reparam<float>(a, g.arc, c->cs);
                 }
             };
-            for (int which = 0; which < 5; ++which) {
+            for (int which = 0; which < 4; ++which) {
                 if (which == 1 && !g.dipole) continue;
                 cudaEventRecord(ev[2 * k], c->cs);
                 run(which);
@@ -952,7 +961,7 @@ ss_status ss_string_info(const ss_ctx* c, int string, ss_string_desc* out) {
 int ss_kernels_per_iteration(const ss_ctx* c) {
     if (!c) return 0;
     int n = 0;
-    for (const Group& g : c->groups) n += g.dipole ? 5 : 4;
+    for (const Group& g : c->groups) n += g.dipole ? 4 : 3;
     return n;
 }
 

@@ -375,9 +375,17 @@ template <typename C, typename W> inline void fft_stage_twiddles(const FftPlan& 
 // pass 2, role k1:        X[k1 + 16 k2] = DFT8(Z[.][k1])[k2].
 // A line with a zero upper half (x[n] = 0 for n >= 64) drops the second term of u; a transform read
 // only below 64 evaluates k2 < 4 in pass 2 (the other outputs are dead code).
-// kF128Line (ss_internal.h): line stride of the exchange buffer Z[line][n2][k1] (complex elements)
-constexpr int kF128N2 = 18;  // n2 stride: 16 lanes (n2, par) or (k1) of one line hit 16 distinct bank pairs
-__host__ __device__ constexpr int f128_pos(int line, int n2, int k1) { return line * kF128Line + n2 * kF128N2 + k1; }
+// Exchange buffer Z[line][n2][k1] at line * kF128Line + n2 * kF128N2 + k1 (kF128Line = 1 mod 16, in
+// ss_internal.h): the 16 lanes of a half-warp reading 16 consecutive k1 of one line, or writing 8 n2 of
+// two consecutive lines (pass-1 roles below), touch 16 distinct bank pairs.
+constexpr int kF128N2 = 18;
+// Pass-1 role r -> (line, n2, par): n2 = r & 7, then four consecutive lines, then par, so par is uniform
+// across a warp; lines are taken in groups of four (callers skip line >= their count).
+__device__ __forceinline__ void f128_role1(int r, int& line, int& n2, int& par) {
+    n2 = r & 7;
+    par = (r >> 5) & 1;
+    line = ((r >> 6) << 2) | ((r >> 3) & 3);
+}
 
 // a * W_16^J for a compile-time J < 8, W_16 = exp(-2 pi i / 16)
 template <int J, typename C> __device__ __forceinline__ C mul_w16(C a) {

@@ -96,7 +96,9 @@ struct ArcArgs {
     int kchunk;            // image differences per CTA along the string
     int n_kchunks;
     double* dpart;         // [n_str][n_tiles][maxK] squared-distance partials
+    double* dk;            // [n_str][maxK] image distances d_k (k >= 1)
     double* e_last;        // [n_str][maxK] energies of the state before the step
+    unsigned* cnt;         // [n_str][n_kchunks] tile tickets, then [n_str] chunk tickets; zero between launches
     int reparam;           // 0: keep images where they are
 };
 
@@ -105,12 +107,16 @@ enum { kErrInvalidSpin = 1, kErrNonFinite = 2 };
 // Length-128 transforms in two register passes (FP32): the x kernels when Px = 128, the y/z kernel
 // when Py = 128 and nz is 4 or 8.  16 threads per line; their launch shapes follow from the rows per
 // CTA (x kernels) or from nz (y/z kernel), whatever block size and shared memory the caller passes.
-constexpr int kF128Line = 146;  // line stride of their exchange buffers (complex elements)
+constexpr int kF128Line = 145;  // line stride of their exchange buffers (complex elements, 1 mod 16)
+constexpr int kF128Buf = 72;    // line stride of the x kernels' 64-point lines (fft_pad positions, 8 mod 16)
 inline bool f128_x(int real_bytes, int Px) { return real_bytes == 4 && Px == 128; }
 inline bool f128_yz(int real_bytes, int Py, int nz) { return real_bytes == 4 && Py == 128 && (nz == 4 || nz == 8); }
+// rows per CTA of the x kernels: 2, 4 or 8 (compile-time); anything else is taken as 8
+inline int f128_x_rows(int ty) { return ty == 2 || ty == 4 ? ty : 8; }
 inline int f128_x_threads(int rows) { return 48 * rows; }
-inline size_t f128_x_smem(int rows, int lsx) {
-    return (size_t)3 * rows * (lsx + kF128Line) * 8 + 32 * 8 * sizeof(double);  // + reduction scratch
+inline size_t f128_x_smem(int rows) {
+    // line buffer, exchange buffer (lines rounded up to a multiple of 4), reduction scratch
+    return (size_t)(3 * rows * kF128Buf + (3 * rows + 3) / 4 * 4 * kF128Line) * 8 + 32 * 8 * sizeof(double);
 }
 inline int f128_yz_threads(int nz) { return 48 * nz; }
 inline size_t f128_yz_smem(int nz, int Py, bool* stage_dhat) {
@@ -127,7 +133,6 @@ void launch_xinv_step(const GroupArgs<T>& g, bool do_fft, T dt, int nthr, size_t
 template <typename T>
 void launch_xinv_eval(const GroupArgs<T>& g, bool do_fft, T* hout, int nthr, size_t smem, cudaStream_t st);
 template <typename T> void launch_arc(const GroupArgs<T>& g, const ArcArgs& a, int nthr, cudaStream_t st);
-template <typename T> void launch_reparam(const GroupArgs<T>& g, const ArcArgs& a, cudaStream_t st);
 template <typename T>
 void launch_eval_reduce(const GroupArgs<T>& g, const ArcArgs& a, double* terms, double* energies, cudaStream_t st);
 template <typename T, typename Tin>

@@ -103,14 +103,19 @@ __device__ __forceinline__ void griddep_launch_dependents() { asm volatile("grid
 
 // ------------------------------------------------------------------------------------------------
 // Gather of rows [y0, y0+rows) of layer z for pair p: s[img] = normalise((1-t) sp[src0] + t sp[src1])
-// (or a copy), written back to s and, when buf is given, to line c*rows + yy of buf (stride lsx,
+// (or a copy), written back to s and, when buf is given, to line c*lrows + yy of buf (stride ls,
 // fft_pad positions) as re/im of the pair.
 template <typename T>
-__device__ __forceinline__ void xfwd_gather(const GroupArgs<T>& g, cplx<T>* buf, int p, int z, int y0, int rows,
-                                            int tid, int nthr) {
+__device__ __forceinline__ void xfwd_gather(const GroupArgs<T>& g, cplx<T>* buf, int ls, int lrows, int p, int z,
+                                            int y0, int rows, int tid, int nthr) {
     using C = cplx<T>;
     const int nx = g.nx, N = g.N;
     const int ia = 2 * p;
+    // the pair's two table entries, loaded once (the stores below could alias them for the compiler)
+    InterpEntry ent[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+        if (ia + h < g.n_img) ent[h] = g.interp[ia + h];
     for (int it = tid; it < rows * nx; it += nthr) {
         const int yy = it / nx, x = it - yy * nx;
         const int site = (z * g.ny + y0 + yy) * nx + x;
@@ -120,7 +125,7 @@ __device__ __forceinline__ void xfwd_gather(const GroupArgs<T>& g, cplx<T>* buf,
             const int im = ia + h;
             out[h][0] = out[h][1] = out[h][2] = T(0);
             if (im < g.n_img) {
-                const InterpEntry e = g.interp[im];
+                const InterpEntry& e = ent[h];
                 const T* a = g.sp + (size_t)e.src0 * 3 * N + site;
                 T u0 = a[0], u1 = a[N], u2 = a[2 * N];
                 if (!e.copy) {
@@ -146,7 +151,7 @@ __device__ __forceinline__ void xfwd_gather(const GroupArgs<T>& g, cplx<T>* buf,
         }
         if (buf) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) buf[(c * rows + yy) * g.lsx + fft_pad(x)] = C{out[0][c], out[1][c]};
+            for (int c = 0; c < 3; ++c) buf[(c * lrows + yy) * ls + fft_pad(x)] = C{out[0][c], out[1][c]};
         }
     }
 }
@@ -169,7 +174,7 @@ __global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xfwd_kernel(GroupAr
         for (int i = tid; i < g.Px; i += nthr) tw[i] = PX > 0 ? g.twxs[i] : g.twx[i];
     griddep_wait();
     griddep_launch_dependents();
-    xfwd_gather(g, DO_FFT ? buf : (C*)nullptr, p, z, y0, rows, tid, nthr);
+    xfwd_gather(g, DO_FFT ? buf : (C*)nullptr, g.lsx, rows, p, z, y0, rows, tid, nthr);
     if (!DO_FFT) return;
     const int padw = g.Px - nx;
     for (int it = tid; it < 3 * rows * padw; it += nthr) {
@@ -189,41 +194,49 @@ __global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xfwd_kernel(GroupAr
     }
 }
 
-// xfwd for Px = 128 (nx <= 64): the same gather, then the x-transform of the 3*rows lines in two
-// register passes (f128_pass1/2) with 16 roles per line; the second pass writes the spectrum straight
-// to global memory, rows fastest across a warp (the rows of one (kx, c) are contiguous there).
-template <typename T>
+// xfwd for Px = 128 (nx <= 64), ROWS (2, 4 or 8) rows per CTA: the same gather, then the x-transform of
+// the 3*ROWS lines in two register passes (f128_pass1/2) with 16 roles per line; the second pass writes
+// the spectrum straight to global memory, rows fastest across a warp (the rows of one (kx, c) are
+// contiguous there).  Rows past ny (last CTA) are skipped.
+template <typename T, int ROWS>
 __global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xfwd128_kernel(GroupArgs<T> g) {
     using C = cplx<T>;
+    static_assert(16 % ROWS == 0, "the pass-2 role permutation needs ROWS | 16");
+    constexpr int L = 3 * ROWS, NQ = 16 / ROWS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int rows_max = g.ty_a;
-    C* buf = reinterpret_cast<C*>(smem_raw);  // 3*rows lines, stride lsx, fft_pad positions
-    C* zx = buf + 3 * rows_max * g.lsx;       // exchange buffer, 3*rows lines of kF128Line
+    C* buf = reinterpret_cast<C*>(smem_raw);  // L lines of kF128Buf, fft_pad positions
+    C* zx = buf + L * kF128Buf;                // exchange buffer
     const int tid = threadIdx.x, nthr = blockDim.x;
-    const int p = blockIdx.z, z = blockIdx.y, y0 = blockIdx.x * rows_max;
-    const int rows = min(rows_max, g.ny - y0);
-    const int nx = g.nx, L = 3 * rows;
+    const int p = blockIdx.z, z = blockIdx.y, y0 = blockIdx.x * ROWS;
+    const int rows = min(ROWS, g.ny - y0);
+    const int nx = g.nx;
     const C* __restrict__ tw = g.twx;  // W_128^k
     griddep_wait();
     griddep_launch_dependents();
-    xfwd_gather(g, buf, p, z, y0, rows, tid, nthr);
+    xfwd_gather(g, buf, kF128Buf, ROWS, p, z, y0, rows, tid, nthr);
     __syncthreads();
-    for (int r = tid; r < 16 * L; r += nthr) {
-        const int par = r & 1, n2 = (r >> 1) & 7, line = r >> 4;
-        const C* b = buf + line * g.lsx;
+    for (int r = tid; r < 16 * ((L + 3) & ~3); r += nthr) {
+        int line, n2, par;
+        f128_role1(r, line, n2, par);
+        if (line >= L || line % ROWS >= rows) continue;
+        const C* b = buf + line * kF128Buf;
         C u[8];
 #pragma unroll
         for (int n1 = 0; n1 < 8; ++n1) u[n1] = 8 * n1 + n2 < nx ? b[fft_pad(8 * n1 + n2)] : C{T(0), T(0)};
         f128_pass1<false>(u, u, n2, par, tw, zx + line * kF128Line);
     }
     __syncthreads();
+    // pass 2: role (c, j, yy), yy fastest; k1 = a permutation of j that puts a half-warp's 16 reads (rows
+    // yy, k1 spaced by ROWS) in distinct banks
     const size_t kstride = (size_t)3 * g.nz * g.ny;  // between consecutive kx
     C* outp = g.spec + (size_t)p * 128 * kstride + (size_t)z * g.ny + y0;
     for (int r = tid; r < 16 * L; r += nthr) {
-        const int c = r / (16 * rows), rem = r - c * 16 * rows;
-        const int k1 = rem / rows, yy = rem - k1 * rows;
+        const int c = r / (16 * ROWS), rem = r % (16 * ROWS);
+        const int j = rem / ROWS, yy = rem % ROWS;
+        if (yy >= rows) continue;
+        const int k1 = (j % NQ) * ROWS + j / NQ;
         C v[8];
-        f128_pass2(v, zx + (c * rows + yy) * kF128Line, k1);
+        f128_pass2(v, zx + (c * ROWS + yy) * kF128Line, k1);
         C* o = outp + (size_t)k1 * kstride + (size_t)c * g.nz * g.ny + yy;
 #pragma unroll
         for (int k2 = 0; k2 < 8; ++k2) o[(size_t)16 * k2 * kstride] = v[k2];
@@ -465,11 +478,12 @@ __global__ void __launch_bounds__(kMaxThreadsYz, kMinBlocksYz) yz_kernel(GroupAr
 // (f128_pass1/2, 16 roles per line, 16 * 3 * NZ threads) around the z-convolution.  Two shared
 // regions of 3*NZ lines alternate: R1 = forward exchange, then the z-convolution output; R2 = forward
 // output (z-convolution input, stride kLz), then the inverse exchange.
-constexpr int kLz = 136;  // line stride of the z-convolution input/output ([line][ky])
+constexpr int kLz = 136;  // line stride of the z-convolution input/output ([line][ky], 8 mod 16)
 template <typename T, int NZ>
 __global__ void __launch_bounds__(kMaxThreadsYz, kMinBlocksYz) yz128_kernel(GroupArgs<T> g, int stage_dhat) {
     using C = cplx<T>;
     constexpr int L = 3 * NZ, hy = 64;
+    static_assert(L % 4 == 0, "pass-1 roles take lines in groups of four");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* R1 = reinterpret_cast<C*>(smem_raw);
     C* R2 = R1 + L * kF128Line;
@@ -488,7 +502,8 @@ __global__ void __launch_bounds__(kMaxThreadsYz, kMinBlocksYz) yz128_kernel(Grou
     griddep_wait();
     griddep_launch_dependents();
     for (int r = tid; r < 16 * L; r += nthr) {
-        const int par = r & 1, n2 = (r >> 1) & 7, line = r >> 4;
+        int line, n2, par;
+        f128_role1(r, line, n2, par);
         const C* src = blk + (size_t)line * ny + n2;
         C u[8];
 #pragma unroll
@@ -508,7 +523,8 @@ __global__ void __launch_bounds__(kMaxThreadsYz, kMinBlocksYz) yz128_kernel(Grou
     zconv_c<NZ, false>(R2, R1, kLz, 128, kx, g.Px, dslab, 1, hy + 1, tid, nthr);
     __syncthreads();
     for (int r = tid; r < 16 * L; r += nthr) {
-        const int par = r & 1, n2 = (r >> 1) & 7, line = r >> 4;
+        int line, n2, par;
+        f128_role1(r, line, n2, par);
         const C* b = R1 + line * kLz + n2;
         C u[8], hi[8];
 #pragma unroll
@@ -535,8 +551,8 @@ __global__ void __launch_bounds__(kMaxThreadsYz, kMinBlocksYz) yz128_kernel(Grou
 // forward transforms of the conjugated field spectra (line c*rows + yy, fft_pad positions) when
 // HAS_CONV.
 template <typename T, bool HAS_CONV, int MODE>
-__device__ __forceinline__ void xinv_sites(const GroupArgs<T>& g, T dt, T* hout, const cplx<T>* buf, double* red,
-                                           int p, int z, int y0, int rows, int tid, int nthr) {
+__device__ __forceinline__ void xinv_sites(const GroupArgs<T>& g, T dt, T* hout, const cplx<T>* buf, int ls,
+                                           double* red, int p, int z, int y0, int rows, int tid, int nthr) {
     using C = cplx<T>;
     const int nx = g.nx, ny = g.ny, nz = g.nz, N = g.N;
     const int ia = 2 * p;
@@ -574,7 +590,7 @@ __device__ __forceinline__ void xinv_sites(const GroupArgs<T>& g, T dt, T* hout,
         if (HAS_CONV) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const C v = buf[(c * rows + yy) * g.lsx + fft_pad(x)];
+                const C v = buf[(c * rows + yy) * ls + fft_pad(x)];
                 conv[c] = h == 0 ? v.x : -v.y;  // conjugate of the forward transform of the conjugate
             }
         }
@@ -690,32 +706,37 @@ __global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xinv_kernel(GroupAr
         __syncthreads();
         fft_lines_any<PX, false, true>(buf, tw, g.planx, g.lsx, 3 * rows, tid, nthr);
     }
-    xinv_sites<T, DO_FFT, MODE>(g, dt, hout, buf, red, p, z, y0, rows, tid, nthr);
+    xinv_sites<T, DO_FFT, MODE>(g, dt, hout, buf, g.lsx, red, p, z, y0, rows, tid, nthr);
 }
 
-// xinv for Px = 128 (nx <= 64): the inverse x-transform (a forward transform of the conjugate) of the
-// 3*rows lines in two register passes, inputs read straight from the spectrum (rows fastest across a
-// warp), outputs x < 64 into buf; then the same per-site work as xinv_kernel.
-template <typename T, int MODE>
+// xinv for Px = 128 (nx <= 64), ROWS (2, 4 or 8) rows per CTA: the inverse x-transform (a forward
+// transform of the conjugate) of the 3*ROWS lines in two register passes, inputs read straight from the
+// spectrum (rows fastest across a warp), outputs x < 64 into buf; then the same per-site work as
+// xinv_kernel.  Rows past ny (last CTA) are skipped.
+template <typename T, int MODE, int ROWS>
 __global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xinv128_kernel(GroupArgs<T> g, T dt, T* hout) {
     using C = cplx<T>;
+    static_assert(16 % ROWS == 0 && ROWS >= 2, "the pass-1 role permutation needs ROWS in {2, 4, 8, 16}");
+    constexpr int L = 3 * ROWS, NQ = 16 / ROWS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int rows_max = g.ty_c;
-    C* buf = reinterpret_cast<C*>(smem_raw);  // 3*rows lines, stride lsx, fft_pad positions
-    C* zx = buf + 3 * rows_max * g.lsx;       // exchange buffer, 3*rows lines of kF128Line
-    double* red = reinterpret_cast<double*>(zx + 3 * rows_max * kF128Line);
+    C* buf = reinterpret_cast<C*>(smem_raw);  // L lines of kF128Buf, fft_pad positions
+    C* zx = buf + L * kF128Buf;                // exchange buffer
+    double* red = reinterpret_cast<double*>(zx + (L + 3) / 4 * 4 * kF128Line);
     const int tid = threadIdx.x, nthr = blockDim.x;
-    const int p = blockIdx.z, z = blockIdx.y, y0 = blockIdx.x * rows_max;
-    const int rows = min(rows_max, g.ny - y0);
-    const int L = 3 * rows;
-    const C* __restrict__ tw = g.twx;  // W_128^k
+    const int p = blockIdx.z, z = blockIdx.y, y0 = blockIdx.x * ROWS;
+    const int rows = min(ROWS, g.ny - y0);
     const size_t kstride = (size_t)3 * g.nz * g.ny;  // between consecutive kx
     const C* inp = g.spec + (size_t)p * 128 * kstride + (size_t)z * g.ny + y0;
+    const C* __restrict__ tw = g.twx;  // W_128^k
     griddep_wait();
     griddep_launch_dependents();
+    // pass 1: role (c, par, j, yy), yy fastest, then j (n2 a permutation of j that puts a half-warp's
+    // stores in distinct banks), so par is uniform across a warp for ROWS >= 4
     for (int r = tid; r < 16 * L; r += nthr) {
-        const int t = r / rows, yy = r - t * rows;
-        const int par = t & 1, n2 = (t >> 1) & 7, c = t >> 4;
+        const int t = r / ROWS, yy = r % ROWS;
+        if (yy >= rows) continue;
+        const int j = t & 7, par = (t >> 3) & 1, c = t >> 4;
+        const int n2 = (j % NQ) * (8 / NQ) + j / NQ;
         const C* s = inp + (size_t)n2 * kstride + (size_t)c * g.nz * g.ny + yy;  // kx = 8 n1 + n2
         C u[8], hi[8];
 #pragma unroll
@@ -723,44 +744,78 @@ __global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xinv128_kernel(Grou
             u[n1] = cconj(s[(size_t)8 * n1 * kstride]);
             hi[n1] = cconj(s[(size_t)(8 * n1 + 64) * kstride]);
         }
-        f128_pass1<true>(u, hi, n2, par, tw, zx + (c * rows + yy) * kF128Line);
+        f128_pass1<true>(u, hi, n2, par, tw, zx + (c * ROWS + yy) * kF128Line);
     }
     __syncthreads();
     for (int r = tid; r < 16 * L; r += nthr) {
         const int k1 = r & 15, line = r >> 4;
+        if (line % ROWS >= rows) continue;
         C v[8];
         f128_pass2(v, zx + line * kF128Line, k1);
-        C* b = buf + line * g.lsx;
+        C* b = buf + (line / ROWS * rows + line % ROWS) * kF128Buf;  // xinv_sites reads line c*rows + yy
 #pragma unroll
         for (int k2 = 0; k2 < 4; ++k2) b[fft_pad(k1 + 16 * k2)] = v[k2];
     }
     __syncthreads();
-    xinv_sites<T, true, MODE>(g, dt, hout, buf, red, p, z, y0, rows, tid, nthr);
+    xinv_sites<T, true, MODE>(g, dt, hout, buf, kF128Buf, red, p, z, y0, rows, tid, nthr);
 }
 
 // ------------------------------------------------------------------------------------------------
-// arc: grid (n_tiles, n_kchunks, n_str).  Squared distances |sp_k - sp_{k-1}|^2 over all 3N
-// components (Eq. 11), one partial per (string, k, tile), summed in T per thread and warp, in FP64
-// across warps.
+// arc: grid (n_tiles, n_kchunks, n_str), 256 threads.  Squared distances |sp_k - sp_{k-1}|^2 over all
+// 3N components (Eq. 11), one partial per (string, k, tile), summed in T per thread and warp, in FP64
+// across warps.  Then, without another launch:
+//  * the last tile CTA of each (string, chunk) to finish (ticket counter) sums the tile partials of
+//    the chunk's differences in FP64 and tile order, d_k = sqrt(.), and the step kernel's energy
+//    partials of the chunk's images (e_last);
+//  * the last chunk CTA of the string to finish scans the d_k into the arc length s_k (Eq. 11),
+//    alpha*_k = s_k / s_{K-1} (Eq. 12), and for every interior image k finds the largest j with
+//    alpha*_j <= k/(K-1) and t: the interpolation table the next xfwd applies.
+// Nothing waits on another CTA; the counters are back at zero when the launch ends.  GB300 issues
+// FP64 at a low rate, so the FP64 work is spread over the chunk CTAs and kept to few warp instructions.
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;  // lane 0
+}
+
 template <typename T>
-__global__ void __launch_bounds__(256) arc_kernel(GroupArgs<T> g, ArcArgs a) {
+__global__ void __launch_bounds__(256, 3) arc_kernel(GroupArgs<T> g, ArcArgs a) {
     __shared__ double red[32 * kArcMaxChunk];
-    const int tid = threadIdx.x, nthr = blockDim.x;
-    const int str = blockIdx.z;
+    __shared__ double alpha[kArcMaxK];
+    __shared__ double wsum[32];
+    __shared__ int s_flag;
+    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
+    const int str = blockIdx.z, chunk = blockIdx.y;
     const int K = a.str_K[str], img0 = a.str_img0[str];
-    const int k_lo = blockIdx.y * a.kchunk;
+    const int n_act = max(1, (K - 2 + a.kchunk) / a.kchunk);  // chunks this string uses (one when K = 1)
+    const int k_lo = chunk * a.kchunk;
     const int nd = max(0, min(a.kchunk, K - 1 - k_lo));  // differences (k_lo+i, k_lo+i+1), i < nd
     griddep_wait();
     griddep_launch_dependents();
-    if (nd == 0) return;  // uniform over the block
+    if (chunk >= n_act) return;  // uniform over the block
+    const size_t sb = (size_t)str * a.maxK;
+    if (blockIdx.x == 0) {
+        // e_last of the chunk's images from the step kernel's partials (no dependence on the distances,
+        // so one tile CTA per chunk does it before its own share)
+        const int k_hi = chunk == n_act - 1 ? K : k_lo + a.kchunk;
+        for (int k = k_lo + warp; k < k_hi; k += nwarp) {
+            const double* ep = g.epart + img0 + k;  // [block][image]
+            double e = 0.0;
+            for (int b = lane; b < g.n_eblk; b += 32) e += ep[(size_t)b * g.n_img];
+            e = warp_sum_d(e);
+            if (lane == 0) {
+                if (!isfinite(e)) atomicOr(g.err, kErrNonFinite);
+                a.e_last[sb + k] = e;
+            }
+        }
+    }
     const size_t M = (size_t)3 * g.N;
     const size_t e0 = (size_t)blockIdx.x * a.tile_elems;
     const size_t e1 = min(M, e0 + a.tile_elems);
-    double acc[kArcMaxChunk];
     T part[kArcMaxChunk];  // the thread's few squared differences per image pair, summed in T first
 #pragma unroll
     for (int i = 0; i < kArcMaxChunk; ++i) part[i] = T(0);
-    if (sizeof(T) == 4 && (M & 3) == 0 && (e0 & 3) == 0) {
+    if (nd > 0 && sizeof(T) == 4 && (M & 3) == 0 && (e0 & 3) == 0) {
         // four components per thread and load: 16-byte loads of every image of the chunk up front
         const float4* base = reinterpret_cast<const float4*>(g.sp + (size_t)(img0 + k_lo) * M);
         const size_t M4 = M >> 2;
@@ -778,7 +833,7 @@ __global__ void __launch_bounds__(256) arc_kernel(GroupArgs<T> g, ArcArgs a) {
                 }
             }
         }
-    } else {
+    } else if (nd > 0) {
         for (size_t e = e0 + tid; e < e1; e += nthr) {
             const T* col = g.sp + (size_t)(img0 + k_lo) * M + e;
             T prev = col[0];
@@ -793,122 +848,151 @@ __global__ void __launch_bounds__(256) arc_kernel(GroupArgs<T> g, ArcArgs a) {
             }
         }
     }
-    block_reduce_t2d<kArcMaxChunk>(part, acc, red);
-    if (tid == 0)
-        for (int i = 0; i < nd; ++i) a.dpart[((size_t)str * a.n_tiles + blockIdx.x) * a.maxK + k_lo + i + 1] = acc[i];
-}
-
-// reparam: grid (n_str), 1024 threads, one image per thread.  d_k = sqrt(sum over tiles of the
-// squared-distance partials) in FP64 and tile order; s_k by an inclusive block scan (Eq. 11);
-// alpha*_k = s_k / s_{K-1} (Eq. 12); for every interior image k the largest j with
-// alpha*_j <= k/(K-1) and t; writes the interpolation table the next xfwd applies.  GB300 issues
-// FP64 at a low rate, so each FP64 instruction here serves 32 images at once.
-template <typename T>
-__global__ void __launch_bounds__(1024) reparam_kernel(GroupArgs<T> g, ArcArgs a) {
-    __shared__ double alpha[kArcMaxK];
-    __shared__ double wsum[32];
-    const int tid = threadIdx.x, nthr = blockDim.x;
-    const int str = blockIdx.x;
-    const int K = a.str_K[str], img0 = a.str_img0[str];
-    const int lane = tid & 31, warp = tid >> 5, nwarp = (K + 31) >> 5;
-    // partial sums: warp w takes tiles (and step-kernel blocks) w, w+32, ... for 32 images at a time
-    // (lane = image), so the loads of all warps are in flight together; then warp k combines the 32
-    // warp partials of image k0+k by a fixed shuffle tree.  Fixed order throughout (deterministic).
-    __shared__ double pd[32][33], pe[32][33], dd[kArcMaxK];
-    griddep_wait();
-    griddep_launch_dependents();
-    for (int k0 = 0; k0 < K; k0 += 32) {
-        const int k = k0 + lane;
-        double d2 = 0.0, e = 0.0;
-        if (k < K) {
-            // [tile][image] and [block][image] layouts: a warp reads 32 consecutive images
-            if (k > 0) {
-                const double* dp = a.dpart + (size_t)str * a.n_tiles * a.maxK + k;
-                for (int t = warp; t < a.n_tiles; t += 32) d2 += dp[(size_t)t * a.maxK];
-            }
-            const double* ep = g.epart + img0 + k;
-            for (int b = warp; b < g.n_eblk; b += 32) e += ep[(size_t)b * g.n_img];
-        }
-        pd[warp][lane] = d2;
-        pe[warp][lane] = e;
-        __syncthreads();
-        const int kk = k0 + warp;  // image combined by this warp
-        if (kk < K) {
-            double sd = pd[lane][warp], se = pe[lane][warp];
+    // block sum: T within each warp (fixed shuffle tree); warp totals in FP64 by 32 lanes of warp 0 at
+    // once, lane (i, q) adding warps q, q+4, ... of difference i, then a two-level tree over q
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                sd += __shfl_down_sync(0xffffffffu, sd, o);
-                se += __shfl_down_sync(0xffffffffu, se, o);
-            }
-            if (lane == 0) {
-                a.e_last[(size_t)str * a.maxK + kk] = se;
-                if (!isfinite(se) || !isfinite(sd)) atomicOr(g.err, kErrNonFinite);
-                dd[kk] = sqrt_nr(sd);  // d_k (Eq. 11)
-            }
-        }
-        __syncthreads();
-    }
-    if (warp >= nwarp) return;  // whole warps beyond the images; no barrier below counts them
-    const double d = tid < K ? dd[tid] : 0.0;
-    // s_k = d_1 + ... + d_k, s_0 = 0 (Eq. 11): inclusive scan, warp shuffles then warp totals
-    double v = d;
+    for (int i = 0; i < kArcMaxChunk; ++i)
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const double u = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += u;
+        for (int o = 16; o > 0; o >>= 1) part[i] += __shfl_down_sync(0xffffffffu, part[i], o);
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < kArcMaxChunk; ++i) red[warp * kArcMaxChunk + i] = double(part[i]);
+    __syncthreads();
+    if (warp == 0) {
+        static_assert(kArcMaxChunk * 4 == 32, "one lane per (difference, quarter)");
+        const int i = lane >> 2, q = lane & 3;
+        double v = 0.0;
+        for (int w = q; w < nwarp; w += 4) v += red[w * kArcMaxChunk + i];
+        v += __shfl_down_sync(0xffffffffu, v, 2);
+        v += __shfl_down_sync(0xffffffffu, v, 1);
+        if (q == 0 && i < nd) a.dpart[((size_t)str * a.n_tiles + blockIdx.x) * a.maxK + k_lo + i + 1] = v;
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) s_flag = atomicAdd(&a.cnt[str * a.n_kchunks + chunk], 1u) == gridDim.x - 1;
     }
-    if (nwarp > 1) {
+    __syncthreads();
+    if (!s_flag) return;
+    // ---- last tile CTA of (string, chunk): d_k of the chunk's differences ----
+    __threadfence();
+    if (warp < nd) {
+        const int k = k_lo + warp + 1;
+        const double* dp = a.dpart + (size_t)str * a.n_tiles * a.maxK + k;
+        // tile partials lane-strided, loads issued in groups of four before their (ordered) adds
+        double d2 = 0.0;
+        for (int t0 = lane; t0 < a.n_tiles; t0 += 128) {
+            double v[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int t = t0 + 32 * j;
+                v[j] = t < a.n_tiles ? __ldcg(dp + (size_t)t * a.maxK) : 0.0;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) d2 += v[j];
+        }
+        d2 = warp_sum_d(d2);
+        if (lane == 0) {
+            if (!isfinite(d2)) atomicOr(g.err, kErrNonFinite);
+            a.dk[sb + k] = sqrt_nr(d2);  // d_k (Eq. 11)
+            __threadfence();
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        a.cnt[str * a.n_kchunks + chunk] = 0u;  // every tile CTA of this chunk has counted
+        s_flag = atomicAdd(&a.cnt[a.n_str * a.n_kchunks + str], 1u) == (unsigned)(n_act - 1);
+    }
+    __syncthreads();
+    if (!s_flag) return;
+    // ---- last chunk CTA of the string: arc length, targets, interpolation table ----
+    __threadfence();
+    if (tid == 0) a.cnt[a.n_str * a.n_kchunks + str] = 0u;
+    const int per = (K + nthr - 1) / nthr;  // images per thread, <= 4 since K <= kArcMaxK = 4 * 256
+    const int kb = tid * per;
+    const int nw = ((K + per - 1) / per + 31) >> 5;  // warps holding images
+    // s_k = d_1 + ... + d_k, s_0 = 0 (Eq. 11): each thread sums the d of its images; an exclusive scan
+    // of those sums (warp shuffles, then the warp totals in order) gives its starting offset
+    if (warp < nw) {
+        double run = 0.0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = kb + q;
+            if (q < per && k >= 1 && k < K) run += __ldcg(a.dk + sb + k);
+        }
+        double v = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double u = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += u;
+        }
+        const double ex = __shfl_up_sync(0xffffffffu, v, 1);
+        red[tid] = lane > 0 ? ex : 0.0;
         if (lane == 31) wsum[warp] = v;
-        asm volatile("bar.sync 1, %0;" ::"r"(nwarp * 32));
-        if (warp == 0) {
-            double w = lane < nwarp ? wsum[lane] : 0.0;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const double u = __shfl_up_sync(0xffffffffu, w, o);
-                if (lane >= o) w += u;
-            }
-            wsum[lane] = w;
-        }
-        asm volatile("bar.sync 1, %0;" ::"r"(nwarp * 32));
-        if (warp > 0) v += wsum[warp - 1];
     }
-    if (tid < K) alpha[tid] = v;
-    asm volatile("bar.sync 1, %0;" ::"r"(nwarp * 32));
+    __syncthreads();
+    if (tid == 0) {
+        double off = 0.0;
+        for (int w = 0; w < nw; ++w) {
+            const double t = wsum[w];
+            wsum[w] = off;
+            off += t;
+        }
+    }
+    __syncthreads();
+    if (warp < nw) {
+        double r = wsum[warp] + red[tid];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = kb + q;
+            if (q < per && k < K) {
+                if (k >= 1) r += __ldcg(a.dk + sb + k);
+                alpha[k] = r;
+            }
+        }
+    }
+    __syncthreads();
     const double sK = alpha[K - 1];
     const bool move = a.reparam && sK > 0.0 && isfinite(sK);
-    if (move && tid < K) alpha[tid] = v * rcp_nr(sK);  // alpha*_k = s_k / s_{K-1} (Eq. 12)
-    asm volatile("bar.sync 1, %0;" ::"r"(nwarp * 32));
-    (void)nthr;
-    if (tid < K) {
-        const int k = tid;
-        InterpEntry e;
-        e.src0 = img0 + k;
-        e.src1 = img0 + k;
-        e.t = 0.0;
-        e.tf = 0.f;
-        e.omtf = 1.f;
-        e.copy = 1;
-        e.pad = 0;
-        if (move && k > 0 && k < K - 1) {
-            const double ak = (double)k / (double)(K - 1);
-            // largest j in [0, K-2] with alpha*_j <= ak (alpha* is non-decreasing; alpha*_0 = 0 <= ak)
-            int lo = 0, hi = K - 2;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (alpha[mid] <= ak)
-                    lo = mid;
-                else
-                    hi = mid - 1;
+    if (move && warp < nw) {
+        const double r = rcp_nr(sK);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (q < per && kb + q < K) alpha[kb + q] *= r;  // alpha*_k = s_k / s_{K-1} (Eq. 12)
+    }
+    __syncthreads();
+    if (warp < nw) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = kb + q;
+            if (q >= per || k >= K) continue;
+            InterpEntry e;
+            e.src0 = img0 + k;
+            e.src1 = img0 + k;
+            e.t = 0.0;
+            e.tf = 0.f;
+            e.omtf = 1.f;
+            e.copy = 1;
+            e.pad = 0;
+            if (move && k > 0 && k < K - 1) {
+                const double ak = (double)k / (double)(K - 1);
+                // largest j in [0, K-2] with alpha*_j <= ak (alpha* is non-decreasing; alpha*_0 = 0 <= ak)
+                int lo = 0, hi = K - 2;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (alpha[mid] <= ak)
+                        lo = mid;
+                    else
+                        hi = mid - 1;
+                }
+                const int j = lo;
+                e.src0 = img0 + j;
+                e.src1 = img0 + j + 1;
+                e.t = (ak - alpha[j]) * rcp_nr(alpha[j + 1] - alpha[j]);
+                e.tf = (float)e.t;
+                e.omtf = (float)(1.0 - e.t);
+                e.copy = 0;
             }
-            const int j = lo;
-            e.src0 = img0 + j;
-            e.src1 = img0 + j + 1;
-            e.t = (ak - alpha[j]) * rcp_nr(alpha[j + 1] - alpha[j]);
-            e.tf = (float)e.t;
-            e.omtf = (float)(1.0 - e.t);
-            e.copy = 0;
+            const_cast<InterpEntry*>(g.interp)[img0 + k] = e;
         }
-        const_cast<InterpEntry*>(g.interp)[img0 + k] = e;
     }
 }
 
@@ -1070,7 +1154,11 @@ template <typename T> void launch_xfwd(const GroupArgs<T>& g, bool do_fft, int n
     }
     if constexpr (std::is_same<T, float>::value) {
         if (f128_x(4, g.Px)) {
-            launch_pdl(xfwd128_kernel<T>, grid, dim3(f128_x_threads(g.ty_a)), f128_x_smem(g.ty_a, g.lsx), st, g);
+            const dim3 blk(f128_x_threads(g.ty_a));
+            const size_t sm = f128_x_smem(g.ty_a);
+            if (g.ty_a == 2) launch_pdl(xfwd128_kernel<T, 2>, grid, blk, sm, st, g);
+            else if (g.ty_a == 4) launch_pdl(xfwd128_kernel<T, 4>, grid, blk, sm, st, g);
+            else launch_pdl(xfwd128_kernel<T, 8>, grid, blk, sm, st, g);  // rows per CTA are 2, 4 or 8
             return;
         }
         switch (g.Px) {
@@ -1127,8 +1215,11 @@ void launch_xinv_step(const GroupArgs<T>& g, bool do_fft, T dt, int nthr, size_t
     }
     if constexpr (std::is_same<T, float>::value) {
         if (f128_x(4, g.Px)) {
-            launch_pdl(xinv128_kernel<T, 0>, grid, dim3(f128_x_threads(g.ty_c)), f128_x_smem(g.ty_c, g.lsx), st, g, dt,
-                       (T*)nullptr);
+            const dim3 blk(f128_x_threads(g.ty_c));
+            const size_t sm = f128_x_smem(g.ty_c);
+            if (g.ty_c == 2) launch_pdl(xinv128_kernel<T, 0, 2>, grid, blk, sm, st, g, dt, (T*)nullptr);
+            else if (g.ty_c == 4) launch_pdl(xinv128_kernel<T, 0, 4>, grid, blk, sm, st, g, dt, (T*)nullptr);
+            else launch_pdl(xinv128_kernel<T, 0, 8>, grid, blk, sm, st, g, dt, (T*)nullptr);
             return;
         }
         switch (g.Px) {
@@ -1149,7 +1240,11 @@ void launch_xinv_eval(const GroupArgs<T>& g, bool do_fft, T* hout, int nthr, siz
     dim3 grid((g.ny + g.ty_c - 1) / g.ty_c, g.nz, g.n_pairs);
     if constexpr (std::is_same<T, float>::value) {
         if (do_fft && f128_x(4, g.Px)) {
-            xinv128_kernel<T, 1><<<grid, f128_x_threads(g.ty_c), f128_x_smem(g.ty_c, g.lsx), st>>>(g, T(0), hout);
+            const int nt = f128_x_threads(g.ty_c);
+            const size_t sm = f128_x_smem(g.ty_c);
+            if (g.ty_c == 2) xinv128_kernel<T, 1, 2><<<grid, nt, sm, st>>>(g, T(0), hout);
+            else if (g.ty_c == 4) xinv128_kernel<T, 1, 4><<<grid, nt, sm, st>>>(g, T(0), hout);
+            else xinv128_kernel<T, 1, 8><<<grid, nt, sm, st>>>(g, T(0), hout);
             return;
         }
     }
@@ -1163,10 +1258,6 @@ void launch_xinv_eval(const GroupArgs<T>& g, bool do_fft, T* hout, int nthr, siz
 template <typename T> void launch_arc(const GroupArgs<T>& g, const ArcArgs& a, int nthr, cudaStream_t st) {
     dim3 grid(a.n_tiles, a.n_kchunks, a.n_str);
     launch_pdl(arc_kernel<T>, grid, dim3(nthr), 0, st, g, a);
-}
-
-template <typename T> void launch_reparam(const GroupArgs<T>& g, const ArcArgs& a, cudaStream_t st) {
-    launch_pdl(reparam_kernel<T>, dim3(a.n_str), dim3(1024), 0, st, g, a);
 }
 
 template <typename T>
@@ -1200,9 +1291,12 @@ template <typename T> void set_smem_limits(int bytes) {
     cudaFuncSetAttribute(xinv_kernel<T, false, 0, 0>, attr, bytes);
     cudaFuncSetAttribute(xinv_kernel<T, false, 1, 0>, attr, bytes);
     if constexpr (std::is_same<T, float>::value) {
-        cudaFuncSetAttribute(xinv128_kernel<T, 1>, attr, bytes);
-        cudaFuncSetAttribute(xfwd128_kernel<T>, attr, bytes);
-        cudaFuncSetAttribute(xinv128_kernel<T, 0>, attr, bytes);
+#define SS_CASE(R)                                                  \
+    cudaFuncSetAttribute(xfwd128_kernel<T, R>, attr, bytes);        \
+    cudaFuncSetAttribute(xinv128_kernel<T, 0, R>, attr, bytes);     \
+    cudaFuncSetAttribute(xinv128_kernel<T, 1, R>, attr, bytes);
+        SS_CASE(2) SS_CASE(4) SS_CASE(8)
+#undef SS_CASE
         cudaFuncSetAttribute(yz128_kernel<T, 4>, attr, bytes);
         cudaFuncSetAttribute(yz128_kernel<T, 8>, attr, bytes);
 #define SS_CASE(P)                                                       \
@@ -1245,7 +1339,6 @@ void launch_interp_identity(InterpEntry* tab, int img0, int K, cudaStream_t st) 
     template void launch_xinv_step<T>(const GroupArgs<T>&, bool, T, int, size_t, cudaStream_t);                \
     template void launch_xinv_eval<T>(const GroupArgs<T>&, bool, T*, int, size_t, cudaStream_t);               \
     template void launch_arc<T>(const GroupArgs<T>&, const ArcArgs&, int, cudaStream_t);                       \
-    template void launch_reparam<T>(const GroupArgs<T>&, const ArcArgs&, cudaStream_t);                        \
     template void launch_eval_reduce<T>(const GroupArgs<T>&, const ArcArgs&, double*, double*, cudaStream_t);  \
     template void launch_aos_to_soa<T, float>(const float*, T*, int, int, int*, cudaStream_t);                 \
     template void launch_aos_to_soa<T, double>(const double*, T*, int, int, int*, cudaStream_t);               \

@@ -156,6 +156,7 @@ extern "C" ss_status ss_field_noalloc(int nx, int ny, int nz, double J, double D
             break;
         }
     }
+    if (dip && f128_x(4, Px)) ty = f128_x_rows(ty);  // the length-128 x kernels take 2, 4 or 8 rows
     const size_t smem_a = (size_t)(Px + 3 * ty * lsx) * sizeof(float2);
     const size_t smem_c = smem_a + 32 * 8 * sizeof(double);
     size_t smem_b = (size_t)(Py + 3 * nz * lsy) * sizeof(float2);
