@@ -87,7 +87,7 @@ struct Group {
     InterpEntry* interp = nullptr;
     double* epart = nullptr;
     int *d_str_img0 = nullptr, *d_str_K = nullptr;
-    double *dpart = nullptr, *dk = nullptr, *e_last = nullptr, *eval_terms = nullptr, *eval_E = nullptr;
+    double *dpart = nullptr, *e_last = nullptr, *eval_terms = nullptr, *eval_E = nullptr;
     unsigned* arc_cnt = nullptr;
     ArcArgs arc{};
 };
@@ -342,11 +342,9 @@ template <typename T> ss_status setup_group(ss_ctx* c, Group& g) {
     TRY(dalloc(c, (void**)&g.d_str_K, nstr * sizeof(int)));
     TRY(dalloc(c, (void**)&g.dpart, (size_t)nstr * maxK * a.n_tiles * sizeof(double)));
     TRY(dalloc(c, (void**)&g.e_last, (size_t)nstr * maxK * sizeof(double)));
-    TRY(dalloc(c, (void**)&g.dk, (size_t)nstr * maxK * sizeof(double)));
-    const size_t n_cnt = (size_t)nstr * (a.n_kchunks + 1);
+    const size_t n_cnt = (size_t)nstr;  // tile CTAs finished per string
     TRY(dalloc(c, (void**)&g.arc_cnt, n_cnt * sizeof(unsigned)));
     CUDA_TRY(c, cudaMemsetAsync(g.arc_cnt, 0, n_cnt * sizeof(unsigned), c->cs));
-    CUDA_TRY(c, cudaMemsetAsync(g.dk, 0, (size_t)nstr * maxK * sizeof(double), c->cs));
     TRY(dalloc(c, (void**)&g.eval_terms, (size_t)nstr * maxK * 4 * sizeof(double)));
     TRY(dalloc(c, (void**)&g.eval_E, (size_t)nstr * maxK * sizeof(double)));
     CUDA_TRY(c, cudaMemcpyAsync(g.d_str_img0, g.str_img0.data(), nstr * sizeof(int), cudaMemcpyHostToDevice, c->cs));
@@ -358,7 +356,6 @@ template <typename T> ss_status setup_group(ss_ctx* c, Group& g) {
     a.str_img0 = g.d_str_img0;
     a.str_K = g.d_str_K;
     a.dpart = g.dpart;
-    a.dk = g.dk;
     a.e_last = g.e_last;
     a.cnt = g.arc_cnt;
     launch_interp_identity(g.interp, 0, g.n_img, c->cs);

@@ -24,6 +24,8 @@ constexpr int kMaxThreadsX = 512;   // largest block of the x-transform kernels 
 constexpr int kMinBlocksX = 2;      // resident 512-thread blocks per SM they are compiled for (64 registers)
 constexpr int kMaxThreadsYz = 384;  // block size of the y/z kernel (3 x 128: one z-convolution row per warp)
 constexpr int kMinBlocksYz = 2;
+constexpr int kMaxThreads128 = 384;  // length-128 x kernels: at most 8 rows of 48 threads
+constexpr int kMinBlocks128 = 3;     // resident 384-thread blocks per SM of the length-128 kernels (56 registers)
 constexpr int kArcMaxChunk = 8;     // image differences one arc CTA accumulates
 constexpr int kArcMaxK = 1024;      // images per string
 
@@ -96,9 +98,8 @@ struct ArcArgs {
     int kchunk;            // image differences per CTA along the string
     int n_kchunks;
     double* dpart;         // [n_str][n_tiles][maxK] squared-distance partials
-    double* dk;            // [n_str][maxK] image distances d_k (k >= 1)
     double* e_last;        // [n_str][maxK] energies of the state before the step
-    unsigned* cnt;         // [n_str][n_kchunks] tile tickets, then [n_str] chunk tickets; zero between launches
+    unsigned* cnt;         // [n_str] tile CTAs finished; zero between launches
     int reparam;           // 0: keep images where they are
 };
 

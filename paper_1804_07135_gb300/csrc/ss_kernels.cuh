@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xfwd_kernel(GroupAr
 // the spectrum straight to global memory, rows fastest across a warp (the rows of one (kx, c) are
 // contiguous there).  Rows past ny (last CTA) are skipped.
 template <typename T, int ROWS>
-__global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xfwd128_kernel(GroupArgs<T> g) {
+__global__ void __launch_bounds__(kMaxThreads128, kMinBlocks128) xfwd128_kernel(GroupArgs<T> g) {
     using C = cplx<T>;
     static_assert(16 % ROWS == 0, "the pass-2 role permutation needs ROWS | 16");
     constexpr int L = 3 * ROWS, NQ = 16 / ROWS;
@@ -480,7 +480,7 @@ __global__ void __launch_bounds__(kMaxThreadsYz, kMinBlocksYz) yz_kernel(GroupAr
 // output (z-convolution input, stride kLz), then the inverse exchange.
 constexpr int kLz = 136;  // line stride of the z-convolution input/output ([line][ky], 8 mod 16)
 template <typename T, int NZ>
-__global__ void __launch_bounds__(kMaxThreadsYz, kMinBlocksYz) yz128_kernel(GroupArgs<T> g, int stage_dhat) {
+__global__ void __launch_bounds__(kMaxThreadsYz, kMinBlocks128) yz128_kernel(GroupArgs<T> g, int stage_dhat) {
     using C = cplx<T>;
     constexpr int L = 3 * NZ, hy = 64;
     static_assert(L % 4 == 0, "pass-1 roles take lines in groups of four");
@@ -714,7 +714,7 @@ __global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xinv_kernel(GroupAr
 // spectrum (rows fastest across a warp), outputs x < 64 into buf; then the same per-site work as
 // xinv_kernel.  Rows past ny (last CTA) are skipped.
 template <typename T, int MODE, int ROWS>
-__global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xinv128_kernel(GroupArgs<T> g, T dt, T* hout) {
+__global__ void __launch_bounds__(kMaxThreads128, kMinBlocks128) xinv128_kernel(GroupArgs<T> g, T dt, T* hout) {
     using C = cplx<T>;
     static_assert(16 % ROWS == 0 && ROWS >= 2, "the pass-1 role permutation needs ROWS in {2, 4, 8, 16}");
     constexpr int L = 3 * ROWS, NQ = 16 / ROWS;
@@ -761,17 +761,15 @@ __global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xinv128_kernel(Grou
 }
 
 // ------------------------------------------------------------------------------------------------
-// arc: grid (n_tiles, n_kchunks, n_str), 256 threads.  Squared distances |sp_k - sp_{k-1}|^2 over all
-// 3N components (Eq. 11), one partial per (string, k, tile), summed in T per thread and warp, in FP64
-// across warps.  Then, without another launch:
-//  * the last tile CTA of each (string, chunk) to finish (ticket counter) sums the tile partials of
-//    the chunk's differences in FP64 and tile order, d_k = sqrt(.), and the step kernel's energy
-//    partials of the chunk's images (e_last);
-//  * the last chunk CTA of the string to finish scans the d_k into the arc length s_k (Eq. 11),
-//    alpha*_k = s_k / s_{K-1} (Eq. 12), and for every interior image k finds the largest j with
-//    alpha*_j <= k/(K-1) and t: the interpolation table the next xfwd applies.
-// Nothing waits on another CTA; the counters are back at zero when the launch ends.  GB300 issues
-// FP64 at a low rate, so the FP64 work is spread over the chunk CTAs and kept to few warp instructions.
+// arc: grid (n_tiles + 1, n_kchunks, n_str), 256 threads.  Tile CTAs: squared distances
+// |sp_k - sp_{k-1}|^2 over their share of the 3N components (Eq. 11), one partial per (string, k,
+// tile), summed in T per thread and warp, in FP64 across warps.  The last tile CTA of a string to
+// finish (ticket counter; nothing waits on another CTA) then sums the tile partials of every d_k in
+// FP64 and tile order, scans them into the arc length s_k (Eq. 11), alpha*_k = s_k / s_{K-1} (Eq. 12),
+// and for every interior image k finds the largest j with alpha*_j <= k/(K-1) and t: the
+// interpolation table the next xfwd applies.  The extra CTA of each chunk (x = n_tiles) sums the step
+// kernel's energy partials of the chunk's images (e_last), off that path.  The counters are back at
+// zero when the launch ends.
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -781,7 +779,7 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 template <typename T>
 __global__ void __launch_bounds__(256, 3) arc_kernel(GroupArgs<T> g, ArcArgs a) {
     __shared__ double red[32 * kArcMaxChunk];
-    __shared__ double alpha[kArcMaxK];
+    __shared__ double alpha[kArcMaxK];  // d_k, then s_k, then alpha*_k
     __shared__ double wsum[32];
     __shared__ int s_flag;
     const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
@@ -790,13 +788,13 @@ __global__ void __launch_bounds__(256, 3) arc_kernel(GroupArgs<T> g, ArcArgs a) 
     const int n_act = max(1, (K - 2 + a.kchunk) / a.kchunk);  // chunks this string uses (one when K = 1)
     const int k_lo = chunk * a.kchunk;
     const int nd = max(0, min(a.kchunk, K - 1 - k_lo));  // differences (k_lo+i, k_lo+i+1), i < nd
+    const int n_tiles = a.n_tiles;
     griddep_wait();
     griddep_launch_dependents();
     if (chunk >= n_act) return;  // uniform over the block
     const size_t sb = (size_t)str * a.maxK;
-    if (blockIdx.x == 0) {
-        // e_last of the chunk's images from the step kernel's partials (no dependence on the distances,
-        // so one tile CTA per chunk does it before its own share)
+    if ((int)blockIdx.x == n_tiles) {
+        // e_last of the chunk's images from the step kernel's partials
         const int k_hi = chunk == n_act - 1 ? K : k_lo + a.kchunk;
         for (int k = k_lo + warp; k < k_hi; k += nwarp) {
             const double* ep = g.epart + img0 + k;  // [block][image]
@@ -808,6 +806,7 @@ __global__ void __launch_bounds__(256, 3) arc_kernel(GroupArgs<T> g, ArcArgs a) 
                 a.e_last[sb + k] = e;
             }
         }
+        return;
     }
     const size_t M = (size_t)3 * g.N;
     const size_t e0 = (size_t)blockIdx.x * a.tile_elems;
@@ -865,58 +864,65 @@ __global__ void __launch_bounds__(256, 3) arc_kernel(GroupArgs<T> g, ArcArgs a) 
         for (int w = q; w < nwarp; w += 4) v += red[w * kArcMaxChunk + i];
         v += __shfl_down_sync(0xffffffffu, v, 2);
         v += __shfl_down_sync(0xffffffffu, v, 1);
-        if (q == 0 && i < nd) a.dpart[((size_t)str * a.n_tiles + blockIdx.x) * a.maxK + k_lo + i + 1] = v;
+        if (q == 0 && i < nd) a.dpart[((size_t)str * n_tiles + blockIdx.x) * a.maxK + k_lo + i + 1] = v;
         __threadfence();
         __syncwarp();
-        if (lane == 0) s_flag = atomicAdd(&a.cnt[str * a.n_kchunks + chunk], 1u) == gridDim.x - 1;
+        if (lane == 0)
+            s_flag = atomicAdd(&a.cnt[str], 1u) == (unsigned)(n_tiles * n_act - 1);
     }
     __syncthreads();
     if (!s_flag) return;
-    // ---- last tile CTA of (string, chunk): d_k of the chunk's differences ----
+    // ---- last tile CTA of the string: d_k for k = 1..K-1 ----
+    // 8 lanes per difference (lane = 8 j + l, four differences per warp), lane l summing tiles l, l + 8,
+    // ... in order (loads twelve at a time), then a three-level tree over l: few FP64 instructions, as
+    // GB300 issues FP64 at a low rate
     __threadfence();
-    if (warp < nd) {
-        const int k = k_lo + warp + 1;
-        const double* dp = a.dpart + (size_t)str * a.n_tiles * a.maxK + k;
-        // tile partials lane-strided, loads issued in groups of four before their (ordered) adds
-        double d2 = 0.0;
-        for (int t0 = lane; t0 < a.n_tiles; t0 += 128) {
-            double v[4];
+    if (tid == 0) a.cnt[str] = 0u;  // every tile CTA of the string has counted
+    {
+        const double* dp = a.dpart + (size_t)str * n_tiles * a.maxK;
+        const int j = lane >> 3, l = lane & 7;
+        for (int k0 = 1 + 4 * warp; k0 < K; k0 += 4 * nwarp) {
+            const int k = k0 + j;
+            double v = 0.0;
+            if (k < K) {
+                for (int t0 = l; t0 < n_tiles; t0 += 96) {
+                    double x[12];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int t = t0 + 32 * j;
-                v[j] = t < a.n_tiles ? __ldcg(dp + (size_t)t * a.maxK) : 0.0;
+                    for (int q = 0; q < 12; ++q) {
+                        const int t = t0 + 8 * q;
+                        x[q] = t < n_tiles ? __ldcg(dp + (size_t)t * a.maxK + k) : 0.0;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 12; ++q) v += x[q];
+                }
             }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) d2 += v[j];
-        }
-        d2 = warp_sum_d(d2);
-        if (lane == 0) {
-            if (!isfinite(d2)) atomicOr(g.err, kErrNonFinite);
-            a.dk[sb + k] = sqrt_nr(d2);  // d_k (Eq. 11)
-            __threadfence();
+            v += __shfl_down_sync(0xffffffffu, v, 4);
+            v += __shfl_down_sync(0xffffffffu, v, 2);
+            v += __shfl_down_sync(0xffffffffu, v, 1);
+            if (l == 0 && k < K) {
+                if (!isfinite(v)) atomicOr(g.err, kErrNonFinite);
+                alpha[k] = sqrt_nr(v);  // d_k (Eq. 11)
+            }
         }
     }
+    if (tid == 0) alpha[0] = 0.0;
     __syncthreads();
-    if (tid == 0) {
-        a.cnt[str * a.n_kchunks + chunk] = 0u;  // every tile CTA of this chunk has counted
-        s_flag = atomicAdd(&a.cnt[a.n_str * a.n_kchunks + str], 1u) == (unsigned)(n_act - 1);
-    }
-    __syncthreads();
-    if (!s_flag) return;
-    // ---- last chunk CTA of the string: arc length, targets, interpolation table ----
-    __threadfence();
-    if (tid == 0) a.cnt[a.n_str * a.n_kchunks + str] = 0u;
+    // ---- arc length, targets, interpolation table ----
     const int per = (K + nthr - 1) / nthr;  // images per thread, <= 4 since K <= kArcMaxK = 4 * 256
     const int kb = tid * per;
     const int nw = ((K + per - 1) / per + 31) >> 5;  // warps holding images
-    // s_k = d_1 + ... + d_k, s_0 = 0 (Eq. 11): each thread sums the d of its images; an exclusive scan
-    // of those sums (warp shuffles, then the warp totals in order) gives its starting offset
+    // s_k = d_1 + ... + d_k (Eq. 11): each thread sums the d of its images; an exclusive scan of those
+    // sums (warp shuffles, then the warp totals in order) gives its starting offset
+    double dloc[4] = {0.0, 0.0, 0.0, 0.0}, ex = 0.0;
     if (warp < nw) {
         double run = 0.0;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int k = kb + q;
-            if (q < per && k >= 1 && k < K) run += __ldcg(a.dk + sb + k);
+            if (q < per && k < K) {
+                dloc[q] = alpha[k];
+                run += dloc[q];
+            }
         }
         double v = run;
 #pragma unroll
@@ -924,8 +930,8 @@ __global__ void __launch_bounds__(256, 3) arc_kernel(GroupArgs<T> g, ArcArgs a) 
             const double u = __shfl_up_sync(0xffffffffu, v, o);
             if (lane >= o) v += u;
         }
-        const double ex = __shfl_up_sync(0xffffffffu, v, 1);
-        red[tid] = lane > 0 ? ex : 0.0;
+        ex = __shfl_up_sync(0xffffffffu, v, 1);
+        if (lane == 0) ex = 0.0;
         if (lane == 31) wsum[warp] = v;
     }
     __syncthreads();
@@ -939,12 +945,12 @@ __global__ void __launch_bounds__(256, 3) arc_kernel(GroupArgs<T> g, ArcArgs a) 
     }
     __syncthreads();
     if (warp < nw) {
-        double r = wsum[warp] + red[tid];
+        double r = wsum[warp] + ex;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int k = kb + q;
             if (q < per && k < K) {
-                if (k >= 1) r += __ldcg(a.dk + sb + k);
+                r += dloc[q];
                 alpha[k] = r;
             }
         }
@@ -1256,7 +1262,7 @@ void launch_xinv_eval(const GroupArgs<T>& g, bool do_fft, T* hout, int nthr, siz
 }
 
 template <typename T> void launch_arc(const GroupArgs<T>& g, const ArcArgs& a, int nthr, cudaStream_t st) {
-    dim3 grid(a.n_tiles, a.n_kchunks, a.n_str);
+    dim3 grid(a.n_tiles + 1, a.n_kchunks, a.n_str);  // + one energy CTA per chunk
     launch_pdl(arc_kernel<T>, grid, dim3(nthr), 0, st, g, a);
 }
 
@@ -1281,33 +1287,38 @@ void launch_extract_octant(const double2* spec, T* dhat, int Px, int Py, int nz,
     extract_octant_kernel<T><<<grid1d(total, 256), 256, 0, st>>>(spec, dhat, Px, Py, nz, scale);
 }
 
-// Raises the dynamic shared-memory limit of every kernel that stages lines in shared memory.
+// Raises the dynamic shared-memory limit of every kernel that stages lines in shared memory to
+// `bytes` less the kernel's static shared memory (the two together may not exceed `bytes`).
+template <typename F> static inline void set_dyn_smem(F* kernel, int bytes) {
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return;
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes - (int)fa.sharedSizeBytes);
+}
 template <typename T> void set_smem_limits(int bytes) {
-    const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    cudaFuncSetAttribute(xfwd_kernel<T, true, 0>, attr, bytes);
-    cudaFuncSetAttribute(yz_kernel<T, 0, 0>, attr, bytes);
-    cudaFuncSetAttribute(xinv_kernel<T, true, 0, 0>, attr, bytes);
-    cudaFuncSetAttribute(xinv_kernel<T, true, 1, 0>, attr, bytes);
-    cudaFuncSetAttribute(xinv_kernel<T, false, 0, 0>, attr, bytes);
-    cudaFuncSetAttribute(xinv_kernel<T, false, 1, 0>, attr, bytes);
+    set_dyn_smem(xfwd_kernel<T, true, 0>, bytes);
+    set_dyn_smem(yz_kernel<T, 0, 0>, bytes);
+    set_dyn_smem(xinv_kernel<T, true, 0, 0>, bytes);
+    set_dyn_smem(xinv_kernel<T, true, 1, 0>, bytes);
+    set_dyn_smem(xinv_kernel<T, false, 0, 0>, bytes);
+    set_dyn_smem(xinv_kernel<T, false, 1, 0>, bytes);
     if constexpr (std::is_same<T, float>::value) {
-#define SS_CASE(R)                                                  \
-    cudaFuncSetAttribute(xfwd128_kernel<T, R>, attr, bytes);        \
-    cudaFuncSetAttribute(xinv128_kernel<T, 0, R>, attr, bytes);     \
-    cudaFuncSetAttribute(xinv128_kernel<T, 1, R>, attr, bytes);
+#define SS_CASE(R)                                  \
+    set_dyn_smem(xfwd128_kernel<T, R>, bytes);      \
+    set_dyn_smem(xinv128_kernel<T, 0, R>, bytes);   \
+    set_dyn_smem(xinv128_kernel<T, 1, R>, bytes);
         SS_CASE(2) SS_CASE(4) SS_CASE(8)
 #undef SS_CASE
-        cudaFuncSetAttribute(yz128_kernel<T, 4>, attr, bytes);
-        cudaFuncSetAttribute(yz128_kernel<T, 8>, attr, bytes);
-#define SS_CASE(P)                                                       \
-    cudaFuncSetAttribute(xfwd_kernel<T, true, P>, attr, bytes);          \
-    cudaFuncSetAttribute(xinv_kernel<T, true, 0, P>, attr, bytes);
+        set_dyn_smem(yz128_kernel<T, 4>, bytes);
+        set_dyn_smem(yz128_kernel<T, 8>, bytes);
+#define SS_CASE(P)                                  \
+    set_dyn_smem(xfwd_kernel<T, true, P>, bytes);   \
+    set_dyn_smem(xinv_kernel<T, true, 0, P>, bytes);
         SS_FOR_PX(SS_CASE)
 #undef SS_CASE
-#define SS_CASE(P, Z) cudaFuncSetAttribute(yz_kernel<T, P, Z>, attr, bytes);
+#define SS_CASE(P, Z) set_dyn_smem(yz_kernel<T, P, Z>, bytes);
         SS_FOR_PYNZ(SS_CASE)
 #undef SS_CASE
-#define SS_CASE(Z) cudaFuncSetAttribute(yz_kernel<T, 0, Z>, attr, bytes);
+#define SS_CASE(Z) set_dyn_smem(yz_kernel<T, 0, Z>, bytes);
         SS_FOR_NZ(SS_CASE)
 #undef SS_CASE
     }
