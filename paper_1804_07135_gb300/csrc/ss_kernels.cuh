@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xfwd_kernel(GroupAr
 // the spectrum straight to global memory, rows fastest across a warp (the rows of one (kx, c) are
 // contiguous there).  Rows past ny (last CTA) are skipped.
 template <typename T, int ROWS>
-__global__ void __launch_bounds__(kMaxThreads128, kMinBlocks128) xfwd128_kernel(GroupArgs<T> g) {
+__global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xfwd128_kernel(GroupArgs<T> g) {
     using C = cplx<T>;
     static_assert(16 % ROWS == 0, "the pass-2 role permutation needs ROWS | 16");
     constexpr int L = 3 * ROWS, NQ = 16 / ROWS;
@@ -776,6 +776,15 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     return v;  // lane 0
 }
 
+// Ticket: atomic add with release (the calling thread's earlier writes, and those ordered before it by a
+// barrier, are visible to whoever acquires the new value) and acquire (the writes released by earlier
+// tickets are visible to this thread, and after a barrier to its CTA) semantics at GPU scope.
+__device__ __forceinline__ unsigned ticket_acq_rel(unsigned* p) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(p) : "memory");
+    return old;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256, 3) arc_kernel(GroupArgs<T> g, ArcArgs a) {
     __shared__ double red[32 * kArcMaxChunk];
@@ -865,10 +874,8 @@ __global__ void __launch_bounds__(256, 3) arc_kernel(GroupArgs<T> g, ArcArgs a) 
         v += __shfl_down_sync(0xffffffffu, v, 2);
         v += __shfl_down_sync(0xffffffffu, v, 1);
         if (q == 0 && i < nd) a.dpart[((size_t)str * n_tiles + blockIdx.x) * a.maxK + k_lo + i + 1] = v;
-        __threadfence();
         __syncwarp();
-        if (lane == 0)
-            s_flag = atomicAdd(&a.cnt[str], 1u) == (unsigned)(n_tiles * n_act - 1);
+        if (lane == 0) s_flag = ticket_acq_rel(&a.cnt[str]) == (unsigned)(n_tiles * n_act - 1);
     }
     __syncthreads();
     if (!s_flag) return;
@@ -876,7 +883,6 @@ __global__ void __launch_bounds__(256, 3) arc_kernel(GroupArgs<T> g, ArcArgs a) 
     // 8 lanes per difference (lane = 8 j + l, four differences per warp), lane l summing tiles l, l + 8,
     // ... in order (loads twelve at a time), then a three-level tree over l: few FP64 instructions, as
     // GB300 issues FP64 at a low rate
-    __threadfence();
     if (tid == 0) a.cnt[str] = 0u;  // every tile CTA of the string has counted
     {
         const double* dp = a.dpart + (size_t)str * n_tiles * a.maxK;
@@ -892,8 +898,12 @@ __global__ void __launch_bounds__(256, 3) arc_kernel(GroupArgs<T> g, ArcArgs a) 
                         const int t = t0 + 8 * q;
                         x[q] = t < n_tiles ? __ldcg(dp + (size_t)t * a.maxK + k) : 0.0;
                     }
+                    // fixed pairwise tree (FP64 latency is long on GB300; depth 4 instead of 12)
 #pragma unroll
-                    for (int q = 0; q < 12; ++q) v += x[q];
+                    for (int q = 0; q < 6; ++q) x[q] = x[2 * q] + x[2 * q + 1];
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) x[q] = x[2 * q] + x[2 * q + 1];
+                    v += (x[0] + x[1]) + x[2];
                 }
             }
             v += __shfl_down_sync(0xffffffffu, v, 4);
@@ -934,18 +944,20 @@ __global__ void __launch_bounds__(256, 3) arc_kernel(GroupArgs<T> g, ArcArgs a) 
         if (lane == 0) ex = 0.0;
         if (lane == 31) wsum[warp] = v;
     }
-    __syncthreads();
-    if (tid == 0) {
-        double off = 0.0;
-        for (int w = 0; w < nw; ++w) {
-            const double t = wsum[w];
-            wsum[w] = off;
-            off += t;
+    if (nw > 1) {  // uniform over the block
+        __syncthreads();
+        if (tid == 0) {
+            double off = 0.0;
+            for (int w = 0; w < nw; ++w) {
+                const double t = wsum[w];
+                wsum[w] = off;
+                off += t;
+            }
         }
+        __syncthreads();
     }
-    __syncthreads();
     if (warp < nw) {
-        double r = wsum[warp] + ex;
+        double r = (nw > 1 ? wsum[warp] : 0.0) + ex;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int k = kb + q;
@@ -980,16 +992,15 @@ __global__ void __launch_bounds__(256, 3) arc_kernel(GroupArgs<T> g, ArcArgs a) 
             e.pad = 0;
             if (move && k > 0 && k < K - 1) {
                 const double ak = (double)k / (double)(K - 1);
-                // largest j in [0, K-2] with alpha*_j <= ak (alpha* is non-decreasing; alpha*_0 = 0 <= ak)
-                int lo = 0, hi = K - 2;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (alpha[mid] <= ak)
-                        lo = mid;
-                    else
-                        hi = mid - 1;
+                // largest j in [0, K-2] with alpha*_j <= ak (alpha* is non-decreasing; alpha*_0 = 0 <= ak),
+                // walking from j = k: after a few iterations the images are nearly evenly spaced
+                int j = min(k, K - 2);
+                if (alpha[j] <= ak) {
+                    while (j < K - 2 && alpha[j + 1] <= ak) ++j;
+                } else {
+                    do --j;
+                    while (alpha[j] > ak);
                 }
-                const int j = lo;
                 e.src0 = img0 + j;
                 e.src1 = img0 + j + 1;
                 e.t = (ak - alpha[j]) * rcp_nr(alpha[j + 1] - alpha[j]);
