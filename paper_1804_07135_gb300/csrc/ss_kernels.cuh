@@ -116,6 +116,57 @@ __device__ __forceinline__ void xfwd_gather(const GroupArgs<T>& g, cplx<T>* buf,
 #pragma unroll
     for (int h = 0; h < 2; ++h)
         if (ia + h < g.n_img) ent[h] = g.interp[ia + h];
+    if constexpr (std::is_same<T, float>::value) {
+        if ((nx & 1) == 0) {
+            // two adjacent sites (x even, x + 1) per thread: the spin planes move as float2
+            const int hx = nx >> 1;
+            for (int it = tid; it < rows * hx; it += nthr) {
+                const int yy = it / hx, x = 2 * (it - yy * hx);
+                const int site = (z * g.ny + y0 + yy) * nx + x;
+                float out[2][2][3];  // [image][site][component]
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int im = ia + h;
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) out[h][k][0] = out[h][k][1] = out[h][k][2] = 0.f;
+                    if (im >= g.n_img) continue;
+                    const InterpEntry& e = ent[h];
+                    const float* a = g.sp + (size_t)e.src0 * 3 * N + site;
+                    float2 u[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) u[c] = *reinterpret_cast<const float2*>(a + (size_t)c * N);
+                    if (!e.copy) {
+                        const float t = e.tf, omt = e.omtf;
+                        const float* b = g.sp + (size_t)e.src1 * 3 * N + site;
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            const float2 v = *reinterpret_cast<const float2*>(b + (size_t)c * N);
+                            u[c] = make_float2(omt * u[c].x + t * v.x, omt * u[c].y + t * v.y);
+                        }
+                        const float r0 = rsqrtf(u[0].x * u[0].x + u[1].x * u[1].x + u[2].x * u[2].x);
+                        const float r1 = rsqrtf(u[0].y * u[0].y + u[1].y * u[1].y + u[2].y * u[2].y);
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) u[c] = make_float2(u[c].x * r0, u[c].y * r1);
+                    }
+                    float* d = g.s + (size_t)im * 3 * N + site;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        *reinterpret_cast<float2*>(d + (size_t)c * N) = u[c];
+                        out[h][0][c] = u[c].x;
+                        out[h][1][c] = u[c].y;
+                    }
+                }
+                if (buf) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+#pragma unroll
+                        for (int k = 0; k < 2; ++k)
+                            buf[(c * lrows + yy) * ls + fft_pad(x + k)] = C{out[0][k][c], out[1][k][c]};
+                }
+            }
+            return;
+        }
+    }
     for (int it = tid; it < rows * nx; it += nthr) {
         const int yy = it / nx, x = it - yy * nx;
         const int site = (z * g.ny + y0 + yy) * nx + x;
@@ -547,6 +598,91 @@ __global__ void __launch_bounds__(kMaxThreadsYz, kMinBlocks128) yz128_kernel(Gro
 }
 
 // ------------------------------------------------------------------------------------------------
+// h at one site (Eqs. 3-6) from its six neighbours (zero outside the lattice) and the dipole
+// convolution:
+//   h = J sum_nn s_j - D (s_z^{+x} - s_z^{-x}, s_z^{+y} - s_z^{-y}, -s_x^{+x} + s_x^{-x} - s_y^{+y} + s_y^{-y})
+//       + 2 K s_z z + w conv
+template <typename T>
+__device__ __forceinline__ void local_field(const ImgParam<T>& pr, const T* s0, const T* xp, const T* xm, const T* yp,
+                                            const T* ym, const T* zp, const T* zm, const T* conv, T* hf) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) hf[c] = pr.J * (xp[c] + xm[c] + yp[c] + ym[c] + zp[c] + zm[c]) + pr.w * conv[c];
+    hf[0] += -pr.D * (xp[2] - xm[2]);
+    hf[1] += -pr.D * (yp[2] - ym[2]);
+    hf[2] += -pr.D * (-xp[0] + xm[0] - yp[1] + ym[1]) + T(2) * pr.K * s0[2];
+}
+// Eqs. 8, 10, 13 at one site: returns -(1/2) h.s; un = normalise(s + dt (h - (s.h) s))
+template <typename T>
+__device__ __forceinline__ T step_site(const T* s0, const T* hf, T dt, T* un) {
+    const T sh = s0[0] * hf[0] + s0[1] * hf[1] + s0[2] * hf[2];
+    T u[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) u[c] = s0[c] + dt * (hf[c] - sh * s0[c]);
+    const T r = rsqrt_t<T>(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) un[c] = u[c] * r;
+    return T(-0.5) * sh;
+}
+
+// Step mode, FP32, even nx: two adjacent sites (x even, x + 1) per thread and pass, so the spin planes
+// move as float2 (one load serves both sites' y and z neighbours, and the inner x neighbours come from
+// the pair itself).  eacc[h] accumulates the energy terms of image 2p + h.
+__device__ __forceinline__ void xinv_sites_step2(const GroupArgs<float>& g, float dt, const float2* buf, int ls, int p,
+                                                 int z, int y0, int rows, int tid, int nthr, float (&eacc)[2]) {
+    const int nx = g.nx, ny = g.ny, nz = g.nz, N = g.N, hx = nx >> 1;
+    const int ia = 2 * p;
+    const float2 zero = make_float2(0.f, 0.f);
+#pragma unroll 1
+    for (int it = tid; it < 2 * rows * hx; it += nthr) {
+        const int h = it / (rows * hx);
+        const int rem = it - h * rows * hx;
+        const int yy = rem / hx, x = 2 * (rem - yy * hx);
+        const int im = ia + h;
+        if (im >= g.n_img) continue;
+        const int y = y0 + yy;
+        const int site = (z * ny + y) * nx + x;
+        const ImgParam<float> pr = g.prm[im];
+        const float* __restrict__ sb = g.s + (size_t)im * 3 * N;
+        float2 c0[3], xp[3], xm[3], yp[3], ym[3], zp[3], zm[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float* q = sb + (size_t)c * N + site;
+            const float2 cur = *reinterpret_cast<const float2*>(q);
+            const float l = x > 0 ? q[-1] : 0.f, r = x + 2 < nx ? q[2] : 0.f;
+            c0[c] = cur;
+            xm[c] = make_float2(l, cur.x);
+            xp[c] = make_float2(cur.y, r);
+            yp[c] = y + 1 < ny ? *reinterpret_cast<const float2*>(q + nx) : zero;
+            ym[c] = y > 0 ? *reinterpret_cast<const float2*>(q - nx) : zero;
+            zp[c] = z + 1 < nz ? *reinterpret_cast<const float2*>(q + nx * ny) : zero;
+            zm[c] = z > 0 ? *reinterpret_cast<const float2*>(q - nx * ny) : zero;
+        }
+        float un[2][3];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            float s0[3], a[3], b[3], cc[3], d[3], e[3], f[3], conv[3], hf[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                s0[c] = k ? c0[c].y : c0[c].x;
+                a[c] = k ? xp[c].y : xp[c].x;
+                b[c] = k ? xm[c].y : xm[c].x;
+                cc[c] = k ? yp[c].y : yp[c].x;
+                d[c] = k ? ym[c].y : ym[c].x;
+                e[c] = k ? zp[c].y : zp[c].x;
+                f[c] = k ? zm[c].y : zm[c].x;
+                const float2 v = buf[(c * rows + yy) * ls + fft_pad(x + k)];
+                conv[c] = h == 0 ? v.x : -v.y;  // conjugate of the forward transform of the conjugate
+            }
+            local_field(pr, s0, a, b, cc, d, e, f, conv, hf);
+            eacc[h] += step_site(s0, hf, dt, un[k]);
+        }
+        float* __restrict__ o = g.sp + (size_t)im * 3 * N + site;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) *reinterpret_cast<float2*>(o + (size_t)c * N) = make_float2(un[0][c], un[1][c]);
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
 // Per-site work of the x-inverse kernels on rows [y0, y0+rows) of layer z, pair p; buf holds the
 // forward transforms of the conjugated field spectra (line c*rows + yy, fft_pad positions) when
 // HAS_CONV.
@@ -561,10 +697,17 @@ __device__ __forceinline__ void xinv_sites(const GroupArgs<T>& g, T dt, T* hout,
 #pragma unroll
     for (int k = 0; k < NV; ++k) acc[k] = 0.0;
     T eacc[2] = {T(0), T(0)};  // step mode: the thread's few per-site terms, summed in T before FP64
+    bool done = false;
+    if constexpr (MODE == 0 && HAS_CONV && std::is_same<T, float>::value) {
+        if ((nx & 1) == 0) {  // uniform over the grid
+            xinv_sites_step2(g, dt, buf, ls, p, z, y0, rows, tid, nthr, eacc);
+            done = true;
+        }
+    }
     // two sites per thread per pass; restrict-qualified spin planes let the loads of both be issued
     // before either is stored
 #pragma unroll 2
-    for (int it = tid; it < 2 * rows * nx; it += nthr) {
+    for (int it = done ? 2 * rows * nx : tid; it < 2 * rows * nx; it += nthr) {
         const int h = it / (rows * nx);
         const int rem = it - h * rows * nx;
         const int yy = rem / nx, x = rem - yy * nx;
@@ -595,22 +738,14 @@ __device__ __forceinline__ void xinv_sites(const GroupArgs<T>& g, T dt, T* hout,
             }
         }
         T hf[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) hf[c] = pr.J * (xp[c] + xm[c] + yp[c] + ym[c] + zp[c] + zm[c]) + pr.w * conv[c];
-        hf[0] += -pr.D * (xp[2] - xm[2]);
-        hf[1] += -pr.D * (yp[2] - ym[2]);
-        hf[2] += -pr.D * (-xp[0] + xm[0] - yp[1] + ym[1]) + T(2) * pr.K * s0[2];
+        local_field(pr, s0, xp, xm, yp, ym, zp, zm, conv, hf);
         if (MODE == 0) {
-            const T sh = s0[0] * hf[0] + s0[1] * hf[1] + s0[2] * hf[2];
-            eacc[h] += T(-0.5) * sh;
-            T u[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) u[c] = s0[c] + dt * (hf[c] - sh * s0[c]);
-            const T r = rsqrt_t<T>(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+            T un[3];
+            eacc[h] += step_site(s0, hf, dt, un);
             T* __restrict__ o = g.sp + (size_t)im * 3 * N + site;
-            o[0] = u[0] * r;
-            o[N] = u[1] * r;
-            o[2 * N] = u[2] * r;
+            o[0] = un[0];
+            o[N] = un[1];
+            o[2 * N] = un[2];
         } else {
             auto nrm = [](const T* v, double* o) {
                 const double a = v[0], b = v[1], c = v[2];
