@@ -120,10 +120,13 @@ inline size_t f128_x_smem(int rows) {
     return (size_t)(3 * rows * kF128Buf + (3 * rows + 3) / 4 * 4 * kF128Line) * 8 + 32 * 8 * sizeof(double);
 }
 inline int f128_yz_threads(int nz) { return 48 * nz; }
+// The length-128 y/z kernel reads its tensor slab through L1 rather than staging it in shared memory
+// (measured faster: the 16 pairs of one kx would otherwise each copy the same slab, and the smaller
+// shared footprint leaves more L1).
 inline size_t f128_yz_smem(int nz, int Py, bool* stage_dhat) {
-    const size_t slab = (size_t)(Py / 2 + 1) * nz * 6 * sizeof(float);
-    *stage_dhat = slab <= 24 * 1024;
-    return (size_t)2 * 3 * nz * kF128Line * 8 + (*stage_dhat ? slab : 0);
+    (void)Py;
+    *stage_dhat = false;
+    return (size_t)2 * 3 * nz * kF128Line * 8;
 }
 
 // ---- launchers (defined in ss_kernels.cuh, instantiated for float and double) ----
