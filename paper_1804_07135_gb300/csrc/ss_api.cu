@@ -112,7 +112,7 @@ struct ss_ctx {
     size_t stage_bytes = 0;
     std::vector<void*> allocs;
     cudaGraphExec_t graph1 = nullptr, graphN = nullptr;
-    int graphN_iters = 16;
+    int graphN_iters = 64;
     std::string err;
 };
 

@@ -97,7 +97,7 @@ struct ArcArgs {
     int tile_elems;        // components per tile
     int kchunk;            // image differences per CTA along the string
     int n_kchunks;
-    double* dpart;         // [n_str][n_tiles][maxK] squared-distance partials
+    double* dpart;         // [n_str][maxK][n_tiles] squared-distance partials
     double* e_last;        // [n_str][maxK] energies of the state before the step
     unsigned* cnt;         // [n_str] tile CTAs finished; zero between launches
     int reparam;           // 0: keep images where they are

@@ -1008,7 +1008,7 @@ __global__ void __launch_bounds__(256, 3) arc_kernel(GroupArgs<T> g, ArcArgs a) 
         for (int w = q; w < nwarp; w += 4) v += red[w * kArcMaxChunk + i];
         v += __shfl_down_sync(0xffffffffu, v, 2);
         v += __shfl_down_sync(0xffffffffu, v, 1);
-        if (q == 0 && i < nd) a.dpart[((size_t)str * n_tiles + blockIdx.x) * a.maxK + k_lo + i + 1] = v;
+        if (q == 0 && i < nd) a.dpart[((size_t)str * a.maxK + k_lo + i + 1) * n_tiles + blockIdx.x] = v;
         __syncwarp();
         if (lane == 0) s_flag = ticket_acq_rel(&a.cnt[str]) == (unsigned)(n_tiles * n_act - 1);
     }
@@ -1020,7 +1020,7 @@ __global__ void __launch_bounds__(256, 3) arc_kernel(GroupArgs<T> g, ArcArgs a) 
     // GB300 issues FP64 at a low rate
     if (tid == 0) a.cnt[str] = 0u;  // every tile CTA of the string has counted
     {
-        const double* dp = a.dpart + (size_t)str * n_tiles * a.maxK;
+        const double* dp = a.dpart + (size_t)str * a.maxK * n_tiles;  // [k][tile]
         const int j = lane >> 3, l = lane & 7;
         for (int k0 = 1 + 4 * warp; k0 < K; k0 += 4 * nwarp) {
             const int k = k0 + j;
@@ -1031,7 +1031,7 @@ __global__ void __launch_bounds__(256, 3) arc_kernel(GroupArgs<T> g, ArcArgs a) 
 #pragma unroll
                     for (int q = 0; q < 12; ++q) {
                         const int t = t0 + 8 * q;
-                        x[q] = t < n_tiles ? __ldcg(dp + (size_t)t * a.maxK + k) : 0.0;
+                        x[q] = t < n_tiles ? __ldcg(dp + (size_t)k * n_tiles + t) : 0.0;
                     }
                     // fixed pairwise tree (FP64 latency is long on GB300; depth 4 instead of 12)
 #pragma unroll
