@@ -323,7 +323,8 @@ def main():
         line["barrier_abs_err_vs_fp64_gpu"] = abs(dE - dE64)
     if not args.no_other_workloads:
         line["other_workloads"] = {w.name: other_workload(binding, w, stream) for w in
-                                   (workloads.boundary_sweep(), workloads.uneven_study())}
+                                   (workloads.boundary_sweep(), workloads.uneven_study(),
+                                    workloads.paper_monolayer_workload(), workloads.paper_phase_diagram())}
     if not args.no_cpu_baseline and world == 1:
         v, cores, t = cpu_oracle_sample(spec, wl.dt)
         line["cpu_baseline"] = {"value": v, "unit": "spin-updates/s", "cores": cores, "kind": "oracle",
@@ -358,6 +359,8 @@ def other_workload(binding, wl, stream, iters=20, warm=3):
 
 
 def padded(n):
+    """The library's padded transform length: smallest 2^a 3^b >= 2n - 1, or the power of two >= 2n - 1
+    when that is at most 1/8 longer."""
     m = max(1, 2 * n - 1)
     while True:
         q = m
@@ -366,8 +369,12 @@ def padded(n):
         while q % 3 == 0:
             q //= 3
         if q == 1:
-            return m
+            break
         m += 1
+    p2 = 1
+    while p2 < 2 * n - 1:
+        p2 *= 2
+    return p2 if 8 * p2 <= 9 * m else m
 
 
 if __name__ == "__main__":

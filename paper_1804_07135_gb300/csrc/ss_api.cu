@@ -32,10 +32,14 @@ bool is_smooth23(int m) {
 
 // Padded transform length: the smallest 2^a 3^b >= 2n - 1, enough for the linear (non-circular)
 // convolution of n sites with offsets -(n-1)..(n-1) (Sec. II-A, the zero-padded kernel).
+// Padded transform length for n sites: the smallest 2^a 3^b >= 2n - 1, or the power of two >= 2n - 1
+// when that is at most 1/8 longer (its transforms need no radix-3 stages: 112 sites pad to 256, not 243).
 int padded_len(int n) {
     int m = std::max(1, 2 * n - 1);
     while (!is_smooth23(m)) ++m;
-    return m;
+    int p2 = 1;
+    while (p2 < 2 * n - 1) p2 <<= 1;
+    return 8 * p2 <= 9 * m ? p2 : m;
 }
 
 FftPlan make_plan(int P) { return fft_make_plan(P); }

@@ -1295,7 +1295,7 @@ static inline int grid1d(size_t n, int thr) {
 // Compile-time padded lengths and (Py, nz) pairs of the workloads (FP32 only; the FP64 path and any
 // other size use the runtime plans).
 #define SS_FOR_PX(X) X(32) X(128) X(192) X(256) X(384)
-#define SS_FOR_PYNZ(X) X(32, 1) X(128, 4) X(128, 8) X(192, 4) X(256, 4) X(256, 8) X(384, 8)
+#define SS_FOR_PYNZ(X) X(32, 1) X(128, 4) X(128, 8) X(192, 4) X(256, 1) X(256, 4) X(256, 8) X(384, 8)
 #define SS_FOR_NZ(X) X(1) X(4) X(8)
 
 template <typename T> void launch_xfwd(const GroupArgs<T>& g, bool do_fft, int nthr, size_t smem, cudaStream_t st) {

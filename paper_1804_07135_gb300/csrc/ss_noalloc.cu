@@ -64,10 +64,12 @@ bool smooth23(int m) {
     while (m % 3 == 0) m /= 3;
     return m == 1;
 }
-int pad_len(int n) {
+int pad_len(int n) {  // the context's rule: smallest 2^a 3^b >= 2n - 1, or a power of two <= 1/8 longer
     int m = n > 1 ? 2 * n - 1 : 1;
     while (!smooth23(m)) ++m;
-    return m;
+    int p2 = 1;
+    while (p2 < 2 * n - 1) p2 <<= 1;
+    return 8 * p2 <= 9 * m ? p2 : m;
 }
 FftPlan plan_of(int P) { return fft_make_plan(P); }
 int up32(int v) { return ((v + 31) / 32) * 32; }

@@ -164,3 +164,45 @@ def uneven_study(seed: int = 7) -> Workload:
         n, nz = sizes[si]
         strings.append(StringSpec(n, n, nz, 1.0, D, K, 0.01, 32, "bloch" if i % 2 == 0 else "boundary", n / 8.0))
     return Workload("uneven-study-20x32", tuple(strings), 5000)
+
+
+# ---- the paper's monolayer (Sec. IV) ------------------------------------------------------------------
+# 112 x 112 x 1 sites on a simple cubic lattice, a = 0.2715 nm, |S| = 2.3737 mu_B, J = 54.23 meV, 60 images
+# per string; the DM and anisotropy energies d and k are varied.  In the library's reduced units energies
+# are in J: D = d / J, K = k / J and w = mu0 |S|^2 / (4 pi a^3) / J.
+PAPER_A_NM = 0.2715
+PAPER_MOMENT_MUB = 2.3737
+PAPER_J_MEV = 54.23
+MU0 = 1.25663706212e-6          # vacuum permeability, N / A^2 (CODATA 2018)
+MU_B = 9.2740100783e-24         # Bohr magneton, J / T (CODATA 2018)
+MEV = 1.602176634e-22           # 1 meV in J (exact)
+
+
+def paper_w() -> float:
+    """Reduced dipole strength w / J of the paper's constants (about 2.79e-4)."""
+    S = PAPER_MOMENT_MUB * MU_B
+    a = PAPER_A_NM * 1e-9
+    return MU0 * S * S / (4.0 * math.pi * a ** 3) / (PAPER_J_MEV * MEV)
+
+
+def paper_monolayer(d_meV: float = 5.30, k_meV: float = 1.0, path: str = "bloch", n_images: int = 60) -> StringSpec:
+    """One string of the paper's monolayer: d and k in meV; initial skyrmion radius 14 sites (nx/8)."""
+    return StringSpec(112, 112, 1, 1.0, d_meV / PAPER_J_MEV, k_meV / PAPER_J_MEV, paper_w(), n_images, path, 14.0)
+
+
+def paper_monolayer_workload() -> Workload:
+    """The paper's monolayer at d = 5.30 meV (its Fig. 4 value), k = 1.0 meV, Bloch-point path, 5000
+    iterations (the paper runs 100-10000)."""
+    return Workload("paper-monolayer-112x112x1-K60", (paper_monolayer(),), 5000)
+
+
+PHASE_D_MEV = (4.5, 5.3, 6.1)
+PHASE_K_MEV = (0.8, 1.2, 1.6)
+
+
+def paper_phase_diagram() -> Workload:
+    """A 3 x 3 (d, k) grid in meV around the paper's d = 5.30 meV, for both annihilation paths (18 strings
+    of 60 images on the 112 x 112 x 1 monolayer), 5000 iterations."""
+    strings = tuple(paper_monolayer(d, k, path) for path in ("bloch", "boundary") for d in PHASE_D_MEV for k in PHASE_K_MEV)
+    return Workload("paper-phase-diagram-112x112x1-18x60", strings, 5000)
+

@@ -49,7 +49,8 @@ FIELD_CASES = [
 
 
 def _padded(n):
-    """Smallest 2^a 3^b >= 2n - 1 (the zero-padded transform length)."""
+    """The zero-padded transform length: the smallest 2^a 3^b >= 2n - 1, or the power of two >= 2n - 1
+    when that is at most 1/8 longer."""
     m = 2 * n - 1
     best = None
     a = 1
@@ -60,7 +61,10 @@ def _padded(n):
                 best = b
             b *= 3
         a *= 2
-    return best
+    p2 = 1
+    while p2 < m:
+        p2 *= 2
+    return p2 if 8 * p2 <= 9 * best else best
 
 
 @pytest.mark.parametrize("prec", [FP32, FP64])
@@ -232,6 +236,40 @@ def test_long_and_short_strings_in_one_size_group(ss, prec):
         # oracle's path after n_iter - 1 iterations
         _, e_prev = oracle.string_run(_model(c), _unit(s0), n_iter - 1, 0.1)
         np.testing.assert_allclose(e, e_prev, rtol=0, atol=tol * 10)
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_paper_monolayer(ss, prec):
+    # the paper's 112x112x1 monolayer (Sec. IV constants, d = 5.30 meV, padded length 256): the field at
+    # sampled sites of two images, then three iterations of a six-image sub-string (images 0, 12, ..., 48
+    # and the last) against the oracle
+    spec = W.paper_monolayer()
+    path = spec.initial_path()
+    sub = np.concatenate([path[:-1:12], path[-1:]])
+    case = (spec.nx, spec.ny, spec.nz, spec.J, spec.D, spec.K, spec.w, sub.shape[0])
+    m = _model(case)
+    sites = np.random.default_rng(5).integers(0, spec.n_sites, size=64)
+    with _sm(ss, [case], precision=prec) as sm:
+        sm.set_path(0, sub)
+        start = sm.get_path(0)
+        h = sm.field(0)
+        sm.step(3)
+        got = sm.get_path(0)
+        e = sm.energies(0)
+        dE, k = sm.barrier(0)
+    for img in (1, 3):
+        ref = oracle.field_at(m, _unit(start[img]), sites)
+        assert np.abs(h[img][sites] - ref).max() <= (1e-5 if prec == FP32 else 1e-12) * np.abs(ref).max()
+    ref, e_ref = oracle.string_run(m, _unit(start), 3, 0.1)
+    dE_ref, k_ref = oracle.barrier(e_ref)
+    assert np.abs(got - ref).max() < (1e-5 if prec == FP32 else 1e-12)
+    # FP32: the two states differ by rounding, so to first order dE = -sum h . ds with independent
+    # per-component errors of about u |s| per step: RMS u |h| sqrt(3N) ~ 6e-8 * 4 * 194 ~ 5e-5 per step,
+    # 1.4e-4 after three; 1e-3 leaves a margin of seven.  FP64: energies near -2.5e4 are sums of 3N terms
+    # in different orders on the two sides, so 1e-12 relative
+    tol = 1e-3 if prec == FP32 else 1e-12 * np.abs(e_ref).max()
+    np.testing.assert_allclose(e, e_ref, rtol=0, atol=tol)
+    assert abs(dE - dE_ref) < tol and k == k_ref
 
 
 @pytest.mark.parametrize("dims", [(64, 64, 8), (192, 192, 8)])
