@@ -66,6 +66,8 @@ def _load():
             "or_step": (None, [i, d, dp, dp]),
             "or_reparam": (None, [i, i, dp, dp, dp]),
             "or_string_run": (i, [mp, i, i, d, dp, dp]),
+            "or_string_run_rk": (i, [mp, i, i, d, d, d, dp, dp, dp, P(ctypes.c_long)]),
+            "or_dp_tableau": (None, [dp, dp, dp]),
             "or_barrier": (d, [i, dp, P(i)]),
             "or_energy_param_grad": (None, [mp, dp, dp]),
             "or_max_threads": (i, []),
@@ -185,6 +187,31 @@ def string_run(m: OracleModel, path, n_iter: int, dt: float, with_energies: bool
                              _ptr(e) if with_energies else None) != 0:
         raise MemoryError("oracle string run: out of memory")
     return phi, e
+
+
+def string_run_rk(m: OracleModel, path, n_iter: int, T: float, rtol: float = 1e-6, atol: float = 1e-8,
+                  step: float | None = None, with_energies: bool = True):
+    """Sec. III loop with the Dormand-Prince 5(4) evolution of the string over T per iteration.
+    Returns (final path, energies or None, carried step, (accepted, rejected))."""
+    phi = _f64(path).copy()
+    K = phi.shape[0]
+    e = np.zeros(K) if with_energies else None
+    h = ctypes.c_double(T if step is None else step)
+    counts = (ctypes.c_long * 2)()
+    rc = _load().or_string_run_rk(ctypes.byref(m), K, int(n_iter), float(T), float(rtol), float(atol),
+                                  ctypes.byref(h), _ptr(phi), _ptr(e) if with_energies else None, counts)
+    if rc == -1:
+        raise MemoryError("oracle RK string run: out of memory")
+    if rc != 0:
+        raise RuntimeError("oracle RK string run: step size collapsed or non-finite error norm")
+    return phi, e, h.value, (counts[0], counts[1])
+
+
+def dp_tableau():
+    """The Dormand-Prince 5(4) coefficients the oracle uses: (a[7][6], b[7], bhat[7])."""
+    a, b, bh = np.zeros((7, 6)), np.zeros(7), np.zeros(7)
+    _load().or_dp_tableau(_ptr(a), _ptr(b), _ptr(bh))
+    return a, b, bh
 
 
 def barrier(energies_) -> tuple[float, int]:

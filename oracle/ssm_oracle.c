@@ -332,6 +332,159 @@ int or_string_run(const or_model* m, int K, int n_iter, double dt, double* phi, 
 
 /* Sec. III: the barrier is the energy of the highest image relative to the first image.  Ties go
  * to the lowest index. */
+/* Adaptive explicit Runge-Kutta evolution of the images (Sec. III: "explicit Runge-Kutta methods with
+ * adaptive step-size control ... the Dormand-Prince method"), in place of the fixed projected-Euler step
+ * of or_string_run.  Each iteration integrates the whole string, read as one ODE system
+ *     d phi_k / d tau = F(phi_k) = h(phi_k) - (phi_k . h(phi_k)) phi_k      (Eq. 13, every image k)
+ * over the reduced interval T with the Dormand-Prince 5(4) pair, then reparametrises (Eqs. 11-12).
+ * Stage states are not renormalised (h is evaluated on them as they are); each accepted step is
+ * followed by per-site renormalisation.  Error norm: err = sqrt(mean_j (e_j / sc_j)^2) over all
+ * K * 3N components, e = step * sum_i (b_i - bhat_i) k_i, sc_j = atol + rtol * max(|y_j|, |y5_j|).
+ * A step is accepted when err <= 1.  Next step: step * clamp(0.9 err^(-1/5), 0.2, 5) after an
+ * accepted step, with the upper bound 1 after a rejected one.  Attempts are cut to end exactly at T.
+ * *step_io carries the step from one iteration to the next (set it to T before the first).
+ * counts (optional): [accepted, rejected] summed over the iterations.  Returns 0, -1 (memory), or
+ * -2 (more than 100000 attempts in one iteration, or a non-finite error norm). */
+static const double DP_A[7][6] = {
+    {0, 0, 0, 0, 0, 0},
+    {1.0 / 5.0, 0, 0, 0, 0, 0},
+    {3.0 / 40.0, 9.0 / 40.0, 0, 0, 0, 0},
+    {44.0 / 45.0, -56.0 / 15.0, 32.0 / 9.0, 0, 0, 0},
+    {19372.0 / 6561.0, -25360.0 / 2187.0, 64448.0 / 6561.0, -212.0 / 729.0, 0, 0},
+    {9017.0 / 3168.0, -355.0 / 33.0, 46732.0 / 5247.0, 49.0 / 176.0, -5103.0 / 18656.0, 0},
+    {35.0 / 384.0, 0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0, 11.0 / 84.0}};
+static const double DP_B[7] = {35.0 / 384.0, 0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0, 11.0 / 84.0, 0};
+static const double DP_BHAT[7] = {5179.0 / 57600.0, 0,      7571.0 / 16695.0, 393.0 / 640.0, -92097.0 / 339200.0,
+                                  187.0 / 2100.0,  1.0 / 40.0};
+
+void or_dp_tableau(double a[7][6], double b[7], double bhat[7]) {
+    memcpy(a, DP_A, sizeof(DP_A));
+    memcpy(b, DP_B, sizeof(DP_B));
+    memcpy(bhat, DP_BHAT, sizeof(DP_BHAT));
+}
+
+/* F of Eq. 13 for every image of y (K images of M = 3N components) into f. */
+static void force_all(const or_model* m, const double* table, int K, const double* y, double* hbuf, double* f) {
+    const int N = m->nx * m->ny * m->nz;
+    const size_t M = (size_t)3 * N;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int k = 0; k < K; ++k) {
+        const double* yk = y + k * M;
+        double* hk = hbuf + k * M;
+        field_one(m, table, yk, hk);
+        for (int i = 0; i < N; ++i) {
+            const double* si = yk + 3 * i;
+            const double* hi = hk + 3 * i;
+            const double sh = si[0] * hi[0] + si[1] * hi[1] + si[2] * hi[2];
+            for (int c = 0; c < 3; ++c) f[k * M + 3 * i + c] = hi[c] - sh * si[c];
+        }
+    }
+}
+
+int or_string_run_rk(const or_model* m, int K, int n_iter, double T, double rtol, double atol, double* step_io,
+                     double* phi, double* energies, long* counts) {
+    const int N = m->nx * m->ny * m->nz;
+    const size_t M = (size_t)3 * N, L = M * (size_t)K;
+    double* table = NULL;
+    if (m->w != 0.0) {
+        table = dipole_table(m);
+        if (!table) return -1;
+    }
+    double* kk = (double*)malloc(sizeof(double) * L * 7);
+    double* ys = (double*)malloc(sizeof(double) * L);
+    double* y5 = (double*)malloc(sizeof(double) * L);
+    double* hb = (double*)malloc(sizeof(double) * L);
+    if (!kk || !ys || !y5 || !hb) {
+        free(table);
+        free(kk);
+        free(ys);
+        free(y5);
+        free(hb);
+        return -1;
+    }
+    int rc = 0;
+    double step = *step_io;
+    long acc = 0, rej = 0;
+    for (int it = 0; it < n_iter && rc == 0; ++it) {
+        double t = 0.0;
+        int have_k1 = 0, attempts = 0;
+        while (t < T) {
+            if (++attempts > 100000) {
+                rc = -2;
+                break;
+            }
+            const double hs = step < T - t ? step : T - t;
+            if (!have_k1) force_all(m, table, K, phi, hb, kk);
+            have_k1 = 1;
+            for (int st = 1; st < 7; ++st) {
+                for (size_t j = 0; j < L; ++j) {
+                    double a = 0.0;
+                    for (int q = 0; q < st; ++q) a += DP_A[st][q] * kk[q * L + j];
+                    ys[j] = phi[j] + hs * a;
+                }
+                force_all(m, table, K, ys, hb, kk + st * L);
+            }
+            double e2 = 0.0;
+            for (size_t j = 0; j < L; ++j) {
+                double b5 = 0.0, e = 0.0;
+                for (int q = 0; q < 7; ++q) {
+                    b5 += DP_B[q] * kk[q * L + j];
+                    e += (DP_B[q] - DP_BHAT[q]) * kk[q * L + j];
+                }
+                y5[j] = phi[j] + hs * b5;
+                const double ay = fabs(phi[j]), a5 = fabs(y5[j]);
+                const double sc = atol + rtol * (ay > a5 ? ay : a5);
+                const double r = hs * e / sc;
+                e2 += r * r;
+            }
+            const double err = sqrt(e2 / (double)L);
+            if (!isfinite(err)) {
+                rc = -2;
+                break;
+            }
+            double fac = err > 0.0 ? 0.9 * pow(err, -0.2) : 5.0;
+            if (fac < 0.2) fac = 0.2;
+            if (err <= 1.0) {
+                if (fac > 5.0) fac = 5.0;
+                t = hs == T - t ? T : t + hs;
+                for (int k = 0; k < K; ++k)
+                    for (int i = 0; i < N; ++i) {
+                        const double* v = y5 + k * M + 3 * i;
+                        const double n = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+                        for (int c = 0; c < 3; ++c) phi[k * M + 3 * i + c] = v[c] / n;
+                    }
+                have_k1 = 0;
+                ++acc;
+            } else {
+                if (fac > 1.0) fac = 1.0;
+                ++rej;
+            }
+            step = hs * fac;
+        }
+        if (rc) break;
+        memcpy(ys, phi, sizeof(double) * L);
+        or_reparam(K, N, ys, phi, NULL);
+    }
+    *step_io = step;
+    if (counts) {
+        counts[0] = acc;
+        counts[1] = rej;
+    }
+    if (rc == 0 && energies) {
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int k = 0; k < K; ++k) {
+            field_one(m, table, phi + k * M, hb + k * M);
+            energies[k] = or_energy_from_field(N, phi + k * M, hb + k * M);
+        }
+    }
+    free(table);
+    free(kk);
+    free(ys);
+    free(y5);
+    free(hb);
+    return rc;
+}
+
 double or_barrier(int K, const double* energies, int* k_max) {
     int kb = 0;
     for (int k = 1; k < K; ++k)

@@ -1,0 +1,77 @@
+"""Pins of the oracle's adaptive Runge-Kutta string evolution (Sec. III, Dormand-Prince 5(4)), CPU.
+
+* the tableau satisfies the order conditions of a 5th-order method (b) with an embedded 4th-order one
+  (bhat), and its rows sum to the nodes c = (0, 1/5, 3/10, 4/5, 8/9, 1, 1): a wrong coefficient fails;
+* a lone spin under uniaxial anisotropy relaxes as dtheta/dtau = -K sin(2 theta) (Eq. 13 with
+  h = 2K s_z z), i.e. tan(theta) = tan(theta0) exp(-2 K tau), and the integrator follows it within its
+  tolerance, more closely as the tolerance tightens;
+* a state where F = 0 is a fixed point (no rejected steps, no motion).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+
+C = np.array([0, 1 / 5, 3 / 10, 4 / 5, 8 / 9, 1, 1])
+
+
+def test_dormand_prince_order_conditions():
+    a, b, bh = oracle.dp_tableau()
+    A = np.zeros((7, 7))
+    A[:, :6] = a
+    np.testing.assert_allclose(A.sum(1), C, atol=1e-15)
+    for w, order in ((b, 5), (bh, 4)):
+        assert abs(w.sum() - 1) < 1e-15
+        for p in range(1, order):  # quadrature conditions sum w c^p = 1/(p+1)
+            assert abs(w @ C ** p - 1 / (p + 1)) < 1e-14, (order, p)
+        assert abs(w @ (A @ C) - 1 / 6) < 1e-14
+        assert abs(w @ (A @ C ** 2) - 1 / 12) < 1e-14
+        assert abs(w @ (C * (A @ C)) - 1 / 8) < 1e-14
+        assert abs(w @ (A @ (A @ C)) - 1 / 24) < 1e-14
+    # fifth-order conditions hold for b only (bhat is the embedded fourth-order solution)
+    assert abs(b @ (C ** 2 * (A @ C)) - 1 / 10) < 1e-14
+    assert abs(b @ (A @ C ** 3) - 1 / 20) < 1e-14
+    assert abs(b @ (A @ (A @ (A @ C))) - 1 / 120) < 1e-14
+    assert abs(bh @ (A @ (A @ (A @ C))) - 1 / 120) > 1e-6
+
+
+def _lone_spins(thetas):
+    return np.array([[[math.sin(t), 0.0, math.cos(t)]] for t in thetas])
+
+
+@pytest.mark.parametrize("rtol", [1e-6, 1e-9])
+def test_lone_spin_anisotropy_relaxation_closed_form(rtol):
+    K, T, n = 0.7, 0.5, 6
+    m = oracle.model(1, 1, 1, 0.0, 0.0, K, 0.0)
+    th0 = [1.0, 2.0]  # two single-spin images; a two-image string keeps both ends under reparametrisation
+    phi, _, _, (acc, rej) = oracle.string_run_rk(m, _lone_spins(th0), n, T, rtol=rtol, atol=rtol * 1e-2)
+    for k, t0 in enumerate(th0):
+        want = math.atan2(math.tan(t0) * math.exp(-2 * K * n * T), 1.0)
+        want = want + math.pi if t0 > math.pi / 2 else want
+        got = math.atan2(phi[k, 0, 0], phi[k, 0, 2])
+        assert abs(got - want) < 50 * rtol, (rtol, got - want)
+    assert acc >= n
+
+
+def test_tighter_tolerance_is_closer():
+    K, T, n = 0.7, 0.5, 4
+    m = oracle.model(1, 1, 1, 0.0, 0.0, K, 0.0)
+    errs = []
+    for rtol in (1e-4, 1e-8):
+        phi, _, _, _ = oracle.string_run_rk(m, _lone_spins([1.0, 2.0]), n, T, rtol=rtol, atol=rtol * 1e-2)
+        want = math.atan(math.tan(1.0) * math.exp(-2 * K * n * T))
+        errs.append(abs(math.atan2(phi[0, 0, 0], phi[0, 0, 2]) - want))
+    assert errs[1] < errs[0] / 100
+
+
+def test_fixed_point_is_kept():
+    # uniform +z on a 4x4x2 lattice with exchange and K > 0 only (DMI and the dipole field both tilt
+    # the edge spins of an open sample): h is parallel to s everywhere, F = 0
+    m = oracle.model(4, 4, 2, 1.0, 0.0, 0.1, 0.0)
+    path = np.zeros((3, 32, 3))
+    path[..., 2] = 1.0
+    phi, _, _, (acc, rej) = oracle.string_run_rk(m, path, 3, 0.2)
+    np.testing.assert_allclose(phi, path, atol=1e-14)
+    assert rej == 0 and acc == 3
