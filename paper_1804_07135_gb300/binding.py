@@ -21,6 +21,7 @@ SS_OK, SS_ERR_INVALID_ARG, SS_ERR_CUDA, SS_ERR_OOM, SS_ERR_NONFINITE, SS_ERR_TIM
 SS_DTYPE_F32, SS_DTYPE_F64 = 0, 1
 SS_PREC_FP32, SS_PREC_FP64 = 0, 1
 SS_DIPOLE_OFF, SS_DIPOLE_FFT = 0, 2
+SS_INT_EULER, SS_INT_DOPRI5 = 0, 1
 _STATUS = {0: "SS_OK", 1: "SS_ERR_INVALID_ARG", 2: "SS_ERR_CUDA", 3: "SS_ERR_OOM", 4: "SS_ERR_NONFINITE",
            5: "SS_ERR_TIMEOUT", 6: "SS_ERR_STATE"}
 
@@ -55,6 +56,9 @@ _SIGNATURES = {
     "ss_set_path": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "ss_get_path": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "ss_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "ss_set_integrator": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double]),
+    "ss_integrator_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
     "ss_energies": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "ss_step_energies": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "ss_barrier": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -241,6 +245,18 @@ def ss_step(ctx, n_iter: int) -> None:
     _check(_lib.ss_step(ctx, int(n_iter)), ctx)
 
 
+def ss_set_integrator(ctx, kind: int, rtol: float = 1e-6, atol: float = 1e-8) -> None:
+    _check(_lib.ss_set_integrator(ctx, int(kind), float(rtol), float(atol)), ctx)
+
+
+def ss_integrator_state(ctx, string: int) -> tuple[float, int, int]:
+    """(carried step, accepted attempts, rejected attempts) of the adaptive integrator."""
+    h = ctypes.c_double()
+    a, r = ctypes.c_longlong(), ctypes.c_longlong()
+    _check(_lib.ss_integrator_state(ctx, int(string), ctypes.byref(h), ctypes.byref(a), ctypes.byref(r)), ctx)
+    return float(h.value), int(a.value), int(r.value)
+
+
 def ss_energies(ctx, string: int) -> np.ndarray:
     d = ss_string_info(ctx, string)
     out = np.zeros(d.n_images)
@@ -365,6 +381,12 @@ class StringMethod:
 
     def step(self, n_iter):
         ss_step(self.ctx, n_iter)
+
+    def set_integrator(self, kind, rtol=1e-6, atol=1e-8):
+        ss_set_integrator(self.ctx, kind, rtol, atol)
+
+    def integrator_state(self, string=0):
+        return ss_integrator_state(self.ctx, string)
 
     def energies(self, string=0):
         return ss_energies(self.ctx, string)

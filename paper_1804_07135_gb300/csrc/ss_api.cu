@@ -93,6 +93,14 @@ struct Group {
     int *d_str_img0 = nullptr, *d_str_K = nullptr;
     double *dpart = nullptr, *e_last = nullptr, *eval_terms = nullptr, *eval_E = nullptr;
     unsigned* arc_cnt = nullptr;
+    // adaptive Runge-Kutta evolution (allocated by ss_set_integrator)
+    void *rk_y0 = nullptr, *rk_k = nullptr, *rk_y5 = nullptr;
+    double* rk_errp = nullptr;
+    RkString* rk_st = nullptr;
+    int* rk_img_str = nullptr;
+    int* rk_active = nullptr;
+    InterpEntry* interp_ident = nullptr;
+    int rk_tiles = 0;
     ArcArgs arc{};
 };
 
@@ -117,6 +125,9 @@ struct ss_ctx {
     std::vector<void*> allocs;
     cudaGraphExec_t graph1 = nullptr, graphN = nullptr;
     int graphN_iters = 64;
+    int integrator = 0;  // SS_INT_EULER or SS_INT_DOPRI5
+    double rtol = 1e-6, atol = 1e-8;
+    int* h_active = nullptr;  // pinned, one flag per size group
     std::string err;
 };
 
@@ -462,6 +473,107 @@ template <typename T> ss_status tune_group(ss_ctx* c, Group& g) {
     return SS_OK;
 }
 
+// ---- adaptive Runge-Kutta evolution (Sec. III, Dormand-Prince 5(4)) -------------------------------------
+RkString rk_fresh(const ss_ctx* c) {
+    RkString r{};
+    r.step = c->opts.dt;
+    r.hs = c->opts.dt;
+    return r;
+}
+
+template <typename T> RkArgs<T> rk_args(const ss_ctx* c, const Group& g) {
+    RkArgs<T> r{};
+    r.y0 = (T*)g.rk_y0;
+    r.k = (T*)g.rk_k;
+    r.y5 = (T*)g.rk_y5;
+    r.errp = g.rk_errp;
+    r.n_tiles = g.rk_tiles;
+    r.st = g.rk_st;
+    r.img_str = g.rk_img_str;
+    r.active = g.rk_active;
+    r.T_int = c->opts.dt;
+    r.rtol = c->rtol;
+    r.atol = c->atol;
+    return r;
+}
+
+ss_status rk_setup(ss_ctx* c, Group& g) {
+    if (g.rk_y0) return SS_OK;
+    const size_t M = (size_t)3 * g.N, L = M * g.n_img, rs = real_size(c);
+    g.rk_tiles = (int)((M + 1023) / 1024);
+    TRY(dalloc(c, &g.rk_y0, L * rs));
+    TRY(dalloc(c, &g.rk_k, 7 * L * rs));
+    TRY(dalloc(c, &g.rk_y5, L * rs));
+    TRY(dalloc(c, (void**)&g.rk_errp, (size_t)g.n_img * g.rk_tiles * sizeof(double)));
+    TRY(dalloc(c, (void**)&g.rk_st, g.strs.size() * sizeof(RkString)));
+    TRY(dalloc(c, (void**)&g.rk_img_str, g.n_img * sizeof(int)));
+    TRY(dalloc(c, (void**)&g.rk_active, sizeof(int)));
+    TRY(dalloc(c, (void**)&g.interp_ident, g.n_img * sizeof(InterpEntry)));
+    std::vector<int> img_str(g.n_img);
+    for (size_t i = 0; i < g.strs.size(); ++i)
+        for (int k = 0; k < g.str_K[i]; ++k) img_str[g.str_img0[i] + k] = (int)i;
+    std::vector<RkString> st(g.strs.size(), rk_fresh(c));
+    CUDA_TRY(c, cudaMemcpyAsync(g.rk_img_str, img_str.data(), g.n_img * sizeof(int), cudaMemcpyHostToDevice, c->cs));
+    CUDA_TRY(c, cudaMemcpyAsync(g.rk_st, st.data(), st.size() * sizeof(RkString), cudaMemcpyHostToDevice, c->cs));
+    CUDA_TRY(c, cudaMemsetAsync(g.rk_k, 0, 7 * L * rs, c->cs));
+    launch_interp_identity(g.interp_ident, 0, g.n_img, c->cs);
+    CUDA_TRY(c, cudaGetLastError());
+    return SS_OK;
+}
+
+// n_iter iterations: per iteration every string integrates over opts.dt with Dormand-Prince attempts (one
+// host synchronisation per attempt round decides whether another is needed), then the arc kernel
+// reparametrises and sums the energies of the state the interval started from.
+template <typename T> ss_status rk_iterations(ss_ctx* c, int n_iter) {
+    const size_t ng = c->groups.size();
+    for (int it = 0; it < n_iter; ++it) {
+        std::vector<char> active(ng, 1);
+        for (size_t gi = 0; gi < ng; ++gi) {
+            Group& g = c->groups[gi];
+            GroupArgs<T> a = group_args<T>(c, g);
+            GroupArgs<T> ai = a;
+            ai.interp = g.interp_ident;
+            RkArgs<T> r = rk_args<T>(c, g);
+            launch_xfwd<T>(a, false, g.thr_a, 0, c->cs);  // s = reparametrised state
+            CUDA_TRY(c, cudaMemcpyAsync(r.y0, a.s, (size_t)3 * g.N * g.n_img * sizeof(T), cudaMemcpyDeviceToDevice, c->cs));
+            launch_rk_control<T>(ai, r, g.arc, 1, c->cs);
+        }
+        for (int round = 0;; ++round) {
+            bool any = false;
+            for (size_t gi = 0; gi < ng; ++gi) {
+                if (!active[gi]) continue;
+                Group& g = c->groups[gi];
+                GroupArgs<T> ai = group_args<T>(c, g);
+                ai.interp = g.interp_ident;
+                RkArgs<T> r = rk_args<T>(c, g);
+                const size_t stride = (size_t)3 * g.N * g.n_img;
+                for (int st = 0; st < 7; ++st) {
+                    launch_rk_assemble<T>(ai, r, st, c->cs);
+                    launch_xfwd<T>(ai, g.dipole, g.thr_a, g.smem_a, c->cs);
+                    if (g.dipole) launch_yz<T>(ai, g.thr_b, g.smem_b, c->cs);
+                    launch_xinv_force<T>(ai, g.dipole, r.k + st * stride, round == 0 && st == 0, g.thr_c, g.smem_c_eval,
+                                         c->cs);
+                }
+                launch_rk_finish<T>(ai, r, c->cs);
+                launch_rk_control<T>(ai, r, g.arc, 0, c->cs);
+                launch_rk_commit<T>(ai, r, c->cs);
+                CUDA_TRY(c, cudaMemcpyAsync(&c->h_active[gi], r.active, sizeof(int), cudaMemcpyDeviceToHost, c->cs));
+                any = true;
+            }
+            if (!any) break;
+            CUDA_TRY(c, cudaGetLastError());
+            CUDA_TRY(c, cudaStreamSynchronize(c->cs));
+            for (size_t gi = 0; gi < ng; ++gi)
+                if (active[gi]) active[gi] = c->h_active[gi] != 0;
+        }
+        for (Group& g : c->groups) {
+            GroupArgs<T> a = group_args<T>(c, g);
+            launch_arc<T>(a, g.arc, g.thr_arc, c->cs);
+        }
+    }
+    return SS_OK;
+}
+
 // Issue one iteration (Sec. III) of every size group on stream st.
 template <typename T> void issue_iteration(ss_ctx* c, cudaStream_t st) {
     const T dt = T(c->opts.dt);
@@ -511,6 +623,8 @@ ss_status sync_check(ss_ctx* c) {
     if (h) {
         CUDA_TRY(c, cudaMemset(c->d_err, 0, sizeof(int)));
         if (h & kErrInvalidSpin) return fail(c, SS_ERR_INVALID_ARG, "input spin with zero norm or non-finite component");
+        if (h & kErrStepCollapse)
+            return fail(c, SS_ERR_NONFINITE, "Runge-Kutta step size collapsed (more than 100000 attempts in one interval)");
         return fail(c, SS_ERR_NONFINITE, "non-finite energy or arc length on the device");
     }
     return SS_OK;
@@ -754,11 +868,52 @@ ss_status ss_set_path(ss_ctx* c, int string, const void* spins, int dtype, int o
             launch_aos_to_soa<float, float>((const float*)src, dst, K, g.N, c->d_err, c->cs);
     }
     launch_interp_identity(g.interp, r.img0, K, c->cs);
+    if (g.rk_st) {  // the adaptive integrator restarts from step opts.dt on a new path
+        const RkString fresh = rk_fresh(c);
+        CUDA_TRY(c, cudaMemcpyAsync(g.rk_st + r.local, &fresh, sizeof fresh, cudaMemcpyHostToDevice, c->cs));
+    }
     CUDA_TRY(c, cudaGetLastError());
     ss_status st = sync_check(c);
     TRY(leave(c));
     if (st != SS_OK) return st;
     r.has_path = true;
+    return SS_OK;
+}
+
+ss_status ss_set_integrator(ss_ctx* c, int kind, double rtol, double atol) {
+    if (!c) return SS_ERR_INVALID_ARG;
+    if (kind != SS_INT_EULER && kind != SS_INT_DOPRI5) return fail(c, SS_ERR_INVALID_ARG, "unknown integrator %d", kind);
+    if (kind == SS_INT_DOPRI5 && !(rtol > 0.0 && atol > 0.0 && std::isfinite(rtol) && std::isfinite(atol)))
+        return fail(c, SS_ERR_INVALID_ARG, "rtol and atol must be positive and finite");
+    TRY(enter(c));
+    if (kind == SS_INT_DOPRI5) {
+        if (!c->h_active) CUDA_TRY(c, cudaHostAlloc((void**)&c->h_active, c->groups.size() * sizeof(int), cudaHostAllocDefault));
+        for (Group& g : c->groups) TRY(rk_setup(c, g));
+        c->rtol = rtol;
+        c->atol = atol;
+    }
+    c->integrator = kind;
+    ss_status st = sync_check(c);
+    TRY(leave(c));
+    return st;
+}
+
+ss_status ss_integrator_state(ss_ctx* c, int string, double* step, long long* accepted, long long* rejected) {
+    TRY(check_string(c, string));
+    if (!step || !accepted || !rejected) return fail(c, SS_ERR_INVALID_ARG, "output pointer is NULL");
+    const StringRec& r = c->strs[string];
+    const Group& g = c->groups[r.group];
+    RkString h = rk_fresh(c);
+    if (g.rk_st) {
+        TRY(enter(c));
+        CUDA_TRY(c, cudaMemcpyAsync(&h, g.rk_st + r.local, sizeof h, cudaMemcpyDeviceToHost, c->cs));
+        ss_status st = sync_check(c);
+        TRY(leave(c));
+        if (st != SS_OK) return st;
+    }
+    *step = h.step;
+    *accepted = h.acc;
+    *rejected = h.rej;
     return SS_OK;
 }
 
@@ -787,6 +942,10 @@ ss_status ss_step(ss_ctx* c, int n_iter) {
     for (const Group& g : c->groups) TRY(check_paths(c, g));
     if (n_iter == 0) return SS_OK;
     TRY(enter(c));
+    if (c->integrator == SS_INT_DOPRI5) {
+        TRY(use_fp64(c) ? rk_iterations<double>(c, n_iter) : rk_iterations<float>(c, n_iter));
+        return leave(c);
+    }
     const int G = c->graphN_iters;
     if (n_iter >= G && !c->graphN) TRY(capture_graph(c, G, &c->graphN));
     if (n_iter % G && !c->graph1) TRY(capture_graph(c, 1, &c->graph1));
@@ -975,6 +1134,7 @@ void ss_destroy(ss_ctx* c) {
     if (c->graph1) cudaGraphExecDestroy(c->graph1);
     if (c->graphN) cudaGraphExecDestroy(c->graphN);
     for (void* p : c->allocs) cudaFree(p);
+    if (c->h_active) cudaFreeHost(c->h_active);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
     if (c->ev_out) cudaEventDestroy(c->ev_out);
     if (c->cs) cudaStreamDestroy(c->cs);

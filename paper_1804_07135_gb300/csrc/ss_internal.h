@@ -103,7 +103,33 @@ struct ArcArgs {
     int reparam;           // 0: keep images where they are
 };
 
-enum { kErrInvalidSpin = 1, kErrNonFinite = 2 };
+// Adaptive Runge-Kutta evolution (Sec. III, Dormand-Prince 5(4)): controller state of one string.
+struct RkString {
+    double t;           // reduced time reached within the current interval
+    double step;        // step carried between attempts and intervals
+    double hs;          // step of the current attempt (step cut to end at the interval's end)
+    double err;         // error norm of the last attempt
+    long long acc, rej; // accepted and rejected attempts since the path was set
+    int done;           // the interval is complete
+    int accepted;       // the last attempt was accepted
+    int attempts;       // attempts in the current interval
+    int pad;
+};
+
+// Device buffers and constants of the Runge-Kutta evolution of one size group.
+template <typename T> struct RkArgs {
+    T* y0;            // [image][3][N] state at the start of the attempt
+    T* k;             // [7][image][3][N] stage forces
+    T* y5;            // [image][3][N] fifth-order solution of the attempt
+    double* errp;     // [image][tile] squared scaled-error partials
+    int n_tiles;      // tiles of 1024 components per image
+    RkString* st;     // [n_str]
+    const int* img_str;  // [n_img] string of each image
+    int* active;      // any string still inside its interval (written by the controller)
+    double T_int, rtol, atol;
+};
+
+enum { kErrInvalidSpin = 1, kErrNonFinite = 2, kErrStepCollapse = 4 };
 
 // Length-128 transforms in two register passes (FP32): the x kernels when Px = 128, the y/z kernel
 // when Py = 128 and nz is 4 or 8.  16 threads per line; their launch shapes follow from the rows per
@@ -136,6 +162,15 @@ template <typename T>
 void launch_xinv_step(const GroupArgs<T>& g, bool do_fft, T dt, int nthr, size_t smem, cudaStream_t st);
 template <typename T>
 void launch_xinv_eval(const GroupArgs<T>& g, bool do_fft, T* hout, int nthr, size_t smem, cudaStream_t st);
+// Runge-Kutta stage: the force of Eq. 13 at the state in s into kout; energy partials when energies
+template <typename T>
+void launch_xinv_force(const GroupArgs<T>& g, bool do_fft, T* kout, bool energies, int nthr, size_t smem,
+                       cudaStream_t st);
+template <typename T> void launch_rk_assemble(const GroupArgs<T>& g, const RkArgs<T>& r, int stage, cudaStream_t st);
+template <typename T> void launch_rk_finish(const GroupArgs<T>& g, const RkArgs<T>& r, cudaStream_t st);
+template <typename T>
+void launch_rk_control(const GroupArgs<T>& g, const RkArgs<T>& r, const ArcArgs& a, int begin, cudaStream_t st);
+template <typename T> void launch_rk_commit(const GroupArgs<T>& g, const RkArgs<T>& r, cudaStream_t st);
 template <typename T> void launch_arc(const GroupArgs<T>& g, const ArcArgs& a, int nthr, cudaStream_t st);
 template <typename T>
 void launch_eval_reduce(const GroupArgs<T>& g, const ArcArgs& a, double* terms, double* energies, cudaStream_t st);

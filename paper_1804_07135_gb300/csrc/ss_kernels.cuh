@@ -685,14 +685,16 @@ __device__ __forceinline__ void xinv_sites_step2(const GroupArgs<float>& g, floa
 // ------------------------------------------------------------------------------------------------
 // Per-site work of the x-inverse kernels on rows [y0, y0+rows) of layer z, pair p; buf holds the
 // forward transforms of the conjugated field spectra (line c*rows + yy, fft_pad positions) when
-// HAS_CONV.
+// HAS_CONV.  MODE 0: projected Euler step into sp and energy partials.  MODE 1: FP64 energy terms (and
+// the field into hout when given).  MODE 2 (a Runge-Kutta stage): the force F = h - (s.h) s of Eq. 13
+// into hout, s as stored (not renormalised); energy partials only when dt != 0.
 template <typename T, bool HAS_CONV, int MODE>
 __device__ __forceinline__ void xinv_sites(const GroupArgs<T>& g, T dt, T* hout, const cplx<T>* buf, int ls,
                                            double* red, int p, int z, int y0, int rows, int tid, int nthr) {
     using C = cplx<T>;
     const int nx = g.nx, ny = g.ny, nz = g.nz, N = g.N;
     const int ia = 2 * p;
-    constexpr int NV = MODE == 0 ? 2 : 8;
+    constexpr int NV = MODE == 1 ? 8 : 2;
     double acc[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) acc[k] = 0.0;
@@ -746,6 +748,12 @@ __device__ __forceinline__ void xinv_sites(const GroupArgs<T>& g, T dt, T* hout,
             o[0] = un[0];
             o[N] = un[1];
             o[2 * N] = un[2];
+        } else if (MODE == 2) {
+            const T sh = s0[0] * hf[0] + s0[1] * hf[1] + s0[2] * hf[2];
+            eacc[h] += T(-0.5) * sh;
+            T* __restrict__ o = hout + (size_t)im * 3 * N + site;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) o[(size_t)c * N] = hf[c] - sh * s0[c];
         } else {
             auto nrm = [](const T* v, double* o) {
                 const double a = v[0], b = v[1], c = v[2];
@@ -786,7 +794,9 @@ __device__ __forceinline__ void xinv_sites(const GroupArgs<T>& g, T dt, T* hout,
             }
         }
     }
-    if constexpr (MODE == 0)
+    if constexpr (MODE == 2)
+        if (dt == T(0)) return;  // uniform over the grid: no energy partials wanted
+    if constexpr (MODE != 1)
         block_reduce_t2d<2>(eacc, acc, red);
     else
         block_reduce_d<NV>(acc, red);
@@ -795,7 +805,7 @@ __device__ __forceinline__ void xinv_sites(const GroupArgs<T>& g, T dt, T* hout,
         for (int h = 0; h < 2; ++h) {
             const int im = ia + h;
             if (im >= g.n_img) continue;
-            if (MODE == 0) {
+            if (MODE != 1) {
                 g.epart[(size_t)blk * g.n_img + im] = acc[h];  // [block][image]
             } else {
                 for (int k = 0; k < 4; ++k) g.epart[((size_t)blk * g.n_img + im) * 4 + k] = acc[4 * h + k];
@@ -1148,6 +1158,170 @@ __global__ void __launch_bounds__(256, 3) arc_kernel(GroupArgs<T> g, ArcArgs a) 
     }
 }
 
+// ------------------------------------------------------------------------------------------------
+// Adaptive Runge-Kutta evolution of the images (Sec. III: explicit Runge-Kutta with step-size control,
+// the Dormand-Prince 5(4) pair).  Per attempt, for each stage i: Y_i = y0 + hs sum_{q<i} a_iq k_q
+// (rk_assemble into sp), then the field pipeline with an identity table and the step kernel in force
+// mode gives k_i = F(Y_i) (Eq. 13); rk_finish forms y5 = y0 + hs sum b_q k_q and the squared scaled
+// error (hs sum (b_q - bhat_q) k_q / (atol + rtol max(|y0|, |y5|)))^2 per tile; rk_control (one CTA)
+// sums it per string in a fixed order, accepts when sqrt(mean) <= 1 and picks the next step; rk_commit
+// renormalises the accepted y5 into y0 (and into sp once the string's interval is complete).
+// The Dormand-Prince 5(4) coefficients (Dormand and Prince, 1980): a (rows = stages), the fifth-order
+// weights b and the embedded fourth-order weights bh.
+static __constant__ double c_dp_a[7][6] = {
+    {0, 0, 0, 0, 0, 0},
+    {1.0 / 5.0, 0, 0, 0, 0, 0},
+    {3.0 / 40.0, 9.0 / 40.0, 0, 0, 0, 0},
+    {44.0 / 45.0, -56.0 / 15.0, 32.0 / 9.0, 0, 0, 0},
+    {19372.0 / 6561.0, -25360.0 / 2187.0, 64448.0 / 6561.0, -212.0 / 729.0, 0, 0},
+    {9017.0 / 3168.0, -355.0 / 33.0, 46732.0 / 5247.0, 49.0 / 176.0, -5103.0 / 18656.0, 0},
+    {35.0 / 384.0, 0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0, 11.0 / 84.0}};
+static __constant__ double c_dp_b[7] = {35.0 / 384.0, 0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0,
+                                        11.0 / 84.0, 0};
+static __constant__ double c_dp_bh[7] = {5179.0 / 57600.0,    0,
+                                         7571.0 / 16695.0,    393.0 / 640.0,
+                                         -92097.0 / 339200.0, 187.0 / 2100.0,
+                                         1.0 / 40.0};
+constexpr int kRkTile = 1024;  // components per CTA of the element-wise Runge-Kutta kernels
+
+// grid (tiles, images), 256 threads
+template <typename T, int STAGE>
+__global__ void __launch_bounds__(256) rk_assemble_kernel(GroupArgs<T> g, RkArgs<T> r) {
+    const int im = blockIdx.y;
+    const size_t M = (size_t)3 * g.N, base = (size_t)im * M, stride = (size_t)g.n_img * M;
+    const RkString& S = r.st[r.img_str[im]];
+    const T hs = S.done ? T(0) : T(S.hs);
+    const size_t e1 = min(M, (size_t)(blockIdx.x + 1) * kRkTile);
+    for (size_t e = (size_t)blockIdx.x * kRkTile + threadIdx.x; e < e1; e += blockDim.x) {
+        T a = T(0);
+#pragma unroll
+        for (int q = 0; q < STAGE; ++q) a += T(c_dp_a[STAGE][q]) * r.k[q * stride + base + e];
+        g.sp[base + e] = r.y0[base + e] + hs * a;
+    }
+}
+
+// grid (tiles, images), 256 threads
+template <typename T>
+__global__ void __launch_bounds__(256) rk_finish_kernel(GroupArgs<T> g, RkArgs<T> r) {
+    __shared__ double red[32];
+    const int im = blockIdx.y;
+    const size_t M = (size_t)3 * g.N, base = (size_t)im * M, stride = (size_t)g.n_img * M;
+    const RkString& S = r.st[r.img_str[im]];
+    const T hs = S.done ? T(0) : T(S.hs);
+    const T rtol = T(r.rtol), atol = T(r.atol);
+    T v[1] = {T(0)};
+    const size_t e1 = min(M, (size_t)(blockIdx.x + 1) * kRkTile);
+    for (size_t e = (size_t)blockIdx.x * kRkTile + threadIdx.x; e < e1; e += blockDim.x) {
+        T b5 = T(0), d4 = T(0);
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+            const T kq = r.k[q * stride + base + e];
+            b5 += T(c_dp_b[q]) * kq;
+            d4 += T(c_dp_b[q] - c_dp_bh[q]) * kq;
+        }
+        const T y0 = r.y0[base + e];
+        const T y5 = y0 + hs * b5;
+        r.y5[base + e] = y5;
+        const T sc = atol + rtol * max(fabs(y0), fabs(y5));
+        const T q = hs * d4 / sc;
+        v[0] += q * q;
+    }
+    double out[1];
+    block_reduce_t2d<1>(v, out, red);
+    if (threadIdx.x == 0) r.errp[(size_t)im * r.n_tiles + blockIdx.x] = out[0];
+}
+
+// One CTA: per string (a warp each), the error norm sqrt(sum / (K 3N)) summed in image and tile order,
+// then the step-size control.  begin != 0 opens a new interval instead (t = 0, first step cut to T).
+template <typename T>
+__global__ void __launch_bounds__(256) rk_control_kernel(GroupArgs<T> g, RkArgs<T> r, ArcArgs a, int begin) {
+    __shared__ int any;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    const double T_int = r.T_int;
+    for (int s = warp; s < a.n_str; s += nwarp) {
+        RkString S = r.st[s];
+        if (begin) {
+            if (lane == 0) {
+                S.t = 0.0;
+                S.done = 0;
+                S.accepted = 0;
+                S.attempts = 0;
+                S.hs = S.step < T_int ? S.step : T_int;
+                r.st[s] = S;
+                atomicOr(&any, 1);
+            }
+            continue;
+        }
+        if (S.done) {  // finished in an earlier attempt: nothing to commit this time
+            if (lane == 0 && S.accepted) {
+                S.accepted = 0;
+                r.st[s] = S;
+            }
+            continue;
+        }
+        const int n = a.str_K[s] * r.n_tiles;
+        const double* ep = r.errp + (size_t)a.str_img0[s] * r.n_tiles;
+        double v = 0.0;
+        for (int i = lane; i < n; i += 32) v += ep[i];
+        v = warp_sum_d(v);
+        if (lane == 0) {
+            const double err = sqrt(v / (3.0 * (double)g.N * (double)a.str_K[s]));
+            S.err = err;
+            if (!isfinite(err) || ++S.attempts > 100000) {
+                atomicOr(g.err, isfinite(err) ? kErrStepCollapse : kErrNonFinite);
+                S.done = 1;
+                S.accepted = 0;
+            } else {
+                double fac = err > 0.0 ? 0.9 * pow(err, -0.2) : 5.0;
+                if (fac < 0.2) fac = 0.2;
+                if (err <= 1.0) {
+                    if (fac > 5.0) fac = 5.0;
+                    S.t = S.hs == T_int - S.t ? T_int : S.t + S.hs;
+                    S.accepted = 1;
+                    ++S.acc;
+                } else {
+                    if (fac > 1.0) fac = 1.0;
+                    S.accepted = 0;
+                    ++S.rej;
+                }
+                S.step = S.hs * fac;
+                if (S.t >= T_int)
+                    S.done = 1;
+                else
+                    S.hs = S.step < T_int - S.t ? S.step : T_int - S.t;
+            }
+            r.st[s] = S;
+            if (!S.done) atomicOr(&any, 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *r.active = any;
+}
+
+// grid (site tiles of 256, images), 256 threads: y0 = normalise(y5) per site where the attempt was
+// accepted; also into sp once the string's interval is complete
+template <typename T>
+__global__ void __launch_bounds__(256) rk_commit_kernel(GroupArgs<T> g, RkArgs<T> r) {
+    const int im = blockIdx.y;
+    const RkString& S = r.st[r.img_str[im]];
+    if (!S.accepted) return;  // uniform over the CTA
+    const int N = g.N;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const size_t base = (size_t)im * 3 * N + i;
+    T v[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v[c] = r.y5[base + (size_t)c * N];
+    const T nr = rsqrt_t<T>(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        r.y0[base + (size_t)c * N] = v[c] * nr;
+        if (S.done) g.sp[base + (size_t)c * N] = v[c] * nr;
+    }
+}
+
 // eval reduce: grid (n_str), thread per image: terms[str][k][4] and energies[str][k] in FP64.
 template <typename T>
 __global__ void eval_reduce_kernel(GroupArgs<T> g, ArcArgs a, double* terms, double* energies) {
@@ -1407,6 +1581,53 @@ void launch_xinv_eval(const GroupArgs<T>& g, bool do_fft, T* hout, int nthr, siz
     }
 }
 
+template <typename T>
+void launch_xinv_force(const GroupArgs<T>& g, bool do_fft, T* kout, bool energies, int nthr, size_t smem,
+                       cudaStream_t st) {
+    dim3 grid((g.ny + g.ty_c - 1) / g.ty_c, g.nz, g.n_pairs);
+    const T flag = energies ? T(1) : T(0);  // force mode: nonzero asks for the energy partials
+    if constexpr (std::is_same<T, float>::value) {
+        if (do_fft && f128_x(4, g.Px)) {
+            const int nt = f128_x_threads(g.ty_c);
+            const size_t sm = f128_x_smem(g.ty_c);
+            if (g.ty_c == 2) xinv128_kernel<T, 2, 2><<<grid, nt, sm, st>>>(g, flag, kout);
+            else if (g.ty_c == 4) xinv128_kernel<T, 2, 4><<<grid, nt, sm, st>>>(g, flag, kout);
+            else xinv128_kernel<T, 2, 8><<<grid, nt, sm, st>>>(g, flag, kout);
+            return;
+        }
+    }
+    if (do_fft)
+        xinv_kernel<T, true, 2, 0><<<grid, nthr, smem, st>>>(g, flag, kout);
+    else
+        xinv_kernel<T, false, 2, 0><<<grid, nthr, smem, st>>>(g, flag, kout);
+}
+
+template <typename T> void launch_rk_assemble(const GroupArgs<T>& g, const RkArgs<T>& r, int stage, cudaStream_t st) {
+    const dim3 grid(r.n_tiles, g.n_img);
+    switch (stage) {
+        case 0: rk_assemble_kernel<T, 0><<<grid, 256, 0, st>>>(g, r); break;
+        case 1: rk_assemble_kernel<T, 1><<<grid, 256, 0, st>>>(g, r); break;
+        case 2: rk_assemble_kernel<T, 2><<<grid, 256, 0, st>>>(g, r); break;
+        case 3: rk_assemble_kernel<T, 3><<<grid, 256, 0, st>>>(g, r); break;
+        case 4: rk_assemble_kernel<T, 4><<<grid, 256, 0, st>>>(g, r); break;
+        case 5: rk_assemble_kernel<T, 5><<<grid, 256, 0, st>>>(g, r); break;
+        default: rk_assemble_kernel<T, 6><<<grid, 256, 0, st>>>(g, r); break;
+    }
+}
+
+template <typename T> void launch_rk_finish(const GroupArgs<T>& g, const RkArgs<T>& r, cudaStream_t st) {
+    rk_finish_kernel<T><<<dim3(r.n_tiles, g.n_img), 256, 0, st>>>(g, r);
+}
+
+template <typename T>
+void launch_rk_control(const GroupArgs<T>& g, const RkArgs<T>& r, const ArcArgs& a, int begin, cudaStream_t st) {
+    rk_control_kernel<T><<<1, 256, 0, st>>>(g, r, a, begin);
+}
+
+template <typename T> void launch_rk_commit(const GroupArgs<T>& g, const RkArgs<T>& r, cudaStream_t st) {
+    rk_commit_kernel<T><<<dim3((g.N + 255) / 256, g.n_img), 256, 0, st>>>(g, r);
+}
+
 template <typename T> void launch_arc(const GroupArgs<T>& g, const ArcArgs& a, int nthr, cudaStream_t st) {
     dim3 grid(a.n_tiles + 1, a.n_kchunks, a.n_str);  // + one energy CTA per chunk
     launch_pdl(arc_kernel<T>, grid, dim3(nthr), 0, st, g, a);
@@ -1447,11 +1668,14 @@ template <typename T> void set_smem_limits(int bytes) {
     set_dyn_smem(xinv_kernel<T, true, 1, 0>, bytes);
     set_dyn_smem(xinv_kernel<T, false, 0, 0>, bytes);
     set_dyn_smem(xinv_kernel<T, false, 1, 0>, bytes);
+    set_dyn_smem(xinv_kernel<T, true, 2, 0>, bytes);
+    set_dyn_smem(xinv_kernel<T, false, 2, 0>, bytes);
     if constexpr (std::is_same<T, float>::value) {
 #define SS_CASE(R)                                  \
     set_dyn_smem(xfwd128_kernel<T, R>, bytes);      \
     set_dyn_smem(xinv128_kernel<T, 0, R>, bytes);   \
-    set_dyn_smem(xinv128_kernel<T, 1, R>, bytes);
+    set_dyn_smem(xinv128_kernel<T, 1, R>, bytes);   \
+    set_dyn_smem(xinv128_kernel<T, 2, R>, bytes);
         SS_CASE(2) SS_CASE(4) SS_CASE(8)
 #undef SS_CASE
         set_dyn_smem(yz128_kernel<T, 4>, bytes);
@@ -1495,6 +1719,11 @@ void launch_interp_identity(InterpEntry* tab, int img0, int K, cudaStream_t st) 
     template void launch_yz<T>(const GroupArgs<T>&, int, size_t, cudaStream_t);                                \
     template void launch_xinv_step<T>(const GroupArgs<T>&, bool, T, int, size_t, cudaStream_t);                \
     template void launch_xinv_eval<T>(const GroupArgs<T>&, bool, T*, int, size_t, cudaStream_t);               \
+    template void launch_xinv_force<T>(const GroupArgs<T>&, bool, T*, bool, int, size_t, cudaStream_t);        \
+    template void launch_rk_assemble<T>(const GroupArgs<T>&, const RkArgs<T>&, int, cudaStream_t);             \
+    template void launch_rk_finish<T>(const GroupArgs<T>&, const RkArgs<T>&, cudaStream_t);                    \
+    template void launch_rk_control<T>(const GroupArgs<T>&, const RkArgs<T>&, const ArcArgs&, int, cudaStream_t); \
+    template void launch_rk_commit<T>(const GroupArgs<T>&, const RkArgs<T>&, cudaStream_t);                    \
     template void launch_arc<T>(const GroupArgs<T>&, const ArcArgs&, int, cudaStream_t);                       \
     template void launch_eval_reduce<T>(const GroupArgs<T>&, const ArcArgs&, double*, double*, cudaStream_t);  \
     template void launch_aos_to_soa<T, float>(const float*, T*, int, int, int*, cudaStream_t);                 \
