@@ -66,7 +66,7 @@ def _load():
             "or_step": (None, [i, d, dp, dp]),
             "or_reparam": (None, [i, i, dp, dp, dp]),
             "or_string_run": (i, [mp, i, i, d, dp, dp]),
-            "or_string_run_rk": (i, [mp, i, i, d, d, d, dp, dp, dp, P(ctypes.c_long)]),
+            "or_string_run_rk": (i, [mp, i, i, d, d, d, i, dp, dp, dp, P(ctypes.c_long)]),
             "or_dp_tableau": (None, [dp, dp, dp]),
             "or_barrier": (d, [i, dp, P(i)]),
             "or_energy_param_grad": (None, [mp, dp, dp]),
@@ -190,21 +190,28 @@ def string_run(m: OracleModel, path, n_iter: int, dt: float, with_energies: bool
 
 
 def string_run_rk(m: OracleModel, path, n_iter: int, T: float, rtol: float = 1e-6, atol: float = 1e-8,
-                  step: float | None = None, with_energies: bool = True):
-    """Sec. III loop with the Dormand-Prince 5(4) evolution of the string over T per iteration.
-    Returns (final path, energies or None, carried step, (accepted, rejected))."""
+                  step=None, with_energies: bool = True, per_image: bool = False):
+    """Sec. III loop with the Dormand-Prince 5(4) evolution over T per iteration, the whole string one
+    ODE system (per_image=False) or every image its own (per_image=True).  Returns (final path,
+    energies or None, carried step, (accepted, rejected)); with per_image the step is an array of K
+    steps and the counts an array of K (accepted, rejected) rows."""
     phi = _f64(path).copy()
     K = phi.shape[0]
+    n_sys = K if per_image else 1
     e = np.zeros(K) if with_energies else None
-    h = ctypes.c_double(T if step is None else step)
-    counts = (ctypes.c_long * 2)()
+    h = np.full(n_sys, float(T)) if step is None else np.array(np.broadcast_to(np.asarray(step, float), (n_sys,)))
+    counts = (ctypes.c_long * (2 * n_sys))()
     rc = _load().or_string_run_rk(ctypes.byref(m), K, int(n_iter), float(T), float(rtol), float(atol),
-                                  ctypes.byref(h), _ptr(phi), _ptr(e) if with_energies else None, counts)
+                                  int(bool(per_image)), _ptr(h), _ptr(phi), _ptr(e) if with_energies else None,
+                                  counts)
     if rc == -1:
         raise MemoryError("oracle RK string run: out of memory")
     if rc != 0:
         raise RuntimeError("oracle RK string run: step size collapsed or non-finite error norm")
-    return phi, e, h.value, (counts[0], counts[1])
+    c = np.array(counts[:], dtype=np.int64).reshape(n_sys, 2)
+    if per_image:
+        return phi, e, h, c
+    return phi, e, float(h[0]), (int(c[0, 0]), int(c[0, 1]))
 
 
 def dp_tableau():

@@ -330,21 +330,23 @@ int or_string_run(const or_model* m, int K, int n_iter, double dt, double* phi, 
     return 0;
 }
 
-/* Sec. III: the barrier is the energy of the highest image relative to the first image.  Ties go
- * to the lowest index. */
-/* Adaptive explicit Runge-Kutta evolution of the images (Sec. III: "explicit Runge-Kutta methods with
- * adaptive step-size control ... the Dormand-Prince method"), in place of the fixed projected-Euler step
- * of or_string_run.  Each iteration integrates the whole string, read as one ODE system
+/* Adaptive explicit Runge-Kutta evolution of the images (Sec. III names explicit Runge-Kutta methods
+ * with adaptive step-size control, namely the Dormand-Prince pair), in place of the fixed
+ * projected-Euler step of or_string_run.  Each iteration integrates
  *     d phi_k / d tau = F(phi_k) = h(phi_k) - (phi_k . h(phi_k)) phi_k      (Eq. 13, every image k)
  * over the reduced interval T with the Dormand-Prince 5(4) pair, then reparametrises (Eqs. 11-12).
+ * The images do not interact during the evolution, so the step control may treat them together or
+ * apart: per_image = 0 integrates the whole string as one ODE system (one error norm, one step),
+ * per_image = 1 gives every image its own system (its own norm and step).
  * Stage states are not renormalised (h is evaluated on them as they are); each accepted step is
- * followed by per-site renormalisation.  Error norm: err = sqrt(mean_j (e_j / sc_j)^2) over all
- * K * 3N components, e = step * sum_i (b_i - bhat_i) k_i, sc_j = atol + rtol * max(|y_j|, |y5_j|).
+ * followed by per-site renormalisation.  Error norm of a system: err = sqrt(mean_j (e_j / sc_j)^2)
+ * over its components, e = step * sum_i (b_i - bhat_i) k_i, sc_j = atol + rtol * max(|y_j|, |y5_j|).
  * A step is accepted when err <= 1.  Next step: step * clamp(0.9 err^(-1/5), 0.2, 5) after an
  * accepted step, with the upper bound 1 after a rejected one.  Attempts are cut to end exactly at T.
- * *step_io carries the step from one iteration to the next (set it to T before the first).
- * counts (optional): [accepted, rejected] summed over the iterations.  Returns 0, -1 (memory), or
- * -2 (more than 100000 attempts in one iteration, or a non-finite error norm). */
+ * step_io (one per system: 1, or K when per_image) carries the step from one iteration to the next
+ * (set it to T before the first).  counts (optional, two per system): [accepted, rejected] summed over
+ * the iterations.  Returns 0, -1 (memory), or -2 (more than 100000 attempts in one interval, or a
+ * non-finite error norm). */
 static const double DP_A[7][6] = {
     {0, 0, 0, 0, 0, 0},
     {1.0 / 5.0, 0, 0, 0, 0, 0},
@@ -381,95 +383,100 @@ static void force_all(const or_model* m, const double* table, int K, const doubl
     }
 }
 
-int or_string_run_rk(const or_model* m, int K, int n_iter, double T, double rtol, double atol, double* step_io,
-                     double* phi, double* energies, long* counts) {
+/* One interval [0, T] of the system of Ks images at phi (Ks * 3N components), DP 5(4) as above;
+ * kk (7 systems), ys, y5 and hb are scratch of the system's size. */
+static int rk_interval(const or_model* m, const double* table, int Ks, double T, double rtol, double atol,
+                       double* step_io, double* phi, double* kk, double* ys, double* y5, double* hb, long* acc,
+                       long* rej) {
+    const int N = m->nx * m->ny * m->nz;
+    const size_t M = (size_t)3 * N, L = M * (size_t)Ks;
+    double step = *step_io, t = 0.0;
+    int have_k1 = 0, attempts = 0;
+    while (t < T) {
+        if (++attempts > 100000) return -2;
+        const double hs = step < T - t ? step : T - t;
+        if (!have_k1) force_all(m, table, Ks, phi, hb, kk);
+        have_k1 = 1;
+        for (int st = 1; st < 7; ++st) {
+            for (size_t j = 0; j < L; ++j) {
+                double a = 0.0;
+                for (int q = 0; q < st; ++q) a += DP_A[st][q] * kk[q * L + j];
+                ys[j] = phi[j] + hs * a;
+            }
+            force_all(m, table, Ks, ys, hb, kk + st * L);
+        }
+        double e2 = 0.0;
+        for (size_t j = 0; j < L; ++j) {
+            double b5 = 0.0, e = 0.0;
+            for (int q = 0; q < 7; ++q) {
+                b5 += DP_B[q] * kk[q * L + j];
+                e += (DP_B[q] - DP_BHAT[q]) * kk[q * L + j];
+            }
+            y5[j] = phi[j] + hs * b5;
+            const double ay = fabs(phi[j]), a5 = fabs(y5[j]);
+            const double sc = atol + rtol * (ay > a5 ? ay : a5);
+            const double r = hs * e / sc;
+            e2 += r * r;
+        }
+        const double err = sqrt(e2 / (double)L);
+        if (!isfinite(err)) return -2;
+        double fac = err > 0.0 ? 0.9 * pow(err, -0.2) : 5.0;
+        if (fac < 0.2) fac = 0.2;
+        if (err <= 1.0) {
+            if (fac > 5.0) fac = 5.0;
+            t = hs == T - t ? T : t + hs;
+            for (size_t i = 0; i < L / 3; ++i) {
+                const double* v = y5 + 3 * i;
+                const double n = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+                for (int c = 0; c < 3; ++c) phi[3 * i + c] = v[c] / n;
+            }
+            have_k1 = 0;
+            ++*acc;
+        } else {
+            if (fac > 1.0) fac = 1.0;
+            ++*rej;
+        }
+        step = hs * fac;
+    }
+    *step_io = step;
+    return 0;
+}
+
+int or_string_run_rk(const or_model* m, int K, int n_iter, double T, double rtol, double atol, int per_image,
+                     double* step_io, double* phi, double* energies, long* counts) {
     const int N = m->nx * m->ny * m->nz;
     const size_t M = (size_t)3 * N, L = M * (size_t)K;
+    const int n_sys = per_image ? K : 1, Ks = per_image ? 1 : K;
+    const size_t Ls = M * (size_t)Ks;
     double* table = NULL;
     if (m->w != 0.0) {
         table = dipole_table(m);
         if (!table) return -1;
     }
-    double* kk = (double*)malloc(sizeof(double) * L * 7);
+    double* kk = (double*)malloc(sizeof(double) * Ls * 7);
     double* ys = (double*)malloc(sizeof(double) * L);
-    double* y5 = (double*)malloc(sizeof(double) * L);
+    double* y5 = (double*)malloc(sizeof(double) * Ls);
     double* hb = (double*)malloc(sizeof(double) * L);
-    if (!kk || !ys || !y5 || !hb) {
+    long* cnt = (long*)calloc((size_t)2 * n_sys, sizeof(long));
+    if (!kk || !ys || !y5 || !hb || !cnt) {
         free(table);
         free(kk);
         free(ys);
         free(y5);
         free(hb);
+        free(cnt);
         return -1;
     }
     int rc = 0;
-    double step = *step_io;
-    long acc = 0, rej = 0;
     for (int it = 0; it < n_iter && rc == 0; ++it) {
-        double t = 0.0;
-        int have_k1 = 0, attempts = 0;
-        while (t < T) {
-            if (++attempts > 100000) {
-                rc = -2;
-                break;
-            }
-            const double hs = step < T - t ? step : T - t;
-            if (!have_k1) force_all(m, table, K, phi, hb, kk);
-            have_k1 = 1;
-            for (int st = 1; st < 7; ++st) {
-                for (size_t j = 0; j < L; ++j) {
-                    double a = 0.0;
-                    for (int q = 0; q < st; ++q) a += DP_A[st][q] * kk[q * L + j];
-                    ys[j] = phi[j] + hs * a;
-                }
-                force_all(m, table, K, ys, hb, kk + st * L);
-            }
-            double e2 = 0.0;
-            for (size_t j = 0; j < L; ++j) {
-                double b5 = 0.0, e = 0.0;
-                for (int q = 0; q < 7; ++q) {
-                    b5 += DP_B[q] * kk[q * L + j];
-                    e += (DP_B[q] - DP_BHAT[q]) * kk[q * L + j];
-                }
-                y5[j] = phi[j] + hs * b5;
-                const double ay = fabs(phi[j]), a5 = fabs(y5[j]);
-                const double sc = atol + rtol * (ay > a5 ? ay : a5);
-                const double r = hs * e / sc;
-                e2 += r * r;
-            }
-            const double err = sqrt(e2 / (double)L);
-            if (!isfinite(err)) {
-                rc = -2;
-                break;
-            }
-            double fac = err > 0.0 ? 0.9 * pow(err, -0.2) : 5.0;
-            if (fac < 0.2) fac = 0.2;
-            if (err <= 1.0) {
-                if (fac > 5.0) fac = 5.0;
-                t = hs == T - t ? T : t + hs;
-                for (int k = 0; k < K; ++k)
-                    for (int i = 0; i < N; ++i) {
-                        const double* v = y5 + k * M + 3 * i;
-                        const double n = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-                        for (int c = 0; c < 3; ++c) phi[k * M + 3 * i + c] = v[c] / n;
-                    }
-                have_k1 = 0;
-                ++acc;
-            } else {
-                if (fac > 1.0) fac = 1.0;
-                ++rej;
-            }
-            step = hs * fac;
-        }
+        for (int q = 0; q < n_sys && rc == 0; ++q)
+            rc = rk_interval(m, table, Ks, T, rtol, atol, step_io + q, phi + q * Ls, kk, ys, y5, hb, &cnt[2 * q],
+                             &cnt[2 * q + 1]);
         if (rc) break;
         memcpy(ys, phi, sizeof(double) * L);
         or_reparam(K, N, ys, phi, NULL);
     }
-    *step_io = step;
-    if (counts) {
-        counts[0] = acc;
-        counts[1] = rej;
-    }
+    if (counts) memcpy(counts, cnt, sizeof(long) * 2 * n_sys);
     if (rc == 0 && energies) {
 #pragma omp parallel for schedule(dynamic, 1)
         for (int k = 0; k < K; ++k) {
@@ -482,9 +489,12 @@ int or_string_run_rk(const or_model* m, int K, int n_iter, double T, double rtol
     free(ys);
     free(y5);
     free(hb);
+    free(cnt);
     return rc;
 }
 
+/* Sec. III: the barrier is the energy of the highest image relative to the first image.  Ties go
+ * to the lowest index. */
 double or_barrier(int K, const double* energies, int* k_max) {
     int kb = 0;
     for (int k = 1; k < K; ++k)

@@ -75,3 +75,33 @@ def test_fixed_point_is_kept():
     phi, _, _, (acc, rej) = oracle.string_run_rk(m, path, 3, 0.2)
     np.testing.assert_allclose(phi, path, atol=1e-14)
     assert rej == 0 and acc == 3
+
+
+def test_per_image_systems_are_independent_single_image_runs():
+    # A two-image string keeps both ends under reparametrisation, so with per-image step control each
+    # image evolves as on its own.  A string of two identical copies has the same RMS error norm as one
+    # copy, so the whole-string integrator run on [a, a] follows a alone: per_image([a, b]) must equal
+    # (whole([a, a])[0], whole([b, b])[0]), attempt counts included, up to the summation order of the
+    # norm (the error estimate is a difference of nearly equal sums, so its rounding reaches the carried
+    # step at about 1e-11).
+    m = oracle.model(4, 4, 1, 1.0, 0.3, 0.05, 0.02)
+    rng = np.random.default_rng(3)
+    a, b = (v / np.linalg.norm(v, axis=-1, keepdims=True) for v in rng.standard_normal((2, 16, 3)))
+    T, n = 0.6, 3
+    phi, _, steps, counts = oracle.string_run_rk(m, np.stack([a, b]), n, T, per_image=True)
+    for k, v in enumerate((a, b)):
+        ref, _, step, cnt = oracle.string_run_rk(m, np.stack([v, v]), n, T)
+        np.testing.assert_allclose(phi[k], ref[0], rtol=0, atol=1e-14)
+        assert abs(steps[k] - step) <= 1e-9 * step and tuple(counts[k]) == cnt
+    assert tuple(counts[0]) != tuple(counts[1]) or steps[0] != steps[1]
+
+
+def test_per_image_equals_whole_string_when_images_agree():
+    # identical images: every image's norm equals the string's, so both controls take the same steps
+    m = oracle.model(4, 4, 1, 1.0, 0.3, 0.05, 0.02)
+    v = np.random.default_rng(5).standard_normal((16, 3))
+    path = np.stack([v, v, v]) / np.linalg.norm(v, axis=-1, keepdims=True)
+    p1, e1, s1, c1 = oracle.string_run_rk(m, path, 2, 0.6, per_image=True)
+    p0, e0, s0, c0 = oracle.string_run_rk(m, path, 2, 0.6)
+    np.testing.assert_allclose(p1, p0, rtol=0, atol=1e-14)
+    assert all(abs(s - s0) <= 1e-9 * s0 for s in s1) and all(tuple(c) == c0 for c in c1)
