@@ -207,7 +207,7 @@ def string_run_rk(m: OracleModel, path, n_iter: int, T: float, rtol: float = 1e-
     if rc == -1:
         raise MemoryError("oracle RK string run: out of memory")
     if rc != 0:
-        raise RuntimeError("oracle RK string run: step size collapsed or non-finite error norm")
+        raise RuntimeError("oracle RK string run: step size collapsed")
     c = np.array(counts[:], dtype=np.int64).reshape(n_sys, 2)
     if per_image:
         return phi, e, h, c

@@ -342,11 +342,11 @@ int or_string_run(const or_model* m, int K, int n_iter, double dt, double* phi, 
  * followed by per-site renormalisation.  Error norm of a system: err = sqrt(mean_j (e_j / sc_j)^2)
  * over its components, e = step * sum_i (b_i - bhat_i) k_i, sc_j = atol + rtol * max(|y_j|, |y5_j|).
  * A step is accepted when err <= 1.  Next step: step * clamp(0.9 err^(-1/5), 0.2, 5) after an
- * accepted step, with the upper bound 1 after a rejected one.  Attempts are cut to end exactly at T.
+ * accepted step, with the upper bound 1 after a rejected one; a non-finite err (stages that overflowed)
+ * rejects with the factor 0.2.  Attempts are cut to end exactly at T.
  * step_io (one per system: 1, or K when per_image) carries the step from one iteration to the next
  * (set it to T before the first).  counts (optional, two per system): [accepted, rejected] summed over
- * the iterations.  Returns 0, -1 (memory), or -2 (more than 100000 attempts in one interval, or a
- * non-finite error norm). */
+ * the iterations.  Returns 0, -1 (memory), or -2 (more than 100000 attempts in one interval). */
 static const double DP_A[7][6] = {
     {0, 0, 0, 0, 0, 0},
     {1.0 / 5.0, 0, 0, 0, 0, 0},
@@ -419,8 +419,9 @@ static int rk_interval(const or_model* m, const double* table, int Ks, double T,
             e2 += r * r;
         }
         const double err = sqrt(e2 / (double)L);
-        if (!isfinite(err)) return -2;
-        double fac = err > 0.0 ? 0.9 * pow(err, -0.2) : 5.0;
+        /* an attempt whose stages overflowed (the cubic growth of F off the unit sphere) is rejected
+         * with the smallest factor */
+        double fac = !isfinite(err) ? 0.2 : err > 0.0 ? 0.9 * pow(err, -0.2) : 5.0;
         if (fac < 0.2) fac = 0.2;
         if (err <= 1.0) {
             if (fac > 5.0) fac = 5.0;

@@ -105,3 +105,16 @@ def test_per_image_equals_whole_string_when_images_agree():
     p0, e0, s0, c0 = oracle.string_run_rk(m, path, 2, 0.6)
     np.testing.assert_allclose(p1, p0, rtol=0, atol=1e-14)
     assert all(abs(s - s0) <= 1e-9 * s0 for s in s1) and all(tuple(c) == c0 for c in c1)
+
+
+def test_overflowing_attempt_is_rejected_and_recovers():
+    # Off the unit sphere F = h - (s.h) s grows like |s|^3, so a first attempt of length 1000 on a lone
+    # spin overflows within the seven stages (a non-finite error norm); it must count as a rejection
+    # with the smallest factor, and the run must still reach the closed-form relaxation.
+    K, T = 0.7, 1000.0
+    m = oracle.model(1, 1, 1, 0.0, 0.0, K, 0.0)
+    with np.errstate(all="ignore"):
+        phi, _, step, (acc, rej) = oracle.string_run_rk(m, _lone_spins([1.0, 2.0]), 1, T)
+    assert rej >= 1 and step > 0
+    assert abs(math.atan2(phi[0, 0, 0], phi[0, 0, 2])) < 1e-6
+    assert abs(abs(math.atan2(phi[1, 0, 0], phi[1, 0, 2])) - math.pi) < 1e-6
