@@ -325,6 +325,9 @@ def main():
         line["other_workloads"] = {w.name: other_workload(binding, w, stream) for w in
                                    (workloads.boundary_sweep(), workloads.uneven_study(),
                                     workloads.paper_monolayer_workload(), workloads.paper_phase_diagram())}
+        line["adaptive_rk"] = {name: adaptive_rk(binding, wl, stream, kind, per_iter_euler_ms=step_s * 1e3 / n_iter)
+                               for name, kind in (("dopri5_per_string", binding.SS_INT_DOPRI5),
+                                                  ("dopri5_per_image", binding.SS_INT_DOPRI5_IMAGE))}
     if not args.no_cpu_baseline and world == 1:
         v, cores, t = cpu_oracle_sample(spec, wl.dt)
         line["cpu_baseline"] = {"value": v, "unit": "spin-updates/s", "cores": cores, "kind": "oracle",
@@ -334,6 +337,41 @@ def main():
     print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
+
+
+def adaptive_rk(binding, wl, stream, kind, per_iter_euler_ms, iters=10, warm=2, rtol=1e-6, atol=1e-8):
+    """Device-timed Dormand-Prince evolution of the bench workload (each iteration integrates every image
+    over the workload's dt, then reparametrises): spin-updates/s counted like the Euler path (N K per
+    iteration) and force evaluations/s (7 per attempt and site-image), inputs resident."""
+    import torch
+    spec = wl.strings[0]
+    desc = (spec.nx, spec.ny, spec.nz, spec.J, spec.D, spec.K, spec.w, spec.n_images)
+    with binding.StringMethod([desc], dt=wl.dt, stream=stream.cuda_stream) as sm:
+        sm.set_integrator(kind, rtol, atol)
+        sm.set_path(0, torch.from_numpy(spec.initial_path().astype(np.float32)).cuda())
+        sm.step(warm)
+        _, a0, r0 = sm.integrator_state(0)
+        att0 = [sum(sm.integrator_state(0, k)[1:]) for k in range(spec.n_images)]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        sm.step(iters)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        step, a1, r1 = sm.integrator_state(0)
+        att1 = [sum(sm.integrator_state(0, k)[1:]) for k in range(spec.n_images)]
+    units = spec.n_sites * spec.n_images
+    attempts = a1 + r1 - a0 - r0  # summed over the string's systems
+    # every system of the group takes part in each round, so the rounds per interval are set by the
+    # system with the most attempts; with one system per string they equal its attempts
+    rounds = max(b - a for a, b in zip(att0, att1)) if kind == binding.SS_INT_DOPRI5_IMAGE else attempts
+    return {"value": units * iters / t, "unit": "spin-updates/s", "iterations_timed": iters, "rtol": rtol,
+            "atol": atol, "interval": wl.dt, "ms_per_iter": 1e3 * t / iters,
+            "attempts_per_iter": attempts / iters, "accepted": a1 - a0, "rejected": r1 - r0,
+            "rounds_per_iter_min": rounds / iters, "carried_step_min": step,
+            "force_evals_per_s": 7 * units * rounds / t,
+            "ms_per_round_vs_7_euler_iters": (1e3 * t / max(rounds, 1)) / (7 * per_iter_euler_ms)}
 
 
 def other_workload(binding, wl, stream, iters=20, warm=3):

@@ -161,26 +161,35 @@ ss_status ss_field_noalloc(int nx, int ny, int nz, double J, double D, double K,
 ss_status ss_launch_config(const ss_ctx* ctx, int string, int out[8]);
 
 /* How ss_step evolves the images between reparametrisations (Sec. III). */
-enum { SS_INT_EULER = 0, SS_INT_DOPRI5 = 1 };
+enum { SS_INT_EULER = 0, SS_INT_DOPRI5 = 1, SS_INT_DOPRI5_IMAGE = 2 };
 
-/* Chooses the evolution of the images.  SS_INT_EULER (the default): one projected-Euler step of length
- * opts.dt per iteration (Eqs. 10, 13).  SS_INT_DOPRI5: the paper's "explicit Runge-Kutta methods with
- * adaptive step-size control" -- the Dormand-Prince 5(4) pair integrates each string, as one ODE system
- * d phi/d tau = h - (phi.h) phi (Eq. 13, every image), over the reduced interval opts.dt per iteration;
- * an attempt is accepted when sqrt(mean_j (e_j / (atol + rtol max(|y_j|, |y5_j|)))^2) <= 1 over the
- * string's 3N*K components (e = the 5th- minus the 4th-order increment), the next step is
- * step * clamp(0.9 err^(-1/5), 0.2, 5) (at most 1 after a rejection), attempts are cut to end at the
- * interval's end, and spins are renormalised after each accepted step.  The step carries over from one
- * iteration to the next and restarts at opts.dt when a path is set.  Under DOPRI5, ss_step
- * synchronises once per round of attempts (the host decides whether another round is needed) and does
- * not replay a CUDA graph; ss_step_energies reports the energies of the state each interval started
- * from.  rtol and atol must be positive and finite.  A later synchronising call returns
- * SS_ERR_NONFINITE after a non-finite error norm or more than 100000 attempts in one interval. */
+/* Chooses the evolution of the images.
+ *   SS_INT_EULER (the default): one projected-Euler step of length opts.dt per iteration (Eqs. 10, 13).
+ *   SS_INT_DOPRI5, SS_INT_DOPRI5_IMAGE: Sec. III's explicit Runge-Kutta evolution with adaptive step
+ *   size -- the Dormand-Prince 5(4) pair integrates d phi/d tau = h - (phi.h) phi (Eq. 13) over the
+ *   reduced interval opts.dt per iteration, either the whole string as one ODE system (DOPRI5: one
+ *   error norm and one step per string) or every image as its own (DOPRI5_IMAGE: a norm and a step per
+ *   image; the images do not interact between reparametrisations).
+ * An attempt is accepted when sqrt(mean_j (e_j / (atol + rtol max(|y_j|, |y5_j|)))^2) <= 1 over the
+ * system's components (e = the 5th- minus the 4th-order increment).  The next step is
+ * step * clamp(0.9 err^(-1/5), 0.2, 5), at most 1 after a rejection, and 0.2 after an attempt whose
+ * stages overflowed to a non-finite norm (a rejection).  Attempts are cut to end at the interval's end.
+ * Spins are renormalised after each accepted step, not at the stages.  Steps carry over from one
+ * iteration to the next and restart at opts.dt when a path is set or an integrator is chosen.
+ * Under the Runge-Kutta kinds ss_step synchronises once per round of attempts (the host decides whether
+ * another round is needed) and replays no CUDA graph; every system of a size group takes part in each
+ * round, a finished one with a zero step.  ss_step_energies reports the energies of the state each
+ * interval started from.  rtol and atol (ignored for SS_INT_EULER) must be positive and finite.  A later
+ * synchronising call returns SS_ERR_NONFINITE after more than 100000 attempts in one interval.
+ * Allocates 9 copies of the string state per size group on first use. */
 ss_status ss_set_integrator(ss_ctx* ctx, int kind, double rtol, double atol);
 
-/* Adaptive-integrator state of `string`: the carried step and the accepted and rejected attempts since
- * its path was set (opts.dt and zeros before SS_INT_DOPRI5 is chosen).  Synchronises. */
-ss_status ss_integrator_state(ss_ctx* ctx, int string, double* step, long long* accepted, long long* rejected);
+/* Adaptive-integrator state of `string`: for image = -1 the smallest carried step and the accepted and
+ * rejected attempts summed over the string's systems; for image >= 0 those of the system holding that
+ * image (the string's own under SS_INT_DOPRI5).  Counts run from the last ss_set_path or
+ * ss_set_integrator; opts.dt and zeros under SS_INT_EULER.  Synchronises. */
+ss_status ss_integrator_state(ss_ctx* ctx, int string, int image, double* step, long long* accepted,
+                              long long* rejected);
 
 /* Shape queries. */
 int ss_num_strings(const ss_ctx* ctx);

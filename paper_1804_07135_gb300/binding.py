@@ -21,7 +21,7 @@ SS_OK, SS_ERR_INVALID_ARG, SS_ERR_CUDA, SS_ERR_OOM, SS_ERR_NONFINITE, SS_ERR_TIM
 SS_DTYPE_F32, SS_DTYPE_F64 = 0, 1
 SS_PREC_FP32, SS_PREC_FP64 = 0, 1
 SS_DIPOLE_OFF, SS_DIPOLE_FFT = 0, 2
-SS_INT_EULER, SS_INT_DOPRI5 = 0, 1
+SS_INT_EULER, SS_INT_DOPRI5, SS_INT_DOPRI5_IMAGE = 0, 1, 2
 _STATUS = {0: "SS_OK", 1: "SS_ERR_INVALID_ARG", 2: "SS_ERR_CUDA", 3: "SS_ERR_OOM", 4: "SS_ERR_NONFINITE",
            5: "SS_ERR_TIMEOUT", 6: "SS_ERR_STATE"}
 
@@ -57,7 +57,7 @@ _SIGNATURES = {
     "ss_get_path": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "ss_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "ss_set_integrator": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double]),
-    "ss_integrator_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+    "ss_integrator_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
     "ss_energies": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "ss_step_energies": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
@@ -249,11 +249,13 @@ def ss_set_integrator(ctx, kind: int, rtol: float = 1e-6, atol: float = 1e-8) ->
     _check(_lib.ss_set_integrator(ctx, int(kind), float(rtol), float(atol)), ctx)
 
 
-def ss_integrator_state(ctx, string: int) -> tuple[float, int, int]:
-    """(carried step, accepted attempts, rejected attempts) of the adaptive integrator."""
+def ss_integrator_state(ctx, string: int, image: int = -1) -> tuple[float, int, int]:
+    """(carried step, accepted attempts, rejected attempts) of the adaptive integrator: the string's
+    smallest step and summed counts (image = -1), or those of the system holding `image`."""
     h = ctypes.c_double()
     a, r = ctypes.c_longlong(), ctypes.c_longlong()
-    _check(_lib.ss_integrator_state(ctx, int(string), ctypes.byref(h), ctypes.byref(a), ctypes.byref(r)), ctx)
+    _check(_lib.ss_integrator_state(ctx, int(string), int(image), ctypes.byref(h), ctypes.byref(a), ctypes.byref(r)),
+           ctx)
     return float(h.value), int(a.value), int(r.value)
 
 
@@ -385,8 +387,8 @@ class StringMethod:
     def set_integrator(self, kind, rtol=1e-6, atol=1e-8):
         ss_set_integrator(self.ctx, kind, rtol, atol)
 
-    def integrator_state(self, string=0):
-        return ss_integrator_state(self.ctx, string)
+    def integrator_state(self, string=0, image=-1):
+        return ss_integrator_state(self.ctx, string, image)
 
     def energies(self, string=0):
         return ss_energies(self.ctx, string)

@@ -97,7 +97,8 @@ struct Group {
     void *rk_y0 = nullptr, *rk_k = nullptr, *rk_y5 = nullptr;
     double* rk_errp = nullptr;
     RkString* rk_st = nullptr;
-    int* rk_img_str = nullptr;
+    int *rk_img_sys = nullptr, *rk_sys_img0 = nullptr, *rk_sys_cnt = nullptr;
+    int rk_nsys = 0;
     int* rk_active = nullptr;
     InterpEntry* interp_ident = nullptr;
     int rk_tiles = 0;
@@ -489,7 +490,10 @@ template <typename T> RkArgs<T> rk_args(const ss_ctx* c, const Group& g) {
     r.errp = g.rk_errp;
     r.n_tiles = g.rk_tiles;
     r.st = g.rk_st;
-    r.img_str = g.rk_img_str;
+    r.img_sys = g.rk_img_sys;
+    r.sys_img0 = g.rk_sys_img0;
+    r.sys_cnt = g.rk_sys_cnt;
+    r.n_sys = g.rk_nsys;
     r.active = g.rk_active;
     r.T_int = c->opts.dt;
     r.rtol = c->rtol;
@@ -497,28 +501,56 @@ template <typename T> RkArgs<T> rk_args(const ss_ctx* c, const Group& g) {
     return r;
 }
 
-ss_status rk_setup(ss_ctx* c, Group& g) {
-    if (g.rk_y0) return SS_OK;
+// Buffers of the group's Runge-Kutta evolution, allocated on first use; the ODE systems (whole strings,
+// or single images when per_image) and fresh controller states are uploaded on every call.
+ss_status rk_setup(ss_ctx* c, Group& g, bool per_image) {
     const size_t M = (size_t)3 * g.N, L = M * g.n_img, rs = real_size(c);
-    g.rk_tiles = (int)((M + 1023) / 1024);
-    TRY(dalloc(c, &g.rk_y0, L * rs));
-    TRY(dalloc(c, &g.rk_k, 7 * L * rs));
-    TRY(dalloc(c, &g.rk_y5, L * rs));
-    TRY(dalloc(c, (void**)&g.rk_errp, (size_t)g.n_img * g.rk_tiles * sizeof(double)));
-    TRY(dalloc(c, (void**)&g.rk_st, g.strs.size() * sizeof(RkString)));
-    TRY(dalloc(c, (void**)&g.rk_img_str, g.n_img * sizeof(int)));
-    TRY(dalloc(c, (void**)&g.rk_active, sizeof(int)));
-    TRY(dalloc(c, (void**)&g.interp_ident, g.n_img * sizeof(InterpEntry)));
-    std::vector<int> img_str(g.n_img);
-    for (size_t i = 0; i < g.strs.size(); ++i)
-        for (int k = 0; k < g.str_K[i]; ++k) img_str[g.str_img0[i] + k] = (int)i;
-    std::vector<RkString> st(g.strs.size(), rk_fresh(c));
-    CUDA_TRY(c, cudaMemcpyAsync(g.rk_img_str, img_str.data(), g.n_img * sizeof(int), cudaMemcpyHostToDevice, c->cs));
+    if (!g.rk_y0) {
+        g.rk_tiles = (int)((M + 1023) / 1024);
+        TRY(dalloc(c, &g.rk_y0, L * rs));
+        TRY(dalloc(c, &g.rk_k, 7 * L * rs));
+        TRY(dalloc(c, &g.rk_y5, L * rs));
+        TRY(dalloc(c, (void**)&g.rk_errp, (size_t)g.n_img * g.rk_tiles * sizeof(double)));
+        TRY(dalloc(c, (void**)&g.rk_st, g.n_img * sizeof(RkString)));
+        TRY(dalloc(c, (void**)&g.rk_img_sys, g.n_img * sizeof(int)));
+        TRY(dalloc(c, (void**)&g.rk_sys_img0, g.n_img * sizeof(int)));
+        TRY(dalloc(c, (void**)&g.rk_sys_cnt, g.n_img * sizeof(int)));
+        TRY(dalloc(c, (void**)&g.rk_active, sizeof(int)));
+        TRY(dalloc(c, (void**)&g.interp_ident, g.n_img * sizeof(InterpEntry)));
+        CUDA_TRY(c, cudaMemsetAsync(g.rk_k, 0, 7 * L * rs, c->cs));
+        launch_interp_identity(g.interp_ident, 0, g.n_img, c->cs);
+    }
+    std::vector<int> img_sys(g.n_img), sys_img0, sys_cnt;
+    for (size_t i = 0; i < g.strs.size(); ++i) {
+        if (per_image) {
+            for (int k = 0; k < g.str_K[i]; ++k) {
+                img_sys[g.str_img0[i] + k] = (int)sys_img0.size();
+                sys_img0.push_back(g.str_img0[i] + k);
+                sys_cnt.push_back(1);
+            }
+        } else {
+            for (int k = 0; k < g.str_K[i]; ++k) img_sys[g.str_img0[i] + k] = (int)i;
+            sys_img0.push_back(g.str_img0[i]);
+            sys_cnt.push_back(g.str_K[i]);
+        }
+    }
+    g.rk_nsys = (int)sys_img0.size();
+    std::vector<RkString> st(g.rk_nsys, rk_fresh(c));
+    const size_t ni = g.n_img * sizeof(int), ns = g.rk_nsys * sizeof(int);
+    CUDA_TRY(c, cudaMemcpyAsync(g.rk_img_sys, img_sys.data(), ni, cudaMemcpyHostToDevice, c->cs));
+    CUDA_TRY(c, cudaMemcpyAsync(g.rk_sys_img0, sys_img0.data(), ns, cudaMemcpyHostToDevice, c->cs));
+    CUDA_TRY(c, cudaMemcpyAsync(g.rk_sys_cnt, sys_cnt.data(), ns, cudaMemcpyHostToDevice, c->cs));
     CUDA_TRY(c, cudaMemcpyAsync(g.rk_st, st.data(), st.size() * sizeof(RkString), cudaMemcpyHostToDevice, c->cs));
-    CUDA_TRY(c, cudaMemsetAsync(g.rk_k, 0, 7 * L * rs, c->cs));
-    launch_interp_identity(g.interp_ident, 0, g.n_img, c->cs);
     CUDA_TRY(c, cudaGetLastError());
     return SS_OK;
+}
+
+// The controller states of string r: one system, or one per image.
+int rk_first_sys(const ss_ctx* c, const StringRec& r) {
+    return c->integrator == SS_INT_DOPRI5_IMAGE ? r.img0 : r.local;
+}
+int rk_sys_count(const ss_ctx* c, const StringRec& r) {
+    return c->integrator == SS_INT_DOPRI5_IMAGE ? r.d.n_images : 1;
 }
 
 // n_iter iterations: per iteration every string integrates over opts.dt with Dormand-Prince attempts (one
@@ -536,7 +568,7 @@ template <typename T> ss_status rk_iterations(ss_ctx* c, int n_iter) {
             RkArgs<T> r = rk_args<T>(c, g);
             launch_xfwd<T>(a, false, g.thr_a, 0, c->cs);  // s = reparametrised state
             CUDA_TRY(c, cudaMemcpyAsync(r.y0, a.s, (size_t)3 * g.N * g.n_img * sizeof(T), cudaMemcpyDeviceToDevice, c->cs));
-            launch_rk_control<T>(ai, r, g.arc, 1, c->cs);
+            launch_rk_control<T>(ai, r, 1, c->cs);
         }
         for (int round = 0;; ++round) {
             bool any = false;
@@ -555,7 +587,7 @@ template <typename T> ss_status rk_iterations(ss_ctx* c, int n_iter) {
                                          c->cs);
                 }
                 launch_rk_finish<T>(ai, r, c->cs);
-                launch_rk_control<T>(ai, r, g.arc, 0, c->cs);
+                launch_rk_control<T>(ai, r, 0, c->cs);
                 launch_rk_commit<T>(ai, r, c->cs);
                 CUDA_TRY(c, cudaMemcpyAsync(&c->h_active[gi], r.active, sizeof(int), cudaMemcpyDeviceToHost, c->cs));
                 any = true;
@@ -868,9 +900,10 @@ ss_status ss_set_path(ss_ctx* c, int string, const void* spins, int dtype, int o
             launch_aos_to_soa<float, float>((const float*)src, dst, K, g.N, c->d_err, c->cs);
     }
     launch_interp_identity(g.interp, r.img0, K, c->cs);
-    if (g.rk_st) {  // the adaptive integrator restarts from step opts.dt on a new path
-        const RkString fresh = rk_fresh(c);
-        CUDA_TRY(c, cudaMemcpyAsync(g.rk_st + r.local, &fresh, sizeof fresh, cudaMemcpyHostToDevice, c->cs));
+    if (c->integrator != SS_INT_EULER) {  // the adaptive integrator restarts from step opts.dt on a new path
+        const std::vector<RkString> fresh(rk_sys_count(c, r), rk_fresh(c));
+        CUDA_TRY(c, cudaMemcpyAsync(g.rk_st + rk_first_sys(c, r), fresh.data(), fresh.size() * sizeof(RkString),
+                                    cudaMemcpyHostToDevice, c->cs));
     }
     CUDA_TRY(c, cudaGetLastError());
     ss_status st = sync_check(c);
@@ -882,13 +915,14 @@ ss_status ss_set_path(ss_ctx* c, int string, const void* spins, int dtype, int o
 
 ss_status ss_set_integrator(ss_ctx* c, int kind, double rtol, double atol) {
     if (!c) return SS_ERR_INVALID_ARG;
-    if (kind != SS_INT_EULER && kind != SS_INT_DOPRI5) return fail(c, SS_ERR_INVALID_ARG, "unknown integrator %d", kind);
-    if (kind == SS_INT_DOPRI5 && !(rtol > 0.0 && atol > 0.0 && std::isfinite(rtol) && std::isfinite(atol)))
+    if (kind != SS_INT_EULER && kind != SS_INT_DOPRI5 && kind != SS_INT_DOPRI5_IMAGE)
+        return fail(c, SS_ERR_INVALID_ARG, "unknown integrator %d", kind);
+    if (kind != SS_INT_EULER && !(rtol > 0.0 && atol > 0.0 && std::isfinite(rtol) && std::isfinite(atol)))
         return fail(c, SS_ERR_INVALID_ARG, "rtol and atol must be positive and finite");
     TRY(enter(c));
-    if (kind == SS_INT_DOPRI5) {
+    if (kind != SS_INT_EULER) {
         if (!c->h_active) CUDA_TRY(c, cudaHostAlloc((void**)&c->h_active, c->groups.size() * sizeof(int), cudaHostAllocDefault));
-        for (Group& g : c->groups) TRY(rk_setup(c, g));
+        for (Group& g : c->groups) TRY(rk_setup(c, g, kind == SS_INT_DOPRI5_IMAGE));
         c->rtol = rtol;
         c->atol = atol;
     }
@@ -898,22 +932,32 @@ ss_status ss_set_integrator(ss_ctx* c, int kind, double rtol, double atol) {
     return st;
 }
 
-ss_status ss_integrator_state(ss_ctx* c, int string, double* step, long long* accepted, long long* rejected) {
+ss_status ss_integrator_state(ss_ctx* c, int string, int image, double* step, long long* accepted,
+                              long long* rejected) {
     TRY(check_string(c, string));
     if (!step || !accepted || !rejected) return fail(c, SS_ERR_INVALID_ARG, "output pointer is NULL");
     const StringRec& r = c->strs[string];
+    if (image < -1 || image >= r.d.n_images)
+        return fail(c, SS_ERR_INVALID_ARG, "image %d out of range [-1, %d)", image, r.d.n_images);
     const Group& g = c->groups[r.group];
-    RkString h = rk_fresh(c);
-    if (g.rk_st) {
+    std::vector<RkString> h(1, rk_fresh(c));
+    if (c->integrator != SS_INT_EULER) {
+        h.resize(rk_sys_count(c, r));
         TRY(enter(c));
-        CUDA_TRY(c, cudaMemcpyAsync(&h, g.rk_st + r.local, sizeof h, cudaMemcpyDeviceToHost, c->cs));
+        CUDA_TRY(c, cudaMemcpyAsync(h.data(), g.rk_st + rk_first_sys(c, r), h.size() * sizeof(RkString),
+                                    cudaMemcpyDeviceToHost, c->cs));
         ss_status st = sync_check(c);
         TRY(leave(c));
         if (st != SS_OK) return st;
+        if (image >= 0 && h.size() > 1) h = {h[image]};
     }
-    *step = h.step;
-    *accepted = h.acc;
-    *rejected = h.rej;
+    *step = h[0].step;
+    *accepted = *rejected = 0;
+    for (const RkString& x : h) {
+        *step = std::min(*step, x.step);
+        *accepted += x.acc;
+        *rejected += x.rej;
+    }
     return SS_OK;
 }
 
@@ -942,7 +986,7 @@ ss_status ss_step(ss_ctx* c, int n_iter) {
     for (const Group& g : c->groups) TRY(check_paths(c, g));
     if (n_iter == 0) return SS_OK;
     TRY(enter(c));
-    if (c->integrator == SS_INT_DOPRI5) {
+    if (c->integrator != SS_INT_EULER) {
         TRY(use_fp64(c) ? rk_iterations<double>(c, n_iter) : rk_iterations<float>(c, n_iter));
         return leave(c);
     }

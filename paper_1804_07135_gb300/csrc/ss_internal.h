@@ -103,7 +103,8 @@ struct ArcArgs {
     int reparam;           // 0: keep images where they are
 };
 
-// Adaptive Runge-Kutta evolution (Sec. III, Dormand-Prince 5(4)): controller state of one string.
+// Adaptive Runge-Kutta evolution (Sec. III, Dormand-Prince 5(4)): controller state of one ODE system
+// (a whole string, or one image under per-image step control).
 struct RkString {
     double t;           // reduced time reached within the current interval
     double step;        // step carried between attempts and intervals
@@ -123,9 +124,12 @@ template <typename T> struct RkArgs {
     T* y5;            // [image][3][N] fifth-order solution of the attempt
     double* errp;     // [image][tile] squared scaled-error partials
     int n_tiles;      // tiles of 1024 components per image
-    RkString* st;     // [n_str]
-    const int* img_str;  // [n_img] string of each image
-    int* active;      // any string still inside its interval (written by the controller)
+    RkString* st;     // [n_sys]
+    const int* img_sys;   // [n_img] system of each image
+    const int* sys_img0;  // [n_sys] first image of each system (its images are consecutive)
+    const int* sys_cnt;   // [n_sys] images of each system
+    int n_sys;
+    int* active;      // any system still inside its interval (written by the controller)
     double T_int, rtol, atol;
 };
 
@@ -169,7 +173,7 @@ void launch_xinv_force(const GroupArgs<T>& g, bool do_fft, T* kout, bool energie
 template <typename T> void launch_rk_assemble(const GroupArgs<T>& g, const RkArgs<T>& r, int stage, cudaStream_t st);
 template <typename T> void launch_rk_finish(const GroupArgs<T>& g, const RkArgs<T>& r, cudaStream_t st);
 template <typename T>
-void launch_rk_control(const GroupArgs<T>& g, const RkArgs<T>& r, const ArcArgs& a, int begin, cudaStream_t st);
+void launch_rk_control(const GroupArgs<T>& g, const RkArgs<T>& r, int begin, cudaStream_t st);
 template <typename T> void launch_rk_commit(const GroupArgs<T>& g, const RkArgs<T>& r, cudaStream_t st);
 template <typename T> void launch_arc(const GroupArgs<T>& g, const ArcArgs& a, int nthr, cudaStream_t st);
 template <typename T>

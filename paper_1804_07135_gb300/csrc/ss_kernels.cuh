@@ -1189,7 +1189,7 @@ template <typename T, int STAGE>
 __global__ void __launch_bounds__(256) rk_assemble_kernel(GroupArgs<T> g, RkArgs<T> r) {
     const int im = blockIdx.y;
     const size_t M = (size_t)3 * g.N, base = (size_t)im * M, stride = (size_t)g.n_img * M;
-    const RkString& S = r.st[r.img_str[im]];
+    const RkString& S = r.st[r.img_sys[im]];
     const T hs = S.done ? T(0) : T(S.hs);
     const size_t e1 = min(M, (size_t)(blockIdx.x + 1) * kRkTile);
     for (size_t e = (size_t)blockIdx.x * kRkTile + threadIdx.x; e < e1; e += blockDim.x) {
@@ -1206,7 +1206,7 @@ __global__ void __launch_bounds__(256) rk_finish_kernel(GroupArgs<T> g, RkArgs<T
     __shared__ double red[32];
     const int im = blockIdx.y;
     const size_t M = (size_t)3 * g.N, base = (size_t)im * M, stride = (size_t)g.n_img * M;
-    const RkString& S = r.st[r.img_str[im]];
+    const RkString& S = r.st[r.img_sys[im]];
     const T hs = S.done ? T(0) : T(S.hs);
     const T rtol = T(r.rtol), atol = T(r.atol);
     T v[1] = {T(0)};
@@ -1231,16 +1231,16 @@ __global__ void __launch_bounds__(256) rk_finish_kernel(GroupArgs<T> g, RkArgs<T
     if (threadIdx.x == 0) r.errp[(size_t)im * r.n_tiles + blockIdx.x] = out[0];
 }
 
-// One CTA: per string (a warp each), the error norm sqrt(sum / (K 3N)) summed in image and tile order,
+// One CTA: per ODE system (a warp each), the error norm sqrt(sum / (3N x its images)) over its partials,
 // then the step-size control.  begin != 0 opens a new interval instead (t = 0, first step cut to T).
 template <typename T>
-__global__ void __launch_bounds__(256) rk_control_kernel(GroupArgs<T> g, RkArgs<T> r, ArcArgs a, int begin) {
+__global__ void __launch_bounds__(256) rk_control_kernel(GroupArgs<T> g, RkArgs<T> r, int begin) {
     __shared__ int any;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     if (threadIdx.x == 0) any = 0;
     __syncthreads();
     const double T_int = r.T_int;
-    for (int s = warp; s < a.n_str; s += nwarp) {
+    for (int s = warp; s < r.n_sys; s += nwarp) {
         RkString S = r.st[s];
         if (begin) {
             if (lane == 0) {
@@ -1261,20 +1261,22 @@ __global__ void __launch_bounds__(256) rk_control_kernel(GroupArgs<T> g, RkArgs<
             }
             continue;
         }
-        const int n = a.str_K[s] * r.n_tiles;
-        const double* ep = r.errp + (size_t)a.str_img0[s] * r.n_tiles;
+        const int n = r.sys_cnt[s] * r.n_tiles;
+        const double* ep = r.errp + (size_t)r.sys_img0[s] * r.n_tiles;
         double v = 0.0;
         for (int i = lane; i < n; i += 32) v += ep[i];
         v = warp_sum_d(v);
         if (lane == 0) {
-            const double err = sqrt(v / (3.0 * (double)g.N * (double)a.str_K[s]));
+            const double err = sqrt(v / (3.0 * (double)g.N * (double)r.sys_cnt[s]));
             S.err = err;
-            if (!isfinite(err) || ++S.attempts > 100000) {
-                atomicOr(g.err, isfinite(err) ? kErrStepCollapse : kErrNonFinite);
+            if (++S.attempts > 100000) {
+                atomicOr(g.err, kErrStepCollapse);
                 S.done = 1;
                 S.accepted = 0;
             } else {
-                double fac = err > 0.0 ? 0.9 * pow(err, -0.2) : 5.0;
+                // stages that overflowed (F grows like |s|^3 off the unit sphere) give a non-finite
+                // norm: a rejection with the smallest factor
+                double fac = !isfinite(err) ? 0.2 : err > 0.0 ? 0.9 * pow(err, -0.2) : 5.0;
                 if (fac < 0.2) fac = 0.2;
                 if (err <= 1.0) {
                     if (fac > 5.0) fac = 5.0;
@@ -1305,7 +1307,7 @@ __global__ void __launch_bounds__(256) rk_control_kernel(GroupArgs<T> g, RkArgs<
 template <typename T>
 __global__ void __launch_bounds__(256) rk_commit_kernel(GroupArgs<T> g, RkArgs<T> r) {
     const int im = blockIdx.y;
-    const RkString& S = r.st[r.img_str[im]];
+    const RkString& S = r.st[r.img_sys[im]];
     if (!S.accepted) return;  // uniform over the CTA
     const int N = g.N;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1620,8 +1622,8 @@ template <typename T> void launch_rk_finish(const GroupArgs<T>& g, const RkArgs<
 }
 
 template <typename T>
-void launch_rk_control(const GroupArgs<T>& g, const RkArgs<T>& r, const ArcArgs& a, int begin, cudaStream_t st) {
-    rk_control_kernel<T><<<1, 256, 0, st>>>(g, r, a, begin);
+void launch_rk_control(const GroupArgs<T>& g, const RkArgs<T>& r, int begin, cudaStream_t st) {
+    rk_control_kernel<T><<<1, 256, 0, st>>>(g, r, begin);
 }
 
 template <typename T> void launch_rk_commit(const GroupArgs<T>& g, const RkArgs<T>& r, cudaStream_t st) {
@@ -1722,7 +1724,7 @@ void launch_interp_identity(InterpEntry* tab, int img0, int K, cudaStream_t st) 
     template void launch_xinv_force<T>(const GroupArgs<T>&, bool, T*, bool, int, size_t, cudaStream_t);        \
     template void launch_rk_assemble<T>(const GroupArgs<T>&, const RkArgs<T>&, int, cudaStream_t);             \
     template void launch_rk_finish<T>(const GroupArgs<T>&, const RkArgs<T>&, cudaStream_t);                    \
-    template void launch_rk_control<T>(const GroupArgs<T>&, const RkArgs<T>&, const ArcArgs&, int, cudaStream_t); \
+    template void launch_rk_control<T>(const GroupArgs<T>&, const RkArgs<T>&, int, cudaStream_t);                \
     template void launch_rk_commit<T>(const GroupArgs<T>&, const RkArgs<T>&, cudaStream_t);                    \
     template void launch_arc<T>(const GroupArgs<T>&, const ArcArgs&, int, cudaStream_t);                       \
     template void launch_eval_reduce<T>(const GroupArgs<T>&, const ArcArgs&, double*, double*, cudaStream_t);  \

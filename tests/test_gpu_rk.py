@@ -29,15 +29,16 @@ def _model(c):
     return oracle.model(*c[:7])
 
 
-def _gpu_run(ss, cases, paths, T, n_iter, prec, rtol, atol):
+def _gpu_run(ss, cases, paths, T, n_iter, prec, rtol, atol, kind=None):
     with ss.StringMethod(cases, dt=T, precision=prec) as sm:
-        sm.set_integrator(ss.SS_INT_DOPRI5, rtol, atol)
+        sm.set_integrator(ss.SS_INT_DOPRI5 if kind is None else kind, rtol, atol)
         for i, p in enumerate(paths):
             sm.set_path(i, p)
         starts = [sm.get_path(i) for i in range(len(cases))]
         sm.step(n_iter)
         out = [dict(path=sm.get_path(i), state=sm.integrator_state(i), e=sm.energies(i),
-                    e_step=sm.step_energies(i)) for i in range(len(cases))]
+                    e_step=sm.step_energies(i),
+                    images=[sm.integrator_state(i, k) for k in range(cases[i][7])]) for i in range(len(cases))]
     return starts, out
 
 
@@ -91,6 +92,34 @@ def test_dopri5_batch_with_independent_step_histories(ss):
     assert counts[0] != counts[1]
 
 
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_dopri5_per_image_control(ss, prec):
+    # every image its own ODE system: per-image counts and steps against the oracle's per-image run;
+    # two strings in one size group and one in another
+    cases = [(16, 16, 1, 1.0, 0.3, 0.05, 0.01, 6), (16, 16, 1, 1.6, 0.4, 0.1, 0.02, 3),
+             (12, 10, 2, 1.0, 0.2, 0.1, 0.02, 4)]
+    paths = [W.bloch_point_path(c[0], c[1], c[2], c[7], R=3.0, D=c[4]) for c in cases]
+    T, n_iter = 1.0, 3
+    rtol, atol = (1e-6, 1e-8) if prec == FP64 else (1e-4, 1e-6)
+    starts, outs = _gpu_run(ss, cases, paths, T, n_iter, prec, rtol, atol, kind=ss.SS_INT_DOPRI5_IMAGE)
+    for c, s0, g in zip(cases, starts, outs):
+        ref, e_ref, steps_ref, counts_ref = oracle.string_run_rk(_model(c), _unit(s0), n_iter, T, rtol, atol,
+                                                                 per_image=True)
+        got_counts = np.array([st[1:] for st in g["images"]])
+        got_steps = np.array([st[0] for st in g["images"]])
+        if prec == FP64:
+            np.testing.assert_array_equal(got_counts, counts_ref)
+            np.testing.assert_allclose(got_steps, steps_ref, rtol=1e-9)
+            assert np.abs(g["path"] - ref).max() < 1e-10, c
+            np.testing.assert_allclose(g["e"], e_ref, rtol=0, atol=1e-9)
+        else:
+            assert np.abs(got_counts - counts_ref).max() <= 3, c
+            assert np.abs(g["path"] - ref).max() < 1e-4, c
+            np.testing.assert_allclose(g["e"], e_ref, rtol=0, atol=1e-4)
+        assert g["state"] == (got_steps.min(), *got_counts.sum(0))
+        assert len({tuple(x) for x in counts_ref}) > 1  # the images do take different step histories
+
+
 def test_dopri5_state_resets_and_euler_resumes(ss):
     spec = W.tiny_bloch().strings[0]
     c = _case(spec)
@@ -125,3 +154,5 @@ def test_dopri5_invalid_arguments(ss):
             assert ei.value.status == ss.SS_ERR_INVALID_ARG
         with pytest.raises(ss.SsError):
             sm.integrator_state(3)
+        with pytest.raises(ss.SsError):
+            sm.integrator_state(0, spec.n_images)
