@@ -66,6 +66,8 @@ def _load():
             "or_step": (None, [i, d, dp, dp]),
             "or_reparam": (None, [i, i, dp, dp, dp]),
             "or_string_run": (i, [mp, i, i, d, dp, dp]),
+            "or_reparam_v": (None, [i, i, dp, dp, i, i, dp]),
+            "or_string_run_v": (i, [mp, i, i, d, i, i, dp, dp, P(ctypes.c_int)]),
             "or_string_run_rk": (i, [mp, i, i, d, d, d, i, dp, dp, dp, P(ctypes.c_long)]),
             "or_dp_tableau": (None, [dp, dp, dp]),
             "or_barrier": (d, [i, dp, P(i)]),
@@ -187,6 +189,31 @@ def string_run(m: OracleModel, path, n_iter: int, dt: float, with_energies: bool
                              _ptr(e) if with_energies else None) != 0:
         raise MemoryError("oracle string run: out of memory")
     return phi, e
+
+
+def reparam_v(path, spline: bool = False, kc: int = -1, return_alpha: bool = False):
+    """Reparametrisation with the variants: natural cubic spline instead of linear interpolation,
+    and/or a climbing image kc splitting the string into two parts."""
+    star = _f64(path)
+    K = star.shape[0]
+    out = np.zeros_like(star)
+    alpha = np.zeros(K)
+    _load().or_reparam_v(K, star[0].size // 3, _ptr(star), _ptr(out), int(bool(spline)), int(kc), _ptr(alpha))
+    return (out, alpha) if return_alpha else out
+
+
+def string_run_v(m: OracleModel, path, n_iter: int, dt: float, spline: bool = False, climb: bool = False,
+                 with_energies: bool = True):
+    """Sec. III loop (Euler step) with the spline and climbing-image variants.  Returns (final path,
+    energies or None, the climbing image the next iteration would use or -1)."""
+    phi = _f64(path).copy()
+    K = phi.shape[0]
+    e = np.zeros(K) if with_energies else None
+    kc = ctypes.c_int(-1)
+    if _load().or_string_run_v(ctypes.byref(m), K, int(n_iter), float(dt), int(bool(spline)), int(bool(climb)),
+                               _ptr(phi), _ptr(e) if with_energies else None, ctypes.byref(kc)) != 0:
+        raise MemoryError("oracle string run: out of memory")
+    return phi, e, int(kc.value)
 
 
 def string_run_rk(m: OracleModel, path, n_iter: int, T: float, rtol: float = 1e-6, atol: float = 1e-8,

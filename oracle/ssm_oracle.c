@@ -330,6 +330,190 @@ int or_string_run(const or_model* m, int K, int n_iter, double dt, double* phi, 
     return 0;
 }
 
+/* ---- reparametrisation variants and the climbing image ------------------------------------------
+ * Sec. III leaves the interpolation scheme open and names the climbing image as a refinement of the
+ * saddle that the paper itself omits.  Readings taken here:
+ *  - spline: a natural cubic spline (second derivative zero at both ends) through (alpha*_j, phi*_j),
+ *    j over the part, per Cartesian component, evaluated at the targets and renormalised per site;
+ *    a part with a zero-length segment, or with a single segment, is interpolated linearly;
+ *  - climbing image kc (0 < kc < K-1): the string is reparametrised as two parts [0, kc] and
+ *    [kc, K-1], each to equal arc length on its own (targets (k - a) / (b - a) in part [a, b]); kc
+ *    itself does not move;
+ *  - its dynamics: the projected force F = h - (s.h) s with its component along the unit tangent
+ *    reversed, F - 2 (F.tau) tau / (tau.tau), tau = (phi_{kc+1} - phi_{kc-1}) projected per site onto
+ *    the tangent plane at phi_kc, all from the states before the step; one Euler step of dt;
+ *  - which image climbs: the interior image of highest energy among the states the previous
+ *    iteration started from (lowest index on ties); none in the first iteration. */
+
+/* Natural cubic spline second derivatives m[0..n] of (x_j, y_j), j = 0..n (n >= 2, x increasing):
+ * m_0 = m_n = 0 and, for 0 < i < n, h_{i-1} m_{i-1} + 2 (h_{i-1} + h_i) m_i + h_i m_{i+1}
+ * = 6 ((y_{i+1} - y_i) / h_i - (y_i - y_{i-1}) / h_{i-1}), h_i = x_{i+1} - x_i, solved by forward
+ * elimination and back substitution (cp, dp: scratch of n + 1). */
+static void natural_spline(int n, const double* x, const double* y, double* m, double* cp, double* dp) {
+    m[0] = m[n] = 0.0;
+    for (int i = 1; i < n; ++i) {
+        const double hl = x[i] - x[i - 1], hr = x[i + 1] - x[i];
+        const double diag = 2.0 * (hl + hr), rhs = 6.0 * ((y[i + 1] - y[i]) / hr - (y[i] - y[i - 1]) / hl);
+        const double lo = i > 1 ? hl : 0.0;  /* coefficient of m_{i-1} (m_0 = 0 is known) */
+        const double den = diag - lo * (i > 1 ? cp[i - 1] : 0.0);
+        cp[i] = (i < n - 1 ? hr : 0.0) / den;
+        dp[i] = (rhs - lo * (i > 1 ? dp[i - 1] : 0.0)) / den;
+    }
+    for (int i = n - 1; i >= 1; --i) m[i] = dp[i] - (i < n - 1 ? cp[i] * m[i + 1] : 0.0);
+}
+
+/* The spline of (x_j, y_j) with second derivatives m, on segment [x_j, x_{j+1}], at xe. */
+static double spline_at(const double* x, const double* y, const double* m, int j, double xe) {
+    const double h = x[j + 1] - x[j], a = x[j + 1] - xe, b = xe - x[j];
+    return m[j] * a * a * a / (6.0 * h) + m[j + 1] * b * b * b / (6.0 * h) + (y[j] - m[j] * h * h / 6.0) * a / h +
+           (y[j + 1] - m[j + 1] * h * h / 6.0) * b / h;
+}
+
+/* Reparametrisation (Eqs. 11-12) with the variants above: spline != 0 for the cubic spline, kc the
+ * climbing image or -1.  alpha_out (optional, K): alpha*_k within its part. */
+void or_reparam_v(int K, int n_sites, const double* phi_star, double* phi, int spline, int kc, double* alpha_out) {
+    const size_t M = (size_t)3 * n_sites;
+    double* sk = (double*)malloc(sizeof(double) * K * 6);
+    double *al = sk + K, *y = sk + 2 * K, *mm = sk + 3 * K, *cp = sk + 4 * K, *dp = sk + 5 * K;
+    sk[0] = 0.0;
+    for (int k = 1; k < K; ++k) {
+        double d2 = 0.0;
+        for (size_t c = 0; c < M; ++c) {
+            const double d = phi_star[k * M + c] - phi_star[(k - 1) * M + c];
+            d2 += d * d;
+        }
+        sk[k] = sk[k - 1] + sqrt(d2);
+    }
+    memcpy(phi, phi_star, sizeof(double) * M * K);
+    for (int k = 0; k < K; ++k) al[k] = 0.0;
+    const int split = kc > 0 && kc < K - 1;
+    const int parts[2][2] = {{0, split ? kc : K - 1}, {kc, K - 1}};
+    for (int p = 0; p < 1 + split; ++p) {
+        const int a = parts[p][0], b = parts[p][1], n = b - a;
+        const double L = sk[b] - sk[a];
+        if (!(L > 0.0)) continue;
+        for (int j = a; j <= b; ++j) al[j] = (sk[j] - sk[a]) / L;
+        int use_spline = spline && n >= 2;
+        for (int j = a; j < b; ++j)
+            if (!(al[j + 1] > al[j])) use_spline = 0;
+        for (int k = a + 1; k < b; ++k) {
+            const double ak = (double)(k - a) / (double)n;
+            int j = a;
+            for (int i = a; i <= b - 1; ++i)
+                if (al[i] <= ak) j = i;
+            const double t = (ak - al[j]) / (al[j + 1] - al[j]);
+            for (int i = 0; i < n_sites; ++i) {
+                double u[3];
+                for (int c = 0; c < 3; ++c) {
+                    if (use_spline) {
+                        for (int q = 0; q <= n; ++q) y[q] = phi_star[(a + q) * M + 3 * i + c];
+                        natural_spline(n, al + a, y, mm, cp, dp);
+                        u[c] = spline_at(al + a, y, mm, j - a, ak);
+                    } else {
+                        u[c] = (1.0 - t) * phi_star[j * M + 3 * i + c] + t * phi_star[(j + 1) * M + 3 * i + c];
+                    }
+                }
+                const double nr = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+                for (int c = 0; c < 3; ++c) phi[k * M + 3 * i + c] = u[c] / nr;
+            }
+        }
+    }
+    if (alpha_out) memcpy(alpha_out, al, sizeof(double) * K);
+    free(sk);
+}
+
+/* The string iteration of Sec. III with the variants above (Euler step as in or_string_run).  kc_out
+ * (optional): the climbing image the next iteration would use, or -1. */
+int or_string_run_v(const or_model* m, int K, int n_iter, double dt, int spline, int climb, double* phi,
+                    double* energies, int* kc_out) {
+    const int N = m->nx * m->ny * m->nz;
+    const size_t M = (size_t)3 * N;
+    double* table = NULL;
+    if (m->w != 0.0) {
+        table = dipole_table(m);
+        if (!table) return -1;
+    }
+    double* h = (double*)malloc(sizeof(double) * M * K);
+    double* star = (double*)malloc(sizeof(double) * M * K);
+    double* sc = (double*)malloc(sizeof(double) * M);
+    double* e = (double*)malloc(sizeof(double) * K);
+    if (!h || !star || !sc || !e) {
+        free(table);
+        free(h);
+        free(star);
+        free(sc);
+        free(e);
+        return -1;
+    }
+    int kc = -1;
+    for (int it = 0; it < n_iter; ++it) {
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int k = 0; k < K; ++k) {
+            field_one(m, table, phi + k * M, h + k * M);
+            e[k] = or_energy_from_field(N, phi + k * M, h + k * M);
+        }
+        if (kc >= 0) {
+            /* the climbing image's step, from the states before the step */
+            const double *s = phi + kc * M, *hk = h + kc * M, *pp = phi + (kc + 1) * M, *pm = phi + (kc - 1) * M;
+            double ft = 0.0, tt = 0.0;
+            for (int i = 0; i < N; ++i) {
+                const double* si = s + 3 * i;
+                double tau[3], F[3];
+                const double sh = si[0] * hk[3 * i] + si[1] * hk[3 * i + 1] + si[2] * hk[3 * i + 2];
+                for (int c = 0; c < 3; ++c) {
+                    tau[c] = pp[3 * i + c] - pm[3 * i + c];
+                    F[c] = hk[3 * i + c] - sh * si[c];
+                }
+                const double ts = tau[0] * si[0] + tau[1] * si[1] + tau[2] * si[2];
+                for (int c = 0; c < 3; ++c) {
+                    tau[c] -= ts * si[c];
+                    ft += F[c] * tau[c];
+                    tt += tau[c] * tau[c];
+                }
+            }
+            const double cf = tt > 0.0 ? ft / tt : 0.0;
+            for (int i = 0; i < N; ++i) {
+                const double* si = s + 3 * i;
+                const double sh = si[0] * hk[3 * i] + si[1] * hk[3 * i + 1] + si[2] * hk[3 * i + 2];
+                double tau[3], u[3];
+                for (int c = 0; c < 3; ++c) tau[c] = pp[3 * i + c] - pm[3 * i + c];
+                const double ts = tau[0] * si[0] + tau[1] * si[1] + tau[2] * si[2];
+                for (int c = 0; c < 3; ++c) {
+                    tau[c] -= ts * si[c];
+                    u[c] = si[c] + dt * (hk[3 * i + c] - sh * si[c] - 2.0 * cf * tau[c]);
+                }
+                const double nr = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+                for (int c = 0; c < 3; ++c) sc[3 * i + c] = u[c] / nr;
+            }
+        }
+        for (int k = 0; k < K; ++k)
+            if (k != kc) or_step(N, dt, h + k * M, phi + k * M);
+        if (kc >= 0) memcpy(phi + kc * M, sc, sizeof(double) * M);
+        memcpy(star, phi, sizeof(double) * M * K);
+        or_reparam_v(K, N, star, phi, spline, kc, NULL);
+        kc = -1;
+        if (climb && K >= 3) {
+            kc = 1;
+            for (int k = 2; k < K - 1; ++k)
+                if (e[k] > e[kc]) kc = k;
+        }
+    }
+    if (kc_out) *kc_out = kc;
+    if (energies) {
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int k = 0; k < K; ++k) {
+            field_one(m, table, phi + k * M, h + k * M);
+            energies[k] = or_energy_from_field(N, phi + k * M, h + k * M);
+        }
+    }
+    free(table);
+    free(h);
+    free(star);
+    free(sc);
+    free(e);
+    return 0;
+}
+
 /* Adaptive explicit Runge-Kutta evolution of the images (Sec. III names explicit Runge-Kutta methods
  * with adaptive step-size control, namely the Dormand-Prince pair), in place of the fixed
  * projected-Euler step of or_string_run.  Each iteration integrates
