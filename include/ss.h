@@ -191,6 +191,33 @@ ss_status ss_set_integrator(ss_ctx* ctx, int kind, double rtol, double atol);
 ss_status ss_integrator_state(ss_ctx* ctx, int string, int image, double* step, long long* accepted,
                               long long* rejected);
 
+/* Reparametrisation variants (Sec. III leaves the interpolation open, and names the climbing image as a
+ * refinement of the saddle that the paper itself omits). */
+enum { SS_INTERP_LINEAR = 0, SS_INTERP_SPLINE = 1 };
+
+/* Chooses how the images are redistributed after each evolution.
+ *   interp = SS_INTERP_LINEAR (the default): piecewise-linear interpolation in alpha (Eq. 12), then
+ *   per-site renormalisation.  SS_INTERP_SPLINE: a natural cubic spline (second derivative zero at the
+ *   ends) through (alpha*_j, phi*_j) per Cartesian component, evaluated at the targets and renormalised
+ *   per site; a part of the string with a zero-length segment is interpolated linearly.  Strings of at
+ *   most 256 images (longer: SS_ERR_INVALID_ARG).
+ *   climb = 1: the climbing image.  The interior image of highest energy among the states an iteration
+ *   started from climbs in the next iteration (none in a path's first iteration; lowest index on ties):
+ *   its Euler step uses the projected force F = h - (s.h) s with its component along the unit tangent
+ *   reversed, F - 2 (F.tau) tau / (tau.tau), tau = (phi_{kc+1} - phi_{kc-1}) projected per site onto
+ *   the tangent plane at phi_kc (states before the step); the reparametrisation then treats [0, kc]
+ *   and [kc, K-1] as two strings, each brought to equal arc length, kc keeping its place.  Climbing is
+ *   defined for the Euler step only (SS_ERR_STATE under a Runge-Kutta integrator, and
+ *   ss_set_integrator refuses a Runge-Kutta kind while it is on).
+ * Adds 2 launches per size group and iteration for the climbing image and 1 for the spline; allocates
+ * one string-state copy per size group for the climbing image and 2 K^2 doubles per string for the
+ * spline on first use.  Takes effect at the next ss_step; every string restarts without a climbing
+ * image. */
+ss_status ss_set_reparam(ss_ctx* ctx, int interp, int climb);
+
+/* The image of `string` that climbs in the next iteration, or -1 (none, or climbing off).  Synchronises. */
+ss_status ss_climbing_image(ss_ctx* ctx, int string, int* k);
+
 /* Shape queries. */
 int ss_num_strings(const ss_ctx* ctx);
 ss_status ss_string_info(const ss_ctx* ctx, int string, ss_string_desc* out);

@@ -22,6 +22,7 @@ SS_DTYPE_F32, SS_DTYPE_F64 = 0, 1
 SS_PREC_FP32, SS_PREC_FP64 = 0, 1
 SS_DIPOLE_OFF, SS_DIPOLE_FFT = 0, 2
 SS_INT_EULER, SS_INT_DOPRI5, SS_INT_DOPRI5_IMAGE = 0, 1, 2
+SS_INTERP_LINEAR, SS_INTERP_SPLINE = 0, 1
 _STATUS = {0: "SS_OK", 1: "SS_ERR_INVALID_ARG", 2: "SS_ERR_CUDA", 3: "SS_ERR_OOM", 4: "SS_ERR_NONFINITE",
            5: "SS_ERR_TIMEOUT", 6: "SS_ERR_STATE"}
 
@@ -57,6 +58,8 @@ _SIGNATURES = {
     "ss_get_path": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "ss_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "ss_set_integrator": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double]),
+    "ss_set_reparam": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "ss_climbing_image": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "ss_integrator_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
     "ss_energies": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
@@ -249,6 +252,16 @@ def ss_set_integrator(ctx, kind: int, rtol: float = 1e-6, atol: float = 1e-8) ->
     _check(_lib.ss_set_integrator(ctx, int(kind), float(rtol), float(atol)), ctx)
 
 
+def ss_set_reparam(ctx, interp: int = SS_INTERP_LINEAR, climb: bool = False) -> None:
+    _check(_lib.ss_set_reparam(ctx, int(interp), int(bool(climb))), ctx)
+
+
+def ss_climbing_image(ctx, string: int) -> int:
+    k = ctypes.c_int()
+    _check(_lib.ss_climbing_image(ctx, int(string), ctypes.byref(k)), ctx)
+    return int(k.value)
+
+
 def ss_integrator_state(ctx, string: int, image: int = -1) -> tuple[float, int, int]:
     """(carried step, accepted attempts, rejected attempts) of the adaptive integrator: the string's
     smallest step and summed counts (image = -1), or those of the system holding `image`."""
@@ -389,6 +402,12 @@ class StringMethod:
 
     def integrator_state(self, string=0, image=-1):
         return ss_integrator_state(self.ctx, string, image)
+
+    def set_reparam(self, interp=SS_INTERP_LINEAR, climb=False):
+        ss_set_reparam(self.ctx, interp, climb)
+
+    def climbing_image(self, string=0):
+        return ss_climbing_image(self.ctx, string)
 
     def energies(self, string=0):
         return ss_energies(self.ctx, string)

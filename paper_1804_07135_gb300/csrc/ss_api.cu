@@ -102,6 +102,9 @@ struct Group {
     int* rk_active = nullptr;
     InterpEntry* interp_ident = nullptr;
     int rk_tiles = 0;
+    // reparametrisation variants (allocated by ss_set_reparam)
+    void* hc = nullptr;  // [image][3][N] force of the climbing image
+    int* climb_img = nullptr;
     ArcArgs arc{};
 };
 
@@ -126,7 +129,9 @@ struct ss_ctx {
     std::vector<void*> allocs;
     cudaGraphExec_t graph1 = nullptr, graphN = nullptr;
     int graphN_iters = 64;
-    int integrator = 0;  // SS_INT_EULER or SS_INT_DOPRI5
+    int integrator = 0;  // SS_INT_EULER, SS_INT_DOPRI5 or SS_INT_DOPRI5_IMAGE
+    int interp = 0;      // SS_INTERP_LINEAR or SS_INTERP_SPLINE
+    int climb = 0;       // climbing image on
     double rtol = 1e-6, atol = 1e-8;
     int* h_active = nullptr;  // pinned, one flag per size group
     std::string err;
@@ -205,6 +210,7 @@ template <typename T> GroupArgs<T> group_args(const ss_ctx* c, const Group& g) {
     a.ty_a = g.ty_a;
     a.ty_c = g.ty_c;
     a.err = c->d_err;
+    a.climb_img = g.climb_img;
     return a;
 }
 
@@ -601,6 +607,7 @@ template <typename T> ss_status rk_iterations(ss_ctx* c, int n_iter) {
         for (Group& g : c->groups) {
             GroupArgs<T> a = group_args<T>(c, g);
             launch_arc<T>(a, g.arc, g.thr_arc, c->cs);
+            if (c->interp == SS_INTERP_SPLINE) launch_spline_apply<T>(a, g.arc, g.arc.maxK, c->cs);
         }
     }
     return SS_OK;
@@ -613,8 +620,14 @@ template <typename T> void issue_iteration(ss_ctx* c, cudaStream_t st) {
         GroupArgs<T> a = group_args<T>(c, g);
         launch_xfwd<T>(a, g.dipole, g.thr_a, g.smem_a, st);
         if (g.dipole) launch_yz<T>(a, g.thr_b, g.smem_b, st);
-        launch_xinv_step<T>(a, g.dipole, dt, g.thr_c, g.smem_c, st);
+        if (c->climb) {
+            launch_xinv_step_climb<T>(a, g.dipole, dt, (T*)g.hc, g.thr_c, g.smem_c, st);
+            launch_climb<T>(a, g.arc, dt, (const T*)g.hc, st);
+        } else {
+            launch_xinv_step<T>(a, g.dipole, dt, g.thr_c, g.smem_c, st);
+        }
         launch_arc<T>(a, g.arc, g.thr_arc, st);
+        if (c->interp == SS_INTERP_SPLINE) launch_spline_apply<T>(a, g.arc, g.arc.maxK, st);
     }
 }
 
@@ -900,6 +913,11 @@ ss_status ss_set_path(ss_ctx* c, int string, const void* spins, int dtype, int o
             launch_aos_to_soa<float, float>((const float*)src, dst, K, g.N, c->d_err, c->cs);
     }
     launch_interp_identity(g.interp, r.img0, K, c->cs);
+    if (c->climb) {  // no image climbs before the new path's first energies are known
+        const int none = -1;
+        CUDA_TRY(c, cudaMemcpyAsync(g.arc.kc + r.local, &none, sizeof none, cudaMemcpyHostToDevice, c->cs));
+        CUDA_TRY(c, cudaMemsetAsync(g.climb_img + r.img0, 0, (size_t)K * sizeof(int), c->cs));
+    }
     if (c->integrator != SS_INT_EULER) {  // the adaptive integrator restarts from step opts.dt on a new path
         const std::vector<RkString> fresh(rk_sys_count(c, r), rk_fresh(c));
         CUDA_TRY(c, cudaMemcpyAsync(g.rk_st + rk_first_sys(c, r), fresh.data(), fresh.size() * sizeof(RkString),
@@ -919,6 +937,8 @@ ss_status ss_set_integrator(ss_ctx* c, int kind, double rtol, double atol) {
         return fail(c, SS_ERR_INVALID_ARG, "unknown integrator %d", kind);
     if (kind != SS_INT_EULER && !(rtol > 0.0 && atol > 0.0 && std::isfinite(rtol) && std::isfinite(atol)))
         return fail(c, SS_ERR_INVALID_ARG, "rtol and atol must be positive and finite");
+    if (kind != SS_INT_EULER && c->climb)
+        return fail(c, SS_ERR_STATE, "the climbing image is defined for the Euler step only");
     TRY(enter(c));
     if (kind != SS_INT_EULER) {
         if (!c->h_active) CUDA_TRY(c, cudaHostAlloc((void**)&c->h_active, c->groups.size() * sizeof(int), cudaHostAllocDefault));
@@ -927,6 +947,67 @@ ss_status ss_set_integrator(ss_ctx* c, int kind, double rtol, double atol) {
         c->atol = atol;
     }
     c->integrator = kind;
+    ss_status st = sync_check(c);
+    TRY(leave(c));
+    return st;
+}
+
+ss_status ss_set_reparam(ss_ctx* c, int interp, int climb) {
+    if (!c) return SS_ERR_INVALID_ARG;
+    if (interp != SS_INTERP_LINEAR && interp != SS_INTERP_SPLINE)
+        return fail(c, SS_ERR_INVALID_ARG, "unknown interpolation %d", interp);
+    if (climb != 0 && climb != 1) return fail(c, SS_ERR_INVALID_ARG, "climb must be 0 or 1");
+    if (climb && c->integrator != SS_INT_EULER)
+        return fail(c, SS_ERR_STATE, "the climbing image is defined for the Euler step only");
+    if (interp == SS_INTERP_SPLINE)
+        for (const StringRec& r : c->strs)
+            if (r.d.n_images > kSplineMaxK)
+                return fail(c, SS_ERR_INVALID_ARG, "the spline takes strings of at most %d images", kSplineMaxK);
+    TRY(enter(c));
+    for (Group& g : c->groups) {
+        ArcArgs& a = g.arc;
+        const size_t M = (size_t)3 * g.N, nstr = g.strs.size(), mk = (size_t)a.maxK;
+        if (climb && !g.hc) {
+            a.c_tiles = (g.N + kClimbTile - 1) / kClimbTile;
+            TRY(dalloc(c, &g.hc, g.n_img * M * real_size(c)));
+            TRY(dalloc(c, (void**)&g.climb_img, g.n_img * sizeof(int)));
+            TRY(dalloc(c, (void**)&a.kc, nstr * sizeof(int)));
+            TRY(dalloc(c, (void**)&a.cpart, nstr * a.c_tiles * 2 * sizeof(double)));
+            a.climb_img = g.climb_img;
+        }
+        if (climb) {  // every string starts without a climbing image
+            CUDA_TRY(c, cudaMemsetAsync(a.kc, 0xff, nstr * sizeof(int), c->cs));
+            CUDA_TRY(c, cudaMemsetAsync(g.climb_img, 0, g.n_img * sizeof(int), c->cs));
+        }
+        if (interp == SS_INTERP_SPLINE && !a.W) {
+            TRY(dalloc(c, (void**)&a.W, nstr * mk * mk * sizeof(double)));
+            TRY(dalloc(c, (void**)&a.P, nstr * mk * mk * sizeof(double)));
+            TRY(dalloc(c, (void**)&a.wcopy, nstr * mk * sizeof(int)));
+            CUDA_TRY(c, cudaMemsetAsync(a.wcopy, 0xff, nstr * mk * sizeof(int), c->cs));
+        }
+        a.climb = climb;
+        a.spline = interp == SS_INTERP_SPLINE;
+    }
+    c->interp = interp;
+    c->climb = climb;
+    // the captured graphs hold the previous kernel sequence and arguments
+    if (c->graph1) cudaGraphExecDestroy(c->graph1);
+    if (c->graphN) cudaGraphExecDestroy(c->graphN);
+    c->graph1 = c->graphN = nullptr;
+    ss_status st = sync_check(c);
+    TRY(leave(c));
+    return st;
+}
+
+ss_status ss_climbing_image(ss_ctx* c, int string, int* k) {
+    TRY(check_string(c, string));
+    if (!k) return fail(c, SS_ERR_INVALID_ARG, "output pointer is NULL");
+    *k = -1;
+    if (!c->climb) return SS_OK;
+    const StringRec& r = c->strs[string];
+    const Group& g = c->groups[r.group];
+    TRY(enter(c));
+    CUDA_TRY(c, cudaMemcpyAsync(k, g.arc.kc + r.local, sizeof(int), cudaMemcpyDeviceToHost, c->cs));
     ss_status st = sync_check(c);
     TRY(leave(c));
     return st;
@@ -1165,7 +1246,7 @@ ss_status ss_string_info(const ss_ctx* c, int string, ss_string_desc* out) {
 int ss_kernels_per_iteration(const ss_ctx* c) {
     if (!c) return 0;
     int n = 0;
-    for (const Group& g : c->groups) n += g.dipole ? 4 : 3;
+    for (const Group& g : c->groups) n += (g.dipole ? 4 : 3) + (c->climb ? 2 : 0) + (c->interp == SS_INTERP_SPLINE ? 1 : 0);
     return n;
 }
 

@@ -85,6 +85,7 @@ template <typename T> struct GroupArgs {
     int n_eblk;     // = nz * ceil(ny / ty_c)
     int ty_a, ty_c; // y rows per CTA in the x-forward and x-inverse kernels
     int* err;       // sticky error word (bit 1: invalid input spin, bit 2: non-finite value)
+    const int* climb_img;  // [n_img] nonzero for the image that climbs this iteration (climbing mode only)
 };
 
 // Arc-length / reparametrisation bookkeeping of one size group.
@@ -101,7 +102,20 @@ struct ArcArgs {
     double* e_last;        // [n_str][maxK] energies of the state before the step
     unsigned* cnt;         // [n_str] tile CTAs finished; zero between launches
     int reparam;           // 0: keep images where they are
+    // variants (Sec. III leaves the interpolation open and names the climbing image as a refinement)
+    int climb;             // climbing image on: the energy CTAs also take tickets, the finisher picks the next one
+    int* kc;               // [n_str] image climbing in the current iteration, or -1
+    int* climb_img;        // [n_img] flag per image for the next iteration's x-inverse kernel
+    double* cpart;         // [n_str][c_tiles][2] (F.tau, tau.tau) partials of the climbing image
+    int c_tiles;           // site tiles of kClimbTile per image
+    int spline;            // natural cubic spline: the finisher writes W, the apply kernel moves the images
+    double* W;             // [n_str][maxK][maxK] interpolation weights phi_k = sum_q W_kq phi*_q
+    double* P;             // [n_str][maxK][maxK] scratch: d m_i / d y_q of the spline, column q contiguous
+    int* wcopy;            // [n_str][maxK] row k is the identity (image kept as it is)
 };
+
+constexpr int kClimbTile = 1024;  // sites per CTA of the climbing-image kernels
+constexpr int kSplineMaxK = 256;  // longest string the spline variant accepts
 
 // Adaptive Runge-Kutta evolution (Sec. III, Dormand-Prince 5(4)): controller state of one ODE system
 // (a whole string, or one image under per-image step control).
@@ -170,6 +184,10 @@ void launch_xinv_eval(const GroupArgs<T>& g, bool do_fft, T* hout, int nthr, siz
 template <typename T>
 void launch_xinv_force(const GroupArgs<T>& g, bool do_fft, T* kout, bool energies, int nthr, size_t smem,
                        cudaStream_t st);
+template <typename T> void launch_xinv_step_climb(const GroupArgs<T>& g, bool do_fft, T dt, T* hc, int nthr, size_t smem,
+                                                  cudaStream_t st);
+template <typename T> void launch_climb(const GroupArgs<T>& g, const ArcArgs& a, T dt, const T* hc, cudaStream_t st);
+template <typename T> void launch_spline_apply(const GroupArgs<T>& g, const ArcArgs& a, int maxK, cudaStream_t st);
 template <typename T> void launch_rk_assemble(const GroupArgs<T>& g, const RkArgs<T>& r, int stage, cudaStream_t st);
 template <typename T> void launch_rk_finish(const GroupArgs<T>& g, const RkArgs<T>& r, cudaStream_t st);
 template <typename T>

@@ -686,7 +686,9 @@ __device__ __forceinline__ void xinv_sites_step2(const GroupArgs<float>& g, floa
 // Per-site work of the x-inverse kernels on rows [y0, y0+rows) of layer z, pair p; buf holds the
 // forward transforms of the conjugated field spectra (line c*rows + yy, fft_pad positions) when
 // HAS_CONV.  MODE 0: projected Euler step into sp and energy partials.  MODE 1: FP64 energy terms (and
-// the field into hout when given).  MODE 2 (a Runge-Kutta stage): the force F = h - (s.h) s of Eq. 13
+// the field into hout when given).  MODE 3: MODE 0, except that the image flagged in g.climb_img writes
+// its force F = h - (s.h) s into hout instead of stepping (the climbing-image kernels step it).
+// MODE 2 (a Runge-Kutta stage): the force F = h - (s.h) s of Eq. 13
 // into hout, s as stored (not renormalised); energy partials only when dt != 0.
 template <typename T, bool HAS_CONV, int MODE>
 __device__ __forceinline__ void xinv_sites(const GroupArgs<T>& g, T dt, T* hout, const cplx<T>* buf, int ls,
@@ -700,6 +702,12 @@ __device__ __forceinline__ void xinv_sites(const GroupArgs<T>& g, T dt, T* hout,
     for (int k = 0; k < NV; ++k) acc[k] = 0.0;
     T eacc[2] = {T(0), T(0)};  // step mode: the thread's few per-site terms, summed in T before FP64
     bool done = false;
+    int climbs[2] = {0, 0};  // MODE 3: which of the pair's images climbs (uniform per image)
+    if constexpr (MODE == 3) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+            if (ia + h < g.n_img) climbs[h] = g.climb_img[ia + h];
+    }
     if constexpr (MODE == 0 && HAS_CONV && std::is_same<T, float>::value) {
         if ((nx & 1) == 0) {  // uniform over the grid
             xinv_sites_step2(g, dt, buf, ls, p, z, y0, rows, tid, nthr, eacc);
@@ -741,14 +749,14 @@ __device__ __forceinline__ void xinv_sites(const GroupArgs<T>& g, T dt, T* hout,
         }
         T hf[3];
         local_field(pr, s0, xp, xm, yp, ym, zp, zm, conv, hf);
-        if (MODE == 0) {
+        if (MODE == 0 || (MODE == 3 && !climbs[h])) {
             T un[3];
             eacc[h] += step_site(s0, hf, dt, un);
             T* __restrict__ o = g.sp + (size_t)im * 3 * N + site;
             o[0] = un[0];
             o[N] = un[1];
             o[2 * N] = un[2];
-        } else if (MODE == 2) {
+        } else if (MODE == 2 || MODE == 3) {
             const T sh = s0[0] * hf[0] + s0[1] * hf[1] + s0[2] * hf[2];
             eacc[h] += T(-0.5) * sh;
             T* __restrict__ o = hout + (size_t)im * 3 * N + site;
@@ -931,6 +939,129 @@ __device__ __forceinline__ unsigned ticket_acq_rel(unsigned* p) {
 }
 
 template <typename T>
+__device__ __noinline__ void arc_finish(const GroupArgs<T>& g, const ArcArgs& a, int str, int K, int img0,
+                                        double* alpha, double* wsum);
+
+// Reparametrisation variants in the finisher (alpha holds the arc lengths s_k).  A climbing image kc
+// (0 < kc < K-1) splits the string into the parts [0, kc] and [kc, K-1], each brought to equal arc length
+// on its own: alpha*_j = (s_j - s_a) / (s_b - s_a) and targets (k - a) / (b - a) in part [a, b]; kc keeps
+// its place.  Linear interpolation writes the gather table as on the plain path.  The natural cubic
+// spline (second derivative zero at a part's ends) writes the identity table and the weights
+// phi_k = sum_q W_kq phi*_q that spline_apply_kernel applies: with knots x_i = alpha*_{a+i} (n = b - a
+// segments of lengths h_i), the second derivatives m = P y solve the tridiagonal system
+// h_{i-1} m_{i-1} + 2 (h_{i-1} + h_i) m_i + h_i m_{i+1} = 6 ((y_{i+1} - y_i) / h_i - (y_i - y_{i-1}) / h_{i-1})
+// (m_0 = m_n = 0; P column by column, one thread each, by forward elimination and back substitution),
+// and on segment [x_j, x_{j+1}] the spline is A y_j + B y_{j+1} + C m_j + D m_{j+1} with
+// A = (x_{j+1} - x) / h_j, B = 1 - A, C = h_j^2 (A^3 - A) / 6, D = h_j^2 (B^3 - B) / 6.  A part with a
+// zero-length segment takes the linear rows instead; images that keep their place get identity rows.
+template <typename T>
+__device__ __noinline__ void arc_finish_variants(const GroupArgs<T>& g, const ArcArgs& a, int str, int K, int img0,
+                                                 int kc, const double* s) {
+    __shared__ double cp[kSplineMaxK], den[kSplineMaxK];
+    __shared__ int ok_part;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const bool split = kc > 0 && kc < K - 1;
+    const size_t mk = (size_t)a.maxK;
+    double* W = a.W + (size_t)str * mk * mk;
+    double* P = a.P + (size_t)str * mk * mk;
+    for (int k = tid; k < K; k += nthr) {
+        const int a0 = split && k > kc ? kc : 0, b0 = split && k < kc ? kc : K - 1;
+        const double L = s[b0] - s[a0];
+        const bool keep = !a.reparam || k == 0 || k == K - 1 || (split && k == kc) || !(L > 0.0) || !isfinite(L);
+        InterpEntry e;
+        e.src0 = e.src1 = img0 + k;
+        e.t = 0.0;
+        e.tf = 0.f;
+        e.omtf = 1.f;
+        e.copy = 1;
+        e.pad = 0;
+        if (!keep && !a.spline) {
+            const double ak = (double)(k - a0) / (double)(b0 - a0);
+            int j = a0;
+            for (int i = a0; i <= b0 - 1; ++i)
+                if ((s[i] - s[a0]) / L <= ak) j = i;
+            const double x0 = (s[j] - s[a0]) / L, x1 = (s[j + 1] - s[a0]) / L;
+            e.src0 = img0 + j;
+            e.src1 = img0 + j + 1;
+            e.t = (ak - x0) / (x1 - x0);
+            e.tf = (float)e.t;
+            e.omtf = (float)(1.0 - e.t);
+            e.copy = 0;
+        }
+        const_cast<InterpEntry*>(g.interp)[img0 + k] = e;
+        if (a.spline) {
+            // identity rows for now; the interior rows of a moving part are rewritten below
+            double* wr = W + (size_t)k * mk;
+            for (int q = 0; q < K; ++q) wr[q] = q == k ? 1.0 : 0.0;
+            a.wcopy[(size_t)str * mk + k] = keep ? 1 : 0;
+        }
+    }
+    if (!a.spline) return;
+    for (int part = 0; part < (split ? 2 : 1); ++part) {
+        const int a0 = part == 0 ? 0 : kc, b0 = part == 0 && split ? kc : K - 1, n = b0 - a0;
+        const double L = s[b0] - s[a0];
+        __syncthreads();  // identity rows written; cp, den, ok_part free
+        if (!a.reparam || !(L > 0.0) || !isfinite(L) || n < 2) continue;  // uniform: nothing moves here
+        if (tid == 0) {
+            int ok = 1;
+            for (int i = 0; i < n; ++i)
+                if (!((s[a0 + i + 1] - s[a0]) / L > (s[a0 + i] - s[a0]) / L)) ok = 0;
+            for (int i = 1; ok && i < n; ++i) {
+                const double hl = (s[a0 + i] - s[a0]) / L - (s[a0 + i - 1] - s[a0]) / L;
+                const double hr = (s[a0 + i + 1] - s[a0]) / L - (s[a0 + i] - s[a0]) / L;
+                const double lo = i > 1 ? hl : 0.0;
+                den[i] = 2.0 * (hl + hr) - lo * (i > 1 ? cp[i - 1] : 0.0);
+                cp[i] = (i < n - 1 ? hr : 0.0) / den[i];
+            }
+            ok_part = ok;
+        }
+        __syncthreads();
+        const int ok = ok_part;
+        if (ok) {
+            for (int q = tid; q <= n; q += nthr) {  // column q of P: d m_i / d y_q, i = 1..n-1
+                double* pc = P + (size_t)(a0 + q) * mk;
+                double d = 0.0;
+                for (int i = 1; i < n; ++i) {
+                    const double hl = (s[a0 + i] - s[a0]) / L - (s[a0 + i - 1] - s[a0]) / L;
+                    const double hr = (s[a0 + i + 1] - s[a0]) / L - (s[a0 + i] - s[a0]) / L;
+                    double r = 0.0;
+                    if (q == i + 1) r = 6.0 / hr;
+                    if (q == i) r = -6.0 / hr - 6.0 / hl;
+                    if (q == i - 1) r = 6.0 / hl;
+                    d = (r - (i > 1 ? hl : 0.0) * d) / den[i];
+                    pc[i] = d;
+                }
+                for (int i = n - 2; i >= 1; --i) pc[i] -= cp[i] * pc[i + 1];
+            }
+            __syncthreads();
+        }
+        for (int k = a0 + 1 + tid; k < b0; k += nthr) {
+            const double ak = (double)(k - a0) / (double)n;
+            int j = a0;
+            for (int i = a0; i <= b0 - 1; ++i)
+                if ((s[i] - s[a0]) / L <= ak) j = i;
+            const double x0 = (s[j] - s[a0]) / L, x1 = (s[j + 1] - s[a0]) / L, h = x1 - x0;
+            double* wr = W + (size_t)k * mk;
+            wr[k] = 0.0;
+            if (!ok) {
+                const double t = (ak - x0) / h;
+                wr[j] = 1.0 - t;
+                wr[j + 1] = t;
+                continue;
+            }
+            const double A = (x1 - ak) / h, B = (ak - x0) / h;
+            const double C = h * h * (A * A * A - A) / 6.0, D = h * h * (B * B * B - B) / 6.0;
+            const int jr = j - a0;
+            for (int q = 0; q <= n; ++q) {
+                const double* pc = P + (size_t)(a0 + q) * mk;
+                const double mj = jr > 0 ? pc[jr] : 0.0, mj1 = jr + 1 < n ? pc[jr + 1] : 0.0;
+                wr[a0 + q] = (q == jr ? A : 0.0) + (q == jr + 1 ? B : 0.0) + C * mj + D * mj1;
+            }
+        }
+    }
+}
+
+template <typename T>
 __global__ void __launch_bounds__(256, 3) arc_kernel(GroupArgs<T> g, ArcArgs a) {
     __shared__ double red[32 * kArcMaxChunk];
     __shared__ double alpha[kArcMaxK];  // d_k, then s_k, then alpha*_k
@@ -960,6 +1091,13 @@ __global__ void __launch_bounds__(256, 3) arc_kernel(GroupArgs<T> g, ArcArgs a) 
                 a.e_last[sb + k] = e;
             }
         }
+        if (!a.climb) return;
+        // climbing image: the finisher picks the next one from these energies, so they count too
+        __syncthreads();
+        if (tid == 0) s_flag = ticket_acq_rel(&a.cnt[str]) == (unsigned)((n_tiles + 1) * n_act - 1);
+        __syncthreads();
+        if (!s_flag) return;
+        arc_finish(g, a, str, K, img0, alpha, wsum);
         return;
     }
     const size_t M = (size_t)3 * g.N;
@@ -1020,10 +1158,21 @@ __global__ void __launch_bounds__(256, 3) arc_kernel(GroupArgs<T> g, ArcArgs a) 
         v += __shfl_down_sync(0xffffffffu, v, 1);
         if (q == 0 && i < nd) a.dpart[((size_t)str * a.maxK + k_lo + i + 1) * n_tiles + blockIdx.x] = v;
         __syncwarp();
-        if (lane == 0) s_flag = ticket_acq_rel(&a.cnt[str]) == (unsigned)(n_tiles * n_act - 1);
+        if (lane == 0)
+            s_flag = ticket_acq_rel(&a.cnt[str]) == (unsigned)((n_tiles + (a.climb ? 1 : 0)) * n_act - 1);
     }
     __syncthreads();
     if (!s_flag) return;
+    arc_finish(g, a, str, K, img0, alpha, wsum);
+}
+
+// The last CTA of a string (every partial it needs is visible after its ticket): distances, arc
+// length, and the reparametrisation of the variant in use.
+template <typename T>
+__device__ __noinline__ void arc_finish(const GroupArgs<T>& g, const ArcArgs& a, int str, int K, int img0,
+                                        double* alpha, double* wsum) {
+    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
+    const int n_tiles = a.n_tiles;
     // ---- last tile CTA of the string: d_k for k = 1..K-1 ----
     // 8 lanes per difference (lane = 8 j + l, four differences per warp), lane l summing tiles l, l + 8,
     // ... in order (loads twelve at a time), then a three-level tree over l: few FP64 instructions, as
@@ -1113,47 +1262,82 @@ __global__ void __launch_bounds__(256, 3) arc_kernel(GroupArgs<T> g, ArcArgs a) 
         }
     }
     __syncthreads();
-    const double sK = alpha[K - 1];
-    const bool move = a.reparam && sK > 0.0 && isfinite(sK);
-    if (move && warp < nw) {
-        const double r = rcp_nr(sK);
+    const int kcur = a.climb ? a.kc[str] : -1;  // the image that climbed in this iteration
+    if (a.spline || (kcur > 0 && kcur < K - 1)) {
+        arc_finish_variants(g, a, str, K, img0, kcur, alpha);
+    } else {
+        const double sK = alpha[K - 1];
+        const bool move = a.reparam && sK > 0.0 && isfinite(sK);
+        if (move && warp < nw) {
+            const double r = rcp_nr(sK);
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (q < per && kb + q < K) alpha[kb + q] *= r;  // alpha*_k = s_k / s_{K-1} (Eq. 12)
-    }
-    __syncthreads();
-    if (warp < nw) {
+            for (int q = 0; q < 4; ++q)
+                if (q < per && kb + q < K) alpha[kb + q] *= r;  // alpha*_k = s_k / s_{K-1} (Eq. 12)
+        }
+        __syncthreads();
+        if (warp < nw) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int k = kb + q;
-            if (q >= per || k >= K) continue;
-            InterpEntry e;
-            e.src0 = img0 + k;
-            e.src1 = img0 + k;
-            e.t = 0.0;
-            e.tf = 0.f;
-            e.omtf = 1.f;
-            e.copy = 1;
-            e.pad = 0;
-            if (move && k > 0 && k < K - 1) {
-                const double ak = (double)k / (double)(K - 1);
-                // largest j in [0, K-2] with alpha*_j <= ak (alpha* is non-decreasing; alpha*_0 = 0 <= ak),
-                // walking from j = k: after a few iterations the images are nearly evenly spaced
-                int j = min(k, K - 2);
-                if (alpha[j] <= ak) {
-                    while (j < K - 2 && alpha[j + 1] <= ak) ++j;
-                } else {
-                    do --j;
-                    while (alpha[j] > ak);
+            for (int q = 0; q < 4; ++q) {
+                const int k = kb + q;
+                if (q >= per || k >= K) continue;
+                InterpEntry e;
+                e.src0 = img0 + k;
+                e.src1 = img0 + k;
+                e.t = 0.0;
+                e.tf = 0.f;
+                e.omtf = 1.f;
+                e.copy = 1;
+                e.pad = 0;
+                if (move && k > 0 && k < K - 1) {
+                    const double ak = (double)k / (double)(K - 1);
+                    // largest j in [0, K-2] with alpha*_j <= ak (alpha* is non-decreasing; alpha*_0 = 0 <= ak),
+                    // walking from j = k: after a few iterations the images are nearly evenly spaced
+                    int j = min(k, K - 2);
+                    if (alpha[j] <= ak) {
+                        while (j < K - 2 && alpha[j + 1] <= ak) ++j;
+                    } else {
+                        do --j;
+                        while (alpha[j] > ak);
+                    }
+                    e.src0 = img0 + j;
+                    e.src1 = img0 + j + 1;
+                    e.t = (ak - alpha[j]) * rcp_nr(alpha[j + 1] - alpha[j]);
+                    e.tf = (float)e.t;
+                    e.omtf = (float)(1.0 - e.t);
+                    e.copy = 0;
                 }
-                e.src0 = img0 + j;
-                e.src1 = img0 + j + 1;
-                e.t = (ak - alpha[j]) * rcp_nr(alpha[j + 1] - alpha[j]);
-                e.tf = (float)e.t;
-                e.omtf = (float)(1.0 - e.t);
-                e.copy = 0;
+                const_cast<InterpEntry*>(g.interp)[img0 + k] = e;
             }
-            const_cast<InterpEntry*>(g.interp)[img0 + k] = e;
+        }
+    }
+    if (a.climb) {
+        // the next climbing image: the interior maximum of the energies of the states this iteration
+        // started from (lowest index on ties); flags for the next x-inverse launch
+        __syncthreads();  // every thread has read a.kc[str]
+        if (warp == 0) {
+            const double* el = a.e_last + (size_t)str * a.maxK;
+            double best = -INFINITY;
+            int kbest = K;
+            for (int k = 1 + lane; k < K - 1; k += 32) {
+                const double e = __ldcg(el + k);
+                if (e > best) {  // strictly greater: the lane keeps its lowest index
+                    best = e;
+                    kbest = k;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ob = __shfl_down_sync(0xffffffffu, best, o);
+                const int ok = __shfl_down_sync(0xffffffffu, kbest, o);
+                if (ob > best || (ob == best && ok < kbest)) {
+                    best = ob;
+                    kbest = ok;
+                }
+            }
+            kbest = __shfl_sync(0xffffffffu, kbest, 0);
+            const int kn = K >= 3 && kbest < K - 1 ? kbest : -1;
+            if (lane == 0) a.kc[str] = kn;
+            for (int k = lane; k < K; k += 32) a.climb_img[img0 + k] = k == kn;
         }
     }
 }
@@ -1321,6 +1505,120 @@ __global__ void __launch_bounds__(256) rk_commit_kernel(GroupArgs<T> g, RkArgs<T
     for (int c = 0; c < 3; ++c) {
         r.y0[base + (size_t)c * N] = v[c] * nr;
         if (S.done) g.sp[base + (size_t)c * N] = v[c] * nr;
+    }
+}
+
+// ---- climbing image (Euler step) ------------------------------------------------------------------
+// The image kc that climbs this iteration stepped neither in the x-inverse kernel (MODE 3 wrote its force
+// F = h - (s.h) s into hc); its step reverses F's component along the string's tangent:
+//   tau_i = (s_{kc+1,i} - s_{kc-1,i}) - ((s_{kc+1,i} - s_{kc-1,i}) . s_i) s_i   (states before the step)
+//   s_i' = normalise(s_i + dt (F_i - 2 (F.tau) / (tau.tau) tau_i))
+// climb_dot: grid (c_tiles, n_str), 256 threads: FP64 partials of F.tau and tau.tau per tile of
+// kClimbTile sites.  climb_apply: the same grid; every CTA sums its string's partials in one fixed order
+// and steps its sites into sp.  Strings with no climbing image return at once.
+template <typename T>
+__device__ __forceinline__ void climb_site(const GroupArgs<T>& g, const T* hc, int img, int i, T (&s0)[3], T (&F)[3],
+                                           T (&tau)[3]) {
+    const size_t M = (size_t)3 * g.N;
+    const T* sb = g.s + (size_t)img * M + i;
+    const T* fb = hc + (size_t)img * M + i;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        s0[c] = sb[(size_t)c * g.N];
+        F[c] = fb[(size_t)c * g.N];
+        tau[c] = sb[M + (size_t)c * g.N] - sb[(size_t)c * g.N - M];
+    }
+    const T ts = tau[0] * s0[0] + tau[1] * s0[1] + tau[2] * s0[2];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) tau[c] -= ts * s0[c];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) climb_dot_kernel(GroupArgs<T> g, ArcArgs a, const T* hc) {
+    __shared__ double red[64];
+    const int str = blockIdx.y, K = a.str_K[str], kc = a.kc[str];
+    if (!(kc > 0 && kc < K - 1)) return;  // uniform over the CTA
+    const int img = a.str_img0[str] + kc;
+    T v[2] = {T(0), T(0)};
+    const int i1 = min(g.N, (int)(blockIdx.x + 1) * kClimbTile);
+    for (int i = blockIdx.x * kClimbTile + threadIdx.x; i < i1; i += blockDim.x) {
+        T s0[3], F[3], tau[3];
+        climb_site(g, hc, img, i, s0, F, tau);
+        v[0] += F[0] * tau[0] + F[1] * tau[1] + F[2] * tau[2];
+        v[1] += tau[0] * tau[0] + tau[1] * tau[1] + tau[2] * tau[2];
+    }
+    double out[2];
+    block_reduce_t2d<2>(v, out, red);
+    if (threadIdx.x == 0) {
+        double* cp = a.cpart + ((size_t)str * a.c_tiles + blockIdx.x) * 2;
+        cp[0] = out[0];
+        cp[1] = out[1];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) climb_apply_kernel(GroupArgs<T> g, ArcArgs a, const T* hc, T dt) {
+    __shared__ double coef;
+    const int str = blockIdx.y, K = a.str_K[str], kc = a.kc[str];
+    if (!(kc > 0 && kc < K - 1)) return;  // uniform over the CTA
+    const int img = a.str_img0[str] + kc;
+    if (threadIdx.x < 32) {
+        const double* cp = a.cpart + (size_t)str * a.c_tiles * 2;
+        double ft = 0.0, tt = 0.0;
+        for (int t = threadIdx.x; t < a.c_tiles; t += 32) {
+            ft += cp[2 * t];
+            tt += cp[2 * t + 1];
+        }
+        ft = warp_sum_d(ft);
+        tt = warp_sum_d(tt);
+        if (threadIdx.x == 0) coef = tt > 0.0 ? ft / tt : 0.0;
+    }
+    __syncthreads();
+    const T c2 = T(2.0 * coef);
+    const int N = g.N;
+    const int i1 = min(N, (int)(blockIdx.x + 1) * kClimbTile);
+    for (int i = blockIdx.x * kClimbTile + threadIdx.x; i < i1; i += blockDim.x) {
+        T s0[3], F[3], tau[3], u[3];
+        climb_site(g, hc, img, i, s0, F, tau);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) u[c] = s0[c] + dt * (F[c] - c2 * tau[c]);
+        const T r = rsqrt_t<T>(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        T* o = g.sp + (size_t)img * 3 * N + i;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) o[(size_t)c * N] = u[c] * r;
+    }
+}
+
+// ---- natural cubic spline: phi_k = normalise(sum_q W_kq phi*_q) in place on sp -----------------------
+// grid (ceil(N / ts), n_str), ts threads, one site each; dynamic shared memory [K][3][ts] holds the
+// string's K images at the CTA's sites (each thread reads only its own column, so nothing waits).
+template <typename T>
+__global__ void __launch_bounds__(128) spline_apply_kernel(GroupArgs<T> g, ArcArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* y = reinterpret_cast<T*>(smem_raw);
+    const int str = blockIdx.y, ts = blockDim.x, tid = threadIdx.x;
+    const int K = a.str_K[str], img0 = a.str_img0[str], N = g.N;
+    const int i = blockIdx.x * ts + tid;
+    if (i >= N) return;
+    const size_t M = (size_t)3 * N, mk = (size_t)a.maxK;
+    const int* wc = a.wcopy + (size_t)str * mk;
+    const double* W = a.W + (size_t)str * mk * mk;
+    for (int q = 0; q < K; ++q)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) y[(q * 3 + c) * ts + tid] = g.sp[(size_t)(img0 + q) * M + (size_t)c * N + i];
+    for (int k = 1; k < K - 1; ++k) {
+        if (wc[k]) continue;  // kept in place (uniform over the CTA)
+        const double* wr = W + (size_t)k * mk;
+        T u[3] = {T(0), T(0), T(0)};
+        for (int q = 0; q < K; ++q) {
+            const T w = T(__ldg(wr + q));
+#pragma unroll
+            for (int c = 0; c < 3; ++c) u[c] += w * y[(q * 3 + c) * ts + tid];
+        }
+        const T r = rsqrt_t<T>(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        T* o = g.sp + (size_t)(img0 + k) * M + i;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) o[(size_t)c * N] = u[c] * r;
     }
 }
 
@@ -1604,6 +1902,45 @@ void launch_xinv_force(const GroupArgs<T>& g, bool do_fft, T* kout, bool energie
         xinv_kernel<T, false, 2, 0><<<grid, nthr, smem, st>>>(g, flag, kout);
 }
 
+template <typename T>
+void launch_xinv_step_climb(const GroupArgs<T>& g, bool do_fft, T dt, T* hc, int nthr, size_t smem, cudaStream_t st) {
+    dim3 grid((g.ny + g.ty_c - 1) / g.ty_c, g.nz, g.n_pairs);
+    if constexpr (std::is_same<T, float>::value) {
+        if (do_fft && f128_x(4, g.Px)) {
+            const dim3 blk(f128_x_threads(g.ty_c));
+            const size_t sm = f128_x_smem(g.ty_c);
+            if (g.ty_c == 2) launch_pdl(xinv128_kernel<T, 3, 2>, grid, blk, sm, st, g, dt, hc);
+            else if (g.ty_c == 4) launch_pdl(xinv128_kernel<T, 3, 4>, grid, blk, sm, st, g, dt, hc);
+            else launch_pdl(xinv128_kernel<T, 3, 8>, grid, blk, sm, st, g, dt, hc);
+            return;
+        }
+    }
+    if (do_fft)
+        launch_pdl(xinv_kernel<T, true, 3, 0>, grid, dim3(nthr), smem, st, g, dt, hc);
+    else
+        launch_pdl(xinv_kernel<T, false, 3, 0>, grid, dim3(nthr), smem, st, g, dt, hc);
+}
+
+template <typename T> void launch_climb(const GroupArgs<T>& g, const ArcArgs& a, T dt, const T* hc, cudaStream_t st) {
+    const dim3 grid(a.c_tiles, a.n_str);
+    climb_dot_kernel<T><<<grid, 256, 0, st>>>(g, a, hc);
+    climb_apply_kernel<T><<<grid, 256, 0, st>>>(g, a, hc, dt);
+}
+
+// sites per CTA of the spline apply kernel for strings of up to maxK images: the [maxK][3][ts] tile in
+// at most 200 KB of shared memory, ts a power of two in [32, 128]
+template <typename T> int spline_sites_per_cta(int maxK) {
+    int ts = 128;
+    while (ts > 32 && (size_t)maxK * 3 * ts * sizeof(T) > 200 * 1024) ts >>= 1;
+    return ts;
+}
+
+template <typename T> void launch_spline_apply(const GroupArgs<T>& g, const ArcArgs& a, int maxK, cudaStream_t st) {
+    const int ts = spline_sites_per_cta<T>(maxK);
+    const size_t sm = (size_t)maxK * 3 * ts * sizeof(T);
+    spline_apply_kernel<T><<<dim3((g.N + ts - 1) / ts, a.n_str), ts, sm, st>>>(g, a);
+}
+
 template <typename T> void launch_rk_assemble(const GroupArgs<T>& g, const RkArgs<T>& r, int stage, cudaStream_t st) {
     const dim3 grid(r.n_tiles, g.n_img);
     switch (stage) {
@@ -1672,12 +2009,16 @@ template <typename T> void set_smem_limits(int bytes) {
     set_dyn_smem(xinv_kernel<T, false, 1, 0>, bytes);
     set_dyn_smem(xinv_kernel<T, true, 2, 0>, bytes);
     set_dyn_smem(xinv_kernel<T, false, 2, 0>, bytes);
+    set_dyn_smem(xinv_kernel<T, true, 3, 0>, bytes);
+    set_dyn_smem(xinv_kernel<T, false, 3, 0>, bytes);
+    set_dyn_smem(spline_apply_kernel<T>, 200 * 1024);
     if constexpr (std::is_same<T, float>::value) {
 #define SS_CASE(R)                                  \
     set_dyn_smem(xfwd128_kernel<T, R>, bytes);      \
     set_dyn_smem(xinv128_kernel<T, 0, R>, bytes);   \
     set_dyn_smem(xinv128_kernel<T, 1, R>, bytes);   \
-    set_dyn_smem(xinv128_kernel<T, 2, R>, bytes);
+    set_dyn_smem(xinv128_kernel<T, 2, R>, bytes);   \
+    set_dyn_smem(xinv128_kernel<T, 3, R>, bytes);
         SS_CASE(2) SS_CASE(4) SS_CASE(8)
 #undef SS_CASE
         set_dyn_smem(yz128_kernel<T, 4>, bytes);
@@ -1722,6 +2063,9 @@ void launch_interp_identity(InterpEntry* tab, int img0, int K, cudaStream_t st) 
     template void launch_xinv_step<T>(const GroupArgs<T>&, bool, T, int, size_t, cudaStream_t);                \
     template void launch_xinv_eval<T>(const GroupArgs<T>&, bool, T*, int, size_t, cudaStream_t);               \
     template void launch_xinv_force<T>(const GroupArgs<T>&, bool, T*, bool, int, size_t, cudaStream_t);        \
+    template void launch_xinv_step_climb<T>(const GroupArgs<T>&, bool, T, T*, int, size_t, cudaStream_t);       \
+    template void launch_climb<T>(const GroupArgs<T>&, const ArcArgs&, T, const T*, cudaStream_t);             \
+    template void launch_spline_apply<T>(const GroupArgs<T>&, const ArcArgs&, int, cudaStream_t);              \
     template void launch_rk_assemble<T>(const GroupArgs<T>&, const RkArgs<T>&, int, cudaStream_t);             \
     template void launch_rk_finish<T>(const GroupArgs<T>&, const RkArgs<T>&, cudaStream_t);                    \
     template void launch_rk_control<T>(const GroupArgs<T>&, const RkArgs<T>&, int, cudaStream_t);                \
