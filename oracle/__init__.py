@@ -69,6 +69,8 @@ def _load():
             "or_reparam_v": (None, [i, i, dp, dp, i, i, dp]),
             "or_string_run_v": (i, [mp, i, i, d, i, i, dp, dp, P(ctypes.c_int)]),
             "or_string_run_rk": (i, [mp, i, i, d, d, d, i, dp, dp, dp, P(ctypes.c_long)]),
+            "or_llg_run": (i, [mp, i, i, d, d, dp, dp]),
+            "or_llg_run_rk": (i, [mp, i, i, d, d, d, d, i, dp, dp, dp, P(ctypes.c_long)]),
             "or_dp_tableau": (None, [dp, dp, dp]),
             "or_barrier": (d, [i, dp, P(i)]),
             "or_energy_param_grad": (None, [mp, dp, dp]),
@@ -235,6 +237,40 @@ def string_run_rk(m: OracleModel, path, n_iter: int, T: float, rtol: float = 1e-
         raise MemoryError("oracle RK string run: out of memory")
     if rc != 0:
         raise RuntimeError("oracle RK string run: step size collapsed")
+    c = np.array(counts[:], dtype=np.int64).reshape(n_sys, 2)
+    if per_image:
+        return phi, e, h, c
+    return phi, e, float(h[0]), (int(c[0, 0]), int(c[0, 1]))
+
+
+def llg_run(m: OracleModel, states, n_steps: int, dt: float, alpha: float, with_energies: bool = True):
+    """Eq. 9 (reduced units) by explicit Euler steps with renormalisation, every image on its own.
+    Returns (final states, energies or None)."""
+    phi = _f64(states).copy()
+    K = phi.shape[0]
+    e = np.zeros(K) if with_energies else None
+    if _load().or_llg_run(ctypes.byref(m), K, int(n_steps), float(dt), float(alpha), _ptr(phi),
+                          _ptr(e) if with_energies else None) != 0:
+        raise MemoryError("oracle LLG run: out of memory")
+    return phi, e
+
+
+def llg_run_rk(m: OracleModel, states, n_iter: int, T: float, alpha: float, rtol: float = 1e-6, atol: float = 1e-8,
+               step=None, with_energies: bool = True, per_image: bool = False):
+    """Eq. 9 (reduced units) with the Dormand-Prince 5(4) pair over n_iter intervals of T, no
+    reparametrisation.  Returns as string_run_rk."""
+    phi = _f64(states).copy()
+    K = phi.shape[0]
+    n_sys = K if per_image else 1
+    e = np.zeros(K) if with_energies else None
+    h = np.full(n_sys, float(T)) if step is None else np.array(np.broadcast_to(np.asarray(step, float), (n_sys,)))
+    counts = (ctypes.c_long * (2 * n_sys))()
+    rc = _load().or_llg_run_rk(ctypes.byref(m), K, int(n_iter), float(T), float(alpha), float(rtol), float(atol),
+                               int(bool(per_image)), _ptr(h), _ptr(phi), _ptr(e) if with_energies else None, counts)
+    if rc == -1:
+        raise MemoryError("oracle LLG run: out of memory")
+    if rc != 0:
+        raise RuntimeError("oracle LLG run: step size collapsed")
     c = np.array(counts[:], dtype=np.int64).reshape(n_sys, 2)
     if per_image:
         return phi, e, h, c

@@ -549,8 +549,11 @@ void or_dp_tableau(double a[7][6], double b[7], double bhat[7]) {
     memcpy(bhat, DP_BHAT, sizeof(DP_BHAT));
 }
 
-/* F of Eq. 13 for every image of y (K images of M = 3N components) into f. */
-static void force_all(const or_model* m, const double* table, int K, const double* y, double* hbuf, double* f) {
+/* The right-hand side for every image of y (K images of M = 3N components) into f: F of Eq. 13 when
+ * llg is NULL, else the reduced LLG of Eq. 9, f = -a (s x h) + b (h - (s.h) s) with a = llg[0] =
+ * 1 / (1 + alpha^2) and b = llg[1] = alpha / (1 + alpha^2) (-s x (s x h) = h - (s.h) s). */
+static void force_all(const or_model* m, const double* table, int K, const double* y, double* hbuf, double* f,
+                      const double* llg) {
     const int N = m->nx * m->ny * m->nz;
     const size_t M = (size_t)3 * N;
 #pragma omp parallel for schedule(dynamic, 1)
@@ -562,16 +565,23 @@ static void force_all(const or_model* m, const double* table, int K, const doubl
             const double* si = yk + 3 * i;
             const double* hi = hk + 3 * i;
             const double sh = si[0] * hi[0] + si[1] * hi[1] + si[2] * hi[2];
-            for (int c = 0; c < 3; ++c) f[k * M + 3 * i + c] = hi[c] - sh * si[c];
+            double* fi = f + k * M + 3 * i;
+            if (!llg) {
+                for (int c = 0; c < 3; ++c) fi[c] = hi[c] - sh * si[c];
+            } else {
+                const double sxh[3] = {si[1] * hi[2] - si[2] * hi[1], si[2] * hi[0] - si[0] * hi[2],
+                                       si[0] * hi[1] - si[1] * hi[0]};
+                for (int c = 0; c < 3; ++c) fi[c] = -llg[0] * sxh[c] + llg[1] * (hi[c] - sh * si[c]);
+            }
         }
     }
 }
 
 /* One interval [0, T] of the system of Ks images at phi (Ks * 3N components), DP 5(4) as above;
  * kk (7 systems), ys, y5 and hb are scratch of the system's size. */
-static int rk_interval(const or_model* m, const double* table, int Ks, double T, double rtol, double atol,
-                       double* step_io, double* phi, double* kk, double* ys, double* y5, double* hb, long* acc,
-                       long* rej) {
+static int rk_interval(const or_model* m, const double* table, const double* llg, int Ks, double T, double rtol,
+                       double atol, double* step_io, double* phi, double* kk, double* ys, double* y5, double* hb,
+                       long* acc, long* rej) {
     const int N = m->nx * m->ny * m->nz;
     const size_t M = (size_t)3 * N, L = M * (size_t)Ks;
     double step = *step_io, t = 0.0;
@@ -579,7 +589,7 @@ static int rk_interval(const or_model* m, const double* table, int Ks, double T,
     while (t < T) {
         if (++attempts > 100000) return -2;
         const double hs = step < T - t ? step : T - t;
-        if (!have_k1) force_all(m, table, Ks, phi, hb, kk);
+        if (!have_k1) force_all(m, table, Ks, phi, hb, kk, llg);
         have_k1 = 1;
         for (int st = 1; st < 7; ++st) {
             for (size_t j = 0; j < L; ++j) {
@@ -587,7 +597,7 @@ static int rk_interval(const or_model* m, const double* table, int Ks, double T,
                 for (int q = 0; q < st; ++q) a += DP_A[st][q] * kk[q * L + j];
                 ys[j] = phi[j] + hs * a;
             }
-            force_all(m, table, Ks, ys, hb, kk + st * L);
+            force_all(m, table, Ks, ys, hb, kk + st * L, llg);
         }
         double e2 = 0.0;
         for (size_t j = 0; j < L; ++j) {
@@ -627,8 +637,10 @@ static int rk_interval(const or_model* m, const double* table, int Ks, double T,
     return 0;
 }
 
-int or_string_run_rk(const or_model* m, int K, int n_iter, double T, double rtol, double atol, int per_image,
-                     double* step_io, double* phi, double* energies, long* counts) {
+/* The Runge-Kutta driver: n_iter intervals of T of the right-hand side chosen by llg (see force_all),
+ * each followed by the reparametrisation when reparam != 0. */
+static int run_rk(const or_model* m, int K, int n_iter, double T, double rtol, double atol, int per_image,
+                  const double* llg, int reparam, double* step_io, double* phi, double* energies, long* counts) {
     const int N = m->nx * m->ny * m->nz;
     const size_t M = (size_t)3 * N, L = M * (size_t)K;
     const int n_sys = per_image ? K : 1, Ks = per_image ? 1 : K;
@@ -655,11 +667,13 @@ int or_string_run_rk(const or_model* m, int K, int n_iter, double T, double rtol
     int rc = 0;
     for (int it = 0; it < n_iter && rc == 0; ++it) {
         for (int q = 0; q < n_sys && rc == 0; ++q)
-            rc = rk_interval(m, table, Ks, T, rtol, atol, step_io + q, phi + q * Ls, kk, ys, y5, hb, &cnt[2 * q],
+            rc = rk_interval(m, table, llg, Ks, T, rtol, atol, step_io + q, phi + q * Ls, kk, ys, y5, hb, &cnt[2 * q],
                              &cnt[2 * q + 1]);
         if (rc) break;
-        memcpy(ys, phi, sizeof(double) * L);
-        or_reparam(K, N, ys, phi, NULL);
+        if (reparam) {
+            memcpy(ys, phi, sizeof(double) * L);
+            or_reparam(K, N, ys, phi, NULL);
+        }
     }
     if (counts) memcpy(counts, cnt, sizeof(long) * 2 * n_sys);
     if (rc == 0 && energies) {
@@ -676,6 +690,62 @@ int or_string_run_rk(const or_model* m, int K, int n_iter, double T, double rtol
     free(hb);
     free(cnt);
     return rc;
+}
+
+int or_string_run_rk(const or_model* m, int K, int n_iter, double T, double rtol, double atol, int per_image,
+                     double* step_io, double* phi, double* energies, long* counts) {
+    return run_rk(m, K, n_iter, T, rtol, atol, per_image, NULL, 1, step_io, phi, energies, counts);
+}
+
+/* ---- precessional dynamics (Eq. 9) ------------------------------------------------------------------
+ * In reduced units (h in units of J, time in units of mu0 |S| / (gamma J)) Eq. 9 reads
+ *     ds/dtau = -1/(1 + alpha^2) s x h - alpha/(1 + alpha^2) s x (s x h),
+ * every image an independent system and no reparametrisation.  or_llg_run: n_steps explicit Euler
+ * steps s <- normalise(s + dt f(s)).  or_llg_run_rk: n_iter intervals of T with the Dormand-Prince pair
+ * and the controller of or_string_run_rk.  energies (optional): Eq. 8 of the final states. */
+int or_llg_run(const or_model* m, int K, int n_steps, double dt, double alpha, double* phi, double* energies) {
+    const int N = m->nx * m->ny * m->nz;
+    const size_t M = (size_t)3 * N, L = M * (size_t)K;
+    const double llg[2] = {1.0 / (1.0 + alpha * alpha), alpha / (1.0 + alpha * alpha)};
+    double* table = NULL;
+    if (m->w != 0.0) {
+        table = dipole_table(m);
+        if (!table) return -1;
+    }
+    double* hb = (double*)malloc(sizeof(double) * L);
+    double* f = (double*)malloc(sizeof(double) * L);
+    if (!hb || !f) {
+        free(table);
+        free(hb);
+        free(f);
+        return -1;
+    }
+    for (int it = 0; it < n_steps; ++it) {
+        force_all(m, table, K, phi, hb, f, llg);
+        for (size_t i = 0; i < L / 3; ++i) {
+            double u[3];
+            for (int c = 0; c < 3; ++c) u[c] = phi[3 * i + c] + dt * f[3 * i + c];
+            const double nr = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+            for (int c = 0; c < 3; ++c) phi[3 * i + c] = u[c] / nr;
+        }
+    }
+    if (energies) {
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int k = 0; k < K; ++k) {
+            field_one(m, table, phi + k * M, hb + k * M);
+            energies[k] = or_energy_from_field(N, phi + k * M, hb + k * M);
+        }
+    }
+    free(table);
+    free(hb);
+    free(f);
+    return 0;
+}
+
+int or_llg_run_rk(const or_model* m, int K, int n_iter, double T, double alpha, double rtol, double atol,
+                  int per_image, double* step_io, double* phi, double* energies, long* counts) {
+    const double llg[2] = {1.0 / (1.0 + alpha * alpha), alpha / (1.0 + alpha * alpha)};
+    return run_rk(m, K, n_iter, T, rtol, atol, per_image, llg, 0, step_io, phi, energies, counts);
 }
 
 /* Sec. III: the barrier is the energy of the highest image relative to the first image.  Ties go
