@@ -325,6 +325,7 @@ def main():
         line["other_workloads"] = {w.name: other_workload(binding, w, stream) for w in
                                    (workloads.boundary_sweep(), workloads.uneven_study(),
                                     workloads.paper_monolayer_workload(), workloads.paper_phase_diagram())}
+        line["reparam_variants"] = reparam_variants(binding, wl, stream, plain_ms=step_s * 1e3 / n_iter)
         line["adaptive_rk"] = {name: adaptive_rk(binding, wl, stream, kind, per_iter_euler_ms=step_s * 1e3 / n_iter)
                                for name, kind in (("dopri5_per_string", binding.SS_INT_DOPRI5),
                                                   ("dopri5_per_image", binding.SS_INT_DOPRI5_IMAGE))}
@@ -337,6 +338,36 @@ def main():
     print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
+
+
+def reparam_variants(binding, wl, stream, plain_ms, iters=128, warm=64):
+    """Device-timed Euler iterations of the bench workload under the reparametrisation variants
+    (natural cubic spline, climbing image, both), graph-replayed like the headline, inputs resident."""
+    import torch
+    spec = wl.strings[0]
+    desc = (spec.nx, spec.ny, spec.nz, spec.J, spec.D, spec.K, spec.w, spec.n_images)
+    out = {}
+    for name, interp, climb in (("spline", binding.SS_INTERP_SPLINE, False),
+                                ("climbing_image", binding.SS_INTERP_LINEAR, True),
+                                ("spline_and_climbing_image", binding.SS_INTERP_SPLINE, True)):
+        with binding.StringMethod([desc], dt=wl.dt, stream=stream.cuda_stream) as sm:
+            sm.set_reparam(interp, climb)
+            sm.set_path(0, torch.from_numpy(spec.initial_path().astype(np.float32)).cuda())
+            sm.step(warm)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            sm.step(iters)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1e3
+            kc = sm.climbing_image(0)
+            kpi = sm.kernels_per_iteration()
+        units = spec.n_sites * spec.n_images
+        out[name] = {"value": units * iters / t, "unit": "spin-updates/s", "iterations_timed": iters,
+                     "ms_per_iter": 1e3 * t / iters, "vs_plain_ms_per_iter": (1e3 * t / iters) / plain_ms,
+                     "kernels_per_iter": kpi, "climbing_image": kc}
+    return out
 
 
 def adaptive_rk(binding, wl, stream, kind, per_iter_euler_ms, iters=10, warm=2, rtol=1e-6, atol=1e-8):

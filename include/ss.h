@@ -218,6 +218,20 @@ ss_status ss_set_reparam(ss_ctx* ctx, int interp, int climb);
 /* The image of `string` that climbs in the next iteration, or -1 (none, or climbing off).  Synchronises. */
 ss_status ss_climbing_image(ss_ctx* ctx, int string, int* k);
 
+/* What ss_step integrates (Eq. 9). */
+enum { SS_DYN_STRING = 0, SS_DYN_LLG = 1 };
+
+/* Chooses the dynamics.  SS_DYN_STRING (the default): the string method of Sec. III (the damping force of
+ * Eq. 13, then the reparametrisation).  SS_DYN_LLG: the full precessional Landau-Lifshitz-Gilbert
+ * equation (Eq. 9) in reduced units (h in units of J, time in units of mu0 |S| / (gamma J)),
+ *     ds/dtau = -1/(1 + alpha^2) s x h - alpha/(1 + alpha^2) s x (s x h),
+ * for every image as an independent system with no reparametrisation: each ss_step iteration advances
+ * time by opts.dt, by one explicit Euler step with renormalisation (SS_INT_EULER) or by the
+ * Dormand-Prince evolution of ss_set_integrator; ss_step_energies reports the energies of the states
+ * each iteration started from.  alpha (the damping) must be finite and >= 0.  The climbing image is
+ * refused under SS_DYN_LLG (SS_ERR_STATE).  Takes effect at the next ss_step; no synchronisation. */
+ss_status ss_set_dynamics(ss_ctx* ctx, int kind, double alpha);
+
 /* Shape queries. */
 int ss_num_strings(const ss_ctx* ctx);
 ss_status ss_string_info(const ss_ctx* ctx, int string, ss_string_desc* out);

@@ -23,6 +23,7 @@ SS_PREC_FP32, SS_PREC_FP64 = 0, 1
 SS_DIPOLE_OFF, SS_DIPOLE_FFT = 0, 2
 SS_INT_EULER, SS_INT_DOPRI5, SS_INT_DOPRI5_IMAGE = 0, 1, 2
 SS_INTERP_LINEAR, SS_INTERP_SPLINE = 0, 1
+SS_DYN_STRING, SS_DYN_LLG = 0, 1
 _STATUS = {0: "SS_OK", 1: "SS_ERR_INVALID_ARG", 2: "SS_ERR_CUDA", 3: "SS_ERR_OOM", 4: "SS_ERR_NONFINITE",
            5: "SS_ERR_TIMEOUT", 6: "SS_ERR_STATE"}
 
@@ -59,6 +60,7 @@ _SIGNATURES = {
     "ss_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "ss_set_integrator": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double]),
     "ss_set_reparam": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "ss_set_dynamics": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]),
     "ss_climbing_image": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "ss_integrator_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
@@ -256,6 +258,10 @@ def ss_set_reparam(ctx, interp: int = SS_INTERP_LINEAR, climb: bool = False) -> 
     _check(_lib.ss_set_reparam(ctx, int(interp), int(bool(climb))), ctx)
 
 
+def ss_set_dynamics(ctx, kind: int = SS_DYN_STRING, alpha: float = 0.0) -> None:
+    _check(_lib.ss_set_dynamics(ctx, int(kind), float(alpha)), ctx)
+
+
 def ss_climbing_image(ctx, string: int) -> int:
     k = ctypes.c_int()
     _check(_lib.ss_climbing_image(ctx, int(string), ctypes.byref(k)), ctx)
@@ -408,6 +414,9 @@ class StringMethod:
 
     def climbing_image(self, string=0):
         return ss_climbing_image(self.ctx, string)
+
+    def set_dynamics(self, kind=SS_DYN_STRING, alpha=0.0):
+        ss_set_dynamics(self.ctx, kind, alpha)
 
     def energies(self, string=0):
         return ss_energies(self.ctx, string)

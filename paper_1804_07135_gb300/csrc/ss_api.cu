@@ -132,6 +132,8 @@ struct ss_ctx {
     int integrator = 0;  // SS_INT_EULER, SS_INT_DOPRI5 or SS_INT_DOPRI5_IMAGE
     int interp = 0;      // SS_INTERP_LINEAR or SS_INTERP_SPLINE
     int climb = 0;       // climbing image on
+    int dynamics = 0;    // SS_DYN_STRING or SS_DYN_LLG
+    double alpha = 0.0;  // damping of the precessional dynamics
     double rtol = 1e-6, atol = 1e-8;
     int* h_active = nullptr;  // pinned, one flag per size group
     std::string err;
@@ -211,6 +213,8 @@ template <typename T> GroupArgs<T> group_args(const ss_ctx* c, const Group& g) {
     a.ty_c = g.ty_c;
     a.err = c->d_err;
     a.climb_img = g.climb_img;
+    a.llg_a = T(1.0 / (1.0 + c->alpha * c->alpha));
+    a.llg_b = T(c->alpha / (1.0 + c->alpha * c->alpha));
     return a;
 }
 
@@ -589,8 +593,8 @@ template <typename T> ss_status rk_iterations(ss_ctx* c, int n_iter) {
                     launch_rk_assemble<T>(ai, r, st, c->cs);
                     launch_xfwd<T>(ai, g.dipole, g.thr_a, g.smem_a, c->cs);
                     if (g.dipole) launch_yz<T>(ai, g.thr_b, g.smem_b, c->cs);
-                    launch_xinv_force<T>(ai, g.dipole, r.k + st * stride, round == 0 && st == 0, g.thr_c, g.smem_c_eval,
-                                         c->cs);
+                    launch_xinv_force<T>(ai, g.dipole, r.k + st * stride, round == 0 && st == 0,
+                                         c->dynamics == SS_DYN_LLG, g.thr_c, g.smem_c_eval, c->cs);
                 }
                 launch_rk_finish<T>(ai, r, c->cs);
                 launch_rk_control<T>(ai, r, 0, c->cs);
@@ -620,7 +624,9 @@ template <typename T> void issue_iteration(ss_ctx* c, cudaStream_t st) {
         GroupArgs<T> a = group_args<T>(c, g);
         launch_xfwd<T>(a, g.dipole, g.thr_a, g.smem_a, st);
         if (g.dipole) launch_yz<T>(a, g.thr_b, g.smem_b, st);
-        if (c->climb) {
+        if (c->dynamics == SS_DYN_LLG) {
+            launch_xinv_step_llg<T>(a, g.dipole, dt, g.thr_c, g.smem_c, st);
+        } else if (c->climb) {
             launch_xinv_step_climb<T>(a, g.dipole, dt, (T*)g.hc, g.thr_c, g.smem_c, st);
             launch_climb<T>(a, g.arc, dt, (const T*)g.hc, st);
         } else {
@@ -959,6 +965,8 @@ ss_status ss_set_reparam(ss_ctx* c, int interp, int climb) {
     if (climb != 0 && climb != 1) return fail(c, SS_ERR_INVALID_ARG, "climb must be 0 or 1");
     if (climb && c->integrator != SS_INT_EULER)
         return fail(c, SS_ERR_STATE, "the climbing image is defined for the Euler step only");
+    if (climb && c->dynamics != SS_DYN_STRING)
+        return fail(c, SS_ERR_STATE, "the climbing image belongs to the string method, not to the LLG dynamics");
     if (interp == SS_INTERP_SPLINE)
         for (const StringRec& r : c->strs)
             if (r.d.n_images > kSplineMaxK)
@@ -997,6 +1005,22 @@ ss_status ss_set_reparam(ss_ctx* c, int interp, int climb) {
     ss_status st = sync_check(c);
     TRY(leave(c));
     return st;
+}
+
+ss_status ss_set_dynamics(ss_ctx* c, int kind, double alpha) {
+    if (!c) return SS_ERR_INVALID_ARG;
+    if (kind != SS_DYN_STRING && kind != SS_DYN_LLG) return fail(c, SS_ERR_INVALID_ARG, "unknown dynamics %d", kind);
+    if (kind == SS_DYN_LLG && !(alpha >= 0.0 && std::isfinite(alpha)))
+        return fail(c, SS_ERR_INVALID_ARG, "alpha must be finite and >= 0");
+    if (kind == SS_DYN_LLG && c->climb)
+        return fail(c, SS_ERR_STATE, "the climbing image belongs to the string method, not to the LLG dynamics");
+    c->dynamics = kind;
+    c->alpha = kind == SS_DYN_LLG ? alpha : 0.0;
+    for (Group& g : c->groups) g.arc.reparam = kind == SS_DYN_STRING && c->opts.reparam_every != 0;
+    if (c->graph1) cudaGraphExecDestroy(c->graph1);
+    if (c->graphN) cudaGraphExecDestroy(c->graphN);
+    c->graph1 = c->graphN = nullptr;
+    return SS_OK;
 }
 
 ss_status ss_climbing_image(ss_ctx* c, int string, int* k) {

@@ -86,6 +86,7 @@ template <typename T> struct GroupArgs {
     int ty_a, ty_c; // y rows per CTA in the x-forward and x-inverse kernels
     int* err;       // sticky error word (bit 1: invalid input spin, bit 2: non-finite value)
     const int* climb_img;  // [n_img] nonzero for the image that climbs this iteration (climbing mode only)
+    T llg_a, llg_b;        // precessional dynamics (Eq. 9): 1 / (1 + alpha^2) and alpha / (1 + alpha^2)
 };
 
 // Arc-length / reparametrisation bookkeeping of one size group.
@@ -109,7 +110,7 @@ struct ArcArgs {
     double* cpart;         // [n_str][c_tiles][2] (F.tau, tau.tau) partials of the climbing image
     int c_tiles;           // site tiles of kClimbTile per image
     int spline;            // natural cubic spline: the finisher writes W, the apply kernel moves the images
-    double* W;             // [n_str][maxK][maxK] interpolation weights phi_k = sum_q W_kq phi*_q
+    double* W;             // [n_str][maxK][maxK] interpolation weights phi_k = sum_q W_kq phi*_q, stored in T
     double* P;             // [n_str][maxK][maxK] scratch: d m_i / d y_q of the spline, column q contiguous
     int* wcopy;            // [n_str][maxK] row k is the identity (image kept as it is)
 };
@@ -180,12 +181,15 @@ template <typename T>
 void launch_xinv_step(const GroupArgs<T>& g, bool do_fft, T dt, int nthr, size_t smem, cudaStream_t st);
 template <typename T>
 void launch_xinv_eval(const GroupArgs<T>& g, bool do_fft, T* hout, int nthr, size_t smem, cudaStream_t st);
-// Runge-Kutta stage: the force of Eq. 13 at the state in s into kout; energy partials when energies
+// Runge-Kutta stage: the force of Eq. 13 (or with llg the right-hand side of Eq. 9) at the state in s
+// into kout; energy partials when energies
 template <typename T>
-void launch_xinv_force(const GroupArgs<T>& g, bool do_fft, T* kout, bool energies, int nthr, size_t smem,
+void launch_xinv_force(const GroupArgs<T>& g, bool do_fft, T* kout, bool energies, bool llg, int nthr, size_t smem,
                        cudaStream_t st);
 template <typename T> void launch_xinv_step_climb(const GroupArgs<T>& g, bool do_fft, T dt, T* hc, int nthr, size_t smem,
                                                   cudaStream_t st);
+template <typename T> void launch_xinv_step_llg(const GroupArgs<T>& g, bool do_fft, T dt, int nthr, size_t smem,
+                                                cudaStream_t st);
 template <typename T> void launch_climb(const GroupArgs<T>& g, const ArcArgs& a, T dt, const T* hc, cudaStream_t st);
 template <typename T> void launch_spline_apply(const GroupArgs<T>& g, const ArcArgs& a, int maxK, cudaStream_t st);
 template <typename T> void launch_rk_assemble(const GroupArgs<T>& g, const RkArgs<T>& r, int stage, cudaStream_t st);

@@ -624,11 +624,13 @@ __device__ __forceinline__ T step_site(const T* s0, const T* hf, T dt, T* un) {
     return T(-0.5) * sh;
 }
 
-// Step mode, FP32, even nx: two adjacent sites (x even, x + 1) per thread and pass, so the spin planes
-// move as float2 (one load serves both sites' y and z neighbours, and the inner x neighbours come from
-// the pair itself).  eacc[h] accumulates the energy terms of image 2p + h.
-__device__ __forceinline__ void xinv_sites_step2(const GroupArgs<float>& g, float dt, const float2* buf, int ls, int p,
-                                                 int z, int y0, int rows, int tid, int nthr, float (&eacc)[2]) {
+// Step modes (0, 3, 4 of xinv_sites), FP32, even nx: two adjacent sites (x even, x + 1) per thread and
+// pass, so the spin planes move as float2 (one load serves both sites' y and z neighbours, and the inner
+// x neighbours come from the pair itself).  eacc[h] accumulates the energy terms of image 2p + h.
+template <int MODE>
+__device__ __forceinline__ void xinv_sites_step2(const GroupArgs<float>& g, float dt, float* hout, const float2* buf,
+                                                 int ls, int p, int z, int y0, int rows, int tid, int nthr,
+                                                 const int (&climbs)[2], float (&eacc)[2]) {
     const int nx = g.nx, ny = g.ny, nz = g.nz, N = g.N, hx = nx >> 1;
     const int ia = 2 * p;
     const float2 zero = make_float2(0.f, 0.f);
@@ -674,9 +676,27 @@ __device__ __forceinline__ void xinv_sites_step2(const GroupArgs<float>& g, floa
                 conv[c] = h == 0 ? v.x : -v.y;  // conjugate of the forward transform of the conjugate
             }
             local_field(pr, s0, a, b, cc, d, e, f, conv, hf);
-            eacc[h] += step_site(s0, hf, dt, un[k]);
+            if (MODE == 0 || (MODE == 3 && !climbs[h])) {
+                eacc[h] += step_site(s0, hf, dt, un[k]);
+            } else {
+                const float sh = s0[0] * hf[0] + s0[1] * hf[1] + s0[2] * hf[2];
+                eacc[h] += -0.5f * sh;
+                if (MODE == 3) {  // the climbing image: its force, stepped by the climbing-image kernels
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) un[k][c] = hf[c] - sh * s0[c];
+                } else {  // Eq. 9
+                    const float sxh[3] = {s0[1] * hf[2] - s0[2] * hf[1], s0[2] * hf[0] - s0[0] * hf[2],
+                                          s0[0] * hf[1] - s0[1] * hf[0]};
+                    float u[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) u[c] = s0[c] + dt * (-g.llg_a * sxh[c] + g.llg_b * (hf[c] - sh * s0[c]));
+                    const float r = rsqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) un[k][c] = u[c] * r;
+                }
+            }
         }
-        float* __restrict__ o = g.sp + (size_t)im * 3 * N + site;
+        float* __restrict__ o = (MODE == 3 && climbs[h] ? hout : g.sp) + (size_t)im * 3 * N + site;
 #pragma unroll
         for (int c = 0; c < 3; ++c) *reinterpret_cast<float2*>(o + (size_t)c * N) = make_float2(un[0][c], un[1][c]);
     }
@@ -689,7 +709,8 @@ __device__ __forceinline__ void xinv_sites_step2(const GroupArgs<float>& g, floa
 // the field into hout when given).  MODE 3: MODE 0, except that the image flagged in g.climb_img writes
 // its force F = h - (s.h) s into hout instead of stepping (the climbing-image kernels step it).
 // MODE 2 (a Runge-Kutta stage): the force F = h - (s.h) s of Eq. 13
-// into hout, s as stored (not renormalised); energy partials only when dt != 0.
+// into hout, s as stored (not renormalised); energy partials only when dt != 0.  MODES 4 and 5: as 0 and 2
+// with the right-hand side of Eq. 9 (precession and damping, prefactors g.llg_a and g.llg_b).
 template <typename T, bool HAS_CONV, int MODE>
 __device__ __forceinline__ void xinv_sites(const GroupArgs<T>& g, T dt, T* hout, const cplx<T>* buf, int ls,
                                            double* red, int p, int z, int y0, int rows, int tid, int nthr) {
@@ -708,9 +729,9 @@ __device__ __forceinline__ void xinv_sites(const GroupArgs<T>& g, T dt, T* hout,
         for (int h = 0; h < 2; ++h)
             if (ia + h < g.n_img) climbs[h] = g.climb_img[ia + h];
     }
-    if constexpr (MODE == 0 && HAS_CONV && std::is_same<T, float>::value) {
+    if constexpr ((MODE == 0 || MODE == 3 || MODE == 4) && HAS_CONV && std::is_same<T, float>::value) {
         if ((nx & 1) == 0) {  // uniform over the grid
-            xinv_sites_step2(g, dt, buf, ls, p, z, y0, rows, tid, nthr, eacc);
+            xinv_sites_step2<MODE>(g, dt, hout, buf, ls, p, z, y0, rows, tid, nthr, climbs, eacc);
             done = true;
         }
     }
@@ -762,6 +783,27 @@ __device__ __forceinline__ void xinv_sites(const GroupArgs<T>& g, T dt, T* hout,
             T* __restrict__ o = hout + (size_t)im * 3 * N + site;
 #pragma unroll
             for (int c = 0; c < 3; ++c) o[(size_t)c * N] = hf[c] - sh * s0[c];
+        } else if (MODE == 4 || MODE == 5) {
+            // Eq. 9: f = -a (s x h) + b (h - (s.h) s)
+            const T sh = s0[0] * hf[0] + s0[1] * hf[1] + s0[2] * hf[2];
+            eacc[h] += T(-0.5) * sh;
+            const T sxh[3] = {s0[1] * hf[2] - s0[2] * hf[1], s0[2] * hf[0] - s0[0] * hf[2], s0[0] * hf[1] - s0[1] * hf[0]};
+            T f[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) f[c] = -g.llg_a * sxh[c] + g.llg_b * (hf[c] - sh * s0[c]);
+            if (MODE == 4) {
+                T u[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) u[c] = s0[c] + dt * f[c];
+                const T r = rsqrt_t<T>(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+                T* __restrict__ o = g.sp + (size_t)im * 3 * N + site;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) o[(size_t)c * N] = u[c] * r;
+            } else {
+                T* __restrict__ o = hout + (size_t)im * 3 * N + site;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) o[(size_t)c * N] = f[c];
+            }
         } else {
             auto nrm = [](const T* v, double* o) {
                 const double a = v[0], b = v[1], c = v[2];
@@ -802,7 +844,7 @@ __device__ __forceinline__ void xinv_sites(const GroupArgs<T>& g, T dt, T* hout,
             }
         }
     }
-    if constexpr (MODE == 2)
+    if constexpr (MODE == 2 || MODE == 5)
         if (dt == T(0)) return;  // uniform over the grid: no energy partials wanted
     if constexpr (MODE != 1)
         block_reduce_t2d<2>(eacc, acc, red);
@@ -942,30 +984,42 @@ template <typename T>
 __device__ __noinline__ void arc_finish(const GroupArgs<T>& g, const ArcArgs& a, int str, int K, int img0,
                                         double* alpha, double* wsum);
 
-// Reparametrisation variants in the finisher (alpha holds the arc lengths s_k).  A climbing image kc
+// Reparametrisation variants in the finisher (s holds the arc lengths s_k).  A climbing image kc
 // (0 < kc < K-1) splits the string into the parts [0, kc] and [kc, K-1], each brought to equal arc length
-// on its own: alpha*_j = (s_j - s_a) / (s_b - s_a) and targets (k - a) / (b - a) in part [a, b]; kc keeps
-// its place.  Linear interpolation writes the gather table as on the plain path.  The natural cubic
-// spline (second derivative zero at a part's ends) writes the identity table and the weights
-// phi_k = sum_q W_kq phi*_q that spline_apply_kernel applies: with knots x_i = alpha*_{a+i} (n = b - a
-// segments of lengths h_i), the second derivatives m = P y solve the tridiagonal system
+// on its own: knots alpha*_j = (s_j - s_a) / (s_b - s_a) and targets (k - a) / (b - a) in part [a, b]; kc
+// keeps its place.  Linear interpolation writes the gather table as on the plain path.  The natural
+// cubic spline (second derivative zero at a part's ends) writes the identity table and the weights
+// phi_k = sum_q W_kq phi*_q (in T) that spline_apply_kernel applies: with knots x_i = alpha*_{a+i}
+// (n = b - a segments of lengths h_i), the second derivatives m = P y solve the tridiagonal system
 // h_{i-1} m_{i-1} + 2 (h_{i-1} + h_i) m_i + h_i m_{i+1} = 6 ((y_{i+1} - y_i) / h_i - (y_i - y_{i-1}) / h_{i-1})
-// (m_0 = m_n = 0; P column by column, one thread each, by forward elimination and back substitution),
-// and on segment [x_j, x_{j+1}] the spline is A y_j + B y_{j+1} + C m_j + D m_{j+1} with
-// A = (x_{j+1} - x) / h_j, B = 1 - A, C = h_j^2 (A^3 - A) / 6, D = h_j^2 (B^3 - B) / 6.  A part with a
-// zero-length segment takes the linear rows instead; images that keep their place get identity rows.
+// (m_0 = m_n = 0; P column by column, one thread each, by forward elimination and back substitution with
+// the shared elimination factors), and on segment [x_j, x_{j+1}] the spline is
+// A y_j + B y_{j+1} + C m_j + D m_{j+1} with A = (x_{j+1} - x) / h_j, B = (x - x_j) / h_j,
+// C = h_j^2 (A^3 - A) / 6, D = h_j^2 (B^3 - B) / 6.  A part with a zero-length segment takes the linear
+// rows instead; images that keep their place get identity rows.  Each knot, segment reciprocal and
+// elimination factor is formed once (GB300 issues FP64 division slowly).
 template <typename T>
 __device__ __noinline__ void arc_finish_variants(const GroupArgs<T>& g, const ArcArgs& a, int str, int K, int img0,
                                                  int kc, const double* s) {
-    __shared__ double cp[kSplineMaxK], den[kSplineMaxK];
-    __shared__ int ok_part;
+    __shared__ double xs[kArcMaxK];  // knot of image k within its part (kc: 1, the end of part one)
+    __shared__ double hh[kSplineMaxK], rh[kSplineMaxK], rden[kSplineMaxK], cp[kSplineMaxK];
     const int tid = threadIdx.x, nthr = blockDim.x;
     const bool split = kc > 0 && kc < K - 1;
     const size_t mk = (size_t)a.maxK;
-    double* W = a.W + (size_t)str * mk * mk;
+    T* W = reinterpret_cast<T*>(a.W) + (size_t)str * mk * mk;
     double* P = a.P + (size_t)str * mk * mk;
+    auto part_lo = [&](int k) { return split && k > kc ? kc : 0; };
+    auto part_hi = [&](int k) { return split && k <= kc ? kc : K - 1; };
     for (int k = tid; k < K; k += nthr) {
-        const int a0 = split && k > kc ? kc : 0, b0 = split && k < kc ? kc : K - 1;
+        const int a0 = part_lo(k), b0 = part_hi(k);
+        const double L = s[b0] - s[a0];
+        xs[k] = L > 0.0 && isfinite(L) ? (s[k] - s[a0]) / L : 0.0;
+    }
+    __syncthreads();
+    // knot j of the part starting at a0 (kc starts part two at 0)
+    auto knot = [&](int j, int a0) { return j == a0 ? 0.0 : xs[j]; };
+    for (int k = tid; k < K; k += nthr) {
+        const int a0 = part_lo(k), b0 = part_hi(k);
         const double L = s[b0] - s[a0];
         const bool keep = !a.reparam || k == 0 || k == K - 1 || (split && k == kc) || !(L > 0.0) || !isfinite(L);
         InterpEntry e;
@@ -977,10 +1031,14 @@ __device__ __noinline__ void arc_finish_variants(const GroupArgs<T>& g, const Ar
         e.pad = 0;
         if (!keep && !a.spline) {
             const double ak = (double)(k - a0) / (double)(b0 - a0);
-            int j = a0;
-            for (int i = a0; i <= b0 - 1; ++i)
-                if ((s[i] - s[a0]) / L <= ak) j = i;
-            const double x0 = (s[j] - s[a0]) / L, x1 = (s[j + 1] - s[a0]) / L;
+            int j = min(max(k, a0), b0 - 1);  // largest j in [a0, b0 - 1] with knot j <= ak, walking from k
+            if (knot(j, a0) <= ak) {
+                while (j < b0 - 1 && knot(j + 1, a0) <= ak) ++j;
+            } else {
+                do --j;
+                while (knot(j, a0) > ak);
+            }
+            const double x0 = knot(j, a0), x1 = knot(j + 1, a0);
             e.src0 = img0 + j;
             e.src1 = img0 + j + 1;
             e.t = (ak - x0) / (x1 - x0);
@@ -991,8 +1049,8 @@ __device__ __noinline__ void arc_finish_variants(const GroupArgs<T>& g, const Ar
         const_cast<InterpEntry*>(g.interp)[img0 + k] = e;
         if (a.spline) {
             // identity rows for now; the interior rows of a moving part are rewritten below
-            double* wr = W + (size_t)k * mk;
-            for (int q = 0; q < K; ++q) wr[q] = q == k ? 1.0 : 0.0;
+            T* wr = W + (size_t)k * mk;
+            for (int q = 0; q < K; ++q) wr[q] = q == k ? T(1) : T(0);
             a.wcopy[(size_t)str * mk + k] = keep ? 1 : 0;
         }
     }
@@ -1000,35 +1058,33 @@ __device__ __noinline__ void arc_finish_variants(const GroupArgs<T>& g, const Ar
     for (int part = 0; part < (split ? 2 : 1); ++part) {
         const int a0 = part == 0 ? 0 : kc, b0 = part == 0 && split ? kc : K - 1, n = b0 - a0;
         const double L = s[b0] - s[a0];
-        __syncthreads();  // identity rows written; cp, den, ok_part free
+        __syncthreads();  // identity rows written; the shared factors are free
         if (!a.reparam || !(L > 0.0) || !isfinite(L) || n < 2) continue;  // uniform: nothing moves here
-        if (tid == 0) {
-            int ok = 1;
-            for (int i = 0; i < n; ++i)
-                if (!((s[a0 + i + 1] - s[a0]) / L > (s[a0 + i] - s[a0]) / L)) ok = 0;
-            for (int i = 1; ok && i < n; ++i) {
-                const double hl = (s[a0 + i] - s[a0]) / L - (s[a0 + i - 1] - s[a0]) / L;
-                const double hr = (s[a0 + i + 1] - s[a0]) / L - (s[a0 + i] - s[a0]) / L;
-                const double lo = i > 1 ? hl : 0.0;
-                den[i] = 2.0 * (hl + hr) - lo * (i > 1 ? cp[i - 1] : 0.0);
-                cp[i] = (i < n - 1 ? hr : 0.0) / den[i];
+        bool pos = true;
+        for (int i = tid; i < n; i += nthr) {
+            hh[i] = knot(a0 + i + 1, a0) - knot(a0 + i, a0);
+            pos = pos && hh[i] > 0.0;
+            if (pos) rh[i] = 1.0 / hh[i];
+        }
+        const bool ok = __syncthreads_and(pos);
+        if (ok && tid == 0) {  // elimination factors of the tridiagonal system (m_0 = m_n = 0 known)
+            for (int i = 1; i < n; ++i) {
+                const double den = 2.0 * (hh[i - 1] + hh[i]) - (i > 1 ? hh[i - 1] * cp[i - 1] : 0.0);
+                rden[i] = 1.0 / den;
+                cp[i] = (i < n - 1 ? hh[i] : 0.0) * rden[i];
             }
-            ok_part = ok;
         }
         __syncthreads();
-        const int ok = ok_part;
         if (ok) {
             for (int q = tid; q <= n; q += nthr) {  // column q of P: d m_i / d y_q, i = 1..n-1
                 double* pc = P + (size_t)(a0 + q) * mk;
                 double d = 0.0;
                 for (int i = 1; i < n; ++i) {
-                    const double hl = (s[a0 + i] - s[a0]) / L - (s[a0 + i - 1] - s[a0]) / L;
-                    const double hr = (s[a0 + i + 1] - s[a0]) / L - (s[a0 + i] - s[a0]) / L;
-                    double r = 0.0;
-                    if (q == i + 1) r = 6.0 / hr;
-                    if (q == i) r = -6.0 / hr - 6.0 / hl;
-                    if (q == i - 1) r = 6.0 / hl;
-                    d = (r - (i > 1 ? hl : 0.0) * d) / den[i];
+                    double r = 0.0;  // d rhs_i / d y_q
+                    if (q == i + 1) r = 6.0 * rh[i];
+                    if (q == i) r = -6.0 * (rh[i] + rh[i - 1]);
+                    if (q == i - 1) r = 6.0 * rh[i - 1];
+                    d = (r - (i > 1 ? hh[i - 1] * d : 0.0)) * rden[i];
                     pc[i] = d;
                 }
                 for (int i = n - 2; i >= 1; --i) pc[i] -= cp[i] * pc[i + 1];
@@ -1037,25 +1093,29 @@ __device__ __noinline__ void arc_finish_variants(const GroupArgs<T>& g, const Ar
         }
         for (int k = a0 + 1 + tid; k < b0; k += nthr) {
             const double ak = (double)(k - a0) / (double)n;
-            int j = a0;
-            for (int i = a0; i <= b0 - 1; ++i)
-                if ((s[i] - s[a0]) / L <= ak) j = i;
-            const double x0 = (s[j] - s[a0]) / L, x1 = (s[j + 1] - s[a0]) / L, h = x1 - x0;
-            double* wr = W + (size_t)k * mk;
-            wr[k] = 0.0;
+            int j = min(k, b0 - 1);
+            if (knot(j, a0) <= ak) {
+                while (j < b0 - 1 && knot(j + 1, a0) <= ak) ++j;
+            } else {
+                do --j;
+                while (knot(j, a0) > ak);
+            }
+            const double x0 = knot(j, a0), x1 = knot(j + 1, a0);
+            T* wr = W + (size_t)k * mk;
+            wr[k] = T(0);
             if (!ok) {
-                const double t = (ak - x0) / h;
-                wr[j] = 1.0 - t;
-                wr[j + 1] = t;
+                const double t = (ak - x0) / (x1 - x0);
+                wr[j] = T(1.0 - t);
+                wr[j + 1] = T(t);
                 continue;
             }
-            const double A = (x1 - ak) / h, B = (ak - x0) / h;
-            const double C = h * h * (A * A * A - A) / 6.0, D = h * h * (B * B * B - B) / 6.0;
             const int jr = j - a0;
+            const double h = hh[jr], A = (x1 - ak) * rh[jr], B = (ak - x0) * rh[jr];
+            const double C = h * h * (A * A * A - A) * (1.0 / 6.0), D = h * h * (B * B * B - B) * (1.0 / 6.0);
             for (int q = 0; q <= n; ++q) {
                 const double* pc = P + (size_t)(a0 + q) * mk;
                 const double mj = jr > 0 ? pc[jr] : 0.0, mj1 = jr + 1 < n ? pc[jr + 1] : 0.0;
-                wr[a0 + q] = (q == jr ? A : 0.0) + (q == jr + 1 ? B : 0.0) + C * mj + D * mj1;
+                wr[a0 + q] = T((q == jr ? A : 0.0) + (q == jr + 1 ? B : 0.0) + C * mj + D * mj1);
             }
         }
     }
@@ -1602,16 +1662,16 @@ __global__ void __launch_bounds__(128) spline_apply_kernel(GroupArgs<T> g, ArcAr
     if (i >= N) return;
     const size_t M = (size_t)3 * N, mk = (size_t)a.maxK;
     const int* wc = a.wcopy + (size_t)str * mk;
-    const double* W = a.W + (size_t)str * mk * mk;
+    const T* W = reinterpret_cast<const T*>(a.W) + (size_t)str * mk * mk;
     for (int q = 0; q < K; ++q)
 #pragma unroll
         for (int c = 0; c < 3; ++c) y[(q * 3 + c) * ts + tid] = g.sp[(size_t)(img0 + q) * M + (size_t)c * N + i];
     for (int k = 1; k < K - 1; ++k) {
         if (wc[k]) continue;  // kept in place (uniform over the CTA)
-        const double* wr = W + (size_t)k * mk;
+        const T* wr = W + (size_t)k * mk;
         T u[3] = {T(0), T(0), T(0)};
         for (int q = 0; q < K; ++q) {
-            const T w = T(__ldg(wr + q));
+            const T w = __ldg(wr + q);
 #pragma unroll
             for (int c = 0; c < 3; ++c) u[c] += w * y[(q * 3 + c) * ts + tid];
         }
@@ -1881,25 +1941,53 @@ void launch_xinv_eval(const GroupArgs<T>& g, bool do_fft, T* hout, int nthr, siz
     }
 }
 
-template <typename T>
-void launch_xinv_force(const GroupArgs<T>& g, bool do_fft, T* kout, bool energies, int nthr, size_t smem,
-                       cudaStream_t st) {
+template <typename T, int MODE>
+static void launch_xinv_force_mode(const GroupArgs<T>& g, bool do_fft, T* kout, T flag, int nthr, size_t smem,
+                                   cudaStream_t st) {
     dim3 grid((g.ny + g.ty_c - 1) / g.ty_c, g.nz, g.n_pairs);
-    const T flag = energies ? T(1) : T(0);  // force mode: nonzero asks for the energy partials
     if constexpr (std::is_same<T, float>::value) {
         if (do_fft && f128_x(4, g.Px)) {
             const int nt = f128_x_threads(g.ty_c);
             const size_t sm = f128_x_smem(g.ty_c);
-            if (g.ty_c == 2) xinv128_kernel<T, 2, 2><<<grid, nt, sm, st>>>(g, flag, kout);
-            else if (g.ty_c == 4) xinv128_kernel<T, 2, 4><<<grid, nt, sm, st>>>(g, flag, kout);
-            else xinv128_kernel<T, 2, 8><<<grid, nt, sm, st>>>(g, flag, kout);
+            if (g.ty_c == 2) xinv128_kernel<T, MODE, 2><<<grid, nt, sm, st>>>(g, flag, kout);
+            else if (g.ty_c == 4) xinv128_kernel<T, MODE, 4><<<grid, nt, sm, st>>>(g, flag, kout);
+            else xinv128_kernel<T, MODE, 8><<<grid, nt, sm, st>>>(g, flag, kout);
             return;
         }
     }
     if (do_fft)
-        xinv_kernel<T, true, 2, 0><<<grid, nthr, smem, st>>>(g, flag, kout);
+        xinv_kernel<T, true, MODE, 0><<<grid, nthr, smem, st>>>(g, flag, kout);
     else
-        xinv_kernel<T, false, 2, 0><<<grid, nthr, smem, st>>>(g, flag, kout);
+        xinv_kernel<T, false, MODE, 0><<<grid, nthr, smem, st>>>(g, flag, kout);
+}
+
+template <typename T>
+void launch_xinv_force(const GroupArgs<T>& g, bool do_fft, T* kout, bool energies, bool llg, int nthr, size_t smem,
+                       cudaStream_t st) {
+    const T flag = energies ? T(1) : T(0);  // force mode: nonzero asks for the energy partials
+    if (llg)
+        launch_xinv_force_mode<T, 5>(g, do_fft, kout, flag, nthr, smem, st);
+    else
+        launch_xinv_force_mode<T, 2>(g, do_fft, kout, flag, nthr, smem, st);
+}
+
+template <typename T>
+void launch_xinv_step_llg(const GroupArgs<T>& g, bool do_fft, T dt, int nthr, size_t smem, cudaStream_t st) {
+    dim3 grid((g.ny + g.ty_c - 1) / g.ty_c, g.nz, g.n_pairs);
+    if constexpr (std::is_same<T, float>::value) {
+        if (do_fft && f128_x(4, g.Px)) {
+            const dim3 blk(f128_x_threads(g.ty_c));
+            const size_t sm = f128_x_smem(g.ty_c);
+            if (g.ty_c == 2) launch_pdl(xinv128_kernel<T, 4, 2>, grid, blk, sm, st, g, dt, (T*)nullptr);
+            else if (g.ty_c == 4) launch_pdl(xinv128_kernel<T, 4, 4>, grid, blk, sm, st, g, dt, (T*)nullptr);
+            else launch_pdl(xinv128_kernel<T, 4, 8>, grid, blk, sm, st, g, dt, (T*)nullptr);
+            return;
+        }
+    }
+    if (do_fft)
+        launch_pdl(xinv_kernel<T, true, 4, 0>, grid, dim3(nthr), smem, st, g, dt, (T*)nullptr);
+    else
+        launch_pdl(xinv_kernel<T, false, 4, 0>, grid, dim3(nthr), smem, st, g, dt, (T*)nullptr);
 }
 
 template <typename T>
@@ -1928,9 +2016,9 @@ template <typename T> void launch_climb(const GroupArgs<T>& g, const ArcArgs& a,
 }
 
 // sites per CTA of the spline apply kernel for strings of up to maxK images: the [maxK][3][ts] tile in
-// at most 200 KB of shared memory, ts a power of two in [32, 128]
+// at most 200 KB of shared memory, ts a power of two in [32, 64]
 template <typename T> int spline_sites_per_cta(int maxK) {
-    int ts = 128;
+    int ts = 64;
     while (ts > 32 && (size_t)maxK * 3 * ts * sizeof(T) > 200 * 1024) ts >>= 1;
     return ts;
 }
@@ -2011,6 +2099,10 @@ template <typename T> void set_smem_limits(int bytes) {
     set_dyn_smem(xinv_kernel<T, false, 2, 0>, bytes);
     set_dyn_smem(xinv_kernel<T, true, 3, 0>, bytes);
     set_dyn_smem(xinv_kernel<T, false, 3, 0>, bytes);
+    set_dyn_smem(xinv_kernel<T, true, 4, 0>, bytes);
+    set_dyn_smem(xinv_kernel<T, false, 4, 0>, bytes);
+    set_dyn_smem(xinv_kernel<T, true, 5, 0>, bytes);
+    set_dyn_smem(xinv_kernel<T, false, 5, 0>, bytes);
     set_dyn_smem(spline_apply_kernel<T>, 200 * 1024);
     if constexpr (std::is_same<T, float>::value) {
 #define SS_CASE(R)                                  \
@@ -2018,7 +2110,9 @@ template <typename T> void set_smem_limits(int bytes) {
     set_dyn_smem(xinv128_kernel<T, 0, R>, bytes);   \
     set_dyn_smem(xinv128_kernel<T, 1, R>, bytes);   \
     set_dyn_smem(xinv128_kernel<T, 2, R>, bytes);   \
-    set_dyn_smem(xinv128_kernel<T, 3, R>, bytes);
+    set_dyn_smem(xinv128_kernel<T, 3, R>, bytes);   \
+    set_dyn_smem(xinv128_kernel<T, 4, R>, bytes);   \
+    set_dyn_smem(xinv128_kernel<T, 5, R>, bytes);
         SS_CASE(2) SS_CASE(4) SS_CASE(8)
 #undef SS_CASE
         set_dyn_smem(yz128_kernel<T, 4>, bytes);
@@ -2062,7 +2156,8 @@ void launch_interp_identity(InterpEntry* tab, int img0, int K, cudaStream_t st) 
     template void launch_yz<T>(const GroupArgs<T>&, int, size_t, cudaStream_t);                                \
     template void launch_xinv_step<T>(const GroupArgs<T>&, bool, T, int, size_t, cudaStream_t);                \
     template void launch_xinv_eval<T>(const GroupArgs<T>&, bool, T*, int, size_t, cudaStream_t);               \
-    template void launch_xinv_force<T>(const GroupArgs<T>&, bool, T*, bool, int, size_t, cudaStream_t);        \
+    template void launch_xinv_force<T>(const GroupArgs<T>&, bool, T*, bool, bool, int, size_t, cudaStream_t);  \
+    template void launch_xinv_step_llg<T>(const GroupArgs<T>&, bool, T, int, size_t, cudaStream_t);             \
     template void launch_xinv_step_climb<T>(const GroupArgs<T>&, bool, T, T*, int, size_t, cudaStream_t);       \
     template void launch_climb<T>(const GroupArgs<T>&, const ArcArgs&, T, const T*, cudaStream_t);             \
     template void launch_spline_apply<T>(const GroupArgs<T>&, const ArcArgs&, int, cudaStream_t);              \
