@@ -41,7 +41,9 @@ L2_FLUSH_BYTES = 256 << 20
 #   xinv: read the spectrum 24, read s 12, write sp 12
 #   arc:  read sp 12 (its last CTAs then reduce per-image partials and write the interpolation table)
 KERNEL_NAMES = ("xfwd", "yz", "xinv", "arc")
-BYTES_PER_SITE_IMAGE = {"xfwd": 48, "yz": 48, "xinv": 48, "arc": 12}
+BYTES_PER_SITE_IMAGE = {"xfwd": 48, "yz": 48, "xinv": 48, "arc": 12, "spline": 24}
+# the climbing-image kernels touch one image per string: F, s at kc and kc +- 1 read twice, the step written
+CLIMB_BYTES_PER_SITE = 9 * 12
 REF_IMAGES = 8
 
 
@@ -55,7 +57,31 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-accuracy", action="store_true", help="skip the FP64-GPU barrier comparison")
     p.add_argument("--no-other-workloads", action="store_true", help="skip the short runs of the batch workloads")
+    p.add_argument("--variant", choices=tuple(VARIANTS), default="plain",
+                   help="run the timed steps under a method variant (the headline is 'plain')")
     return p.parse_args()
+
+
+# method variants: (interpolation, climbing image, integrator, dynamics)
+VARIANTS = {
+    "plain": ("linear", False, "euler", "string"),
+    "spline": ("spline", False, "euler", "string"),
+    "climbing_image": ("linear", True, "euler", "string"),
+    "spline_and_climbing_image": ("spline", True, "euler", "string"),
+    "dopri5_per_string": ("linear", False, "dopri5", "string"),
+    "dopri5_per_image": ("linear", False, "dopri5_image", "string"),
+    "llg_euler": ("linear", False, "euler", "llg"),
+}
+LLG_ALPHA = 0.1
+
+
+def apply_variant(binding, sm, name, rtol=1e-6, atol=1e-8):
+    interp, climb, integ, dyn = VARIANTS[name]
+    if dyn == "llg":
+        sm.set_dynamics(binding.SS_DYN_LLG, LLG_ALPHA)
+    sm.set_reparam(binding.SS_INTERP_SPLINE if interp == "spline" else binding.SS_INTERP_LINEAR, climb)
+    if integ != "euler":
+        sm.set_integrator(binding.SS_INT_DOPRI5 if integ == "dopri5" else binding.SS_INT_DOPRI5_IMAGE, rtol, atol)
 
 
 def dist_env():
@@ -216,6 +242,7 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
     sm = binding.StringMethod([desc], dt=wl.dt, stream=stream.cuda_stream)
+    apply_variant(binding, sm, args.variant)
     kpi = sm.kernels_per_iteration()
 
     def one_step(src):
@@ -243,8 +270,11 @@ def main():
     for _ in range(args.warmup):
         one_step(path_dev)
     barrier_all()
+    rk = VARIANTS[args.variant][2] != "euler"
     with ClockSampler(local_rank) as clk:
         t_dev = timed(path_dev, args.steps)
+        if rk:  # attempts of the last timed step (set_path restarts the counts each step)
+            rk_attempts = [sum(sm.integrator_state(0, k)[1:]) for k in range(spec.n_images)]
         barrier_all()
         t_e2e = timed(path_host, args.steps)
         barrier_all()
@@ -267,14 +297,18 @@ def main():
 
     # per-kernel roofline (kernels launched one by one on the library stream, CUDA-event timed)
     sm.set_path(0, path_dev)
+    if rk:  # the field kernels are timed in the Euler iteration
+        sm.set_integrator(binding.SS_INT_EULER)
     ms = sm.time_kernels(reps=20)
-    names = [n for n in KERNEL_NAMES if n != "yz" or len(ms) == len(KERNEL_NAMES)]
+    interp, climb, integ, dyn = VARIANTS[args.variant]
+    names = ["xfwd", "yz", "xinv"] + (["climb"] if climb else []) + ["arc"] + (["spline"] if interp == "spline" else [])
     share = ms / ms.sum()
     dom = int(np.argmax(ms))
     dname = names[dom]
     launch_units = spec.n_sites * spec.n_images
     peaks, peak_kind = measured_peaks()
-    alg_bytes = BYTES_PER_SITE_IMAGE[dname] * launch_units
+    alg_bytes = (CLIMB_BYTES_PER_SITE * spec.n_sites if dname == "climb" else
+                 BYTES_PER_SITE_IMAGE[dname] * launch_units)
     if dname == "yz":
         alg_bytes += 4 * 6 * spec.nz * (padded(spec.nx) // 2 + 1) * (padded(spec.ny) // 2 + 1)
     achieved = alg_bytes / (ms[dom] * 1e-3) / 1e9
@@ -291,7 +325,8 @@ def main():
         "metric": "spin-updates/s", "value": value, "unit": "spin-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": wl.name, "lattice": [spec.nx, spec.ny, spec.nz], "images": spec.n_images,
+        "config": {"workload": wl.name, "variant": args.variant, "lattice": [spec.nx, spec.ny, spec.nz],
+                   "images": spec.n_images,
                    "iterations_per_step": n_iter, "dt": wl.dt, "J": spec.J, "D": spec.D, "K": spec.K, "w": spec.w,
                    "padded_xy": [padded(spec.nx), padded(spec.ny)],
                    "precision": "fp32 spins, fields and FFTs; fp64 energy and arc-length reductions",
@@ -299,7 +334,12 @@ def main():
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_value, "unit": "spin-updates/s", "h2d_bytes_per_step": int(path.nbytes),
                 "d2h_bytes_per_step": int(spec.n_images * 8)},
-        "gpu_launches": int(args.steps * (2 + n_iter * kpi + 4)),
+        "gpu_launches": int(args.steps * (2 + n_iter * kpi + 4)) if not rk else
+        # per attempt round 7 x (assemble, x-forward, y/z, x-inverse) + finish, control, commit; per
+        # iteration the gather, the controller's start and the arc kernel; rounds = the string's attempts
+        # (per-image control: the most attempts of one image, a lower bound)
+        int(args.steps * (2 + 4 + 3 * n_iter + (7 * kpi + 3) *  # kpi: the 3 or 4 field kernels and arc -> assemble
+                          (max(rk_attempts) if args.variant == "dopri5_per_image" else rk_attempts[0]))),
         "roofline": roofline,
         "clocks": clk.summary(),
         "barrier": {"dE": dE, "k_max": kmax},
@@ -325,7 +365,7 @@ def main():
         line["other_workloads"] = {w.name: other_workload(binding, w, stream) for w in
                                    (workloads.boundary_sweep(), workloads.uneven_study(),
                                     workloads.paper_monolayer_workload(), workloads.paper_phase_diagram())}
-        line["reparam_variants"] = reparam_variants(binding, wl, stream, plain_ms=step_s * 1e3 / n_iter)
+        line["variants"] = variant_runs(binding, wl, stream, plain_ms=step_s * 1e3 / n_iter)
         line["adaptive_rk"] = {name: adaptive_rk(binding, wl, stream, kind, per_iter_euler_ms=step_s * 1e3 / n_iter)
                                for name, kind in (("dopri5_per_string", binding.SS_INT_DOPRI5),
                                                   ("dopri5_per_image", binding.SS_INT_DOPRI5_IMAGE))}
@@ -340,18 +380,16 @@ def main():
         pg.destroy_process_group()
 
 
-def reparam_variants(binding, wl, stream, plain_ms, iters=128, warm=64):
-    """Device-timed Euler iterations of the bench workload under the reparametrisation variants
-    (natural cubic spline, climbing image, both), graph-replayed like the headline, inputs resident."""
+def variant_runs(binding, wl, stream, plain_ms, iters=128, warm=64):
+    """Device-timed Euler iterations of the bench workload under the variants that replay a CUDA graph
+    (natural cubic spline, climbing image, both, precessional LLG), inputs resident."""
     import torch
     spec = wl.strings[0]
     desc = (spec.nx, spec.ny, spec.nz, spec.J, spec.D, spec.K, spec.w, spec.n_images)
     out = {}
-    for name, interp, climb in (("spline", binding.SS_INTERP_SPLINE, False),
-                                ("climbing_image", binding.SS_INTERP_LINEAR, True),
-                                ("spline_and_climbing_image", binding.SS_INTERP_SPLINE, True)):
+    for name in ("spline", "climbing_image", "spline_and_climbing_image", "llg_euler"):
         with binding.StringMethod([desc], dt=wl.dt, stream=stream.cuda_stream) as sm:
-            sm.set_reparam(interp, climb)
+            apply_variant(binding, sm, name)
             sm.set_path(0, torch.from_numpy(spec.initial_path().astype(np.float32)).cuda())
             sm.step(warm)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -367,6 +405,8 @@ def reparam_variants(binding, wl, stream, plain_ms, iters=128, warm=64):
         out[name] = {"value": units * iters / t, "unit": "spin-updates/s", "iterations_timed": iters,
                      "ms_per_iter": 1e3 * t / iters, "vs_plain_ms_per_iter": (1e3 * t / iters) / plain_ms,
                      "kernels_per_iter": kpi, "climbing_image": kc}
+        if name == "llg_euler":
+            out[name]["alpha"] = LLG_ALPHA
     return out
 
 

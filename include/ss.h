@@ -122,12 +122,14 @@ ss_status ss_grad(ss_ctx* ctx, int string, int image, void* dE_ds, int dtype, in
  * entry is that term with its constant set to 1), in FP64.  Synchronises. */
 ss_status ss_energy_terms(ss_ctx* ctx, int string, double* out);
 
-/* Measures the kernels of one iteration: each kernel is launched on its own (not from the graph) on
- * the context's stream, bracketed by CUDA events, for `reps` >= 1 timed iterations after one untimed
- * iteration.  ms_out[i] (host, up to max_out entries) receives the mean duration in milliseconds of
- * kernel i, in launch order: for each size group xfwd, yz (when the group has a dipole term), xinv,
- * arc (which also reparametrises).  *n_out receives the number of kernels.  The strings advance by reps + 1 iterations.
- * Synchronises. */
+/* Measures the kernels of one Euler iteration in the current mode: each entry is launched on its own
+ * (not from the graph) on the context's stream, bracketed by CUDA events, for `reps` >= 1 timed
+ * iterations after one untimed iteration.  ms_out[i] (host, up to max_out entries) receives the mean
+ * duration in milliseconds of entry i, in launch order: for each size group xfwd, yz (when the group has
+ * a dipole term), xinv (in its step, climbing-image or LLG mode), the two climbing-image kernels as one
+ * entry (climbing image on), arc (which also reparametrises), the spline apply kernel (spline on).
+ * *n_out receives the number of entries.  The strings advance by reps + 1 iterations.  SS_ERR_STATE
+ * under a Runge-Kutta integrator.  Synchronises. */
 ss_status ss_time_kernels(ss_ctx* ctx, int reps, double* ms_out, int max_out, int* n_out);
 
 /* Effective field of a batch of images, for callers that cannot allocate device memory.  The paper

@@ -484,6 +484,34 @@ template <typename T> ss_status tune_group(ss_ctx* c, Group& g) {
     return SS_OK;
 }
 
+// The launches of one Euler iteration of group g in the current mode, as timed entries: xfwd, yz (with a
+// dipole term), xinv (step, climbing-image or LLG mode), the two climbing-image kernels as one entry,
+// arc, spline apply.
+template <typename T> int time_entries(ss_ctx* c, Group& g, int which_only) {
+    GroupArgs<T> a = group_args<T>(c, g);
+    const T dt = T(c->opts.dt);
+    int e = 0;
+    auto entry = [&](bool on, auto&& launch) {
+        if (!on) return;
+        if (which_only < 0 || which_only == e) launch();
+        ++e;
+    };
+    entry(true, [&] { launch_xfwd<T>(a, g.dipole, g.thr_a, g.smem_a, c->cs); });
+    entry(g.dipole, [&] { launch_yz<T>(a, g.thr_b, g.smem_b, c->cs); });
+    entry(true, [&] {
+        if (c->dynamics == SS_DYN_LLG)
+            launch_xinv_step_llg<T>(a, g.dipole, dt, g.thr_c, g.smem_c, c->cs);
+        else if (c->climb)
+            launch_xinv_step_climb<T>(a, g.dipole, dt, (T*)g.hc, g.thr_c, g.smem_c, c->cs);
+        else
+            launch_xinv_step<T>(a, g.dipole, dt, g.thr_c, g.smem_c, c->cs);
+    });
+    entry(c->climb != 0, [&] { launch_climb<T>(a, g.arc, dt, (const T*)g.hc, c->cs); });
+    entry(true, [&] { launch_arc<T>(a, g.arc, g.thr_arc, c->cs); });
+    entry(c->interp == SS_INTERP_SPLINE, [&] { launch_spline_apply<T>(a, g.arc, g.arc.maxK, c->cs); });
+    return e;
+}
+
 // ---- adaptive Runge-Kutta evolution (Sec. III, Dormand-Prince 5(4)) -------------------------------------
 RkString rk_fresh(const ss_ctx* c) {
     RkString r{};
@@ -995,6 +1023,7 @@ ss_status ss_set_reparam(ss_ctx* c, int interp, int climb) {
         }
         a.climb = climb;
         a.spline = interp == SS_INTERP_SPLINE;
+        a.p_dim = a.spline ? std::min(a.maxK, kSplineSmemP) : 0;
     }
     c->interp = interp;
     c->climb = climb;
@@ -1198,8 +1227,14 @@ ss_status ss_energy_terms(ss_ctx* c, int string, double* out) {
 
 ss_status ss_time_kernels(ss_ctx* c, int reps, double* ms_out, int max_out, int* n_out) {
     if (!c || reps < 1 || !n_out) return c ? fail(c, SS_ERR_INVALID_ARG, "reps >= 1 and n_out required") : SS_ERR_INVALID_ARG;
+    if (c->integrator != SS_INT_EULER) return fail(c, SS_ERR_STATE, "kernel timing covers the Euler iteration");
     for (const Group& g : c->groups) TRY(check_paths(c, g));
-    const int nk = ss_kernels_per_iteration(c);
+    std::vector<int> per_group;
+    int nk = 0;
+    for (Group& g : c->groups) {
+        per_group.push_back(use_fp64(c) ? time_entries<double>(c, g, -2) : time_entries<float>(c, g, -2));
+        nk += per_group.back();
+    }
     *n_out = nk;
     std::vector<cudaEvent_t> ev(2 * nk, nullptr);
     for (auto& e : ev) CUDA_TRY(c, cudaEventCreate(&e));
@@ -1208,26 +1243,14 @@ ss_status ss_time_kernels(ss_ctx* c, int reps, double* ms_out, int max_out, int*
     ss_status st = SS_OK;
     for (int r = 0; r <= reps && st == SS_OK; ++r) {
         int k = 0;
-        for (Group& g : c->groups) {
-            auto run = [&](int which) {
-                if (use_fp64(c)) {
-                    GroupArgs<double> a = group_args<double>(c, g);
-                    if (which == 0) launch_xfwd<double>(a, g.dipole, g.thr_a, g.smem_a, c->cs);
-                    if (which == 1) launch_yz<double>(a, g.thr_b, g.smem_b, c->cs);
-                    if (which == 2) launch_xinv_step<double>(a, g.dipole, c->opts.dt, g.thr_c, g.smem_c, c->cs);
-                    if (which == 3) launch_arc<double>(a, g.arc, g.thr_arc, c->cs);
-                } else {
-                    GroupArgs<float> a = group_args<float>(c, g);
-                    if (which == 0) launch_xfwd<float>(a, g.dipole, g.thr_a, g.smem_a, c->cs);
-                    if (which == 1) launch_yz<float>(a, g.thr_b, g.smem_b, c->cs);
-                    if (which == 2) launch_xinv_step<float>(a, g.dipole, (float)c->opts.dt, g.thr_c, g.smem_c, c->cs);
-                    if (which == 3) launch_arc<float>(a, g.arc, g.thr_arc, c->cs);
-                }
-            };
-            for (int which = 0; which < 4; ++which) {
-                if (which == 1 && !g.dipole) continue;
+        for (size_t gi = 0; gi < c->groups.size(); ++gi) {
+            Group& g = c->groups[gi];
+            for (int which = 0; which < per_group[gi]; ++which) {
                 cudaEventRecord(ev[2 * k], c->cs);
-                run(which);
+                if (use_fp64(c))
+                    time_entries<double>(c, g, which);
+                else
+                    time_entries<float>(c, g, which);
                 cudaEventRecord(ev[2 * k + 1], c->cs);
                 ++k;
             }

@@ -111,12 +111,14 @@ struct ArcArgs {
     int c_tiles;           // site tiles of kClimbTile per image
     int spline;            // natural cubic spline: the finisher writes W, the apply kernel moves the images
     double* W;             // [n_str][maxK][maxK] interpolation weights phi_k = sum_q W_kq phi*_q, stored in T
-    double* P;             // [n_str][maxK][maxK] scratch: d m_i / d y_q of the spline, column q contiguous
+    double* P;             // [n_str][maxK][maxK] scratch: d m_i / d y_q of the spline (in T), column q contiguous
     int* wcopy;            // [n_str][maxK] row k is the identity (image kept as it is)
+    int p_dim;             // spline operator columns kept in the finisher's dynamic shared memory (0: none)
 };
 
-constexpr int kClimbTile = 1024;  // sites per CTA of the climbing-image kernels
+constexpr int kClimbTile = 256;   // sites per CTA of the climbing-image kernels (one per thread)
 constexpr int kSplineMaxK = 256;  // longest string the spline variant accepts
+constexpr int kSplineSmemP = 64;  // parts of up to 63 segments keep the spline operator P in shared memory
 
 // Adaptive Runge-Kutta evolution (Sec. III, Dormand-Prince 5(4)): controller state of one ODE system
 // (a whole string, or one image under per-image step control).

@@ -1002,12 +1002,16 @@ template <typename T>
 __device__ __noinline__ void arc_finish_variants(const GroupArgs<T>& g, const ArcArgs& a, int str, int K, int img0,
                                                  int kc, const double* s) {
     __shared__ double xs[kArcMaxK];  // knot of image k within its part (kc: 1, the end of part one)
-    __shared__ double hh[kSplineMaxK], rh[kSplineMaxK], rden[kSplineMaxK], cp[kSplineMaxK];
+    __shared__ double hh_raw[kSplineMaxK], rh_raw[kSplineMaxK], rden_raw[kSplineMaxK], cp_raw[kSplineMaxK];
+    // P of a part of up to a.p_dim - 1 segments stays on chip in the launch's dynamic shared memory (the
+    // recurrences along a column are dependent, so each step's latency counts); longer parts use the
+    // global scratch
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* Psm = reinterpret_cast<double*>(smem_raw);
     const int tid = threadIdx.x, nthr = blockDim.x;
     const bool split = kc > 0 && kc < K - 1;
     const size_t mk = (size_t)a.maxK;
     T* W = reinterpret_cast<T*>(a.W) + (size_t)str * mk * mk;
-    double* P = a.P + (size_t)str * mk * mk;
     auto part_lo = [&](int k) { return split && k > kc ? kc : 0; };
     auto part_hi = [&](int k) { return split && k <= kc ? kc : K - 1; };
     for (int k = tid; k < K; k += nthr) {
@@ -1055,6 +1059,12 @@ __device__ __noinline__ void arc_finish_variants(const GroupArgs<T>& g, const Ar
         }
     }
     if (!a.spline) return;
+    // the spline operator in the path's precision T (its weights are stored in T; FP64 arithmetic is slow
+    // on GB300 and buys the FP32 path nothing); knots and targets as computed above
+    T* hh = reinterpret_cast<T*>(hh_raw);
+    T* rh = reinterpret_cast<T*>(rh_raw);
+    T* rden = reinterpret_cast<T*>(rden_raw);
+    T* cp = reinterpret_cast<T*>(cp_raw);
     for (int part = 0; part < (split ? 2 : 1); ++part) {
         const int a0 = part == 0 ? 0 : kc, b0 = part == 0 && split ? kc : K - 1, n = b0 - a0;
         const double L = s[b0] - s[a0];
@@ -1062,29 +1072,33 @@ __device__ __noinline__ void arc_finish_variants(const GroupArgs<T>& g, const Ar
         if (!a.reparam || !(L > 0.0) || !isfinite(L) || n < 2) continue;  // uniform: nothing moves here
         bool pos = true;
         for (int i = tid; i < n; i += nthr) {
-            hh[i] = knot(a0 + i + 1, a0) - knot(a0 + i, a0);
-            pos = pos && hh[i] > 0.0;
-            if (pos) rh[i] = 1.0 / hh[i];
+            const double hd = knot(a0 + i + 1, a0) - knot(a0 + i, a0);
+            hh[i] = T(hd);
+            pos = pos && hd > 0.0 && hh[i] > T(0);
+            if (pos) rh[i] = T(1) / hh[i];
         }
         const bool ok = __syncthreads_and(pos);
+        const bool on_chip = n + 1 <= a.p_dim;
+        T* P = on_chip ? reinterpret_cast<T*>(Psm) : reinterpret_cast<T*>(a.P) + (size_t)str * mk * mk;
+        const size_t ps = on_chip ? (size_t)a.p_dim : mk;  // column stride
         if (ok && tid == 0) {  // elimination factors of the tridiagonal system (m_0 = m_n = 0 known)
             for (int i = 1; i < n; ++i) {
-                const double den = 2.0 * (hh[i - 1] + hh[i]) - (i > 1 ? hh[i - 1] * cp[i - 1] : 0.0);
-                rden[i] = 1.0 / den;
-                cp[i] = (i < n - 1 ? hh[i] : 0.0) * rden[i];
+                const T den = T(2) * (hh[i - 1] + hh[i]) - (i > 1 ? hh[i - 1] * cp[i - 1] : T(0));
+                rden[i] = T(1) / den;
+                cp[i] = (i < n - 1 ? hh[i] : T(0)) * rden[i];
             }
         }
         __syncthreads();
         if (ok) {
             for (int q = tid; q <= n; q += nthr) {  // column q of P: d m_i / d y_q, i = 1..n-1
-                double* pc = P + (size_t)(a0 + q) * mk;
-                double d = 0.0;
+                T* pc = P + (size_t)q * ps;
+                T d = T(0);
                 for (int i = 1; i < n; ++i) {
-                    double r = 0.0;  // d rhs_i / d y_q
-                    if (q == i + 1) r = 6.0 * rh[i];
-                    if (q == i) r = -6.0 * (rh[i] + rh[i - 1]);
-                    if (q == i - 1) r = 6.0 * rh[i - 1];
-                    d = (r - (i > 1 ? hh[i - 1] * d : 0.0)) * rden[i];
+                    T r = T(0);  // d rhs_i / d y_q
+                    if (q == i + 1) r = T(6) * rh[i];
+                    if (q == i) r = T(-6) * (rh[i] + rh[i - 1]);
+                    if (q == i - 1) r = T(6) * rh[i - 1];
+                    d = (r - (i > 1 ? hh[i - 1] * d : T(0))) * rden[i];
                     pc[i] = d;
                 }
                 for (int i = n - 2; i >= 1; --i) pc[i] -= cp[i] * pc[i + 1];
@@ -1110,12 +1124,12 @@ __device__ __noinline__ void arc_finish_variants(const GroupArgs<T>& g, const Ar
                 continue;
             }
             const int jr = j - a0;
-            const double h = hh[jr], A = (x1 - ak) * rh[jr], B = (ak - x0) * rh[jr];
-            const double C = h * h * (A * A * A - A) * (1.0 / 6.0), D = h * h * (B * B * B - B) * (1.0 / 6.0);
+            const T h = hh[jr], A = T(x1 - ak) * rh[jr], B = T(ak - x0) * rh[jr];
+            const T C = h * h * (A * A * A - A) * T(1.0 / 6.0), D = h * h * (B * B * B - B) * T(1.0 / 6.0);
             for (int q = 0; q <= n; ++q) {
-                const double* pc = P + (size_t)(a0 + q) * mk;
-                const double mj = jr > 0 ? pc[jr] : 0.0, mj1 = jr + 1 < n ? pc[jr + 1] : 0.0;
-                wr[a0 + q] = T((q == jr ? A : 0.0) + (q == jr + 1 ? B : 0.0) + C * mj + D * mj1);
+                const T* pc = P + (size_t)q * ps;
+                const T mj = jr > 0 ? pc[jr] : T(0), mj1 = jr + 1 < n ? pc[jr + 1] : T(0);
+                wr[a0 + q] = (q == jr ? A : T(0)) + (q == jr + 1 ? B : T(0)) + C * mj + D * mj1;
             }
         }
     }
@@ -1650,30 +1664,36 @@ __global__ void __launch_bounds__(256) climb_apply_kernel(GroupArgs<T> g, ArcArg
 }
 
 // ---- natural cubic spline: phi_k = normalise(sum_q W_kq phi*_q) in place on sp -----------------------
-// grid (ceil(N / ts), n_str), ts threads, one site each; dynamic shared memory [K][3][ts] holds the
-// string's K images at the CTA's sites (each thread reads only its own column, so nothing waits).
+// grid (ceil(N / 32), n_str), 256 threads: 32 sites x 8 groups of output rows (row k to group k % 8).
+// Dynamic shared memory: the string's K images at the CTA's 32 sites, [K][3][32], then W [K][K] when
+// w_on_chip (else W is read through L1).  The tile is loaded whole before any row is written back.
 template <typename T>
-__global__ void __launch_bounds__(128) spline_apply_kernel(GroupArgs<T> g, ArcArgs a) {
+__global__ void __launch_bounds__(256) spline_apply_kernel(GroupArgs<T> g, ArcArgs a, int w_on_chip) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* y = reinterpret_cast<T*>(smem_raw);
-    const int str = blockIdx.y, ts = blockDim.x, tid = threadIdx.x;
+    const int str = blockIdx.y, tid = threadIdx.x, lane = tid & 31, grp = tid >> 5;
     const int K = a.str_K[str], img0 = a.str_img0[str], N = g.N;
-    const int i = blockIdx.x * ts + tid;
-    if (i >= N) return;
     const size_t M = (size_t)3 * N, mk = (size_t)a.maxK;
     const int* wc = a.wcopy + (size_t)str * mk;
-    const T* W = reinterpret_cast<const T*>(a.W) + (size_t)str * mk * mk;
-    for (int q = 0; q < K; ++q)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) y[(q * 3 + c) * ts + tid] = g.sp[(size_t)(img0 + q) * M + (size_t)c * N + i];
-    for (int k = 1; k < K - 1; ++k) {
-        if (wc[k]) continue;  // kept in place (uniform over the CTA)
-        const T* wr = W + (size_t)k * mk;
+    const T* Wg = reinterpret_cast<const T*>(a.W) + (size_t)str * mk * mk;
+    T* Ws = y + (size_t)K * 96;
+    const int i0 = blockIdx.x * 32, i = i0 + lane;
+    for (int e = tid; e < K * 96; e += 256) {  // (q, c, site): 32 consecutive sites per warp load
+        const int q = e / 96, r = e - 96 * q, c = r >> 5, l = r & 31;
+        y[e] = i0 + l < N ? g.sp[(size_t)(img0 + q) * M + (size_t)c * N + i0 + l] : T(0);
+    }
+    if (w_on_chip)
+        for (int e = tid; e < K * K; e += 256) Ws[e] = Wg[(size_t)(e / K) * mk + e % K];
+    __syncthreads();
+    if (i >= N) return;
+    for (int k = 1 + grp; k < K - 1; k += 8) {
+        if (wc[k]) continue;  // kept in place
         T u[3] = {T(0), T(0), T(0)};
+        const T* wr = w_on_chip ? Ws + (size_t)k * K : Wg + (size_t)k * mk;
         for (int q = 0; q < K; ++q) {
-            const T w = __ldg(wr + q);
+            const T w = wr[q];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) u[c] += w * y[(q * 3 + c) * ts + tid];
+            for (int c = 0; c < 3; ++c) u[c] += w * y[q * 96 + c * 32 + lane];
         }
         const T r = rsqrt_t<T>(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
         T* o = g.sp + (size_t)(img0 + k) * M + i;
@@ -2015,18 +2035,18 @@ template <typename T> void launch_climb(const GroupArgs<T>& g, const ArcArgs& a,
     climb_apply_kernel<T><<<grid, 256, 0, st>>>(g, a, hc, dt);
 }
 
-// sites per CTA of the spline apply kernel for strings of up to maxK images: the [maxK][3][ts] tile in
-// at most 200 KB of shared memory, ts a power of two in [32, 64]
-template <typename T> int spline_sites_per_cta(int maxK) {
-    int ts = 64;
-    while (ts > 32 && (size_t)maxK * 3 * ts * sizeof(T) > 200 * 1024) ts >>= 1;
-    return ts;
+// The spline apply kernel's shared memory for strings of up to maxK images: the [maxK][3][32] tile, and
+// W on chip when both fit in 200 KB.
+template <typename T> size_t spline_smem(int maxK, bool* w_on_chip) {
+    const size_t tile = (size_t)maxK * 96 * sizeof(T), w = (size_t)maxK * maxK * sizeof(T);
+    *w_on_chip = tile + w <= 200 * 1024;
+    return *w_on_chip ? tile + w : tile;
 }
 
 template <typename T> void launch_spline_apply(const GroupArgs<T>& g, const ArcArgs& a, int maxK, cudaStream_t st) {
-    const int ts = spline_sites_per_cta<T>(maxK);
-    const size_t sm = (size_t)maxK * 3 * ts * sizeof(T);
-    spline_apply_kernel<T><<<dim3((g.N + ts - 1) / ts, a.n_str), ts, sm, st>>>(g, a);
+    bool on_chip = false;
+    const size_t sm = spline_smem<T>(maxK, &on_chip);
+    spline_apply_kernel<T><<<dim3((g.N + 31) / 32, a.n_str), 256, sm, st>>>(g, a, on_chip ? 1 : 0);
 }
 
 template <typename T> void launch_rk_assemble(const GroupArgs<T>& g, const RkArgs<T>& r, int stage, cudaStream_t st) {
@@ -2057,7 +2077,7 @@ template <typename T> void launch_rk_commit(const GroupArgs<T>& g, const RkArgs<
 
 template <typename T> void launch_arc(const GroupArgs<T>& g, const ArcArgs& a, int nthr, cudaStream_t st) {
     dim3 grid(a.n_tiles + 1, a.n_kchunks, a.n_str);  // + one energy CTA per chunk
-    launch_pdl(arc_kernel<T>, grid, dim3(nthr), 0, st, g, a);
+    launch_pdl(arc_kernel<T>, grid, dim3(nthr), (size_t)a.p_dim * a.p_dim * sizeof(double), st, g, a);
 }
 
 template <typename T>
@@ -2104,6 +2124,7 @@ template <typename T> void set_smem_limits(int bytes) {
     set_dyn_smem(xinv_kernel<T, true, 5, 0>, bytes);
     set_dyn_smem(xinv_kernel<T, false, 5, 0>, bytes);
     set_dyn_smem(spline_apply_kernel<T>, 200 * 1024);
+    set_dyn_smem(arc_kernel<T>, bytes);
     if constexpr (std::is_same<T, float>::value) {
 #define SS_CASE(R)                                  \
     set_dyn_smem(xfwd128_kernel<T, R>, bytes);      \

@@ -205,3 +205,18 @@ def test_dopri5_with_spline(ss):
                                              with_energies=False)[0][0] for im in _unit(s0)])
     ref = oracle.reparam_v(evolved, spline=True)
     assert np.abs(got - ref).max() < 1e-10
+
+
+def test_kernel_timing_follows_the_mode(ss):
+    spec = W.tiny_bloch().strings[0]
+    with ss.StringMethod([_case(spec)], dt=0.1) as sm:
+        sm.set_path(0, spec.initial_path())
+        assert len(sm.time_kernels(reps=2)) == 4  # xfwd, yz, xinv, arc
+        sm.set_reparam(ss.SS_INTERP_SPLINE, True)
+        ms = sm.time_kernels(reps=2)  # xfwd, yz, xinv, climbing-image pair, arc, spline
+        assert len(ms) == 6 and (ms > 0).all()
+        sm.set_reparam(ss.SS_INTERP_LINEAR, False)
+        sm.set_integrator(ss.SS_INT_DOPRI5, 1e-6, 1e-8)
+        with pytest.raises(ss.SsError) as ei:
+            sm.time_kernels(reps=2)
+        assert ei.value.status == ss.SS_ERR_STATE
