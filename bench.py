@@ -21,6 +21,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import subprocess
 import sys
@@ -320,6 +321,15 @@ def main():
                 "launch_config": sm.launch_config(0),
                 "x_config_env": "SS_X_CONFIG={threads_xfwd}:{rows_xfwd}:{threads_xinv}:{rows_xinv}".format(**sm.launch_config(0)),
                 "alg_bytes_per_launch": alg_bytes}
+    if "yz" in names:
+        # the y/z kernel is not HBM-bound (its working set is L2-resident): its FP32 arithmetic against
+        # the FP32 (non-tensor) peak, 152 SMs x 128 FMA lanes x 2 FLOP x the maximum SM clock
+        flops = yz_flops(spec)
+        peak_tf = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        ach_tf = flops / (ms[names.index("yz")] * 1e-3) / 1e12
+        roofline["secondary"] = {"kernel": "yz", "bound": "alu", "achieved": ach_tf, "peak": peak_tf,
+                                 "unit": "TFLOP/s", "frac": ach_tf / peak_tf, "flops_per_launch": flops,
+                                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x sm_max_mhz"}
 
     line = {
         "metric": "spin-updates/s", "value": value, "unit": "spin-updates/s", "n_gpus": world,
@@ -465,6 +475,17 @@ def other_workload(binding, wl, stream, iters=20, warm=3):
     return {"value": wl.spin_updates_per_iter * iters / t, "unit": "spin-updates/s", "iterations_timed": iters,
             "strings": len(wl.strings), "spin_updates_per_iter": wl.spin_updates_per_iter,
             "ms_per_iter": 1e3 * t / iters, "kernel_ms_total": float(ms.sum())}
+
+
+def yz_flops(spec):
+    """Algorithmic FP32 operations of one y/z launch: per image pair and kx, the forward and inverse y
+    transforms of 3 nz lines of length Py at the nominal 5 P log2 P each, and per frequency the
+    z-convolution's 9 nz^2 real-by-complex products (4 FLOP each)."""
+    px, py, nz = padded(spec.nx), padded(spec.ny), spec.nz
+    pairs = (spec.n_images + 1) // 2
+    fft = 2 * px * 3 * nz * 5 * py * math.log2(py)
+    conv = px * py * 36 * nz * nz
+    return pairs * (fft + conv)
 
 
 def padded(n):
