@@ -536,6 +536,7 @@ template <typename T> RkArgs<T> rk_args(const ss_ctx* c, const Group& g) {
     r.T_int = c->opts.dt;
     r.rtol = c->rtol;
     r.atol = c->atol;
+    r.dp = dp_coefficients<T>();
     return r;
 }
 

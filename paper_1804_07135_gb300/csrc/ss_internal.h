@@ -134,6 +134,15 @@ struct RkString {
     int pad;
 };
 
+// The Dormand-Prince 5(4) tableau (Dormand and Prince, 1980) in the path's precision: stage rows a, the
+// fifth-order weights b and the error weights e = b - bhat (bhat: the embedded fourth-order weights).
+template <typename T> struct DpCoef {
+    T a[7][6];
+    T b[7];
+    T e[7];
+};
+template <typename T> DpCoef<T> dp_coefficients();
+
 // Device buffers and constants of the Runge-Kutta evolution of one size group.
 template <typename T> struct RkArgs {
     T* y0;            // [image][3][N] state at the start of the attempt
@@ -148,6 +157,7 @@ template <typename T> struct RkArgs {
     int n_sys;
     int* active;      // any system still inside its interval (written by the controller)
     double T_int, rtol, atol;
+    DpCoef<T> dp;
 };
 
 enum { kErrInvalidSpin = 1, kErrNonFinite = 2, kErrStepCollapse = 4 };

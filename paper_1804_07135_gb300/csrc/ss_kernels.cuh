@@ -1421,12 +1421,12 @@ __device__ __noinline__ void arc_finish(const GroupArgs<T>& g, const ArcArgs& a,
 // the Dormand-Prince 5(4) pair).  Per attempt, for each stage i: Y_i = y0 + hs sum_{q<i} a_iq k_q
 // (rk_assemble into sp), then the field pipeline with an identity table and the step kernel in force
 // mode gives k_i = F(Y_i) (Eq. 13); rk_finish forms y5 = y0 + hs sum b_q k_q and the squared scaled
-// error (hs sum (b_q - bhat_q) k_q / (atol + rtol max(|y0|, |y5|)))^2 per tile; rk_control (one CTA)
-// sums it per string in a fixed order, accepts when sqrt(mean) <= 1 and picks the next step; rk_commit
+// error (hs sum (b_q - bhat_q) k_q / (atol + rtol max(|y0|, |y5|)))^2 per tile; rk_control (one CTA per
+// ODE system) sums it in a fixed order, accepts when sqrt(mean) <= 1 and picks the next step; rk_commit
 // renormalises the accepted y5 into y0 (and into sp once the string's interval is complete).
 // The Dormand-Prince 5(4) coefficients (Dormand and Prince, 1980): a (rows = stages), the fifth-order
 // weights b and the embedded fourth-order weights bh.
-static __constant__ double c_dp_a[7][6] = {
+constexpr double kDpA[7][6] = {
     {0, 0, 0, 0, 0, 0},
     {1.0 / 5.0, 0, 0, 0, 0, 0},
     {3.0 / 40.0, 9.0 / 40.0, 0, 0, 0, 0},
@@ -1434,12 +1434,21 @@ static __constant__ double c_dp_a[7][6] = {
     {19372.0 / 6561.0, -25360.0 / 2187.0, 64448.0 / 6561.0, -212.0 / 729.0, 0, 0},
     {9017.0 / 3168.0, -355.0 / 33.0, 46732.0 / 5247.0, 49.0 / 176.0, -5103.0 / 18656.0, 0},
     {35.0 / 384.0, 0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0, 11.0 / 84.0}};
-static __constant__ double c_dp_b[7] = {35.0 / 384.0, 0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0,
-                                        11.0 / 84.0, 0};
-static __constant__ double c_dp_bh[7] = {5179.0 / 57600.0,    0,
-                                         7571.0 / 16695.0,    393.0 / 640.0,
-                                         -92097.0 / 339200.0, 187.0 / 2100.0,
-                                         1.0 / 40.0};
+constexpr double kDpB[7] = {35.0 / 384.0, 0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0, 11.0 / 84.0, 0};
+constexpr double kDpBh[7] = {5179.0 / 57600.0, 0, 7571.0 / 16695.0, 393.0 / 640.0, -92097.0 / 339200.0,
+                             187.0 / 2100.0, 1.0 / 40.0};
+
+// The tableau rounded once to the path's precision (the kernels receive it as a launch argument, so
+// the FP32 path does no FP64 arithmetic per element); e = b - bhat formed in FP64 first.
+template <typename T> DpCoef<T> dp_coefficients() {
+    DpCoef<T> c{};
+    for (int i = 0; i < 7; ++i) {
+        for (int j = 0; j < 6; ++j) c.a[i][j] = T(kDpA[i][j]);
+        c.b[i] = T(kDpB[i]);
+        c.e[i] = T(kDpB[i] - kDpBh[i]);
+    }
+    return c;
+}
 constexpr int kRkTile = 1024;  // components per CTA of the element-wise Runge-Kutta kernels
 
 // grid (tiles, images), 256 threads
@@ -1453,7 +1462,7 @@ __global__ void __launch_bounds__(256) rk_assemble_kernel(GroupArgs<T> g, RkArgs
     for (size_t e = (size_t)blockIdx.x * kRkTile + threadIdx.x; e < e1; e += blockDim.x) {
         T a = T(0);
 #pragma unroll
-        for (int q = 0; q < STAGE; ++q) a += T(c_dp_a[STAGE][q]) * r.k[q * stride + base + e];
+        for (int q = 0; q < STAGE; ++q) a += r.dp.a[STAGE][q] * r.k[q * stride + base + e];
         g.sp[base + e] = r.y0[base + e] + hs * a;
     }
 }
@@ -1467,6 +1476,7 @@ __global__ void __launch_bounds__(256) rk_finish_kernel(GroupArgs<T> g, RkArgs<T
     const RkString& S = r.st[r.img_sys[im]];
     const T hs = S.done ? T(0) : T(S.hs);
     const T rtol = T(r.rtol), atol = T(r.atol);
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *r.active = 0;  // the controllers set it again
     T v[1] = {T(0)};
     const size_t e1 = min(M, (size_t)(blockIdx.x + 1) * kRkTile);
     for (size_t e = (size_t)blockIdx.x * kRkTile + threadIdx.x; e < e1; e += blockDim.x) {
@@ -1474,8 +1484,8 @@ __global__ void __launch_bounds__(256) rk_finish_kernel(GroupArgs<T> g, RkArgs<T
 #pragma unroll
         for (int q = 0; q < 7; ++q) {
             const T kq = r.k[q * stride + base + e];
-            b5 += T(c_dp_b[q]) * kq;
-            d4 += T(c_dp_b[q] - c_dp_bh[q]) * kq;
+            b5 += r.dp.b[q] * kq;
+            d4 += r.dp.e[q] * kq;
         }
         const T y0 = r.y0[base + e];
         const T y5 = y0 + hs * b5;
@@ -1489,75 +1499,71 @@ __global__ void __launch_bounds__(256) rk_finish_kernel(GroupArgs<T> g, RkArgs<T
     if (threadIdx.x == 0) r.errp[(size_t)im * r.n_tiles + blockIdx.x] = out[0];
 }
 
-// One CTA: per ODE system (a warp each), the error norm sqrt(sum / (3N x its images)) over its partials,
-// then the step-size control.  begin != 0 opens a new interval instead (t = 0, first step cut to T).
+// grid (n_sys), 256 threads: the system's error norm sqrt(sum / (3N x its images)) over its partials
+// (a fixed order), then the step-size control by thread 0, which also marks *r.active (cleared by
+// rk_finish) while the system is inside its interval.  begin != 0 opens a new interval instead (t = 0,
+// first step cut to T) and marks every system active.
 template <typename T>
 __global__ void __launch_bounds__(256) rk_control_kernel(GroupArgs<T> g, RkArgs<T> r, int begin) {
-    __shared__ int any;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    if (threadIdx.x == 0) any = 0;
-    __syncthreads();
+    __shared__ double red[32];
+    const int s = blockIdx.x;
     const double T_int = r.T_int;
-    for (int s = warp; s < r.n_sys; s += nwarp) {
-        RkString S = r.st[s];
-        if (begin) {
-            if (lane == 0) {
-                S.t = 0.0;
-                S.done = 0;
-                S.accepted = 0;
-                S.attempts = 0;
-                S.hs = S.step < T_int ? S.step : T_int;
-                r.st[s] = S;
-                atomicOr(&any, 1);
-            }
-            continue;
-        }
-        if (S.done) {  // finished in an earlier attempt: nothing to commit this time
-            if (lane == 0 && S.accepted) {
-                S.accepted = 0;
-                r.st[s] = S;
-            }
-            continue;
-        }
-        const int n = r.sys_cnt[s] * r.n_tiles;
-        const double* ep = r.errp + (size_t)r.sys_img0[s] * r.n_tiles;
-        double v = 0.0;
-        for (int i = lane; i < n; i += 32) v += ep[i];
-        v = warp_sum_d(v);
-        if (lane == 0) {
-            const double err = sqrt(v / (3.0 * (double)g.N * (double)r.sys_cnt[s]));
-            S.err = err;
-            if (++S.attempts > 100000) {
-                atomicOr(g.err, kErrStepCollapse);
-                S.done = 1;
-                S.accepted = 0;
-            } else {
-                // stages that overflowed (F grows like |s|^3 off the unit sphere) give a non-finite
-                // norm: a rejection with the smallest factor
-                double fac = !isfinite(err) ? 0.2 : err > 0.0 ? 0.9 * pow(err, -0.2) : 5.0;
-                if (fac < 0.2) fac = 0.2;
-                if (err <= 1.0) {
-                    if (fac > 5.0) fac = 5.0;
-                    S.t = S.hs == T_int - S.t ? T_int : S.t + S.hs;
-                    S.accepted = 1;
-                    ++S.acc;
-                } else {
-                    if (fac > 1.0) fac = 1.0;
-                    S.accepted = 0;
-                    ++S.rej;
-                }
-                S.step = S.hs * fac;
-                if (S.t >= T_int)
-                    S.done = 1;
-                else
-                    S.hs = S.step < T_int - S.t ? S.step : T_int - S.t;
-            }
+    RkString S = r.st[s];
+    if (begin) {
+        if (threadIdx.x == 0) {
+            S.t = 0.0;
+            S.done = 0;
+            S.accepted = 0;
+            S.attempts = 0;
+            S.hs = S.step < T_int ? S.step : T_int;
             r.st[s] = S;
-            if (!S.done) atomicOr(&any, 1);
+            if (s == 0) *r.active = 1;
         }
+        return;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) *r.active = any;
+    if (S.done) {  // finished in an earlier attempt: nothing to commit this time (uniform over the CTA)
+        if (threadIdx.x == 0 && S.accepted) {
+            S.accepted = 0;
+            r.st[s] = S;
+        }
+        return;
+    }
+    const int n = r.sys_cnt[s] * r.n_tiles;
+    const double* ep = r.errp + (size_t)r.sys_img0[s] * r.n_tiles;
+    double v[1] = {0.0};
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v[0] += ep[i];
+    block_reduce_d<1>(v, red);
+    if (threadIdx.x == 0) {
+        const double err = sqrt(v[0] / (3.0 * (double)g.N * (double)r.sys_cnt[s]));
+        S.err = err;
+        if (++S.attempts > 100000) {
+            atomicOr(g.err, kErrStepCollapse);
+            S.done = 1;
+            S.accepted = 0;
+        } else {
+            // stages that overflowed (F grows like |s|^3 off the unit sphere) give a non-finite norm:
+            // a rejection with the smallest factor
+            double fac = !isfinite(err) ? 0.2 : err > 0.0 ? 0.9 * pow(err, -0.2) : 5.0;
+            if (fac < 0.2) fac = 0.2;
+            if (err <= 1.0) {
+                if (fac > 5.0) fac = 5.0;
+                S.t = S.hs == T_int - S.t ? T_int : S.t + S.hs;
+                S.accepted = 1;
+                ++S.acc;
+            } else {
+                if (fac > 1.0) fac = 1.0;
+                S.accepted = 0;
+                ++S.rej;
+            }
+            S.step = S.hs * fac;
+            if (S.t >= T_int)
+                S.done = 1;
+            else
+                S.hs = S.step < T_int - S.t ? S.step : T_int - S.t;
+        }
+        r.st[s] = S;
+        if (!S.done) atomicOr(r.active, 1);
+    }
 }
 
 // grid (site tiles of 256, images), 256 threads: y0 = normalise(y5) per site where the attempt was
@@ -2068,7 +2074,7 @@ template <typename T> void launch_rk_finish(const GroupArgs<T>& g, const RkArgs<
 
 template <typename T>
 void launch_rk_control(const GroupArgs<T>& g, const RkArgs<T>& r, int begin, cudaStream_t st) {
-    rk_control_kernel<T><<<1, 256, 0, st>>>(g, r, begin);
+    rk_control_kernel<T><<<r.n_sys, 256, 0, st>>>(g, r, begin);
 }
 
 template <typename T> void launch_rk_commit(const GroupArgs<T>& g, const RkArgs<T>& r, cudaStream_t st) {
@@ -2182,6 +2188,7 @@ void launch_interp_identity(InterpEntry* tab, int img0, int K, cudaStream_t st) 
     template void launch_xinv_step_climb<T>(const GroupArgs<T>&, bool, T, T*, int, size_t, cudaStream_t);       \
     template void launch_climb<T>(const GroupArgs<T>&, const ArcArgs&, T, const T*, cudaStream_t);             \
     template void launch_spline_apply<T>(const GroupArgs<T>&, const ArcArgs&, int, cudaStream_t);              \
+    template DpCoef<T> dp_coefficients<T>();                                                                  \
     template void launch_rk_assemble<T>(const GroupArgs<T>&, const RkArgs<T>&, int, cudaStream_t);             \
     template void launch_rk_finish<T>(const GroupArgs<T>&, const RkArgs<T>&, cudaStream_t);                    \
     template void launch_rk_control<T>(const GroupArgs<T>&, const RkArgs<T>&, int, cudaStream_t);                \
