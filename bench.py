@@ -191,6 +191,23 @@ def ncu_traffic(kernel: str, units: int):
     return None
 
 
+def max_over_ranks(pg, values, device):
+    """Each timing's maximum over the ranks (the slowest replica sets the job's time); pg is
+    torch.distributed or None for one rank."""
+    if pg is None:
+        return list(values)
+    import torch
+    t = torch.tensor(values, device=device, dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return t.tolist()
+
+
+def whole_job_value(units_per_rank, world, seconds):
+    """Weak scaling: every rank runs its own replica of the workload, so the job processes
+    world x units in the slowest rank's time."""
+    return units_per_rank * world / seconds
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -279,15 +296,10 @@ def main():
         barrier_all()
         t_e2e = timed(path_host, args.steps)
         barrier_all()
-    step_s = float(np.mean(t_dev))
-    e2e_s = float(np.mean(t_e2e))
-    if pg:
-        t = torch.tensor([step_s, e2e_s], device="cuda", dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        step_s, e2e_s = t.tolist()
+    step_s, e2e_s = max_over_ranks(pg, [float(np.mean(t_dev)), float(np.mean(t_e2e))], "cuda")
     units = spec.n_sites * spec.n_images * n_iter
-    value = units * world / step_s
-    e2e_value = units * world / e2e_s
+    value = whole_job_value(units, world, step_s)
+    e2e_value = whole_job_value(units, world, e2e_s)
     dE, kmax = sm.barrier(0)
 
     if rank != 0:
