@@ -72,6 +72,8 @@ def _load():
             "or_llg_run": (i, [mp, i, i, d, d, dp, dp]),
             "or_llg_run_rk": (i, [mp, i, i, d, d, d, d, i, dp, dp, dp, P(ctypes.c_long)]),
             "or_dp_tableau": (None, [dp, dp, dp]),
+            "or_rkf_tableau": (None, [dp, dp, dp]),
+            "or_string_run_rk_method": (i, [mp, i, i, d, d, d, i, i, dp, dp, dp, P(ctypes.c_long)]),
             "or_barrier": (d, [i, dp, P(i)]),
             "or_energy_param_grad": (None, [mp, dp, dp]),
             "or_max_threads": (i, []),
@@ -219,20 +221,22 @@ def string_run_v(m: OracleModel, path, n_iter: int, dt: float, spline: bool = Fa
 
 
 def string_run_rk(m: OracleModel, path, n_iter: int, T: float, rtol: float = 1e-6, atol: float = 1e-8,
-                  step=None, with_energies: bool = True, per_image: bool = False):
-    """Sec. III loop with the Dormand-Prince 5(4) evolution over T per iteration, the whole string one
-    ODE system (per_image=False) or every image its own (per_image=True).  Returns (final path,
-    energies or None, carried step, (accepted, rejected)); with per_image the step is an array of K
-    steps and the counts an array of K (accepted, rejected) rows."""
+                  step=None, with_energies: bool = True, per_image: bool = False, method: str = "dopri5"):
+    """Sec. III loop with an adaptive embedded Runge-Kutta evolution over T per iteration: the
+    Dormand-Prince 5(4) pair (method="dopri5") or the Runge-Kutta-Fehlberg 4(5) pair ("rkf45"); the
+    whole string one ODE system (per_image=False) or every image its own (per_image=True).  Returns
+    (final path, energies or None, carried step, (accepted, rejected)); with per_image the step is an
+    array of K steps and the counts an array of K (accepted, rejected) rows."""
     phi = _f64(path).copy()
     K = phi.shape[0]
     n_sys = K if per_image else 1
     e = np.zeros(K) if with_energies else None
     h = np.full(n_sys, float(T)) if step is None else np.array(np.broadcast_to(np.asarray(step, float), (n_sys,)))
     counts = (ctypes.c_long * (2 * n_sys))()
-    rc = _load().or_string_run_rk(ctypes.byref(m), K, int(n_iter), float(T), float(rtol), float(atol),
-                                  int(bool(per_image)), _ptr(h), _ptr(phi), _ptr(e) if with_energies else None,
-                                  counts)
+    meth = {"dopri5": 0, "rkf45": 1}[method]
+    rc = _load().or_string_run_rk_method(ctypes.byref(m), K, int(n_iter), float(T), float(rtol), float(atol), meth,
+                                         int(bool(per_image)), _ptr(h), _ptr(phi), _ptr(e) if with_energies else None,
+                                         counts)
     if rc == -1:
         raise MemoryError("oracle RK string run: out of memory")
     if rc != 0:
@@ -282,6 +286,13 @@ def dp_tableau():
     a, b, bh = np.zeros((7, 6)), np.zeros(7), np.zeros(7)
     _load().or_dp_tableau(_ptr(a), _ptr(b), _ptr(bh))
     return a, b, bh
+
+
+def rkf_tableau():
+    """The Runge-Kutta-Fehlberg 4(5) coefficients the oracle uses: (a[6][5], b4[6], b5[6])."""
+    a, b4, b5 = np.zeros((6, 5)), np.zeros(6), np.zeros(6)
+    _load().or_rkf_tableau(_ptr(a), _ptr(b4), _ptr(b5))
+    return a, b4, b5
 
 
 def barrier(energies_) -> tuple[float, int]:

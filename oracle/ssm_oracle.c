@@ -549,6 +549,55 @@ void or_dp_tableau(double a[7][6], double b[7], double bhat[7]) {
     memcpy(bhat, DP_BHAT, sizeof(DP_BHAT));
 }
 
+/* The Runge-Kutta-Fehlberg 4(5) pair (Fehlberg, 1969; Sec. III names it beside Dormand-Prince): six
+ * stages, the fourth-order weights B4 (the solution carried forward, as in Fehlberg's method) and the
+ * fifth-order weights B5 (the error estimate y5 - y4). */
+static const double RKF_A[6][5] = {
+    {0, 0, 0, 0, 0},
+    {1.0 / 4.0, 0, 0, 0, 0},
+    {3.0 / 32.0, 9.0 / 32.0, 0, 0, 0},
+    {1932.0 / 2197.0, -7200.0 / 2197.0, 7296.0 / 2197.0, 0, 0},
+    {439.0 / 216.0, -8.0, 3680.0 / 513.0, -845.0 / 4104.0, 0},
+    {-8.0 / 27.0, 2.0, -3544.0 / 2565.0, 1859.0 / 4104.0, -11.0 / 40.0}};
+static const double RKF_B4[6] = {25.0 / 216.0, 0, 1408.0 / 2565.0, 2197.0 / 4104.0, -1.0 / 5.0, 0};
+static const double RKF_B5[6] = {16.0 / 135.0, 0, 6656.0 / 12825.0, 28561.0 / 56430.0, -9.0 / 50.0, 2.0 / 55.0};
+
+void or_rkf_tableau(double a[6][5], double b4[6], double b5[6]) {
+    memcpy(a, RKF_A, sizeof(RKF_A));
+    memcpy(b4, RKF_B4, sizeof(RKF_B4));
+    memcpy(b5, RKF_B5, sizeof(RKF_B5));
+}
+
+/* An embedded pair as the interval loop uses it: stage rows a (stage i uses a[i][0..i-1]), the weights
+ * of the carried solution and the error weights (difference of the two solutions' weights). */
+typedef struct {
+    int stages;
+    double a[7][6];
+    double b[7];
+    double e[7];
+} rk_pair;
+
+static rk_pair pair_of(int method) {
+    rk_pair p;
+    memset(&p, 0, sizeof p);
+    if (method == 0) {
+        p.stages = 7;
+        memcpy(p.a, DP_A, sizeof(DP_A));
+        for (int i = 0; i < 7; ++i) {
+            p.b[i] = DP_B[i];
+            p.e[i] = DP_B[i] - DP_BHAT[i];
+        }
+    } else {
+        p.stages = 6;
+        for (int i = 0; i < 6; ++i) {
+            for (int j = 0; j < 5; ++j) p.a[i][j] = RKF_A[i][j];
+            p.b[i] = RKF_B4[i];
+            p.e[i] = RKF_B5[i] - RKF_B4[i];
+        }
+    }
+    return p;
+}
+
 /* The right-hand side for every image of y (K images of M = 3N components) into f: F of Eq. 13 when
  * llg is NULL, else the reduced LLG of Eq. 9, f = -a (s x h) + b (h - (s.h) s) with a = llg[0] =
  * 1 / (1 + alpha^2) and b = llg[1] = alpha / (1 + alpha^2) (-s x (s x h) = h - (s.h) s). */
@@ -579,9 +628,9 @@ static void force_all(const or_model* m, const double* table, int K, const doubl
 
 /* One interval [0, T] of the system of Ks images at phi (Ks * 3N components), DP 5(4) as above;
  * kk (7 systems), ys, y5 and hb are scratch of the system's size. */
-static int rk_interval(const or_model* m, const double* table, const double* llg, int Ks, double T, double rtol,
-                       double atol, double* step_io, double* phi, double* kk, double* ys, double* y5, double* hb,
-                       long* acc, long* rej) {
+static int rk_interval(const or_model* m, const double* table, const double* llg, const rk_pair* pr, int Ks,
+                       double T, double rtol, double atol, double* step_io, double* phi, double* kk, double* ys,
+                       double* y5, double* hb, long* acc, long* rej) {
     const int N = m->nx * m->ny * m->nz;
     const size_t M = (size_t)3 * N, L = M * (size_t)Ks;
     double step = *step_io, t = 0.0;
@@ -591,10 +640,10 @@ static int rk_interval(const or_model* m, const double* table, const double* llg
         const double hs = step < T - t ? step : T - t;
         if (!have_k1) force_all(m, table, Ks, phi, hb, kk, llg);
         have_k1 = 1;
-        for (int st = 1; st < 7; ++st) {
+        for (int st = 1; st < pr->stages; ++st) {
             for (size_t j = 0; j < L; ++j) {
                 double a = 0.0;
-                for (int q = 0; q < st; ++q) a += DP_A[st][q] * kk[q * L + j];
+                for (int q = 0; q < st; ++q) a += pr->a[st][q] * kk[q * L + j];
                 ys[j] = phi[j] + hs * a;
             }
             force_all(m, table, Ks, ys, hb, kk + st * L, llg);
@@ -602,9 +651,9 @@ static int rk_interval(const or_model* m, const double* table, const double* llg
         double e2 = 0.0;
         for (size_t j = 0; j < L; ++j) {
             double b5 = 0.0, e = 0.0;
-            for (int q = 0; q < 7; ++q) {
-                b5 += DP_B[q] * kk[q * L + j];
-                e += (DP_B[q] - DP_BHAT[q]) * kk[q * L + j];
+            for (int q = 0; q < pr->stages; ++q) {
+                b5 += pr->b[q] * kk[q * L + j];
+                e += pr->e[q] * kk[q * L + j];
             }
             y5[j] = phi[j] + hs * b5;
             const double ay = fabs(phi[j]), a5 = fabs(y5[j]);
@@ -639,8 +688,9 @@ static int rk_interval(const or_model* m, const double* table, const double* llg
 
 /* The Runge-Kutta driver: n_iter intervals of T of the right-hand side chosen by llg (see force_all),
  * each followed by the reparametrisation when reparam != 0. */
-static int run_rk(const or_model* m, int K, int n_iter, double T, double rtol, double atol, int per_image,
+static int run_rk(const or_model* m, int K, int n_iter, double T, double rtol, double atol, int method, int per_image,
                   const double* llg, int reparam, double* step_io, double* phi, double* energies, long* counts) {
+    const rk_pair pr = pair_of(method);
     const int N = m->nx * m->ny * m->nz;
     const size_t M = (size_t)3 * N, L = M * (size_t)K;
     const int n_sys = per_image ? K : 1, Ks = per_image ? 1 : K;
@@ -667,8 +717,8 @@ static int run_rk(const or_model* m, int K, int n_iter, double T, double rtol, d
     int rc = 0;
     for (int it = 0; it < n_iter && rc == 0; ++it) {
         for (int q = 0; q < n_sys && rc == 0; ++q)
-            rc = rk_interval(m, table, llg, Ks, T, rtol, atol, step_io + q, phi + q * Ls, kk, ys, y5, hb, &cnt[2 * q],
-                             &cnt[2 * q + 1]);
+            rc = rk_interval(m, table, llg, &pr, Ks, T, rtol, atol, step_io + q, phi + q * Ls, kk, ys, y5, hb,
+                             &cnt[2 * q], &cnt[2 * q + 1]);
         if (rc) break;
         if (reparam) {
             memcpy(ys, phi, sizeof(double) * L);
@@ -694,7 +744,14 @@ static int run_rk(const or_model* m, int K, int n_iter, double T, double rtol, d
 
 int or_string_run_rk(const or_model* m, int K, int n_iter, double T, double rtol, double atol, int per_image,
                      double* step_io, double* phi, double* energies, long* counts) {
-    return run_rk(m, K, n_iter, T, rtol, atol, per_image, NULL, 1, step_io, phi, energies, counts);
+    return run_rk(m, K, n_iter, T, rtol, atol, 0, per_image, NULL, 1, step_io, phi, energies, counts);
+}
+
+/* As or_string_run_rk with the pair chosen by method: 0 Dormand-Prince 5(4), 1 Runge-Kutta-Fehlberg 4(5)
+ * (the fourth-order solution carried forward). */
+int or_string_run_rk_method(const or_model* m, int K, int n_iter, double T, double rtol, double atol, int method,
+                            int per_image, double* step_io, double* phi, double* energies, long* counts) {
+    return run_rk(m, K, n_iter, T, rtol, atol, method, per_image, NULL, 1, step_io, phi, energies, counts);
 }
 
 /* ---- precessional dynamics (Eq. 9) ------------------------------------------------------------------
@@ -745,7 +802,7 @@ int or_llg_run(const or_model* m, int K, int n_steps, double dt, double alpha, d
 int or_llg_run_rk(const or_model* m, int K, int n_iter, double T, double alpha, double rtol, double atol,
                   int per_image, double* step_io, double* phi, double* energies, long* counts) {
     const double llg[2] = {1.0 / (1.0 + alpha * alpha), alpha / (1.0 + alpha * alpha)};
-    return run_rk(m, K, n_iter, T, rtol, atol, per_image, llg, 0, step_io, phi, energies, counts);
+    return run_rk(m, K, n_iter, T, rtol, atol, 0, per_image, llg, 0, step_io, phi, energies, counts);
 }
 
 /* Sec. III: the barrier is the energy of the highest image relative to the first image.  Ties go

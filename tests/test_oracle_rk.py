@@ -118,3 +118,50 @@ def test_overflowing_attempt_is_rejected_and_recovers():
     assert rej >= 1 and step > 0
     assert abs(math.atan2(phi[0, 0, 0], phi[0, 0, 2])) < 1e-6
     assert abs(abs(math.atan2(phi[1, 0, 0], phi[1, 0, 2])) - math.pi) < 1e-6
+
+
+C6 = np.array([0, 1 / 4, 3 / 8, 12 / 13, 1, 1 / 2])
+
+
+def test_fehlberg_order_conditions():
+    a, b4, b5 = oracle.rkf_tableau()
+    A = np.zeros((6, 6))
+    A[:, :5] = a
+    np.testing.assert_allclose(A.sum(1), C6, atol=1e-15)
+    for w, order in ((b4, 4), (b5, 5)):
+        assert abs(w.sum() - 1) < 1e-15
+        for p in range(1, order):
+            assert abs(w @ C6 ** p - 1 / (p + 1)) < 1e-14, (order, p)
+        assert abs(w @ (A @ C6) - 1 / 6) < 1e-14
+        assert abs(w @ (A @ C6 ** 2) - 1 / 12) < 1e-14
+        assert abs(w @ (C6 * (A @ C6)) - 1 / 8) < 1e-14
+        assert abs(w @ (A @ (A @ C6)) - 1 / 24) < 1e-14
+    assert abs(b5 @ (A @ (A @ (A @ C6))) - 1 / 120) < 1e-14
+    assert abs(b5 @ C6 ** 4 - 1 / 5) < 1e-14
+    assert abs(b4 @ C6 ** 4 - 1 / 5) > 1e-5  # b4 is fourth order only
+
+
+@pytest.mark.parametrize("rtol", [1e-6, 1e-9])
+def test_fehlberg_lone_spin_closed_form(rtol):
+    K, T, n = 0.7, 0.5, 6
+    m = oracle.model(1, 1, 1, 0.0, 0.0, K, 0.0)
+    th0 = [1.0, 2.0]
+    phi, _, _, (acc, rej) = oracle.string_run_rk(m, _lone_spins(th0), n, T, rtol=rtol, atol=rtol * 1e-2,
+                                                 method="rkf45")
+    for k, t0 in enumerate(th0):
+        want = math.atan2(math.tan(t0) * math.exp(-2 * K * n * T), 1.0)
+        want = want + math.pi if t0 > math.pi / 2 else want
+        got = math.atan2(phi[k, 0, 0], phi[k, 0, 2])
+        assert abs(got - want) < 100 * rtol, (rtol, got - want)
+    assert acc >= n
+
+
+def test_fehlberg_and_dormand_prince_agree_within_tolerance():
+    m = oracle.model(4, 4, 1, 1.0, 0.3, 0.05, 0.02)
+    rng = np.random.default_rng(8)
+    path = rng.standard_normal((3, 16, 3))
+    path /= np.linalg.norm(path, axis=-1, keepdims=True)
+    a, _, _, ca = oracle.string_run_rk(m, path, 2, 0.5, 1e-9, 1e-11)
+    b, _, _, cb = oracle.string_run_rk(m, path, 2, 0.5, 1e-9, 1e-11, method="rkf45")
+    assert np.abs(a - b).max() < 1e-6
+    assert ca != cb  # different pairs take different step sequences
