@@ -163,7 +163,7 @@ ss_status ss_field_noalloc(int nx, int ny, int nz, double J, double D, double K,
 ss_status ss_launch_config(const ss_ctx* ctx, int string, int out[8]);
 
 /* How ss_step evolves the images between reparametrisations (Sec. III). */
-enum { SS_INT_EULER = 0, SS_INT_DOPRI5 = 1, SS_INT_DOPRI5_IMAGE = 2 };
+enum { SS_INT_EULER = 0, SS_INT_DOPRI5 = 1, SS_INT_DOPRI5_IMAGE = 2, SS_INT_RKF45 = 3, SS_INT_RKF45_IMAGE = 4 };
 
 /* Chooses the evolution of the images.
  *   SS_INT_EULER (the default): one projected-Euler step of length opts.dt per iteration (Eqs. 10, 13).
@@ -172,6 +172,9 @@ enum { SS_INT_EULER = 0, SS_INT_DOPRI5 = 1, SS_INT_DOPRI5_IMAGE = 2 };
  *   reduced interval opts.dt per iteration, either the whole string as one ODE system (DOPRI5: one
  *   error norm and one step per string) or every image as its own (DOPRI5_IMAGE: a norm and a step per
  *   image; the images do not interact between reparametrisations).
+ *   SS_INT_RKF45, SS_INT_RKF45_IMAGE: the same with the Runge-Kutta-Fehlberg 4(5) pair (six stages, the
+ *   fourth-order solution carried forward, the fifth-order one estimating the error), which Sec. III
+ *   names beside Dormand-Prince.
  * An attempt is accepted when sqrt(mean_j (e_j / (atol + rtol max(|y_j|, |y5_j|)))^2) <= 1 over the
  * system's components (e = the 5th- minus the 4th-order increment).  The next step is
  * step * clamp(0.9 err^(-1/5), 0.2, 5), at most 1 after a rejection, and 0.2 after an attempt whose
@@ -188,7 +191,7 @@ ss_status ss_set_integrator(ss_ctx* ctx, int kind, double rtol, double atol);
 
 /* Adaptive-integrator state of `string`: for image = -1 the smallest carried step and the accepted and
  * rejected attempts summed over the string's systems; for image >= 0 those of the system holding that
- * image (the string's own under SS_INT_DOPRI5).  Counts run from the last ss_set_path or
+ * image (the string's own under the whole-string kinds).  Counts run from the last ss_set_path or
  * ss_set_integrator; opts.dt and zeros under SS_INT_EULER.  Synchronises. */
 ss_status ss_integrator_state(ss_ctx* ctx, int string, int image, double* step, long long* accepted,
                               long long* rejected);

@@ -129,7 +129,7 @@ struct ss_ctx {
     std::vector<void*> allocs;
     cudaGraphExec_t graph1 = nullptr, graphN = nullptr;
     int graphN_iters = 64;
-    int integrator = 0;  // SS_INT_EULER, SS_INT_DOPRI5 or SS_INT_DOPRI5_IMAGE
+    int integrator = 0;  // SS_INT_EULER or one of the Runge-Kutta kinds
     int interp = 0;      // SS_INTERP_LINEAR or SS_INTERP_SPLINE
     int climb = 0;       // climbing image on
     int dynamics = 0;    // SS_DYN_STRING or SS_DYN_LLG
@@ -513,6 +513,10 @@ template <typename T> int time_entries(ss_ctx* c, Group& g, int which_only) {
 }
 
 // ---- adaptive Runge-Kutta evolution (Sec. III, Dormand-Prince 5(4)) -------------------------------------
+// The Runge-Kutta kinds: the pair (0 Dormand-Prince, 1 Runge-Kutta-Fehlberg) and the control granularity.
+int rk_method(const ss_ctx* c) { return c->integrator == SS_INT_RKF45 || c->integrator == SS_INT_RKF45_IMAGE; }
+bool rk_per_image(int kind) { return kind == SS_INT_DOPRI5_IMAGE || kind == SS_INT_RKF45_IMAGE; }
+
 RkString rk_fresh(const ss_ctx* c) {
     RkString r{};
     r.step = c->opts.dt;
@@ -536,7 +540,7 @@ template <typename T> RkArgs<T> rk_args(const ss_ctx* c, const Group& g) {
     r.T_int = c->opts.dt;
     r.rtol = c->rtol;
     r.atol = c->atol;
-    r.dp = dp_coefficients<T>();
+    r.dp = dp_coefficients<T>(rk_method(c));
     return r;
 }
 
@@ -586,10 +590,10 @@ ss_status rk_setup(ss_ctx* c, Group& g, bool per_image) {
 
 // The controller states of string r: one system, or one per image.
 int rk_first_sys(const ss_ctx* c, const StringRec& r) {
-    return c->integrator == SS_INT_DOPRI5_IMAGE ? r.img0 : r.local;
+    return rk_per_image(c->integrator) ? r.img0 : r.local;
 }
 int rk_sys_count(const ss_ctx* c, const StringRec& r) {
-    return c->integrator == SS_INT_DOPRI5_IMAGE ? r.d.n_images : 1;
+    return rk_per_image(c->integrator) ? r.d.n_images : 1;
 }
 
 // n_iter iterations: per iteration every string integrates over opts.dt with Dormand-Prince attempts (one
@@ -618,7 +622,7 @@ template <typename T> ss_status rk_iterations(ss_ctx* c, int n_iter) {
                 ai.interp = g.interp_ident;
                 RkArgs<T> r = rk_args<T>(c, g);
                 const size_t stride = (size_t)3 * g.N * g.n_img;
-                for (int st = 0; st < 7; ++st) {
+                for (int st = 0; st < r.dp.stages; ++st) {
                     launch_rk_assemble<T>(ai, r, st, c->cs);
                     launch_xfwd<T>(ai, g.dipole, g.thr_a, g.smem_a, c->cs);
                     if (g.dipole) launch_yz<T>(ai, g.thr_b, g.smem_b, c->cs);
@@ -968,7 +972,8 @@ ss_status ss_set_path(ss_ctx* c, int string, const void* spins, int dtype, int o
 
 ss_status ss_set_integrator(ss_ctx* c, int kind, double rtol, double atol) {
     if (!c) return SS_ERR_INVALID_ARG;
-    if (kind != SS_INT_EULER && kind != SS_INT_DOPRI5 && kind != SS_INT_DOPRI5_IMAGE)
+    if (kind != SS_INT_EULER && kind != SS_INT_DOPRI5 && kind != SS_INT_DOPRI5_IMAGE && kind != SS_INT_RKF45 &&
+        kind != SS_INT_RKF45_IMAGE)
         return fail(c, SS_ERR_INVALID_ARG, "unknown integrator %d", kind);
     if (kind != SS_INT_EULER && !(rtol > 0.0 && atol > 0.0 && std::isfinite(rtol) && std::isfinite(atol)))
         return fail(c, SS_ERR_INVALID_ARG, "rtol and atol must be positive and finite");
@@ -977,7 +982,7 @@ ss_status ss_set_integrator(ss_ctx* c, int kind, double rtol, double atol) {
     TRY(enter(c));
     if (kind != SS_INT_EULER) {
         if (!c->h_active) CUDA_TRY(c, cudaHostAlloc((void**)&c->h_active, c->groups.size() * sizeof(int), cudaHostAllocDefault));
-        for (Group& g : c->groups) TRY(rk_setup(c, g, kind == SS_INT_DOPRI5_IMAGE));
+        for (Group& g : c->groups) TRY(rk_setup(c, g, rk_per_image(kind)));
         c->rtol = rtol;
         c->atol = atol;
     }

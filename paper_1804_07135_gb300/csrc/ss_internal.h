@@ -134,14 +134,18 @@ struct RkString {
     int pad;
 };
 
-// The Dormand-Prince 5(4) tableau (Dormand and Prince, 1980) in the path's precision: stage rows a, the
-// fifth-order weights b and the error weights e = b - bhat (bhat: the embedded fourth-order weights).
+// An embedded Runge-Kutta pair in the path's precision: `stages` stage rows a (stage i uses a[i][0..i-1]),
+// the weights b of the solution carried forward and the error weights e (difference of the two
+// solutions' weights).  method 0: Dormand-Prince 5(4) (Dormand and Prince, 1980; 7 stages, the
+// fifth-order solution carried); method 1: Runge-Kutta-Fehlberg 4(5) (Fehlberg, 1969; 6 stages, the
+// fourth-order solution carried).
 template <typename T> struct DpCoef {
+    int stages;
     T a[7][6];
     T b[7];
     T e[7];
 };
-template <typename T> DpCoef<T> dp_coefficients();
+template <typename T> DpCoef<T> dp_coefficients(int method);
 
 // Device buffers and constants of the Runge-Kutta evolution of one size group.
 template <typename T> struct RkArgs {

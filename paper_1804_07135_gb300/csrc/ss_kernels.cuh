@@ -1438,14 +1438,35 @@ constexpr double kDpB[7] = {35.0 / 384.0, 0, 500.0 / 1113.0, 125.0 / 192.0, -218
 constexpr double kDpBh[7] = {5179.0 / 57600.0, 0, 7571.0 / 16695.0, 393.0 / 640.0, -92097.0 / 339200.0,
                              187.0 / 2100.0, 1.0 / 40.0};
 
-// The tableau rounded once to the path's precision (the kernels receive it as a launch argument, so
-// the FP32 path does no FP64 arithmetic per element); e = b - bhat formed in FP64 first.
-template <typename T> DpCoef<T> dp_coefficients() {
+// The Runge-Kutta-Fehlberg 4(5) coefficients (Fehlberg, 1969): a (rows = stages), the fourth-order
+// weights b4 (carried forward) and the fifth-order weights b5.
+constexpr double kRkfA[6][5] = {{0, 0, 0, 0, 0},
+                                {1.0 / 4.0, 0, 0, 0, 0},
+                                {3.0 / 32.0, 9.0 / 32.0, 0, 0, 0},
+                                {1932.0 / 2197.0, -7200.0 / 2197.0, 7296.0 / 2197.0, 0, 0},
+                                {439.0 / 216.0, -8.0, 3680.0 / 513.0, -845.0 / 4104.0, 0},
+                                {-8.0 / 27.0, 2.0, -3544.0 / 2565.0, 1859.0 / 4104.0, -11.0 / 40.0}};
+constexpr double kRkfB4[6] = {25.0 / 216.0, 0, 1408.0 / 2565.0, 2197.0 / 4104.0, -1.0 / 5.0, 0};
+constexpr double kRkfB5[6] = {16.0 / 135.0, 0, 6656.0 / 12825.0, 28561.0 / 56430.0, -9.0 / 50.0, 2.0 / 55.0};
+
+// The pair rounded once to the path's precision (the kernels receive it as a launch argument, so the
+// FP32 path does no FP64 arithmetic per element); error weights formed in FP64 first.
+template <typename T> DpCoef<T> dp_coefficients(int method) {
     DpCoef<T> c{};
-    for (int i = 0; i < 7; ++i) {
-        for (int j = 0; j < 6; ++j) c.a[i][j] = T(kDpA[i][j]);
-        c.b[i] = T(kDpB[i]);
-        c.e[i] = T(kDpB[i] - kDpBh[i]);
+    if (method == 0) {
+        c.stages = 7;
+        for (int i = 0; i < 7; ++i) {
+            for (int j = 0; j < 6; ++j) c.a[i][j] = T(kDpA[i][j]);
+            c.b[i] = T(kDpB[i]);
+            c.e[i] = T(kDpB[i] - kDpBh[i]);
+        }
+    } else {
+        c.stages = 6;
+        for (int i = 0; i < 6; ++i) {
+            for (int j = 0; j < 5; ++j) c.a[i][j] = T(kRkfA[i][j]);
+            c.b[i] = T(kRkfB4[i]);
+            c.e[i] = T(kRkfB5[i] - kRkfB4[i]);
+        }
     }
     return c;
 }
@@ -1483,6 +1504,7 @@ __global__ void __launch_bounds__(256) rk_finish_kernel(GroupArgs<T> g, RkArgs<T
         T b5 = T(0), d4 = T(0);
 #pragma unroll
         for (int q = 0; q < 7; ++q) {
+            if (q >= r.dp.stages) break;  // a six-stage pair leaves k_6 unused (it may hold anything)
             const T kq = r.k[q * stride + base + e];
             b5 += r.dp.b[q] * kq;
             d4 += r.dp.e[q] * kq;
@@ -2188,7 +2210,7 @@ void launch_interp_identity(InterpEntry* tab, int img0, int K, cudaStream_t st) 
     template void launch_xinv_step_climb<T>(const GroupArgs<T>&, bool, T, T*, int, size_t, cudaStream_t);       \
     template void launch_climb<T>(const GroupArgs<T>&, const ArcArgs&, T, const T*, cudaStream_t);             \
     template void launch_spline_apply<T>(const GroupArgs<T>&, const ArcArgs&, int, cudaStream_t);              \
-    template DpCoef<T> dp_coefficients<T>();                                                                  \
+    template DpCoef<T> dp_coefficients<T>(int);                                                               \
     template void launch_rk_assemble<T>(const GroupArgs<T>&, const RkArgs<T>&, int, cudaStream_t);             \
     template void launch_rk_finish<T>(const GroupArgs<T>&, const RkArgs<T>&, cudaStream_t);                    \
     template void launch_rk_control<T>(const GroupArgs<T>&, const RkArgs<T>&, int, cudaStream_t);                \

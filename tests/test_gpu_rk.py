@@ -156,3 +156,36 @@ def test_dopri5_invalid_arguments(ss):
             sm.integrator_state(3)
         with pytest.raises(ss.SsError):
             sm.integrator_state(0, spec.n_images)
+
+
+@pytest.mark.parametrize("per_image", [False, True])
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_rkf45_against_oracle(ss, prec, per_image):
+    # the Runge-Kutta-Fehlberg 4(5) pair (six stages, fourth-order solution carried)
+    spec = W.tiny_bloch().strings[0]
+    c = _case(spec)
+    n_iter, T = 6, 0.5
+    rtol, atol = (1e-6, 1e-8) if prec == FP64 else (1e-4, 1e-6)
+    kind = ss.SS_INT_RKF45_IMAGE if per_image else ss.SS_INT_RKF45
+    (start,), (g,) = _gpu_run(ss, [c], [spec.initial_path()], T, n_iter, prec, rtol, atol, kind=kind)
+    ref, e_ref, steps_ref, counts_ref = oracle.string_run_rk(_model(c), _unit(start), n_iter, T, rtol, atol,
+                                                             per_image=per_image, method="rkf45")
+    if per_image:
+        got_counts = np.array([st[1:] for st in g["images"]])
+        got_steps = np.array([st[0] for st in g["images"]])
+    else:
+        got_counts = np.array([g["state"][1:]])
+        got_steps = np.array([g["state"][0]])
+        counts_ref, steps_ref = np.array([counts_ref]), np.array([steps_ref])
+    if prec == FP64:
+        np.testing.assert_array_equal(got_counts, counts_ref)
+        np.testing.assert_allclose(got_steps, steps_ref, rtol=1e-6)
+        assert np.abs(g["path"] - ref).max() < 1e-10
+        np.testing.assert_allclose(g["e"], e_ref, rtol=0, atol=1e-9)
+    else:
+        assert np.abs(got_counts - counts_ref).max() <= 3
+        assert np.abs(g["path"] - ref).max() < 1e-4
+        np.testing.assert_allclose(g["e"], e_ref, rtol=0, atol=1e-4)
+    # the pairs differ: Dormand-Prince takes another step sequence on the same problem
+    _, _, _, counts_dp = oracle.string_run_rk(_model(c), _unit(start), n_iter, T, rtol, atol, per_image=per_image)
+    assert not np.array_equal(np.asarray(counts_dp).reshape(-1, 2), np.asarray(counts_ref).reshape(-1, 2))
