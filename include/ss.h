@@ -216,8 +216,8 @@ enum { SS_INTERP_LINEAR = 0, SS_INTERP_SPLINE = 1 };
  *   ss_set_integrator refuses a Runge-Kutta kind while it is on).
  * Adds 2 launches per size group and iteration for the climbing image and 1 for the spline; allocates
  * one string-state copy per size group for the climbing image and 2 K^2 doubles per string for the
- * spline on first use.  Takes effect at the next ss_step; every string restarts without a climbing
- * image. */
+ * spline on first use.  Takes effect at the next ss_step (a linear reparametrisation still pending
+ * from the previous iteration is applied first); every string restarts without a climbing image. */
 ss_status ss_set_reparam(ss_ctx* ctx, int interp, int climb);
 
 /* The image of `string` that climbs in the next iteration, or -1 (none, or climbing off).  Synchronises. */
@@ -231,10 +231,11 @@ enum { SS_DYN_STRING = 0, SS_DYN_LLG = 1 };
  * equation (Eq. 9) in reduced units (h in units of J, time in units of mu0 |S| / (gamma J)),
  *     ds/dtau = -1/(1 + alpha^2) s x h - alpha/(1 + alpha^2) s x (s x h),
  * for every image as an independent system with no reparametrisation: each ss_step iteration advances
- * time by opts.dt, by one explicit Euler step with renormalisation (SS_INT_EULER) or by the
- * Dormand-Prince evolution of ss_set_integrator; ss_step_energies reports the energies of the states
- * each iteration started from.  alpha (the damping) must be finite and >= 0.  The climbing image is
- * refused under SS_DYN_LLG (SS_ERR_STATE).  Takes effect at the next ss_step; no synchronisation. */
+ * time by opts.dt, by one explicit Euler step with renormalisation (SS_INT_EULER) or by the adaptive
+ * Runge-Kutta evolution chosen with ss_set_integrator; ss_step_energies reports the energies of the
+ * states each iteration started from.  alpha (the damping) must be finite and >= 0.  The climbing image
+ * is refused under SS_DYN_LLG (SS_ERR_STATE) and the interpolation choice has no effect there.  Takes
+ * effect at the next ss_step; no synchronisation. */
 ss_status ss_set_dynamics(ss_ctx* ctx, int kind, double alpha);
 
 /* Shape queries. */
