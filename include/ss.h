@@ -19,7 +19,8 @@
  *   - Spin/field arrays crossing the ABI are [image][site][3] (x, y, z components), site index
  *     (z*ny + y)*nx + x, dtype SS_DTYPE_F32 or SS_DTYPE_F64, on the host (on_device = 0) or on the
  *     context's device (on_device = 1).  They are caller-owned and never retained.
- *   - All device memory is owned by the context (allocated in ss_create*, freed in ss_destroy).
+ *   - All device memory is owned by the context (allocated in ss_create* or on first use of a variant,
+ *     freed in ss_destroy), from cudaMalloc or from the allocator given to ss_set_allocator.
  *   - Work is issued on an internal stream that is ordered after, and before, opts.stream (or the
  *     legacy default stream when opts.stream is NULL).  ss_step is asynchronous; every other call
  *     that returns data synchronises.  A sticky device error word (non-finite values) is read at
@@ -28,6 +29,8 @@
  */
 #ifndef SS_H
 #define SS_H
+
+#include <stddef.h>
 
 #ifdef __cplusplus
 extern "C" {
@@ -237,6 +240,20 @@ enum { SS_DYN_STRING = 0, SS_DYN_LLG = 1 };
  * is refused under SS_DYN_LLG (SS_ERR_STATE) and the interpolation choice has no effect there.  Takes
  * effect at the next ss_step; no synchronisation. */
 ss_status ss_set_dynamics(ss_ctx* ctx, int kind, double alpha);
+
+/* Device allocator for contexts (optional).  By default a context's device memory comes from
+ * cudaMalloc and goes back with cudaFree in ss_destroy.  A framework with its own caching allocator
+ * (e.g. PyTorch's) can supply one instead: alloc(bytes, device, stream, user) returns device memory on
+ * `device` aligned to 256 bytes (or NULL: the creating call fails with SS_ERR_OOM; a misaligned pointer
+ * is handed back to free and the call fails with SS_ERR_INVALID_ARG), free(ptr, bytes, device, stream,
+ * user) releases it; `stream` is the context's opts.stream.  The pair applies to contexts created after
+ * the call (each context keeps the pair it was created with, and frees through it in ss_destroy after
+ * synchronising its work), so the allocator must outlive them.  alloc and free both NULL restore
+ * cudaMalloc; one NULL and not the other is SS_ERR_INVALID_ARG.  Process-wide and thread-safe.  Scratch
+ * of ss_create's one-off tensor-spectrum build and ss_field_noalloc's array are not affected. */
+typedef void* (*ss_alloc_fn)(size_t bytes, int device, void* stream, void* user);
+typedef void (*ss_free_fn)(void* ptr, size_t bytes, int device, void* stream, void* user);
+ss_status ss_set_allocator(ss_alloc_fn alloc, ss_free_fn free, void* user);
 
 /* Shape queries. */
 int ss_num_strings(const ss_ctx* ctx);

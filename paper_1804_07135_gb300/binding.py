@@ -47,6 +47,11 @@ class ss_string_desc(ctypes.Structure):
 _lib = None
 _lock = threading.Lock()
 
+# device allocator callbacks (ss_set_allocator)
+SS_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p)
+SS_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p)
+_allocator_refs = None  # keeps the installed callbacks alive
+
 # name -> (restype, argtypes); mirrors include/ss.h
 _SIGNATURES = {
     "ss_default_opts": (None, [ctypes.POINTER(ss_opts)]),
@@ -60,6 +65,7 @@ _SIGNATURES = {
     "ss_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "ss_set_integrator": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double]),
     "ss_set_reparam": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "ss_set_allocator": (ctypes.c_int, [SS_ALLOC_FN, SS_FREE_FN, ctypes.c_void_p]),
     "ss_set_dynamics": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]),
     "ss_climbing_image": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "ss_integrator_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -252,6 +258,39 @@ def ss_step(ctx, n_iter: int) -> None:
 
 def ss_set_integrator(ctx, kind: int, rtol: float = 1e-6, atol: float = 1e-8) -> None:
     _check(_lib.ss_set_integrator(ctx, int(kind), float(rtol), float(atol)), ctx)
+
+
+def ss_set_allocator(alloc, free, user=None) -> None:
+    """Install device allocator callbacks (SS_ALLOC_FN / SS_FREE_FN instances, or both null) for
+    contexts created afterwards; the caller keeps the callback objects alive."""
+    _check(_lib.ss_set_allocator(alloc, free, user))
+
+
+def use_torch_allocator() -> None:
+    """Contexts created from now on take their device memory from PyTorch's caching allocator
+    (on the context's opts.stream) and give it back to it in ss_destroy."""
+    global _allocator_refs
+    import torch
+
+    def _alloc(nbytes, device, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), int(device), int(stream or 0))
+        except Exception:  # out of memory: the library reports SS_ERR_OOM
+            return None
+
+    def _free(ptr, nbytes, device, stream, user):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    refs = (SS_ALLOC_FN(_alloc), SS_FREE_FN(_free))
+    ss_set_allocator(refs[0], refs[1], None)
+    _allocator_refs = refs
+
+
+def use_cuda_malloc() -> None:
+    """Contexts created from now on allocate with cudaMalloc again."""
+    global _allocator_refs
+    ss_set_allocator(SS_ALLOC_FN(), SS_FREE_FN(), None)
+    _allocator_refs = None
 
 
 def ss_set_reparam(ctx, interp: int = SS_INTERP_LINEAR, climb: bool = False) -> None:

@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <array>
+#include <cstdint>
 #include <cstdlib>
 #include <mutex>
 #include <new>
@@ -126,7 +127,10 @@ struct ss_ctx {
     int* d_err = nullptr;
     void* stage = nullptr;  // device staging buffer for host copies
     size_t stage_bytes = 0;
-    std::vector<void*> allocs;
+    std::vector<std::pair<void*, size_t>> allocs;
+    ss_alloc_fn alloc_fn = nullptr;  // the allocator the context was created with (null: cudaMalloc)
+    ss_free_fn free_fn = nullptr;
+    void* alloc_user = nullptr;
     cudaGraphExec_t graph1 = nullptr, graphN = nullptr;
     int graphN_iters = 64;
     int integrator = 0;  // SS_INT_EULER or one of the Runge-Kutta kinds
@@ -162,17 +166,33 @@ ss_status fail(ss_ctx* c, ss_status st, const char* fmt, ...) {
                         "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
     } while (0)
 
+// Device memory of a context: from the allocator it was created with (ss_set_allocator), else cudaMalloc.
 ss_status dalloc(ss_ctx* c, void** p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc(p, bytes);
-    if (e != cudaSuccess) {
-        *p = nullptr;
-        return fail(c, SS_ERR_OOM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    if (c->alloc_fn) {
+        *p = c->alloc_fn(bytes, c->device, c->opts.stream, c->alloc_user);
+        if (!*p) return fail(c, SS_ERR_OOM, "allocator callback returned NULL for %zu bytes", bytes);
+        if (reinterpret_cast<uintptr_t>(*p) % 256 != 0) {
+            c->free_fn(*p, bytes, c->device, c->opts.stream, c->alloc_user);
+            *p = nullptr;
+            return fail(c, SS_ERR_INVALID_ARG, "allocator callback returned a pointer not aligned to 256 bytes");
+        }
+    } else {
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e != cudaSuccess) {
+            *p = nullptr;
+            return fail(c, SS_ERR_OOM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+        }
     }
-    c->allocs.push_back(*p);
+    c->allocs.push_back({*p, bytes});
     return SS_OK;
 }
+
+std::mutex g_alloc_mu;
+ss_alloc_fn g_alloc_fn = nullptr;
+ss_free_fn g_free_fn = nullptr;
+void* g_alloc_user = nullptr;
 
 #define TRY(x)                        \
     do {                              \
@@ -853,6 +873,12 @@ ss_status ss_create_batch(int n_strings, const ss_string_desc* descs, const ss_o
     if (!c) return fail(nullptr, SS_ERR_OOM, "host allocation failed");
     c->opts = o;
     c->device = dev;
+    {
+        std::lock_guard<std::mutex> lock(g_alloc_mu);
+        c->alloc_fn = g_alloc_fn;
+        c->free_fn = g_free_fn;
+        c->alloc_user = g_alloc_user;
+    }
     auto bail = [&](ss_status st) {
         g_create_error = c->err;
         ss_destroy(c);
@@ -1296,6 +1322,18 @@ ss_status ss_string_info(const ss_ctx* c, int string, ss_string_desc* out) {
     return SS_OK;
 }
 
+ss_status ss_set_allocator(ss_alloc_fn alloc, ss_free_fn free, void* user) {
+    if ((alloc == nullptr) != (free == nullptr)) {
+        g_create_error = "ss_set_allocator: alloc and free must both be given or both be NULL";
+        return SS_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    g_alloc_fn = alloc;
+    g_free_fn = free;
+    g_alloc_user = alloc ? user : nullptr;
+    return SS_OK;
+}
+
 int ss_kernels_per_iteration(const ss_ctx* c) {
     if (!c) return 0;
     int n = 0;
@@ -1311,7 +1349,12 @@ void ss_destroy(ss_ctx* c) {
     if (c->cs) cudaStreamSynchronize(c->cs);
     if (c->graph1) cudaGraphExecDestroy(c->graph1);
     if (c->graphN) cudaGraphExecDestroy(c->graphN);
-    for (void* p : c->allocs) cudaFree(p);
+    for (const auto& a : c->allocs) {
+        if (c->free_fn)
+            c->free_fn(a.first, a.second, c->device, c->opts.stream, c->alloc_user);
+        else
+            cudaFree(a.first);
+    }
     if (c->h_active) cudaFreeHost(c->h_active);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
     if (c->ev_out) cudaEventDestroy(c->ev_out);

@@ -60,3 +60,11 @@ def test_argument_validation_on_host():
     with pytest.raises(binding.SsError) as e:
         binding.ss_create(8, 8, 1, 1.0, 0.3, 0.05, 0.01, 4, binding.make_opts(dt=-1.0))
     assert e.value.status == binding.SS_ERR_INVALID_ARG
+
+
+def test_allocator_pair_must_be_complete():
+    # one callback without the other is refused (host-side check, no GPU involved)
+    binding.load()
+    alloc = binding.SS_ALLOC_FN(lambda n, d, s, u: None)
+    assert binding._lib.ss_set_allocator(alloc, binding.SS_FREE_FN(), None) == binding.SS_ERR_INVALID_ARG
+    assert binding._lib.ss_set_allocator(binding.SS_ALLOC_FN(), binding.SS_FREE_FN(), None) == binding.SS_OK

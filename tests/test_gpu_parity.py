@@ -381,3 +381,32 @@ def test_uneven_parameter_study_batch(ss):
                 ref = oracle.field_at(m, _unit(state[k]), sites)
                 assert np.abs(h[k][sites] - ref).max() <= 1e-5 * np.abs(ref).max()
     assert len(checked) == 4
+
+
+def test_torch_caching_allocator(ss):
+    # device memory from PyTorch's caching allocator: accounted by torch while the context lives,
+    # returned by ss_destroy, and the results equal those of a cudaMalloc context
+    spec = W.tiny_bloch().strings[0]
+    case = (spec.nx, spec.ny, spec.nz, spec.J, spec.D, spec.K, spec.w, spec.n_images)
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_allocated()
+    ss.use_torch_allocator()
+    try:
+        with _sm(ss, [case], precision=FP64) as sm:
+            assert torch.cuda.memory_allocated() > before
+            sm.set_integrator(ss.SS_INT_DOPRI5, 1e-6, 1e-8)  # variant buffers come from it too
+            grown = torch.cuda.memory_allocated()
+            sm.set_integrator(ss.SS_INT_EULER, 1e-6, 1e-8)
+            sm.set_path(0, spec.initial_path())
+            sm.step(20)
+            got = sm.get_path(0)
+        assert grown > before
+    finally:
+        ss.use_cuda_malloc()
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == before
+    with _sm(ss, [case], precision=FP64) as sm:
+        sm.set_path(0, spec.initial_path())
+        sm.step(20)
+        ref = sm.get_path(0)
+    assert np.array_equal(got, ref)
