@@ -220,3 +220,52 @@ def test_kernel_timing_follows_the_mode(ss):
         with pytest.raises(ss.SsError) as ei:
             sm.time_kernels(reps=2)
         assert ei.value.status == ss.SS_ERR_STATE
+
+
+@pytest.mark.parametrize("K", [2, 3])
+def test_degenerate_strings_with_spline_and_climbing(ss, K):
+    # K = 2: no interior image (nothing moves, nothing climbs); K = 3: the one interior image climbs
+    # and both parts have no interior image
+    c = (6, 5, 2, 1.0, 0.3, 0.05, 0.02, K)
+    path = W.bloch_point_path(6, 5, 2, K, R=2.0, D=0.3)
+    n_iter = 6
+    (s0,), (g,) = _run(ss, [c], [path], n_iter, FP64, True, True)
+    ref, e_ref, kc_ref = oracle.string_run_v(_model(c), _unit(s0), n_iter, 0.1, spline=True, climb=True)
+    assert g["kc"] == kc_ref == (-1 if K == 2 else 1)
+    assert np.abs(g["path"] - ref).max() < 1e-11
+    np.testing.assert_allclose(g["e"], e_ref, rtol=0, atol=1e-10)
+
+
+def test_spline_on_a_string_of_identical_images(ss):
+    # zero arc length: the reparametrisation keeps every image
+    c = (8, 8, 1, 1.0, 0.3, 0.05, 0.01, 5)
+    one = W.bloch_point_path(8, 8, 1, 2, R=3.0, D=0.3)[0]
+    path = np.repeat(one[None], 5, axis=0)
+    (s0,), (g,) = _run(ss, [c], [path], 3, FP64, True, False)
+    ref, _, _ = oracle.string_run_v(_model(c), _unit(s0), 3, 0.1, spline=True)
+    assert np.abs(g["path"] - ref).max() < 1e-12
+    assert np.abs(g["path"] - g["path"][0]).max() < 1e-12  # the images stay identical
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_llg_and_dopri5_on_a_one_column_lattice(ss, prec):
+    # nx = 1 (no x bonds, odd x length for the paired sites), two images
+    c = (1, 6, 2, 1.0, 0.3, 0.05, 0.02, 2)
+    path = _unit(np.random.default_rng(12).standard_normal((2, 12, 3)))
+    tol = 1e-4 if prec == FP32 else 1e-11
+    with ss.StringMethod([c], dt=0.05, precision=prec) as sm:
+        sm.set_dynamics(ss.SS_DYN_LLG, 0.3)
+        sm.set_path(0, path)
+        s0 = sm.get_path(0)
+        sm.step(20)
+        got = sm.get_path(0)
+        sm.set_dynamics(ss.SS_DYN_STRING)
+        sm.set_integrator(ss.SS_INT_DOPRI5_IMAGE, 1e-6, 1e-8)
+        sm.set_path(0, path)
+        s1 = sm.get_path(0)
+        sm.step(4)
+        got_rk = sm.get_path(0)
+    ref, _ = oracle.llg_run(_model(c), _unit(s0), 20, 0.05, 0.3)
+    assert np.abs(got - ref).max() < tol
+    ref_rk, _, _, _ = oracle.string_run_rk(_model(c), _unit(s1), 4, 0.05, 1e-6, 1e-8, per_image=True)
+    assert np.abs(got_rk - ref_rk).max() < (1e-4 if prec == FP32 else 1e-10)
