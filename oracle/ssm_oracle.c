@@ -17,8 +17,11 @@
  * i = (z*ny + y)*nx + x; spin arrays are [site][3] (x,y,z components); a string is [image][site][3].
  *
  * Parity status: every function here is pinned by a CPU test against closed forms, finite
- * differences or geometry, except or_string_run's barrier value, whose only check beyond the pinned
- * parts it is composed of is sanity (barrier >= 0): "parity unpinned" for the barrier number itself.
+ * differences, geometry or an independent library routine, except the barrier value of a general
+ * string run (or_string_run and its variants on a workload whose saddle has no closed form), whose
+ * only check beyond the pinned parts it is composed of is sanity (barrier >= 0): "parity unpinned" for
+ * that number.  With the climbing image the barrier is pinned where the saddle is known exactly (a
+ * lone spin under anisotropy: K; a small ferromagnet's coherent rotation: N K).
  */
 #include <math.h>
 #include <stdlib.h>
