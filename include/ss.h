@@ -51,12 +51,15 @@ typedef enum {
 enum { SS_DTYPE_F32 = 0, SS_DTYPE_F64 = 1 };
 enum { SS_PREC_FP32 = 0, /* FP32 spins, fields and FFTs; FP64 energies and arc lengths */
        SS_PREC_FP64 = 1  /* the plain FP64 GPU method: FP64 everywhere */ };
-enum { SS_DIPOLE_OFF = 0, SS_DIPOLE_FFT = 2 };
+enum { SS_DIPOLE_OFF = 0, SS_DIPOLE_DIRECT = 1, SS_DIPOLE_FFT = 2 };
 
 typedef struct {
     double dt;          /* step length of the projected-descent step (> 0); prefactors of Eq. 9 absorbed */
     int precision;      /* SS_PREC_FP32 or SS_PREC_FP64 */
-    int dipole;         /* SS_DIPOLE_FFT (default) or SS_DIPOLE_OFF (dipole term dropped whatever w) */
+    int dipole;         /* SS_DIPOLE_FFT (default: the zero-padded FFT convolution of Sec. II-A),
+                           SS_DIPOLE_DIRECT (the O(N^2) sum of Eq. 6 over all pairs of an image, for
+                           small lattices and as an FFT-free check), or SS_DIPOLE_OFF (dipole term
+                           dropped whatever w) */
     int reparam_every;  /* 1 = reparametrise after every step (Sec. III); 0 = never (plain relaxation) */
     void* stream;       /* cudaStream_t to order against, e.g. torch.cuda.current_stream(); NULL = legacy */
 } ss_opts;

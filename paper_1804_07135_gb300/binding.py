@@ -20,7 +20,7 @@ from . import build as _build
 SS_OK, SS_ERR_INVALID_ARG, SS_ERR_CUDA, SS_ERR_OOM, SS_ERR_NONFINITE, SS_ERR_TIMEOUT, SS_ERR_STATE = range(7)
 SS_DTYPE_F32, SS_DTYPE_F64 = 0, 1
 SS_PREC_FP32, SS_PREC_FP64 = 0, 1
-SS_DIPOLE_OFF, SS_DIPOLE_FFT = 0, 2
+SS_DIPOLE_OFF, SS_DIPOLE_DIRECT, SS_DIPOLE_FFT = 0, 1, 2
 SS_INT_EULER, SS_INT_DOPRI5, SS_INT_DOPRI5_IMAGE, SS_INT_RKF45, SS_INT_RKF45_IMAGE = 0, 1, 2, 3, 4
 SS_INTERP_LINEAR, SS_INTERP_SPLINE = 0, 1
 SS_DYN_STRING, SS_DYN_LLG = 0, 1

@@ -79,7 +79,9 @@ struct Group {
     int n_img = 0, n_pairs = 0;
     std::vector<int> strs;  // context string ids, in group order
     std::vector<int> str_img0, str_K;
-    bool dipole = false;
+    bool dipole = false;  // FFT dipole convolution (SS_DIPOLE_FFT and some w != 0)
+    bool direct = false;  // direct dipole sums (SS_DIPOLE_DIRECT and some w != 0)
+    void* hdir = nullptr; // [image][3][N] direct sums
     FftPlan planx{}, plany{};
     int lsx = 1, lsy = 1;
     int ty_a = 1, ty_c = 1, thr_a = 128, thr_b = 128, thr_c = 128, thr_arc = 256;
@@ -233,6 +235,7 @@ template <typename T> GroupArgs<T> group_args(const ss_ctx* c, const Group& g) {
     a.ty_c = g.ty_c;
     a.err = c->d_err;
     a.climb_img = g.climb_img;
+    a.hdir = (const T*)g.hdir;
     a.llg_a = T(1.0 / (1.0 + c->alpha * c->alpha));
     a.llg_b = T(c->alpha / (1.0 + c->alpha * c->alpha));
     return a;
@@ -344,6 +347,7 @@ template <typename T> ss_status setup_group(ss_ctx* c, Group& g) {
     TRY(dalloc(c, &g.twy, g.Py * sizeof(C)));
     TRY(dalloc(c, &g.twxs, g.Px * sizeof(C)));
     TRY(dalloc(c, &g.twys, g.Py * sizeof(C)));
+    if (g.direct) TRY(dalloc(c, &g.hdir, (size_t)g.n_img * 3 * g.N * sizeof(T)));
     if (g.dipole) {
         TRY(dalloc(c, &g.spec, (size_t)g.n_pairs * g.Px * 3 * g.nz * g.ny * sizeof(C)));
         TRY(dalloc(c, &g.dhat, (size_t)(g.Px / 2 + 1) * (g.Py / 2 + 1) * g.nz * 6 * sizeof(T)));
@@ -518,6 +522,7 @@ template <typename T> int time_entries(ss_ctx* c, Group& g, int which_only) {
     };
     entry(true, [&] { launch_xfwd<T>(a, g.dipole, g.thr_a, g.smem_a, c->cs); });
     entry(g.dipole, [&] { launch_yz<T>(a, g.thr_b, g.smem_b, c->cs); });
+    entry(g.direct, [&] { launch_dipole_direct<T>(a, (T*)g.hdir, c->cs); });
     entry(true, [&] {
         if (c->dynamics == SS_DYN_LLG)
             launch_xinv_step_llg<T>(a, g.dipole, dt, g.thr_c, g.smem_c, c->cs);
@@ -646,6 +651,7 @@ template <typename T> ss_status rk_iterations(ss_ctx* c, int n_iter) {
                     launch_rk_assemble<T>(ai, r, st, c->cs);
                     launch_xfwd<T>(ai, g.dipole, g.thr_a, g.smem_a, c->cs);
                     if (g.dipole) launch_yz<T>(ai, g.thr_b, g.smem_b, c->cs);
+                    if (g.direct) launch_dipole_direct<T>(ai, (T*)g.hdir, c->cs);
                     launch_xinv_force<T>(ai, g.dipole, r.k + st * stride, round == 0 && st == 0,
                                          c->dynamics == SS_DYN_LLG, g.thr_c, g.smem_c_eval, c->cs);
                 }
@@ -677,6 +683,7 @@ template <typename T> void issue_iteration(ss_ctx* c, cudaStream_t st) {
         GroupArgs<T> a = group_args<T>(c, g);
         launch_xfwd<T>(a, g.dipole, g.thr_a, g.smem_a, st);
         if (g.dipole) launch_yz<T>(a, g.thr_b, g.smem_b, st);
+        if (g.direct) launch_dipole_direct<T>(a, (T*)g.hdir, st);
         if (c->dynamics == SS_DYN_LLG) {
             launch_xinv_step_llg<T>(a, g.dipole, dt, g.thr_c, g.smem_c, st);
         } else if (c->climb) {
@@ -694,6 +701,7 @@ template <typename T> void issue_eval(ss_ctx* c, Group& g, T* hout, cudaStream_t
     GroupArgs<T> a = group_args<T>(c, g);
     launch_xfwd<T>(a, g.dipole, g.thr_a, g.smem_a, st);
     if (g.dipole) launch_yz<T>(a, g.thr_b, g.smem_b, st);
+    if (g.direct) launch_dipole_direct<T>(a, (T*)g.hdir, st);
     launch_xinv_eval<T>(a, g.dipole, hout, g.thr_c, g.smem_c_eval, st);
     launch_eval_reduce<T>(a, g.arc, g.eval_terms, g.eval_E, st);
 }
@@ -859,7 +867,8 @@ ss_status ss_create_batch(int n_strings, const ss_string_desc* descs, const ss_o
     if (!(o.dt > 0.0) || !isfinite(o.dt)) return fail(nullptr, SS_ERR_INVALID_ARG, "dt must be finite and > 0");
     if (o.precision != SS_PREC_FP32 && o.precision != SS_PREC_FP64)
         return fail(nullptr, SS_ERR_INVALID_ARG, "precision %d", o.precision);
-    if (o.dipole != SS_DIPOLE_OFF && o.dipole != SS_DIPOLE_FFT) return fail(nullptr, SS_ERR_INVALID_ARG, "dipole mode %d", o.dipole);
+    if (o.dipole != SS_DIPOLE_OFF && o.dipole != SS_DIPOLE_FFT && o.dipole != SS_DIPOLE_DIRECT)
+        return fail(nullptr, SS_ERR_INVALID_ARG, "dipole mode %d", o.dipole);
     for (int i = 0; i < n_strings; ++i) TRY(validate_desc(descs[i]));
 
     int dev = 0;
@@ -909,7 +918,8 @@ ss_status ss_create_batch(int n_strings, const ss_string_desc* descs, const ss_o
         g.str_img0.push_back(g.n_img);
         g.str_K.push_back(d.n_images);
         g.n_img += d.n_images;
-        if (o.dipole != SS_DIPOLE_OFF && d.w != 0.0) g.dipole = true;
+        if (o.dipole == SS_DIPOLE_FFT && d.w != 0.0) g.dipole = true;
+        if (o.dipole == SS_DIPOLE_DIRECT && d.w != 0.0) g.direct = true;
         c->strs.push_back(r);
     }
     size_t stage = 0;
@@ -1337,7 +1347,8 @@ ss_status ss_set_allocator(ss_alloc_fn alloc, ss_free_fn free, void* user) {
 int ss_kernels_per_iteration(const ss_ctx* c) {
     if (!c) return 0;
     int n = 0;
-    for (const Group& g : c->groups) n += (g.dipole ? 4 : 3) + (c->climb ? 2 : 0) + (c->interp == SS_INTERP_SPLINE ? 1 : 0);
+    for (const Group& g : c->groups)
+        n += (g.dipole || g.direct ? 4 : 3) + (c->climb ? 2 : 0) + (c->interp == SS_INTERP_SPLINE ? 1 : 0);
     return n;
 }
 

@@ -87,6 +87,7 @@ template <typename T> struct GroupArgs {
     int* err;       // sticky error word (bit 1: invalid input spin, bit 2: non-finite value)
     const int* climb_img;  // [n_img] nonzero for the image that climbs this iteration (climbing mode only)
     T llg_a, llg_b;        // precessional dynamics (Eq. 9): 1 / (1 + alpha^2) and alpha / (1 + alpha^2)
+    const T* hdir;         // [image][3][N] direct dipole sums (SS_DIPOLE_DIRECT), or null
 };
 
 // Arc-length / reparametrisation bookkeeping of one size group.
@@ -206,6 +207,7 @@ template <typename T> void launch_xinv_step_climb(const GroupArgs<T>& g, bool do
                                                   cudaStream_t st);
 template <typename T> void launch_xinv_step_llg(const GroupArgs<T>& g, bool do_fft, T dt, int nthr, size_t smem,
                                                 cudaStream_t st);
+template <typename T> void launch_dipole_direct(const GroupArgs<T>& g, T* hdir, cudaStream_t st);
 template <typename T> void launch_climb(const GroupArgs<T>& g, const ArcArgs& a, T dt, const T* hc, cudaStream_t st);
 template <typename T> void launch_spline_apply(const GroupArgs<T>& g, const ArcArgs& a, int maxK, cudaStream_t st);
 template <typename T> void launch_rk_assemble(const GroupArgs<T>& g, const RkArgs<T>& r, int stage, cudaStream_t st);

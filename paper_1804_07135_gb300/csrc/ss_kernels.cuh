@@ -767,6 +767,9 @@ __device__ __forceinline__ void xinv_sites(const GroupArgs<T>& g, T dt, T* hout,
                 const C v = buf[(c * rows + yy) * ls + fft_pad(x)];
                 conv[c] = h == 0 ? v.x : -v.y;  // conjugate of the forward transform of the conjugate
             }
+        } else if (g.hdir) {  // direct dipole sums
+#pragma unroll
+            for (int c = 0; c < 3; ++c) conv[c] = g.hdir[(size_t)im * 3 * N + (size_t)c * N + site];
         }
         T hf[3];
         local_field(pr, s0, xp, xm, yp, ym, zp, zm, conv, hf);
@@ -1610,6 +1613,52 @@ __global__ void __launch_bounds__(256) rk_commit_kernel(GroupArgs<T> g, RkArgs<T
     }
 }
 
+// ---- direct dipole sum (SS_DIPOLE_DIRECT) -------------------------------------------------------------
+// conv_i = sum_{j != i} (3 (r.s_j) r / r^5 - s_j / r^3), r = r_j - r_i in lattice units: Eq. 6 with the
+// tensor of Eq. 7 (its 1/(4 pi) cancels against the 4 pi of w's definition); the x-inverse kernel
+// multiplies by w.  grid (ceil(N / 128), n_img), 128 threads, one site i each; the image's spins (from s,
+// the gathered state) and their coordinates stream through shared memory in tiles of 128 sites.
+template <typename T>
+__global__ void __launch_bounds__(128) dipole_direct_kernel(GroupArgs<T> g, T* hdir) {
+    __shared__ T sj[3][128];
+    __shared__ int xj[128], yj[128], zj[128];
+    const int im = blockIdx.y, tid = threadIdx.x, N = g.N, nx = g.nx, ny = g.ny;
+    const int i = blockIdx.x * 128 + tid;
+    const T* s = g.s + (size_t)im * 3 * N;
+    const int xi = i % nx, yi = (i / nx) % ny, zi = i / (nx * ny);
+    T a0 = T(0), a1 = T(0), a2 = T(0);
+    for (int t0 = 0; t0 < N; t0 += 128) {
+        const int j = t0 + tid;
+        __syncthreads();  // the previous tile is consumed
+        if (j < N) {
+            sj[0][tid] = s[j];
+            sj[1][tid] = s[N + j];
+            sj[2][tid] = s[2 * N + j];
+            xj[tid] = j % nx;
+            yj[tid] = (j / nx) % ny;
+            zj[tid] = j / (nx * ny);
+        }
+        __syncthreads();
+        const int nt = min(128, N - t0);
+        for (int q = 0; q < nt; ++q) {
+            const T dx = T(xj[q] - xi), dy = T(yj[q] - yi), dz = T(zj[q] - zi);
+            const T r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 == T(0)) continue;  // j == i
+            const T ir = rsqrt_t<T>(r2), ir3 = ir * ir * ir, ir5 = ir3 * ir * ir;
+            const T rs3 = T(3) * (dx * sj[0][q] + dy * sj[1][q] + dz * sj[2][q]) * ir5;
+            a0 += rs3 * dx - sj[0][q] * ir3;
+            a1 += rs3 * dy - sj[1][q] * ir3;
+            a2 += rs3 * dz - sj[2][q] * ir3;
+        }
+    }
+    if (i < N) {
+        T* o = hdir + (size_t)im * 3 * N + i;
+        o[0] = a0;
+        o[N] = a1;
+        o[2 * N] = a2;
+    }
+}
+
 // ---- climbing image (Euler step) ------------------------------------------------------------------
 // The image kc that climbs this iteration stepped neither in the x-inverse kernel (MODE 3 wrote its force
 // F = h - (s.h) s into hc); its step reverses F's component along the string's tangent:
@@ -2057,6 +2106,10 @@ void launch_xinv_step_climb(const GroupArgs<T>& g, bool do_fft, T dt, T* hc, int
         launch_pdl(xinv_kernel<T, false, 3, 0>, grid, dim3(nthr), smem, st, g, dt, hc);
 }
 
+template <typename T> void launch_dipole_direct(const GroupArgs<T>& g, T* hdir, cudaStream_t st) {
+    dipole_direct_kernel<T><<<dim3((g.N + 127) / 128, g.n_img), 128, 0, st>>>(g, hdir);
+}
+
 template <typename T> void launch_climb(const GroupArgs<T>& g, const ArcArgs& a, T dt, const T* hc, cudaStream_t st) {
     const dim3 grid(a.c_tiles, a.n_str);
     climb_dot_kernel<T><<<grid, 256, 0, st>>>(g, a, hc);
@@ -2209,6 +2262,7 @@ void launch_interp_identity(InterpEntry* tab, int img0, int K, cudaStream_t st) 
     template void launch_xinv_step_llg<T>(const GroupArgs<T>&, bool, T, int, size_t, cudaStream_t);             \
     template void launch_xinv_step_climb<T>(const GroupArgs<T>&, bool, T, T*, int, size_t, cudaStream_t);       \
     template void launch_climb<T>(const GroupArgs<T>&, const ArcArgs&, T, const T*, cudaStream_t);             \
+    template void launch_dipole_direct<T>(const GroupArgs<T>&, T*, cudaStream_t);                              \
     template void launch_spline_apply<T>(const GroupArgs<T>&, const ArcArgs&, int, cudaStream_t);              \
     template DpCoef<T> dp_coefficients<T>(int);                                                               \
     template void launch_rk_assemble<T>(const GroupArgs<T>&, const RkArgs<T>&, int, cudaStream_t);             \

@@ -410,3 +410,38 @@ def test_torch_caching_allocator(ss):
         sm.step(20)
         ref = sm.get_path(0)
     assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+@pytest.mark.parametrize("case", [FIELD_CASES[0], FIELD_CASES[1], FIELD_CASES[2], FIELD_CASES[5], FIELD_CASES[6]])
+def test_direct_dipole_field_parity(ss, case, prec):
+    # SS_DIPOLE_DIRECT: the O(N^2) sum on the GPU against the oracle's direct sum
+    nx, ny, nz, J, D, K, w, n = case
+    path = W.random_spins((n, nx * ny * nz, 3), seed=nx * 100 + ny + 7)
+    with _sm(ss, [case], precision=prec, dipole=ss.SS_DIPOLE_DIRECT) as sm:
+        sm.set_path(0, path)
+        state = sm.get_path(0)
+        h = sm.field(0)
+        terms = sm.energy_terms(0)
+    ref = oracle.field(_model(case), _unit(state))
+    tol = (1e-5 if prec == FP32 else 1e-12) * np.abs(ref).max()
+    assert np.abs(h - ref).max() <= tol
+    want = np.array([[t for t in oracle.energy_param_grad(_model(case), s)] for s in _unit(state)])
+    np.testing.assert_allclose(terms, want, rtol=0, atol=(1e-3 if prec == FP32 else 1e-9))
+
+
+def test_direct_dipole_trajectory_matches_fft_and_oracle(ss):
+    wl = W.tiny_bloch()
+    spec = wl.strings[0]
+    case = (spec.nx, spec.ny, spec.nz, spec.J, spec.D, spec.K, spec.w, spec.n_images)
+    out = {}
+    for mode in (ss.SS_DIPOLE_DIRECT, ss.SS_DIPOLE_FFT):
+        with _sm(ss, [case], precision=FP64, dipole=mode) as sm:
+            sm.set_path(0, spec.initial_path())
+            start = sm.get_path(0)
+            sm.step(100)
+            out[mode] = (sm.get_path(0), sm.barrier(0))
+    ref, e_ref = oracle.string_run(_model(case), _unit(start), 100, 0.1)
+    assert np.abs(out[ss.SS_DIPOLE_DIRECT][0] - ref).max() < 1e-10
+    assert np.abs(out[ss.SS_DIPOLE_DIRECT][0] - out[ss.SS_DIPOLE_FFT][0]).max() < 1e-10
+    assert abs(out[ss.SS_DIPOLE_DIRECT][1][0] - oracle.barrier(e_ref)[0]) < 1e-9
