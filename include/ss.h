@@ -60,7 +60,8 @@ typedef struct {
                            SS_DIPOLE_DIRECT (the O(N^2) sum of Eq. 6 over all pairs of an image, for
                            small lattices and as an FFT-free check), or SS_DIPOLE_OFF (dipole term
                            dropped whatever w) */
-    int reparam_every;  /* 1 = reparametrise after every step (Sec. III); 0 = never (plain relaxation) */
+    int reparam_every;  /* 1 = reparametrise after every step (Sec. III); 0 = never (plain relaxation);
+                           other values are SS_ERR_INVALID_ARG */
     void* stream;       /* cudaStream_t to order against, e.g. torch.cuda.current_stream(); NULL = legacy */
 } ss_opts;
 

@@ -869,6 +869,8 @@ ss_status ss_create_batch(int n_strings, const ss_string_desc* descs, const ss_o
         return fail(nullptr, SS_ERR_INVALID_ARG, "precision %d", o.precision);
     if (o.dipole != SS_DIPOLE_OFF && o.dipole != SS_DIPOLE_FFT && o.dipole != SS_DIPOLE_DIRECT)
         return fail(nullptr, SS_ERR_INVALID_ARG, "dipole mode %d", o.dipole);
+    if (o.reparam_every != 0 && o.reparam_every != 1)
+        return fail(nullptr, SS_ERR_INVALID_ARG, "reparam_every must be 0 or 1 (got %d)", o.reparam_every);
     for (int i = 0; i < n_strings; ++i) TRY(validate_desc(descs[i]));
 
     int dev = 0;

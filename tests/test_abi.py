@@ -68,3 +68,12 @@ def test_allocator_pair_must_be_complete():
     alloc = binding.SS_ALLOC_FN(lambda n, d, s, u: None)
     assert binding._lib.ss_set_allocator(alloc, binding.SS_FREE_FN(), None) == binding.SS_ERR_INVALID_ARG
     assert binding._lib.ss_set_allocator(binding.SS_ALLOC_FN(), binding.SS_FREE_FN(), None) == binding.SS_OK
+
+
+def test_options_validation_on_host():
+    # checked before any device work: an unknown dipole mode, a reparametrisation period other than
+    # 0 or 1, a non-positive dt
+    for kw in ({"dipole": 3}, {"reparam_every": 2}, {"dt": 0.0}, {"dt": float("nan")}):
+        with pytest.raises(binding.SsError) as e:
+            binding.ss_create(8, 8, 1, 1.0, 0.3, 0.05, 0.01, 4, binding.make_opts(**kw))
+        assert e.value.status == binding.SS_ERR_INVALID_ARG, kw
