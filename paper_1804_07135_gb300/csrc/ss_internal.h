@@ -24,6 +24,7 @@ constexpr int kMaxThreadsX = 512;   // largest block of the x-transform kernels 
 constexpr int kMinBlocksX = 2;      // resident 512-thread blocks per SM they are compiled for (64 registers)
 constexpr int kMaxThreadsYz = 384;  // block size of the y/z kernel (3 x 128: one z-convolution row per warp)
 constexpr int kMinBlocksYz = 2;
+constexpr int kYzKxb1 = 4;          // kx columns per CTA of the y/z kernel for single-layer films
 constexpr int kMaxThreads128 = 384;  // length-128 x kernels: at most 8 rows of 48 threads
 constexpr int kMinBlocks128 = 3;     // resident 384-thread blocks per SM of the length-128 kernels (56 registers)
 constexpr int kArcMaxChunk = 8;     // image differences one arc CTA accumulates

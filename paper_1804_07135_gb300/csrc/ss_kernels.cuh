@@ -482,17 +482,20 @@ __device__ __forceinline__ void zconv_any(C* A, int lsy, int Py, int nz, int kx,
     }
 }
 
-template <typename T, int PY, int NZ>
+// KXB > 1 (single-layer films): KXB consecutive kx columns per CTA (their spectra are contiguous), so
+// the short per-column work is amortised over more lines per barrier; the tensor slab is then read
+// through L1 (stage_dhat is ignored).
+template <typename T, int PY, int NZ, int KXB = 1>
 __global__ void __launch_bounds__(kMaxThreadsYz, kMinBlocksYz) yz_kernel(GroupArgs<T> g, int stage_dhat) {
     using C = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tw = reinterpret_cast<C*>(smem_raw);
-    C* A = tw + g.Py;  // 3*nz lines of stride lsy
+    C* A = tw + g.Py;  // KXB*3*nz lines of stride lsy
     const int tid = threadIdx.x, nthr = blockDim.x;
-    const int kx = blockIdx.x, p = blockIdx.y;
+    const int kx = blockIdx.x * KXB, p = blockIdx.y;
     const int Py = PY > 0 ? PY : g.Py;
     const int nz = NZ > 0 ? NZ : g.nz;
-    const int ny = g.ny, L = 3 * nz;
+    const int ny = g.ny, L = 3 * nz * KXB;
     const int hy = Py / 2;
     const int kxo = min(kx, g.Px - kx);
     C* blk = g.spec + ((size_t)p * g.Px + kx) * 3 * nz * ny;
@@ -501,7 +504,7 @@ __global__ void __launch_bounds__(kMaxThreadsYz, kMinBlocksYz) yz_kernel(GroupAr
     const T* dslab = g.dhat + (size_t)kxo * (hy + 1) * nz * 6;
     const int dk = 1, dq = hy + 1;  // strides of kyo and of (|dz|*6 + comp)
     T* dsm = reinterpret_cast<T*>(A + L * g.lsy);
-    if (stage_dhat) {
+    if (KXB == 1 && stage_dhat) {
         for (int i = tid; i < (hy + 1) * nz * 6; i += nthr) dsm[i] = dslab[i];
         dslab = dsm;
     }
@@ -514,10 +517,19 @@ __global__ void __launch_bounds__(kMaxThreadsYz, kMinBlocksYz) yz_kernel(GroupAr
     }
     __syncthreads();
     fft_lines_any<PY, true, false>(A, tw, g.plany, g.lsy, L, tid, nthr);
-    if constexpr (NZ > 0)
-        zconv_c<NZ>(A, A, g.lsy, Py, kx, g.Px, dslab, dk, dq, tid, nthr);
-    else
-        zconv_any(A, g.lsy, Py, nz, kx, g.Px, dslab, dk, dq, tid, nthr);
+    if constexpr (KXB == 1) {
+        if constexpr (NZ > 0)
+            zconv_c<NZ>(A, A, g.lsy, Py, kx, g.Px, dslab, dk, dq, tid, nthr);
+        else
+            zconv_any(A, g.lsy, Py, nz, kx, g.Px, dslab, dk, dq, tid, nthr);
+    } else {
+        static_assert(NZ > 0, "several kx per CTA only with a compile-time layer count");
+        for (int b = 0; b < KXB; ++b) {
+            const int kxb = kx + b, kxob = min(kxb, g.Px - kxb);
+            zconv_c<NZ>(A + (size_t)b * 3 * NZ * g.lsy, A + (size_t)b * 3 * NZ * g.lsy, g.lsy, Py, kxb, g.Px,
+                        g.dhat + (size_t)kxob * (hy + 1) * NZ * 6, dk, dq, tid, nthr);
+        }
+    }
     fft_lines_any<PY, false, true>(A, tw, g.plany, g.lsy, L, tid, nthr);
     for (int it = tid; it < L * ny; it += nthr) {
         const int line = it / ny, y = it - line * ny;
@@ -1971,6 +1983,18 @@ template <typename T> void launch_yz(const GroupArgs<T>& g, int nthr, size_t sme
                 launch_pdl(yz128_kernel<T, 4>, grid, dim3(f128_yz_threads(4)), sm128, st, g, (int)st128);
             return;
         }
+        if (g.nz == 1 && g.Px % kYzKxb1 == 0) {  // single layer: several kx columns per CTA
+            const dim3 gridb(g.Px / kYzKxb1, g.n_pairs);
+            const size_t smb = (size_t)(g.Py + 3 * kYzKxb1 * g.lsy) * sizeof(cplx<T>);
+            if (g.Py == 256) {
+                launch_pdl(yz_kernel<T, 256, 1, kYzKxb1>, gridb, dim3(nthr), smb, st, g, 0);
+                return;
+            }
+            if (g.Py == 32) {
+                launch_pdl(yz_kernel<T, 32, 1, kYzKxb1>, gridb, dim3(nthr), smb, st, g, 0);
+                return;
+            }
+        }
 #define SS_CASE(P, Z)                                                   \
     if (g.Py == P && g.nz == Z) {                                       \
         launch_pdl(yz_kernel<T, P, Z>, grid, dim3(nthr), smem, st, g, stage); \
@@ -2224,6 +2248,8 @@ template <typename T> void set_smem_limits(int bytes) {
     set_dyn_smem(xinv_kernel<T, true, 0, P>, bytes);
         SS_FOR_PX(SS_CASE)
 #undef SS_CASE
+        set_dyn_smem(yz_kernel<T, 256, 1, kYzKxb1>, bytes);
+        set_dyn_smem(yz_kernel<T, 32, 1, kYzKxb1>, bytes);
 #define SS_CASE(P, Z) set_dyn_smem(yz_kernel<T, P, Z>, bytes);
         SS_FOR_PYNZ(SS_CASE)
 #undef SS_CASE
