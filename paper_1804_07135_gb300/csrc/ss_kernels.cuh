@@ -1995,6 +1995,15 @@ template <typename T> void launch_yz(const GroupArgs<T>& g, int nthr, size_t sme
                 return;
             }
         }
+        if (g.nz == 4 && g.Px % 2 == 0 && (g.Py == 192 || g.Py == 256)) {  // four layers: two kx columns
+            const dim3 gridb(g.Px / 2, g.n_pairs);
+            const size_t smb = (size_t)(g.Py + 3 * 4 * 2 * g.lsy) * sizeof(cplx<T>);
+            if (g.Py == 192)
+                launch_pdl(yz_kernel<T, 192, 4, 2>, gridb, dim3(nthr), smb, st, g, 0);
+            else
+                launch_pdl(yz_kernel<T, 256, 4, 2>, gridb, dim3(nthr), smb, st, g, 0);
+            return;
+        }
 #define SS_CASE(P, Z)                                                   \
     if (g.Py == P && g.nz == Z) {                                       \
         launch_pdl(yz_kernel<T, P, Z>, grid, dim3(nthr), smem, st, g, stage); \
@@ -2250,6 +2259,8 @@ template <typename T> void set_smem_limits(int bytes) {
 #undef SS_CASE
         set_dyn_smem(yz_kernel<T, 256, 1, kYzKxb1>, bytes);
         set_dyn_smem(yz_kernel<T, 32, 1, kYzKxb1>, bytes);
+        set_dyn_smem(yz_kernel<T, 192, 4, 2>, bytes);
+        set_dyn_smem(yz_kernel<T, 256, 4, 2>, bytes);
 #define SS_CASE(P, Z) set_dyn_smem(yz_kernel<T, P, Z>, bytes);
         SS_FOR_PYNZ(SS_CASE)
 #undef SS_CASE

@@ -45,6 +45,9 @@ FIELD_CASES = [
     (57, 61, 8, 1.0, 0.3, 0.05, 0.03, 3),   # ragged x and y, nz = 8, odd image count
     (60, 20, 3, 1.0, 0.3, 0.05, 0.02, 2),   # x kernels only (Py = 48), ragged CTA rows
     (20, 58, 4, 0.9, -0.3, 0.05, 0.04, 2),  # y/z kernel only (Px = 48)
+    # two kx columns per y/z CTA (four layers, Py = 192 and 256)
+    (20, 90, 4, 1.0, 0.3, 0.05, 0.03, 3),
+    (22, 112, 4, 1.0, 0.25, 0.1, 0.02, 2),
 ]
 
 
