@@ -77,3 +77,21 @@ def test_options_validation_on_host():
         with pytest.raises(binding.SsError) as e:
             binding.ss_create(8, 8, 1, 1.0, 0.3, 0.05, 0.01, 4, binding.make_opts(**kw))
         assert e.value.status == binding.SS_ERR_INVALID_ARG, kw
+
+
+def test_product_path_never_touches_the_oracle():
+    # the package (binding, workloads, study, autograd, build) neither imports nor loads the oracle:
+    # only the tests, the smoke check and the benchmark's CPU baseline may
+    import ast
+    pkg = os.path.join(ROOT, "paper_1804_07135_gb300")
+    for name in os.listdir(pkg):
+        if not name.endswith(".py"):
+            continue
+        tree = ast.parse(open(os.path.join(pkg, name)).read())
+        for node in ast.walk(tree):
+            if isinstance(node, ast.Import):
+                assert all(a.name.split(".")[0] != "oracle" for a in node.names), name
+            if isinstance(node, ast.ImportFrom):
+                assert (node.module or "").split(".")[0] != "oracle", name
+            if isinstance(node, ast.Constant) and isinstance(node.value, str):
+                assert "ssm_oracle" not in node.value, name
