@@ -269,3 +269,23 @@ def test_llg_and_dopri5_on_a_one_column_lattice(ss, prec):
     assert np.abs(got - ref).max() < tol
     ref_rk, _, _, _ = oracle.string_run_rk(_model(c), _unit(s1), 4, 0.05, 1e-6, 1e-8, per_image=True)
     assert np.abs(got_rk - ref_rk).max() < (1e-4 if prec == FP32 else 1e-10)
+
+
+def test_climbing_image_gives_exact_barrier_derivative(ss):
+    # The barrier's derivative by the anisotropy constant, by the envelope theorem, is dE/dK at the saddle
+    # minus dE/dK at the minimum (Eq. 1 is linear in K).  For the coherent rotation of a 3x3 ferromagnet
+    # the saddle is all spins in plane (dE/dK = 0) and the minimum all along z (dE/dK = -N): the
+    # climbing image yields N = 9 exactly, the plain string's highest image less.
+    c = (3, 3, 1, 1.0, 0.0, 0.2, 0.0, 8)
+    path = _great_circle_path(8, 9)
+    out = {}
+    for climb in (False, True):
+        with ss.StringMethod([c], dt=0.1, precision=FP64) as sm:
+            sm.set_reparam(ss.SS_INTERP_LINEAR, climb)
+            sm.set_path(0, path)
+            sm.step(300)
+            terms = sm.energy_terms(0)  # [image][dE/dJ, dE/dD, dE/dK, dE/dw]
+            k = sm.barrier(0)[1]
+            out[climb] = terms[k, 2] - terms[0, 2]
+    assert abs(out[True] - 9.0) < 1e-6
+    assert out[False] < 9.0 - 1e-2
