@@ -96,8 +96,10 @@ ss_status ss_set_path(ss_ctx* ctx, int string, const void* spins, int dtype, int
 ss_status ss_get_path(ss_ctx* ctx, int string, void* out, int dtype, int on_device);
 
 /* Runs n_iter >= 0 iterations of the string method (Sec. III) on every string of the context.
- * Asynchronous on the context's stream (replayed from a captured CUDA graph).  Errors raised on the
- * device are reported by the next synchronising call.  SS_ERR_STATE if some string has no path. */
+ * Asynchronous on the context's stream (replayed from a captured CUDA graph) under the Euler step;
+ * under a Runge-Kutta integrator (ss_set_integrator) it synchronises once per round of attempts.
+ * Errors raised on the device are reported by the next synchronising call.  SS_ERR_STATE if some
+ * string has no path. */
 ss_status ss_step(ss_ctx* ctx, int n_iter);
 
 /* Energy (Eq. 1 / Eq. 8) of every image of the current path of `string`, into host out[n_images], in
@@ -132,8 +134,9 @@ ss_status ss_energy_terms(ss_ctx* ctx, int string, double* out);
 /* Measures the kernels of one Euler iteration in the current mode: each entry is launched on its own
  * (not from the graph) on the context's stream, bracketed by CUDA events, for `reps` >= 1 timed
  * iterations after one untimed iteration.  ms_out[i] (host, up to max_out entries) receives the mean
- * duration in milliseconds of entry i, in launch order: for each size group xfwd, yz (when the group has
- * a dipole term), xinv (in its step, climbing-image or LLG mode), the two climbing-image kernels as one
+ * duration in milliseconds of entry i, in launch order: for each size group xfwd, yz (with the FFT
+ * dipole term), the direct dipole sums (with SS_DIPOLE_DIRECT), xinv (in its step, climbing-image or LLG
+ * mode), the two climbing-image kernels as one
  * entry (climbing image on), arc (which also reparametrises), the spline apply kernel (spline on).
  * *n_out receives the number of entries.  The strings advance by reps + 1 iterations.  SS_ERR_STATE
  * under a Runge-Kutta integrator.  Synchronises. */
