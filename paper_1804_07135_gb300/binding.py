@@ -466,6 +466,29 @@ class StringMethod:
     def barrier(self, string=0):
         return ss_barrier(self.ctx, string)
 
+    def relax(self, tol=1e-6, check_every=100, max_iter=100000):
+        """Iterate until every string's barrier changes by at most `tol` (in units of J) between two
+        checks `check_every` iterations apart (Sec. III repeats the two steps until the string
+        converges; the paper states no criterion), or until max_iter iterations.  Returns
+        (iterations done, converged, {string: [barrier at each check]})."""
+        if check_every < 1 or max_iter < 0 or not tol >= 0:
+            raise ValueError("check_every >= 1, max_iter >= 0 and tol >= 0 are required")
+        n = ss_num_strings(self.ctx)
+        history = {i: [self.barrier(i)[0]] for i in range(n)}
+        done = 0
+        while done < max_iter:
+            k = min(check_every, max_iter - done)
+            self.step(k)
+            done += k
+            converged = True
+            for i in range(n):
+                dE = self.barrier(i)[0]
+                converged &= abs(dE - history[i][-1]) <= tol
+                history[i].append(dE)
+            if converged:
+                return done, True, history
+        return done, False, history
+
     def field(self, string=0, dtype=np.float64):
         out = np.zeros(self.shape(string), dtype=dtype)
         ss_field(self.ctx, string, out)

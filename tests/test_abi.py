@@ -95,3 +95,27 @@ def test_product_path_never_touches_the_oracle():
                 assert (node.module or "").split(".")[0] != "oracle", name
             if isinstance(node, ast.Constant) and isinstance(node.value, str):
                 assert "ssm_oracle" not in node.value, name
+
+
+def test_relax_loop_logic(monkeypatch):
+    # the convergence loop of StringMethod.relax on a stand-in context whose barrier settles
+    class Fake(binding.StringMethod):
+        def __init__(self):
+            self.ctx = None
+            self.t = 0
+
+        def step(self, n):
+            self.t += n
+
+        def barrier(self, string=0):
+            return (1.0 - 0.5 ** (self.t / 100.0), 0)
+
+    monkeypatch.setattr(binding, "ss_num_strings", lambda ctx: 2)
+    sm = Fake()
+    done, ok, hist = sm.relax(tol=1e-3, check_every=100, max_iter=10000)
+    assert ok and done % 100 == 0 and abs(hist[0][-1] - hist[0][-2]) <= 1e-3 < abs(hist[0][-2] - hist[0][-3])
+    sm = Fake()
+    done, ok, _ = sm.relax(tol=0.0, check_every=50, max_iter=120)
+    assert not ok and done == 120
+    with pytest.raises(ValueError):
+        sm.relax(check_every=0)

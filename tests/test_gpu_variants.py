@@ -289,3 +289,15 @@ def test_climbing_image_gives_exact_barrier_derivative(ss):
             out[climb] = terms[k, 2] - terms[0, 2]
     assert abs(out[True] - 9.0) < 1e-6
     assert out[False] < 9.0 - 1e-2
+
+
+def test_relax_until_the_barrier_settles(ss):
+    # the convergence loop on the coherent-rotation saddle with the climbing image: it stops once the
+    # barrier moves by less than the tolerance between checks, at N K
+    c = (3, 3, 1, 1.0, 0.0, 0.2, 0.0, 8)
+    with ss.StringMethod([c], dt=0.1, precision=FP64) as sm:
+        sm.set_reparam(ss.SS_INTERP_LINEAR, True)
+        sm.set_path(0, _great_circle_path(8, 9))
+        done, ok, hist = sm.relax(tol=1e-10, check_every=50, max_iter=5000)
+    assert ok and done < 5000
+    assert abs(hist[0][-1] - 1.8) < 1e-8
