@@ -102,9 +102,12 @@ ss_status ss_get_path(ss_ctx* ctx, int string, void* out, int dtype, int on_devi
  * string has no path. */
 ss_status ss_step(ss_ctx* ctx, int n_iter);
 
-/* Energy (Eq. 1 / Eq. 8) of every image of the current path of `string`, into host out[n_images], in
- * FP64: a fresh field evaluation of the current path; the local terms are summed in FP64 from the
- * stored spins renormalised in FP64.  Synchronises. */
+/* Energy (Eq. 1 / Eq. 8) of every image of the current path of `string`, into host out[n_images]: a
+ * fresh FP64 evaluation of the current path -- the stored spins renormalised in FP64, every term
+ * (the dipole convolution included) in FP64.  On an SS_PREC_FP32 context this is the FP64 pipeline
+ * applied to the FP32 state widened to FP64, so the reported energies carry no FP32 round-off of
+ * their own (only the FP32 trajectory's); its FP64 buffers (about twice the context's) are allocated
+ * on the first call of this, ss_barrier, ss_energy_terms or ss_grad with dE_dJDKw.  Synchronises. */
 ss_status ss_energies(ss_ctx* ctx, int string, double* out);
 
 /* Per-image energies from the last ss_step iteration (the state before that iteration's step),
@@ -121,14 +124,16 @@ ss_status ss_barrier(ss_ctx* ctx, int string, double* dE, int* k_max);
 ss_status ss_field(ss_ctx* ctx, int string, void* out, int dtype, int on_device);
 
 /* Derivatives of the energy of image `image` of `string` (Eq. 2 and the linearity of Eq. 1 in its
- * constants): dE_ds ([N][3], dtype, host or device; may be NULL) receives dE/ds = -h, and
- * dE_dJDKw (host, 4 doubles; may be NULL) receives (dE/dJ, dE/dD, dE/dK, dE/dw), each the energy
- * term with its constant set to 1, in FP64.  Synchronises. */
+ * constants): dE_ds ([N][3], dtype, host or device; may be NULL) receives dE/ds = -h (the field in the
+ * context's precision), and dE_dJDKw (host, 4 doubles; may be NULL) receives (dE/dJ, dE/dD, dE/dK,
+ * dE/dw), each the energy term with its constant set to 1, from the FP64 evaluation of ss_energies.
+ * Synchronises. */
 ss_status ss_grad(ss_ctx* ctx, int string, int image, void* dE_ds, int dtype, int on_device, double* dE_dJDKw);
 
 /* The four energy terms of every image of the current path of `string`, from one evaluation: host
  * out[n_images][4] = (dE/dJ, dE/dD, dE/dK, dE/dw) per image (Eq. 1 is linear in each constant, so each
- * entry is that term with its constant set to 1), in FP64.  Synchronises. */
+ * entry is that term with its constant set to 1), from the FP64 evaluation of ss_energies.
+ * Synchronises. */
 ss_status ss_energy_terms(ss_ctx* ctx, int string, double* out);
 
 /* Measures the kernels of one Euler iteration in the current mode: each entry is launched on its own
@@ -143,26 +148,29 @@ ss_status ss_energy_terms(ss_ctx* ctx, int string, double* out);
 ss_status ss_time_kernels(ss_ctx* ctx, int reps, double* ms_out, int max_out, int* n_out);
 
 /* Effective field of a batch of images, for callers that cannot allocate device memory.  The paper
- * has no counterpart: this exists for code that must not call cudaMalloc -- an application that owns
- * all device memory through its own pool, a plugin whose host forbids allocation, or code running
- * while an allocation would disturb the caller's memory accounting.  It computes the same field as
- * ss_field (Eqs. 2-7, FP32 path, dipole by the zero-padded FFT convolution) without a context and
- * without allocating: every intermediate lives in one device array built into libss, of 32 MiB,
- * which each GPU that loads the library keeps reserved until the process exits.
- *   spins  device, [n_images][N][3] float32 (normalised on the fly; need not be unit length)
- *   field  device, [n_images][N][3] float32, written
+ * has no counterpart: this entry point exists for code that must not call cudaMalloc -- an application
+ * that owns all device memory through its own pool, or a plugin whose host forbids allocation.  It
+ * returns the same field as ss_field on an FP32 context (dipole term by the zero-padded FFT
+ * convolution) without a context and without allocating: every intermediate lives in one device array
+ * built into libss, of 32 MiB, which each GPU that loads the library keeps reserved until the process
+ * exits.
+ *   spins  device memory of the current device, [n_images][N][3] float32 (normalised on the fly; need
+ *          not be unit length)
+ *   field  device memory of the current device, [n_images][N][3] float32, written
  *   stream cudaStream_t (NULL = legacy default stream); the call synchronises it before returning
  * Limits: dims in [1,1024] x [1,1024] x [1,64], n_images in [1,1024], and the scratch the call needs
  * must fit the 32 MiB array -- roughly 96*nz*Px*Py bytes while the dipole spectrum is built (Px, Py
  * the padded lengths, about 2*nx and 2*ny) and 24*n_images*N + 48*ceil(n_images/2)*nz*ny*Px bytes
  * for the images; larger requests return SS_ERR_INVALID_ARG without touching the GPU.
  * The first call on each device looks up the array's device address (cudaGetSymbolAddress, with that
- * device current) and raises kernel shared-memory limits: make that first call before any stream
- * capture.  All calls share the one array and it keeps the last call's contents (each call rewrites
- * what it reads and clears its error word), so calls whose GPU work overlaps -- on two streams, or
- * from two threads -- race and must be serialised by the caller.
- * Errors: SS_ERR_INVALID_ARG (bad dims/constants/pointers, too large, or a zero-norm/non-finite input
- * spin), SS_ERR_CUDA (no sm_103 device or a CUDA failure).  ss_last_error does not cover this call. */
+ * device current) and raises kernel shared-memory limits.  The call cannot be captured in a CUDA graph:
+ * it synchronises its stream and reads an error word back, so a stream under capture is refused with
+ * SS_ERR_STATE before any work is issued.  All calls share the one array and it keeps the last call's
+ * contents (each call rewrites what it reads and clears its error word), so calls whose GPU work
+ * overlaps -- on two streams, or from two threads -- race and must be serialised by the caller.
+ * Errors: SS_ERR_INVALID_ARG (bad dims or constants, a pointer that is not device memory of the current
+ * device, too large, or a zero-norm/non-finite input spin), SS_ERR_STATE (capturing stream),
+ * SS_ERR_CUDA (no sm_103 device or a CUDA failure).  ss_last_error does not cover this call. */
 ss_status ss_field_noalloc(int nx, int ny, int nz, double J, double D, double K, double w_dip, int n_images,
                            const float* spins, float* field, void* stream);
 

@@ -4,7 +4,8 @@ The energy of every image (Eq. 1) is a function of the spin components and, line
 constants (J, D, K, w).  Its partial derivatives are
     dE_k/ds_k = -h_k                      (Eq. 2: the effective field, every term of it),
     dE_k/d(J, D, K, w) = the four terms   (each term of Eq. 1 with its constant set to 1),
-both evaluated by the library's kernels (the field kernel and the FP64 term reductions).  The spin
+both evaluated by the library's kernels: the field in the context's precision, the terms by the FP64
+evaluation the library uses for every reported energy.  The spin
 gradient is the unconstrained partial derivative of Eq. 1 written in the spin components; callers
 that optimise on the unit sphere project it themselves.  d(barrier)/d(theta) follows from the
 envelope theorem at the two stationary images: dE/dtheta at the highest image minus at image 0.
@@ -35,7 +36,9 @@ class StringEnergy(torch.autograd.Function):
         sm.set_path(string, src)
         energies = sm.energies(string)
         terms = sm.energy_terms(string)
-        field = torch.zeros(spins.shape, dtype=torch.float32, device=spins.device)
+        # the field in the context's precision (FP64 contexts keep their FP64 field)
+        fdt = torch.float64 if sm.opts.precision == binding.SS_PREC_FP64 else torch.float32
+        field = torch.zeros(spins.shape, dtype=fdt, device=spins.device)
         binding.ss_field(sm.ctx, string, field)
         ctx.save_for_backward(field, torch.from_numpy(terms))
         ctx.spin_dtype = spins.dtype

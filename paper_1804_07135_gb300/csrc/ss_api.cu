@@ -75,6 +75,7 @@ std::vector<double2> twiddles(int P) {
 
 // ---- context --------------------------------------------------------------------------------------
 struct Group {
+    int rbytes = 4;  // bytes of the group's real type (4: the FP32 path, 8: FP64)
     int nx = 0, ny = 0, nz = 0, N = 0, Px = 1, Py = 1;
     int n_img = 0, n_pairs = 0;
     std::vector<int> strs;  // context string ids, in group order
@@ -134,6 +135,10 @@ struct ss_ctx {
     ss_free_fn free_fn = nullptr;
     void* alloc_user = nullptr;
     cudaGraphExec_t graph1 = nullptr, graphN = nullptr;
+    // several size groups: one graph branch per group (their strings never interact), forked from and
+    // joined back into cs
+    std::vector<cudaStream_t> branch;  // size groups 1.. (group 0 stays on cs)
+    std::vector<cudaEvent_t> branch_ev;  // [0] fork, [1..] joins
     int graphN_iters = 64;
     int integrator = 0;  // SS_INT_EULER or one of the Runge-Kutta kinds
     int interp = 0;      // SS_INTERP_LINEAR or SS_INTERP_SPLINE
@@ -142,6 +147,9 @@ struct ss_ctx {
     double alpha = 0.0;  // damping of the precessional dynamics
     double rtol = 1e-6, atol = 1e-8;
     int* h_active = nullptr;  // pinned, one flag per size group
+    // FP32 contexts: an FP64 copy of every size group's evaluation pipeline, built on the first energy
+    // query; reported energies and energy terms are evaluated there from the FP32 state
+    std::vector<Group> ev64;
     std::string err;
 };
 
@@ -243,31 +251,38 @@ template <typename T> GroupArgs<T> group_args(const ss_ctx* c, const Group& g) {
 
 // Rows per CTA and block sizes of the x-forward (a) and x-inverse (c) kernels and the shared memory
 // they need.
-void set_rows(const ss_ctx* c, Group& g, int ty_a, int ty_c, int thr_a = 256, int thr_c = 256) {
-    const size_t cs = 2 * real_size(c);
-    if (g.dipole && f128_x((int)real_size(c), g.Px)) {
+void set_rows(Group& g, int ty_a, int ty_c, int thr_a = 256, int thr_c = 256) {
+    const size_t cs = 2 * (size_t)g.rbytes;
+    if (g.dipole && f128_x(g.rbytes, g.Px)) {
         ty_a = f128_x_rows(ty_a);
         ty_c = f128_x_rows(ty_c);
     }
+    const bool x2 = g.dipole && x2p_ok(g.rbytes, g.Px);  // two-pass x kernels: fixed rows per CTA
+    if (x2) ty_a = ty_c = kX2Rows;
     g.ty_a = ty_a;
     g.ty_c = ty_c;
     g.thr_a = thr_a;
     g.thr_c = thr_c;
     g.smem_a = (size_t)(g.Px + 3 * g.ty_a * g.lsx) * cs;
     g.smem_c = (size_t)(g.Px + 3 * g.ty_c * g.lsx) * cs + 32 * 8 * sizeof(double);
-    if (g.dipole && f128_x((int)real_size(c), g.Px)) {  // the launchers derive these shapes themselves
+    if (g.dipole && f128_x(g.rbytes, g.Px)) {  // the launchers derive these shapes themselves
         g.thr_a = f128_x_threads(ty_a);
         g.thr_c = f128_x_threads(ty_c);
         g.smem_a = f128_x_smem(ty_a);
         g.smem_c = f128_x_smem(ty_c);
+    }
+    if (x2) {
+        g.thr_a = g.thr_c = kX2Threads;
+        g.smem_a = x2_smem(g.Px, false);
+        g.smem_c = x2_smem(g.Px, true);
     }
     g.smem_c_eval = g.smem_c;
     g.n_eblk = g.nz * ((g.ny + g.ty_c - 1) / g.ty_c);
 }
 
 // Launch shapes of one size group (shared memory, rows per CTA, block sizes).
-void configure_group(const ss_ctx* c, Group& g) {
-    const size_t cs = 2 * real_size(c);  // complex element
+void configure_group(Group& g) {
+    const size_t cs = 2 * (size_t)g.rbytes;  // complex element
     g.lsx = fft_line_stride(g.Px);
     g.lsy = fft_line_stride(g.Py);
     // x kernels: 256 threads; rows per CTA such that the 3*rows lines take one FFT pass and the
@@ -281,18 +296,22 @@ void configure_group(const ss_ctx* c, Group& g) {
             break;
         }
     }
-    if (g.dipole && f128_x((int)real_size(c), g.Px)) ty = 8;  // 384 threads
-    set_rows(c, g, ty, ty, 512, 512);
+    if (g.dipole && f128_x(g.rbytes, g.Px)) ty = 8;  // 384 threads
+    set_rows(g, ty, ty, 512, 512);
     // y/z kernel: all 3*nz lines of one (pair, kx) in shared memory, plus the kx slab of the tensor
     // spectrum when it is small enough to stage
     g.thr_b = kMaxThreadsYz;
     g.smem_b = (size_t)(g.Py + 3 * g.nz * g.lsy) * cs;
-    const size_t slab = (size_t)(g.Py / 2 + 1) * g.nz * 6 * real_size(c);
+    const size_t slab = (size_t)(g.Py / 2 + 1) * g.nz * 6 * (size_t)g.rbytes;
     if (slab <= 24 * 1024) g.smem_b += slab;
-    if (g.dipole && f128_yz((int)real_size(c), g.Py, g.nz)) {
+    if (g.dipole && f128_yz(g.rbytes, g.Py, g.nz)) {
         bool stage = false;
         g.thr_b = f128_yz_threads(g.nz);
         g.smem_b = f128_yz_smem(g.nz, g.Py, &stage);
+    }
+    if (g.dipole && yz2p_ok(g.rbytes, g.Py, g.nz, g.Px)) {
+        g.thr_b = kYz2Threads;
+        g.smem_b = yz2p_smem(g.Py, g.nz);
     }
 }
 
@@ -434,7 +453,7 @@ template <typename T> ss_status tune_group(ss_ctx* c, Group& g) {
         if (sscanf(env, "%d:%d:%d:%d", &ta, &ya, &tc, &yc) == 4 &&
             (f128 || ((ta == 256 || ta == 512) && (tc == 256 || tc == 512))) && ya >= 1 && yc >= 1 && ya <= g.ny &&
             yc <= g.ny) {  // the x kernels for Px = 128 take 2, 4 or 8 rows (others become 8)
-            set_rows(c, g, ya, yc, ta, tc);
+            set_rows(g, ya, yc, ta, tc);
             return SS_OK;
         }
     }
@@ -444,13 +463,15 @@ template <typename T> ss_status tune_group(ss_ctx* c, Group& g) {
         for (auto& e : g_tuned)
             if (e.first == key) {
                 const int* v = e.second.data();
-                set_rows(c, g, v[1], v[3], v[0], v[2]);
+                set_rows(g, v[1], v[3], v[0], v[2]);
                 return SS_OK;
             }
     }
     const size_t cs = 2 * real_size(c);
     std::vector<std::pair<int, int>> cands;  // (threads, rows)
-    if (g.dipole && f128_x((int)real_size(c), g.Px)) {
+    if (g.dipole && x2p_ok((int)real_size(c), g.Px)) {
+        cands.push_back({kX2Threads, kX2Rows});  // one shape: nothing to tune
+    } else if (g.dipole && f128_x((int)real_size(c), g.Px)) {
         for (int ty : {2, 4, 8})  // 48 threads per row; row counts that divide 16 keep the passes conflict-free
             cands.push_back({f128_x_threads(ty), ty});
     } else {
@@ -469,7 +490,7 @@ template <typename T> ss_status tune_group(ss_ctx* c, Group& g) {
     std::pair<int, int> pick[2] = {{g.thr_a, g.ty_a}, {g.thr_c, g.ty_c}};
     const T dt = T(c->opts.dt);
     for (auto [thr, ty] : cands) {
-        set_rows(c, g, ty, ty, thr, thr);
+        set_rows(g, ty, ty, thr, thr);
         GroupArgs<T> a = group_args<T>(c, g);
         for (int which = 0; which < 2; ++which) {
             auto run = [&]() {
@@ -498,7 +519,7 @@ template <typename T> ss_status tune_group(ss_ctx* c, Group& g) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    set_rows(c, g, pick[0].second, pick[1].second, pick[0].first, pick[1].first);
+    set_rows(g, pick[0].second, pick[1].second, pick[0].first, pick[1].first);
     const size_t M = (size_t)3 * g.N * g.n_img * real_size(c);
     CUDA_TRY(c, cudaMemsetAsync(g.s, 0, M, c->cs));
     CUDA_TRY(c, cudaMemsetAsync(g.sp, 0, M, c->cs));
@@ -676,10 +697,10 @@ template <typename T> ss_status rk_iterations(ss_ctx* c, int n_iter) {
     return SS_OK;
 }
 
-// Issue one iteration (Sec. III) of every size group on stream st.
-template <typename T> void issue_iteration(ss_ctx* c, cudaStream_t st) {
+// Issue one iteration (Sec. III) of size group g on stream st.
+template <typename T> void issue_group_iteration(ss_ctx* c, Group& g, cudaStream_t st) {
     const T dt = T(c->opts.dt);
-    for (Group& g : c->groups) {
+    {
         GroupArgs<T> a = group_args<T>(c, g);
         launch_xfwd<T>(a, g.dipole, g.thr_a, g.smem_a, st);
         if (g.dipole) launch_yz<T>(a, g.thr_b, g.smem_b, st);
@@ -791,22 +812,109 @@ ss_status evaluate_group(ss_ctx* c, Group& g, bool want_field) {
     return SS_OK;
 }
 
+// The FP64 evaluation copy of every size group of an FP32 context (same lattice, strings, constants and
+// dipole spectrum, FP64 buffers and kernels), set up on first use.
+ss_status ensure_ev64(ss_ctx* c) {
+    if (use_fp64(c) || !c->ev64.empty()) return SS_OK;
+    std::vector<Group> ev;
+    for (const Group& g : c->groups) {
+        Group e;
+        e.rbytes = 8;
+        e.nx = g.nx;
+        e.ny = g.ny;
+        e.nz = g.nz;
+        e.N = g.N;
+        e.Px = g.Px;
+        e.Py = g.Py;
+        e.n_img = g.n_img;
+        e.n_pairs = g.n_pairs;
+        e.strs = g.strs;
+        e.str_img0 = g.str_img0;
+        e.str_K = g.str_K;
+        e.dipole = g.dipole;
+        e.direct = g.direct;
+        e.planx = g.planx;
+        e.plany = g.plany;
+        configure_group(e);
+        if (e.smem_a > 227 * 1024 || e.smem_b > 227 * 1024 || e.smem_c > 227 * 1024)
+            return fail(c, SS_ERR_INVALID_ARG, "lattice %d x %d x %d: the FP64 evaluation needs more shared memory than a CTA has",
+                        g.nx, g.ny, g.nz);
+        ev.push_back(e);
+    }
+    set_smem_limits<double>(227 * 1024);
+    for (Group& e : ev) TRY(setup_group<double>(c, e));
+    CUDA_TRY(c, cudaStreamSynchronize(c->cs));
+    c->ev64 = std::move(ev);
+    return SS_OK;
+}
+
+// Energies and energy terms of every image of size group gi, evaluated in FP64 (Eqs. 1, 8): on the FP64
+// path by its own evaluation, on the FP32 path by the FP64 pipeline applied to the FP32 state (the
+// gathered spins widened to FP64), so that the reported energies carry no FP32 convolution round-off.
+// *out points at the group whose eval_E / eval_terms hold the result once the stream reaches them.
+ss_status evaluate_energies(ss_ctx* c, int gi, const Group** out) {
+    Group& g = c->groups[gi];
+    if (use_fp64(c)) {
+        TRY(evaluate_group(c, g, false));
+        *out = &g;
+        return SS_OK;
+    }
+    TRY(ensure_ev64(c));
+    Group& e = c->ev64[gi];
+    issue_materialise<float>(c, g, c->cs);
+    launch_widen_unit((const float*)g.s, (double*)e.sp, g.n_img, g.N, c->cs);
+    issue_eval<double>(c, e, nullptr, c->cs);
+    CUDA_TRY(c, cudaGetLastError());
+    *out = &e;
+    return SS_OK;
+}
+
 ss_status check_paths(ss_ctx* c, const Group& g) {
     for (int id : g.strs)
         if (!c->strs[id].has_path) return fail(c, SS_ERR_STATE, "string %d has no path (call ss_set_path first)", id);
     return SS_OK;
 }
 
+// Capture `iters` iterations of every size group.  With several groups each group's chain of launches is
+// its own branch of the graph (forked from and joined back into cs), so the groups' kernels overlap on
+// the GPU instead of running one group after another; within a branch the launches keep their order and
+// programmatic dependent launch.
 ss_status capture_graph(ss_ctx* c, int iters, cudaGraphExec_t* out) {
+    const int G = (int)c->groups.size();
+    if (G > 1 && c->branch.empty()) {
+        c->branch.assign(G - 1, nullptr);
+        c->branch_ev.assign(G, nullptr);
+        for (auto& st : c->branch) CUDA_TRY(c, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        for (auto& ev : c->branch_ev) CUDA_TRY(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    }
     cudaGraph_t graph = nullptr;
     CUDA_TRY(c, cudaStreamBeginCapture(c->cs, cudaStreamCaptureModeThreadLocal));
-    for (int i = 0; i < iters; ++i) {
-        if (use_fp64(c))
-            issue_iteration<double>(c, c->cs);
-        else
-            issue_iteration<float>(c, c->cs);
+    cudaError_t e = cudaSuccess;
+    if (G > 1) {
+        e = cudaEventRecord(c->branch_ev[0], c->cs);
+        for (int b = 0; b < G - 1 && e == cudaSuccess; ++b) e = cudaStreamWaitEvent(c->branch[b], c->branch_ev[0], 0);
     }
-    cudaError_t e = cudaStreamEndCapture(c->cs, &graph);
+    for (int gi = 0; gi < G && e == cudaSuccess; ++gi) {
+        cudaStream_t st = gi == 0 ? c->cs : c->branch[gi - 1];
+        for (int i = 0; i < iters; ++i) {
+            if (use_fp64(c))
+                issue_group_iteration<double>(c, c->groups[gi], st);
+            else
+                issue_group_iteration<float>(c, c->groups[gi], st);
+        }
+    }
+    if (G > 1) {
+        for (int b = 0; b < G - 1 && e == cudaSuccess; ++b) {
+            e = cudaEventRecord(c->branch_ev[b + 1], c->branch[b]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(c->cs, c->branch_ev[b + 1], 0);
+        }
+    }
+    const cudaError_t e_end = cudaStreamEndCapture(c->cs, &graph);
+    if (e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return fail(c, SS_ERR_CUDA, "graph capture (branches): %s", cudaGetErrorString(e));
+    }
+    e = e_end;
     if (e != cudaSuccess) return fail(c, SS_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
     e = cudaGraphInstantiate(out, graph, 0);
     cudaGraphDestroy(graph);
@@ -931,7 +1039,8 @@ ss_status ss_create_batch(int n_strings, const ss_string_desc* descs, const ss_o
         g.Py = g.dipole ? padded_len(g.ny) : 1;
         g.planx = make_plan(g.Px);
         g.plany = make_plan(g.Py);
-        configure_group(c, g);
+        g.rbytes = (int)real_size(c);
+        configure_group(g);
         const size_t smem_max = 227 * 1024;
         if (g.smem_a > smem_max || g.smem_b > smem_max || g.smem_c > smem_max)
             return bail(fail(c, SS_ERR_INVALID_ARG, "lattice %d x %d x %d needs more shared memory than a CTA has",
@@ -1074,6 +1183,10 @@ ss_status ss_set_reparam(ss_ctx* c, int interp, int climb) {
     // the captured graphs hold the previous kernel sequence and arguments
     if (c->graph1) cudaGraphExecDestroy(c->graph1);
     if (c->graphN) cudaGraphExecDestroy(c->graphN);
+    for (auto st : c->branch)
+        if (st) cudaStreamDestroy(st);
+    for (auto ev : c->branch_ev)
+        if (ev) cudaEventDestroy(ev);
     c->graph1 = c->graphN = nullptr;
     ss_status st = sync_check(c);
     TRY(leave(c));
@@ -1092,6 +1205,10 @@ ss_status ss_set_dynamics(ss_ctx* c, int kind, double alpha) {
     for (Group& g : c->groups) g.arc.reparam = kind == SS_DYN_STRING && c->opts.reparam_every != 0;
     if (c->graph1) cudaGraphExecDestroy(c->graph1);
     if (c->graphN) cudaGraphExecDestroy(c->graphN);
+    for (auto st : c->branch)
+        if (st) cudaStreamDestroy(st);
+    for (auto ev : c->branch_ev)
+        if (ev) cudaEventDestroy(ev);
     c->graph1 = c->graphN = nullptr;
     return SS_OK;
 }
@@ -1183,8 +1300,9 @@ ss_status ss_energies(ss_ctx* c, int string, double* out) {
     Group& g = c->groups[r.group];
     TRY(check_paths(c, g));
     TRY(enter(c));
-    TRY(evaluate_group(c, g, false));
-    CUDA_TRY(c, cudaMemcpyAsync(out, g.eval_E + (size_t)r.local * g.arc.maxK, r.d.n_images * sizeof(double),
+    const Group* ev = nullptr;
+    TRY(evaluate_energies(c, r.group, &ev));
+    CUDA_TRY(c, cudaMemcpyAsync(out, ev->eval_E + (size_t)r.local * ev->arc.maxK, r.d.n_images * sizeof(double),
                                 cudaMemcpyDeviceToHost, c->cs));
     ss_status st = sync_check(c);
     TRY(leave(c));
@@ -1241,14 +1359,17 @@ ss_status ss_grad(ss_ctx* c, int string, int image, void* dE_ds, int dtype, int 
     Group& g = c->groups[r.group];
     TRY(check_paths(c, g));
     TRY(enter(c));
-    TRY(evaluate_group(c, g, dE_ds != nullptr));
-    if (dE_ds) {
+    if (dE_ds) {  // the field in the path's precision
+        TRY(evaluate_group(c, g, true));
         const char* base = (const char*)g.hout + (size_t)(r.img0 + image) * 3 * g.N * real_size(c);
         TRY(export_soa(c, base, 1, g.N, dE_ds, dtype, on_device, -1.0));
     }
-    if (dE_dJDKw)
-        CUDA_TRY(c, cudaMemcpyAsync(dE_dJDKw, g.eval_terms + ((size_t)r.local * g.arc.maxK + image) * 4,
+    if (dE_dJDKw) {  // the energy terms in FP64
+        const Group* ev = nullptr;
+        TRY(evaluate_energies(c, r.group, &ev));
+        CUDA_TRY(c, cudaMemcpyAsync(dE_dJDKw, ev->eval_terms + ((size_t)r.local * ev->arc.maxK + image) * 4,
                                     4 * sizeof(double), cudaMemcpyDeviceToHost, c->cs));
+    }
     ss_status st = sync_check(c);
     TRY(leave(c));
     return st;
@@ -1261,9 +1382,10 @@ ss_status ss_energy_terms(ss_ctx* c, int string, double* out) {
     Group& g = c->groups[r.group];
     TRY(check_paths(c, g));
     TRY(enter(c));
-    TRY(evaluate_group(c, g, false));
-    CUDA_TRY(c, cudaMemcpyAsync(out, g.eval_terms + (size_t)r.local * g.arc.maxK * 4, (size_t)r.d.n_images * 4 * sizeof(double),
-                                cudaMemcpyDeviceToHost, c->cs));
+    const Group* ev = nullptr;
+    TRY(evaluate_energies(c, r.group, &ev));
+    CUDA_TRY(c, cudaMemcpyAsync(out, ev->eval_terms + (size_t)r.local * ev->arc.maxK * 4,
+                                (size_t)r.d.n_images * 4 * sizeof(double), cudaMemcpyDeviceToHost, c->cs));
     ss_status st = sync_check(c);
     TRY(leave(c));
     return st;
@@ -1362,6 +1484,10 @@ void ss_destroy(ss_ctx* c) {
     if (c->cs) cudaStreamSynchronize(c->cs);
     if (c->graph1) cudaGraphExecDestroy(c->graph1);
     if (c->graphN) cudaGraphExecDestroy(c->graphN);
+    for (auto st : c->branch)
+        if (st) cudaStreamDestroy(st);
+    for (auto ev : c->branch_ev)
+        if (ev) cudaEventDestroy(ev);
     for (const auto& a : c->allocs) {
         if (c->free_fn)
             c->free_fn(a.first, a.second, c->device, c->opts.stream, c->alloc_user);

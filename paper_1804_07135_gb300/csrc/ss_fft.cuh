@@ -84,6 +84,54 @@ template <typename C> struct Dft<8, C> {
     }
 };
 
+// Size 6 and 12 by Cooley-Tukey over 3 x 2 and 3 x 4 (n = M n1 + n2, k = k1 + 3 k2 with M = 2 or 4):
+// 3-point DFTs over n1 for each n2, the twiddles W_N^{n2 k1}, then 2- or 4-point DFTs over n2.
+template <typename C> struct Dft<6, C> {
+    static __device__ __forceinline__ void run(C* v) {
+        using R = decltype(v[0].x);
+        const R h = R(0.8660254037844386467637231707529362);  // sqrt(3)/2
+        C a[3] = {v[0], v[2], v[4]}, b[3] = {v[1], v[3], v[5]};
+        Dft<3, C>::run(a);
+        Dft<3, C>::run(b);
+        b[1] = cmul(b[1], C{R(0.5), -h});    // W_6^1
+        b[2] = cmul(b[2], C{R(-0.5), -h});   // W_6^2
+#pragma unroll
+        for (int k1 = 0; k1 < 3; ++k1) {
+            v[k1] = cadd(a[k1], b[k1]);
+            v[k1 + 3] = csub(a[k1], b[k1]);
+        }
+    }
+};
+
+template <typename C> struct Dft<12, C> {
+    static __device__ __forceinline__ void run(C* v) {
+        using R = decltype(v[0].x);
+        const R h = R(0.8660254037844386467637231707529362);  // sqrt(3)/2
+        C a[4][3];
+#pragma unroll
+        for (int n2 = 0; n2 < 4; ++n2) {
+            a[n2][0] = v[n2];
+            a[n2][1] = v[4 + n2];
+            a[n2][2] = v[8 + n2];
+            Dft<3, C>::run(a[n2]);
+        }
+        // W_12^{n2 k1}: n2 k1 in {1, 2, 2, 3, 4, 6}
+        a[1][1] = cmul(a[1][1], C{h, R(-0.5)});      // W_12^1
+        a[1][2] = cmul(a[1][2], C{R(0.5), -h});      // W_12^2
+        a[2][1] = cmul(a[2][1], C{R(0.5), -h});      // W_12^2
+        a[2][2] = cmul(a[2][2], C{R(-0.5), -h});     // W_12^4
+        a[3][1] = cmi(a[3][1]);                      // W_12^3 = -i
+        a[3][2] = C{-a[3][2].x, -a[3][2].y};         // W_12^6 = -1
+#pragma unroll
+        for (int k1 = 0; k1 < 3; ++k1) {
+            C q[4] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1]};
+            Dft<4, C>::run(q);
+#pragma unroll
+            for (int k2 = 0; k2 < 4; ++k2) v[k1 + 3 * k2] = q[k2];
+        }
+    }
+};
+
 // Size-R DFTs whose inputs R/2..R-1 are zero (the zero-padded half of a forward transform).
 template <int R, typename C> struct DftHalfIn;
 template <typename C> struct DftHalfIn<2, C> {
@@ -439,6 +487,86 @@ template <typename C> __device__ __forceinline__ void f128_pass2(C (&v)[8], cons
     const C* z = zl + k1;
 #pragma unroll
     for (int n2 = 0; n2 < 8; ++n2) v[n2] = z[n2 * kF128N2];
+    Dft<8, C>::run(v);
+}
+
+// ---- lengths P = 16 R2 (R2 = 12, 16, 24: 192, 256, 384) in two register passes ------------------------
+// A line of P elements is held in shared memory as R2 rows of 16 at row stride kT2Row = 17 (element
+// (r, c) at r * 17 + c; a line takes kT2Row * R2 slots).  With n = R2 n1 + n2, k = k1 + 16 k2 (n1, k1 < 16;
+// n2, k2 < R2) the forward transform is
+//   X[k1 + 16 k2] = sum_{n2} W_R2^{n2 k2} Z[n2][k1],   Z[n2][k1] = W_P^{n2 k1} sum_{n1} W_16^{n1 k1} x[R2 n1 + n2],
+// both sums split by the parity of their output index into half-size DFTs (W = W_P, as for length 128):
+// pass 1, role (n2, par), inputs x[R2 n1 + n2]: an 8-point DFT of (x[R2 j + n2] +- x[R2 (j+8) + n2]) W_16^{j par}
+//   -> row n2 of Z (k1 = 2m + par);
+// pass 2, role (k1, par2), column k1 of Z: an R2/2-point DFT of (Z[j][k1] +- Z[j + R2/2][k1]) W_R2^{j par2}
+//   -> X[k1 + 16 (2m + par2)], written back in place into column k1 (row k2), so X[ky] sits at
+//   (ky >> 4) * 17 + (ky & 15).
+// The inverse direction (a forward transform of the conjugate) starts from that column layout: with
+// y = y2 + R2 y1,
+//   Y[y2 + R2 y1] = sum_{k1} W_16^{k1 y1} T[k1][y2],   T[k1][y2] = W_P^{k1 y2} sum_{k2} W_R2^{k2 y2} V[k1 + 16 k2];
+// pass A, role (k1, par2), column k1: the R2/2-point DFTs as in pass 2, times W_P^{k1 y2}, back into column k1
+//   (row y2);
+// pass B, role (y2, par), row y2: an 8-point DFT of (T[j][y2] +- T[j+8][y2]) W_16^{j par} -> Y[y2 + R2 (2m + par)];
+// an inverse read below P/2 keeps m < 4.  Twiddles W_P^e come from the flat table (e < P); the ramp
+// W_R2^j = W_P^{16 j}.
+__device__ __forceinline__ int t2_pos(int ky) { return (ky >> 4) * kT2Row + (ky & 15); }
+
+// Pass 1 of a line whose upper half is zero: u[j] = x[R2 j + n2] (j < 8) on entry; writes row n2 of Z.
+template <int P, typename C>
+__device__ __forceinline__ void t2_pass1(C (&u)[8], int n2, int par, const C* __restrict__ tw, C* line) {
+    if (par) mul_w16_ramp(u);
+    Dft<8, C>::run(u);
+    C* z = line + n2 * kT2Row + par;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) z[2 * m] = cmul(u[m], tw[n2 * (2 * m + par)]);  // tw[0] = 1 exactly
+}
+
+// The R2/2-point DFTs of pass 2 (TW_OUT = false) or pass A (TW_OUT = true) for column k1 and parity par2:
+// a[m] = the output of row 2m + par2 (times W_P^{k1 (2m + par2)} in pass A).  col(j) returns the column's
+// row j (from shared or global memory).
+template <int P, bool TW_OUT, typename C, typename Col>
+__device__ __forceinline__ void t2_col_vals(C (&a)[P / 32], Col col, int k1, int par2, const C* __restrict__ tw) {
+    constexpr int R2 = P / 16, H = R2 / 2;
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+        const C lo = col(j), hi = col(j + H);
+        a[j] = par2 ? csub(lo, hi) : cadd(lo, hi);
+    }
+    if (par2) {
+#pragma unroll
+        for (int j = 1; j < H; ++j) a[j] = cmul(a[j], tw[16 * j]);  // W_R2^j
+    }
+    Dft<H, C>::run(a);
+    if constexpr (TW_OUT) {
+#pragma unroll
+        for (int m = 0; m < H; ++m) a[m] = cmul(a[m], tw[k1 * (2 * m + par2)]);
+    }
+}
+
+// Pass 2 / pass A in place on a shared line: reads column k1, writes rows 2m + par2 of the same column.
+// The caller pairs the roles par2 = 0 and 1 of a column in one warp; the column is read whole before
+// either writes (a __syncwarp between the reads and the writes).
+template <int P, bool TW_OUT, typename C>
+__device__ __forceinline__ void t2_cols(C* line, int k1, int par2, const C* __restrict__ tw) {
+    constexpr int H = P / 32;
+    C a[H];
+    const C* col = line + k1;
+    t2_col_vals<P, TW_OUT>(a, [&](int j) { return col[j * kT2Row]; }, k1, par2, tw);
+    __syncwarp();
+    C* o = line + k1 + par2 * kT2Row;
+#pragma unroll
+    for (int m = 0; m < H; ++m) o[2 * m * kT2Row] = a[m];
+}
+
+// Pass B of row y2: v[m] = Y[y2 + R2 (2m + par)] for m < 4 (the outputs below P/2).
+template <typename C> __device__ __forceinline__ void t2_passB(C (&v)[8], const C* line, int y2, int par) {
+    const C* r = line + y2 * kT2Row;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const C lo = r[j], hi = r[j + 8];
+        v[j] = par ? csub(lo, hi) : cadd(lo, hi);
+    }
+    if (par) mul_w16_ramp(v);
     Dft<8, C>::run(v);
 }
 

@@ -192,6 +192,31 @@ inline size_t f128_yz_smem(int nz, int Py, bool* stage_dhat) {
     return (size_t)2 * 3 * nz * kF128Line * 8;
 }
 
+
+// Lengths 192, 256 and 384 in two register passes (FP32, ss_fft.cuh): a line is R2 = P/16 rows of 16 at
+// row stride kT2Row; the y/z kernel for those Py with 1, 4 or 8 layers (24 lines per CTA: 8, 2 or 1 kx
+// columns), the x kernels for those Px with kX2Rows rows per CTA.
+constexpr int kT2Row = 17;
+__host__ __device__ constexpr int t2_line(int P) { return kT2Row * (P / 16); }
+constexpr int kYz2Threads = 384;
+inline int yz2p_kxb(int nz) { return nz == 1 ? 8 : nz == 4 ? 2 : nz == 8 ? 1 : 0; }
+inline bool yz2p_ok(int real_bytes, int Py, int nz, int Px) {
+    if (real_bytes != 4 || !(Py == 192 || Py == 256 || Py == 384)) return false;
+    const int kxb = yz2p_kxb(nz);
+    return kxb > 0 && Px % kxb == 0;
+}
+inline size_t yz2p_smem(int Py, int nz) { return (size_t)3 * nz * yz2p_kxb(nz) * t2_line(Py) * 8; }
+constexpr int kX2Rows = 4;
+constexpr int kX2Threads = 384;
+__host__ __device__ constexpr int x2_round(int v) { return v + ((16 / kX2Rows - v % 16) + 16) % 16; }
+__host__ __device__ constexpr int x2_lsx(int P) { return x2_round(t2_line(P) - 1); }  // transform lines
+__host__ __device__ constexpr int x2_lb(int P) { return x2_round(fft_pad(P / 2 - 1) + 1); }  // x-space lines
+inline bool x2p_ok(int real_bytes, int Px) { return real_bytes == 4 && (Px == 192 || Px == 256 || Px == 384); }
+inline size_t x2_smem(int P, bool inverse) {
+    return (size_t)3 * kX2Rows * (x2_lsx(P) + x2_lb(P)) * 8 + (inverse ? 32 * 8 * 8 : 0);
+}
+
+
 // ---- launchers (defined in ss_kernels.cuh, instantiated for float and double) ----
 template <typename T> void launch_xfwd(const GroupArgs<T>& g, bool do_fft, int nthr, size_t smem, cudaStream_t st);
 template <typename T> void launch_yz(const GroupArgs<T>& g, int nthr, size_t smem, cudaStream_t st);
@@ -224,6 +249,8 @@ void launch_aos_to_soa(const Tin* src, T* dst, int K, int N, int* err, cudaStrea
 template <typename T, typename Tout>
 void launch_soa_to_aos(const T* src, Tout* dst, int K, int N, Tout scale, cudaStream_t st);
 void launch_interp_identity(InterpEntry* tab, int img0, int K, cudaStream_t st);
+// the FP32 state [K][3][N] handed to the FP64 energy evaluation: every spin renormalised in FP64
+void launch_widen_unit(const float* src, double* dst, int K, int N, cudaStream_t st);
 // FP64 setup of the dipole-tensor spectrum: x then y transforms of the padded real-space tensor
 // (data [6*nz][Py][Px] complex, in place), then the octant extraction into dhat.
 void launch_fft_strided_f64(double2* data, const double2* tw, const FftPlan& plan, int n_lines, long elem_stride,

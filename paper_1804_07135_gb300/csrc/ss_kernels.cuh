@@ -37,6 +37,15 @@ __device__ __forceinline__ double sqrt_nr(double x) {
     const double r = fma(-s, s, x);                // residual x - s^2
     return fma(0.5 * y, r, s);                     // one Newton step: ~1e-14 relative
 }
+// 1 / sqrt(x) for positive finite x in FP32 range: an FP32 seed and two Newton-Raphson steps for the
+// reciprocal square root, y <- y + (y / 2) (1 - x y^2), in FP64 multiply-adds (each step squares the
+// relative error: ~1e-7 -> ~1e-14 -> rounding level).
+__device__ __forceinline__ double rsqrt_nr(double x) {
+    double y = (double)rsqrtf((float)x);
+    y = fma(0.5 * y, fma(-x * y, y, 1.0), y);
+    y = fma(0.5 * y, fma(-x * y, y, 1.0), y);
+    return y;
+}
 __device__ __forceinline__ double rcp_nr(double x) {
     double r = (double)(1.0f / (float)x);
     r = fma(r, fma(-x, r, 1.0), r);
@@ -609,6 +618,136 @@ __global__ void __launch_bounds__(kMaxThreadsYz, kMinBlocks128) yz128_kernel(Gro
     }
 }
 
+// yz for Py = P in {192, 256, 384} (ny <= P/2), FP32, NZ layers, KXB kx columns per CTA: the y-transforms
+// in two register passes each way (t2_pass1 / t2_cols / t2_passB, ss_fft.cuh) on lines held in the
+// 17-strided row layout, the z-convolution in place between them.  One shared line per (column, component,
+// layer): 3 NZ KXB lines of t2_line(P) complex elements, read from the spectrum in pass 1 and written back
+// (rows y < ny) in pass B; one shared-memory round trip per pass instead of one per Stockham stage.
+// 384 threads; pass 2 and pass A take one warp per line (16 columns x 2 parities).
+template <int NZ, int P>
+__device__ __forceinline__ void zconv_t2(float2* A, int kx, int Px, const float* dslab, int tid, int nthr) {
+    constexpr int LS = t2_line(P), hy = P / 2, dq = P / 2 + 1;
+    const float sxg = kx > Px / 2 ? -1.f : 1.f;
+    const int nk = nthr / 3;
+    // rounds of nk frequencies; a round reads and writes only its own ky, so one barrier (between its
+    // reads and its writes) orders it against every other round
+    for (int k0 = 0; k0 < P; k0 += nk) {
+        const int a = tid / nk;
+        const int ky = k0 + (tid - a * nk);
+        const bool act = a < 3 && ky < P;
+        float2 out[NZ];
+        int pky = 0;
+        if (act) {
+            const int kyo = min(ky, P - ky);
+            const float syg = ky > hy ? -1.f : 1.f;
+            const float* d = dslab + kyo;
+            pky = t2_pos(ky);
+            const int i0 = a == 0 ? 0 : (a == 1 ? 3 : 4);
+            const int i1 = a == 0 ? 3 : (a == 1 ? 1 : 5);
+            const int i2 = a == 0 ? 4 : (a == 1 ? 5 : 2);
+            const float f0 = a == 0 ? 1.f : (a == 1 ? sxg * syg : sxg);
+            const float f1 = a == 0 ? sxg * syg : (a == 1 ? 1.f : syg);
+            const float f2 = a == 0 ? sxg : (a == 1 ? syg : 1.f);
+            float e0[NZ], e1[NZ], e2[NZ];
+#pragma unroll
+            for (int q = 0; q < NZ; ++q) {
+                e0[q] = d[(q * 6 + i0) * dq] * f0;
+                e1[q] = d[(q * 6 + i1) * dq] * f1;
+                e2[q] = d[(q * 6 + i2) * dq] * f2;
+            }
+#pragma unroll
+            for (int z = 0; z < NZ; ++z) out[z] = make_float2(0.f, 0.f);
+            // paired FP32 form as in zconv_c: out += (e, e) * S and (g, g) * (i S), i S = (-S.y, S.x)
+            if (a < 2) {
+#pragma unroll
+                for (int zp = 0; zp < NZ; ++zp) {
+                    const float2 sx = A[(0 * NZ + zp) * LS + pky];
+                    const float2 sy = A[(1 * NZ + zp) * LS + pky];
+                    const float2 sz = A[(2 * NZ + zp) * LS + pky];
+                    const float2 isz = make_float2(-sz.y, sz.x), nisz = make_float2(sz.y, -sz.x);
+#pragma unroll
+                    for (int z = 0; z < NZ; ++z) {
+                        const int q = z >= zp ? z - zp : zp - z;
+                        out[z] = __ffma2_rn(make_float2(e0[q], e0[q]), sx, out[z]);
+                        out[z] = __ffma2_rn(make_float2(e1[q], e1[q]), sy, out[z]);
+                        out[z] = __ffma2_rn(make_float2(e2[q], e2[q]), z >= zp ? isz : nisz, out[z]);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int zp = 0; zp < NZ; ++zp) {
+                    const float2 sx = A[(0 * NZ + zp) * LS + pky];
+                    const float2 sy = A[(1 * NZ + zp) * LS + pky];
+                    const float2 sz = A[(2 * NZ + zp) * LS + pky];
+                    const float2 isx = make_float2(-sx.y, sx.x), nisx = make_float2(sx.y, -sx.x);
+                    const float2 isy = make_float2(-sy.y, sy.x), nisy = make_float2(sy.y, -sy.x);
+#pragma unroll
+                    for (int z = 0; z < NZ; ++z) {
+                        const int q = z >= zp ? z - zp : zp - z;
+                        out[z] = __ffma2_rn(make_float2(e0[q], e0[q]), z >= zp ? isx : nisx, out[z]);
+                        out[z] = __ffma2_rn(make_float2(e1[q], e1[q]), z >= zp ? isy : nisy, out[z]);
+                        out[z] = __ffma2_rn(make_float2(e2[q], e2[q]), sz, out[z]);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (act) {
+#pragma unroll
+            for (int z = 0; z < NZ; ++z) A[(a * NZ + z) * LS + pky] = cconj(out[z]);
+        }
+    }
+}
+
+template <int P, int NZ, int KXB>
+__global__ void __launch_bounds__(kYz2Threads, P == 384 ? 2 : 3) yz2p_kernel(GroupArgs<float> g) {
+    using C = float2;
+    constexpr int R2 = P / 16, LS = t2_line(P), L = 3 * NZ * KXB;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* A = reinterpret_cast<C*>(smem_raw);
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int kx = blockIdx.x * KXB, p = blockIdx.y;
+    const int ny = g.ny;
+    C* blk = g.spec + ((size_t)p * g.Px + kx) * 3 * NZ * ny;  // KXB consecutive columns are contiguous
+    const C* __restrict__ tw = g.twy;                         // W_P^k
+    griddep_wait();
+    griddep_launch_dependents();
+    // pass 1, role (n2, line, par), n2 fastest: the zero-padded spectrum lines in, rows of Z out
+    for (int r = tid; r < 2 * R2 * L; r += nthr) {
+        const int n2 = r % R2, q = r / R2, line = q % L, par = q / L;
+        const C* src = blk + (size_t)line * ny + n2;
+        C u[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) u[j] = R2 * j + n2 < ny ? src[R2 * j] : make_float2(0.f, 0.f);
+        t2_pass1<P>(u, n2, par, tw, A + line * LS);
+    }
+    __syncthreads();
+    // pass 2: one warp per line (lanes = 16 columns x 2 parities)
+    for (int r = tid; r < 32 * L; r += nthr) t2_cols<P, false>(A + (r >> 5) * LS, r & 15, (r >> 4) & 1, tw);
+    __syncthreads();
+#pragma unroll 1
+    for (int b = 0; b < KXB; ++b) {
+        const int kxb = kx + b, kxo = min(kxb, g.Px - kxb);
+        zconv_t2<NZ, P>(A + b * 3 * NZ * LS, kxb, g.Px, g.dhat + (size_t)kxo * (P / 2 + 1) * NZ * 6, tid, nthr);
+    }
+    __syncthreads();
+    // pass A (the inverse transform of the conjugated field spectra, in place by columns)
+    for (int r = tid; r < 32 * L; r += nthr) t2_cols<P, true>(A + (r >> 5) * LS, r & 15, (r >> 4) & 1, tw);
+    __syncthreads();
+    // pass B, role (y2, line, par): rows y < ny back to the spectrum, conjugated
+    for (int r = tid; r < 2 * R2 * L; r += nthr) {
+        const int y2 = r % R2, q = r / R2, line = q % L, par = q / L;
+        C v[8];
+        t2_passB(v, A + line * LS, y2, par);
+        C* dst = blk + (size_t)line * ny;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int y = y2 + R2 * (2 * m + par);
+            if (y < ny) dst[y] = cconj(v[m]);
+        }
+    }
+}
+
 // ------------------------------------------------------------------------------------------------
 // h at one site (Eqs. 3-6) from its six neighbours (zero outside the lattice) and the dipole
 // convolution:
@@ -823,7 +962,7 @@ __device__ __forceinline__ void xinv_sites(const GroupArgs<T>& g, T dt, T* hout,
             auto nrm = [](const T* v, double* o) {
                 const double a = v[0], b = v[1], c = v[2];
                 const double n2 = a * a + b * b + c * c;
-                const double r = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
+                const double r = n2 > 0.0 ? rsqrt_nr(n2) : 0.0;
                 o[0] = a * r;
                 o[1] = b * r;
                 o[2] = c * r;
@@ -968,6 +1107,102 @@ __global__ void __launch_bounds__(kMaxThreads128, kMinBlocks128) xinv128_kernel(
     }
     __syncthreads();
     xinv_sites<T, true, MODE>(g, dt, hout, buf, kF128Buf, red, p, z, y0, rows, tid, nthr);
+}
+
+// ------------------------------------------------------------------------------------------------
+// x kernels for Px = P in {192, 256, 384} (nx <= P/2), FP32: the x-transforms in two register passes
+// (ss_fft.cuh) on kX2Rows rows of one layer of an image pair per CTA.  Every role order puts the rows
+// fastest across a warp: the spectrum's rows of one (kx, c) are contiguous in global memory, and with
+// line strides = 16 / kX2Rows (mod 16) the lanes of a half-warp (kX2Rows rows x 16 / kX2Rows consecutive
+// columns or rows of a line) hit distinct shared-memory banks.
+// xfwd: the gather (Eq. 12) into x-space lines, pass 1 into the transform lines, pass 2 straight to the
+// spectrum spec[p][kx][c][z][y].
+template <int P>
+__global__ void __launch_bounds__(kX2Threads, P == 384 ? 2 : 3) xfwd2p_kernel(GroupArgs<float> g) {
+    using C = float2;
+    constexpr int R2 = P / 16, H = R2 / 2, ROWS = kX2Rows, L = 3 * ROWS, LSX = x2_lsx(P), LB = x2_lb(P);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* xb = reinterpret_cast<C*>(smem_raw);  // line c * ROWS + yy: the pair at x, fft_pad positions
+    C* A = xb + L * LB;                       // line c * ROWS + yy: rows of Z
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int p = blockIdx.z, z = blockIdx.y, y0 = blockIdx.x * ROWS;
+    const int rows = min(ROWS, g.ny - y0), nx = g.nx;
+    const C* __restrict__ tw = g.twx;  // W_P^k
+    griddep_wait();
+    griddep_launch_dependents();
+    xfwd_gather(g, xb, LB, ROWS, p, z, y0, rows, tid, nthr);
+    __syncthreads();
+    // pass 1, role (yy, n2, c, par)
+    for (int r = tid; r < 2 * R2 * L; r += nthr) {
+        const int yy = r % ROWS, q = r / ROWS, n2 = q % R2, q2 = q / R2, c = q2 % 3, par = q2 / 3;
+        if (yy >= rows) continue;
+        const C* b = xb + (c * ROWS + yy) * LB;
+        C u[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) u[j] = R2 * j + n2 < nx ? b[fft_pad(R2 * j + n2)] : make_float2(0.f, 0.f);
+        t2_pass1<P>(u, n2, par, tw, A + (c * ROWS + yy) * LSX);
+    }
+    __syncthreads();
+    // pass 2, role (yy, k1, par2, c): X[k1 + 16 (2m + par2)] to the spectrum
+    const size_t kstride = (size_t)3 * g.nz * g.ny;  // between consecutive kx
+    C* outp = g.spec + (size_t)p * P * kstride + (size_t)z * g.ny + y0;
+    for (int r = tid; r < 32 * L; r += nthr) {
+        const int yy = r % ROWS, q = r / ROWS, k1 = q & 15, par2 = (q >> 4) & 1, c = q >> 5;
+        if (yy >= rows) continue;
+        const C* col = A + (c * ROWS + yy) * LSX + k1;
+        C a[H];
+        t2_col_vals<P, false>(a, [&](int j) { return col[j * kT2Row]; }, k1, par2, tw);
+        C* o = outp + (size_t)c * g.nz * g.ny + yy;
+#pragma unroll
+        for (int m = 0; m < H; ++m) o[(size_t)(k1 + 16 * (2 * m + par2)) * kstride] = a[m];
+    }
+}
+
+// xinv: pass A straight from the spectrum (conjugated) into the transform lines, pass B into x-space
+// lines (fft_pad positions, line c * rows + yy), then the per-site work of xinv_sites in mode MODE.
+template <int P, int MODE>
+__global__ void __launch_bounds__(kX2Threads, P == 384 ? 2 : 3) xinv2p_kernel(GroupArgs<float> g, float dt, float* hout) {
+    using C = float2;
+    constexpr int R2 = P / 16, H = R2 / 2, ROWS = kX2Rows, L = 3 * ROWS, LSX = x2_lsx(P), LB = x2_lb(P);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* A = reinterpret_cast<C*>(smem_raw);  // line c * ROWS + yy: columns of T
+    C* xb = A + L * LSX;                     // line c * rows + yy: the field convolution at x
+    double* red = reinterpret_cast<double*>(xb + L * LB);
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int p = blockIdx.z, z = blockIdx.y, y0 = blockIdx.x * ROWS;
+    const int rows = min(ROWS, g.ny - y0), nx = g.nx;
+    const size_t kstride = (size_t)3 * g.nz * g.ny;
+    const C* inp = g.spec + (size_t)p * P * kstride + (size_t)z * g.ny + y0;
+    const C* __restrict__ tw = g.twx;
+    griddep_wait();
+    griddep_launch_dependents();
+    // pass A, role (yy, k1, par2, c): column k1 of the conjugated spectrum line (c, yy)
+    for (int r = tid; r < 32 * L; r += nthr) {
+        const int yy = r % ROWS, q = r / ROWS, k1 = q & 15, par2 = (q >> 4) & 1, c = q >> 5;
+        if (yy >= rows) continue;
+        const C* sc = inp + (size_t)c * g.nz * g.ny + yy + (size_t)k1 * kstride;
+        C a[H];
+        t2_col_vals<P, true>(a, [&](int j) { return cconj(sc[(size_t)16 * j * kstride]); }, k1, par2, tw);
+        C* o = A + (c * ROWS + yy) * LSX + k1 + par2 * kT2Row;
+#pragma unroll
+        for (int m = 0; m < H; ++m) o[2 * m * kT2Row] = a[m];
+    }
+    __syncthreads();
+    // pass B, role (yy, y2, c, par): x = y2 + R2 (2m + par) < nx
+    for (int r = tid; r < 2 * R2 * L; r += nthr) {
+        const int yy = r % ROWS, q = r / ROWS, y2 = q % R2, q2 = q / R2, c = q2 % 3, par = q2 / 3;
+        if (yy >= rows) continue;
+        C v[8];
+        t2_passB(v, A + (c * ROWS + yy) * LSX, y2, par);
+        C* b = xb + (c * rows + yy) * LB;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int x = y2 + R2 * (2 * m + par);
+            if (x < nx) b[fft_pad(x)] = v[m];
+        }
+    }
+    __syncthreads();
+    xinv_sites<float, true, MODE>(g, dt, hout, xb, LB, red, p, z, y0, rows, tid, nthr);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -1896,6 +2131,21 @@ __global__ void extract_octant_kernel(const double2* spec, T* dhat, int Px, int 
 }
 
 #ifdef SS_COMMON_LAUNCHERS
+// [K][3][N] FP32 spins -> the same spins renormalised in FP64 (the dipole convolution of the FP64
+// evaluation then sees unit vectors, as the local terms do)
+__global__ void widen_unit_kernel(const float* __restrict__ src, double* __restrict__ dst, int K, int N) {
+    const size_t total = (size_t)K * N;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t k = i / N, n = i - k * N, b = k * 3 * N + n;
+        const double a0 = src[b], a1 = src[b + N], a2 = src[b + 2 * (size_t)N];
+        const double n2 = a0 * a0 + a1 * a1 + a2 * a2;
+        const double r = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
+        dst[b] = a0 * r;
+        dst[b + N] = a1 * r;
+        dst[b + 2 * (size_t)N] = a2 * r;
+    }
+}
+
 __global__ void interp_identity_kernel(InterpEntry* tab, int img0, int K) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
         InterpEntry e;
@@ -1929,6 +2179,36 @@ static inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
     cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
+// As launch_pdl, with programmatic stream serialisation only when pdl is set.
+template <typename... KArgs, typename... Args>
+static inline void launch_ex(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool pdl,
+                             Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+// The two-pass x-inverse kernel in mode MODE when Px is one of its lengths (rows per CTA kX2Rows, set by
+// the host); false otherwise.
+template <int MODE>
+static inline bool launch_xinv2p(const GroupArgs<float>& g, float dt, float* hout, bool pdl, cudaStream_t st) {
+    if (!x2p_ok(4, g.Px)) return false;
+    const dim3 grid((g.ny + g.ty_c - 1) / g.ty_c, g.nz, g.n_pairs), blk(kX2Threads);
+    const size_t sm = x2_smem(g.Px, true);
+    if (g.Px == 192) launch_ex(xinv2p_kernel<192, MODE>, grid, blk, sm, st, pdl, g, dt, hout);
+    else if (g.Px == 256) launch_ex(xinv2p_kernel<256, MODE>, grid, blk, sm, st, pdl, g, dt, hout);
+    else launch_ex(xinv2p_kernel<384, MODE>, grid, blk, sm, st, pdl, g, dt, hout);
+    return true;
+}
+
 static inline int grid1d(size_t n, int thr) {
     size_t b = (n + thr - 1) / thr;
     if (b > 152 * 16) b = 152 * 16;
@@ -1948,6 +2228,13 @@ template <typename T> void launch_xfwd(const GroupArgs<T>& g, bool do_fft, int n
         return;
     }
     if constexpr (std::is_same<T, float>::value) {
+        if (x2p_ok(4, g.Px)) {  // rows per CTA are kX2Rows (set by the host)
+            const size_t sm = x2_smem(g.Px, false);
+            if (g.Px == 192) launch_pdl(xfwd2p_kernel<192>, grid, dim3(kX2Threads), sm, st, g);
+            else if (g.Px == 256) launch_pdl(xfwd2p_kernel<256>, grid, dim3(kX2Threads), sm, st, g);
+            else launch_pdl(xfwd2p_kernel<384>, grid, dim3(kX2Threads), sm, st, g);
+            return;
+        }
         if (f128_x(4, g.Px)) {
             const dim3 blk(f128_x_threads(g.ty_a));
             const size_t sm = f128_x_smem(g.ty_a);
@@ -1974,6 +2261,19 @@ template <typename T> void launch_yz(const GroupArgs<T>& g, int nthr, size_t sme
     const size_t base = (size_t)(g.Py + 3 * g.nz * g.lsy) * sizeof(cplx<T>);
     const int stage = smem >= base + (size_t)(g.Py / 2 + 1) * g.nz * 6 * sizeof(T);
     if constexpr (std::is_same<T, float>::value) {
+        if (yz2p_ok(4, g.Py, g.nz, g.Px)) {
+            const size_t sm = yz2p_smem(g.Py, g.nz);
+            const dim3 blk(kYz2Threads);
+#define SS_CASE(P)                                                                                          \
+    if (g.Py == P) {                                                                                        \
+        if (g.nz == 1) launch_pdl(yz2p_kernel<P, 1, 8>, dim3(g.Px / 8, g.n_pairs), blk, sm, st, g);            \
+        else if (g.nz == 4) launch_pdl(yz2p_kernel<P, 4, 2>, dim3(g.Px / 2, g.n_pairs), blk, sm, st, g);       \
+        else launch_pdl(yz2p_kernel<P, 8, 1>, dim3(g.Px, g.n_pairs), blk, sm, st, g);                          \
+        return;                                                                                             \
+    }
+            SS_CASE(192) SS_CASE(256) SS_CASE(384)
+#undef SS_CASE
+        }
         if (f128_yz(4, g.Py, g.nz)) {
             bool st128 = false;
             const size_t sm128 = f128_yz_smem(g.nz, g.Py, &st128);
@@ -2030,6 +2330,7 @@ void launch_xinv_step(const GroupArgs<T>& g, bool do_fft, T dt, int nthr, size_t
         return;
     }
     if constexpr (std::is_same<T, float>::value) {
+        if (launch_xinv2p<0>(g, dt, nullptr, true, st)) return;
         if (f128_x(4, g.Px)) {
             const dim3 blk(f128_x_threads(g.ty_c));
             const size_t sm = f128_x_smem(g.ty_c);
@@ -2055,6 +2356,7 @@ template <typename T>
 void launch_xinv_eval(const GroupArgs<T>& g, bool do_fft, T* hout, int nthr, size_t smem, cudaStream_t st) {
     dim3 grid((g.ny + g.ty_c - 1) / g.ty_c, g.nz, g.n_pairs);
     if constexpr (std::is_same<T, float>::value) {
+        if (do_fft && launch_xinv2p<1>(g, T(0), hout, false, st)) return;
         if (do_fft && f128_x(4, g.Px)) {
             const int nt = f128_x_threads(g.ty_c);
             const size_t sm = f128_x_smem(g.ty_c);
@@ -2076,6 +2378,7 @@ static void launch_xinv_force_mode(const GroupArgs<T>& g, bool do_fft, T* kout, 
                                    cudaStream_t st) {
     dim3 grid((g.ny + g.ty_c - 1) / g.ty_c, g.nz, g.n_pairs);
     if constexpr (std::is_same<T, float>::value) {
+        if (do_fft && launch_xinv2p<MODE>(g, flag, kout, false, st)) return;
         if (do_fft && f128_x(4, g.Px)) {
             const int nt = f128_x_threads(g.ty_c);
             const size_t sm = f128_x_smem(g.ty_c);
@@ -2105,6 +2408,7 @@ template <typename T>
 void launch_xinv_step_llg(const GroupArgs<T>& g, bool do_fft, T dt, int nthr, size_t smem, cudaStream_t st) {
     dim3 grid((g.ny + g.ty_c - 1) / g.ty_c, g.nz, g.n_pairs);
     if constexpr (std::is_same<T, float>::value) {
+        if (do_fft && launch_xinv2p<4>(g, dt, nullptr, true, st)) return;
         if (do_fft && f128_x(4, g.Px)) {
             const dim3 blk(f128_x_threads(g.ty_c));
             const size_t sm = f128_x_smem(g.ty_c);
@@ -2124,6 +2428,7 @@ template <typename T>
 void launch_xinv_step_climb(const GroupArgs<T>& g, bool do_fft, T dt, T* hc, int nthr, size_t smem, cudaStream_t st) {
     dim3 grid((g.ny + g.ty_c - 1) / g.ty_c, g.nz, g.n_pairs);
     if constexpr (std::is_same<T, float>::value) {
+        if (do_fft && launch_xinv2p<3>(g, dt, hc, true, st)) return;
         if (do_fft && f128_x(4, g.Px)) {
             const dim3 blk(f128_x_threads(g.ty_c));
             const size_t sm = f128_x_smem(g.ty_c);
@@ -2252,6 +2557,19 @@ template <typename T> void set_smem_limits(int bytes) {
 #undef SS_CASE
         set_dyn_smem(yz128_kernel<T, 4>, bytes);
         set_dyn_smem(yz128_kernel<T, 8>, bytes);
+#define SS_CASE(P)                                 \
+    set_dyn_smem(xfwd2p_kernel<P>, bytes);         \
+    set_dyn_smem(xinv2p_kernel<P, 0>, bytes);      \
+    set_dyn_smem(xinv2p_kernel<P, 1>, bytes);      \
+    set_dyn_smem(xinv2p_kernel<P, 2>, bytes);      \
+    set_dyn_smem(xinv2p_kernel<P, 3>, bytes);      \
+    set_dyn_smem(xinv2p_kernel<P, 4>, bytes);      \
+    set_dyn_smem(xinv2p_kernel<P, 5>, bytes);      \
+    set_dyn_smem(yz2p_kernel<P, 1, 8>, bytes);     \
+    set_dyn_smem(yz2p_kernel<P, 4, 2>, bytes);     \
+    set_dyn_smem(yz2p_kernel<P, 8, 1>, bytes);
+        SS_CASE(192) SS_CASE(256) SS_CASE(384)
+#undef SS_CASE
 #define SS_CASE(P)                                  \
     set_dyn_smem(xfwd_kernel<T, true, P>, bytes);   \
     set_dyn_smem(xinv_kernel<T, true, 0, P>, bytes);
@@ -2286,6 +2604,10 @@ void launch_fft_strided_f64(double2* data, const double2* tw, const FftPlan& pla
 
 void launch_interp_identity(InterpEntry* tab, int img0, int K, cudaStream_t st) {
     interp_identity_kernel<<<(K + 127) / 128, 128, 0, st>>>(tab, img0, K);
+}
+
+void launch_widen_unit(const float* src, double* dst, int K, int N, cudaStream_t st) {
+    widen_unit_kernel<<<grid1d((size_t)K * N, 256), 256, 0, st>>>(src, dst, K, N);
 }
 #endif
 

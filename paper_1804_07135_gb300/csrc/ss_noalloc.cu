@@ -2,16 +2,16 @@
 // device memory.
 //
 // Who needs it: callers that must not call cudaMalloc -- code running inside an application that
-// owns all device memory through its own pool, plugins whose host forbids allocation, or code that
-// runs while a device-wide allocation would break an ongoing stream capture.  Everything the field
-// evaluation needs beyond the caller's input and output (the pair spectra, the dipole-tensor
+// owns all device memory through its own pool, or a plugin whose host forbids allocation.  Everything
+// the field evaluation needs beyond the caller's input and output (the pair spectra, the dipole-tensor
 // spectrum and its FP64 build area, twiddles, the SoA copies of spins and field, bookkeeping) lives in
 // one file-scope device array, g_scratch, of kNoAllocScratchBytes.  Every GPU that loads libss
 // reserves that array until the process exits.
 //
 // Host code must not use g_scratch's name as a device address (in host code it names a host-side
 // stand-in); the device address comes from cudaGetSymbolAddress, taken once per device with that
-// device current, on the first call.
+// device current, on the first call.  The call synchronises its stream and reads an error word back,
+// so it refuses a stream that is being captured (before issuing any work) rather than break the capture.
 #include <limits.h>
 #include <math.h>
 
@@ -58,7 +58,8 @@ ss_status scratch_of_current_device(unsigned char** out) {
     return SS_OK;
 }
 
-// ---- sizes and launch shapes (same rules as the context path, restated without containers) ----
+// ---- sizes and launch shapes: the padded-length rule of the context path; the x-kernel row count is a
+// fixed rule of its own (no autotuning), chosen to keep every CTA's shared memory under 48 KB ----
 bool smooth23(int m) {
     while (m % 2 == 0) m /= 2;
     while (m % 3 == 0) m /= 3;
@@ -145,6 +146,24 @@ extern "C" ss_status ss_field_noalloc(int nx, int ny, int nz, double J, double D
     if (!isfinite(J) || !isfinite(D) || !isfinite(K) || !isfinite(w)) return SS_ERR_INVALID_ARG;
     if (!spins || !field) return SS_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
+    // a capturing stream would record this call's work into the caller's graph and fail at the
+    // synchronisation below: refuse it before issuing anything
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return SS_ERR_CUDA;
+    if (cap != cudaStreamCaptureStatusNone) return SS_ERR_STATE;
+    // both arrays must be device memory of the current device (checked on the host, before any launch)
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return SS_ERR_CUDA;
+        for (const void* ptr : {(const void*)spins, (const void*)field}) {
+            cudaPointerAttributes at{};
+            if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+                cudaGetLastError();  // clear the query's error
+                return SS_ERR_INVALID_ARG;
+            }
+            if (at.type != cudaMemoryTypeDevice || at.device != dev) return SS_ERR_INVALID_ARG;
+        }
+    }
     const bool dip = w != 0.0;
     const int N = nx * ny * nz;
     const int Px = dip ? pad_len(nx) : 1, Py = dip ? pad_len(ny) : 1;
@@ -159,6 +178,7 @@ extern "C" ss_status ss_field_noalloc(int nx, int ny, int nz, double J, double D
         }
     }
     if (dip && f128_x(4, Px)) ty = f128_x_rows(ty);  // the length-128 x kernels take 2, 4 or 8 rows
+    if (dip && x2p_ok(4, Px)) ty = kX2Rows;          // the lengths-192/256/384 x kernels take kX2Rows
     const size_t smem_a = (size_t)(Px + 3 * ty * lsx) * sizeof(float2);
     const size_t smem_c = smem_a + 32 * 8 * sizeof(double);
     size_t smem_b = (size_t)(Py + 3 * nz * lsy) * sizeof(float2);

@@ -96,3 +96,35 @@ def test_autograd_full_size_against_oracle_field_and_terms(ss):
     ref = oracle.energy_param_grad(m, sk) - oracle.energy_param_grad(m, s0)
     np.testing.assert_allclose(d_barrier, ref, rtol=REL, atol=REL)
     assert dE >= 0.0
+
+
+def test_autograd_fp32_against_the_fp64_gpu_method(ss):
+    # the same state through an FP32 context and through the plain FP64 GPU method: dE/ds (the field,
+    # Eq. 2) agrees to the FP32 field tolerance; the energies and the barrier's parameter derivatives
+    # d(barrier)/d(J, D, K, w), both FP64 evaluations of that state, agree to FP64 rounding.  The FP64
+    # context is given the FP32 context's stored state, so both evaluate the same spins.
+    spec = W.bloch_collapse().strings[0]
+    case = (spec.nx, spec.ny, spec.nz, spec.J, spec.D, spec.K, spec.w, spec.n_images)
+    sm32, state = _relaxed(ss, case, spec.initial_path(), 100)
+    out = {}
+    try:
+        with ss.StringMethod([case], precision=ss.SS_PREC_FP64) as sm64:
+            for name, sm, dt in (("fp32", sm32, torch.float32), ("fp64", sm64, torch.float64)):
+                spins = torch.tensor(state, dtype=dt, device="cuda", requires_grad=True)
+                params = torch.tensor([spec.J, spec.D, spec.K, spec.w], dtype=torch.float64, requires_grad=True)
+                e = ag.string_energies(sm, 0, spins, params)
+                k = int(torch.argmax(e).item())
+                (e[k] - e[0]).backward()
+                out[name] = dict(e=e.detach().cpu().numpy(), k=k, g_s=spins.grad.double().cpu().numpy(),
+                                 g_p=params.grad.cpu().numpy(), bpg=ag.barrier_param_grad(sm, 0))
+                if name == "fp32":
+                    state = sm32.get_path(0)  # the FP32 state, handed to the FP64 context
+    finally:
+        sm32.close()
+    a, b = out["fp32"], out["fp64"]
+    assert a["k"] == b["k"] and a["bpg"][1] == b["bpg"][1]
+    scale = np.abs(b["g_s"]).max()
+    assert np.abs(a["g_s"] - b["g_s"]).max() <= 1e-5 * scale
+    np.testing.assert_allclose(a["e"], b["e"], rtol=1e-12, atol=1e-9)
+    np.testing.assert_allclose(a["g_p"], b["g_p"], rtol=1e-10, atol=1e-9)
+    np.testing.assert_allclose(a["bpg"][0], b["bpg"][0], rtol=1e-10, atol=1e-9)
