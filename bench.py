@@ -1,17 +1,24 @@
 #!/usr/bin/env python
 """Throughput of the string method on one GB300 (or N replicas under torchrun).
 
-Workload: the Bloch-point collapse string -- 64x64x8 lattice (32768 spins), 32 images, J=1, D=0.25,
-K=0.1, w=0.02, dipole by FFT convolution, 2000 iterations of dt=0.1.  One bench step is the whole hot
-path once: set the initial path, run 2000 iterations (field, step, per-image energies, equal-arc-length
-reparametrisation), evaluate the barrier.  Metric: spin-updates/s = spins x images x iterations / time.
+Headline workload: the uneven-size parameter study -- 20 strings of 32 images on lattices drawn from
+{64^2 x 4, 96^2 x 4, 128^2 x 8, 192^2 x 8} (seed 7), K ~ U[0, 0.2], D ~ U[0.15, 0.4], w = 0.01, dipole by
+FFT convolution, dt = 0.1: four size groups, 72.1M spin-updates per iteration.  One bench step is the
+whole hot path once over that batch: set the 20 initial paths, run ITERS_PER_STEP iterations (field,
+step, per-image energies, equal-arc-length reparametrisation), evaluate the 20 barriers in FP64.
+Metric: spin-updates/s = sum over strings of spins x images x iterations / time.  The study runs 5000
+iterations in all; a step runs ITERS_PER_STEP of them so that the timed region stays near a minute.
 
-  value     device-timed (CUDA events on the calling stream), initial path already resident in HBM
-  e2e       the same through the public API with the path copied from pinned host memory each step and
+  value     device-timed (CUDA events on the calling stream), initial paths already resident in HBM
+  e2e       the same through the public API with the paths copied from pinned host memory each step and
             the energies read back
   roofline  the dominant kernel's algorithmic bytes per launch / its mean event-timed duration
   cpu_baseline / --impl reference   the FP64 CPU oracle on a bounded sample (one iteration of an
-            8-image sub-string of the same workload), timed on this host's cores
+            8-image sub-string of the study's first 64 x 64 x 4 string), timed on this host's cores
+
+The line also carries the previous headline (the 64x64x8, 32-image Bloch-point string, 2000 iterations
+per step, with its FP64-GPU barrier comparison), the other workloads, the method variants and the plain
+FP64 GPU method's rate on the headline workload.
 
 N > 1 (torchrun): every rank runs its own replica of the workload (independent strings; weak scaling,
 no collective on the data path); time = max over ranks.
@@ -54,7 +61,7 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    p.add_argument("--iters", type=int, default=None, help="iterations per step (default: the workload's)")
+    p.add_argument("--iters", type=int, default=None, help=f"iterations per step (default {ITERS_PER_STEP})")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-accuracy", action="store_true", help="skip the FP64-GPU barrier comparison")
     p.add_argument("--no-other-workloads", action="store_true", help="skip the short runs of the batch workloads")
@@ -152,10 +159,25 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_sample(spec, dt, n_images=REF_IMAGES):
-    """One oracle iteration (field, step, reparam) of the first n_images images of the workload's path."""
+ITERS_PER_STEP = 200       # iterations of the headline workload per bench step (of its 5000)
+C2_ITERS_PER_STEP = 2000   # the 64x64x8 string: its full iteration count per step
+
+
+def headline_workload():
+    return workloads.uneven_study()
+
+
+def oracle_sample_spec():
+    """The string the CPU baseline samples: the study's first 64 x 64 x 4 string (the oracle's direct
+    dipole sum costs N^2 per image, so the smallest lattice of the study keeps the sample bounded)."""
+    return next(s for s in headline_workload().strings if s.nx == 64)
+
+
+def cpu_oracle_sample(spec, dt, n_images=REF_IMAGES, threads=None):
+    """One oracle iteration (field, step, reparam) of the first n_images images of spec's path; returns
+    (spin-updates/s, threads used, seconds)."""
     import oracle
-    cores = len(os.sched_getaffinity(0))
+    cores = len(os.sched_getaffinity(0)) if threads is None else threads
     oracle.set_threads(cores)
     m = oracle.model(spec.nx, spec.ny, spec.nz, spec.J, spec.D, spec.K, spec.w)
     path = spec.initial_path()[:n_images]
@@ -164,6 +186,11 @@ def cpu_oracle_sample(spec, dt, n_images=REF_IMAGES):
     t = time.perf_counter() - t0
     units = spec.n_sites * n_images
     return units / t, min(cores, n_images), t  # the oracle's threads run over images
+
+
+def oracle_sample_text(spec, n_images=REF_IMAGES):
+    return (f"one oracle iteration (direct O(N^2) dipole) of the first {n_images} images of the uneven study's "
+            f"first {spec.nx}x{spec.ny}x{spec.nz} string")
 
 
 def kernel_source_hash():
@@ -211,8 +238,8 @@ def whole_job_value(units_per_rank, world, seconds):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    wl = workloads.bloch_collapse()
-    spec = wl.strings[0]
+    wl = headline_workload()
+    spec = oracle_sample_spec()
     times = []
     cores = len(os.sched_getaffinity(0))
     for i in range(args.warmup + args.steps):
@@ -221,17 +248,57 @@ def run_reference(args, rank, world):
             times.append(t)
     units = spec.n_sites * REF_IMAGES
     value = units * len(times) / sum(times)
-    sample = f"one oracle iteration (direct O(N^2) dipole) of the first {REF_IMAGES} images of the 64x64x8 path"
     line = {
         "impl": "reference", "metric": "spin-updates/s", "value": value, "unit": "spin-updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl.name, "lattice": [spec.nx, spec.ny, spec.nz], "images": REF_IMAGES,
+        "config": {"workload": wl.name, "sampled_string": [spec.nx, spec.ny, spec.nz], "images": REF_IMAGES,
                    "iterations_per_step": 1},
-        "cpu_baseline": {"value": value, "unit": "spin-updates/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "spin-updates/s", "cores": cores, "kind": "oracle",
+                         "sample": oracle_sample_text(spec)},
         "e2e": {"value": value, "unit": "spin-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def group_keys(wl):
+    """Size groups of a workload in the library's order (first appearance) with their image counts."""
+    keys, imgs = [], {}
+    for s in wl.strings:
+        k = (s.nx, s.ny, s.nz)
+        if k not in imgs:
+            keys.append(k)
+            imgs[k] = 0
+        imgs[k] += s.n_images
+    return keys, imgs
+
+
+def kernel_roofline(sm, wl, names_per_group, peaks, peak_kind, ms):
+    """The dominant kernel's HBM roofline: algorithmic bytes per launch / event-timed mean duration."""
+    keys, imgs = group_keys(wl)
+    entries = []
+    i = 0
+    for k in keys:
+        for n in names_per_group:
+            entries.append((k, n))
+            i += 1
+    dom = int(np.argmax(ms))
+    (nx, ny, nz), dname = entries[dom]
+    units = nx * ny * nz * imgs[(nx, ny, nz)]
+    alg = BYTES_PER_SITE_IMAGE[dname] * units
+    if dname == "yz":
+        alg += 4 * 6 * nz * (padded(nx) // 2 + 1) * (padded(ny) // 2 + 1)
+    achieved = alg / (ms[dom] * 1e-3) / 1e9
+    tag = f"{dname}[{nx}x{ny}x{nz}]"
+    total_alg = sum(BYTES_PER_SITE_IMAGE[n] * k[0] * k[1] * k[2] * imgs[k] for k, n in entries)
+    return {"bound": "hbm", "kernel": tag, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "peak_source": peak_kind,
+            "traffic": ncu_traffic(tag, units), "alg_bytes_per_launch": alg, "units_per_launch": units,
+            "kernel_ms": {f"{n}[{k[0]}x{k[1]}x{k[2]}]": float(v) for (k, n), v in zip(entries, ms)},
+            "kernel_share": {f"{n}[{k[0]}x{k[1]}x{k[2]}]": float(v / ms.sum()) for (k, n), v in zip(entries, ms)},
+            "iteration": {"alg_bytes": total_alg, "kernel_ms_sum": float(ms.sum()),
+                          "achieved_gbs": total_alg / (ms.sum() * 1e-3) / 1e9,
+                          "frac": total_alg / (ms.sum() * 1e-3) / 1e9 / peaks["hbm_gbs"]}}
 
 
 def main():
@@ -250,31 +317,32 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
         pg = dist
 
-    wl = workloads.bloch_collapse()
-    spec = wl.strings[0]
-    n_iter = args.iters or wl.n_iter
-    desc = (spec.nx, spec.ny, spec.nz, spec.J, spec.D, spec.K, spec.w, spec.n_images)
-    path = spec.initial_path().astype(np.float32)
-    path_dev = torch.from_numpy(path).cuda()
-    path_host = torch.from_numpy(path).pin_memory()
+    wl = headline_workload()
+    n_iter = args.iters or ITERS_PER_STEP
+    n_str = len(wl.strings)
+    descs = [(s.nx, s.ny, s.nz, s.J, s.D, s.K, s.w, s.n_images) for s in wl.strings]
+    paths = [s.initial_path().astype(np.float32) for s in wl.strings]
+    paths_dev = [torch.from_numpy(p).cuda() for p in paths]
+    paths_host = [torch.from_numpy(p).pin_memory() for p in paths]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
-    sm = binding.StringMethod([desc], dt=wl.dt, stream=stream.cuda_stream)
+    sm = binding.StringMethod(descs, dt=wl.dt, stream=stream.cuda_stream)
     apply_variant(binding, sm, args.variant)
     kpi = sm.kernels_per_iteration()
 
-    def one_step(src):
-        sm.set_path(0, src)
+    def one_step(srcs):
+        for i, src in enumerate(srcs):
+            sm.set_path(i, src)
         sm.step(n_iter)
-        return sm.barrier(0)
+        return [sm.barrier(i) for i in range(n_str)]
 
-    def timed(src, n):
+    def timed(srcs, n):
         out = []
         for _ in range(n):
             flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            one_step(src)
+            one_step(srcs)
             e1.record(stream)
             torch.cuda.synchronize()
             out.append(e0.elapsed_time(e1) / 1e3)
@@ -286,21 +354,21 @@ def main():
         torch.cuda.synchronize()
 
     for _ in range(args.warmup):
-        one_step(path_dev)
+        one_step(paths_dev)
     barrier_all()
     rk = VARIANTS[args.variant][2] != "euler"
     with ClockSampler(local_rank) as clk:
-        t_dev = timed(path_dev, args.steps)
-        if rk:  # attempts of the last timed step (set_path restarts the counts each step)
-            rk_attempts = [sum(sm.integrator_state(0, k)[1:]) for k in range(spec.n_images)]
+        t_dev = timed(paths_dev, args.steps)
+        if rk:  # attempts of the last timed step of string 0 (set_path restarts the counts each step)
+            rk_attempts = [sum(sm.integrator_state(0, k)[1:]) for k in range(wl.strings[0].n_images)]
         barrier_all()
-        t_e2e = timed(path_host, args.steps)
+        t_e2e = timed(paths_host, args.steps)
         barrier_all()
     step_s, e2e_s = max_over_ranks(pg, [float(np.mean(t_dev)), float(np.mean(t_e2e))], "cuda")
-    units = spec.n_sites * spec.n_images * n_iter
+    units = wl.spin_updates_per_iter * n_iter
     value = whole_job_value(units, world, step_s)
     e2e_value = whole_job_value(units, world, e2e_s)
-    dE, kmax = sm.barrier(0)
+    barriers = [sm.barrier(i) for i in range(n_str)]
 
     if rank != 0:
         sm.close()
@@ -309,97 +377,149 @@ def main():
         return
 
     # per-kernel roofline (kernels launched one by one on the library stream, CUDA-event timed)
-    sm.set_path(0, path_dev)
+    for i, p in enumerate(paths_dev):
+        sm.set_path(i, p)
     if rk:  # the field kernels are timed in the Euler iteration
         sm.set_integrator(binding.SS_INT_EULER)
-    ms = sm.time_kernels(reps=20)
+    ms = sm.time_kernels(reps=10)
     interp, climb, integ, dyn = VARIANTS[args.variant]
     names = ["xfwd", "yz", "xinv"] + (["climb"] if climb else []) + ["arc"] + (["spline"] if interp == "spline" else [])
-    share = ms / ms.sum()
-    dom = int(np.argmax(ms))
-    dname = names[dom]
-    launch_units = spec.n_sites * spec.n_images
     peaks, peak_kind = measured_peaks()
-    alg_bytes = (CLIMB_BYTES_PER_SITE * spec.n_sites if dname == "climb" else
-                 BYTES_PER_SITE_IMAGE[dname] * launch_units)
-    if dname == "yz":
-        alg_bytes += 4 * 6 * spec.nz * (padded(spec.nx) // 2 + 1) * (padded(spec.ny) // 2 + 1)
-    achieved = alg_bytes / (ms[dom] * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "peak_source": peak_kind,
-                "traffic": ncu_traffic(dname, launch_units),
-                "kernel_ms": {n: float(v) for n, v in zip(names, ms)},
-                "kernel_share": {n: float(v) for n, v in zip(names, share)},
-                "launch_config": sm.launch_config(0),
-                "x_config_env": "SS_X_CONFIG={threads_xfwd}:{rows_xfwd}:{threads_xinv}:{rows_xinv}".format(**sm.launch_config(0)),
-                "alg_bytes_per_launch": alg_bytes}
-    if "yz" in names:
-        # the y/z kernel is not HBM-bound (its working set is L2-resident): its FP32 arithmetic against
-        # the FP32 (non-tensor) peak, 152 SMs x 128 FMA lanes x 2 FLOP x the maximum SM clock
-        flops = yz_flops(spec)
-        peak_tf = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        ach_tf = flops / (ms[names.index("yz")] * 1e-3) / 1e12
-        roofline["secondary"] = {"kernel": "yz", "bound": "alu", "achieved": ach_tf, "peak": peak_tf,
-                                 "unit": "TFLOP/s", "frac": ach_tf / peak_tf, "flops_per_launch": flops,
-                                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x sm_max_mhz"}
-
+    roofline = kernel_roofline(sm, wl, names, peaks, peak_kind, ms) if not climb else None
+    keys, _ = group_keys(wl)
     line = {
         "metric": "spin-updates/s", "value": value, "unit": "spin-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": wl.name, "variant": args.variant, "lattice": [spec.nx, spec.ny, spec.nz],
-                   "images": spec.n_images,
-                   "iterations_per_step": n_iter, "dt": wl.dt, "J": spec.J, "D": spec.D, "K": spec.K, "w": spec.w,
-                   "padded_xy": [padded(spec.nx), padded(spec.ny)],
-                   "precision": "fp32 spins, fields and FFTs; fp64 energy and arc-length reductions",
-                   "l2": "flushed before every step (256 MB write); the step's working set stays on chip across its iterations",
+        "config": {"workload": wl.name, "variant": args.variant, "strings": n_str,
+                   "images": int(sum(s.n_images for s in wl.strings)),
+                   "lattices": sorted({f"{s.nx}x{s.ny}x{s.nz}" for s in wl.strings}),
+                   "padded_xy": {f"{k[0]}x{k[1]}x{k[2]}": [padded(k[0]), padded(k[1])] for k in keys},
+                   "spin_updates_per_iteration": wl.spin_updates_per_iter,
+                   "iterations_per_step": n_iter, "workload_iterations": wl.n_iter, "dt": wl.dt, "w": 0.01,
+                   "precision": "fp32 spins, fields and FFTs; fp64 energy and arc-length reductions; "
+                                "barriers from an fp64 evaluation of the fp32 state",
+                   "l2": "flushed before every step (256 MB write); the working set (about 6 GB) exceeds L2",
                    "parallelism": f"replicas x{world}"},
-        "e2e": {"value": e2e_value, "unit": "spin-updates/s", "h2d_bytes_per_step": int(path.nbytes),
-                "d2h_bytes_per_step": int(spec.n_images * 8)},
-        "gpu_launches": int(args.steps * (2 + n_iter * kpi + 4)) if not rk else
-        # per attempt round 7 x (assemble, x-forward, y/z, x-inverse) + finish, control, commit; per
-        # iteration the gather, the controller's start and the arc kernel; rounds = the string's attempts
-        # (per-image control: the most attempts of one image, a lower bound)
-        int(args.steps * (2 + 4 + 3 * n_iter + (7 * kpi + 3) *  # kpi: the 3 or 4 field kernels and arc -> assemble
-                          (max(rk_attempts) if args.variant == "dopri5_per_image" else rk_attempts[0]))),
+        "e2e": {"value": e2e_value, "unit": "spin-updates/s",
+                "h2d_bytes_per_step": int(sum(p.nbytes for p in paths)),
+                "d2h_bytes_per_step": int(sum(8 * s.n_images for s in wl.strings))},
+        # per step: the 20 path uploads (conversion kernels), n_iter graph-replayed iterations, and per
+        # size group the FP64 evaluation of the barriers (gather, widen, x-forward, y/z, x-inverse, reduce)
+        "gpu_launches": int(args.steps * (2 * n_str + n_iter * kpi + 6 * len(keys))) if not rk else None,
         "roofline": roofline,
         "clocks": clk.summary(),
-        "barrier": {"dE": dE, "k_max": kmax},
+        "barriers": [{"dE": b[0], "k_max": b[1]} for b in barriers],
     }
+    if rk:
+        line["gpu_launches"] = int(args.steps * (2 * n_str + 6 * len(keys) + 3 * n_iter + (7 * kpi + 3) *
+                                                 (max(rk_attempts) if args.variant == "dopri5_per_image" else rk_attempts[0])))
     if not args.no_accuracy:
-        iters64 = min(n_iter, 200)
-        with binding.StringMethod([desc], dt=wl.dt, precision=binding.SS_PREC_FP64, stream=stream.cuda_stream) as s64:
-            s64.set_path(0, path_dev)
-            s64.step(1)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            s64.step(iters64)
-            torch.cuda.synchronize()
-            t64 = time.perf_counter() - t0
-            s64.set_path(0, path_dev)
-            s64.step(n_iter)
-            dE64, k64 = s64.barrier(0)
-        line["fp64_gpu"] = {"value": spec.n_sites * spec.n_images * iters64 / t64, "unit": "spin-updates/s",
-                            "iterations_timed": iters64, "barrier_dE": dE64, "k_max": k64}
-        line["speedup_vs_fp64_gpu"] = value / line["fp64_gpu"]["value"]
-        line["barrier_abs_err_vs_fp64_gpu"] = abs(dE - dE64)
+        line["fp64_gpu"] = fp64_gpu_rate(binding, wl, stream, paths_dev)
+        line["speedup_vs_fp64_gpu"] = line["fp64_gpu"]["ms_per_iter"] / (1e3 * step_s / n_iter)
     if not args.no_other_workloads:
+        line["bloch_64x64x8"] = bloch_64x64x8(binding, stream, peaks, peak_kind, no_accuracy=args.no_accuracy)
         line["other_workloads"] = {w.name: other_workload(binding, w, stream) for w in
-                                   (workloads.boundary_sweep(), workloads.uneven_study(),
-                                    workloads.paper_monolayer_workload(), workloads.paper_phase_diagram())}
-        line["variants"] = variant_runs(binding, wl, stream, plain_ms=step_s * 1e3 / n_iter)
-        line["adaptive_rk"] = {name: adaptive_rk(binding, wl, stream, kind, per_iter_euler_ms=step_s * 1e3 / n_iter)
+                                   (workloads.boundary_sweep(), workloads.paper_monolayer_workload(),
+                                    workloads.paper_phase_diagram())}
+        c2 = workloads.bloch_collapse()
+        line["variants"] = variant_runs(binding, c2, stream, plain_ms=line["bloch_64x64x8"]["ms_per_iter"])
+        line["adaptive_rk"] = {name: adaptive_rk(binding, c2, stream, kind,
+                                                 per_iter_euler_ms=line["bloch_64x64x8"]["ms_per_iter"])
                                for name, kind in (("dopri5_per_string", binding.SS_INT_DOPRI5),
                                                   ("dopri5_per_image", binding.SS_INT_DOPRI5_IMAGE))}
     if not args.no_cpu_baseline and world == 1:
+        spec = oracle_sample_spec()
         v, cores, t = cpu_oracle_sample(spec, wl.dt)
+        v1, _, t1 = cpu_oracle_sample(spec, wl.dt, threads=1)
         line["cpu_baseline"] = {"value": v, "unit": "spin-updates/s", "cores": cores, "kind": "oracle",
-                                "sample": f"one oracle iteration (direct O(N^2) dipole) of the first {REF_IMAGES} "
-                                          f"images of the 64x64x8 path, {t:.1f} s"}
+                                "sample": f"{oracle_sample_text(spec)}, {t:.1f} s",
+                                "single_thread": {"value": v1, "cores": 1, "seconds": t1}}
     sm.close()
     print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
+
+
+def fp64_gpu_rate(binding, wl, stream, paths_dev, iters=10):
+    """The plain FP64 GPU method on the headline workload: device-timed iterations (CUDA events), the
+    one-iteration graph captured in the warm-up so that no capture falls in the timed region."""
+    import torch
+    descs = [(s.nx, s.ny, s.nz, s.J, s.D, s.K, s.w, s.n_images) for s in wl.strings]
+    with binding.StringMethod(descs, dt=wl.dt, precision=binding.SS_PREC_FP64, stream=stream.cuda_stream) as s64:
+        for i, p in enumerate(paths_dev):
+            s64.set_path(i, p)
+        s64.step(1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s64.step(iters)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+    return {"value": wl.spin_updates_per_iter * iters / t, "unit": "spin-updates/s", "iterations_timed": iters,
+            "ms_per_iter": 1e3 * t / iters}
+
+
+def bloch_64x64x8(binding, stream, peaks, peak_kind, no_accuracy=False, steps=3):
+    """The 64x64x8, 32-image Bloch-point string (2000 iterations per step, L2-resident working set):
+    device-timed steps as the headline's, its kernel roofline, and the barrier against the plain FP64 GPU
+    method after the same 2000 iterations (split into the evaluation and the drift of the FP32
+    trajectory) with the FP64 method's rate (its 64-iteration graph captured before the timed region)."""
+    import torch
+    wl = workloads.bloch_collapse()
+    spec = wl.strings[0]
+    desc = (spec.nx, spec.ny, spec.nz, spec.J, spec.D, spec.K, spec.w, spec.n_images)
+    path_dev = torch.from_numpy(spec.initial_path().astype(np.float32)).cuda()
+    n_iter = C2_ITERS_PER_STEP
+    out = {}
+    with binding.StringMethod([desc], dt=wl.dt, stream=stream.cuda_stream) as sm:
+        for _ in range(2):
+            sm.set_path(0, path_dev)
+            sm.step(n_iter)
+            sm.barrier(0)
+        ts = []
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sm.set_path(0, path_dev)
+            sm.step(n_iter)
+            dE, k = sm.barrier(0)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        g32 = sm.get_path(0)
+        sm.set_path(0, path_dev)
+        ms = sm.time_kernels(reps=20)
+        roof = kernel_roofline(sm, wl, ["xfwd", "yz", "xinv", "arc"], peaks, peak_kind, ms)
+    t = float(np.mean(ts))
+    units = spec.n_sites * spec.n_images * n_iter
+    out.update({"value": units / t, "unit": "spin-updates/s", "iterations_per_step": n_iter,
+                "ms_per_step": 1e3 * t, "ms_per_iter": 1e3 * t / n_iter, "barrier": {"dE": dE, "k_max": k},
+                "l2": "the step's working set (about 55 MB) stays in L2 across its iterations",
+                "roofline": roof})
+    if not no_accuracy:
+        with binding.StringMethod([desc], dt=wl.dt, precision=binding.SS_PREC_FP64, stream=stream.cuda_stream) as s64:
+            s64.set_path(0, path_dev)
+            s64.step(64)  # captures the 64-iteration graph outside the timed region
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s64.step(192)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t64 = e0.elapsed_time(e1) / 1e3 / 192
+            s64.set_path(0, path_dev)
+            s64.step(n_iter)
+            dE64, k64 = s64.barrier(0)
+            s64.set_path(0, g32)  # the FP32 final state, evaluated by the FP64 method
+            dE64_of_32, _ = s64.barrier(0)
+        out["fp64_gpu"] = {"value": spec.n_sites * spec.n_images / t64, "unit": "spin-updates/s",
+                           "iterations_timed": 192, "ms_per_iter": 1e3 * t64, "barrier_dE": dE64, "k_max": k64}
+        out["speedup_vs_fp64_gpu"] = t64 / (t / n_iter)
+        out["barrier_abs_err_vs_fp64_gpu"] = abs(dE - dE64)
+        out["barrier_err_split"] = {"evaluation": dE - dE64_of_32, "drift": dE64_of_32 - dE64}
+    return out
 
 
 def variant_runs(binding, wl, stream, plain_ms, iters=128, warm=64):

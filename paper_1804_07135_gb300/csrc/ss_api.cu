@@ -73,9 +73,31 @@ std::vector<double2> twiddles(int P) {
 
 }  // namespace
 
+// Twiddle tables of the two-pass transforms (layout in GroupArgs::t2x / t2y) of length P from the flat
+// FP64 table w[k] = W_P^k; zeros when P is not a multiple of 16 (no two-pass transform then).
+template <typename C> void two_pass_twiddles(int P, const std::vector<double2>& w, C* out) {
+    using R = decltype(C{}.x);
+    for (int i = 0; i < 2 * P; ++i) out[i] = C{R(0), R(0)};
+    if (P % 16 != 0) return;
+    const int R2 = P / 16;
+    for (int e = 0; e < 16; ++e)  // e = 2m + par
+        for (int n2 = 0; n2 < R2; ++n2) {
+            const double2 x = w[(n2 * e) % P];
+            out[e * R2 + n2] = C{R(x.x), R(x.y)};
+        }
+    for (int e = 0; e < R2; ++e)  // e = 2m + par2
+        for (int k1 = 0; k1 < 16; ++k1) {
+            const double2 x = w[(k1 * e) % P];
+            out[P + e * 16 + k1] = C{R(x.x), R(x.y)};
+        }
+}
+
 // ---- context --------------------------------------------------------------------------------------
 struct Group {
     int rbytes = 4;  // bytes of the group's real type (4: the FP32 path, 8: FP64)
+    // energy evaluations are cached per state: state_epoch advances whenever the group's path changes
+    // (ss_set_path, ss_step, ss_time_kernels), eval_epoch records the state the FP64 energies are of
+    long long state_epoch = 0, eval_epoch = -1;
     int nx = 0, ny = 0, nz = 0, N = 0, Px = 1, Py = 1;
     int n_img = 0, n_pairs = 0;
     std::vector<int> strs;  // context string ids, in group order
@@ -91,6 +113,7 @@ struct Group {
     // device
     void *s = nullptr, *sp = nullptr, *spec = nullptr, *dhat = nullptr, *twx = nullptr, *twy = nullptr;
     void *twxs = nullptr, *twys = nullptr;
+    void *t2x = nullptr, *t2y = nullptr;  // two-pass twiddle tables (2 Px, 2 Py entries)
     void *prm = nullptr, *hout = nullptr;
     InterpEntry* interp = nullptr;
     double* epart = nullptr;
@@ -233,6 +256,8 @@ template <typename T> GroupArgs<T> group_args(const ss_ctx* c, const Group& g) {
     a.twy = (const cplx<T>*)g.twy;
     a.twxs = (const cplx<T>*)g.twxs;
     a.twys = (const cplx<T>*)g.twys;
+    a.t2x = (const cplx<T>*)g.t2x;
+    a.t2y = (const cplx<T>*)g.t2y;
     a.planx = g.planx;
     a.plany = g.plany;
     a.prm = (const ImgParam<T>*)g.prm;
@@ -366,6 +391,8 @@ template <typename T> ss_status setup_group(ss_ctx* c, Group& g) {
     TRY(dalloc(c, &g.twy, g.Py * sizeof(C)));
     TRY(dalloc(c, &g.twxs, g.Px * sizeof(C)));
     TRY(dalloc(c, &g.twys, g.Py * sizeof(C)));
+    TRY(dalloc(c, &g.t2x, 2 * g.Px * sizeof(C)));
+    TRY(dalloc(c, &g.t2y, 2 * g.Py * sizeof(C)));
     if (g.direct) TRY(dalloc(c, &g.hdir, (size_t)g.n_img * 3 * g.N * sizeof(T)));
     if (g.dipole) {
         TRY(dalloc(c, &g.spec, (size_t)g.n_pairs * g.Px * 3 * g.nz * g.ny * sizeof(C)));
@@ -398,6 +425,11 @@ template <typename T> ss_status setup_group(ss_ctx* c, Group& g) {
     fft_stage_twiddles(g.plany, twy.data(), sy.data());
     CUDA_TRY(c, cudaMemcpyAsync(g.twxs, sx.data(), g.Px * sizeof(C), cudaMemcpyHostToDevice, c->cs));
     CUDA_TRY(c, cudaMemcpyAsync(g.twys, sy.data(), g.Py * sizeof(C), cudaMemcpyHostToDevice, c->cs));
+    std::vector<C> t2x(2 * g.Px), t2y(2 * g.Py);
+    two_pass_twiddles(g.Px, twx, t2x.data());
+    two_pass_twiddles(g.Py, twy, t2y.data());
+    CUDA_TRY(c, cudaMemcpyAsync(g.t2x, t2x.data(), 2 * g.Px * sizeof(C), cudaMemcpyHostToDevice, c->cs));
+    CUDA_TRY(c, cudaMemcpyAsync(g.t2y, t2y.data(), 2 * g.Py * sizeof(C), cudaMemcpyHostToDevice, c->cs));
     // arc-length bookkeeping
     ArcArgs& a = g.arc;
     a.n_str = nstr;
@@ -852,19 +884,24 @@ ss_status ensure_ev64(ss_ctx* c) {
 // path by its own evaluation, on the FP32 path by the FP64 pipeline applied to the FP32 state (the
 // gathered spins widened to FP64), so that the reported energies carry no FP32 convolution round-off.
 // *out points at the group whose eval_E / eval_terms hold the result once the stream reaches them.
+// The result is cached until the group's path changes, so the strings of a size group share one evaluation.
 ss_status evaluate_energies(ss_ctx* c, int gi, const Group** out) {
     Group& g = c->groups[gi];
     if (use_fp64(c)) {
-        TRY(evaluate_group(c, g, false));
+        if (g.eval_epoch != g.state_epoch) TRY(evaluate_group(c, g, false));
+        g.eval_epoch = g.state_epoch;
         *out = &g;
         return SS_OK;
     }
     TRY(ensure_ev64(c));
     Group& e = c->ev64[gi];
-    issue_materialise<float>(c, g, c->cs);
-    launch_widen_unit((const float*)g.s, (double*)e.sp, g.n_img, g.N, c->cs);
-    issue_eval<double>(c, e, nullptr, c->cs);
-    CUDA_TRY(c, cudaGetLastError());
+    if (g.eval_epoch != g.state_epoch) {
+        issue_materialise<float>(c, g, c->cs);
+        launch_widen_unit((const float*)g.s, (double*)e.sp, g.n_img, g.N, c->cs);
+        issue_eval<double>(c, e, nullptr, c->cs);
+        CUDA_TRY(c, cudaGetLastError());
+        g.eval_epoch = g.state_epoch;
+    }
     *out = &e;
     return SS_OK;
 }
@@ -1078,6 +1115,7 @@ ss_status ss_set_path(ss_ctx* c, int string, const void* spins, int dtype, int o
     Group& g = c->groups[r.group];
     const int K = r.d.n_images;
     const size_t bytes = (size_t)K * g.N * 3 * dtype_size(dtype);
+    ++g.state_epoch;
     TRY(enter(c));
     const void* src = spins;
     if (!on_device) {
@@ -1280,6 +1318,7 @@ ss_status ss_step(ss_ctx* c, int n_iter) {
     if (n_iter < 0) return fail(c, SS_ERR_INVALID_ARG, "n_iter < 0");
     for (const Group& g : c->groups) TRY(check_paths(c, g));
     if (n_iter == 0) return SS_OK;
+    for (Group& g : c->groups) ++g.state_epoch;
     TRY(enter(c));
     if (c->integrator != SS_INT_EULER) {
         TRY(use_fp64(c) ? rk_iterations<double>(c, n_iter) : rk_iterations<float>(c, n_iter));
@@ -1397,6 +1436,7 @@ ss_status ss_time_kernels(ss_ctx* c, int reps, double* ms_out, int max_out, int*
     for (const Group& g : c->groups) TRY(check_paths(c, g));
     std::vector<int> per_group;
     int nk = 0;
+    for (Group& g : c->groups) ++g.state_epoch;  // the strings advance
     for (Group& g : c->groups) {
         per_group.push_back(use_fp64(c) ? time_entries<double>(c, g, -2) : time_entries<float>(c, g, -2));
         nk += per_group.back();

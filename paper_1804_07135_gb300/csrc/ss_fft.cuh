@@ -467,9 +467,9 @@ template <typename C> __device__ __forceinline__ void mul_w16_ramp(C (&u)[8]) {
 
 // Pass 1 for role (n2, par) of one line.  u holds x[8 n1 + n2] for n1 < 8 on entry; hi (when given)
 // holds x[8 n1 + 64 + n2].  Writes Z[n2][2m + par] of the line at zl = exchange buffer + line offset.
-// tw: flat table W_128^k (k < 128).
+// t1: the pass-1 twiddle table (GroupArgs::t2x / t2y), W_128^{n2 (2m + par)} at (2m + par) * 8 + n2.
 template <bool HAS_HI, typename C>
-__device__ __forceinline__ void f128_pass1(C (&u)[8], const C (&hi)[8], int n2, int par, const C* __restrict__ tw,
+__device__ __forceinline__ void f128_pass1(C (&u)[8], const C (&hi)[8], int n2, int par, const C* __restrict__ t1,
                                            C* zl) {
     if constexpr (HAS_HI) {
 #pragma unroll
@@ -479,7 +479,7 @@ __device__ __forceinline__ void f128_pass1(C (&u)[8], const C (&hi)[8], int n2, 
     Dft<8, C>::run(u);
     C* z = zl + n2 * kF128N2 + par;
 #pragma unroll
-    for (int m = 0; m < 8; ++m) z[2 * m] = cmul(u[m], tw[n2 * (2 * m + par)]);  // tw[0] = 1 exactly
+    for (int m = 0; m < 8; ++m) z[2 * m] = cmul(u[m], t1[(2 * m + par) * 8 + n2]);  // W_128^{n2 (2m + par)}
 }
 
 // Pass 2 for role k1 of one line: v[k2] = X[k1 + 16 k2] (k2 < KOUT) from Z[.][k1] at zl + k1.
@@ -507,25 +507,27 @@ template <typename C> __device__ __forceinline__ void f128_pass2(C (&v)[8], cons
 // pass A, role (k1, par2), column k1: the R2/2-point DFTs as in pass 2, times W_P^{k1 y2}, back into column k1
 //   (row y2);
 // pass B, role (y2, par), row y2: an 8-point DFT of (T[j][y2] +- T[j+8][y2]) W_16^{j par} -> Y[y2 + R2 (2m + par)];
-// an inverse read below P/2 keeps m < 4.  Twiddles W_P^e come from the flat table (e < P); the ramp
-// W_R2^j = W_P^{16 j}.
+// an inverse read below P/2 keeps m < 4.  The twiddles of pass 1 and pass A come from the tables of
+// GroupArgs::t2x / t2y (t1 = the pass-1 half, ta = the pass-A half, indexed so that a warp's lanes read
+// consecutive entries); the ramp W_R2^j = W_P^{16 j} from the flat table tw (the same entry across a warp).
 __device__ __forceinline__ int t2_pos(int ky) { return (ky >> 4) * kT2Row + (ky & 15); }
 
 // Pass 1 of a line whose upper half is zero: u[j] = x[R2 j + n2] (j < 8) on entry; writes row n2 of Z.
 template <int P, typename C>
-__device__ __forceinline__ void t2_pass1(C (&u)[8], int n2, int par, const C* __restrict__ tw, C* line) {
+__device__ __forceinline__ void t2_pass1(C (&u)[8], int n2, int par, const C* __restrict__ t1, C* line) {
     if (par) mul_w16_ramp(u);
     Dft<8, C>::run(u);
     C* z = line + n2 * kT2Row + par;
 #pragma unroll
-    for (int m = 0; m < 8; ++m) z[2 * m] = cmul(u[m], tw[n2 * (2 * m + par)]);  // tw[0] = 1 exactly
+    for (int m = 0; m < 8; ++m) z[2 * m] = cmul(u[m], t1[(2 * m + par) * (P / 16) + n2]);  // W_P^{n2 (2m + par)}
 }
 
 // The R2/2-point DFTs of pass 2 (TW_OUT = false) or pass A (TW_OUT = true) for column k1 and parity par2:
 // a[m] = the output of row 2m + par2 (times W_P^{k1 (2m + par2)} in pass A).  col(j) returns the column's
 // row j (from shared or global memory).
 template <int P, bool TW_OUT, typename C, typename Col>
-__device__ __forceinline__ void t2_col_vals(C (&a)[P / 32], Col col, int k1, int par2, const C* __restrict__ tw) {
+__device__ __forceinline__ void t2_col_vals(C (&a)[P / 32], Col col, int k1, int par2, const C* __restrict__ tw,
+                                            const C* __restrict__ ta) {
     constexpr int R2 = P / 16, H = R2 / 2;
 #pragma unroll
     for (int j = 0; j < H; ++j) {
@@ -539,7 +541,7 @@ __device__ __forceinline__ void t2_col_vals(C (&a)[P / 32], Col col, int k1, int
     Dft<H, C>::run(a);
     if constexpr (TW_OUT) {
 #pragma unroll
-        for (int m = 0; m < H; ++m) a[m] = cmul(a[m], tw[k1 * (2 * m + par2)]);
+        for (int m = 0; m < H; ++m) a[m] = cmul(a[m], ta[(2 * m + par2) * 16 + k1]);  // W_P^{k1 (2m + par2)}
     }
 }
 
@@ -547,11 +549,11 @@ __device__ __forceinline__ void t2_col_vals(C (&a)[P / 32], Col col, int k1, int
 // The caller pairs the roles par2 = 0 and 1 of a column in one warp; the column is read whole before
 // either writes (a __syncwarp between the reads and the writes).
 template <int P, bool TW_OUT, typename C>
-__device__ __forceinline__ void t2_cols(C* line, int k1, int par2, const C* __restrict__ tw) {
+__device__ __forceinline__ void t2_cols(C* line, int k1, int par2, const C* __restrict__ tw, const C* __restrict__ ta) {
     constexpr int H = P / 32;
     C a[H];
     const C* col = line + k1;
-    t2_col_vals<P, TW_OUT>(a, [&](int j) { return col[j * kT2Row]; }, k1, par2, tw);
+    t2_col_vals<P, TW_OUT>(a, [&](int j) { return col[j * kT2Row]; }, k1, par2, tw, ta);
     __syncwarp();
     C* o = line + k1 + par2 * kT2Row;
 #pragma unroll

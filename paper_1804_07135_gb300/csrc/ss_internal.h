@@ -79,6 +79,11 @@ template <typename T> struct GroupArgs {
     const cplx<T>* twy;
     const cplx<T>* twxs;  // per-stage twiddle tables (compile-time plans), P entries each
     const cplx<T>* twys;
+    // two-pass transforms (P = 128, 192, 256, 384), 2P entries each, laid out so that the lanes of a warp
+    // read consecutive entries: [0, P) pass 1, W_P^{n2 (2m + par)} at (2m + par) * P/16 + n2; [P, 2P) pass A,
+    // W_P^{k1 (2m + par2)} at P + (2m + par2) * 16 + k1
+    const cplx<T>* t2x;
+    const cplx<T>* t2y;
     FftPlan planx, plany;
     const ImgParam<T>* prm;
     const InterpEntry* interp;

@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xfwd128_kernel(Grou
     const int p = blockIdx.z, z = blockIdx.y, y0 = blockIdx.x * ROWS;
     const int rows = min(ROWS, g.ny - y0);
     const int nx = g.nx;
-    const C* __restrict__ tw = g.twx;  // W_128^k
+    const C* __restrict__ tw = g.t2x;  // pass-1 twiddles of length 128
     griddep_wait();
     griddep_launch_dependents();
     xfwd_gather(g, buf, kF128Buf, ROWS, p, z, y0, rows, tid, nthr);
@@ -570,7 +570,7 @@ __global__ void __launch_bounds__(kMaxThreadsYz, kMinBlocks128) yz128_kernel(Gro
         for (int i = tid; i < (hy + 1) * NZ * 6; i += nthr) dsm[i] = dslab[i];
         dslab = dsm;
     }
-    const C* __restrict__ tw = g.twy;  // W_128^k
+    const C* __restrict__ tw = g.t2y;  // pass-1 twiddles of length 128
     griddep_wait();
     griddep_launch_dependents();
     for (int r = tid; r < 16 * L; r += nthr) {
@@ -710,6 +710,8 @@ __global__ void __launch_bounds__(kYz2Threads, P == 384 ? 2 : 3) yz2p_kernel(Gro
     const int ny = g.ny;
     C* blk = g.spec + ((size_t)p * g.Px + kx) * 3 * NZ * ny;  // KXB consecutive columns are contiguous
     const C* __restrict__ tw = g.twy;                         // W_P^k
+    const C* __restrict__ t1 = g.t2y;                         // pass 1
+    const C* __restrict__ ta = g.t2y + P;                     // pass A
     griddep_wait();
     griddep_launch_dependents();
     // pass 1, role (n2, line, par), n2 fastest: the zero-padded spectrum lines in, rows of Z out
@@ -719,11 +721,11 @@ __global__ void __launch_bounds__(kYz2Threads, P == 384 ? 2 : 3) yz2p_kernel(Gro
         C u[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) u[j] = R2 * j + n2 < ny ? src[R2 * j] : make_float2(0.f, 0.f);
-        t2_pass1<P>(u, n2, par, tw, A + line * LS);
+        t2_pass1<P>(u, n2, par, t1, A + line * LS);
     }
     __syncthreads();
     // pass 2: one warp per line (lanes = 16 columns x 2 parities)
-    for (int r = tid; r < 32 * L; r += nthr) t2_cols<P, false>(A + (r >> 5) * LS, r & 15, (r >> 4) & 1, tw);
+    for (int r = tid; r < 32 * L; r += nthr) t2_cols<P, false>(A + (r >> 5) * LS, r & 15, (r >> 4) & 1, tw, ta);
     __syncthreads();
 #pragma unroll 1
     for (int b = 0; b < KXB; ++b) {
@@ -732,7 +734,7 @@ __global__ void __launch_bounds__(kYz2Threads, P == 384 ? 2 : 3) yz2p_kernel(Gro
     }
     __syncthreads();
     // pass A (the inverse transform of the conjugated field spectra, in place by columns)
-    for (int r = tid; r < 32 * L; r += nthr) t2_cols<P, true>(A + (r >> 5) * LS, r & 15, (r >> 4) & 1, tw);
+    for (int r = tid; r < 32 * L; r += nthr) t2_cols<P, true>(A + (r >> 5) * LS, r & 15, (r >> 4) & 1, tw, ta);
     __syncthreads();
     // pass B, role (y2, line, par): rows y < ny back to the spectrum, conjugated
     for (int r = tid; r < 2 * R2 * L; r += nthr) {
@@ -1076,7 +1078,7 @@ __global__ void __launch_bounds__(kMaxThreads128, kMinBlocks128) xinv128_kernel(
     const int rows = min(ROWS, g.ny - y0);
     const size_t kstride = (size_t)3 * g.nz * g.ny;  // between consecutive kx
     const C* inp = g.spec + (size_t)p * 128 * kstride + (size_t)z * g.ny + y0;
-    const C* __restrict__ tw = g.twx;  // W_128^k
+    const C* __restrict__ tw = g.t2x;  // pass-1 twiddles of length 128
     griddep_wait();
     griddep_launch_dependents();
     // pass 1: role (c, par, j, yy), yy fastest, then j (n2 a permutation of j that puts a half-warp's
@@ -1128,6 +1130,7 @@ __global__ void __launch_bounds__(kX2Threads, P == 384 ? 2 : 3) xfwd2p_kernel(Gr
     const int p = blockIdx.z, z = blockIdx.y, y0 = blockIdx.x * ROWS;
     const int rows = min(ROWS, g.ny - y0), nx = g.nx;
     const C* __restrict__ tw = g.twx;  // W_P^k
+    const C* __restrict__ t1 = g.t2x;  // pass 1
     griddep_wait();
     griddep_launch_dependents();
     xfwd_gather(g, xb, LB, ROWS, p, z, y0, rows, tid, nthr);
@@ -1140,7 +1143,7 @@ __global__ void __launch_bounds__(kX2Threads, P == 384 ? 2 : 3) xfwd2p_kernel(Gr
         C u[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) u[j] = R2 * j + n2 < nx ? b[fft_pad(R2 * j + n2)] : make_float2(0.f, 0.f);
-        t2_pass1<P>(u, n2, par, tw, A + (c * ROWS + yy) * LSX);
+        t2_pass1<P>(u, n2, par, t1, A + (c * ROWS + yy) * LSX);
     }
     __syncthreads();
     // pass 2, role (yy, k1, par2, c): X[k1 + 16 (2m + par2)] to the spectrum
@@ -1151,7 +1154,7 @@ __global__ void __launch_bounds__(kX2Threads, P == 384 ? 2 : 3) xfwd2p_kernel(Gr
         if (yy >= rows) continue;
         const C* col = A + (c * ROWS + yy) * LSX + k1;
         C a[H];
-        t2_col_vals<P, false>(a, [&](int j) { return col[j * kT2Row]; }, k1, par2, tw);
+        t2_col_vals<P, false>(a, [&](int j) { return col[j * kT2Row]; }, k1, par2, tw, tw);
         C* o = outp + (size_t)c * g.nz * g.ny + yy;
 #pragma unroll
         for (int m = 0; m < H; ++m) o[(size_t)(k1 + 16 * (2 * m + par2)) * kstride] = a[m];
@@ -1174,6 +1177,7 @@ __global__ void __launch_bounds__(kX2Threads, P == 384 ? 2 : 3) xinv2p_kernel(Gr
     const size_t kstride = (size_t)3 * g.nz * g.ny;
     const C* inp = g.spec + (size_t)p * P * kstride + (size_t)z * g.ny + y0;
     const C* __restrict__ tw = g.twx;
+    const C* __restrict__ ta = g.t2x + P;  // pass A
     griddep_wait();
     griddep_launch_dependents();
     // pass A, role (yy, k1, par2, c): column k1 of the conjugated spectrum line (c, yy)
@@ -1182,7 +1186,7 @@ __global__ void __launch_bounds__(kX2Threads, P == 384 ? 2 : 3) xinv2p_kernel(Gr
         if (yy >= rows) continue;
         const C* sc = inp + (size_t)c * g.nz * g.ny + yy + (size_t)k1 * kstride;
         C a[H];
-        t2_col_vals<P, true>(a, [&](int j) { return cconj(sc[(size_t)16 * j * kstride]); }, k1, par2, tw);
+        t2_col_vals<P, true>(a, [&](int j) { return cconj(sc[(size_t)16 * j * kstride]); }, k1, par2, tw, ta);
         C* o = A + (c * ROWS + yy) * LSX + k1 + par2 * kT2Row;
 #pragma unroll
         for (int m = 0; m < H; ++m) o[2 * m * kT2Row] = a[m];

@@ -126,6 +126,21 @@ __global__ void na_stage_twiddles(FftPlan p, const double2* tw64, float2* out) {
     }
 }
 
+// Two-pass twiddle tables (layout of GroupArgs::t2x / t2y) from the flat FP64 table; zeros when P is not
+// a multiple of 16.
+__global__ void na_t2_table(int P, const double2* tw64, float2* out) {
+    const int R2 = P / 16;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 * P; i += gridDim.x * blockDim.x) {
+        float2 v = make_float2(0.f, 0.f);
+        if (P % 16 == 0) {
+            const int e = i < P ? i / R2 : (i - P) / 16, q = i < P ? i % R2 : (i - P) % 16;
+            const double2 x = tw64[(q * e) % P];
+            v = make_float2((float)x.x, (float)x.y);
+        }
+        out[i] = v;
+    }
+}
+
 __global__ void na_params(ImgParam<float>* prm, int n, float J, float D, float K, float w) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         ImgParam<float> p;
@@ -197,6 +212,7 @@ extern "C" ss_status ss_field_noalloc(int nx, int ny, int nz, double J, double D
     const size_t o_tw64x = take(Px * sizeof(double2)), o_tw64y = take(Py * sizeof(double2));
     const size_t o_twx = take(Px * sizeof(float2)), o_twy = take(Py * sizeof(float2));
     const size_t o_twxs = take(Px * sizeof(float2)), o_twys = take(Py * sizeof(float2));
+    const size_t o_t2x = take(2 * Px * sizeof(float2)), o_t2y = take(2 * Py * sizeof(float2));
     const size_t o_dhat = take(dip ? (size_t)(Px / 2 + 1) * (Py / 2 + 1) * nz * 6 * sizeof(float) : 0);
     const size_t o_prm = take(n_images * sizeof(ImgParam<float>));
     const size_t o_interp = take(n_images * sizeof(InterpEntry));
@@ -228,6 +244,10 @@ extern "C" ss_status ss_field_noalloc(int nx, int ny, int nz, double J, double D
     float2* twys = reinterpret_cast<float2*>(base + o_twys);
     na_stage_twiddles<<<1, 256, 0, st>>>(px, tw64x, twxs);
     na_stage_twiddles<<<1, 256, 0, st>>>(py, tw64y, twys);
+    float2* t2x = reinterpret_cast<float2*>(base + o_t2x);
+    float2* t2y = reinterpret_cast<float2*>(base + o_t2y);
+    na_t2_table<<<(2 * Px + 127) / 128, 128, 0, st>>>(Px, tw64x, t2x);
+    na_t2_table<<<(2 * Py + 127) / 128, 128, 0, st>>>(Py, tw64y, t2y);
     if (dip) {
         // the tensor spectrum is rebuilt on every call: the build area is shared with the spins below
         double2* tens = reinterpret_cast<double2*>(base + o_work);
@@ -263,6 +283,8 @@ extern "C" ss_status ss_field_noalloc(int nx, int ny, int nz, double J, double D
     g.twy = twy;
     g.twxs = twxs;
     g.twys = twys;
+    g.t2x = t2x;
+    g.t2y = t2y;
     g.planx = px;
     g.plany = py;
     g.prm = prm;
