@@ -418,6 +418,7 @@ def main():
         line["fp64_gpu"] = fp64_gpu_rate(binding, wl, stream, paths_dev)
         line["speedup_vs_fp64_gpu"] = line["fp64_gpu"]["ms_per_iter"] / (1e3 * step_s / n_iter)
     if not args.no_other_workloads:
+        line["size_groups_alone"] = group_standalone(binding, wl, stream)
         line["bloch_64x64x8"] = bloch_64x64x8(binding, stream, peaks, peak_kind, no_accuracy=args.no_accuracy)
         line["other_workloads"] = {w.name: other_workload(binding, w, stream) for w in
                                    (workloads.boundary_sweep(), workloads.paper_monolayer_workload(),
@@ -607,6 +608,33 @@ def other_workload(binding, wl, stream, iters=20, warm=3):
     return {"value": wl.spin_updates_per_iter * iters / t, "unit": "spin-updates/s", "iterations_timed": iters,
             "strings": len(wl.strings), "spin_updates_per_iter": wl.spin_updates_per_iter,
             "ms_per_iter": 1e3 * t / iters, "kernel_ms_total": float(ms.sum())}
+
+
+def group_standalone(binding, wl, stream, iters=20, warm=3):
+    """Each size group of a batch workload run alone (its strings in a context of their own), device-timed
+    as other_workload, against all groups in one context; the sum of the lone groups' times per iteration
+    against the combined one shows what running the groups as concurrent graph branches saves."""
+    import torch
+    keys, _ = group_keys(wl)
+    out = {}
+    for k in keys + [None]:
+        strings = [s for s in wl.strings if k is None or (s.nx, s.ny, s.nz) == k]
+        descs = [(s.nx, s.ny, s.nz, s.J, s.D, s.K, s.w, s.n_images) for s in strings]
+        with binding.StringMethod(descs, dt=wl.dt, stream=stream.cuda_stream) as sm:
+            for i, s in enumerate(strings):
+                sm.set_path(i, torch.from_numpy(s.initial_path().astype(np.float32)).cuda())
+            sm.step(warm)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            sm.step(iters)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out["combined" if k is None else f"{k[0]}x{k[1]}x{k[2]}"] = e0.elapsed_time(e1) / iters
+    combined = out.pop("combined")
+    total = sum(out.values())
+    return {"ms_per_iter": out, "sum_ms_per_iter": total, "combined_ms_per_iter": combined,
+            "combined_vs_sum": combined / total}
 
 
 def yz_flops(spec):
