@@ -115,8 +115,13 @@ ss_status ss_energies(ss_ctx* ctx, int string, double* out);
  * iteration (Sec. III).  Host out[n_images].  Synchronises. */
 ss_status ss_step_energies(ss_ctx* ctx, int string, double* out);
 
-/* Barrier of `string` (Sec. III): *dE = max_k E_k - E_0 over ss_energies, *k_max = the maximising
- * image (lowest index on ties).  Either pointer may be NULL.  Synchronises. */
+/* Barrier of `string` (Sec. III): *dE = max_k E_k - E_0 over the FP64 energies of ss_energies, *k_max =
+ * the maximising image (lowest index on ties).  On an SS_PREC_FP32 context only the images that can
+ * decide it are evaluated in FP64: the FP32 evaluation bounds every image's energy (its FFT round-off
+ * bound), and image 0 and every image whose upper bound reaches the highest lower bound are evaluated by
+ * the FP64 pipeline, so the result equals the one from all FP64 energies; the selection is made once
+ * per size group and path state and shared by the group's strings.  Either pointer may be NULL.
+ * Synchronises. */
 ss_status ss_barrier(ss_ctx* ctx, int string, double* dE, int* k_max);
 
 /* Effective field h = -dE/ds (Eqs. 2-7) of every image of the current path of `string` into `out`

@@ -118,7 +118,13 @@ struct Group {
     InterpEntry* interp = nullptr;
     double* epart = nullptr;
     int *d_str_img0 = nullptr, *d_str_K = nullptr;
-    double *dpart = nullptr, *e_last = nullptr, *eval_terms = nullptr, *eval_E = nullptr;
+    double *dpart = nullptr, *e_last = nullptr, *eval_terms = nullptr, *eval_E = nullptr, *eval_cn = nullptr;
+    int* pair_on = nullptr;  // FP64 evaluation copy: the pairs holding barrier candidates
+    // barrier candidates of an FP32 context (ss_barrier): the FP32 energies and round-off bounds select the
+    // images whose FP64 energy can decide the barrier; their FP64 energies, valid for state bar_epoch
+    long long bar_epoch = -1;
+    std::vector<double> bar_E;  // [image] FP64 energy of a candidate, or NaN
+
     unsigned* arc_cnt = nullptr;
     // adaptive Runge-Kutta evolution (allocated by ss_set_integrator)
     void *rk_y0 = nullptr, *rk_k = nullptr, *rk_y5 = nullptr;
@@ -289,7 +295,7 @@ void set_rows(Group& g, int ty_a, int ty_c, int thr_a = 256, int thr_c = 256) {
     g.thr_a = thr_a;
     g.thr_c = thr_c;
     g.smem_a = (size_t)(g.Px + 3 * g.ty_a * g.lsx) * cs;
-    g.smem_c = (size_t)(g.Px + 3 * g.ty_c * g.lsx) * cs + 32 * 8 * sizeof(double);
+    g.smem_c = (size_t)(g.Px + 3 * g.ty_c * g.lsx) * cs + 32 * 2 * kEvalTerms * sizeof(double);
     if (g.dipole && f128_x(g.rbytes, g.Px)) {  // the launchers derive these shapes themselves
         g.thr_a = f128_x_threads(ty_a);
         g.thr_c = f128_x_threads(ty_c);
@@ -386,7 +392,7 @@ template <typename T> ss_status setup_group(ss_ctx* c, Group& g) {
     TRY(dalloc(c, &g.sp, g.n_img * M * sizeof(T)));
     TRY(dalloc(c, (void**)&g.interp, g.n_img * sizeof(InterpEntry)));
     TRY(dalloc(c, &g.prm, g.n_img * sizeof(ImgParam<T>)));
-    TRY(dalloc(c, (void**)&g.epart, (size_t)g.n_img * 4 * g.nz * g.ny * sizeof(double)));  // any rows per CTA
+    TRY(dalloc(c, (void**)&g.epart, (size_t)g.n_img * kEvalTerms * g.nz * g.ny * sizeof(double)));  // any rows per CTA
     TRY(dalloc(c, &g.twx, g.Px * sizeof(C)));
     TRY(dalloc(c, &g.twy, g.Py * sizeof(C)));
     TRY(dalloc(c, &g.twxs, g.Px * sizeof(C)));
@@ -434,7 +440,9 @@ template <typename T> ss_status setup_group(ss_ctx* c, Group& g) {
     ArcArgs& a = g.arc;
     a.n_str = nstr;
     a.maxK = maxK;
-    a.tile_elems = 1024;  // 4 components per thread of a 256-thread CTA
+    // components per tile CTA: 1024 (4 per thread of a 256-thread CTA), more on large lattices so that a
+    // string has at most about 128 tiles -- the finisher sums every tile's partial of every distance
+    a.tile_elems = 1024 * std::max(1, std::min(16, (int)(M / (1024 * 128))));
     a.n_tiles = (int)((M + a.tile_elems - 1) / a.tile_elems);
     a.kchunk = std::max(1, std::min(8, maxK - 1));
     a.n_kchunks = std::max(1, (maxK - 1 + a.kchunk - 1) / a.kchunk);
@@ -448,6 +456,8 @@ template <typename T> ss_status setup_group(ss_ctx* c, Group& g) {
     CUDA_TRY(c, cudaMemsetAsync(g.arc_cnt, 0, n_cnt * sizeof(unsigned), c->cs));
     TRY(dalloc(c, (void**)&g.eval_terms, (size_t)nstr * maxK * 4 * sizeof(double)));
     TRY(dalloc(c, (void**)&g.eval_E, (size_t)nstr * maxK * sizeof(double)));
+    TRY(dalloc(c, (void**)&g.eval_cn, (size_t)nstr * maxK * sizeof(double)));
+    TRY(dalloc(c, (void**)&g.pair_on, (size_t)g.n_pairs * sizeof(int)));
     CUDA_TRY(c, cudaMemcpyAsync(g.d_str_img0, g.str_img0.data(), nstr * sizeof(int), cudaMemcpyHostToDevice, c->cs));
     CUDA_TRY(c, cudaMemcpyAsync(g.d_str_K, g.str_K.data(), nstr * sizeof(int), cudaMemcpyHostToDevice, c->cs));
     CUDA_TRY(c, cudaMemsetAsync(g.dpart, 0, (size_t)nstr * maxK * a.n_tiles * sizeof(double), c->cs));
@@ -750,13 +760,16 @@ template <typename T> void issue_group_iteration(ss_ctx* c, Group& g, cudaStream
     }
 }
 
-template <typename T> void issue_eval(ss_ctx* c, Group& g, T* hout, cudaStream_t st) {
+// The evaluation pipeline (energies, terms, convolution norms; the field into hout when given).  pair_on
+// (device flags per image pair, or null) restricts it to the flagged pairs.
+template <typename T> void issue_eval(ss_ctx* c, Group& g, T* hout, cudaStream_t st, const int* pair_on = nullptr) {
     GroupArgs<T> a = group_args<T>(c, g);
+    a.pair_on = pair_on;
     launch_xfwd<T>(a, g.dipole, g.thr_a, g.smem_a, st);
     if (g.dipole) launch_yz<T>(a, g.thr_b, g.smem_b, st);
     if (g.direct) launch_dipole_direct<T>(a, (T*)g.hdir, st);
     launch_xinv_eval<T>(a, g.dipole, hout, g.thr_c, g.smem_c_eval, st);
-    launch_eval_reduce<T>(a, g.arc, g.eval_terms, g.eval_E, st);
+    launch_eval_reduce<T>(a, g.arc, g.eval_terms, g.eval_E, g.eval_cn, st);
 }
 
 template <typename T> void issue_materialise(ss_ctx* c, Group& g, cudaStream_t st) {
@@ -903,6 +916,66 @@ ss_status evaluate_energies(ss_ctx* c, int gi, const Group** out) {
         g.eval_epoch = g.state_epoch;
     }
     *out = &e;
+    return SS_OK;
+}
+
+// FP32 contexts: the FP64 energies of the images that can decide a barrier (Sec. III: max_k E_k - E_0) of
+// every string of size group gi, for the group's current state, into *out ([image], NaN for the others).
+// The FP32 evaluation gives each image's energy E_k with a round-off bound B_k: the local terms are FP64
+// sums over the spins renormalised in FP64, and the dipole term's FFT round-off obeys
+// ||d conv||_2 <= eps ||conv||_2, eps = u (2 log2(Px Py) + 3 nz + 4), so |dE_k| <= w (1/2) eps ||conv_k||_2
+// sqrt(N), plus 1e-9 + 1e-13 |E_k| for the FP64 sums.  An image whose upper bound E_k + B_k lies below the
+// largest lower bound max_j (E_j - B_j) of its string cannot be the highest one, so only image 0 and the
+// remaining images are evaluated in FP64 -- the pairs holding them, on the FP64 evaluation copy.
+ss_status barrier_energies(ss_ctx* c, int gi, const std::vector<double>** out) {
+    Group& g = c->groups[gi];
+    if (g.bar_epoch == g.state_epoch) {
+        *out = &g.bar_E;
+        return SS_OK;
+    }
+    TRY(ensure_ev64(c));
+    Group& e = c->ev64[gi];
+    const int nstr = (int)g.strs.size(), mk = g.arc.maxK;
+    std::vector<double> E(g.n_img, NAN), buf((size_t)nstr * mk), cn((size_t)nstr * mk);
+    if (g.eval_epoch == g.state_epoch) {  // every image has its FP64 energy already
+        CUDA_TRY(c, cudaMemcpyAsync(buf.data(), e.eval_E, buf.size() * sizeof(double), cudaMemcpyDeviceToHost, c->cs));
+        TRY(sync_check(c));
+        for (int i = 0; i < nstr; ++i)
+            for (int k = 0; k < g.str_K[i]; ++k) E[g.str_img0[i] + k] = buf[(size_t)i * mk + k];
+    } else {
+        TRY(evaluate_group(c, g, false));  // FP32 energies and convolution norms (and the gathered state in s)
+        CUDA_TRY(c, cudaMemcpyAsync(buf.data(), g.eval_E, buf.size() * sizeof(double), cudaMemcpyDeviceToHost, c->cs));
+        CUDA_TRY(c, cudaMemcpyAsync(cn.data(), g.eval_cn, cn.size() * sizeof(double), cudaMemcpyDeviceToHost, c->cs));
+        TRY(sync_check(c));
+        const double eps = std::ldexp(1.0, -24) * (2.0 * std::log2((double)g.Px * g.Py) + 3.0 * g.nz + 4.0);
+        std::vector<int> on(g.n_pairs, 0);
+        for (int i = 0; i < nstr; ++i) {
+            const ss_string_desc& d = c->strs[g.strs[i]].d;
+            const double w = g.dipole ? std::fabs(d.w) : 0.0;
+            const int K = g.str_K[i], img0 = g.str_img0[i];
+            auto bound = [&](int k) {
+                const size_t q = (size_t)i * mk + k;
+                return w * 0.5 * eps * std::sqrt(std::max(cn[q], 0.0)) * std::sqrt((double)g.N) + 1e-9 +
+                       1e-13 * std::fabs(buf[q]);
+            };
+            double lo_max = -INFINITY;
+            for (int k = 0; k < K; ++k) lo_max = std::max(lo_max, buf[(size_t)i * mk + k] - bound(k));
+            for (int k = 0; k < K; ++k)
+                if (k == 0 || !(buf[(size_t)i * mk + k] + bound(k) < lo_max)) on[(img0 + k) >> 1] = 1;
+        }
+        CUDA_TRY(c, cudaMemcpyAsync(e.pair_on, on.data(), on.size() * sizeof(int), cudaMemcpyHostToDevice, c->cs));
+        launch_widen_unit((const float*)g.s, (double*)e.sp, g.n_img, g.N, c->cs);
+        issue_eval<double>(c, e, nullptr, c->cs, e.pair_on);
+        CUDA_TRY(c, cudaGetLastError());
+        CUDA_TRY(c, cudaMemcpyAsync(buf.data(), e.eval_E, buf.size() * sizeof(double), cudaMemcpyDeviceToHost, c->cs));
+        TRY(sync_check(c));
+        for (int i = 0; i < nstr; ++i)
+            for (int k = 0; k < g.str_K[i]; ++k)
+                if (on[(g.str_img0[i] + k) >> 1]) E[g.str_img0[i] + k] = buf[(size_t)i * mk + k];
+    }
+    g.bar_E = std::move(E);
+    g.bar_epoch = g.state_epoch;
+    *out = &g.bar_E;
     return SS_OK;
 }
 
@@ -1365,7 +1438,17 @@ ss_status ss_barrier(ss_ctx* c, int string, double* dE, int* k_max) {
     TRY(check_string(c, string));
     const int K = c->strs[string].d.n_images;
     std::vector<double> e(K);
-    TRY(ss_energies(c, string, e.data()));
+    if (use_fp64(c)) {
+        TRY(ss_energies(c, string, e.data()));
+    } else {  // FP64 energies of the images that can decide the barrier (see barrier_energies)
+        StringRec& r = c->strs[string];
+        TRY(check_paths(c, c->groups[r.group]));
+        TRY(enter(c));
+        const std::vector<double>* be = nullptr;
+        TRY(barrier_energies(c, r.group, &be));
+        TRY(leave(c));
+        for (int k = 0; k < K; ++k) e[k] = (*be)[r.img0 + k];  // NaN: cannot be the highest image
+    }
     int kb = 0;
     for (int k = 1; k < K; ++k)
         if (e[k] > e[kb]) kb = k;

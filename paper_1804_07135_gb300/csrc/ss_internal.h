@@ -94,7 +94,11 @@ template <typename T> struct GroupArgs {
     const int* climb_img;  // [n_img] nonzero for the image that climbs this iteration (climbing mode only)
     T llg_a, llg_b;        // precessional dynamics (Eq. 9): 1 / (1 + alpha^2) and alpha / (1 + alpha^2)
     const T* hdir;         // [image][3][N] direct dipole sums (SS_DIPOLE_DIRECT), or null
+    const int* pair_on;    // [n_pairs] evaluate only the pairs flagged here (generic kernels), or null: all
 };
+// Energy partials per image of the evaluation mode: the four terms of Eq. 1 (J, D, K, w with the constant
+// set to 1) and the squared norm of the dipole convolution (for the FP32 round-off bound of the w term).
+constexpr int kEvalTerms = 5;
 
 // Arc-length / reparametrisation bookkeeping of one size group.
 struct ArcArgs {
@@ -185,7 +189,7 @@ inline int f128_x_rows(int ty) { return ty == 2 || ty == 4 ? ty : 8; }
 inline int f128_x_threads(int rows) { return 48 * rows; }
 inline size_t f128_x_smem(int rows) {
     // line buffer, exchange buffer (lines rounded up to a multiple of 4), reduction scratch
-    return (size_t)(3 * rows * kF128Buf + (3 * rows + 3) / 4 * 4 * kF128Line) * 8 + 32 * 8 * sizeof(double);
+    return (size_t)(3 * rows * kF128Buf + (3 * rows + 3) / 4 * 4 * kF128Line) * 8 + 32 * 2 * kEvalTerms * sizeof(double);
 }
 inline int f128_yz_threads(int nz) { return 48 * nz; }
 // The length-128 y/z kernel reads its tensor slab through L1 rather than staging it in shared memory
@@ -218,7 +222,7 @@ __host__ __device__ constexpr int x2_lsx(int P) { return x2_round(t2_line(P) - 1
 __host__ __device__ constexpr int x2_lb(int P) { return x2_round(fft_pad(P / 2 - 1) + 1); }  // x-space lines
 inline bool x2p_ok(int real_bytes, int Px) { return real_bytes == 4 && (Px == 192 || Px == 256 || Px == 384); }
 inline size_t x2_smem(int P, bool inverse) {
-    return (size_t)3 * kX2Rows * (x2_lsx(P) + x2_lb(P)) * 8 + (inverse ? 32 * 8 * 8 : 0);
+    return (size_t)3 * kX2Rows * (x2_lsx(P) + x2_lb(P)) * 8 + (inverse ? 32 * 2 * kEvalTerms * 8 : 0);
 }
 
 
@@ -248,7 +252,8 @@ void launch_rk_control(const GroupArgs<T>& g, const RkArgs<T>& r, int begin, cud
 template <typename T> void launch_rk_commit(const GroupArgs<T>& g, const RkArgs<T>& r, cudaStream_t st);
 template <typename T> void launch_arc(const GroupArgs<T>& g, const ArcArgs& a, int nthr, cudaStream_t st);
 template <typename T>
-void launch_eval_reduce(const GroupArgs<T>& g, const ArcArgs& a, double* terms, double* energies, cudaStream_t st);
+void launch_eval_reduce(const GroupArgs<T>& g, const ArcArgs& a, double* terms, double* energies, double* cnorm2,
+                        cudaStream_t st);
 template <typename T, typename Tin>
 void launch_aos_to_soa(const Tin* src, T* dst, int K, int N, int* err, cudaStream_t st);
 template <typename T, typename Tout>

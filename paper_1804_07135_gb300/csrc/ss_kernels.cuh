@@ -230,6 +230,7 @@ __global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xfwd_kernel(GroupAr
     const int p = blockIdx.z, z = blockIdx.y, y0 = blockIdx.x * g.ty_a;
     const int rows = min(g.ty_a, g.ny - y0);
     const int nx = g.nx;
+    if (g.pair_on && !g.pair_on[p]) return;  // uniform over the CTA
     if (DO_FFT)
         for (int i = tid; i < g.Px; i += nthr) tw[i] = PX > 0 ? g.twxs[i] : g.twx[i];
     griddep_wait();
@@ -502,6 +503,7 @@ __global__ void __launch_bounds__(kMaxThreadsYz, kMinBlocksYz) yz_kernel(GroupAr
     C* A = tw + g.Py;  // KXB*3*nz lines of stride lsy
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int kx = blockIdx.x * KXB, p = blockIdx.y;
+    if (g.pair_on && !g.pair_on[p]) return;  // uniform over the CTA
     const int Py = PY > 0 ? PY : g.Py;
     const int nz = NZ > 0 ? NZ : g.nz;
     const int ny = g.ny, L = 3 * nz * KXB;
@@ -870,7 +872,7 @@ __device__ __forceinline__ void xinv_sites(const GroupArgs<T>& g, T dt, T* hout,
     using C = cplx<T>;
     const int nx = g.nx, ny = g.ny, nz = g.nz, N = g.N;
     const int ia = 2 * p;
-    constexpr int NV = MODE == 1 ? 8 : 2;
+    constexpr int NV = MODE == 1 ? 2 * kEvalTerms : 2;
     double acc[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) acc[k] = 0.0;
@@ -988,10 +990,11 @@ __device__ __forceinline__ void xinv_sites(const GroupArgs<T>& g, T dt, T* hout,
             }
             const double tK = -si[2] * si[2];
             const double tw_ = -0.5 * ((double)conv[0] * si[0] + (double)conv[1] * si[1] + (double)conv[2] * si[2]);
-            acc[4 * h + 0] += tJ;
-            acc[4 * h + 1] += tD;
-            acc[4 * h + 2] += tK;
-            acc[4 * h + 3] += tw_;
+            acc[kEvalTerms * h + 0] += tJ;
+            acc[kEvalTerms * h + 1] += tD;
+            acc[kEvalTerms * h + 2] += tK;
+            acc[kEvalTerms * h + 3] += tw_;
+            acc[kEvalTerms * h + 4] += (double)conv[0] * conv[0] + (double)conv[1] * conv[1] + (double)conv[2] * conv[2];
             if (hout) {
                 T* o = hout + (size_t)im * 3 * N + site;
                 o[0] = hf[0];
@@ -1014,7 +1017,8 @@ __device__ __forceinline__ void xinv_sites(const GroupArgs<T>& g, T dt, T* hout,
             if (MODE != 1) {
                 g.epart[(size_t)blk * g.n_img + im] = acc[h];  // [block][image]
             } else {
-                for (int k = 0; k < 4; ++k) g.epart[((size_t)blk * g.n_img + im) * 4 + k] = acc[4 * h + k];
+                for (int k = 0; k < kEvalTerms; ++k)
+                    g.epart[((size_t)blk * g.n_img + im) * kEvalTerms + k] = acc[kEvalTerms * h + k];
             }
         }
     }
@@ -1041,6 +1045,7 @@ __global__ void __launch_bounds__(kMaxThreadsX, kMinBlocksX) xinv_kernel(GroupAr
     const int p = blockIdx.z, z = blockIdx.y, y0 = blockIdx.x * g.ty_c;
     const int rows = min(g.ty_c, g.ny - y0);
     const int ny = g.ny, nz = g.nz;
+    if (g.pair_on && !g.pair_on[p]) return;  // uniform over the CTA
     if (DO_FFT)
         for (int i = tid; i < g.Px; i += nthr) tw[i] = PX > 0 ? g.twxs[i] : g.twx[i];
     griddep_wait();
@@ -1120,7 +1125,7 @@ __global__ void __launch_bounds__(kMaxThreads128, kMinBlocks128) xinv128_kernel(
 // xfwd: the gather (Eq. 12) into x-space lines, pass 1 into the transform lines, pass 2 straight to the
 // spectrum spec[p][kx][c][z][y].
 template <int P>
-__global__ void __launch_bounds__(kX2Threads, P == 384 ? 2 : 3) xfwd2p_kernel(GroupArgs<float> g) {
+__global__ void __launch_bounds__(kX2Threads, 3) xfwd2p_kernel(GroupArgs<float> g) {
     using C = float2;
     constexpr int R2 = P / 16, H = R2 / 2, ROWS = kX2Rows, L = 3 * ROWS, LSX = x2_lsx(P), LB = x2_lb(P);
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1164,7 +1169,7 @@ __global__ void __launch_bounds__(kX2Threads, P == 384 ? 2 : 3) xfwd2p_kernel(Gr
 // xinv: pass A straight from the spectrum (conjugated) into the transform lines, pass B into x-space
 // lines (fft_pad positions, line c * rows + yy), then the per-site work of xinv_sites in mode MODE.
 template <int P, int MODE>
-__global__ void __launch_bounds__(kX2Threads, P == 384 ? 2 : 3) xinv2p_kernel(GroupArgs<float> g, float dt, float* hout) {
+__global__ void __launch_bounds__(kX2Threads, 3) xinv2p_kernel(GroupArgs<float> g, float dt, float* hout) {
     using C = float2;
     constexpr int R2 = P / 16, H = R2 / 2, ROWS = kX2Rows, L = 3 * ROWS, LSX = x2_lsx(P), LB = x2_lb(P);
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -2030,21 +2035,25 @@ __global__ void __launch_bounds__(256) spline_apply_kernel(GroupArgs<T> g, ArcAr
     }
 }
 
-// eval reduce: grid (n_str), thread per image: terms[str][k][4] and energies[str][k] in FP64.
+// eval reduce: grid (n_str), thread per image: terms[str][k][4], energies[str][k] and (when cnorm2 is
+// given) the squared norm of the dipole convolution cnorm2[str][k], in FP64.  Images of pairs that
+// g.pair_on leaves out are skipped (their partials were not written).
 template <typename T>
-__global__ void eval_reduce_kernel(GroupArgs<T> g, ArcArgs a, double* terms, double* energies) {
+__global__ void eval_reduce_kernel(GroupArgs<T> g, ArcArgs a, double* terms, double* energies, double* cnorm2) {
     const int str = blockIdx.x;
     const int K = a.str_K[str], img0 = a.str_img0[str];
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         const int im = img0 + k;
-        double t[4];
-        for (int q = 0; q < 4; ++q) {
+        if (g.pair_on && !g.pair_on[im >> 1]) continue;
+        double t[kEvalTerms];
+        for (int q = 0; q < kEvalTerms; ++q) {
             double v = 0.0;
-            const double* ep = g.epart + (size_t)im * 4 + q;
-            for (int b = 0; b < g.n_eblk; ++b) v += ep[(size_t)b * g.n_img * 4];
+            const double* ep = g.epart + (size_t)im * kEvalTerms + q;
+            for (int b = 0; b < g.n_eblk; ++b) v += ep[(size_t)b * g.n_img * kEvalTerms];
             t[q] = v;
-            terms[((size_t)str * a.maxK + k) * 4 + q] = v;
+            if (q < 4) terms[((size_t)str * a.maxK + k) * 4 + q] = v;
         }
+        if (cnorm2) cnorm2[(size_t)str * a.maxK + k] = t[4];
         const ImgParam<T> pr = g.prm[im];
         const double e = (double)pr.J * t[0] + (double)pr.D * t[1] + (double)pr.K * t[2] + (double)pr.w * t[3];
         energies[(size_t)str * a.maxK + k] = e;
@@ -2504,8 +2513,9 @@ template <typename T> void launch_arc(const GroupArgs<T>& g, const ArcArgs& a, i
 }
 
 template <typename T>
-void launch_eval_reduce(const GroupArgs<T>& g, const ArcArgs& a, double* terms, double* energies, cudaStream_t st) {
-    eval_reduce_kernel<T><<<a.n_str, 128, 0, st>>>(g, a, terms, energies);
+void launch_eval_reduce(const GroupArgs<T>& g, const ArcArgs& a, double* terms, double* energies, double* cnorm2,
+                        cudaStream_t st) {
+    eval_reduce_kernel<T><<<a.n_str, 128, 0, st>>>(g, a, terms, energies, cnorm2);
 }
 
 template <typename T, typename Tin>
@@ -2633,7 +2643,7 @@ void launch_widen_unit(const float* src, double* dst, int K, int N, cudaStream_t
     template void launch_rk_control<T>(const GroupArgs<T>&, const RkArgs<T>&, int, cudaStream_t);                \
     template void launch_rk_commit<T>(const GroupArgs<T>&, const RkArgs<T>&, cudaStream_t);                    \
     template void launch_arc<T>(const GroupArgs<T>&, const ArcArgs&, int, cudaStream_t);                       \
-    template void launch_eval_reduce<T>(const GroupArgs<T>&, const ArcArgs&, double*, double*, cudaStream_t);  \
+    template void launch_eval_reduce<T>(const GroupArgs<T>&, const ArcArgs&, double*, double*, double*, cudaStream_t); \
     template void launch_aos_to_soa<T, float>(const float*, T*, int, int, int*, cudaStream_t);                 \
     template void launch_aos_to_soa<T, double>(const double*, T*, int, int, int*, cudaStream_t);               \
     template void launch_soa_to_aos<T, float>(const T*, float*, int, int, float, cudaStream_t);                \

@@ -195,7 +195,7 @@ extern "C" ss_status ss_field_noalloc(int nx, int ny, int nz, double J, double D
     if (dip && f128_x(4, Px)) ty = f128_x_rows(ty);  // the length-128 x kernels take 2, 4 or 8 rows
     if (dip && x2p_ok(4, Px)) ty = kX2Rows;          // the lengths-192/256/384 x kernels take kX2Rows
     const size_t smem_a = (size_t)(Px + 3 * ty * lsx) * sizeof(float2);
-    const size_t smem_c = smem_a + 32 * 8 * sizeof(double);
+    const size_t smem_c = smem_a + 32 * 2 * kEvalTerms * sizeof(double);
     size_t smem_b = (size_t)(Py + 3 * nz * lsy) * sizeof(float2);
     const size_t slab = (size_t)(Py / 2 + 1) * nz * 6 * sizeof(float);
     if (slab <= 24 * 1024) smem_b += slab;
@@ -216,7 +216,7 @@ extern "C" ss_status ss_field_noalloc(int nx, int ny, int nz, double J, double D
     const size_t o_dhat = take(dip ? (size_t)(Px / 2 + 1) * (Py / 2 + 1) * nz * 6 * sizeof(float) : 0);
     const size_t o_prm = take(n_images * sizeof(ImgParam<float>));
     const size_t o_interp = take(n_images * sizeof(InterpEntry));
-    const size_t o_epart = take((size_t)n_images * 4 * n_eblk * sizeof(double));
+    const size_t o_epart = take((size_t)n_images * kEvalTerms * n_eblk * sizeof(double));
     const size_t o_work = off;
     const size_t tensor_bytes = dip ? (size_t)6 * nz * Px * Py * sizeof(double2) : 0;
     const size_t o_s = o_work;

@@ -479,3 +479,21 @@ def test_direct_dipole_trajectory_matches_fft_and_oracle(ss):
     assert np.abs(out[ss.SS_DIPOLE_DIRECT][0] - ref).max() < 1e-10
     assert np.abs(out[ss.SS_DIPOLE_DIRECT][0] - out[ss.SS_DIPOLE_FFT][0]).max() < 1e-10
     assert abs(out[ss.SS_DIPOLE_DIRECT][1][0] - oracle.barrier(e_ref)[0]) < 1e-9
+
+
+@pytest.mark.parametrize("n_iter", [0, 7, 40])
+def test_barrier_from_selected_images_equals_full_fp64(ss, n_iter):
+    # ss_barrier on an FP32 context evaluates in FP64 only the images whose FP32 energy bound can reach
+    # the maximum; the result must equal the barrier over every image's FP64 energy (ss_energies) exactly
+    cases = [(16, 16, 1, 1.0, 0.3, 0.05, 0.01, 16), (16, 16, 1, 1.0, 0.2, 0.1, 0.02, 9),
+             (12, 10, 3, 1.0, 0.25, 0.1, 0.05, 6), (20, 21, 2, 1.0, 0.3, 0.0, 0.0, 5)]
+    paths = [W.bloch_point_path(c[0], c[1], c[2], c[7], R=3.5, D=c[4]) for c in cases]
+    with _sm(ss, cases) as sm:
+        for i, p in enumerate(paths):
+            sm.set_path(i, p)
+        sm.step(n_iter)
+        bars = [sm.barrier(i) for i in range(len(cases))]
+        full = [sm.energies(i) for i in range(len(cases))]
+    for (dE, k), e in zip(bars, full):
+        kf = int(np.argmax(e))
+        assert k == kf and dE == e[kf] - e[0]
