@@ -108,6 +108,7 @@ struct Group {
     FftPlan planx{}, plany{};
     int lsx = 1, lsy = 1;
     int ty_a = 1, ty_c = 1, thr_a = 128, thr_b = 128, thr_c = 128, thr_arc = 256;
+    int yz_kxb = 0;  // kx columns per CTA of the two-pass y/z kernel (0: default; autotuned)
     size_t smem_a = 0, smem_b = 0, smem_c = 0, smem_c_eval = 0;
     int n_eblk = 0;
     // device
@@ -272,6 +273,7 @@ template <typename T> GroupArgs<T> group_args(const ss_ctx* c, const Group& g) {
     a.n_eblk = g.n_eblk;
     a.ty_a = g.ty_a;
     a.ty_c = g.ty_c;
+    a.yz_kxb = g.yz_kxb;
     a.err = c->d_err;
     a.climb_img = g.climb_img;
     a.hdir = (const T*)g.hdir;
@@ -342,8 +344,13 @@ void configure_group(Group& g) {
     }
     if (g.dipole && yz2p_ok(g.rbytes, g.Py, g.nz, g.Px)) {
         g.thr_b = kYz2Threads;
-        g.smem_b = yz2p_smem(g.Py, g.nz);
+        g.smem_b = yz2p_smem(g.Py, g.nz, yz2p_kxb_use(g.nz, g.yz_kxb));
     }
+}
+
+// The two-pass y/z kernel's shared memory for the group's column count (after the autotuner's choice).
+void configure_yz_smem(Group& g) {
+    if (g.dipole && yz2p_ok(g.rbytes, g.Py, g.nz, g.Px)) g.smem_b = yz2p_smem(g.Py, g.nz, yz2p_kxb_use(g.nz, g.yz_kxb));
 }
 
 template <typename T> ss_status build_tensor_spectrum(ss_ctx* c, Group& g) {
@@ -475,16 +482,18 @@ template <typename T> ss_status setup_group(ss_ctx* c, Group& g) {
     return SS_OK;
 }
 
-// Autotuner: rows per CTA of the x kernels, timed with CUDA events on the context's stream (the
-// kernels are data-independent; the buffers hold zeros and are cleared again afterwards).  Choices
-// are cached per (lattice, precision, device) for the life of the process.
+// Autotuner: rows per CTA and block size of the x kernels and kx columns per CTA of the two-pass y/z
+// kernel, timed with CUDA events on the context's stream (the kernels are data-independent; the buffers
+// hold zeros and are cleared again afterwards).  Choices are cached per (lattice, image pairs, precision,
+// device) for the life of the process.
 struct TuneKey {
-    int nx, ny, nz, prec, dev, dipole;
+    int nx, ny, nz, prec, dev, dipole, pairs;  // the best shape also depends on how many CTAs a launch has
     bool operator==(const TuneKey& o) const {
-        return nx == o.nx && ny == o.ny && nz == o.nz && prec == o.prec && dev == o.dev && dipole == o.dipole;
+        return nx == o.nx && ny == o.ny && nz == o.nz && prec == o.prec && dev == o.dev && dipole == o.dipole &&
+               pairs == o.pairs;
     }
 };
-std::vector<std::pair<TuneKey, std::array<int, 4>>> g_tuned;  // (thr_a, ty_a, thr_c, ty_c)
+std::vector<std::pair<TuneKey, std::array<int, 5>>> g_tuned;  // (thr_a, ty_a, thr_c, ty_c, yz_kxb)
 std::mutex g_tune_mu;
 
 template <typename T> ss_status tune_group(ss_ctx* c, Group& g) {
@@ -499,13 +508,15 @@ template <typename T> ss_status tune_group(ss_ctx* c, Group& g) {
             return SS_OK;
         }
     }
-    const TuneKey key{g.nx, g.ny, g.nz, c->opts.precision, c->device, g.dipole ? 1 : 0};
+    const TuneKey key{g.nx, g.ny, g.nz, c->opts.precision, c->device, g.dipole ? 1 : 0, g.n_pairs};
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         for (auto& e : g_tuned)
             if (e.first == key) {
                 const int* v = e.second.data();
+                g.yz_kxb = v[4];
                 set_rows(g, v[1], v[3], v[0], v[2]);
+                configure_yz_smem(g);
                 return SS_OK;
             }
     }
@@ -523,51 +534,80 @@ template <typename T> ss_status tune_group(ss_ctx* c, Group& g) {
                     fft_lines_per_pass(thr, g.Px) >= 1 && 3 * ty <= 2 * fft_lines_per_pass(thr, g.Px))
                     cands.push_back({thr, ty});
     }
-    if (cands.size() <= 1) return SS_OK;
+    std::vector<int> kxbs;  // y/z columns per CTA
+    if (g.dipole && yz2p_ok((int)real_size(c), g.Py, g.nz, g.Px) && yz2p_kxb_alt(g.nz) > 0 &&
+        g.Px % yz2p_kxb_alt(g.nz) == 0)
+        kxbs = {yz2p_kxb(g.nz), yz2p_kxb_alt(g.nz)};
+    if (cands.size() <= 1 && kxbs.size() <= 1) return SS_OK;
     cudaEvent_t e0, e1;
     CUDA_TRY(c, cudaEventCreate(&e0));
     CUDA_TRY(c, cudaEventCreate(&e1));
     const int reps = 6, trials = 3;
+    auto time_it = [&](auto&& run, float* out) -> ss_status {
+        run();
+        float ms_best = 1e30f;
+        for (int tr = 0; tr < trials; ++tr) {
+            CUDA_TRY(c, cudaEventRecord(e0, c->cs));
+            for (int r = 0; r < reps; ++r) run();
+            CUDA_TRY(c, cudaEventRecord(e1, c->cs));
+            CUDA_TRY(c, cudaEventSynchronize(e1));
+            CUDA_TRY(c, cudaGetLastError());
+            float ms = 0.f;
+            CUDA_TRY(c, cudaEventElapsedTime(&ms, e0, e1));
+            ms_best = std::min(ms_best, ms);
+        }
+        *out = ms_best;
+        return SS_OK;
+    };
     float best[2] = {1e30f, 1e30f};
     std::pair<int, int> pick[2] = {{g.thr_a, g.ty_a}, {g.thr_c, g.ty_c}};
     const T dt = T(c->opts.dt);
-    for (auto [thr, ty] : cands) {
-        set_rows(g, ty, ty, thr, thr);
-        GroupArgs<T> a = group_args<T>(c, g);
-        for (int which = 0; which < 2; ++which) {
-            auto run = [&]() {
-                if (which == 0)
-                    launch_xfwd<T>(a, g.dipole, g.thr_a, g.smem_a, c->cs);
-                else
-                    launch_xinv_step<T>(a, g.dipole, dt, g.thr_c, g.smem_c, c->cs);
-            };
-            run();
-            float ms_best = 1e30f;
-            for (int tr = 0; tr < trials; ++tr) {
-                CUDA_TRY(c, cudaEventRecord(e0, c->cs));
-                for (int r = 0; r < reps; ++r) run();
-                CUDA_TRY(c, cudaEventRecord(e1, c->cs));
-                CUDA_TRY(c, cudaEventSynchronize(e1));
-                CUDA_TRY(c, cudaGetLastError());
+    if (cands.size() > 1) {
+        for (auto [thr, ty] : cands) {
+            set_rows(g, ty, ty, thr, thr);
+            GroupArgs<T> a = group_args<T>(c, g);
+            for (int which = 0; which < 2; ++which) {
                 float ms = 0.f;
-                CUDA_TRY(c, cudaEventElapsedTime(&ms, e0, e1));
-                ms_best = std::min(ms_best, ms);
-            }
-            if (ms_best < best[which]) {
-                best[which] = ms_best;
-                pick[which] = {thr, ty};
+                TRY(time_it([&]() {
+                    if (which == 0)
+                        launch_xfwd<T>(a, g.dipole, g.thr_a, g.smem_a, c->cs);
+                    else
+                        launch_xinv_step<T>(a, g.dipole, dt, g.thr_c, g.smem_c, c->cs);
+                }, &ms));
+                if (ms < best[which]) {
+                    best[which] = ms;
+                    pick[which] = {thr, ty};
+                }
             }
         }
+        set_rows(g, pick[0].second, pick[1].second, pick[0].first, pick[1].first);
+    }
+    if (kxbs.size() > 1) {
+        float best_b = 1e30f;
+        int pick_b = kxbs[0];
+        for (int kxb : kxbs) {
+            g.yz_kxb = kxb;
+            GroupArgs<T> a = group_args<T>(c, g);
+            float ms = 0.f;
+            TRY(time_it([&]() { launch_yz<T>(a, g.thr_b, g.smem_b, c->cs); }, &ms));
+            if (ms < best_b) {
+                best_b = ms;
+                pick_b = kxb;
+            }
+        }
+        g.yz_kxb = pick_b;
+        configure_yz_smem(g);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    set_rows(g, pick[0].second, pick[1].second, pick[0].first, pick[1].first);
     const size_t M = (size_t)3 * g.N * g.n_img * real_size(c);
     CUDA_TRY(c, cudaMemsetAsync(g.s, 0, M, c->cs));
     CUDA_TRY(c, cudaMemsetAsync(g.sp, 0, M, c->cs));
+    if (g.spec)
+        CUDA_TRY(c, cudaMemsetAsync(g.spec, 0, (size_t)g.n_pairs * g.Px * 3 * g.nz * g.ny * 2 * real_size(c), c->cs));
     CUDA_TRY(c, cudaStreamSynchronize(c->cs));
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tuned.push_back({key, {pick[0].first, pick[0].second, pick[1].first, pick[1].second}});
+    g_tuned.push_back({key, {g.thr_a, g.ty_a, g.thr_c, g.ty_c, g.yz_kxb}});
     return SS_OK;
 }
 

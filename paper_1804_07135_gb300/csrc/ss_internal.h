@@ -95,6 +95,7 @@ template <typename T> struct GroupArgs {
     T llg_a, llg_b;        // precessional dynamics (Eq. 9): 1 / (1 + alpha^2) and alpha / (1 + alpha^2)
     const T* hdir;         // [image][3][N] direct dipole sums (SS_DIPOLE_DIRECT), or null
     const int* pair_on;    // [n_pairs] evaluate only the pairs flagged here (generic kernels), or null: all
+    int yz_kxb;            // kx columns per CTA of the two-pass y/z kernel (autotuned; 0: the default)
 };
 // Energy partials per image of the evaluation mode: the four terms of Eq. 1 (J, D, K, w with the constant
 // set to 1) and the squared norm of the dipole convolution (for the FP32 round-off bound of the w term).
@@ -208,13 +209,18 @@ inline size_t f128_yz_smem(int nz, int Py, bool* stage_dhat) {
 constexpr int kT2Row = 17;
 __host__ __device__ constexpr int t2_line(int P) { return kT2Row * (P / 16); }
 constexpr int kYz2Threads = 384;
+// kx columns per CTA: the default (24 lines) and the alternative the autotuner also times (12 lines for
+// one or four layers); 0 when nz has no two-pass kernel
 inline int yz2p_kxb(int nz) { return nz == 1 ? 8 : nz == 4 ? 2 : nz == 8 ? 1 : 0; }
+inline int yz2p_kxb_alt(int nz) { return nz == 1 ? 4 : nz == 4 ? 1 : 0; }
 inline bool yz2p_ok(int real_bytes, int Py, int nz, int Px) {
     if (real_bytes != 4 || !(Py == 192 || Py == 256 || Py == 384)) return false;
     const int kxb = yz2p_kxb(nz);
     return kxb > 0 && Px % kxb == 0;
 }
-inline size_t yz2p_smem(int Py, int nz) { return (size_t)3 * nz * yz2p_kxb(nz) * t2_line(Py) * 8; }
+// columns per CTA a launch uses: the tuned choice when it is one of the two, else the default
+inline int yz2p_kxb_use(int nz, int tuned) { return tuned > 0 && (tuned == yz2p_kxb(nz) || tuned == yz2p_kxb_alt(nz)) ? tuned : yz2p_kxb(nz); }
+inline size_t yz2p_smem(int Py, int nz, int kxb) { return (size_t)3 * nz * kxb * t2_line(Py) * 8; }
 constexpr int kX2Rows = 4;
 constexpr int kX2Threads = 384;
 __host__ __device__ constexpr int x2_round(int v) { return v + ((16 / kX2Rows - v % 16) + 16) % 16; }

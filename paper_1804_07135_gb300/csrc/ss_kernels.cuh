@@ -2274,15 +2274,18 @@ template <typename T> void launch_yz(const GroupArgs<T>& g, int nthr, size_t sme
     const size_t base = (size_t)(g.Py + 3 * g.nz * g.lsy) * sizeof(cplx<T>);
     const int stage = smem >= base + (size_t)(g.Py / 2 + 1) * g.nz * 6 * sizeof(T);
     if constexpr (std::is_same<T, float>::value) {
-        if (yz2p_ok(4, g.Py, g.nz, g.Px)) {
-            const size_t sm = yz2p_smem(g.Py, g.nz);
-            const dim3 blk(kYz2Threads);
-#define SS_CASE(P)                                                                                          \
-    if (g.Py == P) {                                                                                        \
-        if (g.nz == 1) launch_pdl(yz2p_kernel<P, 1, 8>, dim3(g.Px / 8, g.n_pairs), blk, sm, st, g);            \
-        else if (g.nz == 4) launch_pdl(yz2p_kernel<P, 4, 2>, dim3(g.Px / 2, g.n_pairs), blk, sm, st, g);       \
-        else launch_pdl(yz2p_kernel<P, 8, 1>, dim3(g.Px, g.n_pairs), blk, sm, st, g);                          \
-        return;                                                                                             \
+        if (yz2p_ok(4, g.Py, g.nz, g.Px) && g.Px % yz2p_kxb_use(g.nz, g.yz_kxb) == 0) {
+            const int kxb = yz2p_kxb_use(g.nz, g.yz_kxb);
+            const size_t sm = yz2p_smem(g.Py, g.nz, kxb);
+            const dim3 blk(kYz2Threads), gr(g.Px / kxb, g.n_pairs);
+#define SS_CASE(P)                                                                         \
+    if (g.Py == P) {                                                                       \
+        if (g.nz == 1 && kxb == 8) launch_pdl(yz2p_kernel<P, 1, 8>, gr, blk, sm, st, g);      \
+        else if (g.nz == 1) launch_pdl(yz2p_kernel<P, 1, 4>, gr, blk, sm, st, g);             \
+        else if (g.nz == 4 && kxb == 2) launch_pdl(yz2p_kernel<P, 4, 2>, gr, blk, sm, st, g); \
+        else if (g.nz == 4) launch_pdl(yz2p_kernel<P, 4, 1>, gr, blk, sm, st, g);             \
+        else launch_pdl(yz2p_kernel<P, 8, 1>, gr, blk, sm, st, g);                            \
+        return;                                                                            \
     }
             SS_CASE(192) SS_CASE(256) SS_CASE(384)
 #undef SS_CASE
@@ -2579,6 +2582,8 @@ template <typename T> void set_smem_limits(int bytes) {
     set_dyn_smem(xinv2p_kernel<P, 3>, bytes);      \
     set_dyn_smem(xinv2p_kernel<P, 4>, bytes);      \
     set_dyn_smem(xinv2p_kernel<P, 5>, bytes);      \
+    set_dyn_smem(yz2p_kernel<P, 1, 4>, bytes);     \
+    set_dyn_smem(yz2p_kernel<P, 4, 1>, bytes);     \
     set_dyn_smem(yz2p_kernel<P, 1, 8>, bytes);     \
     set_dyn_smem(yz2p_kernel<P, 4, 2>, bytes);     \
     set_dyn_smem(yz2p_kernel<P, 8, 1>, bytes);
