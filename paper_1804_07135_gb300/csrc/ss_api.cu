@@ -1000,8 +1000,8 @@ ss_status barrier_energies(ss_ctx* c, int gi, const std::vector<double>** out) {
             };
             double lo_max = -INFINITY;
             for (int k = 0; k < K; ++k) lo_max = std::max(lo_max, buf[(size_t)i * mk + k] - bound(k));
-            for (int k = 0; k < K; ++k)
-                if (k == 0 || !(buf[(size_t)i * mk + k] + bound(k) < lo_max)) on[(img0 + k) >> 1] = 1;
+            for (int k = 0; k < K; ++k)  // the direct dipole sum has no such bound here: every image then
+                if (k == 0 || g.direct || !(buf[(size_t)i * mk + k] + bound(k) < lo_max)) on[(img0 + k) >> 1] = 1;
         }
         CUDA_TRY(c, cudaMemcpyAsync(e.pair_on, on.data(), on.size() * sizeof(int), cudaMemcpyHostToDevice, c->cs));
         launch_widen_unit((const float*)g.s, (double*)e.sp, g.n_img, g.N, c->cs);

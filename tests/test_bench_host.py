@@ -51,3 +51,19 @@ def test_variants_map_to_library_modes():
         assert interp in ("linear", "spline") and integ in ("euler", "dopri5", "dopri5_image")
         assert dyn in ("string", "llg") and not (climb and integ != "euler")
     assert binding.SS_INT_DOPRI5 == 1 and binding.SS_INTERP_SPLINE == 1 and binding.SS_DYN_LLG == 1
+
+
+def test_group_flop_count_matches_the_string_count():
+    # a single-string group gives the per-string count; pairs are formed over the group's images
+    spec = workloads.bloch_collapse().strings[0]
+    assert bench.yz_flops_group(spec.nx, spec.ny, spec.nz, spec.n_images) == bench.yz_flops(spec)
+    assert bench.yz_flops_group(64, 64, 8, 33) == 17 * bench.yz_flops_group(64, 64, 8, 2)
+
+
+def test_headline_is_the_largest_workload():
+    wl = bench.headline_workload()
+    assert wl.name == "uneven-study-20x32" and len(wl.strings) == 20
+    assert wl.spin_updates_per_iter > workloads.boundary_sweep().spin_updates_per_iter
+    keys, imgs = bench.group_keys(wl)
+    assert len(keys) == 4 and sum(imgs.values()) == 640
+    assert bench.oracle_sample_spec().nx == 64
