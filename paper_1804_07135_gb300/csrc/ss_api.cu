@@ -961,10 +961,10 @@ ss_status evaluate_energies(ss_ctx* c, int gi, const Group** out) {
 
 // FP32 contexts: the FP64 energies of the images that can decide a barrier (Sec. III: max_k E_k - E_0) of
 // every string of size group gi, for the group's current state, into *out ([image], NaN for the others).
-// The FP32 evaluation gives each image's energy E_k with a round-off bound B_k: the local terms are FP64
-// sums over the spins renormalised in FP64, and the dipole term's FFT round-off obeys
-// ||d conv||_2 <= eps ||conv||_2, eps = u (2 log2(Px Py) + 3 nz + 4), so |dE_k| <= w (1/2) eps ||conv_k||_2
-// sqrt(N), plus 1e-9 + 1e-13 |E_k| for the FP64 sums.  An image whose upper bound E_k + B_k lies below the
+// The FP32 evaluation gives each image's energy E_k with a round-off bound B_k: its local terms are FP32
+// per site and summed in FP32 per thread and warp (bounded below), and the dipole term's FFT round-off
+// obeys ||d conv||_2 <= eps ||conv||_2, eps = u (2 log2(Px Py) + 3 nz + 4), so |dE_k| <= w (1/2) eps
+// ||conv_k||_2 sqrt(N), plus 1e-9 + 1e-13 |E_k| for the FP64 sums.  An image whose upper bound E_k + B_k lies below the
 // largest lower bound max_j (E_j - B_j) of its string cannot be the highest one, so only image 0 and the
 // remaining images are evaluated in FP64 -- the pairs holding them, on the FP64 evaluation copy.
 ss_status barrier_energies(ss_ctx* c, int gi, const std::vector<double>** out) {
@@ -993,10 +993,16 @@ ss_status barrier_energies(ss_ctx* c, int gi, const std::vector<double>** out) {
             const ss_string_desc& d = c->strs[g.strs[i]].d;
             const double w = g.dipole ? std::fabs(d.w) : 0.0;
             const int K = g.str_K[i], img0 = g.str_img0[i];
+            // the local terms: computed per site in FP32 from spins renormalised in FP32 (relative error
+            // below 20 u per term), summed per thread over at most m sites in FP32 and over a warp by a
+            // five-level FP32 tree, then in FP64; |term_i| <= 3 |J| + 2 |D| + |K| per site
+            const double m = std::ceil(2.0 * g.ty_c * g.nx / std::max(1, g.thr_c));
+            const double u = std::ldexp(1.0, -24);
+            const double local = (25.0 + m) * u * (double)g.N * (3.0 * std::fabs(d.J) + 2.0 * std::fabs(d.D) + std::fabs(d.K));
             auto bound = [&](int k) {
                 const size_t q = (size_t)i * mk + k;
-                return w * 0.5 * eps * std::sqrt(std::max(cn[q], 0.0)) * std::sqrt((double)g.N) + 1e-9 +
-                       1e-13 * std::fabs(buf[q]);
+                return w * 0.5 * eps * std::sqrt(std::max(cn[q], 0.0)) * std::sqrt((double)g.N) * (1.0 + (25.0 + m) * u) +
+                       local + 1e-9 + 1e-13 * std::fabs(buf[q]);
             };
             double lo_max = -INFINITY;
             for (int k = 0; k < K; ++k) lo_max = std::max(lo_max, buf[(size_t)i * mk + k] - bound(k));

@@ -877,6 +877,7 @@ __device__ __forceinline__ void xinv_sites(const GroupArgs<T>& g, T dt, T* hout,
 #pragma unroll
     for (int k = 0; k < NV; ++k) acc[k] = 0.0;
     T eacc[2] = {T(0), T(0)};  // step mode: the thread's few per-site terms, summed in T before FP64
+    float facc[MODE == 1 ? NV : 1] = {};  // FP32 evaluation mode: the same for its terms
     bool done = false;
     int climbs[2] = {0, 0};  // MODE 3: which of the pair's images climbs (uniform per image)
     if constexpr (MODE == 3) {
@@ -963,17 +964,27 @@ __device__ __forceinline__ void xinv_sites(const GroupArgs<T>& g, T dt, T* hout,
                 for (int c = 0; c < 3; ++c) o[(size_t)c * N] = f[c];
             }
         } else {
-            auto nrm = [](const T* v, double* o) {
-                const double a = v[0], b = v[1], c = v[2];
-                const double n2 = a * a + b * b + c * c;
-                const double r = n2 > 0.0 ? rsqrt_nr(n2) : 0.0;
+            // Eq. 1's terms with their constants set to 1, of the spins renormalised per site, bonds to +x,
+            // +y, +z counted once, and the squared norm of the dipole convolution.  In the path's
+            // precision R: the FP64 path sums FP64 terms; the FP32 path's evaluation (its energies only
+            // select the images the FP64 evaluation computes, and bound their own round-off) keeps the
+            // terms in FP32 and sums them per thread in FP32 and across warps in FP64
+            using R = T;
+            auto nrm = [](const T* v, R* o) {
+                const R a = v[0], b = v[1], c = v[2];
+                const R n2 = a * a + b * b + c * c;
+                R r = R(0);
+                if constexpr (std::is_same<T, float>::value)
+                    r = n2 > 0.f ? rsqrtf(n2) : 0.f;
+                else
+                    r = n2 > 0.0 ? rsqrt_nr(n2) : 0.0;
                 o[0] = a * r;
                 o[1] = b * r;
                 o[2] = c * r;
             };
-            double si[3], sx[3], sy[3], sz[3];
+            R si[3], sx[3], sy[3], sz[3];
             nrm(s0, si);
-            double tJ = 0.0, tD = 0.0;
+            R tJ = R(0), tD = R(0);
             if (x + 1 < nx) {
                 nrm(xp, sx);
                 tJ -= si[0] * sx[0] + si[1] * sx[1] + si[2] * sx[2];
@@ -988,13 +999,22 @@ __device__ __forceinline__ void xinv_sites(const GroupArgs<T>& g, T dt, T* hout,
                 nrm(zp, sz);
                 tJ -= si[0] * sz[0] + si[1] * sz[1] + si[2] * sz[2];
             }
-            const double tK = -si[2] * si[2];
-            const double tw_ = -0.5 * ((double)conv[0] * si[0] + (double)conv[1] * si[1] + (double)conv[2] * si[2]);
-            acc[kEvalTerms * h + 0] += tJ;
-            acc[kEvalTerms * h + 1] += tD;
-            acc[kEvalTerms * h + 2] += tK;
-            acc[kEvalTerms * h + 3] += tw_;
-            acc[kEvalTerms * h + 4] += (double)conv[0] * conv[0] + (double)conv[1] * conv[1] + (double)conv[2] * conv[2];
+            const R tK = -si[2] * si[2];
+            const R tw_ = R(-0.5) * (conv[0] * si[0] + conv[1] * si[1] + conv[2] * si[2]);
+            const R cn = conv[0] * conv[0] + conv[1] * conv[1] + conv[2] * conv[2];
+            if constexpr (std::is_same<T, float>::value) {
+                facc[kEvalTerms * h + 0] += tJ;
+                facc[kEvalTerms * h + 1] += tD;
+                facc[kEvalTerms * h + 2] += tK;
+                facc[kEvalTerms * h + 3] += tw_;
+                facc[kEvalTerms * h + 4] += cn;
+            } else {
+                acc[kEvalTerms * h + 0] += tJ;
+                acc[kEvalTerms * h + 1] += tD;
+                acc[kEvalTerms * h + 2] += tK;
+                acc[kEvalTerms * h + 3] += tw_;
+                acc[kEvalTerms * h + 4] += cn;
+            }
             if (hout) {
                 T* o = hout + (size_t)im * 3 * N + site;
                 o[0] = hf[0];
@@ -1007,6 +1027,8 @@ __device__ __forceinline__ void xinv_sites(const GroupArgs<T>& g, T dt, T* hout,
         if (dt == T(0)) return;  // uniform over the grid: no energy partials wanted
     if constexpr (MODE != 1)
         block_reduce_t2d<2>(eacc, acc, red);
+    else if constexpr (std::is_same<T, float>::value)
+        block_reduce_t2d<NV>(facc, acc, red);
     else
         block_reduce_d<NV>(acc, red);
     if (tid == 0) {
