@@ -497,14 +497,17 @@ std::vector<std::pair<TuneKey, std::array<int, 5>>> g_tuned;  // (thr_a, ty_a, t
 std::mutex g_tune_mu;
 
 template <typename T> ss_status tune_group(ss_ctx* c, Group& g) {
-    // SS_X_CONFIG="thr_a:ty_a:thr_c:ty_c" pins the x-kernel shapes (e.g. to profile the tuned ones)
+    // SS_X_CONFIG="thr_a:ty_a:thr_c:ty_c[:kxb]" pins the x-kernel shapes and, optionally, the two-pass y/z
+    // kernel's columns per CTA (e.g. to profile the tuned shapes, or to compare both column counts)
     if (const char* env = getenv("SS_X_CONFIG")) {
-        int ta = 0, ya = 0, tc = 0, yc = 0;
+        int ta = 0, ya = 0, tc = 0, yc = 0, kxb = 0;
         const bool f128 = g.dipole && f128_x((int)real_size(c), g.Px);  // block size follows the rows
-        if (sscanf(env, "%d:%d:%d:%d", &ta, &ya, &tc, &yc) == 4 &&
-            (f128 || ((ta == 256 || ta == 512) && (tc == 256 || tc == 512))) && ya >= 1 && yc >= 1 && ya <= g.ny &&
-            yc <= g.ny) {  // the x kernels for Px = 128 take 2, 4 or 8 rows (others become 8)
+        const int n = sscanf(env, "%d:%d:%d:%d:%d", &ta, &ya, &tc, &yc, &kxb);
+        if (n >= 4 && (f128 || ((ta == 256 || ta == 512) && (tc == 256 || tc == 512))) && ya >= 1 && yc >= 1 &&
+            ya <= g.ny && yc <= g.ny) {  // the x kernels for Px = 128 take 2, 4 or 8 rows (others become 8)
+            g.yz_kxb = n == 5 ? kxb : 0;  // a count the kernel does not take falls back to the default
             set_rows(g, ya, yc, ta, tc);
+            configure_yz_smem(g);
             return SS_OK;
         }
     }

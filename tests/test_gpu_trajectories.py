@@ -155,3 +155,23 @@ def test_uneven_batch_through_every_kernel_family(ss):
     assert {128, 192, 256, 384} <= seen
     for c, s0, g, e, b in zip(FAMILY_CASES, starts, got, es, bs):
         _check(c, s0, g, e, b, 3, FP32)
+
+
+@pytest.mark.parametrize("case", [(30, 120, 1, 1.0, 0.3, 0.05, 0.05, 5),   # Py = 256, nz = 1: 8 or 4 columns
+                                  (20, 90, 4, 1.0, 0.3, 0.05, 0.05, 4)])   # Py = 192, nz = 4: 2 or 1 column
+def test_yz_columns_per_cta_do_not_change_the_field(ss, case, monkeypatch):
+    # the autotuner picks the two-pass y/z kernel's kx columns per CTA; every column is transformed and
+    # convolved the same way whatever the count, so both counts give bit-identical fields (and the
+    # default one is pinned to the oracle by the family test)
+    nz = case[2]
+    counts = (8, 4) if nz == 1 else (2, 1)
+    path = W.random_spins((case[7], case[0] * case[1] * case[2], 3), seed=77 + nz)
+    fields = []
+    for kxb in counts:
+        monkeypatch.setenv("SS_X_CONFIG", f"256:4:256:4:{kxb}")
+        with ss.StringMethod([case]) as sm:
+            sm.set_path(0, path)
+            fields.append(sm.field(0, dtype=np.float32))
+    np.testing.assert_array_equal(fields[0], fields[1])
+    ref = oracle.field(_model(case), _unit(path))
+    assert np.abs(fields[0] - ref).max() <= 1e-5 * np.abs(ref).max()
