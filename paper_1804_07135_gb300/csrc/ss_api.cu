@@ -165,6 +165,8 @@ struct ss_ctx {
     ss_free_fn free_fn = nullptr;
     void* alloc_user = nullptr;
     cudaGraphExec_t graph1 = nullptr, graphN = nullptr;
+    cudaGraphExec_t rk_graph1 = nullptr, rk_graphN = nullptr;  // adaptive integrator: 1 and kRkGraphIters iterations
+    cudaStream_t rk_body = nullptr;  // captures the bodies of the attempt-round WHILE nodes
     // several size groups: one graph branch per group (their strings never interact), forked from and
     // joined back into cs
     std::vector<cudaStream_t> branch;  // size groups 1.. (group 0 stays on cs)
@@ -176,7 +178,6 @@ struct ss_ctx {
     int dynamics = 0;    // SS_DYN_STRING or SS_DYN_LLG
     double alpha = 0.0;  // damping of the precessional dynamics
     double rtol = 1e-6, atol = 1e-8;
-    int* h_active = nullptr;  // pinned, one flag per size group
     // FP32 contexts: an FP64 copy of every size group's evaluation pipeline, built on the first energy
     // query; reported energies and energy terms are evaluated there from the FP32 state
     std::vector<Group> ev64;
@@ -727,58 +728,127 @@ int rk_sys_count(const ss_ctx* c, const StringRec& r) {
     return rk_per_image(c->integrator) ? r.d.n_images : 1;
 }
 
-// n_iter iterations: per iteration every string integrates over opts.dt with Dormand-Prince attempts (one
-// host synchronisation per attempt round decides whether another is needed), then the arc kernel
-// reparametrises and sums the energies of the state the interval started from.
-template <typename T> ss_status rk_iterations(ss_ctx* c, int n_iter) {
-    const size_t ng = c->groups.size();
-    for (int it = 0; it < n_iter; ++it) {
-        std::vector<char> active(ng, 1);
-        for (size_t gi = 0; gi < ng; ++gi) {
-            Group& g = c->groups[gi];
-            GroupArgs<T> a = group_args<T>(c, g);
-            GroupArgs<T> ai = a;
-            ai.interp = g.interp_ident;
-            RkArgs<T> r = rk_args<T>(c, g);
-            launch_xfwd<T>(a, false, g.thr_a, 0, c->cs);  // s = reparametrised state
-            CUDA_TRY(c, cudaMemcpyAsync(r.y0, a.s, (size_t)3 * g.N * g.n_img * sizeof(T), cudaMemcpyDeviceToDevice, c->cs));
-            launch_rk_control<T>(ai, r, 1, c->cs);
-        }
-        for (int round = 0;; ++round) {
-            bool any = false;
-            for (size_t gi = 0; gi < ng; ++gi) {
-                if (!active[gi]) continue;
-                Group& g = c->groups[gi];
-                GroupArgs<T> ai = group_args<T>(c, g);
-                ai.interp = g.interp_ident;
-                RkArgs<T> r = rk_args<T>(c, g);
-                const size_t stride = (size_t)3 * g.N * g.n_img;
-                for (int st = 0; st < r.dp.stages; ++st) {
-                    launch_rk_assemble<T>(ai, r, st, c->cs);
-                    launch_xfwd<T>(ai, g.dipole, g.thr_a, g.smem_a, c->cs);
-                    if (g.dipole) launch_yz<T>(ai, g.thr_b, g.smem_b, c->cs);
-                    if (g.direct) launch_dipole_direct<T>(ai, (T*)g.hdir, c->cs);
-                    launch_xinv_force<T>(ai, g.dipole, r.k + st * stride, round == 0 && st == 0,
-                                         c->dynamics == SS_DYN_LLG, g.thr_c, g.smem_c_eval, c->cs);
-                }
-                launch_rk_finish<T>(ai, r, c->cs);
-                launch_rk_control<T>(ai, r, 0, c->cs);
-                launch_rk_commit<T>(ai, r, c->cs);
-                CUDA_TRY(c, cudaMemcpyAsync(&c->h_active[gi], r.active, sizeof(int), cudaMemcpyDeviceToHost, c->cs));
-                any = true;
-            }
-            if (!any) break;
-            CUDA_TRY(c, cudaGetLastError());
-            CUDA_TRY(c, cudaStreamSynchronize(c->cs));
-            for (size_t gi = 0; gi < ng; ++gi)
-                if (active[gi]) active[gi] = c->h_active[gi] != 0;
-        }
-        for (Group& g : c->groups) {
-            GroupArgs<T> a = group_args<T>(c, g);
-            launch_arc<T>(a, g.arc, g.thr_arc, c->cs);
-            if (c->interp == SS_INTERP_SPLINE) launch_spline_apply<T>(a, g.arc, g.arc.maxK, c->cs);
+// One attempt round of size group g (Sec. III) on stream st: for every stage i, Y_i from y0 and the
+// earlier stages, then k_i = F(Y_i) through the field pipeline (identity table) and the step kernel in
+// force mode; then the fifth-order solution with its scaled error, the step-size control and the commit of
+// accepted attempts.  The first round of an interval also sums the energies of the state the interval
+// starts from (its stage 0 is that state).
+template <typename T> void issue_rk_round(ss_ctx* c, Group& g, bool first, cudaStream_t st) {
+    GroupArgs<T> ai = group_args<T>(c, g);
+    ai.interp = g.interp_ident;
+    RkArgs<T> r = rk_args<T>(c, g);
+    const size_t stride = (size_t)3 * g.N * g.n_img;
+    for (int s = 0; s < r.dp.stages; ++s) {
+        launch_rk_assemble<T>(ai, r, s, st);
+        launch_xfwd<T>(ai, g.dipole, g.thr_a, g.smem_a, st);
+        if (g.dipole) launch_yz<T>(ai, g.thr_b, g.smem_b, st);
+        if (g.direct) launch_dipole_direct<T>(ai, (T*)g.hdir, st);
+        launch_xinv_force<T>(ai, g.dipole, r.k + s * stride, first && s == 0, c->dynamics == SS_DYN_LLG, g.thr_c,
+                             g.smem_c_eval, st);
+    }
+    launch_rk_finish<T>(ai, r, st);
+    launch_rk_control<T>(ai, r, 0, st);
+    launch_rk_commit<T>(ai, r, st);
+}
+
+// One iteration of size group g captured on stream st (a stream capturing the graph): the reparametrised
+// state becomes y0 and a new interval opens; the first attempt round runs unconditionally, the further
+// ones inside a conditional WHILE node whose body ends by setting the condition from the group's active
+// flag (some system has not reached the end of its interval), so the rounds need no host round trip.
+// Then the arc kernel reparametrises (Eqs. 11-12).  The body is captured on c->rk_body.
+template <typename T> cudaError_t capture_rk_group_iteration(ss_ctx* c, Group& g, cudaStream_t st) {
+    GroupArgs<T> a = group_args<T>(c, g);
+    GroupArgs<T> ai = a;
+    ai.interp = g.interp_ident;
+    RkArgs<T> r = rk_args<T>(c, g);
+    launch_xfwd<T>(a, false, g.thr_a, 0, st);  // s = reparametrised state
+    cudaError_t e = cudaMemcpyAsync(r.y0, a.s, (size_t)3 * g.N * g.n_img * sizeof(T), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+    launch_rk_control<T>(ai, r, 1, st);
+    issue_rk_round<T>(c, g, true, st);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaGraph_t graph = nullptr;
+    if ((e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph)) != cudaSuccess) return e;
+    if (cs != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+    cudaGraphConditionalHandle h{};
+    if ((e = cudaGraphConditionalHandleCreate(&h, graph, 0, cudaGraphCondAssignDefault)) != cudaSuccess) return e;
+    launch_rk_condition(h, r.active, st);
+    const cudaGraphNode_t* deps = nullptr;
+    size_t n_deps = 0;
+    if ((e = cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, nullptr, &n_deps)) != cudaSuccess) return e;
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    if ((e = cudaGraphAddNode(&node, graph, deps, nullptr, n_deps, &p)) != cudaSuccess) return e;
+    if ((e = cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies)) != cudaSuccess)
+        return e;
+    cudaGraph_t body = p.conditional.phGraph_out[0];
+    if ((e = cudaStreamBeginCaptureToGraph(c->rk_body, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+        cudaSuccess)
+        return e;
+    issue_rk_round<T>(c, g, false, c->rk_body);
+    launch_rk_condition(h, r.active, c->rk_body);
+    cudaGraph_t body_out = nullptr;
+    if ((e = cudaStreamEndCapture(c->rk_body, &body_out)) != cudaSuccess) return e;
+    launch_arc<T>(a, g.arc, g.thr_arc, st);
+    if (c->interp == SS_INTERP_SPLINE) launch_spline_apply<T>(a, g.arc, g.arc.maxK, st);
+    return cudaGetLastError();
+}
+
+ss_status ensure_branches(ss_ctx* c);
+constexpr int kRkGraphIters = 8;
+
+// Capture `iters` Runge-Kutta iterations of every size group, one graph branch per group as in
+// capture_graph: each group loops over its own attempt rounds, so a group whose systems all finished
+// their interval waits for no other group's rejected attempts.
+ss_status capture_rk_graph(ss_ctx* c, int iters, cudaGraphExec_t* out) {
+    const int G = (int)c->groups.size();
+    TRY(ensure_branches(c));
+    if (!c->rk_body) CUDA_TRY(c, cudaStreamCreateWithFlags(&c->rk_body, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    CUDA_TRY(c, cudaStreamBeginCapture(c->cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    if (G > 1) {
+        e = cudaEventRecord(c->branch_ev[0], c->cs);
+        for (int b = 0; b < G - 1 && e == cudaSuccess; ++b) e = cudaStreamWaitEvent(c->branch[b], c->branch_ev[0], 0);
+    }
+    for (int gi = 0; gi < G && e == cudaSuccess; ++gi) {
+        cudaStream_t st = gi == 0 ? c->cs : c->branch[gi - 1];
+        for (int i = 0; i < iters && e == cudaSuccess; ++i)
+            e = use_fp64(c) ? capture_rk_group_iteration<double>(c, c->groups[gi], st)
+                            : capture_rk_group_iteration<float>(c, c->groups[gi], st);
+    }
+    if (G > 1) {
+        for (int b = 0; b < G - 1 && e == cudaSuccess; ++b) {
+            e = cudaEventRecord(c->branch_ev[b + 1], c->branch[b]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(c->cs, c->branch_ev[b + 1], 0);
         }
     }
+    const cudaError_t e_end = cudaStreamEndCapture(c->cs, &graph);
+    if (e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return fail(c, SS_ERR_CUDA, "Runge-Kutta graph capture: %s", cudaGetErrorString(e));
+    }
+    if (e_end != cudaSuccess) return fail(c, SS_ERR_CUDA, "Runge-Kutta graph capture: %s", cudaGetErrorString(e_end));
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(c, SS_ERR_CUDA, "Runge-Kutta graph instantiate: %s", cudaGetErrorString(e));
+    return SS_OK;
+}
+
+// n_iter iterations of the adaptive integrator: per iteration every string integrates over opts.dt with
+// as many attempt rounds as its step-size control needs, then reparametrises; replayed from graphs of
+// kRkGraphIters and of one iteration.
+ss_status rk_iterations(ss_ctx* c, int n_iter) {
+    const int G = kRkGraphIters;
+    if (n_iter >= G && !c->rk_graphN) TRY(capture_rk_graph(c, G, &c->rk_graphN));
+    if (n_iter % G && !c->rk_graph1) TRY(capture_rk_graph(c, 1, &c->rk_graph1));
+    for (int i = 0; i < n_iter / G; ++i) CUDA_TRY(c, cudaGraphLaunch(c->rk_graphN, c->cs));
+    for (int i = 0; i < n_iter % G; ++i) CUDA_TRY(c, cudaGraphLaunch(c->rk_graph1, c->cs));
     return SS_OK;
 }
 
@@ -1034,11 +1104,8 @@ ss_status check_paths(ss_ctx* c, const Group& g) {
     return SS_OK;
 }
 
-// Capture `iters` iterations of every size group.  With several groups each group's chain of launches is
-// its own branch of the graph (forked from and joined back into cs), so the groups' kernels overlap on
-// the GPU instead of running one group after another; within a branch the launches keep their order and
-// programmatic dependent launch.
-ss_status capture_graph(ss_ctx* c, int iters, cudaGraphExec_t* out) {
+// The streams and events of the graph branches (one per size group after the first).
+ss_status ensure_branches(ss_ctx* c) {
     const int G = (int)c->groups.size();
     if (G > 1 && c->branch.empty()) {
         c->branch.assign(G - 1, nullptr);
@@ -1046,6 +1113,24 @@ ss_status capture_graph(ss_ctx* c, int iters, cudaGraphExec_t* out) {
         for (auto& st : c->branch) CUDA_TRY(c, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
         for (auto& ev : c->branch_ev) CUDA_TRY(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     }
+    return SS_OK;
+}
+
+// The captured graphs hold kernel sequences and arguments that the variant setters change.
+void drop_graphs(ss_ctx* c) {
+    for (cudaGraphExec_t* gp : {&c->graph1, &c->graphN, &c->rk_graph1, &c->rk_graphN}) {
+        if (*gp) cudaGraphExecDestroy(*gp);
+        *gp = nullptr;
+    }
+}
+
+// Capture `iters` iterations of every size group.  With several groups each group's chain of launches is
+// its own branch of the graph (forked from and joined back into cs), so the groups' kernels overlap on
+// the GPU instead of running one group after another; within a branch the launches keep their order and
+// programmatic dependent launch.
+ss_status capture_graph(ss_ctx* c, int iters, cudaGraphExec_t* out) {
+    const int G = (int)c->groups.size();
+    TRY(ensure_branches(c));
     cudaGraph_t graph = nullptr;
     CUDA_TRY(c, cudaStreamBeginCapture(c->cs, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
@@ -1288,12 +1373,12 @@ ss_status ss_set_integrator(ss_ctx* c, int kind, double rtol, double atol) {
         return fail(c, SS_ERR_STATE, "the climbing image is defined for the Euler step only");
     TRY(enter(c));
     if (kind != SS_INT_EULER) {
-        if (!c->h_active) CUDA_TRY(c, cudaHostAlloc((void**)&c->h_active, c->groups.size() * sizeof(int), cudaHostAllocDefault));
         for (Group& g : c->groups) TRY(rk_setup(c, g, rk_per_image(kind)));
         c->rtol = rtol;
         c->atol = atol;
     }
     c->integrator = kind;
+    drop_graphs(c);
     ss_status st = sync_check(c);
     TRY(leave(c));
     return st;
@@ -1340,14 +1425,7 @@ ss_status ss_set_reparam(ss_ctx* c, int interp, int climb) {
     }
     c->interp = interp;
     c->climb = climb;
-    // the captured graphs hold the previous kernel sequence and arguments
-    if (c->graph1) cudaGraphExecDestroy(c->graph1);
-    if (c->graphN) cudaGraphExecDestroy(c->graphN);
-    for (auto st : c->branch)
-        if (st) cudaStreamDestroy(st);
-    for (auto ev : c->branch_ev)
-        if (ev) cudaEventDestroy(ev);
-    c->graph1 = c->graphN = nullptr;
+    drop_graphs(c);
     ss_status st = sync_check(c);
     TRY(leave(c));
     return st;
@@ -1363,13 +1441,7 @@ ss_status ss_set_dynamics(ss_ctx* c, int kind, double alpha) {
     c->dynamics = kind;
     c->alpha = kind == SS_DYN_LLG ? alpha : 0.0;
     for (Group& g : c->groups) g.arc.reparam = kind == SS_DYN_STRING && c->opts.reparam_every != 0;
-    if (c->graph1) cudaGraphExecDestroy(c->graph1);
-    if (c->graphN) cudaGraphExecDestroy(c->graphN);
-    for (auto st : c->branch)
-        if (st) cudaStreamDestroy(st);
-    for (auto ev : c->branch_ev)
-        if (ev) cudaEventDestroy(ev);
-    c->graph1 = c->graphN = nullptr;
+    drop_graphs(c);
     return SS_OK;
 }
 
@@ -1443,7 +1515,7 @@ ss_status ss_step(ss_ctx* c, int n_iter) {
     for (Group& g : c->groups) ++g.state_epoch;
     TRY(enter(c));
     if (c->integrator != SS_INT_EULER) {
-        TRY(use_fp64(c) ? rk_iterations<double>(c, n_iter) : rk_iterations<float>(c, n_iter));
+        TRY(rk_iterations(c, n_iter));
         return leave(c);
     }
     const int G = c->graphN_iters;
@@ -1654,8 +1726,8 @@ void ss_destroy(ss_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
     if (c->cs) cudaStreamSynchronize(c->cs);
-    if (c->graph1) cudaGraphExecDestroy(c->graph1);
-    if (c->graphN) cudaGraphExecDestroy(c->graphN);
+    drop_graphs(c);
+    if (c->rk_body) cudaStreamDestroy(c->rk_body);
     for (auto st : c->branch)
         if (st) cudaStreamDestroy(st);
     for (auto ev : c->branch_ev)
@@ -1666,7 +1738,6 @@ void ss_destroy(ss_ctx* c) {
         else
             cudaFree(a.first);
     }
-    if (c->h_active) cudaFreeHost(c->h_active);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
     if (c->ev_out) cudaEventDestroy(c->ev_out);
     if (c->cs) cudaStreamDestroy(c->cs);

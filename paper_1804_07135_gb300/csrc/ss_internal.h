@@ -256,6 +256,7 @@ template <typename T> void launch_rk_finish(const GroupArgs<T>& g, const RkArgs<
 template <typename T>
 void launch_rk_control(const GroupArgs<T>& g, const RkArgs<T>& r, int begin, cudaStream_t st);
 template <typename T> void launch_rk_commit(const GroupArgs<T>& g, const RkArgs<T>& r, cudaStream_t st);
+void launch_rk_condition(cudaGraphConditionalHandle h, const int* active, cudaStream_t st);
 template <typename T> void launch_arc(const GroupArgs<T>& g, const ArcArgs& a, int nthr, cudaStream_t st);
 template <typename T>
 void launch_eval_reduce(const GroupArgs<T>& g, const ArcArgs& a, double* terms, double* energies, double* cnorm2,

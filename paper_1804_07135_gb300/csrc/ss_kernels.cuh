@@ -1754,12 +1754,33 @@ template <typename T> DpCoef<T> dp_coefficients(int method) {
 constexpr int kRkTile = 1024;  // components per CTA of the element-wise Runge-Kutta kernels
 
 // grid (tiles, images), 256 threads
+// FP32 with N a multiple of 4: the element-wise Runge-Kutta kernels move float4s, one per thread and
+// tile (kRkTile = 4 x 256), so every thread has all of its loads in flight at once
+template <typename T> __device__ __forceinline__ bool rk_vec4(const GroupArgs<T>& g) {
+    return std::is_same<T, float>::value && (g.N & 3) == 0;
+}
+__device__ __forceinline__ float4 f4_fma(float a, float4 x, float4 y) {
+    return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+}
+
 template <typename T, int STAGE>
 __global__ void __launch_bounds__(256) rk_assemble_kernel(GroupArgs<T> g, RkArgs<T> r) {
     const int im = blockIdx.y;
     const size_t M = (size_t)3 * g.N, base = (size_t)im * M, stride = (size_t)g.n_img * M;
     const RkString& S = r.st[r.img_sys[im]];
     const T hs = S.done ? T(0) : T(S.hs);
+    if constexpr (std::is_same<T, float>::value) {
+        if (rk_vec4(g)) {
+            const size_t e4 = (size_t)blockIdx.x * (kRkTile / 4) + threadIdx.x;
+            if (4 * e4 >= M) return;
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int q = 0; q < STAGE; ++q)
+                a = f4_fma(r.dp.a[STAGE][q], reinterpret_cast<const float4*>(r.k + q * stride + base)[e4], a);
+            reinterpret_cast<float4*>(g.sp + base)[e4] = f4_fma(hs, a, reinterpret_cast<const float4*>(r.y0 + base)[e4]);
+            return;
+        }
+    }
     const size_t e1 = min(M, (size_t)(blockIdx.x + 1) * kRkTile);
     for (size_t e = (size_t)blockIdx.x * kRkTile + threadIdx.x; e < e1; e += blockDim.x) {
         T a = T(0);
@@ -1781,7 +1802,30 @@ __global__ void __launch_bounds__(256) rk_finish_kernel(GroupArgs<T> g, RkArgs<T
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *r.active = 0;  // the controllers set it again
     T v[1] = {T(0)};
     const size_t e1 = min(M, (size_t)(blockIdx.x + 1) * kRkTile);
-    for (size_t e = (size_t)blockIdx.x * kRkTile + threadIdx.x; e < e1; e += blockDim.x) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (rk_vec4(g)) {
+            const size_t e4 = (size_t)blockIdx.x * (kRkTile / 4) + threadIdx.x;
+            if (4 * e4 < M) {
+                float4 b5 = make_float4(0.f, 0.f, 0.f, 0.f), d4 = b5;
+#pragma unroll
+                for (int q = 0; q < 7; ++q) {
+                    if (q >= r.dp.stages) break;
+                    const float4 kq = reinterpret_cast<const float4*>(r.k + q * stride + base)[e4];
+                    b5 = f4_fma(r.dp.b[q], kq, b5);
+                    d4 = f4_fma(r.dp.e[q], kq, d4);
+                }
+                const float4 y0 = reinterpret_cast<const float4*>(r.y0 + base)[e4];
+                const float4 y5 = f4_fma(hs, b5, y0);
+                reinterpret_cast<float4*>(r.y5 + base)[e4] = y5;
+                const float q0 = hs * d4.x / (atol + rtol * fmaxf(fabsf(y0.x), fabsf(y5.x)));
+                const float q1 = hs * d4.y / (atol + rtol * fmaxf(fabsf(y0.y), fabsf(y5.y)));
+                const float q2 = hs * d4.z / (atol + rtol * fmaxf(fabsf(y0.z), fabsf(y5.z)));
+                const float q3 = hs * d4.w / (atol + rtol * fmaxf(fabsf(y0.w), fabsf(y5.w)));
+                v[0] = (q0 * q0 + q1 * q1) + (q2 * q2 + q3 * q3);
+            }
+        }
+    }
+    for (size_t e = rk_vec4(g) ? e1 : (size_t)blockIdx.x * kRkTile + threadIdx.x; e < e1; e += blockDim.x) {
         T b5 = T(0), d4 = T(0);
 #pragma unroll
         for (int q = 0; q < 7; ++q) {
@@ -1877,6 +1921,27 @@ __global__ void __launch_bounds__(256) rk_commit_kernel(GroupArgs<T> g, RkArgs<T
     const RkString& S = r.st[r.img_sys[im]];
     if (!S.accepted) return;  // uniform over the CTA
     const int N = g.N;
+    if constexpr (std::is_same<T, float>::value) {
+        if (rk_vec4(g)) {  // four sites per thread, float4 per component plane
+            const int i4 = blockIdx.x * blockDim.x + threadIdx.x;
+            if (4 * i4 >= N) return;
+            const size_t b4 = ((size_t)im * 3 * N) / 4 + i4, p4 = N / 4;
+            const float4 a = reinterpret_cast<const float4*>(r.y5)[b4];
+            const float4 b = reinterpret_cast<const float4*>(r.y5)[b4 + p4];
+            const float4 c = reinterpret_cast<const float4*>(r.y5)[b4 + 2 * p4];
+            const float nx_ = rsqrtf(a.x * a.x + b.x * b.x + c.x * c.x), ny_ = rsqrtf(a.y * a.y + b.y * b.y + c.y * c.y);
+            const float nz_ = rsqrtf(a.z * a.z + b.z * b.z + c.z * c.z), nw_ = rsqrtf(a.w * a.w + b.w * b.w + c.w * c.w);
+            const float4 o[3] = {make_float4(a.x * nx_, a.y * ny_, a.z * nz_, a.w * nw_),
+                                 make_float4(b.x * nx_, b.y * ny_, b.z * nz_, b.w * nw_),
+                                 make_float4(c.x * nx_, c.y * ny_, c.z * nz_, c.w * nw_)};
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                reinterpret_cast<float4*>(r.y0)[b4 + q * p4] = o[q];
+                if (S.done) reinterpret_cast<float4*>(g.sp)[b4 + q * p4] = o[q];
+            }
+            return;
+        }
+    }
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const size_t base = (size_t)im * 3 * N + i;
@@ -2529,7 +2594,8 @@ void launch_rk_control(const GroupArgs<T>& g, const RkArgs<T>& r, int begin, cud
 }
 
 template <typename T> void launch_rk_commit(const GroupArgs<T>& g, const RkArgs<T>& r, cudaStream_t st) {
-    rk_commit_kernel<T><<<dim3((g.N + 255) / 256, g.n_img), 256, 0, st>>>(g, r);
+    const int per = std::is_same<T, float>::value && (g.N & 3) == 0 ? 4 : 1;  // sites per thread
+    rk_commit_kernel<T><<<dim3((g.N / per + 255) / 256, g.n_img), 256, 0, st>>>(g, r);
 }
 
 template <typename T> void launch_arc(const GroupArgs<T>& g, const ArcArgs& a, int nthr, cudaStream_t st) {

@@ -301,3 +301,24 @@ def test_relax_until_the_barrier_settles(ss):
         done, ok, hist = sm.relax(tol=1e-10, check_every=50, max_iter=5000)
     assert ok and done < 5000
     assert abs(hist[0][-1] - 1.8) < 1e-8
+
+
+def test_resetting_the_graphs_of_several_size_groups(ss):
+    # after a step, choosing the reparametrisation or the dynamics again drops the captured graphs; with
+    # two size groups (two graph branches) the next step must recapture them and carry on exactly as an
+    # uninterrupted run (the oracle's 5 iterations)
+    cases = [(16, 16, 1, 1.0, 0.3, 0.05, 0.01, 5), (12, 10, 2, 1.0, 0.2, 0.1, 0.02, 4)]
+    paths = [W.bloch_point_path(c[0], c[1], c[2], c[7], R=3.0, D=c[4]) for c in cases]
+    with ss.StringMethod(cases, precision=FP64) as sm:
+        for i, p in enumerate(paths):
+            sm.set_path(i, p)
+        starts = [sm.get_path(i) for i in range(2)]
+        sm.step(2)
+        sm.set_reparam(ss.SS_INTERP_LINEAR, False)
+        sm.step(2)
+        sm.set_dynamics(ss.SS_DYN_STRING, 0.0)
+        sm.step(1)
+        got = [sm.get_path(i) for i in range(2)]
+    for c, s0, g in zip(cases, starts, got):
+        ref, _ = oracle.string_run(_model(c), _unit(s0), 5, 0.1)
+        assert np.abs(g - ref).max() < 1e-10
