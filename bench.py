@@ -67,6 +67,10 @@ def parse():
     p.add_argument("--no-other-workloads", action="store_true", help="skip the short runs of the batch workloads")
     p.add_argument("--variant", choices=tuple(VARIANTS), default="plain",
                    help="run the timed steps under a method variant (the headline is 'plain')")
+    p.add_argument("--workload", choices=tuple(WORKLOADS), default=HEADLINE,
+                   help=f"the timed workload (default: the headline, {HEADLINE})")
+    p.add_argument("--lattice", default=None, help="time only the workload's strings of this lattice, NXxNYxNZ")
+    p.add_argument("--strings", type=int, default=None, help="time only the first K strings (after --lattice)")
     return p.parse_args()
 
 
@@ -83,13 +87,18 @@ VARIANTS = {
 LLG_ALPHA = 0.1
 
 
+def rk_kind(binding, integ):
+    """The library's integrator constant for a variant's Runge-Kutta integrator name."""
+    return binding.SS_INT_DOPRI5 if integ == "dopri5" else binding.SS_INT_DOPRI5_IMAGE
+
+
 def apply_variant(binding, sm, name, rtol=1e-6, atol=1e-8):
     interp, climb, integ, dyn = VARIANTS[name]
     if dyn == "llg":
         sm.set_dynamics(binding.SS_DYN_LLG, LLG_ALPHA)
     sm.set_reparam(binding.SS_INTERP_SPLINE if interp == "spline" else binding.SS_INTERP_LINEAR, climb)
     if integ != "euler":
-        sm.set_integrator(binding.SS_INT_DOPRI5 if integ == "dopri5" else binding.SS_INT_DOPRI5_IMAGE, rtol, atol)
+        sm.set_integrator(rk_kind(binding, integ), rtol, atol)
 
 
 def dist_env():
@@ -167,10 +176,43 @@ def headline_workload():
     return workloads.uneven_study()
 
 
-def oracle_sample_spec():
-    """The string the CPU baseline samples: the study's first 64 x 64 x 4 string (the oracle's direct
-    dipole sum costs N^2 per image, so the smallest lattice of the study keeps the sample bounded)."""
-    return next(s for s in headline_workload().strings if s.nx == 64)
+# the workloads bench.py can time (the first is the headline); the others are also measured briefly in
+# the headline run's side entries
+WORKLOADS = {w.name: w for w in (workloads.uneven_study(), workloads.bloch_collapse(), workloads.boundary_sweep(),
+                                 workloads.paper_monolayer_workload(), workloads.paper_phase_diagram())}
+HEADLINE = headline_workload().name
+
+
+def selected_workload(name, lattice=None, n_strings=None):
+    """The named workload, restricted to the strings of one lattice ("NXxNYxNZ") and to its first
+    n_strings strings when given (small cases of the same kernels, e.g. for ncu captures)."""
+    wl = WORKLOADS[name]
+    strings, tag = list(wl.strings), []
+    n_total = len(strings)
+    if lattice:
+        strings = [s for s in strings if f"{s.nx}x{s.ny}x{s.nz}" == lattice]
+        if not strings:
+            raise SystemExit(f"{name} has no {lattice} strings")
+        tag.append(lattice)
+    if n_strings:
+        strings = strings[:n_strings]
+        tag.append(f"{len(strings)} of {n_total} strings")
+    if not tag:
+        return wl
+    return workloads.Workload(f"{wl.name}[{', '.join(tag)}]", tuple(strings), wl.n_iter, wl.dt)
+
+
+def oracle_sample_spec(wl=None):
+    """The string the CPU baseline samples: the workload's first string of the smallest lattice (the
+    oracle's direct dipole sum costs N^2 per image); for the headline study its first 64 x 64 x 4 string."""
+    wl = wl or headline_workload()
+    return min(wl.strings, key=lambda s: s.n_sites)
+
+
+def oracle_sample_images(spec):
+    """Images of the sample: REF_IMAGES for lattices up to 64 x 64 x 4 sites, fewer (at least 2) for
+    larger ones, so that the sample's N^2 cost stays near that of 8 images of 16384 sites."""
+    return max(2, min(REF_IMAGES, int(REF_IMAGES * (16384 / spec.n_sites) ** 2)))
 
 
 def cpu_oracle_sample(spec, dt, n_images=REF_IMAGES, threads=None):
@@ -188,14 +230,19 @@ def cpu_oracle_sample(spec, dt, n_images=REF_IMAGES, threads=None):
     return units / t, min(cores, n_images), t  # the oracle's threads run over images
 
 
-def oracle_sample_text(spec, n_images=REF_IMAGES):
-    return (f"one oracle iteration (direct O(N^2) dipole) of the first {n_images} images of the uneven study's "
-            f"first {spec.nx}x{spec.ny}x{spec.nz} string")
+def oracle_sample_text(spec, n_images=REF_IMAGES, wl_name=None):
+    return (f"one oracle iteration (direct O(N^2) dipole) of the first {n_images} images of "
+            f"{wl_name or headline_workload().name}'s first {spec.nx}x{spec.ny}x{spec.nz} string")
+
+
+# the files that define the iteration's kernels (the host-side API and the no-allocation entry point
+# launch them but do not change their code)
+KERNEL_SOURCES = ("ss_fft.cuh", "ss_internal.h", "ss_kernels.cuh", "ss_kernels_f32.cu", "ss_kernels_f64.cu")
 
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1804_07135_gb300", "csrc"))):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_1804_07135_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -238,27 +285,44 @@ def whole_job_value(units_per_rank, world, seconds):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    wl = headline_workload()
-    spec = oracle_sample_spec()
+    wl = selected_workload(args.workload, args.lattice, args.strings)
+    spec = oracle_sample_spec(wl)
+    n_img = oracle_sample_images(spec)
     times = []
     cores = len(os.sched_getaffinity(0))
     for i in range(args.warmup + args.steps):
-        v, cores, t = cpu_oracle_sample(spec, wl.dt)
+        v, cores, t = cpu_oracle_sample(spec, wl.dt, n_img)
         if i >= args.warmup:
             times.append(t)
-    units = spec.n_sites * REF_IMAGES
+    units = spec.n_sites * n_img
     value = units * len(times) / sum(times)
     line = {
         "impl": "reference", "metric": "spin-updates/s", "value": value, "unit": "spin-updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl.name, "sampled_string": [spec.nx, spec.ny, spec.nz], "images": REF_IMAGES,
+        "config": {"workload": wl.name, "sampled_string": [spec.nx, spec.ny, spec.nz], "images": n_img,
                    "iterations_per_step": 1},
         "cpu_baseline": {"value": value, "unit": "spin-updates/s", "cores": cores, "kind": "oracle",
-                         "sample": oracle_sample_text(spec)},
+                         "sample": oracle_sample_text(spec, n_img, wl.name)},
         "e2e": {"value": value, "unit": "spin-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def working_set_gb(wl):
+    """Device bytes an iteration touches (GB): per string the FP32 state before and after the step
+    (2 x 12 bytes per site-image) and the complex spectrum of its image pairs (Px x ny x nz x 3 x 8
+    bytes per pair)."""
+    b = 0
+    for s in wl.strings:
+        b += 24 * s.n_sites * s.n_images + (s.n_images + 1) // 2 * padded(s.nx) * s.ny * s.nz * 24
+    return b / 1e9
+
+
+def l2_note(wl):
+    ws = working_set_gb(wl)
+    where = "exceeds the 129 MB L2" if ws > 0.129 else "stays in L2 across a step's iterations"
+    return f"flushed before every step (256 MB write); the working set (about {ws:.2g} GB) {where}"
 
 
 def group_keys(wl):
@@ -329,7 +393,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
         pg = dist
 
-    wl = headline_workload()
+    wl = selected_workload(args.workload, args.lattice, args.strings)
     n_iter = args.iters or ITERS_PER_STEP
     n_str = len(wl.strings)
     descs = [(s.nx, s.ny, s.nz, s.J, s.D, s.K, s.w, s.n_images) for s in wl.strings]
@@ -391,7 +455,10 @@ def main():
     # per-kernel roofline (kernels launched one by one on the library stream, CUDA-event timed)
     for i, p in enumerate(paths_dev):
         sm.set_path(i, p)
-    if rk:  # the field kernels are timed in the Euler iteration
+    rk_kernels = None
+    if rk:  # the round's kernels one by one (single-string workloads), then the field kernels in the Euler iteration
+        if n_str == 1:
+            rk_kernels = rk_kernel_times(binding, sm, wl.strings[0], rk_kind(binding, VARIANTS[args.variant][2]))
         sm.set_integrator(binding.SS_INT_EULER)
     ms = sm.time_kernels(reps=10)
     interp, climb, integ, dyn = VARIANTS[args.variant]
@@ -411,7 +478,7 @@ def main():
                    "iterations_per_step": n_iter, "workload_iterations": wl.n_iter, "dt": wl.dt, "w": 0.01,
                    "precision": "fp32 spins, fields and FFTs; fp64 energy and arc-length reductions; "
                                 "barriers from an fp64 evaluation of the fp32 state",
-                   "l2": "flushed before every step (256 MB write); the working set (about 6 GB) exceeds L2",
+                   "l2": l2_note(wl),
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_value, "unit": "spin-updates/s",
                 "h2d_bytes_per_step": int(sum(p.nbytes for p in paths)),
@@ -423,8 +490,12 @@ def main():
         "clocks": clk.summary(),
         "barriers": [{"dE": b[0], "k_max": b[1]} for b in barriers],
     }
+    if rk_kernels:
+        line["rk_kernels"] = rk_kernels
     if rk:
-        line["gpu_launches"] = int(args.steps * (2 * n_str + 6 * len(keys) + 3 * n_iter + (7 * kpi + 3) *
+        # per iteration and group: the interval's opening (x-forward, control), per attempt round seven
+        # stages of kpi launches, finish, control, commit and the round condition, and the arc kernel
+        line["gpu_launches"] = int(args.steps * (2 * n_str + 6 * len(keys) + 3 * n_iter + (7 * kpi + 4) *
                                                  (max(rk_attempts) if args.variant == "dopri5_per_image" else rk_attempts[0])))
     if not args.no_accuracy:
         line["fp64_gpu"] = fp64_gpu_rate(binding, wl, stream, paths_dev)
@@ -442,11 +513,12 @@ def main():
                                for name, kind in (("dopri5_per_string", binding.SS_INT_DOPRI5),
                                                   ("dopri5_per_image", binding.SS_INT_DOPRI5_IMAGE))}
     if not args.no_cpu_baseline and world == 1:
-        spec = oracle_sample_spec()
-        v, cores, t = cpu_oracle_sample(spec, wl.dt)
-        v1, _, t1 = cpu_oracle_sample(spec, wl.dt, threads=1)
+        spec = oracle_sample_spec(wl)
+        n_img = oracle_sample_images(spec)
+        v, cores, t = cpu_oracle_sample(spec, wl.dt, n_img)
+        v1, _, t1 = cpu_oracle_sample(spec, wl.dt, n_img, threads=1)
         line["cpu_baseline"] = {"value": v, "unit": "spin-updates/s", "cores": cores, "kind": "oracle",
-                                "sample": f"{oracle_sample_text(spec)}, {t:.1f} s",
+                                "sample": f"{oracle_sample_text(spec, n_img, wl.name)}, {t:.1f} s",
                                 "single_thread": {"value": v1, "cores": 1, "seconds": t1}}
     sm.close()
     print(json.dumps(line), flush=True)
@@ -565,6 +637,34 @@ def variant_runs(binding, wl, stream, plain_ms, iters=128, warm=64):
     return out
 
 
+def rk_stages(binding, kind):
+    return 7 if kind in (binding.SS_INT_DOPRI5, binding.SS_INT_DOPRI5_IMAGE) else 6
+
+
+def rk_kernel_times(binding, sm, spec, kind, reps=5):
+    """The kernels of one attempt round of a one-string, one-lattice context, each launched on its own
+    (ss_time_kernels), summed by kind, with the element-wise Runge-Kutta kernels' rates."""
+    stages = rk_stages(binding, kind)
+    ms = sm.time_kernels(reps=reps)
+    names = ["open"] + ["assemble", "xfwd", "yz", "xinv"] * stages + ["finish", "control", "commit", "arc"]
+    per = {}
+    for n, t in zip(names, ms):
+        per[n] = per.get(n, 0.0) + float(t)
+    units = spec.n_sites * spec.n_images
+    # algorithmic bytes per site-image (FP32 components, 12 bytes per spin vector): stage s assembles
+    # from y0 and s earlier stages into the stage state, (s + 2) x 12; finish reads y0 and every stage
+    # and writes y5, (stages + 2) x 12
+    b_asm = sum((st + 2) * 12 for st in range(stages)) * units
+    b_fin = (stages + 2) * 12 * units
+    peaks, _ = measured_peaks()
+    return {"ms_per_round": {k: round(v, 5) for k, v in per.items()},
+            "assemble_gbs": b_asm / (per["assemble"] * 1e-3) / 1e9,
+            "finish_gbs": b_fin / (per["finish"] * 1e-3) / 1e9,
+            "hbm_peak_gbs": peaks["hbm_gbs"],
+            "note": f"launched one by one; the round's arrays (about {(stages + 4) * 12 * units / 1e9:.2g} GB) "
+                    "may partly stay in L2, so these rates can exceed what HBM alone allows"}
+
+
 def adaptive_rk(binding, wl, stream, kind, per_iter_euler_ms, iters=10, warm=2, rtol=1e-6, atol=1e-8):
     """Device-timed Dormand-Prince evolution of the bench workload (each iteration integrates every image
     over the workload's dt, then reparametrises): spin-updates/s counted like the Euler path (N K per
@@ -587,7 +687,9 @@ def adaptive_rk(binding, wl, stream, kind, per_iter_euler_ms, iters=10, warm=2, 
         t = e0.elapsed_time(e1) / 1e3
         step, a1, r1 = sm.integrator_state(0)
         att1 = [sum(sm.integrator_state(0, k)[1:]) for k in range(spec.n_images)]
+        rk_kernels = rk_kernel_times(binding, sm, spec, kind)
     units = spec.n_sites * spec.n_images
+    stages = rk_stages(binding, kind)
     attempts = a1 + r1 - a0 - r0  # summed over the string's systems
     # every system of the group takes part in each round, so the rounds per interval are set by the
     # system with the most attempts; with one system per string they equal its attempts
@@ -596,8 +698,9 @@ def adaptive_rk(binding, wl, stream, kind, per_iter_euler_ms, iters=10, warm=2, 
             "atol": atol, "interval": wl.dt, "ms_per_iter": 1e3 * t / iters,
             "attempts_per_iter": attempts / iters, "accepted": a1 - a0, "rejected": r1 - r0,
             "rounds_per_iter_min": rounds / iters, "carried_step_min": step,
-            "force_evals_per_s": 7 * units * rounds / t,
-            "ms_per_round_vs_7_euler_iters": (1e3 * t / max(rounds, 1)) / (7 * per_iter_euler_ms)}
+            "force_evals_per_s": stages * units * rounds / t,
+            "ms_per_round_vs_7_euler_iters": (1e3 * t / max(rounds, 1)) / (7 * per_iter_euler_ms),
+            "kernels": rk_kernels}
 
 
 def other_workload(binding, wl, stream, iters=20, warm=3):

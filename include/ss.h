@@ -141,15 +141,18 @@ ss_status ss_grad(ss_ctx* ctx, int string, int image, void* dE_ds, int dtype, in
  * Synchronises. */
 ss_status ss_energy_terms(ss_ctx* ctx, int string, double* out);
 
-/* Measures the kernels of one Euler iteration in the current mode: each entry is launched on its own
- * (not from the graph) on the context's stream, bracketed by CUDA events, for `reps` >= 1 timed
- * iterations after one untimed iteration.  ms_out[i] (host, up to max_out entries) receives the mean
- * duration in milliseconds of entry i, in launch order: for each size group xfwd, yz (with the FFT
+/* Measures the kernels of one iteration in the current mode: each entry is launched on its own (not
+ * from the graph) on the context's stream, bracketed by CUDA events, for `reps` >= 1 timed iterations
+ * after one untimed iteration.  ms_out[i] (host, up to max_out entries) receives the mean duration in
+ * milliseconds of entry i, in launch order.  Euler step, for each size group: xfwd, yz (with the FFT
  * dipole term), the direct dipole sums (with SS_DIPOLE_DIRECT), xinv (in its step, climbing-image or LLG
- * mode), the two climbing-image kernels as one
- * entry (climbing image on), arc (which also reparametrises), the spline apply kernel (spline on).
- * *n_out receives the number of entries.  The strings advance by reps + 1 iterations.  SS_ERR_STATE
- * under a Runge-Kutta integrator.  Synchronises. */
+ * mode), the two climbing-image kernels as one entry (climbing image on), arc (which also
+ * reparametrises), the spline apply kernel (spline on).  Runge-Kutta integrators, for each size group an
+ * iteration with a single attempt round: the interval's opening (x-forward, copy into y0, control) as
+ * one entry, per stage the assembly, xfwd, yz, direct sums and xinv (force mode) as above, then finish,
+ * control, commit, arc and spline apply (an interval that needs more attempts is left unfinished; the
+ * next ss_step opens a new one).  *n_out receives the number of entries.  The strings advance by
+ * reps + 1 iterations.  Synchronises. */
 ss_status ss_time_kernels(ss_ctx* ctx, int reps, double* ms_out, int max_out, int* n_out);
 
 /* Effective field of a batch of images, for callers that cannot allocate device memory.  The paper

@@ -366,11 +366,15 @@ def ss_energy_terms(ctx, string: int) -> np.ndarray:
 
 
 def ss_time_kernels(ctx, reps: int = 10) -> np.ndarray:
-    """Mean milliseconds per kernel of one iteration (xfwd, yz, xinv, arc per size group)."""
-    out = np.zeros(64)
+    """Mean milliseconds per timing entry of one iteration, in launch order (see include/ss.h: xfwd, yz,
+    xinv, arc per size group on the Euler path; the stages of one attempt round under a Runge-Kutta
+    integrator)."""
+    out = np.zeros(4096)
     n = ctypes.c_int()
-    _check(_lib.ss_time_kernels(ctx, int(reps), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 64,
+    _check(_lib.ss_time_kernels(ctx, int(reps), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(out),
                                 ctypes.byref(n)), ctx)
+    if n.value > len(out):
+        raise SsError(SS_ERR_INVALID_ARG, f"{n.value} timing entries exceed the binding's buffer")
     return out[: n.value].copy()
 
 

@@ -169,7 +169,7 @@ struct ss_ctx {
     cudaStream_t rk_body = nullptr;  // captures the bodies of the attempt-round WHILE nodes
     // several size groups: one graph branch per group (their strings never interact), forked from and
     // joined back into cs
-    std::vector<cudaStream_t> branch;  // size groups 1.. (group 0 stays on cs)
+    std::vector<cudaStream_t> branch;  // one per size group
     std::vector<cudaEvent_t> branch_ev;  // [0] fork, [1..] joins
     int graphN_iters = 64;
     int integrator = 0;  // SS_INT_EULER or one of the Runge-Kutta kinds
@@ -617,14 +617,15 @@ template <typename T> ss_status tune_group(ss_ctx* c, Group& g) {
 
 // The launches of one Euler iteration of group g in the current mode, as timed entries: xfwd, yz (with a
 // dipole term), xinv (step, climbing-image or LLG mode), the two climbing-image kernels as one entry,
-// arc, spline apply.
+// arc, spline apply.  Launches entry which_only; which_only < 0 launches nothing and returns the number
+// of entries.
 template <typename T> int time_entries(ss_ctx* c, Group& g, int which_only) {
     GroupArgs<T> a = group_args<T>(c, g);
     const T dt = T(c->opts.dt);
     int e = 0;
     auto entry = [&](bool on, auto&& launch) {
         if (!on) return;
-        if (which_only < 0 || which_only == e) launch();
+        if (which_only == e) launch();
         ++e;
     };
     entry(true, [&] { launch_xfwd<T>(a, g.dipole, g.thr_a, g.smem_a, c->cs); });
@@ -798,46 +799,64 @@ template <typename T> cudaError_t capture_rk_group_iteration(ss_ctx* c, Group& g
     return cudaGetLastError();
 }
 
-ss_status ensure_branches(ss_ctx* c);
+// The launches of one Runge-Kutta iteration of group g with a single attempt round, as the timing entries
+// of ss_time_kernels in launch order: the interval's opening (x-forward of the reparametrised state, copy
+// into y0, control in its opening mode), per stage its assembly, x-forward, y/z (FFT dipole term), direct
+// dipole sums (SS_DIPOLE_DIRECT) and x-inverse in force mode, then finish, control, commit, arc and the
+// spline apply kernel (spline on).  An interval that needs more than one attempt is left unfinished (the
+// next ss_step opens a new one).  which_only < 0 launches nothing and returns the number of entries.
+template <typename T> int rk_time_entries(ss_ctx* c, Group& g, int which_only) {
+    GroupArgs<T> a = group_args<T>(c, g);
+    GroupArgs<T> ai = a;
+    ai.interp = g.interp_ident;
+    RkArgs<T> r = rk_args<T>(c, g);
+    const size_t stride = (size_t)3 * g.N * g.n_img;
+    int e = 0;
+    auto entry = [&](bool on, auto&& launch) {
+        if (!on) return;
+        if (which_only == e) launch();
+        ++e;
+    };
+    entry(true, [&] {
+        launch_xfwd<T>(a, false, g.thr_a, 0, c->cs);
+        cudaMemcpyAsync(r.y0, a.s, stride * sizeof(T), cudaMemcpyDeviceToDevice, c->cs);
+        launch_rk_control<T>(ai, r, 1, c->cs);
+    });
+    for (int st = 0; st < r.dp.stages; ++st) {
+        entry(true, [&] { launch_rk_assemble<T>(ai, r, st, c->cs); });
+        entry(true, [&] { launch_xfwd<T>(ai, g.dipole, g.thr_a, g.smem_a, c->cs); });
+        entry(g.dipole, [&] { launch_yz<T>(ai, g.thr_b, g.smem_b, c->cs); });
+        entry(g.direct, [&] { launch_dipole_direct<T>(ai, (T*)g.hdir, c->cs); });
+        entry(true, [&] {
+            launch_xinv_force<T>(ai, g.dipole, r.k + st * stride, st == 0, c->dynamics == SS_DYN_LLG, g.thr_c,
+                                 g.smem_c_eval, c->cs);
+        });
+    }
+    entry(true, [&] { launch_rk_finish<T>(ai, r, c->cs); });
+    entry(true, [&] { launch_rk_control<T>(ai, r, 0, c->cs); });
+    entry(true, [&] { launch_rk_commit<T>(ai, r, c->cs); });
+    entry(true, [&] { launch_arc<T>(a, g.arc, g.thr_arc, c->cs); });
+    entry(c->interp == SS_INTERP_SPLINE, [&] { launch_spline_apply<T>(a, g.arc, g.arc.maxK, c->cs); });
+    return e;
+}
+
+template <typename F> ss_status capture_branched(ss_ctx* c, const char* what, F issue, cudaGraphExec_t* out);
 constexpr int kRkGraphIters = 8;
 
 // Capture `iters` Runge-Kutta iterations of every size group, one graph branch per group as in
 // capture_graph: each group loops over its own attempt rounds, so a group whose systems all finished
 // their interval waits for no other group's rejected attempts.
 ss_status capture_rk_graph(ss_ctx* c, int iters, cudaGraphExec_t* out) {
-    const int G = (int)c->groups.size();
-    TRY(ensure_branches(c));
     if (!c->rk_body) CUDA_TRY(c, cudaStreamCreateWithFlags(&c->rk_body, cudaStreamNonBlocking));
-    cudaGraph_t graph = nullptr;
-    CUDA_TRY(c, cudaStreamBeginCapture(c->cs, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = cudaSuccess;
-    if (G > 1) {
-        e = cudaEventRecord(c->branch_ev[0], c->cs);
-        for (int b = 0; b < G - 1 && e == cudaSuccess; ++b) e = cudaStreamWaitEvent(c->branch[b], c->branch_ev[0], 0);
-    }
-    for (int gi = 0; gi < G && e == cudaSuccess; ++gi) {
-        cudaStream_t st = gi == 0 ? c->cs : c->branch[gi - 1];
-        for (int i = 0; i < iters && e == cudaSuccess; ++i)
-            e = use_fp64(c) ? capture_rk_group_iteration<double>(c, c->groups[gi], st)
-                            : capture_rk_group_iteration<float>(c, c->groups[gi], st);
-    }
-    if (G > 1) {
-        for (int b = 0; b < G - 1 && e == cudaSuccess; ++b) {
-            e = cudaEventRecord(c->branch_ev[b + 1], c->branch[b]);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(c->cs, c->branch_ev[b + 1], 0);
-        }
-    }
-    const cudaError_t e_end = cudaStreamEndCapture(c->cs, &graph);
-    if (e != cudaSuccess) {
-        if (graph) cudaGraphDestroy(graph);
-        cudaGetLastError();
-        return fail(c, SS_ERR_CUDA, "Runge-Kutta graph capture: %s", cudaGetErrorString(e));
-    }
-    if (e_end != cudaSuccess) return fail(c, SS_ERR_CUDA, "Runge-Kutta graph capture: %s", cudaGetErrorString(e_end));
-    e = cudaGraphInstantiate(out, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return fail(c, SS_ERR_CUDA, "Runge-Kutta graph instantiate: %s", cudaGetErrorString(e));
-    return SS_OK;
+    return capture_branched(
+        c, "Runge-Kutta graph",
+        [&](Group& g, cudaStream_t st) {
+            cudaError_t e = cudaSuccess;
+            for (int i = 0; i < iters && e == cudaSuccess; ++i)
+                e = use_fp64(c) ? capture_rk_group_iteration<double>(c, g, st) : capture_rk_group_iteration<float>(c, g, st);
+            return e;
+        },
+        out);
 }
 
 // n_iter iterations of the adaptive integrator: per iteration every string integrates over opts.dt with
@@ -1104,15 +1123,51 @@ ss_status check_paths(ss_ctx* c, const Group& g) {
     return SS_OK;
 }
 
-// The streams and events of the graph branches (one per size group after the first).
+// The streams and events of the graph branches (one stream per size group).  The branches run at equal
+// priority: launch priorities that favour the largest group (the critical path of a batch iteration), or
+// the smallest, made the uneven study's iteration slower, not faster.
 ss_status ensure_branches(ss_ctx* c) {
     const int G = (int)c->groups.size();
     if (G > 1 && c->branch.empty()) {
-        c->branch.assign(G - 1, nullptr);
-        c->branch_ev.assign(G, nullptr);
+        c->branch.assign(G, nullptr);
+        c->branch_ev.assign(G + 1, nullptr);
         for (auto& st : c->branch) CUDA_TRY(c, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
         for (auto& ev : c->branch_ev) CUDA_TRY(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     }
+    return SS_OK;
+}
+
+// Capture into *out what issue(group, stream) launches for every size group.  With several groups each
+// group's chain is its own branch of the graph, forked from and joined back into cs, so the groups'
+// kernels overlap on the GPU instead of running one group after another (within a branch the launches
+// keep their order and programmatic dependent launch).
+template <typename F> ss_status capture_branched(ss_ctx* c, const char* what, F issue, cudaGraphExec_t* out) {
+    const int G = (int)c->groups.size();
+    TRY(ensure_branches(c));
+    cudaGraph_t graph = nullptr;
+    CUDA_TRY(c, cudaStreamBeginCapture(c->cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    if (G > 1) {
+        e = cudaEventRecord(c->branch_ev[0], c->cs);
+        for (int b = 0; b < G && e == cudaSuccess; ++b) e = cudaStreamWaitEvent(c->branch[b], c->branch_ev[0], 0);
+    }
+    for (int gi = 0; gi < G && e == cudaSuccess; ++gi) e = issue(c->groups[gi], G > 1 ? c->branch[gi] : c->cs);
+    if (G > 1) {
+        for (int b = 0; b < G && e == cudaSuccess; ++b) {
+            e = cudaEventRecord(c->branch_ev[b + 1], c->branch[b]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(c->cs, c->branch_ev[b + 1], 0);
+        }
+    }
+    const cudaError_t e_end = cudaStreamEndCapture(c->cs, &graph);
+    if (e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return fail(c, SS_ERR_CUDA, "%s capture: %s", what, cudaGetErrorString(e));
+    }
+    if (e_end != cudaSuccess) return fail(c, SS_ERR_CUDA, "%s capture: %s", what, cudaGetErrorString(e_end));
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(c, SS_ERR_CUDA, "%s instantiate: %s", what, cudaGetErrorString(e));
     return SS_OK;
 }
 
@@ -1124,46 +1179,20 @@ void drop_graphs(ss_ctx* c) {
     }
 }
 
-// Capture `iters` iterations of every size group.  With several groups each group's chain of launches is
-// its own branch of the graph (forked from and joined back into cs), so the groups' kernels overlap on
-// the GPU instead of running one group after another; within a branch the launches keep their order and
-// programmatic dependent launch.
+// Capture `iters` iterations of every size group (one graph branch per group).
 ss_status capture_graph(ss_ctx* c, int iters, cudaGraphExec_t* out) {
-    const int G = (int)c->groups.size();
-    TRY(ensure_branches(c));
-    cudaGraph_t graph = nullptr;
-    CUDA_TRY(c, cudaStreamBeginCapture(c->cs, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = cudaSuccess;
-    if (G > 1) {
-        e = cudaEventRecord(c->branch_ev[0], c->cs);
-        for (int b = 0; b < G - 1 && e == cudaSuccess; ++b) e = cudaStreamWaitEvent(c->branch[b], c->branch_ev[0], 0);
-    }
-    for (int gi = 0; gi < G && e == cudaSuccess; ++gi) {
-        cudaStream_t st = gi == 0 ? c->cs : c->branch[gi - 1];
-        for (int i = 0; i < iters; ++i) {
-            if (use_fp64(c))
-                issue_group_iteration<double>(c, c->groups[gi], st);
-            else
-                issue_group_iteration<float>(c, c->groups[gi], st);
-        }
-    }
-    if (G > 1) {
-        for (int b = 0; b < G - 1 && e == cudaSuccess; ++b) {
-            e = cudaEventRecord(c->branch_ev[b + 1], c->branch[b]);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(c->cs, c->branch_ev[b + 1], 0);
-        }
-    }
-    const cudaError_t e_end = cudaStreamEndCapture(c->cs, &graph);
-    if (e != cudaSuccess) {
-        if (graph) cudaGraphDestroy(graph);
-        return fail(c, SS_ERR_CUDA, "graph capture (branches): %s", cudaGetErrorString(e));
-    }
-    e = e_end;
-    if (e != cudaSuccess) return fail(c, SS_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
-    e = cudaGraphInstantiate(out, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return fail(c, SS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
-    return SS_OK;
+    return capture_branched(
+        c, "graph",
+        [&](Group& g, cudaStream_t st) {
+            for (int i = 0; i < iters; ++i) {
+                if (use_fp64(c))
+                    issue_group_iteration<double>(c, g, st);
+                else
+                    issue_group_iteration<float>(c, g, st);
+            }
+            return cudaGetLastError();
+        },
+        out);
 }
 
 ss_status validate_desc(const ss_string_desc& d) {
@@ -1636,13 +1665,17 @@ ss_status ss_energy_terms(ss_ctx* c, int string, double* out) {
 
 ss_status ss_time_kernels(ss_ctx* c, int reps, double* ms_out, int max_out, int* n_out) {
     if (!c || reps < 1 || !n_out) return c ? fail(c, SS_ERR_INVALID_ARG, "reps >= 1 and n_out required") : SS_ERR_INVALID_ARG;
-    if (c->integrator != SS_INT_EULER) return fail(c, SS_ERR_STATE, "kernel timing covers the Euler iteration");
     for (const Group& g : c->groups) TRY(check_paths(c, g));
+    const bool rk = c->integrator != SS_INT_EULER;
+    auto entries = [&](Group& g, int which) {
+        if (rk) return use_fp64(c) ? rk_time_entries<double>(c, g, which) : rk_time_entries<float>(c, g, which);
+        return use_fp64(c) ? time_entries<double>(c, g, which) : time_entries<float>(c, g, which);
+    };
     std::vector<int> per_group;
     int nk = 0;
     for (Group& g : c->groups) ++g.state_epoch;  // the strings advance
     for (Group& g : c->groups) {
-        per_group.push_back(use_fp64(c) ? time_entries<double>(c, g, -2) : time_entries<float>(c, g, -2));
+        per_group.push_back(entries(g, -2));
         nk += per_group.back();
     }
     *n_out = nk;
@@ -1657,10 +1690,7 @@ ss_status ss_time_kernels(ss_ctx* c, int reps, double* ms_out, int max_out, int*
             Group& g = c->groups[gi];
             for (int which = 0; which < per_group[gi]; ++which) {
                 cudaEventRecord(ev[2 * k], c->cs);
-                if (use_fp64(c))
-                    time_entries<double>(c, g, which);
-                else
-                    time_entries<float>(c, g, which);
+                entries(g, which);
                 cudaEventRecord(ev[2 * k + 1], c->cs);
                 ++k;
             }

@@ -510,16 +510,17 @@ template <typename C> __device__ __forceinline__ void f128_pass2(C (&v)[8], cons
 // an inverse read below P/2 keeps m < 4.  The twiddles of pass 1 and pass A come from the tables of
 // GroupArgs::t2x / t2y (t1 = the pass-1 half, ta = the pass-A half, indexed so that a warp's lanes read
 // consecutive entries); the ramp W_R2^j = W_P^{16 j} from the flat table tw (the same entry across a warp).
-__device__ __forceinline__ int t2_pos(int ky) { return (ky >> 4) * kT2Row + (ky & 15); }
+__device__ __forceinline__ int t2_at(int r, int c) { return r * kT2Row + c; }
+__device__ __forceinline__ int t2_pos(int ky) { return t2_at(ky >> 4, ky & 15); }
 
 // Pass 1 of a line whose upper half is zero: u[j] = x[R2 j + n2] (j < 8) on entry; writes row n2 of Z.
 template <int P, typename C>
 __device__ __forceinline__ void t2_pass1(C (&u)[8], int n2, int par, const C* __restrict__ t1, C* line) {
     if (par) mul_w16_ramp(u);
     Dft<8, C>::run(u);
-    C* z = line + n2 * kT2Row + par;
 #pragma unroll
-    for (int m = 0; m < 8; ++m) z[2 * m] = cmul(u[m], t1[(2 * m + par) * (P / 16) + n2]);  // W_P^{n2 (2m + par)}
+    for (int m = 0; m < 8; ++m)
+        line[t2_at(n2, 2 * m + par)] = cmul(u[m], t1[(2 * m + par) * (P / 16) + n2]);  // W_P^{n2 (2m + par)}
 }
 
 // The R2/2-point DFTs of pass 2 (TW_OUT = false) or pass A (TW_OUT = true) for column k1 and parity par2:
@@ -552,20 +553,18 @@ template <int P, bool TW_OUT, typename C>
 __device__ __forceinline__ void t2_cols(C* line, int k1, int par2, const C* __restrict__ tw, const C* __restrict__ ta) {
     constexpr int H = P / 32;
     C a[H];
-    const C* col = line + k1;
-    t2_col_vals<P, TW_OUT>(a, [&](int j) { return col[j * kT2Row]; }, k1, par2, tw, ta);
+    t2_col_vals<P, TW_OUT>(a, [&](int j) { return line[t2_at(j, k1)]; }, k1, par2, tw, ta);
     __syncwarp();
-    C* o = line + k1 + par2 * kT2Row;
 #pragma unroll
-    for (int m = 0; m < H; ++m) o[2 * m * kT2Row] = a[m];
+    for (int m = 0; m < H; ++m) line[t2_at(2 * m + par2, k1)] = a[m];
 }
 
 // Pass B of row y2: v[m] = Y[y2 + R2 (2m + par)] for m < 4 (the outputs below P/2).
-template <typename C> __device__ __forceinline__ void t2_passB(C (&v)[8], const C* line, int y2, int par) {
-    const C* r = line + y2 * kT2Row;
+template <typename C>
+__device__ __forceinline__ void t2_passB(C (&v)[8], const C* line, int y2, int par) {
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        const C lo = r[j], hi = r[j + 8];
+        const C lo = line[t2_at(y2, j)], hi = line[t2_at(y2, j + 8)];
         v[j] = par ? csub(lo, hi) : cadd(lo, hi);
     }
     if (par) mul_w16_ramp(v);

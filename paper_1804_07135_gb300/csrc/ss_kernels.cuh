@@ -625,7 +625,9 @@ __global__ void __launch_bounds__(kMaxThreadsYz, kMinBlocks128) yz128_kernel(Gro
 // 17-strided row layout, the z-convolution in place between them.  One shared line per (column, component,
 // layer): 3 NZ KXB lines of t2_line(P) complex elements, read from the spectrum in pass 1 and written back
 // (rows y < ny) in pass B; one shared-memory round trip per pass instead of one per Stockham stage.
-// 384 threads; pass 2 and pass A take one warp per line (16 columns x 2 parities).
+// 384 threads; pass 2 and pass A take one warp per line (16 columns x 2 parities).  Three CTAs per SM,
+// two at P = 384 (its 78 KB lines; there the kernel keeps 80 registers, which runs a batch of size groups
+// faster than three CTAs of 56 registers would, although one group alone runs faster with three).
 template <int NZ, int P>
 __device__ __forceinline__ void zconv_t2(float2* A, int kx, int Px, const float* dslab, int tid, int nthr) {
     constexpr int LS = t2_line(P), hy = P / 2, dq = P / 2 + 1;

@@ -67,3 +67,16 @@ def test_headline_is_the_largest_workload():
     keys, imgs = bench.group_keys(wl)
     assert len(keys) == 4 and sum(imgs.values()) == 640
     assert bench.oracle_sample_spec().nx == 64
+
+
+def test_selected_workload_subsets():
+    wl = bench.selected_workload(bench.HEADLINE, "192x192x8", 1)
+    assert len(wl.strings) == 1 and (wl.strings[0].nx, wl.strings[0].nz) == (192, 8)
+    assert wl.name == "uneven-study-20x32[192x192x8, 1 of 20 strings]"
+    assert bench.selected_workload(bench.HEADLINE) is bench.WORKLOADS[bench.HEADLINE]
+    assert len(bench.selected_workload("boundary-sweep-128x128x4-8x48", None, 3).strings) == 3
+    # the CPU sample's N^2 cost stays bounded: fewer images for larger lattices
+    for w in bench.WORKLOADS.values():
+        spec = bench.oracle_sample_spec(w)
+        assert spec.n_sites == min(s.n_sites for s in w.strings)
+        assert bench.oracle_sample_images(spec) * spec.n_sites ** 2 <= 8 * 16384 ** 2 * 4

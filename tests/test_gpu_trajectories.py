@@ -158,7 +158,9 @@ def test_uneven_batch_through_every_kernel_family(ss):
 
 
 @pytest.mark.parametrize("case", [(30, 120, 1, 1.0, 0.3, 0.05, 0.05, 5),   # Py = 256, nz = 1: 8 or 4 columns
-                                  (20, 90, 4, 1.0, 0.3, 0.05, 0.05, 4)])   # Py = 192, nz = 4: 2 or 1 column
+                                  (20, 90, 4, 1.0, 0.3, 0.05, 0.05, 4),    # Py = 192, nz = 4: 2 or 1 column
+                                  (12, 170, 1, 1.0, 0.3, 0.05, 0.05, 3),   # Py = 384 (XOR line layout), nz = 1
+                                  (12, 170, 4, 1.0, 0.3, 0.05, 0.05, 3)])  # Py = 384, nz = 4
 def test_yz_columns_per_cta_do_not_change_the_field(ss, case, monkeypatch):
     # the autotuner picks the two-pass y/z kernel's kx columns per CTA; every column is transformed and
     # convolved the same way whatever the count, so both counts give bit-identical fields (and the

@@ -217,9 +217,16 @@ def test_kernel_timing_follows_the_mode(ss):
         assert len(ms) == 6 and (ms > 0).all()
         sm.set_reparam(ss.SS_INTERP_LINEAR, False)
         sm.set_integrator(ss.SS_INT_DOPRI5, 1e-6, 1e-8)
-        with pytest.raises(ss.SsError) as ei:
-            sm.time_kernels(reps=2)
-        assert ei.value.status == ss.SS_ERR_STATE
+        # one attempt round: the opening, 7 stages x (assemble, xfwd, yz, xinv), finish, control, commit, arc
+        ms = sm.time_kernels(reps=2)
+        assert len(ms) == 1 + 7 * 4 + 4 and (ms > 0).all()
+        sm.set_integrator(ss.SS_INT_RKF45, 1e-6, 1e-8)
+        assert len(sm.time_kernels(reps=2)) == 1 + 6 * 4 + 4
+        # the timing leaves a unit-length path, and the integrator steps on from it
+        p = sm.get_path(0)
+        np.testing.assert_allclose(np.linalg.norm(p, axis=-1), 1.0, atol=1e-5)
+        sm.step(2)
+        assert np.isfinite(sm.get_path(0)).all()
 
 
 @pytest.mark.parametrize("K", [2, 3])
