@@ -55,10 +55,11 @@ def test_single_rank_passes_timings_through():
 
 class _Args:
     steps, warmup = 1, 0
+    workload, lattice, strings = bench.HEADLINE, None, None
 
 
 def test_reference_arm_prints_on_rank_zero_only(monkeypatch):
-    monkeypatch.setattr(bench, "cpu_oracle_sample", lambda spec, dt: (1.0, 4, 0.25))
+    monkeypatch.setattr(bench, "cpu_oracle_sample", lambda spec, dt, n_images=8: (1.0, 4, 0.25))
     buf = io.StringIO()
     with redirect_stdout(buf):
         bench.run_reference(_Args, rank=1, world=2)
