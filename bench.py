@@ -665,10 +665,12 @@ def rk_kernel_times(binding, sm, spec, kind, reps=5):
                     "may partly stay in L2, so these rates can exceed what HBM alone allows"}
 
 
-def adaptive_rk(binding, wl, stream, kind, per_iter_euler_ms, iters=10, warm=2, rtol=1e-6, atol=1e-8):
+def adaptive_rk(binding, wl, stream, kind, per_iter_euler_ms, iters=16, warm=9, rtol=1e-6, atol=1e-8):
     """Device-timed Dormand-Prince evolution of the bench workload (each iteration integrates every image
     over the workload's dt, then reparametrises): spin-updates/s counted like the Euler path (N K per
-    iteration) and force evaluations/s (7 per attempt and site-image), inputs resident."""
+    iteration) and force evaluations/s (7 per attempt and site-image), inputs resident.  The warm-up
+    (8 + 1 iterations) captures both of the integrator's graphs (8 iterations and one) before the timed
+    region, which replays the 8-iteration graph twice."""
     import torch
     spec = wl.strings[0]
     desc = (spec.nx, spec.ny, spec.nz, spec.J, spec.D, spec.K, spec.w, spec.n_images)
