@@ -1190,16 +1190,6 @@ __global__ void __launch_bounds__(kX2Threads, 3) xfwd2p_kernel(GroupArgs<float> 
     }
 }
 
-// A spectrum element read with a 128-byte L2 fetch size: the CTAs of neighbouring row blocks read
-// adjacent 32-byte pieces of each spectrum row at about the same time, so one wider DRAM fetch serves
-// several of them from L2 instead of each piece being fetched on its own.  Read-only path: the kernel
-// does not write the spectrum, and the kernel that wrote it has completed (griddep_wait).
-__device__ __forceinline__ float2 ld_spec(const float2* p) {
-    float2 v;
-    asm("ld.global.nc.L2::128B.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
-    return v;
-}
-
 // xinv: pass A straight from the spectrum (conjugated) into the transform lines, pass B into x-space
 // lines (fft_pad positions, line c * rows + yy), then the per-site work of xinv_sites in mode MODE.
 template <int P, int MODE>
@@ -1225,7 +1215,7 @@ __global__ void __launch_bounds__(kX2Threads, 3) xinv2p_kernel(GroupArgs<float> 
         if (yy >= rows) continue;
         const C* sc = inp + (size_t)c * g.nz * g.ny + yy + (size_t)k1 * kstride;
         C a[H];
-        t2_col_vals<P, true>(a, [&](int j) { return cconj(ld_spec(sc + (size_t)16 * j * kstride)); }, k1, par2, tw, ta);
+        t2_col_vals<P, true>(a, [&](int j) { return cconj(sc[(size_t)16 * j * kstride]); }, k1, par2, tw, ta);
         C* o = A + (c * ROWS + yy) * LSX + k1 + par2 * kT2Row;
 #pragma unroll
         for (int m = 0; m < H; ++m) o[2 * m * kT2Row] = a[m];
