@@ -438,6 +438,8 @@ def main():
         if rk:  # attempts of the last timed step of string 0 (set_path restarts the counts each step)
             rk_attempts = [sum(sm.integrator_state(0, k)[1:]) for k in range(wl.strings[0].n_images)]
         barrier_all()
+        one_step(paths_host)  # one untimed step of the end-to-end path (its first host upload is the slowest)
+        barrier_all()
         t_e2e = timed(paths_host, args.steps)
         barrier_all()
     step_s, e2e_s = max_over_ranks(pg, [float(np.mean(t_dev)), float(np.mean(t_e2e))], "cuda")
