@@ -1042,7 +1042,7 @@ ss_status evaluate_energies(ss_ctx* c, int gi, const Group** out) {
     Group& e = c->ev64[gi];
     if (g.eval_epoch != g.state_epoch) {
         issue_materialise<float>(c, g, c->cs);
-        launch_widen_unit((const float*)g.s, (double*)e.sp, g.n_img, g.N, c->cs);
+        launch_widen_unit((const float*)g.s, (double*)e.sp, g.n_img, g.N, nullptr, c->cs);
         issue_eval<double>(c, e, nullptr, c->cs);
         CUDA_TRY(c, cudaGetLastError());
         g.eval_epoch = g.state_epoch;
@@ -1102,7 +1102,7 @@ ss_status barrier_energies(ss_ctx* c, int gi, const std::vector<double>** out) {
                 if (k == 0 || g.direct || !(buf[(size_t)i * mk + k] + bound(k) < lo_max)) on[(img0 + k) >> 1] = 1;
         }
         CUDA_TRY(c, cudaMemcpyAsync(e.pair_on, on.data(), on.size() * sizeof(int), cudaMemcpyHostToDevice, c->cs));
-        launch_widen_unit((const float*)g.s, (double*)e.sp, g.n_img, g.N, c->cs);
+        launch_widen_unit((const float*)g.s, (double*)e.sp, g.n_img, g.N, e.pair_on, c->cs);
         issue_eval<double>(c, e, nullptr, c->cs, e.pair_on);
         CUDA_TRY(c, cudaGetLastError());
         CUDA_TRY(c, cudaMemcpyAsync(buf.data(), e.eval_E, buf.size() * sizeof(double), cudaMemcpyDeviceToHost, c->cs));

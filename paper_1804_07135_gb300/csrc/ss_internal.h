@@ -267,7 +267,7 @@ template <typename T, typename Tout>
 void launch_soa_to_aos(const T* src, Tout* dst, int K, int N, Tout scale, cudaStream_t st);
 void launch_interp_identity(InterpEntry* tab, int img0, int K, cudaStream_t st);
 // the FP32 state [K][3][N] handed to the FP64 energy evaluation: every spin renormalised in FP64
-void launch_widen_unit(const float* src, double* dst, int K, int N, cudaStream_t st);
+void launch_widen_unit(const float* src, double* dst, int K, int N, const int* pair_on, cudaStream_t st);
 // FP64 setup of the dipole-tensor spectrum: x then y transforms of the padded real-space tensor
 // (data [6*nz][Py][Px] complex, in place), then the octant extraction into dhat.
 void launch_fft_strided_f64(double2* data, const double2* tw, const FftPlan& plan, int n_lines, long elem_stride,

@@ -2233,15 +2233,19 @@ __global__ void extract_octant_kernel(const double2* spec, T* dhat, int Px, int 
 }
 
 #ifdef SS_COMMON_LAUNCHERS
-// [K][3][N] FP32 spins -> the same spins renormalised in FP64 (the dipole convolution of the FP64
-// evaluation then sees unit vectors, as the local terms do)
-__global__ void widen_unit_kernel(const float* __restrict__ src, double* __restrict__ dst, int K, int N) {
-    const size_t total = (size_t)K * N;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t k = i / N, n = i - k * N, b = k * 3 * N + n;
+// grid (site tiles of 256, images): [K][3][N] FP32 spins -> the same spins renormalised in FP64 (the
+// dipole convolution of the FP64 evaluation then sees unit vectors, as the local terms do); with pair_on,
+// only the images of the flagged pairs (the ones the evaluation computes)
+__global__ void widen_unit_kernel(const float* __restrict__ src, double* __restrict__ dst, int K, int N,
+                                  const int* __restrict__ pair_on) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    for (int k = blockIdx.y; k < K; k += gridDim.y) {
+        if (pair_on && !pair_on[k >> 1]) continue;  // uniform over the CTA
+        const size_t b = (size_t)k * 3 * N + n;
         const double a0 = src[b], a1 = src[b + N], a2 = src[b + 2 * (size_t)N];
         const double n2 = a0 * a0 + a1 * a1 + a2 * a2;
-        const double r = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
+        const double r = n2 > 0.0 ? rsqrt_nr(n2) : 0.0;
         dst[b] = a0 * r;
         dst[b + N] = a1 * r;
         dst[b + 2 * (size_t)N] = a2 * r;
@@ -2715,8 +2719,8 @@ void launch_interp_identity(InterpEntry* tab, int img0, int K, cudaStream_t st) 
     interp_identity_kernel<<<(K + 127) / 128, 128, 0, st>>>(tab, img0, K);
 }
 
-void launch_widen_unit(const float* src, double* dst, int K, int N, cudaStream_t st) {
-    widen_unit_kernel<<<grid1d((size_t)K * N, 256), 256, 0, st>>>(src, dst, K, N);
+void launch_widen_unit(const float* src, double* dst, int K, int N, const int* pair_on, cudaStream_t st) {
+    widen_unit_kernel<<<dim3((N + 255) / 256, std::min(K, 65535)), 256, 0, st>>>(src, dst, K, N, pair_on);
 }
 #endif
 
