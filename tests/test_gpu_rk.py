@@ -189,3 +189,24 @@ def test_rkf45_against_oracle(ss, prec, per_image):
     # the pairs differ: Dormand-Prince takes another step sequence on the same problem
     _, _, _, counts_dp = oracle.string_run_rk(_model(c), _unit(start), n_iter, T, rtol, atol, per_image=per_image)
     assert not np.array_equal(np.asarray(counts_dp).reshape(-1, 2), np.asarray(counts_ref).reshape(-1, 2))
+
+
+def test_dopri5_with_direct_dipole_sums(ss):
+    # the attempt rounds of the graph's WHILE node with the direct O(N^2) dipole sums in place of the FFT
+    # convolution (SS_DIPOLE_DIRECT): attempt counts and path as the oracle's, which sums directly too;
+    # 9 iterations run the 8-iteration graph and the one-iteration graph
+    spec = W.tiny_bloch().strings[0]
+    c = _case(spec)
+    T, n_iter, rtol, atol = 0.5, 9, 1e-6, 1e-8
+    with ss.StringMethod([c], dt=T, precision=FP64, dipole=ss.SS_DIPOLE_DIRECT) as sm:
+        sm.set_integrator(ss.SS_INT_DOPRI5, rtol, atol)
+        sm.set_path(0, spec.initial_path())
+        start = sm.get_path(0)
+        sm.step(n_iter)
+        got, (step, acc, rej) = sm.get_path(0), sm.integrator_state(0)
+        # the round's kernels one by one: the direct sums take the y/z entry's place in every stage
+        assert len(sm.time_kernels(reps=1)) == 1 + 7 * 4 + 4
+    ref, _, step_ref, counts_ref = oracle.string_run_rk(_model(c), _unit(start), n_iter, T, rtol, atol)
+    assert (acc, rej) == counts_ref
+    assert abs(step - step_ref) <= 1e-9 * step_ref
+    assert np.abs(got - ref).max() < 1e-10
